@@ -1,0 +1,378 @@
+"""O2 -- the paper's mapping method, step by step, on dense FP64 arrays.
+
+Steps, in the paper's order (single mode in the main text, multimode in Sec. S1):
+  1. normal-ordered coefficients f_{k,l} of A(0) (Eq. 2): solved from A's number-basis
+     elements with the plain matrix elements <k'|(a^dag)^k a^l|l'> (``f_from_fock``);
+  2. transformed coefficients g_{k,l} = sum_j r^-j/j! f_{k-j,l-j}, r = 1 (Eq. 6);
+  3. one separable initial condition x^p y^q per non-negligible g_{p,q}(0) (Eqs. 10, 13);
+  4. the separation constant C of Eq. 304 per initial condition;
+  5. classical RK4 on the coupled system (Eqs. 9a-c, network form Eqs. 303a-c):
+        dG_x/dt = (O_x + C) G_x,  dG_y/dt = (O_y - C) G_y,
+        dR/dt   = (O_x + O_y + S) R + S(G_x G_y),
+     where, for A -> G, left multiplication of A by a^dag acts as x, by a as d/dx, and
+     right multiplication by a acts as y, by a^dag as d/dy (the variable/derivative
+     assignment of Eqs. 5, 9a, 9b and S7), so that
+        O_x = i :H(x, d/dx): - 1/2 sum_n kappa_n [L_n^dag L_n]_left,
+        O_y = -i :H(d/dy, y): - 1/2 sum_n kappa_n [L_n^dag L_n]_right,
+        S(G) = sum_n kappa_n [L_n^dag]_left [L_n]_right G   (the sandwich term);
+     each of x, d/dx, y, d/dy is a matrix on the monomial basis {x^k} truncated at M
+     (coefficients with an index >= M are zero), products are formed at a padded size
+     and then truncated (the same compression as O1's);
+  6. reconstruction of f(t) by Eq. 11 and of A(t)'s number-basis elements by Eq. 2.
+
+Parity status (tests/test_oracle_mapping.py):
+  * f_from_fock / g_from_f / f_from_g / fock_from_f: pinned by brute force against
+    explicit matrix products of (a^dag)^k a^l and by the identity T_{k,l} = sqrt(k! l!)|k><l|
+    checked numerically at N <= 8 (Eq. 8 summed with a padded truncation).
+  * separation_constant: pinned against a direct numerical minimisation of the functional
+    quoted with Eq. 304 for the uncoupled oscillator.
+  * left/right/sandwich operators + RK4: pinned by (a) the exact G(x,y,t) of a damped
+    Kerr oscillator measured on |m><m| (derived from Eq. 313 / S-eq. 315 reasoning for the
+    standard dissipator), (b) R == 0 for a closed system (Eq. 9c with kappa = 0), (c) the
+    'all in R' run, which is the linear RK4 on G and equals O1 (similarity by
+    diag(sqrt k!)) to rounding, (d) fourth-order convergence of the separated run to O1.
+"""
+
+from __future__ import annotations
+
+import math
+from functools import reduce
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+import scipy.linalg
+
+from workloads.spec import Problem
+from .channels import stage_value
+from .fock import _max_degree, restrict
+
+
+# ---------------------------------------------------------------------------------------
+# Monomial-basis matrices for multiplication by x and differentiation d/dx.
+# ---------------------------------------------------------------------------------------
+
+def x_matrix(P: int) -> np.ndarray:
+    """(x c)_k = c_{k-1}: multiplication of sum_k c_k x^k by x."""
+    X = np.zeros((P, P), dtype=np.complex128)
+    for k in range(1, P):
+        X[k, k - 1] = 1.0
+    return X
+
+
+def d_matrix(P: int) -> np.ndarray:
+    """(d/dx c)_k = (k+1) c_{k+1}."""
+    D = np.zeros((P, P), dtype=np.complex128)
+    for k in range(P - 1):
+        D[k, k + 1] = k + 1.0
+    return D
+
+
+def left_of(u: Sequence[int], v: Sequence[int], dims: Sequence[int]) -> np.ndarray:
+    """Left multiplication by prod_j (a_j^dag)^u_j a_j^v_j -> prod_j x_j^u_j (d/dx_j)^v_j."""
+    mats = [np.linalg.matrix_power(x_matrix(P), uj) @ np.linalg.matrix_power(d_matrix(P), vj)
+            for uj, vj, P in zip(u, v, dims)]
+    return reduce(np.kron, mats)
+
+
+def right_of(u: Sequence[int], v: Sequence[int], dims: Sequence[int]) -> np.ndarray:
+    """Right multiplication A -> A prod_j (a_j^dag)^u_j a_j^v_j -> prod_j y_j^v_j (d/dy_j)^u_j
+    (first u_j right-multiplications by a^dag, i.e. d/dy, then v_j by a, i.e. y)."""
+    mats = [np.linalg.matrix_power(x_matrix(P), vj) @ np.linalg.matrix_power(d_matrix(P), uj)
+            for uj, vj, P in zip(u, v, dims)]
+    return reduce(np.kron, mats)
+
+
+# ---------------------------------------------------------------------------------------
+# Coefficient maps: number basis <-> f (Eq. 2) <-> g (Eqs. 6, 11), r = 1.
+# Arrays have shape (M_1..M_n, M_1..M_n): x-indices first, y-indices second.
+# ---------------------------------------------------------------------------------------
+
+def _pair_axes(n_modes: int, d: int) -> Tuple[int, int]:
+    return d, n_modes + d
+
+
+def _diag_pair_sum(arr: np.ndarray, n_modes: int, d: int, coef) -> np.ndarray:
+    """out[.., k_d, .., l_d, ..] = sum_{j>=0} coef(j) arr[.., k_d - j, .., l_d - j, ..]."""
+    ak, al = _pair_axes(n_modes, d)
+    M = arr.shape[ak]
+    out = np.zeros_like(arr)
+    for j in range(M):
+        c = coef(j)
+        if c == 0.0:
+            continue
+        src = [slice(None)] * arr.ndim
+        dst = [slice(None)] * arr.ndim
+        src[ak] = slice(0, M - j)
+        src[al] = slice(0, arr.shape[al] - j)
+        dst[ak] = slice(j, M)
+        dst[al] = slice(j, arr.shape[al])
+        out[tuple(dst)] += c * arr[tuple(src)]
+    return out
+
+
+def g_from_f(f: np.ndarray, n_modes: int) -> np.ndarray:
+    """Eq. 6 with r = 1: g_{k,l} = sum_j f_{k-j,l-j} / j!  (per mode)."""
+    g = f
+    for d in range(n_modes):
+        g = _diag_pair_sum(g, n_modes, d, lambda j: 1.0 / math.factorial(j))
+    return g
+
+
+def f_from_g(g: np.ndarray, n_modes: int) -> np.ndarray:
+    """Eq. 11 (single reconstruction): f_{k,l} = sum_j (-1)^j / j! g_{k-j,l-j}  (per mode)."""
+    f = g
+    for d in range(n_modes):
+        f = _diag_pair_sum(f, n_modes, d, lambda j: (-1.0) ** j / math.factorial(j))
+    return f
+
+
+def _monomial_element_table(M: int) -> np.ndarray:
+    """W[k', l', k, l] = <k'|(a^dag)^k a^l|l'> on a single mode, from explicit matrix powers."""
+    P = 2 * M + 2
+    a = np.zeros((P, P))
+    for k in range(1, P):
+        a[k - 1, k] = math.sqrt(k)
+    ad = a.T
+    W = np.zeros((M, M, M, M))
+    apow = [np.eye(P)]
+    adpow = [np.eye(P)]
+    for _ in range(M):
+        apow.append(apow[-1] @ a)
+        adpow.append(adpow[-1] @ ad)
+    for k in range(M):
+        for l in range(M):
+            W[:, :, k, l] = (adpow[k] @ apow[l])[:M, :M]
+    return W
+
+
+def fock_from_f(f: np.ndarray, n_modes: int) -> np.ndarray:
+    """<k'|A|l'> = sum_{k,l} f_{k,l} <k'|prod (a^dag)^k a^l|l'>  (Eq. 2, applied per mode)."""
+    A = f.astype(np.complex128)
+    for d in range(n_modes):
+        M = A.shape[d]
+        W = _monomial_element_table(M)
+        ak, al = _pair_axes(n_modes, d)
+        A = np.moveaxis(A, (ak, al), (0, 1))
+        A = np.tensordot(W, A, axes=([2, 3], [0, 1]))
+        A = np.moveaxis(A, (0, 1), (ak, al))
+    return A
+
+
+def f_from_fock(A: np.ndarray, n_modes: int) -> np.ndarray:
+    """Inverse of ``fock_from_f``: solve Eq. 2's matrix-element equations mode by mode.
+
+    <k'|(a^dag)^k a^l|l'> vanishes unless k' - k = l' - l >= 0, so along every diagonal
+    chain (k', k' + d) the system is lower triangular; each chain is solved with
+    scipy.linalg.solve_triangular on the matrix elements from ``_monomial_element_table``."""
+    f = A.astype(np.complex128)
+    for d in range(n_modes):
+        M = f.shape[d]
+        W = _monomial_element_table(M)
+        ak, al = _pair_axes(n_modes, d)
+        f = np.moveaxis(f, (ak, al), (0, 1))
+        out = np.zeros_like(f)
+        for off in range(-(M - 1), M):
+            ks = [k for k in range(M) if 0 <= k + off < M]
+            L = np.array([[W[k1, k1 + off, k2, k2 + off] for k2 in ks] for k1 in ks])
+            rhs = np.stack([f[k, k + off] for k in ks]).reshape(len(ks), -1)
+            sol = scipy.linalg.solve_triangular(L, rhs, lower=True)
+            for i, k in enumerate(ks):
+                out[k, k + off] = sol[i].reshape(f.shape[2:])
+        f = np.moveaxis(out, (0, 1), (ak, al))
+    return f
+
+
+def fock_array(elems, M: Sequence[int]) -> np.ndarray:
+    """Number-basis elements {(k, l): v} as an array of shape (M..., M...)."""
+    A = np.zeros(tuple(M) + tuple(M), dtype=np.complex128)
+    for (k, l), val in elems.items():
+        if all(a < m for a, m in zip(k, M)) and all(b < m for b, m in zip(l, M)):
+            A[tuple(k) + tuple(l)] += val
+    return A
+
+
+# ---------------------------------------------------------------------------------------
+# Initial conditions and separation constant.
+# ---------------------------------------------------------------------------------------
+
+def initial_conditions(g0: np.ndarray, n_modes: int, rel_tol: float = 1e-12):
+    """Eqs. 10 / 13: one separable G^(p,q)(0) = x^p y^q per non-negligible g_{p,q}(0).
+
+    'Non-negligible' (summary step (ii) of the method) is read as |g| > rel_tol * max|g|;
+    the returned list holds (p, q, weight g_{p,q}(0))."""
+    mx = np.max(np.abs(g0)) if g0.size else 0.0
+    out = []
+    for idx in zip(*np.nonzero(np.abs(g0) > rel_tol * mx)):
+        idx = tuple(int(i) for i in idx)
+        out.append((idx[:n_modes], idx[n_modes:], complex(g0[idx])))
+    return out
+
+
+def omega_eta(problem: Problem) -> Tuple[List[float], List[float]]:
+    """omega_j (static coefficient of a_j^dag a_j) and eta_j (of a_j^dag^2 a_j^2) of H."""
+    n = problem.n_modes
+    om = [0.0] * n
+    et = [0.0] * n
+    for t in problem.h_terms:
+        if t.channel >= 0:
+            continue
+        c = complex(t.coef) * (problem.params[t.param] if t.param >= 0 else 1.0)
+        nz = [j for j in range(n) if t.u[j] or t.v[j]]
+        if len(nz) != 1:
+            continue
+        j = nz[0]
+        if t.u[j] == 1 and t.v[j] == 1:
+            om[j] += c.real
+        elif t.u[j] == 2 and t.v[j] == 2:
+            et[j] += c.real
+    return om, et
+
+
+def separation_constant(problem: Problem, p: Sequence[int], q: Sequence[int]) -> complex:
+    """Eq. 304: C = -(i/2) sum_j [ (omega_j - eta_j)(p_j + q_j) + eta_j (p_j^2 + q_j^2) ]."""
+    om, et = omega_eta(problem)
+    s = 0.0
+    for j in range(problem.n_modes):
+        s += (om[j] - et[j]) * (p[j] + q[j]) + et[j] * (p[j] ** 2 + q[j] ** 2)
+    return -0.5j * s
+
+
+# ---------------------------------------------------------------------------------------
+# Generator of the coupled system.
+# ---------------------------------------------------------------------------------------
+
+class MappedModel:
+    def __init__(self, problem: Problem, M: Optional[Sequence[int]] = None):
+        self.p = problem
+        self.M = tuple(M if M is not None else problem.N)
+        n = problem.n_modes
+        pad = 2 * _max_degree(problem) + 2
+        big = tuple(m + pad for m in self.M)
+        self.dim = int(np.prod(self.M))
+
+        def r(m):
+            return restrict(m, big, self.M)
+
+        d = self.dim
+        self.Ox = np.zeros((d, d), dtype=np.complex128)
+        self.Oy = np.zeros((d, d), dtype=np.complex128)
+        self.dyn = []  # (left, right, channel, conj, coef)
+        for t in problem.h_terms:
+            c = complex(t.coef) * (problem.params[t.param] if t.param >= 0 else 1.0)
+            lo = r(left_of(t.u, t.v, big))
+            ro = r(right_of(t.u, t.v, big))
+            if t.channel < 0:
+                self.Ox += 1j * c * lo
+                self.Oy += -1j * c * ro
+            else:
+                self.dyn.append((lo, ro, t.channel, t.conj, c))
+        self.sandwich = []  # (kappa, [L^dag]_left, [L]_right)
+        for jmp in problem.jumps:
+            Ld_left = sum(np.conj(c) * left_of(v, u, big) for c, u, v in jmp.terms)
+            L_left = sum(c * left_of(u, v, big) for c, u, v in jmp.terms)
+            L_right = sum(c * right_of(u, v, big) for c, u, v in jmp.terms)
+            Ld_right = sum(np.conj(c) * right_of(v, u, big) for c, u, v in jmp.terms)
+            self.Ox += -0.5 * jmp.rate * r(Ld_left @ L_left)
+            # A L^dag L = (A L^dag) L: apply [L^dag]_right first, then [L]_right
+            self.Oy += -0.5 * jmp.rate * r(L_right @ Ld_right)
+            self.sandwich.append((jmp.rate, r(Ld_left), r(L_right)))
+        del n
+
+    def operators(self, tau_step: float, c: float, dt: float):
+        p = self.p
+        Ox = self.Ox.copy()
+        Oy = self.Oy.copy()
+        for lo, ro, ch, conj, coef in self.dyn:
+            e = stage_value(p.channels[ch], tau_step, c, dt, p.T, p.reverse_time)
+            h = coef * (np.conj(e) if conj else e)
+            Ox += 1j * h * lo
+            Oy += -1j * h * ro
+        return Ox, Oy
+
+    def rhs(self, Gx, Gy, R, Ox, Oy, C, r_layout: str):
+        dGx = Ox @ Gx + C * Gx
+        dGy = Oy @ Gy - C * Gy
+        if r_layout == "off":
+            return dGx, dGy, np.zeros_like(R)
+        dR = Ox @ R + R @ Oy.T
+        for kappa, Ld_l, L_r in self.sandwich:
+            dR += kappa * (Ld_l @ R @ L_r.T)
+            dR += kappa * np.outer(Ld_l @ Gx, L_r @ Gy)
+        return dGx, dGy, dR
+
+
+class MappedRun:
+    """Result of ``rk4_mapped``: per-IC (p, q, weight, C, Gx, Gy, R)."""
+
+    def __init__(self, model: MappedModel, ics):
+        self.model = model
+        self.ics = ics
+
+    def g_total(self) -> np.ndarray:
+        M = self.model.M
+        d = self.model.dim
+        G = np.zeros((d, d), dtype=np.complex128)
+        for p, q, w, C, Gx, Gy, R in self.ics:
+            G += w * (np.outer(Gx, Gy) + R)
+        return G.reshape(tuple(M) + tuple(M))
+
+    def fock(self) -> np.ndarray:
+        """A(t) in the number basis (shape (M..., M...)) via Eq. 11 then Eq. 2."""
+        n = self.model.p.n_modes
+        return fock_from_f(f_from_g(self.g_total(), n), n)
+
+    def fock_matrix(self) -> np.ndarray:
+        d = self.model.dim
+        return self.fock().reshape(d, d)
+
+
+def map_initial(problem: Problem, M: Optional[Sequence[int]] = None):
+    """Steps 1-3: g(0) of the measured operator (truncated at M) and its IC list."""
+    M = tuple(M if M is not None else problem.N)
+    A0 = fock_array(problem.measured, M)
+    g0 = g_from_f(f_from_fock(A0, problem.n_modes), problem.n_modes)
+    return g0, initial_conditions(g0, problem.n_modes)
+
+
+def rk4_mapped(problem: Problem, M: Optional[Sequence[int]] = None, n_steps: Optional[int] = None,
+               r_layout: str = "full", C_override=None, all_in_R: bool = False) -> MappedRun:
+    """Integrate Eqs. 9a-c for every initial condition with classical RK4.
+
+    ``C_override``: use this separation constant for every IC instead of Eq. 304.
+    ``all_in_R``:   start from G_x = G_y = 0, R = x^p y^q (a pin: then the run is RK4 on G)."""
+    model = MappedModel(problem, M)
+    g0, ics0 = map_initial(problem, model.M)
+    d = model.dim
+    dt = problem.dt
+    steps = problem.n_steps if n_steps is None else n_steps
+    states = []
+    for p, q, w in ics0:
+        C = separation_constant(problem, p, q) if C_override is None else complex(C_override)
+        ip = int(np.ravel_multi_index(p, model.M))
+        iq = int(np.ravel_multi_index(q, model.M))
+        Gx = np.zeros(d, dtype=np.complex128)
+        Gy = np.zeros(d, dtype=np.complex128)
+        R = np.zeros((d, d), dtype=np.complex128)
+        if all_in_R:
+            R[ip, iq] = 1.0
+        else:
+            Gx[ip] = 1.0
+            Gy[iq] = 1.0
+        states.append([p, q, w, C, Gx, Gy, R])
+    for n in range(steps):
+        tau = n * dt
+        O1 = model.operators(tau, 0.0, dt)
+        O2 = model.operators(tau, 0.5, dt)
+        O4 = model.operators(tau, 1.0, dt)
+        for st in states:
+            C, y = st[3], (st[4], st[5], st[6])
+            k1 = model.rhs(*y, *O1, C, r_layout)
+            u = tuple(a + 0.5 * dt * b for a, b in zip(y, k1))
+            k2 = model.rhs(*u, *O2, C, r_layout)
+            u = tuple(a + 0.5 * dt * b for a, b in zip(y, k2))
+            k3 = model.rhs(*u, *O2, C, r_layout)
+            u = tuple(a + dt * b for a, b in zip(y, k3))
+            k4 = model.rhs(*u, *O4, C, r_layout)
+            st[4], st[5], st[6] = tuple(a + (dt / 6.0) * (b1 + 2.0 * b2 + 2.0 * b3 + b4)
+                                        for a, b1, b2, b3, b4 in zip(y, k1, k2, k3, k4))
+    return MappedRun(model, [tuple(s) for s in states])
