@@ -1,0 +1,303 @@
+"""Benchmark of the mapped adjoint-Lindblad solver on GB300.
+
+Default workload (N = 1 GPU): a batch of driven, damped Kerr oscillators drawn from the
+seeded 4096-instance distribution (``workloads.configs.kerr_batch``: Delta, K, gamma, drive
+peak, measured level n in {0,1,2}, truncation N in 10..40), scaled to 65 536 instances so
+that the state (4 arrays x ~0.4 GB in complex FP32) is far larger than the 129 MB L2 and
+the fused RK4 stage kernel streams from HBM.  One bench *step* is one classical RK4 time
+step (dt = 0.002 ns; four fused stage kernels: drive envelopes, stencils, separable
+source, RK4 combine) of every instance followed by the per-instance observable
+Tr(rho0 A) (warp reductions).  ``value`` = grid-point RK-stage updates per second.
+
+Other keys: ``roofline`` (the stage kernel against the measured HBM copy bandwidth),
+``e2e`` (the same step through the C ABI with the state loaded from pinned host memory
+and the observables read back every step), ``cpu_baseline`` (the FP64 oracle timed on a
+bounded sample of the same workload on the host cores), ``clocks`` (nvidia-smi sampled
+during the timed region), ``gpu_launches`` (library kernel launches in the timed region).
+
+``--impl reference`` times the oracle (the plain FP64 CPU implementation) on the same
+workload, each step a bounded sample.  Multi-GPU: every rank solves its own shard of
+independent instances (replicas, weak scaling); no collective is on the data path.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "grid-point RK-stage updates/s"
+DT = 0.002
+HORIZON = 100.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--instances", type=int, default=65536, help="instances per GPU")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(n_inst: int, rank: int):
+    """Instances of this rank: the seeded stream of kerr_batch, rank-major shards."""
+    from workloads import configs
+    allp = configs.kerr_batch(B=n_inst * (rank + 1), T=HORIZON, dt=DT)
+    return allp[n_inst * rank:]
+
+
+def points_of(specs):
+    """(R + G_x + G_y) grid points per instance (grid = Fock truncation)."""
+    tot = 0
+    for p in specs:
+        n = p.N[0]
+        tot += n * n + 2 * n
+    return tot
+
+
+def cpu_baseline(specs, budget_s: float = 12.0):
+    """The FP64 oracle (oracle.mapping.rk4_mapped) on a bounded sample: instances taken in
+    order, 100 RK4 steps each, until ~budget_s of CPU time; single thread."""
+    try:
+        from threadpoolctl import threadpool_limits
+        ctx = threadpool_limits(1)
+    except Exception:  # noqa: BLE001
+        ctx = None
+    from oracle import mapping
+    n_steps = 100
+    done_pts = 0
+    done_inst = 0
+    t0 = time.perf_counter()
+    for p in specs:
+        mapping.rk4_mapped(p, n_steps=n_steps)
+        done_pts += points_of([p]) * 4 * n_steps
+        done_inst += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    if ctx is not None:
+        ctx.unregister() if hasattr(ctx, "unregister") else None
+    return {"value": done_pts / el, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{done_inst} instances x {n_steps} RK4 steps (FP64, numpy, 1 thread), {el:.1f} s"}
+
+
+class Clocks:
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile(prefix="clk", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self, gpu: int):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_reference(args, rank, world):
+    """Oracle arm: rank 0 only, bounded samples of the same workload on the host cores."""
+    if rank != 0:
+        return
+    specs = workload(args.instances, 0)
+    n_steps = 20
+    per_step_inst = 2
+
+    def one(i):
+        from oracle import mapping
+        sel = specs[(i * per_step_inst) % len(specs):][:per_step_inst]
+        t0 = time.perf_counter()
+        for p in sel:
+            mapping.rk4_mapped(p, n_steps=n_steps)
+        return points_of(sel) * 4 * n_steps, time.perf_counter() - t0
+
+    for i in range(args.warmup):
+        one(i)
+    pts, el = 0, 0.0
+    for i in range(args.steps):
+        a, b = one(args.warmup + i)
+        pts += a
+        el += b
+    v = pts / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"kerr_batch x{args.instances} (driven damped Kerr, seed 20220311)",
+                                           "instances": args.instances, "dt_ns": DT},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step_inst} instances x {n_steps} RK4 steps per step"},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2203_05526_gb300 as bq
+    from paper_2203_05526_gb300 import build
+    build.build()
+    specs = workload(args.instances, rank)
+    handles = [bq.problem_from_spec(p) for p in specs]
+    opts = bq.map_opts(method="mapped", dtype=args.dtype, horizon=HORIZON, dt=DT)
+    state = bq.State(handles, opts)
+    pts = points_of(specs)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region --------------------------------------------------
+    for _ in range(args.warmup):
+        state.step(DT, 1)
+        state.evaluate()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = Clocks()
+    clk.start(local)
+    barrier()
+    n_launch0 = bq.launch_count()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        state.step(DT, 1)
+        ev[i][1].record(stream)
+        obs = state.evaluate()
+    t1.record(stream)
+    barrier()
+    launches = bq.launch_count() - n_launch0
+    clocks = clk.stop()
+    ms = t0.elapsed_time(t1)
+    stage_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    assert np.all(np.isfinite(obs))
+    upd_per_step = 4 * pts
+    value = world * upd_per_step * args.steps / (ms / 1e3)
+
+    # roofline of the fused stage kernel: algorithmic bytes = 16 array transfers per RK4 step
+    # per grid point (stage 1: 3, stages 2-3: 5, stage 4: 3), i.e. 4 per stage-launch
+    csz = 8 if args.dtype == "f32" else 16
+    bytes_per_launch = 4 * csz * pts
+    launch_s = stage_ms / 1e3 / (4 * args.steps)
+    achieved = bytes_per_launch / launch_s / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:  # noqa: BLE001
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "bq::k_stage", "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "bytes_per_launch": bytes_per_launch, "avg_launch_us": launch_s * 1e6}
+
+    # ---- end to end through the C ABI: state from pinned host memory, observables back ---
+    nbytes = state.state_bytes()
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    state.store_state(host.data_ptr())
+    torch.cuda.synchronize()
+    for _ in range(2):
+        state.load_state(host.data_ptr())
+        state.step(DT, 1)
+        state.evaluate()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        state.load_state(host.data_ptr())
+        state.step(DT, 1)
+        state.evaluate()  # device -> host read of every instance's observable
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e = {"value": world * upd_per_step * args.steps / (e2e_ms / 1e3), "unit": METRIC,
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 16 * len(specs)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(specs)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c" + args.dtype,
+                "data": "synthetic (seeded kerr_batch distribution)",
+                "config": {"workload": f"kerr_batch x{args.instances}: driven damped Kerr oscillators, "
+                                       f"mapped method (G_x, G_y, full R), one RK4 step of dt={DT} ns + "
+                                       "Tr(rho0 A) per instance per step",
+                           "instances_per_gpu": args.instances, "grid_points_per_gpu": pts,
+                           "state_bytes_per_array": nbytes, "l2": "inputs larger than L2 (4 arrays x "
+                           f"{nbytes / 1e6:.0f} MB vs 129 MB)", "parallelism": f"replicas x{world}"},
+                "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * bq.h -- C ABI of the GB300 solver for the mapped adjoint Lindblad equation
+ * (Makinen et al., "Efficient classical simulation of open bosonic quantum systems").
+ *
+ * The library integrates the adjoint (Heisenberg-picture) master equation of a measured
+ * operator A (Eq. 3) after the paper's mapping of A to generating functions (Eqs. 5-8):
+ * every separable initial condition G^(p,q)(0) = x^p y^q (Eqs. 10, 13) is evolved as the
+ * coupled system G = G_x G_y + R (Eqs. 9a-c, network form Eqs. 303a-c) with classical RK4,
+ * one fused CUDA kernel per RK4 stage.  It also carries the "conventional" direct
+ * number-basis integration of Eq. 3 for the paper's comparison.
+ *
+ * Conventions
+ *   - Every function returns an int status: BQ_OK (0) or a negative BQ_E* code.  A
+ *     human-readable detail of the last failure on the calling thread is returned by
+ *     bq_last_error().  No function aborts the process.
+ *   - Problems (bq_problem) and states (bq_state) are opaque, library-owned host handles.
+ *   - Device memory is caller-owned: bq_map() carves everything it needs (tables,
+ *     state, RK4 scratch) out of one caller-provided device buffer and never frees it.
+ *   - Device work is enqueued asynchronously on the caller's CUDA stream (a
+ *     cudaStream_t passed as void*, NULL = legacy default stream).  Functions that return
+ *     host data synchronise that stream.
+ *   - Operators are normal-ordered monomials prod_j (a_j^dag)^u_j a_j^v_j given by the
+ *     power arrays u, v of length n_modes (Eq. 1 / Eq. S1, o1 = a^dag, o2 = a, r = 1).
+ *   - Time is in ns, angular frequencies in rad/ns.
+ *   - There is no CPU fallback: every step of the path runs in this library's kernels.
+ */
+#ifndef BQ_H_
+#define BQ_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define BQ_OK 0
+#define BQ_EINVAL (-1)        /* bad argument (sizes, indices, non-Hermitian H, ...)   */
+#define BQ_EUNSTABLE_DT (-2)  /* dt above the RK4 imaginary-axis stability bound        */
+#define BQ_ENOMEM (-3)        /* caller's device buffer too small                      */
+#define BQ_ECUDA (-4)         /* a CUDA runtime call failed (detail in bq_last_error)  */
+#define BQ_ENONFINITE (-5)    /* NaN/Inf detected in a result                          */
+#define BQ_ETIMEOUT (-6)      /* a bounded device wait gave up                         */
+#define BQ_EUNSUPPORTED (-7)  /* valid request outside this build's limits             */
+
+/* ---- enums ------------------------------------------------------------------------ */
+/* Channel (drive envelope) kinds, Eq. 301's time dependence.  Parameters:
+ *   CONST: (re, im)                      value re + i im
+ *   GAUSS: (amp_re, amp_im, t0, sigma)   amp exp(-(t - t0)^2 / (2 sigma^2))
+ *   PWC:   (t_start, seg_len, re_0, im_0, re_1, im_1, ...)  piecewise constant
+ *   CEXP:  (amp_re, amp_im, omega)       amp exp(i omega t)
+ * Smooth kinds are evaluated at every RK4 stage time; PWC at the midpoint of each step
+ * (the Hamiltonian is held constant within a step).  With reverse_time the physical time
+ * of integration time tau is t = horizon - tau (Heisenberg picture of a time-dependent
+ * Hamiltonian); otherwise t = tau. */
+enum { BQ_CH_CONST = 0, BQ_CH_GAUSS = 1, BQ_CH_PWC = 2, BQ_CH_CEXP = 3 };
+
+enum { BQ_METHOD_MAPPED = 0, BQ_METHOD_DIRECT = 1 };
+enum { BQ_F64 = 0, BQ_F32 = 1 };
+enum { BQ_R_FULL = 0, BQ_R_OFF = 1 };
+/* Storage basis of the coefficients: MONOMIAL stores g_{k,l} as in Eq. 6; NUMBER stores
+ * sqrt(k! l!) g_{k,l} (a diagonal similarity, exact in exact arithmetic; keeps FP32 in
+ * range for large truncations).  AUTO = MONOMIAL for F64 mapped, NUMBER otherwise. */
+enum { BQ_BASIS_AUTO = 0, BQ_BASIS_MONOMIAL = 1, BQ_BASIS_NUMBER = 2 };
+enum { BQ_C_EQ304 = 0, BQ_C_ZERO = 1 };
+
+#define BQ_MAX_MODES 3
+
+typedef struct bq_problem bq_problem;
+typedef struct bq_state bq_state;
+
+typedef struct bq_map_opts {
+  int method;        /* BQ_METHOD_*                                                     */
+  int dtype;         /* BQ_F64 | BQ_F32: arithmetic and storage type of the state       */
+  int r_layout;      /* BQ_R_FULL | BQ_R_OFF (R ~ 0 when kappa t << 1, main text after Eq. 9) */
+  int basis;         /* BQ_BASIS_*                                                      */
+  int c_mode;        /* BQ_C_EQ304 | BQ_C_ZERO: separation constant                     */
+  int reverse_time;  /* 1: t = horizon - tau                                            */
+  int grid[BQ_MAX_MODES]; /* coefficient truncation M per mode; 0 = the Fock truncation */
+  double horizon;    /* T, physical end time                                            */
+  double dt;         /* time step the state will be stepped with (stability check)      */
+} bq_map_opts;
+
+/* ---- problem construction (host only; Eqs. 1-3, S1-S2) ---------------------------- */
+
+/* New problem with n_modes (1..BQ_MAX_MODES) modes, Fock truncation fock_trunc[j] >= 1. */
+int bq_problem_create(bq_problem** out, int n_modes, const int* fock_trunc);
+void bq_problem_destroy(bq_problem* p);
+
+/* Adds a drive envelope (kinds above); *ch_out receives its index. */
+int bq_problem_add_channel(bq_problem* p, int kind, const double* params, int n_params, int* ch_out);
+
+/* Adds h * [param] * [channel(t) or conj(channel(t))] * prod (a^dag)^u a^v to H (Eq. 1).
+ * channel = -1: static.  param = -1: no parameter, else the coefficient is multiplied by
+ * the real parameter params[param] (bq_problem_set_params).  The caller adds Hermitian
+ * conjugate terms explicitly; bq_map() rejects a non-Hermitian H with BQ_EINVAL. */
+int bq_problem_add_h_term(bq_problem* p, double re, double im, const int* u, const int* v,
+                          int channel, int conj, int param);
+
+/* Sets the real parameter values referenced by H terms. */
+int bq_problem_set_params(bq_problem* p, const double* values, int n);
+
+/* Adds a Lindblad channel with rate kappa >= 0 and jump operator
+ * L = sum_t (c_re[t] + i c_im[t]) prod (a^dag)^u[t] a^v[t]; u, v are n_terms x n_modes,
+ * row-major (Eq. 3). */
+int bq_problem_add_jump(bq_problem* p, double kappa, int n_terms, const double* c_re,
+                        const double* c_im, const int* u, const int* v);
+
+/* Measured operator A(0) by number-basis elements <k|A|l> = re + i im; k, l are n x n_modes
+ * row-major.  Repeated (k, l) pairs add up. */
+int bq_problem_set_measured(bq_problem* p, int n, const int* k, const int* l, const double* re,
+                            const double* im);
+
+/* Initial density matrix rho0 by elements <k|rho0|l> (default: vacuum |0><0|); used by
+ * bq_evaluate for Tr(rho0 A(t)). */
+int bq_problem_set_rho0(bq_problem* p, int n, const int* k, const int* l, const double* re,
+                        const double* im);
+
+/* ---- mapping (Eqs. 6, 10-13, 304) ---------------------------------------------------- */
+
+/* Device bytes bq_map() needs for B problems mapped with the same options. */
+int bq_required_bytes(const bq_problem* const* probs, int B, const bq_map_opts* opts, size_t* out);
+
+/* Maps B problems into one batched state inside [device_pool, device_pool + pool_bytes)
+ * (256-byte aligned, caller-owned).  For the mapped method every non-negligible
+ * g_{p,q}(0) = <p|A|q>/sqrt(p! q!) (Eq. 6 with Eq. 8's basis) becomes one separable
+ * initial condition G_x = x^p, G_y = y^q, R = 0 with separation constant C (Eq. 304);
+ * for the direct method the state is A(0) itself.  Returns BQ_EUNSTABLE_DT if
+ * opts->dt exceeds the RK4 bound 2 sqrt(2) / rho, rho a Gershgorin bound of the generator. */
+int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* opts, void* device_pool,
+           size_t pool_bytes, void* stream, bq_state** out);
+
+/* ---- stepping (Eqs. 9a-c / 303a-c, classical RK4) ----------------------------------- */
+
+/* Advances every system of the state by n_steps RK4 steps of size dt (the mapped value
+ * of dt must not exceed the bound checked at bq_map).  Four fused stage kernels per step,
+ * replayed from a CUDA graph; asynchronous on stream. */
+int bq_step(bq_state* s, double dt, int64_t n_steps, void* stream);
+
+/* Current integration time tau of the state (host copy, no synchronisation). */
+int bq_time(const bq_state* s, double* tau);
+
+/* ---- evaluation (Eqs. 7, 11) --------------------------------------------------------- */
+
+/* out_host[2b], out_host[2b+1] = Re, Im of Tr(rho0_b A_b(tau)) for every problem b
+ * (warp reductions over initial conditions and rho0's support).  Synchronises stream. */
+int bq_evaluate(bq_state* s, double* out_host, void* stream);
+
+/* Number-basis block <k|A_b(tau)|l> for every mode index < lo (the paper's epsilon_r
+ * block uses lo = 3).  out_host holds B * D * D complex values (re, im interleaved),
+ * D = prod_j min(lo, grid_j), row-major (k, l).  Synchronises stream. */
+int bq_fock_block(bq_state* s, int lo, double* out_host, void* stream);
+
+/* Shape of the state for bq_read_state: number of systems (initial conditions) in
+ * total, and per system the element counts of G_x, G_y and R (0 if absent). */
+int bq_state_info(const bq_state* s, int* n_systems, int64_t* total_elems);
+int bq_system_info(const bq_state* s, int sys, int* problem, int* p_idx, int* q_idx,
+                   int64_t* n_gx, int64_t* n_gy, int64_t* n_r, double* weight_re_im,
+                   double* c_re_im);
+
+/* Copies system sys's G_x, G_y, R (or A for the direct method, in R) to host as
+ * complex FP64, converted to the monomial basis g_{k,l} of Eq. 6 (number-basis values
+ * A_{k,l} for the direct method).  Buffers may be NULL to skip.  Synchronises stream. */
+int bq_read_system(bq_state* s, int sys, double* gx, double* gy, double* r, void* stream);
+
+/* Raw state snapshot (checkpoint / resume, host-resident inputs): the G_x, G_y, R arrays
+ * of every system in storage layout, *nbytes = total_elems * complex element size.
+ * bq_store_state copies device -> host, bq_load_state host -> device (the integration
+ * time tau is part of neither; bq_set_time sets it).  Host buffers may be pageable or
+ * pinned; both calls are asynchronous on stream for pinned memory. */
+int bq_state_bytes(const bq_state* s, size_t* nbytes);
+int bq_store_state(bq_state* s, void* host, void* stream);
+int bq_load_state(bq_state* s, const void* host, void* stream);
+int bq_set_time(bq_state* s, double tau);
+
+void bq_state_destroy(bq_state* s);
+
+/* ---- diagnostics ---------------------------------------------------------------------- */
+const char* bq_status_string(int status);
+const char* bq_last_error(void);
+
+/* Number of kernel launches this library has enqueued since load (graph replays count
+ * every kernel node). */
+int64_t bq_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BQ_H_ */

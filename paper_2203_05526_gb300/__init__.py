@@ -1,0 +1,8 @@
+"""GB300 (sm_103a) solver for the mapped adjoint Lindblad equation of arXiv 2203.05526.
+
+The numerical work runs in ``libbq.so`` (CUDA kernels + C ABI, include/bq.h); this package
+is the thin ctypes binding.  ``build.build()`` compiles the library in-tree.
+"""
+
+from .binding import (BQError, ProblemHandle, State, check, exported_symbols, launch_count, lib,  # noqa: F401
+                      map_opts, problem_from_spec)

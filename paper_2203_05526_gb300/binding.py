@@ -1,0 +1,296 @@
+"""ctypes binding of the C ABI declared in include/bq.h (argument marshalling only).
+
+Every numerical step runs inside ``libbq.so``; this module converts Python values to the
+C argument types, owns the device buffer a state lives in (a torch uint8 tensor, i.e. the
+PyTorch caching allocator provides device memory) and passes torch's current CUDA stream.
+If the library is missing the import fails loudly: there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Iterable, List, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbq.so")
+
+BQ_OK = 0
+BQ_EINVAL = -1
+BQ_EUNSTABLE_DT = -2
+BQ_ENOMEM = -3
+BQ_ECUDA = -4
+BQ_ENONFINITE = -5
+BQ_ETIMEOUT = -6
+BQ_EUNSUPPORTED = -7
+
+CH_KIND = {"const": 0, "gauss": 1, "pwc": 2, "cexp": 3}
+METHOD = {"mapped": 0, "direct": 1}
+DTYPE = {"f64": 0, "f32": 1}
+R_LAYOUT = {"full": 0, "off": 1}
+BASIS = {"auto": 0, "monomial": 1, "number": 2}
+C_MODE = {"eq304": 0, "zero": 1}
+MAX_MODES = 3
+
+
+class BQError(RuntimeError):
+    def __init__(self, status: int, detail: str):
+        super().__init__(f"bq status {status}: {detail}")
+        self.status = status
+
+
+class bq_map_opts(C.Structure):
+    _fields_ = [("method", C.c_int), ("dtype", C.c_int), ("r_layout", C.c_int), ("basis", C.c_int),
+                ("c_mode", C.c_int), ("reverse_time", C.c_int), ("grid", C.c_int * MAX_MODES),
+                ("horizon", C.c_double), ("dt", C.c_double)]
+
+
+_lib: Optional[C.CDLL] = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2203_05526_gb300.build.build() "
+                          "(the solver has no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    vp, ip, dp, i64 = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int64
+    sig = {
+        "bq_problem_create": (C.c_int, [C.POINTER(vp), C.c_int, ip]),
+        "bq_problem_destroy": (None, [vp]),
+        "bq_problem_add_channel": (C.c_int, [vp, C.c_int, dp, C.c_int, ip]),
+        "bq_problem_add_h_term": (C.c_int, [vp, C.c_double, C.c_double, ip, ip, C.c_int, C.c_int, C.c_int]),
+        "bq_problem_set_params": (C.c_int, [vp, dp, C.c_int]),
+        "bq_problem_add_jump": (C.c_int, [vp, C.c_double, C.c_int, dp, dp, ip, ip]),
+        "bq_problem_set_measured": (C.c_int, [vp, C.c_int, ip, ip, dp, dp]),
+        "bq_problem_set_rho0": (C.c_int, [vp, C.c_int, ip, ip, dp, dp]),
+        "bq_required_bytes": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(bq_map_opts), C.POINTER(C.c_size_t)]),
+        "bq_map": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(bq_map_opts), vp, C.c_size_t, vp, C.POINTER(vp)]),
+        "bq_step": (C.c_int, [vp, C.c_double, i64, vp]),
+        "bq_time": (C.c_int, [vp, dp]),
+        "bq_evaluate": (C.c_int, [vp, dp, vp]),
+        "bq_fock_block": (C.c_int, [vp, C.c_int, dp, vp]),
+        "bq_state_info": (C.c_int, [vp, ip, C.POINTER(C.c_int64)]),
+        "bq_system_info": (C.c_int, [vp, C.c_int, ip, ip, ip, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_int64), dp, dp]),
+        "bq_read_system": (C.c_int, [vp, C.c_int, dp, dp, dp, vp]),
+        "bq_state_bytes": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
+        "bq_store_state": (C.c_int, [vp, vp, vp]),
+        "bq_load_state": (C.c_int, [vp, vp, vp]),
+        "bq_set_time": (C.c_int, [vp, C.c_double]),
+        "bq_state_destroy": (None, [vp]),
+        "bq_status_string": (C.c_char_p, [C.c_int]),
+        "bq_last_error": (C.c_char_p, []),
+        "bq_launch_count": (C.c_int64, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols() -> List[str]:
+    """Names declared in include/bq.h that the binding resolves."""
+    return [n for n in ("bq_problem_create", "bq_problem_destroy", "bq_problem_add_channel",
+                        "bq_problem_add_h_term", "bq_problem_set_params", "bq_problem_add_jump",
+                        "bq_problem_set_measured", "bq_problem_set_rho0", "bq_required_bytes", "bq_map",
+                        "bq_step", "bq_time", "bq_evaluate", "bq_fock_block", "bq_state_info",
+                        "bq_system_info", "bq_read_system", "bq_state_bytes", "bq_store_state",
+                        "bq_load_state", "bq_set_time", "bq_state_destroy", "bq_status_string",
+                        "bq_last_error", "bq_launch_count")]
+
+
+def check(status: int) -> None:
+    if status != BQ_OK:
+        L = lib()
+        raise BQError(status, f"{L.bq_status_string(status).decode()}: {L.bq_last_error().decode()}")
+
+
+def _iarr(xs: Iterable[int]):
+    xs = list(int(x) for x in xs)
+    return (C.c_int * max(1, len(xs)))(*xs)
+
+
+def _darr(xs: Iterable[float]):
+    xs = list(float(x) for x in xs)
+    return (C.c_double * max(1, len(xs)))(*xs)
+
+
+class ProblemHandle:
+    """Owns a bq_problem* built through the C ABI."""
+
+    def __init__(self, n_modes: int, fock_trunc: Sequence[int]):
+        self.ptr = C.c_void_p()
+        self.n_modes = n_modes
+        check(lib().bq_problem_create(C.byref(self.ptr), n_modes, _iarr(fock_trunc)))
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and self.ptr.value and _lib is not None:
+            _lib.bq_problem_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def add_channel(self, kind: str, params: Sequence[float]) -> int:
+        out = C.c_int()
+        check(lib().bq_problem_add_channel(self.ptr, CH_KIND[kind], _darr(params), len(params), C.byref(out)))
+        return out.value
+
+    def add_h_term(self, coef: complex, u, v, channel: int = -1, conj: bool = False, param: int = -1):
+        check(lib().bq_problem_add_h_term(self.ptr, coef.real, coef.imag, _iarr(u), _iarr(v), channel,
+                                          1 if conj else 0, param))
+
+    def set_params(self, values: Sequence[float]):
+        check(lib().bq_problem_set_params(self.ptr, _darr(values), len(values)))
+
+    def add_jump(self, rate: float, terms):
+        cre = [complex(c).real for c, _, _ in terms]
+        cim = [complex(c).imag for c, _, _ in terms]
+        u = [x for _, uu, _ in terms for x in uu]
+        v = [x for _, _, vv in terms for x in vv]
+        check(lib().bq_problem_add_jump(self.ptr, rate, len(terms), _darr(cre), _darr(cim), _iarr(u), _iarr(v)))
+
+    def _elems(self, fn, elems):
+        items = list(elems.items())
+        k = [x for (kk, _), _ in items for x in kk]
+        l = [x for (_, ll), _ in items for x in ll]
+        re = [complex(v).real for _, v in items]
+        im = [complex(v).imag for _, v in items]
+        check(fn(self.ptr, len(items), _iarr(k), _iarr(l), _darr(re), _darr(im)))
+
+    def set_measured(self, elems):
+        self._elems(lib().bq_problem_set_measured, elems)
+
+    def set_rho0(self, elems):
+        self._elems(lib().bq_problem_set_rho0, elems)
+
+
+def problem_from_spec(spec) -> ProblemHandle:
+    """Marshals a ``workloads.spec.Problem`` (or any object with the same fields)."""
+    h = ProblemHandle(spec.n_modes, spec.N)
+    for ch in spec.channels:
+        h.add_channel(ch.kind, ch.params)
+    if spec.params:
+        h.set_params(spec.params)
+    for t in spec.h_terms:
+        h.add_h_term(complex(t.coef), t.u, t.v, t.channel, t.conj, t.param)
+    for j in spec.jumps:
+        h.add_jump(j.rate, j.terms)
+    h.set_measured(spec.measured)
+    if spec.rho0 is not None:
+        h.set_rho0(spec.rho0)
+    return h
+
+
+def map_opts(method="mapped", dtype="f64", r_layout="full", basis="auto", c_mode="eq304", reverse_time=True,
+             grid: Optional[Sequence[int]] = None, horizon: float = 0.0, dt: float = 0.0) -> bq_map_opts:
+    o = bq_map_opts()
+    o.method, o.dtype, o.r_layout = METHOD[method], DTYPE[dtype], R_LAYOUT[r_layout]
+    o.basis, o.c_mode, o.reverse_time = BASIS[basis], C_MODE[c_mode], 1 if reverse_time else 0
+    g = list(grid or [])
+    for j in range(MAX_MODES):
+        o.grid[j] = int(g[j]) if j < len(g) else 0
+    o.horizon, o.dt = float(horizon), float(dt)
+    return o
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class State:
+    """A batch of mapped (or direct) problems resident in one torch-owned device buffer."""
+
+    def __init__(self, handles: Sequence[ProblemHandle], opts: bq_map_opts, device=None, stream=None):
+        import torch
+        self.handles = list(handles)  # keep problems alive while the state exists
+        arr = (C.c_void_p * len(handles))(*[h.ptr.value for h in handles])
+        nbytes = C.c_size_t()
+        check(lib().bq_required_bytes(arr, len(handles), C.byref(opts), C.byref(nbytes)))
+        self.nbytes = nbytes.value
+        self.pool = torch.empty(self.nbytes, dtype=torch.uint8, device=device or "cuda")
+        self.ptr = C.c_void_p()
+        self.B = len(handles)
+        self.opts = opts
+        check(lib().bq_map(arr, len(handles), C.byref(opts), C.c_void_p(self.pool.data_ptr()), self.nbytes,
+                           _stream_ptr(stream), C.byref(self.ptr)))
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and self.ptr.value and _lib is not None:
+            _lib.bq_state_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def step(self, dt: float, n_steps: int, stream=None):
+        check(lib().bq_step(self.ptr, float(dt), int(n_steps), _stream_ptr(stream)))
+
+    def time(self) -> float:
+        t = C.c_double()
+        check(lib().bq_time(self.ptr, C.byref(t)))
+        return t.value
+
+    def evaluate(self, stream=None) -> np.ndarray:
+        out = (C.c_double * (2 * self.B))()
+        check(lib().bq_evaluate(self.ptr, out, _stream_ptr(stream)))
+        a = np.frombuffer(out, dtype=np.float64).copy()
+        return a[0::2] + 1j * a[1::2]
+
+    def fock_block(self, lo: int = 3, dim: Optional[int] = None, stream=None) -> np.ndarray:
+        if dim is None:
+            raise ValueError("dim (prod_j min(3, M_j)) is required")
+        out = (C.c_double * (2 * self.B * dim * dim))()
+        check(lib().bq_fock_block(self.ptr, lo, out, _stream_ptr(stream)))
+        a = np.frombuffer(out, dtype=np.float64).copy()
+        return (a[0::2] + 1j * a[1::2]).reshape(self.B, dim, dim)
+
+    def state_bytes(self) -> int:
+        n = C.c_size_t()
+        check(lib().bq_state_bytes(self.ptr, C.byref(n)))
+        return n.value
+
+    def store_state(self, host_ptr: int, stream=None):
+        check(lib().bq_store_state(self.ptr, C.c_void_p(host_ptr), _stream_ptr(stream)))
+
+    def load_state(self, host_ptr: int, stream=None):
+        check(lib().bq_load_state(self.ptr, C.c_void_p(host_ptr), _stream_ptr(stream)))
+
+    def set_time(self, tau: float):
+        check(lib().bq_set_time(self.ptr, float(tau)))
+
+    def n_systems(self) -> int:
+        n = C.c_int()
+        check(lib().bq_state_info(self.ptr, C.byref(n), None))
+        return n.value
+
+    def system_info(self, sys: int) -> dict:
+        prob, p, q = C.c_int(), C.c_int(), C.c_int()
+        ngx, ngy, nr = C.c_int64(), C.c_int64(), C.c_int64()
+        w, c = (C.c_double * 2)(), (C.c_double * 2)()
+        check(lib().bq_system_info(self.ptr, sys, C.byref(prob), C.byref(p), C.byref(q), C.byref(ngx),
+                                   C.byref(ngy), C.byref(nr), w, c))
+        return dict(problem=prob.value, p=p.value, q=q.value, n_gx=ngx.value, n_gy=ngy.value, n_r=nr.value,
+                    weight=complex(w[0], w[1]), C=complex(c[0], c[1]))
+
+    def read_system(self, sys: int, stream=None):
+        info = self.system_info(sys)
+        bufs = []
+        for n in (info["n_gx"], info["n_gy"], info["n_r"]):
+            bufs.append((C.c_double * (2 * n))() if n else None)
+        check(lib().bq_read_system(self.ptr, sys, bufs[0], bufs[1], bufs[2], _stream_ptr(stream)))
+        out = []
+        for b in bufs:
+            if b is None:
+                out.append(None)
+            else:
+                a = np.frombuffer(b, dtype=np.float64).copy()
+                out.append(a[0::2] + 1j * a[1::2])
+        return info, out[0], out[1], out[2]
+
+
+def launch_count() -> int:
+    return int(lib().bq_launch_count())

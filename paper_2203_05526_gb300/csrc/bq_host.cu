@@ -1,0 +1,1055 @@
+// Host side of the C ABI in include/bq.h: problem construction, the problem compiler
+// (normal ordering and stencil tables of the coupled system, Eqs. 9a-c / 303a-c), the
+// mapping of the measured operator (Eqs. 6, 10-13, 304), device layout, and stepping /
+// evaluation drivers around the kernels of bq_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/bq.h"
+#include "bq_internal.h"
+#include "bq_launch.h"
+
+using cplx = std::complex<double>;
+using bq::ChanDesc;
+using bq::EvalEntry;
+using bq::EvalGroup;
+using bq::InitEntry;
+using bq::SysDesc;
+using bq::TermDesc;
+using bq::WorkItem;
+
+// ---------------------------------------------------------------------------------------
+// Errors.
+// ---------------------------------------------------------------------------------------
+static thread_local std::string g_err;
+static std::atomic<long long> g_launches{0};
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(BQ_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));           \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------
+// Problem.
+// ---------------------------------------------------------------------------------------
+struct HTermH {
+  cplx c;
+  std::vector<int> u, v;
+  int ch, conj, param;
+};
+struct JumpH {
+  double rate;
+  std::vector<cplx> c;
+  std::vector<std::vector<int>> u, v;
+};
+struct ChannelH {
+  int kind;
+  std::vector<double> par;
+};
+using Key = std::pair<std::vector<int>, std::vector<int>>;
+
+struct bq_problem {
+  int nm = 0;
+  std::vector<int> N;
+  std::vector<HTermH> h;
+  std::vector<JumpH> jumps;
+  std::vector<ChannelH> ch;
+  std::vector<double> params;
+  std::map<Key, cplx> measured, rho0;
+  bool rho0_set = false;
+};
+
+static bool valid_powers(const bq_problem* p, const int* a) {
+  for (int j = 0; j < p->nm; ++j)
+    if (a[j] < 0 || a[j] > 16) return false;
+  return true;
+}
+
+extern "C" int bq_problem_create(bq_problem** out, int n_modes, const int* fock_trunc) {
+  if (!out) return fail(BQ_EINVAL, "out is NULL");
+  if (n_modes < 1 || n_modes > BQ_MAX_MODES) return fail(BQ_EINVAL, "n_modes=%d outside 1..%d", n_modes, BQ_MAX_MODES);
+  if (!fock_trunc) return fail(BQ_EINVAL, "fock_trunc is NULL");
+  for (int j = 0; j < n_modes; ++j)
+    if (fock_trunc[j] < 1 || fock_trunc[j] > 4096) return fail(BQ_EINVAL, "fock_trunc[%d]=%d", j, fock_trunc[j]);
+  auto* p = new bq_problem();
+  p->nm = n_modes;
+  p->N.assign(fock_trunc, fock_trunc + n_modes);
+  *out = p;
+  return BQ_OK;
+}
+
+extern "C" void bq_problem_destroy(bq_problem* p) { delete p; }
+
+extern "C" int bq_problem_add_channel(bq_problem* p, int kind, const double* params, int n_params, int* ch_out) {
+  if (!p) return fail(BQ_EINVAL, "problem is NULL");
+  static const int need[4] = {2, 4, 2, 3};
+  if (kind < 0 || kind > 3) return fail(BQ_EINVAL, "unknown channel kind %d", kind);
+  if (n_params < need[kind] || (n_params > 0 && !params)) return fail(BQ_EINVAL, "channel kind %d needs >= %d params", kind, need[kind]);
+  if (kind == BQ_CH_PWC && (n_params % 2 != 0 || !(params[1] > 0.0)))
+    return fail(BQ_EINVAL, "PWC channel needs (t_start, seg_len>0, re, im, ...)");
+  if (kind == BQ_CH_GAUSS && !(params[3] > 0.0)) return fail(BQ_EINVAL, "GAUSS sigma must be > 0");
+  p->ch.push_back({kind, std::vector<double>(params, params + n_params)});
+  if (ch_out) *ch_out = (int)p->ch.size() - 1;
+  return BQ_OK;
+}
+
+extern "C" int bq_problem_add_h_term(bq_problem* p, double re, double im, const int* u, const int* v, int channel,
+                                     int conj, int param) {
+  if (!p || !u || !v) return fail(BQ_EINVAL, "NULL argument");
+  if (!valid_powers(p, u) || !valid_powers(p, v)) return fail(BQ_EINVAL, "monomial powers outside 0..16");
+  if (channel < -1 || channel >= (int)p->ch.size()) return fail(BQ_EINVAL, "channel %d not defined", channel);
+  if (param < -1) return fail(BQ_EINVAL, "param %d", param);
+  p->h.push_back({cplx(re, im), std::vector<int>(u, u + p->nm), std::vector<int>(v, v + p->nm), channel,
+                  channel < 0 ? 0 : (conj ? 1 : 0), param});
+  return BQ_OK;
+}
+
+extern "C" int bq_problem_set_params(bq_problem* p, const double* values, int n) {
+  if (!p || (n > 0 && !values) || n < 0) return fail(BQ_EINVAL, "bad params");
+  p->params.assign(values, values + n);
+  return BQ_OK;
+}
+
+extern "C" int bq_problem_add_jump(bq_problem* p, double kappa, int n_terms, const double* c_re, const double* c_im,
+                                   const int* u, const int* v) {
+  if (!p || n_terms < 1 || !c_re || !c_im || !u || !v) return fail(BQ_EINVAL, "bad jump arguments");
+  if (!(kappa >= 0.0)) return fail(BQ_EINVAL, "jump rate must be >= 0");
+  JumpH j;
+  j.rate = kappa;
+  for (int t = 0; t < n_terms; ++t) {
+    if (!valid_powers(p, u + t * p->nm) || !valid_powers(p, v + t * p->nm))
+      return fail(BQ_EINVAL, "jump monomial powers outside 0..16");
+    j.c.push_back(cplx(c_re[t], c_im[t]));
+    j.u.emplace_back(u + t * p->nm, u + (t + 1) * p->nm);
+    j.v.emplace_back(v + t * p->nm, v + (t + 1) * p->nm);
+  }
+  p->jumps.push_back(std::move(j));
+  return BQ_OK;
+}
+
+static int set_elems(bq_problem* p, std::map<Key, cplx>& dst, int n, const int* k, const int* l, const double* re,
+                     const double* im) {
+  if (!p || n < 0 || (n > 0 && (!k || !l || !re || !im))) return fail(BQ_EINVAL, "bad element arguments");
+  dst.clear();
+  for (int i = 0; i < n; ++i) {
+    std::vector<int> kk(k + i * p->nm, k + (i + 1) * p->nm), ll(l + i * p->nm, l + (i + 1) * p->nm);
+    for (int j = 0; j < p->nm; ++j)
+      if (kk[j] < 0 || ll[j] < 0) return fail(BQ_EINVAL, "negative Fock index");
+    dst[{kk, ll}] += cplx(re[i], im[i]);
+  }
+  return BQ_OK;
+}
+
+extern "C" int bq_problem_set_measured(bq_problem* p, int n, const int* k, const int* l, const double* re,
+                                       const double* im) {
+  return set_elems(p, p->measured, n, k, l, re, im);
+}
+
+extern "C" int bq_problem_set_rho0(bq_problem* p, int n, const int* k, const int* l, const double* re,
+                                   const double* im) {
+  int r = set_elems(p, p->rho0, n, k, l, re, im);
+  if (r == BQ_OK) p->rho0_set = true;
+  return r;
+}
+
+// ---------------------------------------------------------------------------------------
+// Normal ordering (S-eq. 103, r = 1): per mode
+//   (a^dag)^p1 a^q1 (a^dag)^p2 a^q2 = sum_s s! C(q1,s) C(p2,s) (a^dag)^(p1+p2-s) a^(q1+q2-s).
+// ---------------------------------------------------------------------------------------
+using Poly = std::map<Key, cplx>;  // normal-ordered monomial -> coefficient
+
+static double binom(int n, int k) {
+  if (k < 0 || k > n) return 0.0;
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+static double fact(int n) {
+  double r = 1.0;
+  for (int i = 2; i <= n; ++i) r *= i;
+  return r;
+}
+
+static Poly product(const Key& m1, const Key& m2, cplx c) {
+  const int nm = (int)m1.first.size();
+  Poly out;
+  out[{std::vector<int>(nm, 0), std::vector<int>(nm, 0)}] = c;
+  for (int j = 0; j < nm; ++j) {
+    const int p1 = m1.first[j], q1 = m1.second[j], p2 = m2.first[j], q2 = m2.second[j];
+    Poly next;
+    for (auto& [key, val] : out) {
+      for (int s = 0; s <= std::min(q1, p2); ++s) {
+        const double w = fact(s) * binom(q1, s) * binom(p2, s);
+        Key k2 = key;
+        k2.first[j] = p1 + p2 - s;
+        k2.second[j] = q1 + q2 - s;
+        next[k2] += val * w;
+      }
+    }
+    out.swap(next);
+  }
+  return out;
+}
+
+// ---------------------------------------------------------------------------------------
+// Compiler.
+// ---------------------------------------------------------------------------------------
+struct RawTerm {
+  int side;
+  cplx c;
+  int ch, conj, param;
+  int a[BQ_MAXD], b[BQ_MAXD];
+};
+
+struct Compiled {
+  int nm, M[3], method, basis, has_sep, has_r;
+  int n_g, n_r;
+  std::vector<TermDesc> terms;         // wtab offsets relative to this problem's weight block
+  std::vector<double> wtab;            // weight tables
+  std::vector<cplx> diag;              // 2*nm tables
+  struct Sys { int p_flat, q_flat; cplx w, C; double gx0, gy0; };  // gx0/gy0: stored values of x^p, y^q
+  std::vector<Sys> sys;
+  std::vector<std::pair<long long, cplx>> init;  // direct method: (R element offset, value)
+  std::vector<EvalEntry> trace_entries;          // Tr(rho0 A) entries (kx, ly, factor)
+  std::vector<EvalEntry> block_entries;          // lo=3 block (one per element)
+  int block_dim;
+  std::vector<ChanDesc> chans;
+  std::vector<double> chpar;
+  int halo_lo, halo_hi;
+  double rho;                                    // spectral-radius bound for the stability check
+};
+
+static double s_of(int basis, int k) { return basis == BQ_BASIS_NUMBER ? std::sqrt(fact(k)) : 1.0; }
+
+// weight of x^a d^b at index k on a grid of size M in the storage basis; 0 if out of grid
+static double weight(int a, int b, int k, int M, int basis) {
+  if (k < a) return 0.0;
+  const int ks = k - a + b;
+  if (ks >= M) return 0.0;
+  double w = 1.0;
+  for (int i = 1; i <= b; ++i) w *= (double)(k - a + i);  // (k-a+b)! / (k-a)!
+  if (basis == BQ_BASIS_NUMBER) w *= std::sqrt(fact(k) / fact(ks));
+  return w;
+}
+
+static double chan_max(const ChannelH& c) {
+  switch (c.kind) {
+    case BQ_CH_CONST: return std::abs(cplx(c.par[0], c.par[1]));
+    case BQ_CH_GAUSS: return std::abs(cplx(c.par[0], c.par[1]));
+    case BQ_CH_CEXP: return std::abs(cplx(c.par[0], c.par[1]));
+    case BQ_CH_PWC: {
+      double m = 0.0;
+      for (size_t i = 2; i + 1 < c.par.size(); i += 2) m = std::max(m, std::abs(cplx(c.par[i], c.par[i + 1])));
+      return m;
+    }
+  }
+  return 0.0;
+}
+
+static int flat_index(const std::vector<int>& k, const int* M, int nm) {
+  int f = 0;
+  for (int j = 0; j < nm; ++j) f = f * M[j] + k[j];
+  return f;
+}
+
+static int check_hermitian(const bq_problem* p) {
+  // H = H^dag term by term: (c, u, v, ch, conj, param) pairs with (c*, v, u, ch, !conj, param).
+  std::map<std::tuple<std::vector<int>, std::vector<int>, int, int, int>, cplx> m;
+  for (auto& t : p->h) m[{t.u, t.v, t.ch, t.conj, t.param}] += t.c;
+  for (auto& [key, c] : m) {
+    auto& [u, v, ch, cj, par] = key;
+    const int cj2 = ch < 0 ? 0 : 1 - cj;
+    auto it = m.find({v, u, ch, cj2, par});
+    const cplx c2 = it == m.end() ? cplx(0, 0) : it->second;
+    if (std::abs(c - std::conj(c2)) > 1e-12 * std::max(1.0, std::abs(c)))
+      return fail(BQ_EINVAL, "Hamiltonian is not Hermitian: add the conjugate of every term (swap u/v, conj channel)");
+  }
+  return BQ_OK;
+}
+
+static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& C) {
+  const int nm = p->nm;
+  C.nm = nm;
+  C.method = o.method;
+  C.basis = o.basis != BQ_BASIS_AUTO ? o.basis
+            : (o.method == BQ_METHOD_MAPPED && o.dtype == BQ_F64 ? BQ_BASIS_MONOMIAL : BQ_BASIS_NUMBER);
+  if (o.method == BQ_METHOD_DIRECT) C.basis = BQ_BASIS_NUMBER;
+  for (int j = 0; j < 3; ++j) C.M[j] = 1;
+  long long ng = 1;
+  for (int j = 0; j < nm; ++j) {
+    C.M[j] = o.grid[j] > 0 ? o.grid[j] : p->N[j];
+    if (C.M[j] < 1 || C.M[j] > 127) return fail(BQ_EUNSUPPORTED, "grid M=%d per mode outside 1..127", C.M[j]);
+    ng *= C.M[j];
+  }
+  if (ng * ng > (1LL << 30)) return fail(BQ_EUNSUPPORTED, "R too large");
+  C.n_g = (int)ng;
+  C.n_r = (int)(ng * ng);
+  C.has_sep = o.method == BQ_METHOD_MAPPED ? 1 : 0;
+  C.has_r = (o.method == BQ_METHOD_DIRECT || o.r_layout == BQ_R_FULL) ? 1 : 0;
+  for (auto& t : p->h)
+    if (t.param >= (int)p->params.size()) return fail(BQ_EINVAL, "H term uses param %d but only %zu set", t.param, p->params.size());
+  int r = check_hermitian(p);
+  if (r != BQ_OK) return r;
+
+  // ---- raw terms -----------------------------------------------------------------
+  std::vector<RawTerm> raw;
+  auto zero = [&](RawTerm& t) { for (int d = 0; d < BQ_MAXD; ++d) t.a[d] = t.b[d] = 0; };
+  for (auto& t : p->h) {
+    const cplx h = t.c * (t.param >= 0 ? p->params[t.param] : 1.0);
+    RawTerm x; zero(x);
+    x.side = bq::SIDE_X; x.c = cplx(0, 1) * h; x.ch = t.ch; x.conj = t.conj; x.param = t.param;
+    for (int j = 0; j < nm; ++j) { x.a[j] = t.u[j]; x.b[j] = t.v[j]; }
+    raw.push_back(x);
+    RawTerm y; zero(y);
+    y.side = bq::SIDE_Y; y.c = cplx(0, -1) * h; y.ch = t.ch; y.conj = t.conj; y.param = t.param;
+    for (int j = 0; j < nm; ++j) { y.a[nm + j] = t.v[j]; y.b[nm + j] = t.u[j]; }
+    raw.push_back(y);
+  }
+  for (auto& jp : p->jumps) {
+    if (jp.rate == 0.0) continue;
+    Poly LdL;
+    for (size_t t = 0; t < jp.c.size(); ++t)
+      for (size_t s = 0; s < jp.c.size(); ++s) {
+        // L^dag L = sum_{t,s} conj(c_t) c_s m_t^dag m_s, m^dag = (a^dag)^v a^u
+        Key mt_dag{jp.v[t], jp.u[t]}, ms{jp.u[s], jp.v[s]};
+        for (auto& [k, v] : product(mt_dag, ms, std::conj(jp.c[t]) * jp.c[s])) LdL[k] += v;
+        // sandwich kappa conj(c_t) c_s (m_t^dag)_left (m_s)_right
+        RawTerm sw; zero(sw);
+        sw.side = bq::SIDE_S; sw.c = jp.rate * std::conj(jp.c[t]) * jp.c[s]; sw.ch = -1; sw.conj = 0; sw.param = -1;
+        for (int j = 0; j < nm; ++j) {
+          sw.a[j] = jp.v[t][j]; sw.b[j] = jp.u[t][j];            // left mult by m_t^dag
+          sw.a[nm + j] = jp.v[s][j]; sw.b[nm + j] = jp.u[s][j];  // right mult by m_s
+        }
+        raw.push_back(sw);
+      }
+    for (auto& [k, v] : LdL) {
+      if (v == cplx(0, 0)) continue;
+      RawTerm x; zero(x);
+      x.side = bq::SIDE_X; x.c = -0.5 * jp.rate * v; x.ch = -1; x.conj = 0; x.param = -1;
+      for (int j = 0; j < nm; ++j) { x.a[j] = k.first[j]; x.b[j] = k.second[j]; }
+      raw.push_back(x);
+      RawTerm y; zero(y);
+      y.side = bq::SIDE_Y; y.c = -0.5 * jp.rate * v; y.ch = -1; y.conj = 0; y.param = -1;
+      for (int j = 0; j < nm; ++j) { y.a[nm + j] = k.second[j]; y.b[nm + j] = k.first[j]; }
+      raw.push_back(y);
+    }
+  }
+
+  // ---- fold static single-dimension diagonal terms; merge the rest -----------------
+  const int ND = 2 * nm;
+  int Md[BQ_MAXD];
+  for (int d = 0; d < ND; ++d) Md[d] = C.M[d % nm];
+  std::vector<int> doff(ND + 1, 0);
+  for (int d = 0; d < ND; ++d) doff[d + 1] = doff[d] + Md[d];
+  C.diag.assign(doff[ND], cplx(0, 0));
+  std::map<std::tuple<int, int, int, int, std::vector<int>>, cplx> merged;
+  for (auto& t : raw) {
+    if (t.c == cplx(0, 0)) continue;
+    bool diag = true;
+    int nact = 0, dact = -1;
+    for (int d = 0; d < ND; ++d) {
+      if (t.a[d] != t.b[d]) diag = false;
+      if (t.a[d] || t.b[d]) { ++nact; dact = d; }
+    }
+    if (t.side != bq::SIDE_S && t.ch < 0 && diag && nact <= 1) {
+      const int d = nact == 0 ? (t.side == bq::SIDE_X ? 0 : nm) : dact;
+      for (int k = 0; k < Md[d]; ++k) {
+        double w = 1.0;
+        for (int i = 0; i < t.a[d]; ++i) w *= (double)(k - i);  // k!/(k-a)!
+        if (k < t.a[d]) w = 0.0;
+        C.diag[doff[d] + k] += t.c * w;
+      }
+      continue;
+    }
+    std::vector<int> ab(2 * ND);
+    for (int d = 0; d < ND; ++d) { ab[d] = t.a[d]; ab[ND + d] = t.b[d]; }
+    merged[{t.side, t.ch, t.conj, t.param, ab}] += t.c;
+  }
+  if ((int)merged.size() > BQ_MAX_TERMS) return fail(BQ_EUNSUPPORTED, "%zu stencil terms > %d", merged.size(), BQ_MAX_TERMS);
+
+  // strides: R index = kflat * n_g + lflat; flat = row-major over modes
+  int stG[3] = {1, 1, 1};
+  for (int j = nm - 2; j >= 0; --j) stG[j] = stG[j + 1] * C.M[j + 1];
+  int stR[BQ_MAXD];
+  for (int j = 0; j < nm; ++j) { stR[j] = stG[j] * C.n_g; stR[nm + j] = stG[j]; }
+
+  C.terms.clear();
+  C.wtab.clear();
+  C.halo_lo = C.halo_hi = 0;
+  double rho_terms = 0.0;
+  for (auto& [key, c] : merged) {
+    if (c == cplx(0, 0)) continue;
+    auto& [side, ch, conj, param, ab] = key;
+    if (!C.has_r && side == bq::SIDE_S) continue;  // sandwich acts only on R (and as its source)
+    TermDesc td;
+    std::memset(&td, 0, sizeof(td));
+    td.c_re = c.real(); td.c_im = c.imag(); td.ch = ch; td.conj = conj; td.side = side; td.param = param;
+    int nact = 0, dR = 0, dGx = 0, dGy = 0;
+    double wmax_num = 1.0;
+    for (int d = 0; d < ND; ++d) {
+      const int a = ab[d], b = ab[ND + d];
+      if (!a && !b) continue;
+      td.dim[nact] = (int8_t)d;
+      td.wtab[nact] = (int)C.wtab.size();
+      double wm = 0.0;
+      for (int k = 0; k < Md[d]; ++k) {
+        C.wtab.push_back(weight(a, b, k, Md[d], C.basis));
+        wm = std::max(wm, weight(a, b, k, Md[d], BQ_BASIS_NUMBER));
+      }
+      wmax_num *= wm;
+      dR += (b - a) * stR[d];
+      if (d < nm) dGx += (b - a) * stG[d]; else dGy += (b - a) * stG[d - nm];
+      ++nact;
+    }
+    td.n_act = nact; td.deltaR = dR; td.deltaGx = dGx; td.deltaGy = dGy;
+    C.halo_lo = std::max(C.halo_lo, -dR);
+    C.halo_hi = std::max(C.halo_hi, dR);
+    C.terms.push_back(td);
+    rho_terms += std::abs(c) * (ch >= 0 ? chan_max(p->ch[ch]) : 1.0) * wmax_num;
+  }
+
+  // ---- stability bound: max |diag| over the grid + sum of off-diagonal magnitudes ----
+  {
+    double dmax = 0.0;
+    const int npts = C.has_r ? C.n_r : C.n_g;
+    const int nd = C.has_r ? ND : nm;
+    std::vector<int> idx(ND, 0);
+    for (int pnt = 0; pnt < npts; ++pnt) {
+      int rr = pnt;
+      for (int d = nd - 1; d >= 0; --d) { idx[d] = rr % Md[d]; rr /= Md[d]; }
+      cplx s(0, 0);
+      for (int d = 0; d < nd; ++d) s += C.diag[doff[d] + idx[d]];
+      dmax = std::max(dmax, std::abs(s));
+      if (!C.has_r) {  // G_y too
+        cplx s2(0, 0);
+        for (int d = 0; d < nm; ++d) s2 += C.diag[doff[nm + d] + idx[d]];
+        dmax = std::max(dmax, std::abs(s2));
+      }
+    }
+    C.rho = dmax + rho_terms;
+  }
+
+  // ---- channels ----------------------------------------------------------------------
+  C.chans.clear(); C.chpar.clear();
+  for (auto& ch : p->ch) {
+    ChanDesc cd;
+    cd.kind = ch.kind; cd.n_par = (int)ch.par.size(); cd.par_off = (int)C.chpar.size(); cd.pad = 0;
+    C.chans.push_back(cd);
+    C.chpar.insert(C.chpar.end(), ch.par.begin(), ch.par.end());
+  }
+
+  // ---- systems (initial conditions, Eqs. 10 / 13) -----------------------------------
+  // om_j, eta_j of Eq. 304: static coefficients of a_j^dag a_j and a_j^dag^2 a_j^2.
+  std::vector<double> om(nm, 0.0), et(nm, 0.0);
+  for (auto& t : p->h) {
+    if (t.ch >= 0) continue;
+    int nz = 0, j0 = -1;
+    for (int j = 0; j < nm; ++j) if (t.u[j] || t.v[j]) { ++nz; j0 = j; }
+    if (nz != 1) continue;
+    const double cr = (t.c * (t.param >= 0 ? p->params[t.param] : 1.0)).real();
+    if (t.u[j0] == 1 && t.v[j0] == 1) om[j0] += cr;
+    if (t.u[j0] == 2 && t.v[j0] == 2) et[j0] += cr;
+  }
+  C.sys.clear(); C.init.clear();
+  auto in_grid = [&](const std::vector<int>& k) {
+    for (int j = 0; j < nm; ++j) if (k[j] >= C.M[j]) return false;
+    return true;
+  };
+  auto sfl = [&](const std::vector<int>& k) {  // s(k) of the storage basis (product over modes)
+    double s = 1.0;
+    for (int j = 0; j < nm; ++j) s *= s_of(C.basis, k[j]);
+    return s;
+  };
+  auto sqfact = [&](const std::vector<int>& k) {
+    double s = 1.0;
+    for (int j = 0; j < nm; ++j) s *= std::sqrt(fact(k[j]));
+    return s;
+  };
+  if (C.method == BQ_METHOD_DIRECT) {
+    C.sys.push_back({0, 0, cplx(1, 0), cplx(0, 0), 0.0, 0.0});
+    for (auto& [kl, v] : p->measured)
+      if (in_grid(kl.first) && in_grid(kl.second) && v != cplx(0, 0))
+        C.init.push_back({(long long)flat_index(kl.first, C.M, nm) * C.n_g + flat_index(kl.second, C.M, nm), v});
+  } else {
+    for (auto& [kl, v] : p->measured) {
+      if (!in_grid(kl.first) || !in_grid(kl.second) || v == cplx(0, 0)) continue;
+      Compiled::Sys s;
+      s.p_flat = flat_index(kl.first, C.M, nm);
+      s.q_flat = flat_index(kl.second, C.M, nm);
+      s.w = v / sqfact(kl.first) / sqfact(kl.second);  // g_{p,q}(0) = <p|A|q>/sqrt(p! q!)
+      double cs = 0.0;
+      for (int j = 0; j < nm; ++j) {
+        const int pj = kl.first[j], qj = kl.second[j];
+        cs += (om[j] - et[j]) * (pj + qj) + et[j] * (pj * pj + qj * qj);
+      }
+      s.C = o.c_mode == BQ_C_ZERO ? cplx(0, 0) : cplx(0, -0.5 * cs);
+      // G_x = x^p, G_y = y^q in the storage basis (values s(p), s(q)); R = 0
+      s.gx0 = sfl(kl.first);
+      s.gy0 = sfl(kl.second);
+      C.sys.push_back(s);
+    }
+  }
+
+  // ---- evaluation entries -----------------------------------------------------------
+  auto unflat = [&](int f) {
+    std::vector<int> k(nm);
+    for (int j = nm - 1; j >= 0; --j) { k[j] = f % C.M[j]; f /= C.M[j]; }
+    return k;
+  };
+  auto factor = [&](int kx, int ly) {  // A_{k,l} = sqrt(k! l!) / (s(k) s(l)) * stored value
+    const auto k = unflat(kx), l = unflat(ly);
+    return sqfact(k) * sqfact(l) / (sfl(k) * sfl(l));
+  };
+  C.trace_entries.clear();
+  std::map<Key, cplx> rho0 = p->rho0;
+  if (!p->rho0_set) rho0[{std::vector<int>(nm, 0), std::vector<int>(nm, 0)}] = cplx(1, 0);
+  for (auto& [kl, r0] : rho0) {
+    // Tr(rho0 A) = sum <k|rho0|l> <l|A|k>
+    if (!in_grid(kl.first) || !in_grid(kl.second) || r0 == cplx(0, 0)) continue;
+    EvalEntry e;
+    std::memset(&e, 0, sizeof(e));
+    e.kx = flat_index(kl.second, C.M, nm);
+    e.ly = flat_index(kl.first, C.M, nm);
+    const cplx f = r0 * factor(e.kx, e.ly);
+    e.f_re = f.real(); e.f_im = f.imag();
+    C.trace_entries.push_back(e);
+  }
+  int lo[3] = {1, 1, 1};
+  int D = 1;
+  for (int j = 0; j < nm; ++j) { lo[j] = std::min(3, C.M[j]); D *= lo[j]; }
+  C.block_dim = D;
+  C.block_entries.clear();
+  for (int a = 0; a < D; ++a)
+    for (int b = 0; b < D; ++b) {
+      std::vector<int> k(nm), l(nm);
+      int ra = a, rb = b;
+      for (int j = nm - 1; j >= 0; --j) { k[j] = ra % lo[j]; ra /= lo[j]; l[j] = rb % lo[j]; rb /= lo[j]; }
+      EvalEntry e;
+      std::memset(&e, 0, sizeof(e));
+      e.kx = flat_index(k, C.M, nm);
+      e.ly = flat_index(l, C.M, nm);
+      e.f_re = factor(e.kx, e.ly); e.f_im = 0.0;
+      C.block_entries.push_back(e);
+    }
+  return BQ_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// State.
+// ---------------------------------------------------------------------------------------
+struct Layout {
+  size_t off_sys, off_terms, off_chans, off_chpar, off_work, off_groups, off_entries, off_out, off_wtab, off_diag,
+      off_ctrl, off_init, off_y, off_ua, off_ub, off_acc, total;
+};
+
+struct bq_state {
+  int B = 0, nm = 0, dtype = 0, method = 0, basis = 0, n_sys = 0, n_work = 0, smem_bytes = 0;
+  int n_trace_groups = 0, n_block_groups = 0, block_dim = 0;
+  int64_t total_elems = 0;
+  double dt_max = 0.0, horizon = 0.0, tau = 0.0;
+  int reverse = 1;
+  char* pool = nullptr;
+  Layout L{};
+  std::vector<SysDesc> sys;
+  std::vector<int> prob_M;  // B * 3
+  // tau control (host mirror) and graph cache
+  double tau_base_host = 0.0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0.0;
+  int graph_steps = 0;
+};
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Plan {
+  std::vector<Compiled> comp;
+  std::vector<SysDesc> sys;
+  std::vector<TermDesc> terms;
+  std::vector<ChanDesc> chans;
+  std::vector<double> chpar;
+  std::vector<WorkItem> work;
+  std::vector<EvalGroup> groups;
+  std::vector<EvalEntry> entries;
+  std::vector<double> wtab;
+  std::vector<cplx> diag;
+  std::vector<InitEntry> init;
+  int n_trace_groups = 0, n_block_groups = 0, block_dim = 0, smem_bytes = 0;
+  int64_t total_elems = 0;
+  double rho = 0.0, dt_max = 0.0;
+  Layout L{};
+};
+
+static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o, Plan& P) {
+  if (!probs || B < 1 || !o) return fail(BQ_EINVAL, "bad map arguments");
+  if (o->method != BQ_METHOD_MAPPED && o->method != BQ_METHOD_DIRECT) return fail(BQ_EINVAL, "method");
+  if (o->dtype != BQ_F64 && o->dtype != BQ_F32) return fail(BQ_EINVAL, "dtype");
+  if (o->r_layout != BQ_R_FULL && o->r_layout != BQ_R_OFF) return fail(BQ_EINVAL, "r_layout");
+  const int nm = probs[0] ? probs[0]->nm : 0;
+  const size_t cs = o->dtype == BQ_F64 ? 16 : 8;  // complex element size
+  const size_t rs = cs / 2;
+  P.comp.resize(B);
+  int64_t elem = 0;
+  for (int b = 0; b < B; ++b) {
+    if (!probs[b]) return fail(BQ_EINVAL, "problem %d is NULL", b);
+    if (probs[b]->nm != nm) return fail(BQ_EINVAL, "all problems of a batch need the same number of modes");
+    int r = compile_problem(probs[b], *o, P.comp[b]);
+    if (r != BQ_OK) return r;
+    Compiled& C = P.comp[b];
+    if (C.sys.empty()) return fail(BQ_EINVAL, "problem %d: measured operator is zero on the grid", b);
+    P.rho = std::max(P.rho, C.rho);
+    const int term_off = (int)P.terms.size();
+    const int wbase = (int)P.wtab.size();
+    for (auto td : C.terms) {
+      for (int i = 0; i < td.n_act; ++i) td.wtab[i] += wbase;
+      if (td.ch >= 0) td.ch += (int)P.chans.size();
+      P.terms.push_back(td);
+    }
+    P.wtab.insert(P.wtab.end(), C.wtab.begin(), C.wtab.end());
+    const int cbase = (int)P.chpar.size();
+    for (auto cd : C.chans) { cd.par_off += cbase; P.chans.push_back(cd); }
+    P.chpar.insert(P.chpar.end(), C.chpar.begin(), C.chpar.end());
+    const int diag_off = (int)P.diag.size();
+    P.diag.insert(P.diag.end(), C.diag.begin(), C.diag.end());
+    const int sys_off = (int)P.sys.size();
+    for (auto& s : C.sys) {
+      SysDesc sd;
+      std::memset(&sd, 0, sizeof(sd));
+      sd.prob = b; sd.nm = nm;
+      for (int j = 0; j < 3; ++j) sd.M[j] = C.M[j];
+      sd.has_sep = C.has_sep; sd.has_r = C.has_r; sd.n_g = C.n_g; sd.n_r = C.n_r;
+      sd.term_off = term_off; sd.n_terms = (int)C.terms.size(); sd.diag_off = diag_off;
+      sd.halo_lo = C.halo_lo; sd.halo_hi = C.halo_hi; sd.p_flat = s.p_flat; sd.q_flat = s.q_flat;
+      int stG[3] = {1, 1, 1};
+      for (int j = nm - 2; j >= 0; --j) stG[j] = stG[j + 1] * C.M[j + 1];
+      for (int j = 0; j < nm; ++j) { sd.stG[j] = stG[j]; sd.stR[j] = stG[j] * C.n_g; sd.stR[nm + j] = stG[j]; }
+      sd.off_gx = sd.off_gy = sd.off_r = -1;
+      // element layout of one system: [G_x | G_y | R], each block 16-element aligned
+      auto pad16 = [](int64_t x) { return (x + 15) & ~(int64_t)15; };
+      if (C.has_sep) { sd.off_gx = elem; elem += pad16(C.n_g); sd.off_gy = elem; elem += pad16(C.n_g); }
+      if (C.has_r) { sd.off_r = elem; elem += pad16(C.n_r); }
+      sd.c_re = s.C.real(); sd.c_im = s.C.imag(); sd.w_re = s.w.real(); sd.w_im = s.w.imag();
+      P.sys.push_back(sd);
+    }
+    // initial values
+    if (C.method == BQ_METHOD_DIRECT) {
+      for (auto& [off, v] : C.init) P.init.push_back({P.sys[sys_off].off_r + off, v.real(), v.imag()});
+    } else {
+      for (size_t i = 0; i < C.sys.size(); ++i) {
+        const SysDesc& sd = P.sys[sys_off + i];
+        P.init.push_back({sd.off_gx + C.sys[i].p_flat, C.sys[i].gx0, 0.0});
+        P.init.push_back({sd.off_gy + C.sys[i].q_flat, C.sys[i].gy0, 0.0});
+      }
+    }
+    // evaluation groups: trace group b, then block groups appended later
+    EvalGroup g;
+    std::memset(&g, 0, sizeof(g));
+    g.prob = b; g.e_off = (int)P.entries.size(); g.n_e = (int)C.trace_entries.size();
+    g.sys_off = sys_off; g.n_sys = (int)C.sys.size();
+    P.entries.insert(P.entries.end(), C.trace_entries.begin(), C.trace_entries.end());
+    P.groups.push_back(g);
+  }
+  P.n_trace_groups = B;
+  P.block_dim = P.comp[0].block_dim;
+  for (int b = 0; b < B; ++b) {
+    const Compiled& C = P.comp[b];
+    if (C.block_dim != P.block_dim) { P.block_dim = -1; break; }
+  }
+  if (P.block_dim > 0) {
+    int sys_off = 0;
+    for (int b = 0; b < B; ++b) {
+      const Compiled& C = P.comp[b];
+      for (auto& e : C.block_entries) {
+        EvalGroup g;
+        std::memset(&g, 0, sizeof(g));
+        g.prob = b; g.e_off = (int)P.entries.size(); g.n_e = 1; g.sys_off = sys_off; g.n_sys = (int)C.sys.size();
+        P.entries.push_back(e);
+        P.groups.push_back(g);
+      }
+      sys_off += (int)C.sys.size();
+    }
+    P.n_block_groups = (int)P.groups.size() - B;
+  }
+  P.total_elems = std::max<int64_t>(elem, 16);
+
+  // ---- work items (tiles of R; the first tile of a system also updates G_x, G_y) ------
+  const int budget = (int)(96 * 1024 / cs);
+  int smem_max = 0;
+  for (int i = 0; i < (int)P.sys.size(); ++i) {
+    const SysDesc& sd = P.sys[i];
+    const int sep = sd.has_sep ? 2 * sd.n_g : 0;
+    if (!sd.has_r) {
+      WorkItem w{i, 0, 0, 1, 0, 0, sep, 0};
+      P.work.push_back(w);
+      smem_max = std::max(smem_max, sep);
+      continue;
+    }
+    if (sd.n_r + sep <= budget) {
+      WorkItem w{i, 0, sd.n_r, sd.has_sep, 0, sd.n_r, sd.n_r + sep, 0};
+      P.work.push_back(w);
+      smem_max = std::max(smem_max, sd.n_r + sep);
+      continue;
+    }
+    const int tl = budget - sep - sd.halo_lo - sd.halo_hi;
+    if (tl < 256) return fail(BQ_EUNSUPPORTED, "stencil halo too large for a shared-memory tile");
+    for (int s = 0; s < sd.n_r; s += tl) {
+      WorkItem w;
+      w.sys = i; w.start = s; w.len = std::min(tl, sd.n_r - s); w.do_sep = (s == 0) ? sd.has_sep : 0;
+      w.win_lo = std::max(0, s - sd.halo_lo);
+      w.win_hi = std::min(sd.n_r, s + w.len + sd.halo_hi);
+      w.smem_elems = (w.win_hi - w.win_lo) + sep; w.pad = 0;
+      smem_max = std::max(smem_max, w.smem_elems);
+      P.work.push_back(w);
+    }
+  }
+  P.smem_bytes = (int)(smem_max * cs);
+  P.dt_max = 2.0 * std::sqrt(2.0) / std::max(P.rho, 1e-300);
+  if (o->dt > 0.0 && o->dt > P.dt_max)
+    return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 stability bound %g (spectral bound %g)", o->dt, P.dt_max, P.rho);
+
+  // ---- layout -------------------------------------------------------------------------
+  Layout& L = P.L;
+  size_t o2 = 0;
+  auto seg = [&](size_t bytes) { size_t s = o2; o2 = align_up(o2 + std::max<size_t>(bytes, 1)); return s; };
+  L.off_sys = seg(P.sys.size() * sizeof(SysDesc));
+  L.off_terms = seg(P.terms.size() * sizeof(TermDesc));
+  L.off_chans = seg(P.chans.size() * sizeof(ChanDesc));
+  L.off_chpar = seg(P.chpar.size() * sizeof(double));
+  L.off_work = seg(P.work.size() * sizeof(WorkItem));
+  L.off_groups = seg(P.groups.size() * sizeof(EvalGroup));
+  L.off_entries = seg(P.entries.size() * sizeof(EvalEntry));
+  L.off_out = seg(P.groups.size() * 2 * sizeof(double));
+  L.off_wtab = seg(P.wtab.size() * rs);
+  L.off_diag = seg(P.diag.size() * cs);
+  L.off_ctrl = seg(64);
+  L.off_init = seg(P.init.size() * sizeof(InitEntry));
+  const size_t sbytes = (size_t)P.total_elems * cs;
+  L.off_y = seg(sbytes);
+  L.off_ua = seg(sbytes);
+  L.off_ub = seg(sbytes);
+  L.off_acc = seg(sbytes);
+  L.total = o2;
+  return BQ_OK;
+}
+
+extern "C" int bq_required_bytes(const bq_problem* const* probs, int B, const bq_map_opts* opts, size_t* out) {
+  if (!out) return fail(BQ_EINVAL, "out is NULL");
+  Plan P;
+  int r = make_plan(probs, B, opts, P);
+  if (r != BQ_OK) return r;
+  *out = P.L.total;
+  return BQ_OK;
+}
+
+template <typename T>
+static std::vector<T> to_real(const std::vector<double>& v) { return std::vector<T>(v.begin(), v.end()); }
+
+extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* o, void* pool, size_t pool_bytes,
+                      void* stream, bq_state** out) {
+  if (!out) return fail(BQ_EINVAL, "out is NULL");
+  *out = nullptr;
+  Plan P;
+  int r = make_plan(probs, B, o, P);
+  if (r != BQ_OK) return r;
+  if (!pool || ((uintptr_t)pool & 255)) return fail(BQ_EINVAL, "device pool must be non-NULL and 256-byte aligned");
+  if (pool_bytes < P.L.total) return fail(BQ_ENOMEM, "pool has %zu bytes, needs %zu", pool_bytes, P.L.total);
+  const double dt_max = P.dt_max;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)pool;
+  const Layout& L = P.L;
+  auto up = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+    if (!bytes) return cudaSuccess;
+    return cudaMemcpyAsync(base + off, src, bytes, cudaMemcpyHostToDevice, s);
+  };
+  CUDA_TRY(up(L.off_sys, P.sys.data(), P.sys.size() * sizeof(SysDesc)));
+  CUDA_TRY(up(L.off_terms, P.terms.data(), P.terms.size() * sizeof(TermDesc)));
+  CUDA_TRY(up(L.off_chans, P.chans.data(), P.chans.size() * sizeof(ChanDesc)));
+  CUDA_TRY(up(L.off_chpar, P.chpar.data(), P.chpar.size() * sizeof(double)));
+  CUDA_TRY(up(L.off_work, P.work.data(), P.work.size() * sizeof(WorkItem)));
+  CUDA_TRY(up(L.off_groups, P.groups.data(), P.groups.size() * sizeof(EvalGroup)));
+  CUDA_TRY(up(L.off_entries, P.entries.data(), P.entries.size() * sizeof(EvalEntry)));
+  if (o->dtype == BQ_F64) {
+    CUDA_TRY(up(L.off_wtab, P.wtab.data(), P.wtab.size() * sizeof(double)));
+    std::vector<double2> d(P.diag.size());
+    for (size_t i = 0; i < d.size(); ++i) d[i] = make_double2(P.diag[i].real(), P.diag[i].imag());
+    CUDA_TRY(up(L.off_diag, d.data(), d.size() * sizeof(double2)));
+  } else {
+    auto w = to_real<float>(P.wtab);
+    CUDA_TRY(up(L.off_wtab, w.data(), w.size() * sizeof(float)));
+    std::vector<float2> d(P.diag.size());
+    for (size_t i = 0; i < d.size(); ++i) d[i] = make_float2((float)P.diag[i].real(), (float)P.diag[i].imag());
+    CUDA_TRY(up(L.off_diag, d.data(), d.size() * sizeof(float2)));
+  }
+  CUDA_TRY(cudaMemsetAsync(base + L.off_ctrl, 0, 64, s));
+  CUDA_TRY(up(L.off_init, P.init.data(), P.init.size() * sizeof(InitEntry)));
+  const size_t cs = o->dtype == BQ_F64 ? 16 : 8;
+  CUDA_TRY(cudaMemsetAsync(base + L.off_y, 0, (size_t)P.total_elems * cs, s));
+  CUDA_TRY(bq::launch_scatter((const InitEntry*)(base + L.off_init), (int)P.init.size(), base + L.off_y, o->dtype, s));
+  g_launches++;
+  CUDA_TRY(cudaStreamSynchronize(s));
+
+  auto* st = new bq_state();
+  st->B = B; st->nm = probs[0]->nm; st->dtype = o->dtype; st->method = o->method; st->basis = P.comp[0].basis;
+  st->n_sys = (int)P.sys.size(); st->n_work = (int)P.work.size(); st->smem_bytes = P.smem_bytes;
+  st->n_trace_groups = P.n_trace_groups; st->n_block_groups = P.n_block_groups; st->block_dim = P.block_dim;
+  st->total_elems = P.total_elems; st->dt_max = dt_max; st->horizon = o->horizon; st->reverse = o->reverse_time;
+  st->pool = base; st->L = L; st->sys = P.sys;
+  for (int b = 0; b < B; ++b) for (int j = 0; j < 3; ++j) st->prob_M.push_back(P.comp[b].M[j]);
+  *out = st;
+  return BQ_OK;
+}
+
+extern "C" void bq_state_destroy(bq_state* s) {
+  if (!s) return;
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  delete s;
+}
+
+// ---------------------------------------------------------------------------------------
+// Stepping.
+// ---------------------------------------------------------------------------------------
+static bq::StageArgs stage_args(bq_state* s, int stage, double dt) {
+  bq::StageArgs a;
+  char* b = s->pool;
+  const Layout& L = s->L;
+  a.sys = (const SysDesc*)(b + L.off_sys);
+  a.terms = (const TermDesc*)(b + L.off_terms);
+  a.chans = (const ChanDesc*)(b + L.off_chans);
+  a.chpar = (const double*)(b + L.off_chpar);
+  a.wtab = b + L.off_wtab;
+  a.diag = b + L.off_diag;
+  a.work = (const WorkItem*)(b + L.off_work);
+  // ping-pong: stage 1 reads y -> ua; 2 reads ua -> ub; 3 reads ub -> ua; 4 reads ua -> y
+  void* y = b + L.off_y;
+  void* ua = b + L.off_ua;
+  void* ub = b + L.off_ub;
+  a.u_in = stage == 1 ? y : (stage == 2 ? ua : (stage == 3 ? ub : ua));
+  a.u_out = stage == 1 ? ua : (stage == 2 ? ub : (stage == 3 ? ua : nullptr));
+  a.y = y;
+  a.acc = b + L.off_acc;
+  a.tau_base = (const double*)(b + L.off_ctrl);
+  a.counter = (long long*)(b + L.off_ctrl + 8);
+  a.ticket = (unsigned int*)(b + L.off_ctrl + 16);
+  a.dt = dt;
+  a.horizon = s->horizon;
+  a.reverse = s->reverse;
+  a.stage = stage;
+  return a;
+}
+
+static cudaError_t enqueue_steps(bq_state* s, double dt, int64_t n, cudaStream_t st) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int stage = 1; stage <= 4; ++stage) {
+      cudaError_t e = bq::launch_stage(stage_args(s, stage, dt), s->dtype, s->nm, s->n_work, s->smem_bytes, st);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
+static const int kGraphSteps = 64;
+
+extern "C" int bq_step(bq_state* s, double dt, int64_t n_steps, void* stream) {
+  if (!s) return fail(BQ_EINVAL, "state is NULL");
+  if (n_steps < 0) return fail(BQ_EINVAL, "n_steps < 0");
+  if (!(dt > 0.0)) return fail(BQ_EINVAL, "dt must be > 0");
+  if (dt > s->dt_max * (1.0 + 1e-12))
+    return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 stability bound %g", dt, s->dt_max);
+  if (n_steps == 0) return BQ_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* b = s->pool;
+  // tau at the start of this call; the stage kernels add counter * dt
+  s->tau_base_host = s->tau;
+  CUDA_TRY(cudaMemcpyAsync(b + s->L.off_ctrl, &s->tau_base_host, sizeof(double), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemsetAsync(b + s->L.off_ctrl + 8, 0, 16, st));
+  int64_t left = n_steps;
+  if (n_steps >= kGraphSteps) {
+    if (!s->graph || s->graph_dt != dt) {
+      if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
+      if (!s->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+      cudaGraph_t g;
+      CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = enqueue_steps(s, dt, kGraphSteps, s->cap_stream);
+      cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &g);
+      if (e != cudaSuccess) return fail(BQ_ECUDA, "capture: %s", cudaGetErrorString(e));
+      if (e2 != cudaSuccess) return fail(BQ_ECUDA, "end capture: %s", cudaGetErrorString(e2));
+      CUDA_TRY(cudaGraphInstantiate(&s->graph, g, 0));
+      cudaGraphDestroy(g);
+      s->graph_dt = dt;
+    }
+    while (left >= kGraphSteps) {
+      CUDA_TRY(cudaGraphLaunch(s->graph, st));
+      g_launches += 4 * kGraphSteps;
+      left -= kGraphSteps;
+    }
+  }
+  if (left > 0) {
+    CUDA_TRY(enqueue_steps(s, dt, left, st));
+    g_launches += 4 * left;
+  }
+  s->tau += (double)n_steps * dt;
+  return BQ_OK;
+}
+
+extern "C" int bq_time(const bq_state* s, double* tau) {
+  if (!s || !tau) return fail(BQ_EINVAL, "NULL argument");
+  *tau = s->tau;
+  return BQ_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Evaluation.
+// ---------------------------------------------------------------------------------------
+static int run_eval(bq_state* s, int g0, int n, double* out_host, cudaStream_t st) {
+  char* b = s->pool;
+  const Layout& L = s->L;
+  CUDA_TRY(bq::launch_eval((const SysDesc*)(b + L.off_sys), (const EvalGroup*)(b + L.off_groups) + g0,
+                           (const EvalEntry*)(b + L.off_entries), b + L.off_y, (double2*)(b + L.off_out) + g0, n,
+                           s->dtype, st));
+  g_launches++;
+  CUDA_TRY(cudaMemcpyAsync(out_host, b + L.off_out + (size_t)g0 * 16, (size_t)n * 16, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < 2 * n; ++i)
+    if (!std::isfinite(out_host[i])) return fail(BQ_ENONFINITE, "non-finite observable");
+  return BQ_OK;
+}
+
+extern "C" int bq_evaluate(bq_state* s, double* out_host, void* stream) {
+  if (!s || !out_host) return fail(BQ_EINVAL, "NULL argument");
+  return run_eval(s, 0, s->n_trace_groups, out_host, (cudaStream_t)stream);
+}
+
+extern "C" int bq_fock_block(bq_state* s, int lo, double* out_host, void* stream) {
+  if (!s || !out_host) return fail(BQ_EINVAL, "NULL argument");
+  if (s->block_dim <= 0) return fail(BQ_EUNSUPPORTED, "problems of the batch have different block shapes");
+  if (lo != 3) return fail(BQ_EUNSUPPORTED, "only lo = 3 (the paper's three lowest levels) is precompiled");
+  return run_eval(s, s->n_trace_groups, s->n_block_groups, out_host, (cudaStream_t)stream);
+}
+
+extern "C" int bq_state_info(const bq_state* s, int* n_systems, int64_t* total_elems) {
+  if (!s) return fail(BQ_EINVAL, "state is NULL");
+  if (n_systems) *n_systems = s->n_sys;
+  if (total_elems) *total_elems = s->total_elems;
+  return BQ_OK;
+}
+
+extern "C" int bq_system_info(const bq_state* s, int sys, int* problem, int* p_idx, int* q_idx, int64_t* n_gx,
+                              int64_t* n_gy, int64_t* n_r, double* w, double* c) {
+  if (!s || sys < 0 || sys >= s->n_sys) return fail(BQ_EINVAL, "bad system index");
+  const SysDesc& sd = s->sys[sys];
+  if (problem) *problem = sd.prob;
+  if (p_idx) *p_idx = sd.p_flat;
+  if (q_idx) *q_idx = sd.q_flat;
+  if (n_gx) *n_gx = sd.has_sep ? sd.n_g : 0;
+  if (n_gy) *n_gy = sd.has_sep ? sd.n_g : 0;
+  if (n_r) *n_r = sd.has_r ? sd.n_r : 0;
+  if (w) { w[0] = sd.w_re; w[1] = sd.w_im; }
+  if (c) { c[0] = sd.c_re; c[1] = sd.c_im; }
+  return BQ_OK;
+}
+
+extern "C" int bq_read_system(bq_state* s, int sys, double* gx, double* gy, double* r, void* stream) {
+  if (!s || sys < 0 || sys >= s->n_sys) return fail(BQ_EINVAL, "bad system index");
+  const SysDesc& sd = s->sys[sys];
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t cs = s->dtype == BQ_F64 ? 16 : 8;
+  const char* y = s->pool + s->L.off_y;
+  const int nm = s->nm;
+  auto sflat = [&](int f) {  // s(k) of the storage basis for a flat per-mode index
+    double v = 1.0;
+    for (int j = nm - 1; j >= 0; --j) { const int k = f % sd.M[j]; f /= sd.M[j]; v *= s_of(s->basis, k); }
+    return v;
+  };
+  auto fetch = [&](int64_t off, int64_t n, double* dst, bool is_r) -> int {
+    std::vector<char> h((size_t)n * cs);
+    CUDA_TRY(cudaMemcpyAsync(h.data(), y + off * cs, (size_t)n * cs, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < n; ++i) {
+      double re, im;
+      if (cs == 16) { re = ((double*)h.data())[2 * i]; im = ((double*)h.data())[2 * i + 1]; }
+      else { re = ((float*)h.data())[2 * i]; im = ((float*)h.data())[2 * i + 1]; }
+      double sc = 1.0;
+      if (s->method == BQ_METHOD_MAPPED) {
+        if (is_r) sc = sflat((int)(i / sd.n_g)) * sflat((int)(i % sd.n_g));
+        else sc = sflat((int)i);
+      }
+      dst[2 * i] = re / sc;
+      dst[2 * i + 1] = im / sc;
+    }
+    return BQ_OK;
+  };
+  int rc;
+  if (gx && sd.has_sep && (rc = fetch(sd.off_gx, sd.n_g, gx, false)) != BQ_OK) return rc;
+  if (gy && sd.has_sep && (rc = fetch(sd.off_gy, sd.n_g, gy, false)) != BQ_OK) return rc;
+  if (r && sd.has_r && (rc = fetch(sd.off_r, sd.n_r, r, true)) != BQ_OK) return rc;
+  return BQ_OK;
+}
+
+extern "C" int bq_state_bytes(const bq_state* s, size_t* nbytes) {
+  if (!s || !nbytes) return fail(BQ_EINVAL, "NULL argument");
+  *nbytes = (size_t)s->total_elems * (s->dtype == BQ_F64 ? 16 : 8);
+  return BQ_OK;
+}
+
+extern "C" int bq_store_state(bq_state* s, void* host, void* stream) {
+  if (!s || !host) return fail(BQ_EINVAL, "NULL argument");
+  const size_t n = (size_t)s->total_elems * (s->dtype == BQ_F64 ? 16 : 8);
+  CUDA_TRY(cudaMemcpyAsync(host, s->pool + s->L.off_y, n, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  return BQ_OK;
+}
+
+extern "C" int bq_load_state(bq_state* s, const void* host, void* stream) {
+  if (!s || !host) return fail(BQ_EINVAL, "NULL argument");
+  const size_t n = (size_t)s->total_elems * (s->dtype == BQ_F64 ? 16 : 8);
+  CUDA_TRY(cudaMemcpyAsync(s->pool + s->L.off_y, host, n, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  return BQ_OK;
+}
+
+extern "C" int bq_set_time(bq_state* s, double tau) {
+  if (!s || !std::isfinite(tau)) return fail(BQ_EINVAL, "bad argument");
+  s->tau = tau;
+  return BQ_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Diagnostics.
+// ---------------------------------------------------------------------------------------
+extern "C" const char* bq_status_string(int status) {
+  switch (status) {
+    case BQ_OK: return "ok";
+    case BQ_EINVAL: return "invalid argument";
+    case BQ_EUNSTABLE_DT: return "time step above the RK4 stability bound";
+    case BQ_ENOMEM: return "device buffer too small";
+    case BQ_ECUDA: return "CUDA error";
+    case BQ_ENONFINITE: return "non-finite value";
+    case BQ_ETIMEOUT: return "device wait timed out";
+    case BQ_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* bq_last_error(void) { return g_err.c_str(); }
+
+extern "C" int64_t bq_launch_count(void) { return g_launches.load(); }

@@ -1,0 +1,113 @@
+// Internal data structures shared by the host compiler and the CUDA kernels.
+// All structs are plain-old-data with identical layout on host and device; they are
+// written into the caller's device pool by bq_map() and read by the kernels.
+#pragma once
+
+#include <stdint.h>
+
+#define BQ_MAXD 6          // max R dimensions = 2 * BQ_MAX_MODES
+#define BQ_MAX_TERMS 64    // max general (non-folded) stencil terms per problem
+#define BQ_BLOCK 128       // threads per CTA of the stage kernels
+
+namespace bq {
+
+enum Side : int { SIDE_X = 0, SIDE_Y = 1, SIDE_S = 2 };
+
+// One general stencil term of the coupled system (Eqs. 9a-c): a monomial x^a d^b in
+// each of its active dimensions (x-dims 0..nm-1, y-dims nm..2nm-1 of R).
+//  * SIDE_X: left multiplication of A by an operator  -> acts on G_x and on R's x-dims;
+//  * SIDE_Y: right multiplication                     -> acts on G_y and on R's y-dims;
+//  * SIDE_S: sandwich L^dag A L                       -> acts on R (x- and y-dims at once)
+//            and is the source S(G_x G_y) of Eq. 9c / 303c.
+// The value added at point k is coef(t) * prod_i W_i[k_dim_i] * u[k + delta], where
+// W_i is a weight table (zero where the source index leaves the grid).
+struct TermDesc {
+  double c_re, c_im;   // static part of the coefficient (rate, param, basis factors folded in)
+  int ch;              // channel index into the state's channel table, -1 = static
+  int conj;            // multiply by conj(channel) instead of channel
+  int side;            // Side
+  int n_act;           // number of active dimensions
+  int deltaR;          // linear source offset in R
+  int deltaGx;         // linear source offset in G_x (SIDE_X, SIDE_S x-part)
+  int deltaGy;         // linear source offset in G_y (SIDE_Y, SIDE_S y-part)
+  int param;           // gradient parameter index or -1 (coefficient = theta * c)
+  int8_t dim[BQ_MAXD];
+  int8_t pad8[2];
+  int wtab[BQ_MAXD];   // element offsets of the weight tables (length M_dim each)
+};
+
+// Drive envelope.
+struct ChanDesc {
+  int kind;
+  int n_par;
+  int par_off;  // into the channel parameter pool (double)
+  int pad;
+};
+
+// One system = one separable initial condition of one problem (or one direct state).
+struct SysDesc {
+  int prob;             // problem index in the batch
+  int nm;               // number of modes
+  int M[3];             // grid per mode
+  int has_sep;          // G_x, G_y present (mapped method)
+  int has_r;            // R present
+  int n_g;              // elements of G_x (= of G_y) = prod M
+  int n_r;              // elements of R = n_g^2
+  int term_off, n_terms;
+  int diag_off;         // complex element offset of 2*nm diagonal tables (length M_d each)
+  int halo_lo, halo_hi; // max negative / positive linear offset of any R term
+  int p_flat, q_flat;   // initial condition indices (flattened)
+  int stR[BQ_MAXD];     // element strides of R (x-dims outer, y-dims inner)
+  int stG[3];           // element strides of G_x / G_y
+  int pad;
+  int64_t off_gx, off_gy, off_r;  // complex element offsets into the state arrays
+  double c_re, c_im;    // separation constant C (Eq. 304)
+  double w_re, w_im;    // weight g_{p,q}(0) of the initial condition
+};
+
+// A CTA's share of one stage: a tile of R points of one system (plus G_x, G_y if sep).
+struct WorkItem {
+  int sys;
+  int start, len;       // R tile [start, start + len)
+  int do_sep;           // this CTA also updates G_x and G_y
+  int win_lo, win_hi;   // R window staged in shared memory
+  int smem_elems;       // complex elements of shared memory this item needs
+  int pad;
+};
+
+// Evaluation: out[g] = sum_{IC of problem} w_IC * sum_{e in group} f_e * G_IC(k_e, l_e)
+// where G_IC(k, l) = gx[k] gy[l] + R[k, l] in storage basis.
+struct EvalGroup {
+  int prob;
+  int e_off, n_e;       // entries
+  int sys_off, n_sys;   // systems (ICs) of the problem (contiguous)
+  int pad[3];
+};
+struct EvalEntry {
+  int kx, ly;           // flat x-index, flat y-index
+  int pad[2];
+  double f_re, f_im;    // factor
+};
+
+struct StageArgs {
+  const SysDesc* sys;
+  const TermDesc* terms;
+  const ChanDesc* chans;
+  const double* chpar;
+  const void* wtab;     // weight tables (real type of the state)
+  const void* diag;     // diagonal tables (complex of the state type)
+  const WorkItem* work;
+  const void* u_in;     // stage input (y for stage 1)
+  void* u_out;          // next stage input (stages 1-3)
+  void* y;              // state (read stages 2-3, written stage 4)
+  void* acc;            // RK4 accumulator
+  const double* tau_base;      // device: tau at counter = 0
+  long long* counter;          // device: completed steps since tau_base
+  unsigned int* ticket;        // device: stage-4 completion ticket
+  double dt;
+  double horizon;
+  int reverse;
+  int stage;            // 1..4
+};
+
+}  // namespace bq

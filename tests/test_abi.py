@@ -1,0 +1,88 @@
+"""CPU-only checks of the C ABI: the library loads, exports every function include/bq.h
+declares, and its host logic (problem validation, planning, stability bound) behaves."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_2203_05526_gb300 as bq
+from paper_2203_05526_gb300 import binding
+from workloads import configs
+from workloads.spec import HTerm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2203_05526_gb300 import build
+    build.build()
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(bq_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported():
+    L = bq.lib()
+    names = declared_functions()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(bq.exported_symbols()) <= set(names)
+
+
+def required(spec, **kw):
+    h = bq.problem_from_spec(spec)
+    arr = (C.c_void_p * 1)(h.ptr.value)
+    n = C.c_size_t()
+    st = bq.lib().bq_required_bytes(arr, 1, C.byref(bq.map_opts(**kw)), C.byref(n))
+    return st, n.value
+
+
+def test_required_bytes_and_layout():
+    st, n = required(configs.kerr_driven(N=40), grid=[12], dt=0.0025, horizon=100.0)
+    assert st == 0 and n > 4 * 16 * (12 * 12 + 2 * 12)
+    st64, n64 = required(configs.kerr_driven(N=40), grid=[12], dt=0.0025, horizon=100.0, dtype="f32")
+    assert st64 == 0 and n64 < n
+
+
+def test_unstable_dt_refused():
+    # N = 40 Kerr at dt = 0.01: |K|/2 * 39 * 38 * dt ~ 9.3 > 2 sqrt 2
+    st, _ = required(configs.kerr_driven(N=40), method="direct", dt=0.01, horizon=100.0)
+    assert st == binding.BQ_EUNSTABLE_DT
+    st, _ = required(configs.kerr_driven(N=40), method="direct", dt=0.0025, horizon=100.0)
+    assert st == 0
+
+
+def test_non_hermitian_hamiltonian_refused():
+    p = configs.kerr_driven(N=8)
+    p.h_terms = p.h_terms[:-1]  # drop the conjugate drive term
+    st, _ = required(p, dt=0.001)
+    assert st == binding.BQ_EINVAL
+    assert "Hermitian" in bq.lib().bq_last_error().decode()
+
+
+def test_bad_arguments():
+    with pytest.raises(bq.BQError):
+        bq.ProblemHandle(0, [4])
+    with pytest.raises(bq.BQError):
+        bq.ProblemHandle(4, [4, 4, 4, 4])
+    h = bq.ProblemHandle(1, [4])
+    with pytest.raises(bq.BQError):
+        h.add_h_term(1.0, [1], [1], channel=3)
+    with pytest.raises(bq.BQError):
+        h.add_channel("gauss", [1.0, 0.0, 1.0, 0.0])  # sigma = 0
+
+
+def test_too_many_modes_grid_unsupported():
+    st, _ = required(configs.kerr_static(N=200), dt=1e-4)
+    assert st == binding.BQ_EUNSUPPORTED

@@ -1,0 +1,158 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.  Tolerances: 1e-10 relative in FP64, 1e-5 in FP32 (relative to the largest
+element of the compared array or block)."""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fock, mapping
+from workloads import configs
+from workloads.spec import Problem
+
+from parity import compare_mapped_systems, gpu_state, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-5
+
+SMALL = [  # (seed, n_modes, N, steps): several tiles only for 2-3 modes, ragged sizes
+    (101, 1, 7, 30),
+    (102, 1, 13, 25),
+    (103, 2, 4, 20),
+    (104, 2, 5, 12),
+    (105, 3, 3, 10),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    from paper_2203_05526_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("seed,nm,N,steps", SMALL)
+@pytest.mark.parametrize("dense", [False, True])
+def test_mapped_f64_state_matches_oracle(seed, nm, N, steps, dense):
+    p = configs.random_problem(seed, n_modes=nm, N=N, n_steps=steps, dt=0.01, dense_measured=dense)
+    st = gpu_state(p)
+    st.step(p.dt, steps)
+    _sync()
+    run = mapping.rk4_mapped(p)
+    compare_mapped_systems(st, run, TOL64)
+    # observables: Tr(rho0 A) and the three-level block
+    A = run.fock_matrix()
+    tr = st.evaluate()[0]
+    ref = A[0, 0]
+    assert abs(tr - ref) <= TOL64 * max(1.0, np.max(np.abs(A)))
+    D = int(np.prod([min(3, n) for n in p.N]))
+    blk = st.fock_block(3, dim=D)[0]
+    assert np.max(np.abs(blk - fock.low_block(A, p.N))) <= TOL64 * max(1.0, np.max(np.abs(A)))
+
+
+@pytest.mark.parametrize("seed,nm,N,steps", SMALL)
+def test_direct_f64_matches_oracle(seed, nm, N, steps):
+    p = configs.random_problem(seed, n_modes=nm, N=N, n_steps=steps, dt=0.01, dense_measured=True)
+    st = gpu_state(p, method="direct")
+    st.step(p.dt, steps)
+    _sync()
+    A = fock.rk4_adjoint(p)
+    info, _, _, r = st.read_system(0)
+    assert rel_err(r, A.reshape(-1)) <= TOL64
+    assert abs(st.evaluate()[0] - A[0, 0]) <= TOL64 * np.max(np.abs(A))
+
+
+def test_mapped_all_in_r_equals_direct_on_gpu():
+    """Both GPU methods integrate the same generator; with M = N they agree to RK4 error."""
+    p = configs.random_problem(111, n_modes=1, N=8, n_steps=40, dt=0.005, dense_measured=True)
+    a = gpu_state(p)
+    b = gpu_state(p, method="direct")
+    a.step(p.dt, 40)
+    b.step(p.dt, 40)
+    _sync()
+    D = 3
+    assert rel_err(a.fock_block(3, dim=D), b.fock_block(3, dim=D)) < 1e-6
+
+
+@pytest.mark.parametrize("seed,nm,N,steps", SMALL[:3])
+def test_mapped_f32_matches_oracle(seed, nm, N, steps):
+    p = configs.random_problem(seed, n_modes=nm, N=N, n_steps=steps, dt=0.01, dense_measured=True)
+    st = gpu_state(p, dtype="f32")
+    st.step(p.dt, steps)
+    _sync()
+    run = mapping.rk4_mapped(p)
+    A = run.fock_matrix()
+    D = int(np.prod([min(3, n) for n in p.N]))
+    assert rel_err(st.fock_block(3, dim=D)[0], fock.low_block(A, p.N)) <= TOL32
+    compare_mapped_systems(st, run, 1e-4)
+
+
+def test_r_layout_off_and_zero_c():
+    p = configs.random_problem(121, n_modes=1, N=6, n_steps=20, dt=0.01)
+    for r_layout, c_mode in (("off", "eq304"), ("full", "zero")):
+        st = gpu_state(p, r_layout=r_layout, c_mode=c_mode)
+        st.step(p.dt, 20)
+        _sync()
+        run = mapping.rk4_mapped(p, r_layout=r_layout, C_override=0.0 if c_mode == "zero" else None)
+        compare_mapped_systems(st, run, TOL64)
+
+
+def test_graph_path_and_split_calls():
+    """130 steps in one call (two CUDA-graph replays + 2 direct steps) equal 3 + 127 steps in
+    two calls and the oracle: the device step counter and tau bookkeeping are exact."""
+    p = configs.random_problem(131, n_modes=1, N=6, n_steps=130, dt=0.005)
+    a = gpu_state(p)
+    a.step(p.dt, 130)
+    b = gpu_state(p)
+    b.step(p.dt, 3)
+    b.step(p.dt, 127)
+    _sync()
+    run = mapping.rk4_mapped(p)
+    compare_mapped_systems(a, run, TOL64)
+    compare_mapped_systems(b, run, TOL64)
+    assert abs(a.time() - 130 * 0.005) < 1e-12
+
+
+def test_kerr_static_full_horizon():
+    """The single damped Kerr oscillator, |1><1|, 10 000 steps of 0.01 ns: mapped (M = 3) and
+    direct (N = 16) against O2 / O1, and the binomial closed form."""
+    p = configs.kerr_static(N=16)
+    st = gpu_state(p, grid=[3])
+    st.step(p.dt, p.n_steps)
+    d = gpu_state(p, method="direct")
+    d.step(p.dt, p.n_steps)
+    _sync()
+    run = mapping.rk4_mapped(p, M=(3,))
+    compare_mapped_systems(st, run, TOL64)
+    A = fock.rk4_adjoint(p)
+    _, _, _, r = d.read_system(0)
+    assert rel_err(r, A.reshape(-1)) <= TOL64
+    gt = 1e-3 * p.T
+    blk = st.fock_block(3, dim=3)[0]
+    for k in range(3):
+        ref = math.comb(k, 1) * math.exp(-gt) * (1 - math.exp(-gt)) ** (k - 1) if k >= 1 else 0.0
+        assert abs(blk[k, k] - ref) < 1e-12
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", TOL64), ("f32", TOL32)])
+def test_kerr_driven_full_horizon(dtype, tol):
+    """Finite temperature + resonant Gaussian drive, N = 40 oracle, grid M = 12, 40 000 steps."""
+    p = configs.kerr_driven(N=40)
+    st = gpu_state(p, grid=[12], dtype=dtype)
+    st.step(p.dt, p.n_steps)
+    _sync()
+    run = mapping.rk4_mapped(p, M=(12,))
+    A = run.fock_matrix()
+    blk = st.fock_block(3, dim=3)[0]
+    assert rel_err(blk, A[:3, :3]) <= tol
+    if dtype == "f64":
+        compare_mapped_systems(st, run, TOL64)
