@@ -138,6 +138,26 @@ int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* opts, void*
  * replayed from a CUDA graph; asynchronous on stream. */
 int bq_step(bq_state* s, double dt, int64_t n_steps, void* stream);
 
+/* bq_step without any memory allocation, for callers that cannot allocate device memory
+ * (code running inside another framework's CUDA-graph capture, where cudaMalloc is
+ * illegal, or embedded callers with a fixed memory budget decided at start-up).  The
+ * paper has no counterpart: it is an alternative scratch placement of bq_step.
+ *
+ * The two RK4 stage buffers and the accumulator are taken from a fixed device array
+ * compiled into this library (3 buffers of 4 MiB each, i.e. states of up to 262 144
+ * complex FP64 or 524 288 complex FP32 elements; larger states get BQ_EUNSUPPORTED).
+ * Every GPU that loads the library holds that array until the process exits.  The state's
+ * own scratch regions in its pool are not touched.  No CUDA graph is used: 4 plain kernel
+ * launches per step on stream.
+ *   - The first call on a device looks up the array's device address (once per device,
+ *     with that device current); make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents; the RK4 stages
+ *     overwrite every element they read, so nothing needs clearing between calls.  Calls
+ *     whose work overlaps on the GPU (different streams, or other threads) race on the
+ *     array: serialise them.
+ * Results equal bq_step's to rounding. */
+int bq_step_fixed_scratch(bq_state* s, double dt, int64_t n_steps, void* stream);
+
 /* Current integration time tau of the state (host copy, no synchronisation). */
 int bq_time(const bq_state* s, double* tau);
 

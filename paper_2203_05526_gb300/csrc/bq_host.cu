@@ -913,6 +913,44 @@ extern "C" int bq_step(bq_state* s, double dt, int64_t n_steps, void* stream) {
   return BQ_OK;
 }
 
+// Same stepping as bq_step, with the RK4 scratch taken from the library's fixed device
+// array (see bq_step_fixed_scratch in bq.h).  No allocation of any kind: plain launches,
+// no CUDA graph.
+extern "C" int bq_step_fixed_scratch(bq_state* s, double dt, int64_t n_steps, void* stream) {
+  if (!s) return fail(BQ_EINVAL, "state is NULL");
+  if (n_steps < 0) return fail(BQ_EINVAL, "n_steps < 0");
+  if (!(dt > 0.0)) return fail(BQ_EINVAL, "dt must be > 0");
+  if (dt > s->dt_max * (1.0 + 1e-12))
+    return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 stability bound %g", dt, s->dt_max);
+  const size_t need = (size_t)s->total_elems * (s->dtype == BQ_F64 ? 16 : 8);
+  if (need > BQ_FIXED_SCRATCH_BYTES)
+    return fail(BQ_EUNSUPPORTED, "state needs %zu bytes per scratch buffer; the fixed scratch holds %u "
+                "(use bq_step for larger states)", need, (unsigned)BQ_FIXED_SCRATCH_BYTES);
+  if (n_steps == 0) return BQ_OK;
+  void* scratch = nullptr;
+  CUDA_TRY(bq::fixed_scratch(&scratch));
+  char* ua = (char*)scratch;
+  char* ub = ua + BQ_FIXED_SCRATCH_BYTES;
+  char* acc = ub + BQ_FIXED_SCRATCH_BYTES;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* b = s->pool;
+  s->tau_base_host = s->tau;
+  CUDA_TRY(cudaMemcpyAsync(b + s->L.off_ctrl, &s->tau_base_host, sizeof(double), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemsetAsync(b + s->L.off_ctrl + 8, 0, 16, st));
+  for (int64_t i = 0; i < n_steps; ++i)
+    for (int stage = 1; stage <= 4; ++stage) {
+      bq::StageArgs a = stage_args(s, stage, dt);
+      void* y = b + s->L.off_y;
+      a.u_in = stage == 1 ? (const void*)y : (stage == 3 ? (const void*)ub : (const void*)ua);
+      a.u_out = stage == 1 ? (void*)ua : (stage == 2 ? (void*)ub : (stage == 3 ? (void*)ua : nullptr));
+      a.acc = acc;
+      CUDA_TRY(bq::launch_stage(a, s->dtype, s->nm, s->n_work, s->smem_bytes, st));
+      g_launches++;
+    }
+  s->tau += (double)n_steps * dt;
+  return BQ_OK;
+}
+
 extern "C" int bq_time(const bq_state* s, double* tau) {
   if (!s || !tau) return fail(BQ_EINVAL, "NULL argument");
   *tau = s->tau;

@@ -13,6 +13,8 @@
 // and accumulator are streamed with coalesced accesses.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "bq_internal.h"
 #include "bq_launch.h"
 
@@ -314,6 +316,34 @@ __global__ void k_scatter(const InitEntry* __restrict__ ent, int n, void* ystate
   C* y = reinterpret_cast<C*>(ystate);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[ent[i].off] = cmk<C>(ent[i].re, ent[i].im);
+}
+
+// ---------------------------------------------------------------------------------------
+// Fixed RK4 scratch for callers that cannot allocate device memory.
+//
+// bq_step_fixed_scratch() takes the two stage buffers and the RK4 accumulator from this
+// file-scope array instead of from the state's pool.  Every GPU that loads the library
+// holds it until the process exits.  Host code must not use the symbol's name as an
+// address: fixed_scratch() looks the device address up once per device.
+// ---------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_fixed_scratch[3 * BQ_FIXED_SCRATCH_BYTES];
+
+cudaError_t fixed_scratch(void** ptr) {
+  static std::mutex mu;
+  static void* cache[256] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cache[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_fixed_scratch);
+    if (e != cudaSuccess) return e;
+    cache[dev] = p;
+  }
+  *ptr = cache[dev];
+  return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------------------
