@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--instances", type=int, default=65536, help="instances per GPU")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 4096-instance full-solve leg")
     return ap.parse_args()
 
 
@@ -139,6 +140,65 @@ class Clocks:
         os.unlink(self.f.name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def batched_leg(world: int):
+    """The 4096-instance batch itself (seed 20220311, complex FP32, T = 100 ns, dt = 0.002 ns,
+    50 000 RK4 steps): full solves through the persistent one-launch path (bq_solve), through
+    the streamed stage kernels (bq_step, CUDA-graph replays), and the plain
+    one-instance-per-launch path (each instance its own state and launches), the latter timed
+    on a sample of instances and steps and scaled to the full batch."""
+    import numpy as np
+    import torch
+
+    import paper_2203_05526_gb300 as bq
+    from workloads import configs
+    specs = configs.kerr_batch(B=4096, T=HORIZON, dt=DT)
+    n_steps = specs[0].n_steps
+    pts = points_of(specs)
+    opts = bq.map_opts(method="mapped", dtype="f32", horizon=HORIZON, dt=DT)
+    handles = [bq.problem_from_spec(p) for p in specs]
+    out = {"workload": "kerr_batch 4096 instances, complex FP32, T=100 ns, dt=0.002 ns (50000 RK4 steps)"}
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    st = bq.State(handles, opts)
+    st.solve(DT, 200)  # warm-up
+    st = bq.State(handles, opts)
+    n0 = bq.launch_count()
+    t_solve = timed(lambda: st.solve(DT, n_steps))
+    launches = bq.launch_count() - n0
+    ev = st.evaluate()
+    out["persistent"] = {"seconds": t_solve, "solves_per_s": 4096 / t_solve,
+                         "updates_per_s": 4 * pts * n_steps / t_solve, "launches": launches,
+                         "finite": bool(np.all(np.isfinite(ev)))}
+    st2 = bq.State(handles, opts)
+    st2.step(DT, 128)
+    st2 = bq.State(handles, opts)
+    t_step = timed(lambda: st2.step(DT, n_steps))
+    out["streamed"] = {"seconds": t_step, "solves_per_s": 4096 / t_step,
+                       "updates_per_s": 4 * pts * n_steps / t_step}
+    # one instance per launch: 16 sampled instances, 2000 steps each, scaled
+    sample = list(range(0, 4096, 256))
+    sample_steps = 2000
+    tot = 0.0
+    for i in sample:
+        s1 = bq.State([handles[i]], opts)
+        s1.step(DT, 64)
+        tot += timed(lambda: s1.step(DT, sample_steps)) * (n_steps / sample_steps)
+    per_inst = tot / len(sample)
+    out["one_instance_per_launch"] = {"seconds_per_instance_solve": per_inst, "solves_per_s": 1.0 / per_inst,
+                                      "sample": f"instances {sample[0]}..{sample[-1]} step 256, {sample_steps} of "
+                                                f"{n_steps} steps each, scaled"}
+    out["persistent_vs_one_per_launch"] = out["persistent"]["solves_per_s"] / out["one_instance_per_launch"]["solves_per_s"]
+    return out
 
 
 def run_reference(args, rank, world):
@@ -238,10 +298,11 @@ def main():
     upd_per_step = 4 * pts
     value = world * upd_per_step * args.steps / (ms / 1e3)
 
-    # roofline of the fused stage kernel: algorithmic bytes = 16 array transfers per RK4 step
-    # per grid point (stage 1: 3, stages 2-3: 5, stage 4: 3), i.e. 4 per stage-launch
+    # roofline of the fused stage kernel: algorithmic bytes = 19 array transfers per RK4 step
+    # per grid point (stage 1: read y, write u, inc = 3; stages 2-3: read u, y, inc, write u, inc
+    # = 5; stage 4: read u, y, inc, comp, write y, comp = 6), i.e. 19/4 per stage launch
     csz = 8 if args.dtype == "f32" else 16
-    bytes_per_launch = 4 * csz * pts
+    bytes_per_launch = 19 * csz * pts / 4
     launch_s = stage_ms / 1e3 / (4 * args.steps)
     achieved = bytes_per_launch / launch_s / 1e9
     peaks = {}
@@ -251,7 +312,7 @@ def main():
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "bq::k_stage", "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "traffic": None, "kernel": "bq::k_stage_m1", "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "bytes_per_launch": bytes_per_launch, "avg_launch_us": launch_s * 1e6}
 
     # ---- end to end through the C ABI: state from pinned host memory, observables back ---
@@ -277,6 +338,10 @@ def main():
     e2e = {"value": world * upd_per_step * args.steps / (e2e_ms / 1e3), "unit": METRIC,
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 16 * len(specs)}
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_leg(world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(specs)
@@ -292,7 +357,7 @@ def main():
                            "instances_per_gpu": args.instances, "grid_points_per_gpu": pts,
                            "state_bytes_per_array": nbytes, "l2": "inputs larger than L2 (4 arrays x "
                            f"{nbytes / 1e6:.0f} MB vs 129 MB)", "parallelism": f"replicas x{world}"},
-                "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches}
+                "roofline": roof, "e2e": e2e, "batched": batched, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -138,12 +138,24 @@ int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* opts, void*
  * replayed from a CUDA graph; asynchronous on stream. */
 int bq_step(bq_state* s, double dt, int64_t n_steps, void* stream);
 
+/* Batched persistent solve (one launch for all steps of all systems of the batch; the
+ * paper's independent initial conditions, main text after Eq. 13, processed as a work
+ * queue): every CTA takes systems from an atomic queue, largest first, keeps the RK4 stage
+ * buffers in shared memory and the state in registers for all n_steps steps.  Same
+ * arithmetic as bq_step (classical RK4, compensated state update).  Applies to single-mode
+ * states whose systems hold at most 1792 points (M <= 41 with the separable part) and at
+ * most two stencil terms per side; other states are stepped with bq_step.  Asynchronous. */
+int bq_solve(bq_state* s, double dt, int64_t n_steps, void* stream);
+
+/* *eligible = 1 if bq_solve runs the persistent kernel for this state, 0 if it falls back. */
+int bq_solve_eligible(const bq_state* s, int* eligible);
+
 /* bq_step without any memory allocation, for callers that cannot allocate device memory
  * (code running inside another framework's CUDA-graph capture, where cudaMalloc is
  * illegal, or embedded callers with a fixed memory budget decided at start-up).  The
  * paper has no counterpart: it is an alternative scratch placement of bq_step.
  *
- * The two RK4 stage buffers and the accumulator are taken from a fixed device array
+ * The two RK4 stage buffers and the stage-sum buffer are taken from a fixed device array
  * compiled into this library (3 buffers of 4 MiB each, i.e. states of up to 262 144
  * complex FP64 or 524 288 complex FP32 elements; larger states get BQ_EUNSUPPORTED).
  * Every GPU that loads the library holds that array until the process exits.  The state's
@@ -186,8 +198,9 @@ int bq_read_system(bq_state* s, int sys, double* gx, double* gy, double* r, void
 
 /* Raw state snapshot (checkpoint / resume, host-resident inputs): the G_x, G_y, R arrays
  * of every system in storage layout, *nbytes = total_elems * complex element size.
- * bq_store_state copies device -> host, bq_load_state host -> device (the integration
- * time tau is part of neither; bq_set_time sets it).  Host buffers may be pageable or
+ * bq_store_state copies device -> host, bq_load_state host -> device and clears the
+ * state's rounding compensation (the integration time tau is part of neither;
+ * bq_set_time sets it).  Host buffers may be pageable or
  * pinned; both calls are asynchronous on stream for pinned memory. */
 int bq_state_bytes(const bq_state* s, size_t* nbytes);
 int bq_store_state(bq_state* s, void* host, void* stream);

@@ -72,6 +72,8 @@ def lib() -> C.CDLL:
         "bq_map": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(bq_map_opts), vp, C.c_size_t, vp, C.POINTER(vp)]),
         "bq_step": (C.c_int, [vp, C.c_double, i64, vp]),
         "bq_step_fixed_scratch": (C.c_int, [vp, C.c_double, i64, vp]),
+        "bq_solve": (C.c_int, [vp, C.c_double, i64, vp]),
+        "bq_solve_eligible": (C.c_int, [vp, ip]),
         "bq_time": (C.c_int, [vp, dp]),
         "bq_evaluate": (C.c_int, [vp, dp, vp]),
         "bq_fock_block": (C.c_int, [vp, C.c_int, dp, vp]),
@@ -101,7 +103,7 @@ def exported_symbols() -> List[str]:
     return [n for n in ("bq_problem_create", "bq_problem_destroy", "bq_problem_add_channel",
                         "bq_problem_add_h_term", "bq_problem_set_params", "bq_problem_add_jump",
                         "bq_problem_set_measured", "bq_problem_set_rho0", "bq_required_bytes", "bq_map",
-                        "bq_step", "bq_step_fixed_scratch", "bq_time", "bq_evaluate", "bq_fock_block", "bq_state_info",
+                        "bq_step", "bq_step_fixed_scratch", "bq_solve", "bq_solve_eligible", "bq_time", "bq_evaluate", "bq_fock_block", "bq_state_info",
                         "bq_system_info", "bq_read_system", "bq_state_bytes", "bq_store_state",
                         "bq_load_state", "bq_set_time", "bq_state_destroy", "bq_status_string",
                         "bq_last_error", "bq_launch_count")]
@@ -229,6 +231,15 @@ class State:
 
     def step(self, dt: float, n_steps: int, stream=None):
         check(lib().bq_step(self.ptr, float(dt), int(n_steps), _stream_ptr(stream)))
+
+    def solve(self, dt: float, n_steps: int, stream=None):
+        """Batched persistent solve: all n_steps of every system in one kernel launch."""
+        check(lib().bq_solve(self.ptr, float(dt), int(n_steps), _stream_ptr(stream)))
+
+    def solve_eligible(self) -> bool:
+        e = C.c_int()
+        check(lib().bq_solve_eligible(self.ptr, C.byref(e)))
+        return bool(e.value)
 
     def step_fixed_scratch(self, dt: float, n_steps: int, stream=None):
         """bq_step with the RK4 scratch in the library's fixed device array (no allocation)."""

@@ -560,12 +560,14 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
 // State.
 // ---------------------------------------------------------------------------------------
 struct Layout {
-  size_t off_sys, off_terms, off_chans, off_chpar, off_work, off_groups, off_entries, off_out, off_wtab, off_diag,
-      off_ctrl, off_init, off_y, off_ua, off_ub, off_acc, total;
+  size_t off_sys, off_terms, off_chans, off_chpar, off_work, off_m1, off_order, off_groups, off_entries, off_out, off_wtab, off_diag,
+      off_ctrl, off_init, off_y, off_comp, off_ua, off_ub, off_acc, total;
 };
 
 struct bq_state {
-  int B = 0, nm = 0, dtype = 0, method = 0, basis = 0, n_sys = 0, n_work = 0, smem_bytes = 0;
+  int B = 0, nm = 0, dtype = 0, method = 0, basis = 0, n_sys = 0, n_work = 0, smem_bytes = 0, use_m1 = 0, m1_variant = 0;
+  int trace_small = 0, block_small = 0;
+  int solve_ok = 0, solve_smem = 0, last_solve_grid = 0;  // thread-per-group evaluation (few pairs per group)
   int n_trace_groups = 0, n_block_groups = 0, block_dim = 0;
   int64_t total_elems = 0;
   double dt_max = 0.0, horizon = 0.0, tau = 0.0;
@@ -597,6 +599,12 @@ struct Plan {
   std::vector<cplx> diag;
   std::vector<InitEntry> init;
   int n_trace_groups = 0, n_block_groups = 0, block_dim = 0, smem_bytes = 0;
+  int use_m1 = 0;  // single-mode fast path: one CTA per system, whole system in shared memory
+  int m1_variant = 0;
+  std::vector<bq::M1Sys> m1;
+  std::vector<int> order;  // batched solve queue (largest system first); empty: not eligible
+  int solve_smem = 0;
+  std::vector<int> wbase;  // per problem: offset of its weight tables in the pool
   int64_t total_elems = 0;
   double rho = 0.0, dt_max = 0.0;
   Layout L{};
@@ -622,6 +630,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
     P.rho = std::max(P.rho, C.rho);
     const int term_off = (int)P.terms.size();
     const int wbase = (int)P.wtab.size();
+    P.wbase.push_back(wbase);
     for (auto td : C.terms) {
       for (int i = 0; i < td.n_act; ++i) td.wtab[i] += wbase;
       if (td.ch >= 0) td.ch += (int)P.chans.size();
@@ -694,10 +703,80 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
   }
   P.total_elems = std::max<int64_t>(elem, 16);
 
+  // ---- single-mode fast path: per-system term programs ---------------------------------
+  if (nm == 1) {
+    size_t m1_max = 0;
+    int max_side = 0;
+    bool ok = true;
+    std::vector<bq::M1Sys> progs;
+    for (int b = 0; b < B && ok; ++b) {
+      const Compiled& C = P.comp[b];
+      bq::M1Sys m;
+      std::memset(&m, 0, sizeof(m));
+      const int M = C.M[0];
+      m.M = M; m.has_sep = C.has_sep; m.has_r = C.has_r;
+      for (int t = 0; t < (int)C.terms.size() && ok; ++t) {
+        const TermDesc& td = C.terms[t];
+        const int woff = P.wbase[b];
+        if (td.side == bq::SIDE_X) {
+          if (m.nX == BQ_M1_MAXT) { ok = false; break; }
+          m.sX[m.nX] = td.deltaGx; m.wX[m.nX] = td.n_act ? td.wtab[0] + woff : -1; m.tX[m.nX++] = t;
+        } else if (td.side == bq::SIDE_Y) {
+          if (m.nY == BQ_M1_MAXT) { ok = false; break; }
+          m.sY[m.nY] = td.deltaGy; m.wY[m.nY] = td.n_act ? td.wtab[0] + woff : -1; m.tY[m.nY++] = t;
+        } else {
+          if (m.nS == BQ_M1_MAXT) { ok = false; break; }
+          m.sSx[m.nS] = td.deltaGx; m.sSy[m.nS] = td.deltaGy; m.wSx[m.nS] = -1; m.wSy[m.nS] = -1;
+          for (int a = 0; a < td.n_act; ++a) {
+            if (td.dim[a] == 0) m.wSx[m.nS] = td.wtab[a] + woff; else m.wSy[m.nS] = td.wtab[a] + woff;
+          }
+          m.tS[m.nS++] = t;
+        }
+      }
+      max_side = std::max(max_side, std::max(m.nX, std::max(m.nY, m.nS)));
+      const size_t bytes = (size_t)((C.has_r ? M * M : 0) + 4 * M) * cs + (size_t)(m.nX + m.nY + 2 * m.nS) * M * rs;
+      if (bytes > 160 * 1024) ok = false;
+      m1_max = std::max(m1_max, bytes);
+      progs.push_back(m);
+    }
+    if (ok) {
+      P.use_m1 = 1;
+      P.m1_variant = max_side <= 2 ? 0 : 1;
+      for (int i = 0; i < (int)P.sys.size(); ++i) {
+        const SysDesc& sd = P.sys[i];
+        bq::M1Sys m = progs[sd.prob];
+        m.term_off = sd.term_off; m.diag_off = sd.diag_off;
+        m.off_gx = sd.off_gx; m.off_gy = sd.off_gy; m.off_r = sd.off_r;
+        m.c_re = sd.c_re; m.c_im = sd.c_im;
+        P.m1.push_back(m);
+        WorkItem w{i, 0, sd.has_r ? sd.n_r : 0, sd.has_sep, 0, sd.has_r ? sd.n_r : 0, 0, 0};
+        P.work.push_back(w);
+      }
+      P.smem_bytes = (int)m1_max;
+      // batched persistent solve: systems up to 1792 points, at most 2 terms per side
+      bool solve_ok = P.m1_variant == 0;
+      size_t solve_max = 0;
+      std::vector<std::pair<int, int>> sz;
+      for (int i = 0; i < (int)P.m1.size() && solve_ok; ++i) {
+        const bq::M1Sys& m = P.m1[i];
+        const int ntot = (m.has_r ? m.M * m.M : 0) + (m.has_sep ? 2 * m.M : 0);
+        if (ntot > 1792) solve_ok = false;
+        const size_t bytes = (size_t)(2 * ntot + 2 * m.M) * cs + (size_t)(m.nX + m.nY + 2 * m.nS) * m.M * rs;
+        solve_max = std::max(solve_max, bytes);
+        sz.push_back({-ntot, i});
+      }
+      if (solve_ok && solve_max <= 160 * 1024) {
+        std::stable_sort(sz.begin(), sz.end());
+        for (auto& e : sz) P.order.push_back(e.second);
+        P.solve_smem = (int)solve_max;
+      }
+    }
+  }
+
   // ---- work items (tiles of R; the first tile of a system also updates G_x, G_y) ------
   const int budget = (int)(96 * 1024 / cs);
   int smem_max = 0;
-  for (int i = 0; i < (int)P.sys.size(); ++i) {
+  for (int i = 0; i < (int)P.sys.size() && !P.use_m1; ++i) {
     const SysDesc& sd = P.sys[i];
     const int sep = sd.has_sep ? 2 * sd.n_g : 0;
     if (!sd.has_r) {
@@ -724,7 +803,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
       P.work.push_back(w);
     }
   }
-  P.smem_bytes = (int)(smem_max * cs);
+  if (!P.use_m1) P.smem_bytes = (int)(smem_max * cs);
   P.dt_max = 2.0 * std::sqrt(2.0) / std::max(P.rho, 1e-300);
   if (o->dt > 0.0 && o->dt > P.dt_max)
     return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 stability bound %g (spectral bound %g)", o->dt, P.dt_max, P.rho);
@@ -738,6 +817,8 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
   L.off_chans = seg(P.chans.size() * sizeof(ChanDesc));
   L.off_chpar = seg(P.chpar.size() * sizeof(double));
   L.off_work = seg(P.work.size() * sizeof(WorkItem));
+  L.off_m1 = seg(P.m1.size() * sizeof(bq::M1Sys));
+  L.off_order = seg(P.order.size() * sizeof(int));
   L.off_groups = seg(P.groups.size() * sizeof(EvalGroup));
   L.off_entries = seg(P.entries.size() * sizeof(EvalEntry));
   L.off_out = seg(P.groups.size() * 2 * sizeof(double));
@@ -747,6 +828,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
   L.off_init = seg(P.init.size() * sizeof(InitEntry));
   const size_t sbytes = (size_t)P.total_elems * cs;
   L.off_y = seg(sbytes);
+  L.off_comp = seg(sbytes);
   L.off_ua = seg(sbytes);
   L.off_ub = seg(sbytes);
   L.off_acc = seg(sbytes);
@@ -788,6 +870,8 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   CUDA_TRY(up(L.off_chans, P.chans.data(), P.chans.size() * sizeof(ChanDesc)));
   CUDA_TRY(up(L.off_chpar, P.chpar.data(), P.chpar.size() * sizeof(double)));
   CUDA_TRY(up(L.off_work, P.work.data(), P.work.size() * sizeof(WorkItem)));
+  CUDA_TRY(up(L.off_m1, P.m1.data(), P.m1.size() * sizeof(bq::M1Sys)));
+  CUDA_TRY(up(L.off_order, P.order.data(), P.order.size() * sizeof(int)));
   CUDA_TRY(up(L.off_groups, P.groups.data(), P.groups.size() * sizeof(EvalGroup)));
   CUDA_TRY(up(L.off_entries, P.entries.data(), P.entries.size() * sizeof(EvalEntry)));
   if (o->dtype == BQ_F64) {
@@ -806,6 +890,7 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   CUDA_TRY(up(L.off_init, P.init.data(), P.init.size() * sizeof(InitEntry)));
   const size_t cs = o->dtype == BQ_F64 ? 16 : 8;
   CUDA_TRY(cudaMemsetAsync(base + L.off_y, 0, (size_t)P.total_elems * cs, s));
+  CUDA_TRY(cudaMemsetAsync(base + L.off_comp, 0, (size_t)P.total_elems * cs, s));
   CUDA_TRY(bq::launch_scatter((const InitEntry*)(base + L.off_init), (int)P.init.size(), base + L.off_y, o->dtype, s));
   g_launches++;
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -813,6 +898,19 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   auto* st = new bq_state();
   st->B = B; st->nm = probs[0]->nm; st->dtype = o->dtype; st->method = o->method; st->basis = P.comp[0].basis;
   st->n_sys = (int)P.sys.size(); st->n_work = (int)P.work.size(); st->smem_bytes = P.smem_bytes;
+  st->use_m1 = P.use_m1;
+  {
+    int mt = 0, mb = 0;
+    for (int g = 0; g < (int)P.groups.size(); ++g) {
+      const int pairs = P.groups[g].n_sys * P.groups[g].n_e;
+      if (g < P.n_trace_groups) mt = std::max(mt, pairs); else mb = std::max(mb, pairs);
+    }
+    st->trace_small = mt <= 8;
+    st->block_small = mb <= 8;
+  }
+  st->m1_variant = P.m1_variant;
+  st->solve_ok = P.order.empty() ? 0 : 1;
+  st->solve_smem = P.solve_smem;
   st->n_trace_groups = P.n_trace_groups; st->n_block_groups = P.n_block_groups; st->block_dim = P.block_dim;
   st->total_elems = P.total_elems; st->dt_max = dt_max; st->horizon = o->horizon; st->reverse = o->reverse_time;
   st->pool = base; st->L = L; st->sys = P.sys;
@@ -850,6 +948,7 @@ static bq::StageArgs stage_args(bq_state* s, int stage, double dt) {
   a.u_out = stage == 1 ? ua : (stage == 2 ? ub : (stage == 3 ? ua : nullptr));
   a.y = y;
   a.acc = b + L.off_acc;
+  a.comp = b + L.off_comp;
   a.tau_base = (const double*)(b + L.off_ctrl);
   a.counter = (long long*)(b + L.off_ctrl + 8);
   a.ticket = (unsigned int*)(b + L.off_ctrl + 16);
@@ -860,10 +959,17 @@ static bq::StageArgs stage_args(bq_state* s, int stage, double dt) {
   return a;
 }
 
+static cudaError_t launch_any_stage(bq_state* s, const bq::StageArgs& a, cudaStream_t st) {
+  if (s->use_m1)
+    return bq::launch_stage_m1(a, (const bq::M1Sys*)(s->pool + s->L.off_m1), s->m1_variant, s->dtype, s->n_work,
+                               s->smem_bytes, st);
+  return bq::launch_stage(a, s->dtype, s->nm, s->n_work, s->smem_bytes, st);
+}
+
 static cudaError_t enqueue_steps(bq_state* s, double dt, int64_t n, cudaStream_t st) {
   for (int64_t i = 0; i < n; ++i)
     for (int stage = 1; stage <= 4; ++stage) {
-      cudaError_t e = bq::launch_stage(stage_args(s, stage, dt), s->dtype, s->nm, s->n_work, s->smem_bytes, st);
+      cudaError_t e = launch_any_stage(s, stage_args(s, stage, dt), st);
       if (e != cudaSuccess) return e;
     }
   return cudaSuccess;
@@ -944,10 +1050,51 @@ extern "C" int bq_step_fixed_scratch(bq_state* s, double dt, int64_t n_steps, vo
       a.u_in = stage == 1 ? (const void*)y : (stage == 3 ? (const void*)ub : (const void*)ua);
       a.u_out = stage == 1 ? (void*)ua : (stage == 2 ? (void*)ub : (stage == 3 ? (void*)ua : nullptr));
       a.acc = acc;
-      CUDA_TRY(bq::launch_stage(a, s->dtype, s->nm, s->n_work, s->smem_bytes, st));
+      CUDA_TRY(launch_any_stage(s, a, st));
       g_launches++;
     }
   s->tau += (double)n_steps * dt;
+  return BQ_OK;
+}
+
+extern "C" int bq_solve(bq_state* s, double dt, int64_t n_steps, void* stream) {
+  if (!s) return fail(BQ_EINVAL, "state is NULL");
+  if (!s->solve_ok) return bq_step(s, dt, n_steps, stream);
+  if (n_steps < 0) return fail(BQ_EINVAL, "n_steps < 0");
+  if (!(dt > 0.0)) return fail(BQ_EINVAL, "dt must be > 0");
+  if (dt > s->dt_max * (1.0 + 1e-12))
+    return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 stability bound %g", dt, s->dt_max);
+  if (n_steps == 0) return BQ_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* b = s->pool;
+  const Layout& L = s->L;
+  CUDA_TRY(cudaMemsetAsync(b + L.off_ctrl + 24, 0, 8, st));
+  bq::SolveArgs a;
+  a.m1 = (const bq::M1Sys*)(b + L.off_m1);
+  a.order = (const int*)(b + L.off_order);
+  a.terms = (const TermDesc*)(b + L.off_terms);
+  a.chans = (const ChanDesc*)(b + L.off_chans);
+  a.chpar = (const double*)(b + L.off_chpar);
+  a.wtab = b + L.off_wtab;
+  a.diag = b + L.off_diag;
+  a.y = b + L.off_y;
+  a.comp = b + L.off_comp;
+  a.queue = (unsigned int*)(b + L.off_ctrl + 24);
+  a.n_sys = s->n_sys;
+  a.reverse = s->reverse;
+  a.n_steps = n_steps;
+  a.dt = dt;
+  a.tau0 = s->tau;
+  a.horizon = s->horizon;
+  CUDA_TRY(bq::launch_solve_m1(a, s->dtype, 0, s->solve_smem, st, &s->last_solve_grid));
+  g_launches++;
+  s->tau += (double)n_steps * dt;
+  return BQ_OK;
+}
+
+extern "C" int bq_solve_eligible(const bq_state* s, int* eligible) {
+  if (!s || !eligible) return fail(BQ_EINVAL, "NULL argument");
+  *eligible = s->solve_ok;
   return BQ_OK;
 }
 
@@ -960,12 +1107,12 @@ extern "C" int bq_time(const bq_state* s, double* tau) {
 // ---------------------------------------------------------------------------------------
 // Evaluation.
 // ---------------------------------------------------------------------------------------
-static int run_eval(bq_state* s, int g0, int n, double* out_host, cudaStream_t st) {
+static int run_eval(bq_state* s, int g0, int n, int small, double* out_host, cudaStream_t st) {
   char* b = s->pool;
   const Layout& L = s->L;
   CUDA_TRY(bq::launch_eval((const SysDesc*)(b + L.off_sys), (const EvalGroup*)(b + L.off_groups) + g0,
                            (const EvalEntry*)(b + L.off_entries), b + L.off_y, (double2*)(b + L.off_out) + g0, n,
-                           s->dtype, st));
+                           s->dtype, small, st));
   g_launches++;
   CUDA_TRY(cudaMemcpyAsync(out_host, b + L.off_out + (size_t)g0 * 16, (size_t)n * 16, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
@@ -976,14 +1123,14 @@ static int run_eval(bq_state* s, int g0, int n, double* out_host, cudaStream_t s
 
 extern "C" int bq_evaluate(bq_state* s, double* out_host, void* stream) {
   if (!s || !out_host) return fail(BQ_EINVAL, "NULL argument");
-  return run_eval(s, 0, s->n_trace_groups, out_host, (cudaStream_t)stream);
+  return run_eval(s, 0, s->n_trace_groups, s->trace_small, out_host, (cudaStream_t)stream);
 }
 
 extern "C" int bq_fock_block(bq_state* s, int lo, double* out_host, void* stream) {
   if (!s || !out_host) return fail(BQ_EINVAL, "NULL argument");
   if (s->block_dim <= 0) return fail(BQ_EUNSUPPORTED, "problems of the batch have different block shapes");
   if (lo != 3) return fail(BQ_EUNSUPPORTED, "only lo = 3 (the paper's three lowest levels) is precompiled");
-  return run_eval(s, s->n_trace_groups, s->n_block_groups, out_host, (cudaStream_t)stream);
+  return run_eval(s, s->n_trace_groups, s->n_block_groups, s->block_small, out_host, (cudaStream_t)stream);
 }
 
 extern "C" int bq_state_info(const bq_state* s, int* n_systems, int64_t* total_elems) {
@@ -1062,6 +1209,7 @@ extern "C" int bq_load_state(bq_state* s, const void* host, void* stream) {
   if (!s || !host) return fail(BQ_EINVAL, "NULL argument");
   const size_t n = (size_t)s->total_elems * (s->dtype == BQ_F64 ? 16 : 8);
   CUDA_TRY(cudaMemcpyAsync(s->pool + s->L.off_y, host, n, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  CUDA_TRY(cudaMemsetAsync(s->pool + s->L.off_comp, 0, n, (cudaStream_t)stream));
   return BQ_OK;
 }
 

@@ -89,6 +89,21 @@ struct EvalEntry {
   double f_re, f_im;    // factor
 };
 
+// Single-mode fast path: one record per system with the term program precompiled on the
+// host (term counts per side, source shifts, weight-table offsets, term indices).
+#define BQ_M1_MAXT 4
+struct M1Sys {
+  int M, nX, nY, nS;
+  int has_sep, has_r, term_off, diag_off;
+  int sX[BQ_M1_MAXT], sY[BQ_M1_MAXT], sSx[BQ_M1_MAXT], sSy[BQ_M1_MAXT];
+  int wX[BQ_M1_MAXT], wY[BQ_M1_MAXT], wSx[BQ_M1_MAXT], wSy[BQ_M1_MAXT];  // -1: weight 1
+  int tX[BQ_M1_MAXT], tY[BQ_M1_MAXT], tS[BQ_M1_MAXT];
+  int pad[4];
+  int64_t off_gx, off_gy, off_r;
+  int64_t pad64;
+  double c_re, c_im;
+};
+
 struct StageArgs {
   const SysDesc* sys;
   const TermDesc* terms;
@@ -100,7 +115,8 @@ struct StageArgs {
   const void* u_in;     // stage input (y for stage 1)
   void* u_out;          // next stage input (stages 1-3)
   void* y;              // state (read stages 2-3, written stage 4)
-  void* acc;            // RK4 accumulator
+  void* acc;            // RK4 stage sum k1 + 2 k2 + 2 k3 (scratch)
+  void* comp;           // compensation of the state update (part of the state, starts at 0)
   const double* tau_base;      // device: tau at counter = 0
   long long* counter;          // device: completed steps since tau_base
   unsigned int* ticket;        // device: stage-4 completion ticket
@@ -108,6 +124,24 @@ struct StageArgs {
   double horizon;
   int reverse;
   int stage;            // 1..4
+};
+
+// Arguments of the batched persistent solve (k_solve_m1).
+struct SolveArgs {
+  const M1Sys* m1;
+  const int* order;        // systems, largest first
+  const TermDesc* terms;
+  const ChanDesc* chans;
+  const double* chpar;
+  const void* wtab;
+  const void* diag;
+  void* y;
+  void* comp;
+  unsigned int* queue;     // device: next queue position (zeroed before the launch)
+  int n_sys;
+  int reverse;
+  long long n_steps;
+  double dt, tau0, horizon;
 };
 
 }  // namespace bq

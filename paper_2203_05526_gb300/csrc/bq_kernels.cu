@@ -13,6 +13,7 @@
 // and accumulator are streamed with coalesced accesses.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "bq_internal.h"
@@ -161,16 +162,32 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
     for (int d = 0; d < ND; ++d) { doff[d] = o; o += Md[d]; }
   }
 
+  // Classical RK4 with the stage sum kept as an increment (inc = k1 + 2 k2 + 2 k3) and a
+  // compensated (Kahan) update of the state at stage 4, y += dt/6 (inc + k4): in FP32 the
+  // per-step increment is a few ulps of y, and adding partial increments to y four times
+  // per step (or even once without compensation) biases the rounding in one direction.
+  C* comp = reinterpret_cast<C*>(A.comp);
   auto combine = [&](int64_t gi, C uc, C k) {
     if (stage == 1) {
       uout[gi] = caxpy(dt * (T)0.5, k, uc);
-      acc[gi] = caxpy(dt * (T)(1.0 / 6.0), k, uc);
+      acc[gi] = k;
     } else if (stage == 4) {
-      y[gi] = caxpy(dt * (T)(1.0 / 6.0), k, acc[gi]);
+      const C yv = y[gi];
+      const C s = cadd(acc[gi], k);
+      const C cv = comp[gi];
+      C d, t, c2;
+      d.x = dt * (T)(1.0 / 6.0) * s.x - cv.x;
+      d.y = dt * (T)(1.0 / 6.0) * s.y - cv.y;
+      t.x = yv.x + d.x;
+      t.y = yv.y + d.y;
+      c2.x = (t.x - yv.x) - d.x;
+      c2.y = (t.y - yv.y) - d.y;
+      y[gi] = t;
+      comp[gi] = c2;
     } else {
       const C yv = y[gi];
       uout[gi] = caxpy(stage == 2 ? dt * (T)0.5 : dt, k, yv);
-      acc[gi] = caxpy(dt * (T)(1.0 / 3.0), k, acc[gi]);
+      acc[gi] = caxpy((T)2, k, acc[gi]);
     }
   };
 
@@ -264,6 +281,413 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Fused RK4 stage, single-mode fast path (the batched workloads of the paper's oscillator
+// family).  One CTA holds one whole system: R (M x M), G_x, G_y, the diagonal tables and the
+// weight tables of its few stencil terms, all in shared memory.  The term program (counts,
+// shifts, table offsets) is precompiled on the host into one M1Sys record per system, read
+// with one coalesced load, so a CTA has exactly two barriers.  Per point:
+//   k(k,l) = (D_x[k] + D_y[l]) u[k,l] + sum_X c W[k] u[k+s,l] + sum_Y c W[l] u[k,l+s]
+//          + sum_S c Wx[k] Wy[l] (u[k+sx,l+sy] + G_x[k+sx] G_y[l+sy]).
+// Out-of-grid sources have zero weight; their (clamped) address stays inside the tile.
+// ---------------------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T dev_exp(T x);
+template <> __device__ __forceinline__ double dev_exp<double>(double x) { return exp(x); }
+template <> __device__ __forceinline__ float dev_exp<float>(float x) { return expf(x); }
+
+// Envelope value in the state's precision (FP32 envelopes are accurate to ~1e-7 relative,
+// far inside the FP32 path's tolerance; FP64 states evaluate in FP64).
+template <typename T>
+__device__ double2 chan_value_t(const ChanDesc& c, const double* p, double t) {
+  p += c.par_off;
+  if (c.kind == 1) {
+    const T d = (T)(t - p[2]);
+    const T e = dev_exp<T>(-(d * d) / ((T)2 * (T)p[3] * (T)p[3]));
+    return make_double2(p[0] * (double)e, p[1] * (double)e);
+  }
+  return chan_value(c, p - c.par_off, t);
+}
+
+template <typename T, int MX, int MY, int MS>
+__global__ void __launch_bounds__(BQ_BLOCK) k_stage_m1(const StageArgs A, const M1Sys* __restrict__ m1) {
+  using C = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ M1Sys s;
+  __shared__ C coef[3 * BQ_M1_MAXT];
+  __shared__ double s_tau;
+  const int tid = threadIdx.x;
+  {
+    const int* src = reinterpret_cast<const int*>(m1 + blockIdx.x);
+    int* dst = reinterpret_cast<int*>(&s);
+    for (int i = tid; i < (int)(sizeof(M1Sys) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    if (tid == 0) s_tau = A.tau_base[0] + (double)(*(volatile long long*)A.counter) * A.dt;
+  }
+  __syncthreads();
+  const int M = s.M, nX = s.nX, nY = s.nY, nS = s.nS;
+  const int has_r = s.has_r, has_sep = s.has_sep;
+  const int nr = has_r ? M * M : 0;
+  // shared layout: u[M*M] | gx[M] | gy[M] | dx[M] | dy[M] | wX[nX*M] wY[nY*M] wSx[nS*M] wSy[nS*M] (real)
+  C* u = reinterpret_cast<C*>(smem_raw);
+  C* gx = u + nr;
+  C* gy = gx + M;
+  C* dx = gy + M;
+  C* dy = dx + M;
+  T* wt = reinterpret_cast<T*>(dy + M);
+  T* wX = wt;
+  T* wY = wX + nX * M;
+  T* wSx = wY + nY * M;
+  T* wSy = wSx + nS * M;
+  // term coefficients at this stage's time (one thread per term)
+  {
+    const int nt = nX + nY + nS;
+    if (tid < nt) {
+      const int t = tid < nX ? s.tX[tid] : (tid < nX + nY ? s.tY[tid - nX] : s.tS[tid - nX - nY]);
+      const TermDesc& td = A.terms[s.term_off + t];
+      double2 c = make_double2(td.c_re, td.c_im);
+      if (td.ch >= 0) {
+        const ChanDesc cd = A.chans[td.ch];
+        const double tau = (cd.kind == 2) ? s_tau + 0.5 * A.dt : s_tau + stage_c(A.stage) * A.dt;
+        double2 e = chan_value_t<T>(cd, A.chpar, A.reverse ? A.horizon - tau : tau);
+        if (td.conj) e.y = -e.y;
+        c = make_double2(c.x * e.x - c.y * e.y, c.x * e.y + c.y * e.x);
+      }
+      coef[tid] = cmk<C>(c.x, c.y);
+    }
+  }
+  const C* uin = reinterpret_cast<const C*>(A.u_in);
+  if (has_r) {
+    const C* src = uin + s.off_r;
+    for (int i = tid; i < nr; i += blockDim.x) u[i] = src[i];
+  }
+  if (has_sep)
+    for (int i = tid; i < M; i += blockDim.x) {
+      gx[i] = uin[s.off_gx + i];
+      gy[i] = uin[s.off_gy + i];
+    }
+  {
+    const C* Dg = reinterpret_cast<const C*>(A.diag) + s.diag_off;
+    const T* W = reinterpret_cast<const T*>(A.wtab);
+    for (int i = tid; i < M; i += blockDim.x) {
+      dx[i] = Dg[i];
+      dy[i] = Dg[M + i];
+#pragma unroll
+      for (int j = 0; j < MX; ++j) if (j < nX) wX[j * M + i] = s.wX[j] >= 0 ? W[s.wX[j] + i] : (T)1;
+#pragma unroll
+      for (int j = 0; j < MY; ++j) if (j < nY) wY[j * M + i] = s.wY[j] >= 0 ? W[s.wY[j] + i] : (T)1;
+#pragma unroll
+      for (int j = 0; j < MS; ++j)
+        if (j < nS) {
+          wSx[j * M + i] = s.wSx[j] >= 0 ? W[s.wSx[j] + i] : (T)1;
+          wSy[j * M + i] = s.wSy[j] >= 0 ? W[s.wSy[j] + i] : (T)1;
+        }
+    }
+  }
+  __syncthreads();
+
+  C cX[MX], cY[MY], cS[MS];
+  int shX[MX], shY[MY], shSx[MS], shSy[MS];
+#pragma unroll
+  for (int j = 0; j < MX; ++j) { cX[j] = coef[min(j, 3 * BQ_M1_MAXT - 1)]; shX[j] = s.sX[j]; }
+#pragma unroll
+  for (int j = 0; j < MY; ++j) { cY[j] = coef[min(nX + j, 3 * BQ_M1_MAXT - 1)]; shY[j] = s.sY[j]; }
+#pragma unroll
+  for (int j = 0; j < MS; ++j) { cS[j] = coef[min(nX + nY + j, 3 * BQ_M1_MAXT - 1)]; shSx[j] = s.sSx[j]; shSy[j] = s.sSy[j]; }
+
+  C* uout = reinterpret_cast<C*>(A.u_out);
+  C* y = reinterpret_cast<C*>(A.y);
+  C* acc = reinterpret_cast<C*>(A.acc);
+  C* comp = reinterpret_cast<C*>(A.comp);
+  const T dt = (T)A.dt;
+  const int stage = A.stage;
+  auto combine = [&](int64_t gi, C uc, C kv) {
+    if (stage == 1) {
+      uout[gi] = caxpy(dt * (T)0.5, kv, uc);
+      acc[gi] = kv;
+    } else if (stage == 4) {
+      const C yv = y[gi];
+      const C sm = cadd(acc[gi], kv);
+      const C cv = comp[gi];
+      C d, t, c2;
+      d.x = dt * (T)(1.0 / 6.0) * sm.x - cv.x;
+      d.y = dt * (T)(1.0 / 6.0) * sm.y - cv.y;
+      t.x = yv.x + d.x;
+      t.y = yv.y + d.y;
+      c2.x = (t.x - yv.x) - d.x;
+      c2.y = (t.y - yv.y) - d.y;
+      y[gi] = t;
+      comp[gi] = c2;
+    } else {
+      const C yv = y[gi];
+      uout[gi] = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, yv);
+      acc[gi] = caxpy((T)2, kv, acc[gi]);
+    }
+  };
+
+  if (has_r) {
+    const float invM = 1.0f / (float)M;
+    for (int p = tid; p < nr; p += blockDim.x) {
+      const int kx = (int)(((float)p + 0.5f) * invM);
+      const int ly = p - kx * M;
+      const C uc = u[p];
+      C kv = cmul(cadd(dx[kx], dy[ly]), uc);
+#pragma unroll
+      for (int j = 0; j < MX; ++j)
+        if (j < nX) {
+          const int r = min(max(kx + shX[j], 0), M - 1);
+          kv = cfma(cX[j], cscale(u[r * M + ly], wX[j * M + kx]), kv);
+        }
+#pragma unroll
+      for (int j = 0; j < MY; ++j)
+        if (j < nY) {
+          const int c = min(max(ly + shY[j], 0), M - 1);
+          kv = cfma(cY[j], cscale(u[kx * M + c], wY[j * M + ly]), kv);
+        }
+#pragma unroll
+      for (int j = 0; j < MS; ++j)
+        if (j < nS) {
+          const int r = min(max(kx + shSx[j], 0), M - 1);
+          const int c = min(max(ly + shSy[j], 0), M - 1);
+          C v = u[r * M + c];
+          if (has_sep) v = cadd(v, cmul(gx[r], gy[c]));
+          kv = cfma(cS[j], cscale(v, wSx[j * M + kx] * wSy[j * M + ly]), kv);
+        }
+      combine(s.off_r + p, uc, kv);
+    }
+  }
+  if (has_sep) {
+    for (int i = tid; i < 2 * M; i += blockDim.x) {
+      const bool isx = i < M;
+      const int g = isx ? i : i - M;
+      const C* gs = isx ? gx : gy;
+      C dg = isx ? cadd(dx[g], cmk<C>(s.c_re, s.c_im)) : cadd(dy[g], cmk<C>(-s.c_re, -s.c_im));
+      C kv = cmul(dg, gs[g]);
+      if (isx) {
+#pragma unroll
+        for (int j = 0; j < MX; ++j)
+          if (j < nX) kv = cfma(cX[j], cscale(gs[min(max(g + shX[j], 0), M - 1)], wX[j * M + g]), kv);
+      } else {
+#pragma unroll
+        for (int j = 0; j < MY; ++j)
+          if (j < nY) kv = cfma(cY[j], cscale(gs[min(max(g + shY[j], 0), M - 1)], wY[j * M + g]), kv);
+      }
+      combine((isx ? s.off_gx : s.off_gy) + g, gs[g], kv);
+    }
+  }
+  if (stage == 4) {
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      const unsigned int t = atomicAdd(A.ticket, 1u);
+      if (t == gridDim.x - 1) {
+        *A.ticket = 0u;
+        *A.counter = *(volatile long long*)A.counter + 1;
+        __threadfence();
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched persistent solve (single mode): one launch integrates every system for n_steps.
+// Each CTA takes systems from an atomic queue (largest first), keeps the two RK4 stage
+// buffers [R | G_x | G_y] in shared memory and the state y, the stage sum and the
+// rounding compensation of the points it owns in registers, and runs all steps with one
+// barrier per stage.  Drive coefficients of the next stage are evaluated by a few threads
+// while the others compute.  There is no inter-CTA waiting of any kind.
+// ---------------------------------------------------------------------------------------
+template <typename T, int BLK, int PPT, int MX, int MY, int MS>
+__global__ void __launch_bounds__(BLK, 2) k_solve_m1(const SolveArgs A) {
+  using C = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ M1Sys s;
+  __shared__ C coef[2][3 * BQ_M1_MAXT];
+  __shared__ int s_next;
+  const int tid = threadIdx.x;
+  C* y_g = reinterpret_cast<C*>(A.y);
+  C* comp_g = reinterpret_cast<C*>(A.comp);
+
+  for (;;) {
+    if (tid == 0) s_next = (int)atomicAdd(A.queue, 1u);
+    __syncthreads();
+    const int qi = s_next;
+    if (qi >= A.n_sys) return;
+    {
+      const int* src = reinterpret_cast<const int*>(A.m1 + A.order[qi]);
+      int* dst = reinterpret_cast<int*>(&s);
+      for (int i = tid; i < (int)(sizeof(M1Sys) / sizeof(int)); i += BLK) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int M = s.M, nX = s.nX, nY = s.nY, nS = s.nS;
+    const int has_r = s.has_r, has_sep = s.has_sep;
+    const int nr = has_r ? M * M : 0;
+    const int ntot = nr + (has_sep ? 2 * M : 0);
+    // shared: B0[ntot] | B1[ntot] | dx[M] | dy[M] | weights (real)
+    C* B0 = reinterpret_cast<C*>(smem_raw);
+    C* B1 = B0 + ntot;
+    C* dx = B1 + ntot;
+    C* dy = dx + M;
+    T* wX = reinterpret_cast<T*>(dy + M);
+    T* wY = wX + nX * M;
+    T* wSx = wY + nY * M;
+    T* wSy = wSx + nS * M;
+    const int nt = nX + nY + nS;
+    auto eval_coef = [&](int buf, int64_t step, int stage) {
+      if (tid < nt) {
+        const int t = tid < nX ? s.tX[tid] : (tid < nX + nY ? s.tY[tid - nX] : s.tS[tid - nX - nY]);
+        const TermDesc& td = A.terms[s.term_off + t];
+        double2 c = make_double2(td.c_re, td.c_im);
+        if (td.ch >= 0) {
+          const ChanDesc cd = A.chans[td.ch];
+          const double ts = A.tau0 + (double)step * A.dt;
+          const double tau = (cd.kind == 2) ? ts + 0.5 * A.dt : ts + stage_c(stage) * A.dt;
+          double2 e = chan_value_t<T>(cd, A.chpar, A.reverse ? A.horizon - tau : tau);
+          if (td.conj) e.y = -e.y;
+          c = make_double2(c.x * e.x - c.y * e.y, c.x * e.y + c.y * e.x);
+        }
+        coef[buf][tid] = cmk<C>(c.x, c.y);
+      }
+    };
+    // global index of element e of [R | G_x | G_y]
+    auto gidx = [&](int e) -> int64_t {
+      return e < nr ? s.off_r + e : (e < nr + M ? s.off_gx + (e - nr) : s.off_gy + (e - nr - M));
+    };
+    C yv[PPT], av[PPT], cv[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      const int e = tid + j * BLK;
+      if (e < ntot) {
+        const int64_t g = gidx(e);
+        yv[j] = y_g[g];
+        cv[j] = comp_g[g];
+        B0[e] = yv[j];
+      }
+    }
+    {
+      const C* Dg = reinterpret_cast<const C*>(A.diag) + s.diag_off;
+      const T* W = reinterpret_cast<const T*>(A.wtab);
+      for (int i = tid; i < M; i += BLK) {
+        dx[i] = Dg[i];
+        dy[i] = Dg[M + i];
+#pragma unroll
+        for (int j = 0; j < MX; ++j) if (j < nX) wX[j * M + i] = s.wX[j] >= 0 ? W[s.wX[j] + i] : (T)1;
+#pragma unroll
+        for (int j = 0; j < MY; ++j) if (j < nY) wY[j * M + i] = s.wY[j] >= 0 ? W[s.wY[j] + i] : (T)1;
+#pragma unroll
+        for (int j = 0; j < MS; ++j)
+          if (j < nS) {
+            wSx[j * M + i] = s.wSx[j] >= 0 ? W[s.wSx[j] + i] : (T)1;
+            wSy[j * M + i] = s.wSy[j] >= 0 ? W[s.wSy[j] + i] : (T)1;
+          }
+      }
+    }
+    eval_coef(0, 0, 1);
+    int shX[MX], shY[MY], shSx[MS], shSy[MS];
+#pragma unroll
+    for (int j = 0; j < MX; ++j) shX[j] = s.sX[j];
+#pragma unroll
+    for (int j = 0; j < MY; ++j) shY[j] = s.sY[j];
+#pragma unroll
+    for (int j = 0; j < MS; ++j) { shSx[j] = s.sSx[j]; shSy[j] = s.sSy[j]; }
+    const C Cc = cmk<C>(s.c_re, s.c_im);
+    const T dt = (T)A.dt;
+    const float invM = 1.0f / (float)M;
+    __syncthreads();
+
+    int buf = 0;
+    for (int64_t step = 0; step < A.n_steps; ++step) {
+#pragma unroll 1
+      for (int stage = 1; stage <= 4; ++stage) {
+        const C* uin = (stage & 1) ? B0 : B1;  // stages 1, 3 read B0; 2, 4 read B1
+        C* uout = (stage & 1) ? B1 : B0;
+        C cX[MX], cY[MY], cS[MS];
+#pragma unroll
+        for (int j = 0; j < MX; ++j) cX[j] = coef[buf][min(j, 3 * BQ_M1_MAXT - 1)];
+#pragma unroll
+        for (int j = 0; j < MY; ++j) cY[j] = coef[buf][min(nX + j, 3 * BQ_M1_MAXT - 1)];
+#pragma unroll
+        for (int j = 0; j < MS; ++j) cS[j] = coef[buf][min(nX + nY + j, 3 * BQ_M1_MAXT - 1)];
+        const C* gxi = uin + nr;
+        const C* gyi = gxi + M;
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+          const int e = tid + j * BLK;
+          if (e >= ntot) continue;
+          const C uc = uin[e];
+          C kv;
+          if (e < nr) {
+            const int kx = (int)(((float)e + 0.5f) * invM);
+            const int ly = e - kx * M;
+            kv = cmul(cadd(dx[kx], dy[ly]), uc);
+#pragma unroll
+            for (int q = 0; q < MX; ++q)
+              if (q < nX) kv = cfma(cX[q], cscale(uin[min(max(kx + shX[q], 0), M - 1) * M + ly], wX[q * M + kx]), kv);
+#pragma unroll
+            for (int q = 0; q < MY; ++q)
+              if (q < nY) kv = cfma(cY[q], cscale(uin[kx * M + min(max(ly + shY[q], 0), M - 1)], wY[q * M + ly]), kv);
+#pragma unroll
+            for (int q = 0; q < MS; ++q)
+              if (q < nS) {
+                const int r = min(max(kx + shSx[q], 0), M - 1);
+                const int c = min(max(ly + shSy[q], 0), M - 1);
+                C v = uin[r * M + c];
+                if (has_sep) v = cadd(v, cmul(gxi[r], gyi[c]));
+                kv = cfma(cS[q], cscale(v, wSx[q * M + kx] * wSy[q * M + ly]), kv);
+              }
+          } else {
+            const bool isx = e < nr + M;
+            const int g = isx ? e - nr : e - nr - M;
+            const C* gs = isx ? gxi : gyi;
+            kv = cmul(isx ? cadd(dx[g], Cc) : cadd(dy[g], cmk<C>(-s.c_re, -s.c_im)), uc);
+            if (isx) {
+#pragma unroll
+              for (int q = 0; q < MX; ++q)
+                if (q < nX) kv = cfma(cX[q], cscale(gs[min(max(g + shX[q], 0), M - 1)], wX[q * M + g]), kv);
+            } else {
+#pragma unroll
+              for (int q = 0; q < MY; ++q)
+                if (q < nY) kv = cfma(cY[q], cscale(gs[min(max(g + shY[q], 0), M - 1)], wY[q * M + g]), kv);
+            }
+          }
+          // RK4 combine (stage sum + compensated state update, as in the stage kernels)
+          if (stage == 1) {
+            uout[e] = caxpy(dt * (T)0.5, kv, yv[j]);
+            av[j] = kv;
+          } else if (stage == 4) {
+            const C sm = cadd(av[j], kv);
+            C d, t;
+            d.x = dt * (T)(1.0 / 6.0) * sm.x - cv[j].x;
+            d.y = dt * (T)(1.0 / 6.0) * sm.y - cv[j].y;
+            t.x = yv[j].x + d.x;
+            t.y = yv[j].y + d.y;
+            cv[j].x = (t.x - yv[j].x) - d.x;
+            cv[j].y = (t.y - yv[j].y) - d.y;
+            yv[j] = t;
+            uout[e] = t;
+          } else {
+            uout[e] = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, yv[j]);
+            av[j] = caxpy((T)2, kv, av[j]);
+          }
+        }
+        // coefficients of the next stage (stage 4 -> stage 1 of the next step)
+        const int nstage = stage == 4 ? 1 : stage + 1;
+        eval_coef(buf ^ 1, stage == 4 ? step + 1 : step, nstage);
+        buf ^= 1;
+        __syncthreads();
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      const int e = tid + j * BLK;
+      if (e < ntot) {
+        const int64_t g = gidx(e);
+        y_g[g] = yv[j];
+        comp_g[g] = cv[j];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Observables: one warp per evaluation group, lanes over (initial condition, entry) pairs.
 // ---------------------------------------------------------------------------------------
 template <typename T>
@@ -307,6 +731,44 @@ __global__ void k_eval(const SysDesc* __restrict__ sys, const EvalGroup* __restr
     im += __shfl_down_sync(0xffffffffu, im, o);
   }
   if (lane == 0) out[warp] = make_double2(re, im);
+}
+
+// Observables for groups with few (initial condition, entry) pairs: one thread per group.
+template <typename T>
+__global__ void k_eval_small(const SysDesc* __restrict__ sys, const EvalGroup* __restrict__ groups,
+                             const EvalEntry* __restrict__ entries, const void* ystate, double2* out, int n_groups) {
+  using C = typename C2T<T>::type;
+  const C* y = reinterpret_cast<const C*>(ystate);
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= n_groups) return;
+  const EvalGroup g = groups[gi];
+  double re = 0.0, im = 0.0;
+  for (int s = 0; s < g.n_sys; ++s) {
+    const SysDesc& sd = sys[g.sys_off + s];
+    const double wr = sd.w_re, wim = sd.w_im;
+    const int sep = sd.has_sep, hr = sd.has_r, ng = sd.n_g;
+    const int64_t ox = sd.off_gx, oy = sd.off_gy, orr = sd.off_r;
+    for (int e = 0; e < g.n_e; ++e) {
+      const EvalEntry en = entries[g.e_off + e];
+      double vr = 0.0, vi = 0.0;
+      if (sep) {
+        const C a = y[ox + en.kx];
+        const C b = y[oy + en.ly];
+        vr += (double)a.x * (double)b.x - (double)a.y * (double)b.y;
+        vi += (double)a.x * (double)b.y + (double)a.y * (double)b.x;
+      }
+      if (hr) {
+        const C r = y[orr + (int64_t)en.kx * ng + en.ly];
+        vr += (double)r.x;
+        vi += (double)r.y;
+      }
+      const double fr = wr * en.f_re - wim * en.f_im;
+      const double fi = wr * en.f_im + wim * en.f_re;
+      re += fr * vr - fi * vi;
+      im += fr * vi + fi * vr;
+    }
+  }
+  out[gi] = make_double2(re, im);
 }
 
 // Initial state: y[off] = value for a list of (offset, value) pairs (the rest is zeroed).
@@ -362,6 +824,60 @@ static cudaError_t launch_stage_t(const StageArgs& a, int n_work, int smem_bytes
   return cudaGetLastError();
 }
 
+template <typename T, int MX, int MY, int MS>
+static cudaError_t launch_stage_m1_t(const StageArgs& a, const M1Sys* m1, int n_work, int smem_bytes, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_stage_m1<T, MX, MY, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         BQ_MAX_DYN_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_stage_m1<T, MX, MY, MS><<<n_work, BQ_BLOCK, smem_bytes, s>>>(a, m1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage_m1(const StageArgs& a, const M1Sys* m1, int variant, int dtype, int n_work, int smem_bytes,
+                            cudaStream_t s) {
+  // variant 0: at most 2 terms per side; variant 1: at most BQ_M1_MAXT
+  if (dtype == 0)
+    return variant == 0 ? launch_stage_m1_t<double, 2, 2, 2>(a, m1, n_work, smem_bytes, s)
+                        : launch_stage_m1_t<double, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>(a, m1, n_work, smem_bytes, s);
+  return variant == 0 ? launch_stage_m1_t<float, 2, 2, 2>(a, m1, n_work, smem_bytes, s)
+                      : launch_stage_m1_t<float, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>(a, m1, n_work, smem_bytes, s);
+}
+
+template <typename T, int BLK, int PPT>
+static cudaError_t launch_solve_t(const SolveArgs& a, int smem_bytes, cudaStream_t s, int* grid_out) {
+  auto kern = k_solve_m1<T, BLK, PPT, 2, 2, 2>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, BQ_MAX_DYN_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLK, smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = std::min(a.n_sys, per_sm * nsm);
+  *grid_out = grid;
+  kern<<<grid, BLK, smem_bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_m1(const SolveArgs& a, int dtype, int capacity_class, int smem_bytes, cudaStream_t s,
+                            int* grid_out) {
+  // capacity: FP32 256 threads x 7 points = 1792, FP64 448 threads x 4 points = 1792 points per system
+  if (capacity_class != 0) return cudaErrorInvalidValue;
+  return dtype == 0 ? launch_solve_t<double, 448, 4>(a, smem_bytes, s, grid_out)
+                    : launch_solve_t<float, 256, 7>(a, smem_bytes, s, grid_out);
+}
+
 cudaError_t launch_stage(const StageArgs& a, int dtype, int nm, int n_work, int smem_bytes, cudaStream_t s) {
   if (dtype == 0) {
     switch (nm) {
@@ -380,9 +896,17 @@ cudaError_t launch_stage(const StageArgs& a, int dtype, int nm, int n_work, int 
 }
 
 cudaError_t launch_eval(const SysDesc* sys, const EvalGroup* groups, const EvalEntry* entries, const void* y,
-                        double2* out, int n_groups, int dtype, cudaStream_t s) {
+                        double2* out, int n_groups, int dtype, int small, cudaStream_t s) {
   if (n_groups <= 0) return cudaSuccess;
   const int threads = 256;
+  if (small) {
+    const int blocks = (n_groups + threads - 1) / threads;
+    if (dtype == 0)
+      k_eval_small<double><<<blocks, threads, 0, s>>>(sys, groups, entries, y, out, n_groups);
+    else
+      k_eval_small<float><<<blocks, threads, 0, s>>>(sys, groups, entries, y, out, n_groups);
+    return cudaGetLastError();
+  }
   const int blocks = (n_groups * 32 + threads - 1) / threads;
   if (dtype == 0)
     k_eval<double><<<blocks, threads, 0, s>>>(sys, groups, entries, y, out, n_groups);

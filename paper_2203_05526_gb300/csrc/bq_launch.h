@@ -17,8 +17,15 @@ struct InitEntry {
 };
 
 cudaError_t launch_stage(const StageArgs& a, int dtype, int nm, int n_work, int smem_bytes, cudaStream_t s);
+// Single-mode fast path (one CTA per system, whole system in shared memory); the caller
+// checks bq_m1_eligible().
+cudaError_t launch_stage_m1(const StageArgs& a, const M1Sys* m1, int variant, int dtype, int n_work, int smem_bytes,
+                            cudaStream_t s);
+// Batched persistent solve; capacity_class 0 = systems of up to 1792 points.
+cudaError_t launch_solve_m1(const SolveArgs& a, int dtype, int capacity_class, int smem_bytes, cudaStream_t s,
+                            int* grid_out);
 cudaError_t launch_eval(const SysDesc* sys, const EvalGroup* groups, const EvalEntry* entries, const void* y,
-                        double2* out, int n_groups, int dtype, cudaStream_t s);
+                        double2* out, int n_groups, int dtype, int small, cudaStream_t s);
 // Device address of the fixed RK4 scratch on the current device (looked up once per device).
 cudaError_t fixed_scratch(void** ptr);
 cudaError_t launch_scatter(const InitEntry* ent, int n, void* y, int dtype, cudaStream_t s);

@@ -1,0 +1,111 @@
+"""Batched solving on the GPU: the persistent one-launch solve (bq_solve) and the streamed
+stage kernels over a ragged batch, against the FP64 oracle and against each other."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mapping
+from workloads import configs
+
+from parity import compare_mapped_systems, gpu_state, rel_err
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "kerr_batch_golden.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    from paper_2203_05526_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def _ragged_batch(n=24, steps=60, dt=0.002, seed=20220311):
+    ps = configs.kerr_batch(B=n, T=steps * dt, dt=dt, seed=seed, n_min=3, n_max=40)
+    return ps
+
+
+def test_solve_f64_ragged_batch_matches_oracle_per_system():
+    ps = _ragged_batch()
+    st = gpu_state(ps)
+    assert st.solve_eligible()
+    st.solve(ps[0].dt, ps[0].n_steps)
+    _sync()
+    for b, p in enumerate(ps):
+        run = mapping.rk4_mapped(p)
+        compare_mapped_systems(st, run, 1e-10, sys_offset=b, n_sys=b + 1)
+    ev = st.evaluate()
+    for b, p in enumerate(ps[:6]):
+        ref = mapping.rk4_mapped(p).fock_matrix()[0, 0]
+        assert abs(ev[b] - ref) <= 1e-10 * max(1.0, abs(ref))
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-6)])
+def test_solve_equals_streamed_stages(dtype, tol):
+    """One persistent launch and 4 stage launches per step give the same numbers."""
+    ps = _ragged_batch(n=40, steps=80)
+    a = gpu_state(ps, dtype=dtype)
+    b = gpu_state(ps, dtype=dtype)
+    a.solve(ps[0].dt, 80)
+    b.step(ps[0].dt, 80)
+    _sync()
+    ea, eb = a.evaluate(), b.evaluate()
+    assert np.max(np.abs(ea - eb)) <= tol * max(1.0, np.max(np.abs(eb)))
+    blk_a = a.fock_block(3, dim=3)
+    blk_b = b.fock_block(3, dim=3)
+    assert rel_err(blk_a, blk_b) <= tol
+
+
+def test_solve_split_calls_and_time():
+    ps = _ragged_batch(n=8, steps=50)
+    a = gpu_state(ps)
+    a.solve(ps[0].dt, 20)
+    a.solve(ps[0].dt, 30)
+    _sync()
+    assert abs(a.time() - 50 * ps[0].dt) < 1e-15
+    for b, p in enumerate(ps):
+        compare_mapped_systems(a, mapping.rk4_mapped(p), 1e-10, sys_offset=b, n_sys=b + 1)
+
+
+def test_multimode_state_falls_back_to_stepping():
+    p = configs.random_problem(77, n_modes=2, N=4, n_steps=10, dt=0.01)
+    st = gpu_state(p)
+    assert not st.solve_eligible()
+    st.solve(p.dt, 10)
+    _sync()
+    compare_mapped_systems(st, mapping.rk4_mapped(p), 1e-10)
+
+
+@pytest.mark.parametrize("path", ["solve", "step"])
+def test_kerr_batch_4096_full_horizon_f32_vs_oracle_samples(path):
+    """The 4096-instance batch (seed 20220311), complex FP32, T = 100 ns, dt = 0.002 ns
+    (50 000 steps), in the launch configuration the benchmark times; sampled instances
+    against FP64 oracle values written by tests/golden/make_kerr_batch_golden.py."""
+    gold = json.load(open(GOLDEN))["results"]
+    ps = configs.kerr_batch(B=4096)
+    st = gpu_state(ps, dtype="f32")
+    if path == "solve":
+        st.solve(ps[0].dt, ps[0].n_steps)
+    else:
+        st.step(ps[0].dt, ps[0].n_steps)
+    _sync()
+    ev = st.evaluate()
+    blk = st.fock_block(3, dim=3)
+    worst = 0.0
+    for g in gold:
+        i = g["index"]
+        ref = np.array(g["block_re"]) + 1j * np.array(g["block_im"])
+        worst = max(worst, rel_err(blk[i], ref))
+        tr = complex(*g["tr_rho0_A"])
+        assert abs(ev[i] - tr) <= 1e-5 * max(1.0, abs(tr))
+    assert worst <= 1e-5, worst
+    assert np.all(np.isfinite(ev))
