@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-instance full-solve leg")
+    ap.add_argument("--only-solve", action="store_true",
+                    help="profiling aid: only the persistent batched solve of --instances for --solve-steps steps")
+    ap.add_argument("--solve-steps", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -65,6 +68,11 @@ def workload(n_inst: int, rank: int):
     from workloads import configs
     allp = configs.kerr_batch(B=n_inst * (rank + 1), T=HORIZON, dt=DT)
     return allp[n_inst * rank:]
+
+
+def configs_batch(n: int):
+    from workloads import configs
+    return configs.kerr_batch(B=n, T=HORIZON, dt=DT)
 
 
 def points_of(specs):
@@ -253,6 +261,18 @@ def main():
     import paper_2203_05526_gb300 as bq
     from paper_2203_05526_gb300 import build
     build.build()
+    if args.only_solve:
+        specs = configs_batch(args.instances)
+        st = bq.State([bq.problem_from_spec(p) for p in specs], bq.map_opts(dtype=args.dtype, horizon=HORIZON, dt=DT))
+        st.solve(DT, 10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st.solve(DT, args.solve_steps)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        print(json.dumps({"only_solve": True, "instances": args.instances, "steps": args.solve_steps, "seconds": el,
+                          "updates_per_s": 4 * points_of(specs) * args.solve_steps / el}))
+        return
     specs = workload(args.instances, rank)
     handles = [bq.problem_from_spec(p) for p in specs]
     opts = bq.map_opts(method="mapped", dtype=args.dtype, horizon=HORIZON, dt=DT)
@@ -312,7 +332,8 @@ def main():
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "bq::k_stage_m1", "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "traffic": None, "kernel": {"pipelined": "bq::k_stage_pipe", "single_mode": "bq::k_stage_m1",
+                                               "generic": "bq::k_stage"}[state.stage_variant()], "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "bytes_per_launch": bytes_per_launch, "avg_launch_us": launch_s * 1e6}
 
     # ---- end to end through the C ABI: state from pinned host memory, observables back ---

@@ -147,8 +147,37 @@ int bq_step(bq_state* s, double dt, int64_t n_steps, void* stream);
  * most two stencil terms per side; other states are stepped with bq_step.  Asynchronous. */
 int bq_solve(bq_state* s, double dt, int64_t n_steps, void* stream);
 
+/* Which fused stage kernel bq_step launches for this state: 0 = generic (1-3 modes, tiles
+ * with halo windows), 1 = single-mode one-CTA-per-system, 2 = single-mode pipelined
+ * (persistent CTAs with 1-D bulk-copy prefetch of the next systems).  Diagnostic only. */
+int bq_stage_variant(const bq_state* s, int* variant);
+
 /* *eligible = 1 if bq_solve runs the persistent kernel for this state, 0 if it falls back. */
 int bq_solve_eligible(const bq_state* s, int* eligible);
+
+/* ---- gradients (discrete adjoint of the RK4 solve) ----------------------------------- */
+
+/* Number of gradient slots of the state: for every problem b in order, its parameters
+ * theta_0..theta_{P_b-1} (bq_problem_set_params), then (Re, Im) of every segment of every
+ * piecewise-constant channel of b, channels in order. */
+int bq_grad_size(const bq_state* s, int* n);
+
+/* Device bytes of the gradient workspace for n_steps steps checkpointed every
+ * checkpoint_every steps: ceil(n/k) checkpoints of the state and 4 k recorded stage inputs,
+ * plus four cotangent arrays. */
+int bq_grad_required_bytes(const bq_state* s, int64_t n_steps, int checkpoint_every, size_t* out);
+
+/* Loss l_b = Re Tr(rho0_b A_b(tau0 + n_steps dt)) of every problem (loss_out[B]) and the
+ * gradient of sum_b l_b (grad_out[bq_grad_size]) with respect to every H parameter and every
+ * piecewise-constant segment value, by the exact discrete adjoint of the RK4 solve: a forward
+ * pass storing the state every checkpoint_every steps, then, segment by segment in reverse, a
+ * recomputation recording the RK4 stage inputs and four adjoint stage kernels per step
+ * (transposed stencils, transposed separable source, per-term gradient reductions).  The
+ * separation constant's dependence on the parameters (Eq. 304) is included.  The state is left
+ * as it was (content and tau).  work: caller-owned device buffer, 256-byte aligned.
+ * Synchronises stream. */
+int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_every, void* work, size_t work_bytes,
+            double* loss_out, double* grad_out, void* stream);
 
 /* bq_step without any memory allocation, for callers that cannot allocate device memory
  * (code running inside another framework's CUDA-graph capture, where cudaMalloc is

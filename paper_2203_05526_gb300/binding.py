@@ -73,7 +73,11 @@ def lib() -> C.CDLL:
         "bq_step": (C.c_int, [vp, C.c_double, i64, vp]),
         "bq_step_fixed_scratch": (C.c_int, [vp, C.c_double, i64, vp]),
         "bq_solve": (C.c_int, [vp, C.c_double, i64, vp]),
+        "bq_grad_size": (C.c_int, [vp, ip]),
+        "bq_grad_required_bytes": (C.c_int, [vp, i64, C.c_int, C.POINTER(C.c_size_t)]),
+        "bq_grad": (C.c_int, [vp, C.c_double, i64, C.c_int, vp, C.c_size_t, dp, dp, vp]),
         "bq_solve_eligible": (C.c_int, [vp, ip]),
+        "bq_stage_variant": (C.c_int, [vp, ip]),
         "bq_time": (C.c_int, [vp, dp]),
         "bq_evaluate": (C.c_int, [vp, dp, vp]),
         "bq_fock_block": (C.c_int, [vp, C.c_int, dp, vp]),
@@ -103,7 +107,7 @@ def exported_symbols() -> List[str]:
     return [n for n in ("bq_problem_create", "bq_problem_destroy", "bq_problem_add_channel",
                         "bq_problem_add_h_term", "bq_problem_set_params", "bq_problem_add_jump",
                         "bq_problem_set_measured", "bq_problem_set_rho0", "bq_required_bytes", "bq_map",
-                        "bq_step", "bq_step_fixed_scratch", "bq_solve", "bq_solve_eligible", "bq_time", "bq_evaluate", "bq_fock_block", "bq_state_info",
+                        "bq_step", "bq_step_fixed_scratch", "bq_solve", "bq_solve_eligible", "bq_stage_variant", "bq_grad_size", "bq_grad_required_bytes", "bq_grad", "bq_time", "bq_evaluate", "bq_fock_block", "bq_state_info",
                         "bq_system_info", "bq_read_system", "bq_state_bytes", "bq_store_state",
                         "bq_load_state", "bq_set_time", "bq_state_destroy", "bq_status_string",
                         "bq_last_error", "bq_launch_count")]
@@ -235,6 +239,25 @@ class State:
     def solve(self, dt: float, n_steps: int, stream=None):
         """Batched persistent solve: all n_steps of every system in one kernel launch."""
         check(lib().bq_solve(self.ptr, float(dt), int(n_steps), _stream_ptr(stream)))
+
+    def grad(self, dt: float, n_steps: int, checkpoint_every: int = 160, stream=None):
+        """(losses[B], gradient) of Re Tr(rho0 A(T)) by the discrete adjoint (bq_grad)."""
+        import torch
+        n = C.c_int()
+        check(lib().bq_grad_size(self.ptr, C.byref(n)))
+        nb = C.c_size_t()
+        check(lib().bq_grad_required_bytes(self.ptr, int(n_steps), int(checkpoint_every), C.byref(nb)))
+        work = torch.empty(nb.value, dtype=torch.uint8, device=self.pool.device)
+        loss = (C.c_double * self.B)()
+        g = (C.c_double * max(1, n.value))()
+        check(lib().bq_grad(self.ptr, float(dt), int(n_steps), int(checkpoint_every), C.c_void_p(work.data_ptr()),
+                            nb.value, loss, g, _stream_ptr(stream)))
+        return np.array(loss[:]), np.array(g[:n.value])
+
+    def stage_variant(self) -> str:
+        v = C.c_int()
+        check(lib().bq_stage_variant(self.ptr, C.byref(v)))
+        return {0: "generic", 1: "single_mode", 2: "pipelined"}[v.value]
 
     def solve_eligible(self) -> bool:
         e = C.c_int()

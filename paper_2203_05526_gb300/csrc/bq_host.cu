@@ -219,6 +219,7 @@ static Poly product(const Key& m1, const Key& m2, cplx c) {
 struct RawTerm {
   int side;
   cplx c;
+  cplx cb;  // coefficient with the parameter value set to 1
   int ch, conj, param;
   int a[BQ_MAXD], b[BQ_MAXD];
 };
@@ -229,7 +230,13 @@ struct Compiled {
   std::vector<TermDesc> terms;         // wtab offsets relative to this problem's weight block
   std::vector<double> wtab;            // weight tables
   std::vector<cplx> diag;              // 2*nm tables
-  struct Sys { int p_flat, q_flat; cplx w, C; double gx0, gy0; };  // gx0/gy0: stored values of x^p, y^q
+  struct Sys {
+    int p_flat, q_flat;
+    cplx w, C;
+    double gx0, gy0;          // stored values of x^p, y^q
+    std::vector<cplx> dC;     // d C / d theta_p (Eq. 304)
+  };
+  int n_params = 0;
   std::vector<Sys> sys;
   std::vector<std::pair<long long, cplx>> init;  // direct method: (R element offset, value)
   std::vector<EvalEntry> trace_entries;          // Tr(rho0 A) entries (kx, ly, factor)
@@ -319,11 +326,11 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
   for (auto& t : p->h) {
     const cplx h = t.c * (t.param >= 0 ? p->params[t.param] : 1.0);
     RawTerm x; zero(x);
-    x.side = bq::SIDE_X; x.c = cplx(0, 1) * h; x.ch = t.ch; x.conj = t.conj; x.param = t.param;
+    x.side = bq::SIDE_X; x.c = cplx(0, 1) * h; x.cb = cplx(0, 1) * t.c; x.ch = t.ch; x.conj = t.conj; x.param = t.param;
     for (int j = 0; j < nm; ++j) { x.a[j] = t.u[j]; x.b[j] = t.v[j]; }
     raw.push_back(x);
     RawTerm y; zero(y);
-    y.side = bq::SIDE_Y; y.c = cplx(0, -1) * h; y.ch = t.ch; y.conj = t.conj; y.param = t.param;
+    y.side = bq::SIDE_Y; y.c = cplx(0, -1) * h; y.cb = cplx(0, -1) * t.c; y.ch = t.ch; y.conj = t.conj; y.param = t.param;
     for (int j = 0; j < nm; ++j) { y.a[nm + j] = t.v[j]; y.b[nm + j] = t.u[j]; }
     raw.push_back(y);
   }
@@ -337,7 +344,7 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
         for (auto& [k, v] : product(mt_dag, ms, std::conj(jp.c[t]) * jp.c[s])) LdL[k] += v;
         // sandwich kappa conj(c_t) c_s (m_t^dag)_left (m_s)_right
         RawTerm sw; zero(sw);
-        sw.side = bq::SIDE_S; sw.c = jp.rate * std::conj(jp.c[t]) * jp.c[s]; sw.ch = -1; sw.conj = 0; sw.param = -1;
+        sw.side = bq::SIDE_S; sw.c = jp.rate * std::conj(jp.c[t]) * jp.c[s]; sw.cb = sw.c; sw.ch = -1; sw.conj = 0; sw.param = -1;
         for (int j = 0; j < nm; ++j) {
           sw.a[j] = jp.v[t][j]; sw.b[j] = jp.u[t][j];            // left mult by m_t^dag
           sw.a[nm + j] = jp.v[s][j]; sw.b[nm + j] = jp.u[s][j];  // right mult by m_s
@@ -347,11 +354,11 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
     for (auto& [k, v] : LdL) {
       if (v == cplx(0, 0)) continue;
       RawTerm x; zero(x);
-      x.side = bq::SIDE_X; x.c = -0.5 * jp.rate * v; x.ch = -1; x.conj = 0; x.param = -1;
+      x.side = bq::SIDE_X; x.c = -0.5 * jp.rate * v; x.cb = x.c; x.ch = -1; x.conj = 0; x.param = -1;
       for (int j = 0; j < nm; ++j) { x.a[j] = k.first[j]; x.b[j] = k.second[j]; }
       raw.push_back(x);
       RawTerm y; zero(y);
-      y.side = bq::SIDE_Y; y.c = -0.5 * jp.rate * v; y.ch = -1; y.conj = 0; y.param = -1;
+      y.side = bq::SIDE_Y; y.c = -0.5 * jp.rate * v; y.cb = y.c; y.ch = -1; y.conj = 0; y.param = -1;
       for (int j = 0; j < nm; ++j) { y.a[nm + j] = k.second[j]; y.b[nm + j] = k.first[j]; }
       raw.push_back(y);
     }
@@ -364,7 +371,7 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
   std::vector<int> doff(ND + 1, 0);
   for (int d = 0; d < ND; ++d) doff[d + 1] = doff[d] + Md[d];
   C.diag.assign(doff[ND], cplx(0, 0));
-  std::map<std::tuple<int, int, int, int, std::vector<int>>, cplx> merged;
+  std::map<std::tuple<int, int, int, int, std::vector<int>>, std::pair<cplx, cplx>> merged;  // (c, cb)
   for (auto& t : raw) {
     if (t.c == cplx(0, 0)) continue;
     bool diag = true;
@@ -373,7 +380,7 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
       if (t.a[d] != t.b[d]) diag = false;
       if (t.a[d] || t.b[d]) { ++nact; dact = d; }
     }
-    if (t.side != bq::SIDE_S && t.ch < 0 && diag && nact <= 1) {
+    if (t.side != bq::SIDE_S && t.ch < 0 && t.param < 0 && diag && nact <= 1) {
       const int d = nact == 0 ? (t.side == bq::SIDE_X ? 0 : nm) : dact;
       for (int k = 0; k < Md[d]; ++k) {
         double w = 1.0;
@@ -385,7 +392,9 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
     }
     std::vector<int> ab(2 * ND);
     for (int d = 0; d < ND; ++d) { ab[d] = t.a[d]; ab[ND + d] = t.b[d]; }
-    merged[{t.side, t.ch, t.conj, t.param, ab}] += t.c;
+    auto& mv = merged[{t.side, t.ch, t.conj, t.param, ab}];
+    mv.first += t.c;
+    mv.second += t.cb;
   }
   if ((int)merged.size() > BQ_MAX_TERMS) return fail(BQ_EUNSUPPORTED, "%zu stencil terms > %d", merged.size(), BQ_MAX_TERMS);
 
@@ -399,19 +408,23 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
   C.wtab.clear();
   C.halo_lo = C.halo_hi = 0;
   double rho_terms = 0.0;
-  for (auto& [key, c] : merged) {
-    if (c == cplx(0, 0)) continue;
+  for (auto& [key, cc] : merged) {
+    const cplx c = cc.first;
+    if (c == cplx(0, 0) && cc.second == cplx(0, 0)) continue;
     auto& [side, ch, conj, param, ab] = key;
     if (!C.has_r && side == bq::SIDE_S) continue;  // sandwich acts only on R (and as its source)
     TermDesc td;
     std::memset(&td, 0, sizeof(td));
     td.c_re = c.real(); td.c_im = c.imag(); td.ch = ch; td.conj = conj; td.side = side; td.param = param;
+    td.cb_re = cc.second.real(); td.cb_im = cc.second.imag();
+    td.gslot_param = -1; td.gslot_pwc = -1;
     int nact = 0, dR = 0, dGx = 0, dGy = 0;
     double wmax_num = 1.0;
     for (int d = 0; d < ND; ++d) {
       const int a = ab[d], b = ab[ND + d];
       if (!a && !b) continue;
       td.dim[nact] = (int8_t)d;
+      td.sh[nact] = (int8_t)(b - a);
       td.wtab[nact] = (int)C.wtab.size();
       double wm = 0.0;
       for (int k = 0; k < Md[d]; ++k) {
@@ -424,8 +437,8 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
       ++nact;
     }
     td.n_act = nact; td.deltaR = dR; td.deltaGx = dGx; td.deltaGy = dGy;
-    C.halo_lo = std::max(C.halo_lo, -dR);
-    C.halo_hi = std::max(C.halo_hi, dR);
+    C.halo_lo = std::max(C.halo_lo, std::abs(dR));  // symmetric: the adjoint gathers from p - delta
+    C.halo_hi = C.halo_lo;
     C.terms.push_back(td);
     rho_terms += std::abs(c) * (ch >= 0 ? chan_max(p->ch[ch]) : 1.0) * wmax_num;
   }
@@ -451,6 +464,7 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
     C.rho = dmax + rho_terms;
   }
 
+  C.n_params = (int)p->params.size();
   // ---- channels ----------------------------------------------------------------------
   C.chans.clear(); C.chpar.clear();
   for (auto& ch : p->ch) {
@@ -488,7 +502,7 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
     return s;
   };
   if (C.method == BQ_METHOD_DIRECT) {
-    C.sys.push_back({0, 0, cplx(1, 0), cplx(0, 0), 0.0, 0.0});
+    C.sys.push_back({0, 0, cplx(1, 0), cplx(0, 0), 0.0, 0.0, std::vector<cplx>(p->params.size(), cplx(0, 0))});
     for (auto& [kl, v] : p->measured)
       if (in_grid(kl.first) && in_grid(kl.second) && v != cplx(0, 0))
         C.init.push_back({(long long)flat_index(kl.first, C.M, nm) * C.n_g + flat_index(kl.second, C.M, nm), v});
@@ -505,6 +519,19 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
         cs += (om[j] - et[j]) * (pj + qj) + et[j] * (pj * pj + qj * qj);
       }
       s.C = o.c_mode == BQ_C_ZERO ? cplx(0, 0) : cplx(0, -0.5 * cs);
+      s.dC.assign(p->params.size(), cplx(0, 0));
+      if (o.c_mode != BQ_C_ZERO) {
+        for (auto& t : p->h) {
+          if (t.param < 0 || t.ch >= 0) continue;
+          int nz = 0, j0 = -1;
+          for (int j = 0; j < nm; ++j) if (t.u[j] || t.v[j]) { ++nz; j0 = j; }
+          if (nz != 1) continue;
+          const double cr = t.c.real();
+          const int pj = kl.first[j0], qj = kl.second[j0];
+          if (t.u[j0] == 1 && t.v[j0] == 1) s.dC[t.param] += cplx(0, -0.5 * cr * (pj + qj));
+          if (t.u[j0] == 2 && t.v[j0] == 2) s.dC[t.param] += cplx(0, -0.5 * cr * (pj * pj + qj * qj - pj - qj));
+        }
+      }
       // G_x = x^p, G_y = y^q in the storage basis (values s(p), s(q)); R = 0
       s.gx0 = sfl(kl.first);
       s.gy0 = sfl(kl.second);
@@ -560,14 +587,21 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
 // State.
 // ---------------------------------------------------------------------------------------
 struct Layout {
-  size_t off_sys, off_terms, off_chans, off_chpar, off_work, off_m1, off_order, off_groups, off_entries, off_out, off_wtab, off_diag,
+  size_t off_sys, off_terms, off_chans, off_chpar, off_work, off_m1, off_order, off_dc, off_pparams, off_precs, off_pcoef, off_groups, off_entries, off_out, off_wtab, off_diag,
       off_ctrl, off_init, off_y, off_comp, off_ua, off_ub, off_acc, total;
 };
 
 struct bq_state {
   int B = 0, nm = 0, dtype = 0, method = 0, basis = 0, n_sys = 0, n_work = 0, smem_bytes = 0, use_m1 = 0, m1_variant = 0;
   int trace_small = 0, block_small = 0;
-  int solve_ok = 0, solve_smem = 0, last_solve_grid = 0;  // thread-per-group evaluation (few pairs per group)
+  int solve_ok = 0, solve_smem = 0, last_solve_grid = 0;
+  int use_pipe = 0, pipe_off_coef = 0, pipe_off_u = 0, pipe_off_y = 0, pipe_off_acc = 0, pipe_off_comp = 0;
+  int pipe_slot[3] = {0, 0, 0}, pipe_nslots[3] = {2, 2, 2}, pipe_grid[3] = {1, 1, 1};
+  int grad_size = 0, adj_smem = 0, srcred_stride = 0, max_s = 0;
+  std::vector<TermDesc> terms_host;
+  std::vector<ChanDesc> chans_host;
+  std::vector<double> chpar_host;
+  std::vector<WorkItem> work_host;  // thread-per-group evaluation (few pairs per group)
   int n_trace_groups = 0, n_block_groups = 0, block_dim = 0;
   int64_t total_elems = 0;
   double dt_max = 0.0, horizon = 0.0, tau = 0.0;
@@ -603,8 +637,18 @@ struct Plan {
   int m1_variant = 0;
   std::vector<bq::M1Sys> m1;
   std::vector<int> order;  // batched solve queue (largest system first); empty: not eligible
+  // pipelined stage kernel
+  int use_pipe = 0, pipe_off_coef = 0, pipe_off_u = 0, pipe_off_y = 0, pipe_off_acc = 0, pipe_off_comp = 0;
+  int pipe_slot[3] = {0, 0, 0};
+  std::vector<unsigned char> pparams;
+  std::vector<bq::PipeRec> precs;
   int solve_smem = 0;
+  int adj_smem = 0;  // shared memory of the adjoint stage kernel
+  int srcred_stride = 0, max_s = 0;
   std::vector<int> wbase;  // per problem: offset of its weight tables in the pool
+  std::vector<int> grad_offs;  // per problem: first gradient slot
+  std::vector<cplx> dc;        // d C / d theta per system and parameter
+  int grad_size = 0;
   int64_t total_elems = 0;
   double rho = 0.0, dt_max = 0.0;
   Layout L{};
@@ -631,7 +675,18 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
     const int term_off = (int)P.terms.size();
     const int wbase = (int)P.wtab.size();
     P.wbase.push_back(wbase);
+    // gradient layout of this problem: [theta_0 .. theta_{P-1} | (Re, Im) of every segment of
+    // every piecewise-constant channel, channels in order]
+    const int grad_off = P.grad_size;
+    std::vector<int> pwc_off(C.chans.size(), -1);
+    int gsz = C.n_params;
+    for (size_t c = 0; c < C.chans.size(); ++c)
+      if (C.chans[c].kind == BQ_CH_PWC) { pwc_off[c] = gsz; gsz += 2 * ((C.chans[c].n_par - 2) / 2); }
+    P.grad_size += gsz;
+    P.grad_offs.push_back(grad_off);
     for (auto td : C.terms) {
+      td.gslot_param = td.param >= 0 ? grad_off + td.param : -1;
+      td.gslot_pwc = (td.ch >= 0 && pwc_off[td.ch] >= 0) ? grad_off + pwc_off[td.ch] : -1;
       for (int i = 0; i < td.n_act; ++i) td.wtab[i] += wbase;
       if (td.ch >= 0) td.ch += (int)P.chans.size();
       P.terms.push_back(td);
@@ -660,6 +715,10 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
       if (C.has_sep) { sd.off_gx = elem; elem += pad16(C.n_g); sd.off_gy = elem; elem += pad16(C.n_g); }
       if (C.has_r) { sd.off_r = elem; elem += pad16(C.n_r); }
       sd.c_re = s.C.real(); sd.c_im = s.C.imag(); sd.w_re = s.w.real(); sd.w_im = s.w.imag();
+      sd.n_params = C.n_params;
+      sd.grad_off = grad_off;
+      sd.dc_off = (int)P.dc.size();
+      P.dc.insert(P.dc.end(), s.dC.begin(), s.dC.end());
       P.sys.push_back(sd);
     }
     // initial values
@@ -765,6 +824,71 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
         solve_max = std::max(solve_max, bytes);
         sz.push_back({-ntot, i});
       }
+      // pipelined stage kernel: parameter blocks per problem, records per system
+      {
+        std::vector<int> poff(B, -1), pbytes(B, 0);
+        size_t blk_max = 0, par_max = 0;
+        for (int b = 0; b < B; ++b) {
+          const Compiled& C = P.comp[b];
+          const bq::M1Sys& m = progs[b];
+          const int M = C.M[0];
+          bq::PipeHdr hd;
+          std::memset(&hd, 0, sizeof(hd));
+          hd.M = M; hd.nX = m.nX; hd.nY = m.nY; hd.nS = m.nS; hd.has_sep = C.has_sep; hd.has_r = C.has_r;
+          hd.ntot = (C.has_r ? M * M : 0) + (C.has_sep ? 2 * M : 0);
+          for (int q = 0; q < BQ_M1_MAXT; ++q) { hd.sX[q] = m.sX[q]; hd.sY[q] = m.sY[q]; hd.sSx[q] = m.sSx[q]; hd.sSy[q] = m.sSy[q]; }
+          std::vector<unsigned char> blk(sizeof(hd));
+          std::memcpy(blk.data(), &hd, sizeof(hd));
+          auto put_c = [&](cplx v) {
+            if (cs == 16) { double d[2] = {v.real(), v.imag()}; blk.insert(blk.end(), (unsigned char*)d, (unsigned char*)d + 16); }
+            else { float f[2] = {(float)v.real(), (float)v.imag()}; blk.insert(blk.end(), (unsigned char*)f, (unsigned char*)f + 8); }
+          };
+          auto put_r = [&](double v) {
+            if (rs == 8) blk.insert(blk.end(), (unsigned char*)&v, (unsigned char*)&v + 8);
+            else { float f = (float)v; blk.insert(blk.end(), (unsigned char*)&f, (unsigned char*)&f + 4); }
+          };
+          for (int i = 0; i < M; ++i) put_c(C.diag[i]);
+          for (int i = 0; i < M; ++i) put_c(C.diag[M + i]);
+          auto put_w = [&](int woff) { for (int i = 0; i < M; ++i) put_r(woff >= 0 ? C.wtab[woff + i] : 1.0); };
+          auto local = [&](int w) { return w >= 0 ? w - P.wbase[b] : -1; };
+          for (int q = 0; q < m.nX; ++q) put_w(local(m.wX[q] >= 0 ? m.wX[q] : -1) >= 0 ? local(m.wX[q]) : -1);
+          for (int q = 0; q < m.nY; ++q) put_w(m.wY[q] >= 0 ? local(m.wY[q]) : -1);
+          for (int q = 0; q < m.nS; ++q) put_w(m.wSx[q] >= 0 ? local(m.wSx[q]) : -1);
+          for (int q = 0; q < m.nS; ++q) put_w(m.wSy[q] >= 0 ? local(m.wSy[q]) : -1);
+          while (blk.size() % 16) blk.push_back(0);
+          poff[b] = (int)P.pparams.size();
+          pbytes[b] = (int)blk.size();
+          P.pparams.insert(P.pparams.end(), blk.begin(), blk.end());
+          par_max = std::max(par_max, blk.size());
+        }
+        for (int i = 0; i < (int)P.sys.size(); ++i) {
+          const SysDesc& sd = P.sys[i];
+          bq::PipeRec r;
+          std::memset(&r, 0, sizeof(r));
+          const int pg = (sd.n_g + 15) & ~15, pr = (sd.n_r + 15) & ~15;
+          r.blk_off = (int)(sd.has_sep ? sd.off_gx : sd.off_r);
+          r.blk_elems = (sd.has_sep ? 2 * pg : 0) + (sd.has_r ? pr : 0);
+          r.param_off = poff[sd.prob];
+          r.param_bytes = pbytes[sd.prob];
+          r.gx_off = sd.has_sep ? 0 : -1;
+          r.gy_off = sd.has_sep ? pg : -1;
+          r.r_off = sd.has_r ? (sd.has_sep ? 2 * pg : 0) : -1;
+          r.sys = i;
+          P.precs.push_back(r);
+          blk_max = std::max(blk_max, (size_t)r.blk_elems);
+        }
+        auto a128 = [](size_t x) { return (x + 127) & ~(size_t)127; };
+        P.pipe_off_coef = (int)a128(par_max);
+        P.pipe_off_u = P.pipe_off_coef + (int)a128(BQ_PIPE_COEF * cs);
+        const int blkb = (int)a128(blk_max * cs);
+        P.pipe_off_y = P.pipe_off_u + blkb;
+        P.pipe_off_acc = P.pipe_off_y + blkb;
+        P.pipe_off_comp = P.pipe_off_acc + blkb;
+        P.pipe_slot[0] = P.pipe_off_y;          // stage 1: parameters, coefficients, input
+        P.pipe_slot[1] = P.pipe_off_comp;       // stages 2-3: + state, stage sum
+        P.pipe_slot[2] = P.pipe_off_comp + blkb;  // stage 4: + compensation
+        P.use_pipe = 2 * (size_t)P.pipe_slot[2] <= 200 * 1024 ? 1 : 0;
+      }
       if (solve_ok && solve_max <= 160 * 1024) {
         std::stable_sort(sz.begin(), sz.end());
         for (auto& e : sz) P.order.push_back(e.second);
@@ -804,6 +928,21 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
     }
   }
   if (!P.use_m1) P.smem_bytes = (int)(smem_max * cs);
+  // adjoint stage kernel: b window + b_gx + b_gy + transposed-source reductions
+  {
+    size_t adj_max = 0;
+    for (auto& w : P.work) {
+      const SysDesc& sd = P.sys[w.sys];
+      const Compiled& C = P.comp[sd.prob];
+      int ns = 0;
+      for (auto& td : C.terms) ns += td.side == bq::SIDE_S;
+      const size_t e = (size_t)(w.win_hi - w.win_lo) + (sd.has_sep ? (size_t)(2 + 2 * ns) * sd.n_g : 0);
+      adj_max = std::max(adj_max, e);
+      P.srcred_stride = std::max(P.srcred_stride, (sd.has_sep && sd.has_r) ? 2 * ns * sd.n_g : 0);
+      P.max_s = std::max(P.max_s, (sd.has_sep && sd.has_r) ? ns : 0);
+    }
+    P.adj_smem = (int)(adj_max * cs);
+  }
   P.dt_max = 2.0 * std::sqrt(2.0) / std::max(P.rho, 1e-300);
   if (o->dt > 0.0 && o->dt > P.dt_max)
     return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 stability bound %g (spectral bound %g)", o->dt, P.dt_max, P.rho);
@@ -819,6 +958,10 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
   L.off_work = seg(P.work.size() * sizeof(WorkItem));
   L.off_m1 = seg(P.m1.size() * sizeof(bq::M1Sys));
   L.off_order = seg(P.order.size() * sizeof(int));
+  L.off_pparams = seg(P.pparams.size());
+  L.off_precs = seg(P.precs.size() * sizeof(bq::PipeRec));
+  L.off_pcoef = seg(P.use_pipe ? (size_t)P.sys.size() * BQ_PIPE_COEF * cs : 0);
+  L.off_dc = seg(P.dc.size() * sizeof(double2));
   L.off_groups = seg(P.groups.size() * sizeof(EvalGroup));
   L.off_entries = seg(P.entries.size() * sizeof(EvalEntry));
   L.off_out = seg(P.groups.size() * 2 * sizeof(double));
@@ -872,6 +1015,13 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   CUDA_TRY(up(L.off_work, P.work.data(), P.work.size() * sizeof(WorkItem)));
   CUDA_TRY(up(L.off_m1, P.m1.data(), P.m1.size() * sizeof(bq::M1Sys)));
   CUDA_TRY(up(L.off_order, P.order.data(), P.order.size() * sizeof(int)));
+  CUDA_TRY(up(L.off_pparams, P.pparams.data(), P.pparams.size()));
+  CUDA_TRY(up(L.off_precs, P.precs.data(), P.precs.size() * sizeof(bq::PipeRec)));
+  {
+    std::vector<double2> dcv(P.dc.size());
+    for (size_t i = 0; i < dcv.size(); ++i) dcv[i] = make_double2(P.dc[i].real(), P.dc[i].imag());
+    CUDA_TRY(up(L.off_dc, dcv.data(), dcv.size() * sizeof(double2)));
+  }
   CUDA_TRY(up(L.off_groups, P.groups.data(), P.groups.size() * sizeof(EvalGroup)));
   CUDA_TRY(up(L.off_entries, P.entries.data(), P.entries.size() * sizeof(EvalEntry)));
   if (o->dtype == BQ_F64) {
@@ -910,6 +1060,32 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   }
   st->m1_variant = P.m1_variant;
   st->solve_ok = P.order.empty() ? 0 : 1;
+  st->use_pipe = P.use_pipe;
+  st->pipe_off_coef = P.pipe_off_coef; st->pipe_off_u = P.pipe_off_u; st->pipe_off_y = P.pipe_off_y;
+  st->pipe_off_acc = P.pipe_off_acc; st->pipe_off_comp = P.pipe_off_comp;
+  for (int q = 0; q < 3; ++q) st->pipe_slot[q] = P.pipe_slot[q];
+  if (st->use_pipe) {
+    int dev = 0, nsm = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    for (int q = 0; q < 3; ++q) {
+      const int slot = st->pipe_slot[q];
+      const int nsl = std::max(2, std::min(4, (200 * 1024) / std::max(1, slot)));
+      st->pipe_nslots[q] = nsl;
+      int per_sm = 0;
+      CUDA_TRY(bq::pipe_blocks_per_sm(o->dtype, P.m1_variant, nsl * slot, &per_sm));
+      if (per_sm < 1) { st->use_pipe = 0; break; }
+      st->pipe_grid[q] = std::min((int)P.sys.size(), per_sm * nsm);
+    }
+  }
+  st->grad_size = P.grad_size;
+  st->adj_smem = P.adj_smem;
+  st->srcred_stride = P.srcred_stride;
+  st->max_s = P.max_s;
+  st->terms_host = P.terms;
+  st->chans_host = P.chans;
+  st->chpar_host = P.chpar;
+  st->work_host = P.work;
   st->solve_smem = P.solve_smem;
   st->n_trace_groups = P.n_trace_groups; st->n_block_groups = P.n_block_groups; st->block_dim = P.block_dim;
   st->total_elems = P.total_elems; st->dt_max = dt_max; st->horizon = o->horizon; st->reverse = o->reverse_time;
@@ -931,6 +1107,7 @@ extern "C" void bq_state_destroy(bq_state* s) {
 // ---------------------------------------------------------------------------------------
 static bq::StageArgs stage_args(bq_state* s, int stage, double dt) {
   bq::StageArgs a;
+  std::memset(&a, 0, sizeof(a));  // every field, including the optional recording pointer
   char* b = s->pool;
   const Layout& L = s->L;
   a.sys = (const SysDesc*)(b + L.off_sys);
@@ -960,6 +1137,33 @@ static bq::StageArgs stage_args(bq_state* s, int stage, double dt) {
 }
 
 static cudaError_t launch_any_stage(bq_state* s, const bq::StageArgs& a, cudaStream_t st) {
+  if (s->use_pipe && !a.rec) {
+    char* b = s->pool;
+    const Layout& L = s->L;
+    bq::PipeArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.recs = (const bq::PipeRec*)(b + L.off_precs);
+    pa.params = (const unsigned char*)(b + L.off_pparams);
+    pa.coef = b + L.off_pcoef;
+    pa.u_in = a.u_in; pa.u_out = a.u_out; pa.y = a.y; pa.acc = a.acc; pa.comp = a.comp;
+    pa.ticket = a.ticket; pa.counter = a.counter;
+    pa.error = (unsigned int*)(b + L.off_ctrl + 32);
+    pa.n_sys = s->n_sys; pa.stage = a.stage;
+    const int q = a.stage == 1 ? 0 : (a.stage == 4 ? 2 : 1);
+    pa.n_slots = s->pipe_nslots[q];
+    pa.slot_bytes = s->pipe_slot[q];
+    pa.off_coef = s->pipe_off_coef; pa.off_u = s->pipe_off_u; pa.off_y = s->pipe_off_y;
+    pa.off_acc = s->pipe_off_acc; pa.off_comp = s->pipe_off_comp;
+    pa.dt = a.dt;
+    bq::CoefArgs ca;
+    std::memset(&ca, 0, sizeof(ca));
+    ca.m1 = (const bq::M1Sys*)(b + L.off_m1);
+    ca.sys = a.sys; ca.terms = a.terms; ca.chans = a.chans; ca.chpar = a.chpar;
+    ca.coef = b + L.off_pcoef;
+    ca.tau_base = a.tau_base; ca.counter = a.counter;
+    ca.dt = a.dt; ca.horizon = a.horizon; ca.n_sys = s->n_sys; ca.stage = a.stage; ca.reverse = a.reverse;
+    return bq::launch_stage_pipe(pa, ca, s->m1_variant, s->dtype, s->pipe_grid[q], pa.n_slots * pa.slot_bytes, st);
+  }
   if (s->use_m1)
     return bq::launch_stage_m1(a, (const bq::M1Sys*)(s->pool + s->L.off_m1), s->m1_variant, s->dtype, s->n_work,
                                s->smem_bytes, st);
@@ -1070,6 +1274,7 @@ extern "C" int bq_solve(bq_state* s, double dt, int64_t n_steps, void* stream) {
   const Layout& L = s->L;
   CUDA_TRY(cudaMemsetAsync(b + L.off_ctrl + 24, 0, 8, st));
   bq::SolveArgs a;
+  std::memset(&a, 0, sizeof(a));
   a.m1 = (const bq::M1Sys*)(b + L.off_m1);
   a.order = (const int*)(b + L.off_order);
   a.terms = (const TermDesc*)(b + L.off_terms);
@@ -1092,9 +1297,169 @@ extern "C" int bq_solve(bq_state* s, double dt, int64_t n_steps, void* stream) {
   return BQ_OK;
 }
 
+extern "C" int bq_stage_variant(const bq_state* s, int* variant) {
+  if (!s || !variant) return fail(BQ_EINVAL, "NULL argument");
+  *variant = s->use_pipe ? 2 : (s->use_m1 ? 1 : 0);
+  return BQ_OK;
+}
+
 extern "C" int bq_solve_eligible(const bq_state* s, int* eligible) {
   if (!s || !eligible) return fail(BQ_EINVAL, "NULL argument");
   *eligible = s->solve_ok;
+  return BQ_OK;
+}
+
+
+static int run_eval(bq_state* s, int g0, int n, int small, double* out_host, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------
+// Gradients (discrete adjoint with checkpointing).
+// ---------------------------------------------------------------------------------------
+struct GradLayout {
+  size_t ckpt, rec, lam, lacc, ba, bb, srcred, grad, total;
+  int64_t n_ckpt;
+};
+
+static GradLayout grad_layout(const bq_state* s, int64_t n_steps, int k) {
+  GradLayout g{};
+  const size_t cs = s->dtype == BQ_F64 ? 16 : 8;
+  const size_t arr = (size_t)s->total_elems * cs;
+  size_t o = 0;
+  auto seg = [&](size_t bytes) { size_t r = o; o = align_up(o + std::max<size_t>(bytes, 1)); return r; };
+  g.n_ckpt = (n_steps + k - 1) / k;
+  g.ckpt = seg(2 * arr * (size_t)g.n_ckpt);
+  g.rec = seg(4 * arr * (size_t)k);
+  g.lam = seg(arr);
+  g.lacc = seg(arr);
+  g.ba = seg(arr);
+  g.bb = seg(arr);
+  g.srcred = seg((size_t)s->n_sys * std::max(1, s->srcred_stride) * cs);
+  g.grad = seg((size_t)std::max(1, s->grad_size) * sizeof(double));
+  g.total = o;
+  return g;
+}
+
+extern "C" int bq_grad_size(const bq_state* s, int* n) {
+  if (!s || !n) return fail(BQ_EINVAL, "NULL argument");
+  *n = s->grad_size;
+  return BQ_OK;
+}
+
+extern "C" int bq_grad_required_bytes(const bq_state* s, int64_t n_steps, int checkpoint_every, size_t* out) {
+  if (!s || !out || n_steps < 1 || checkpoint_every < 1) return fail(BQ_EINVAL, "bad argument");
+  *out = grad_layout(s, n_steps, checkpoint_every).total;
+  return BQ_OK;
+}
+
+static cudaError_t enqueue_steps_rec(bq_state* s, double dt, int64_t n, cudaStream_t st, char* rec, size_t arr) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int stage = 1; stage <= 4; ++stage) {
+      bq::StageArgs a = stage_args(s, stage, dt);
+      a.rec = rec ? rec + ((size_t)i * 4 + stage - 1) * arr : nullptr;
+      cudaError_t e = launch_any_stage(s, a, st);
+      if (e != cudaSuccess) return e;
+      g_launches++;
+    }
+  return cudaSuccess;
+}
+
+static int set_tau(bq_state* s, double tau, cudaStream_t st) {
+  s->tau = tau;
+  s->tau_base_host = tau;
+  CUDA_TRY(cudaMemcpyAsync(s->pool + s->L.off_ctrl, &s->tau_base_host, sizeof(double), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemsetAsync(s->pool + s->L.off_ctrl + 8, 0, 16, st));
+  CUDA_TRY(cudaStreamSynchronize(st));  // the host value above is reused immediately
+  return BQ_OK;
+}
+
+extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_every, void* work, size_t work_bytes,
+                       double* loss_out, double* grad_out, void* stream) {
+  if (!s || !work || !loss_out || !grad_out) return fail(BQ_EINVAL, "NULL argument");
+  if (n_steps < 1 || checkpoint_every < 1 || !(dt > 0.0)) return fail(BQ_EINVAL, "bad step arguments");
+  if (dt > s->dt_max * (1.0 + 1e-12)) return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 bound %g", dt, s->dt_max);
+  const GradLayout G = grad_layout(s, n_steps, checkpoint_every);
+  if (work_bytes < G.total) return fail(BQ_ENOMEM, "gradient workspace has %zu bytes, needs %zu", work_bytes, G.total);
+  if (((uintptr_t)work & 255) != 0) return fail(BQ_EINVAL, "gradient workspace must be 256-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = (char*)work;
+  char* b = s->pool;
+  const Layout& L = s->L;
+  const size_t cs = s->dtype == BQ_F64 ? 16 : 8;
+  const size_t arr = (size_t)s->total_elems * cs;
+  const double tau0 = s->tau;
+  const int k = checkpoint_every;
+  CUDA_TRY(cudaMemsetAsync(w + G.grad, 0, (size_t)std::max(1, s->grad_size) * sizeof(double), st));
+  // ---- forward with checkpoints ----------------------------------------------------------
+  for (int64_t c = 0; c < G.n_ckpt; ++c) {
+    const int64_t n0 = c * k, n1 = std::min<int64_t>(n_steps, n0 + k);
+    CUDA_TRY(cudaMemcpyAsync(w + G.ckpt + (2 * c) * arr, b + L.off_y, arr, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(w + G.ckpt + (2 * c + 1) * arr, b + L.off_comp, arr, cudaMemcpyDeviceToDevice, st));
+    int r = set_tau(s, tau0 + (double)n0 * dt, st);
+    if (r != BQ_OK) return r;
+    CUDA_TRY(enqueue_steps_rec(s, dt, n1 - n0, st, nullptr, arr));
+  }
+  s->tau = tau0 + (double)n_steps * dt;
+  // ---- loss and the cotangent of the final state -----------------------------------------
+  std::vector<double> tr(2 * (size_t)s->B);
+  int r = run_eval(s, 0, s->n_trace_groups, s->trace_small, tr.data(), st);
+  if (r != BQ_OK) return r;
+  for (int i = 0; i < s->B; ++i) loss_out[i] = tr[2 * i];
+  CUDA_TRY(cudaMemsetAsync(w + G.lam, 0, arr, st));
+  CUDA_TRY(bq::launch_adj_seed((const SysDesc*)(b + L.off_sys), (const EvalGroup*)(b + L.off_groups),
+                               (const EvalEntry*)(b + L.off_entries), b + L.off_y, w + G.lam, s->n_trace_groups,
+                               s->dtype, st));
+  g_launches++;
+  // ---- backward sweep ----------------------------------------------------------------------
+  char* lam = w + G.lam;
+  char* lacc = w + G.lacc;
+  bq::AdjArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.sys = (const SysDesc*)(b + L.off_sys);
+  a.terms = (const TermDesc*)(b + L.off_terms);
+  a.chans = (const ChanDesc*)(b + L.off_chans);
+  a.chpar = (const double*)(b + L.off_chpar);
+  a.wtab = b + L.off_wtab;
+  a.diag = b + L.off_diag;
+  a.work = (const WorkItem*)(b + L.off_work);
+  a.dc = (const double2*)(b + L.off_dc);
+  a.srcred = w + G.srcred;
+  a.grad = (double*)(w + G.grad);
+  a.dt = dt;
+  a.horizon = s->horizon;
+  a.reverse = s->reverse;
+  a.srcred_stride = s->srcred_stride;
+  for (int64_t c = G.n_ckpt - 1; c >= 0; --c) {
+    const int64_t n0 = c * k, n1 = std::min<int64_t>(n_steps, n0 + k);
+    // recompute the segment from its checkpoint, recording every stage input
+    CUDA_TRY(cudaMemcpyAsync(b + L.off_y, w + G.ckpt + (2 * c) * arr, arr, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(b + L.off_comp, w + G.ckpt + (2 * c + 1) * arr, arr, cudaMemcpyDeviceToDevice, st));
+    r = set_tau(s, tau0 + (double)n0 * dt, st);
+    if (r != BQ_OK) return r;
+    CUDA_TRY(enqueue_steps_rec(s, dt, n1 - n0, st, w + G.rec, arr));
+    for (int64_t n = n1 - 1; n >= n0; --n) {
+      a.tau_step = tau0 + (double)n * dt;
+      a.lam = lam;
+      a.lacc = lacc;
+      for (int stage = 4; stage >= 1; --stage) {
+        a.stage = stage;
+        a.u = w + G.rec + ((size_t)(n - n0) * 4 + stage - 1) * arr;
+        a.b_in = stage == 4 ? nullptr : (stage == 3 ? (void*)(w + G.ba) : (stage == 2 ? (void*)(w + G.bb) : (void*)(w + G.ba)));
+        a.b_out = stage == 4 ? (void*)(w + G.ba) : (stage == 3 ? (void*)(w + G.bb) : (stage == 2 ? (void*)(w + G.ba) : nullptr));
+        CUDA_TRY(bq::launch_adjoint(a, s->dtype, s->nm, s->n_work, s->adj_smem, s->n_sys, s->max_s, st));
+        g_launches += s->max_s > 0 ? 2 : 1;
+      }
+      std::swap(lam, lacc);
+    }
+  }
+  // leave the state as it was before the call (initial content, tau0)
+  CUDA_TRY(cudaMemcpyAsync(b + L.off_y, w + G.ckpt, arr, cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(b + L.off_comp, w + G.ckpt + arr, arr, cudaMemcpyDeviceToDevice, st));
+  r = set_tau(s, tau0, st);
+  if (r != BQ_OK) return r;
+  CUDA_TRY(cudaMemcpyAsync(grad_out, w + G.grad, (size_t)s->grad_size * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < s->grad_size; ++i)
+    if (!std::isfinite(grad_out[i])) return fail(BQ_ENONFINITE, "non-finite gradient");
   return BQ_OK;
 }
 
@@ -1115,7 +1480,10 @@ static int run_eval(bq_state* s, int g0, int n, int small, double* out_host, cud
                            s->dtype, small, st));
   g_launches++;
   CUDA_TRY(cudaMemcpyAsync(out_host, b + L.off_out + (size_t)g0 * 16, (size_t)n * 16, cudaMemcpyDeviceToHost, st));
+  unsigned int err_word = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err_word, b + L.off_ctrl + 32, sizeof(err_word), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  if (err_word) return fail(BQ_ETIMEOUT, "a bounded device wait gave up during stepping (error word %u)", err_word);
   for (int i = 0; i < 2 * n; ++i)
     if (!std::isfinite(out_host[i])) return fail(BQ_ENONFINITE, "non-finite observable");
   return BQ_OK;

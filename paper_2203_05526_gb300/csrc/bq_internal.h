@@ -34,6 +34,12 @@ struct TermDesc {
   int8_t dim[BQ_MAXD];
   int8_t pad8[2];
   int wtab[BQ_MAXD];   // element offsets of the weight tables (length M_dim each)
+  // gradient metadata
+  double cb_re, cb_im; // coefficient with the parameter value set to 1
+  int8_t sh[BQ_MAXD];  // source shift (b - a) per active dimension
+  int8_t pad8b[2];
+  int gslot_param;     // gradient slot of d/dtheta (absolute, -1: none)
+  int gslot_pwc;       // gradient slot of Re(segment 0) of a piecewise-constant channel (-1: none)
 };
 
 // Drive envelope.
@@ -59,10 +65,13 @@ struct SysDesc {
   int p_flat, q_flat;   // initial condition indices (flattened)
   int stR[BQ_MAXD];     // element strides of R (x-dims outer, y-dims inner)
   int stG[3];           // element strides of G_x / G_y
-  int pad;
+  int dc_off;           // offset of d C / d theta_p (complex, one per parameter) in the gradient tables
   int64_t off_gx, off_gy, off_r;  // complex element offsets into the state arrays
   double c_re, c_im;    // separation constant C (Eq. 304)
   double w_re, w_im;    // weight g_{p,q}(0) of the initial condition
+  int n_params;         // parameters of the problem
+  int grad_off;         // gradient slot of the problem's first parameter
+  int pad2[2];
 };
 
 // A CTA's share of one stage: a tile of R points of one system (plus G_x, G_y if sep).
@@ -117,6 +126,7 @@ struct StageArgs {
   void* y;              // state (read stages 2-3, written stage 4)
   void* acc;            // RK4 stage sum k1 + 2 k2 + 2 k3 (scratch)
   void* comp;           // compensation of the state update (part of the state, starts at 0)
+  void* rec;            // if non-null: the stage input of every point is also written here
   const double* tau_base;      // device: tau at counter = 0
   long long* counter;          // device: completed steps since tau_base
   unsigned int* ticket;        // device: stage-4 completion ticket
@@ -124,6 +134,55 @@ struct StageArgs {
   double horizon;
   int reverse;
   int stage;            // 1..4
+};
+
+// Pipelined single-mode stage kernel (k_stage_pipe): one record per system and one
+// parameter block per problem, both fetched with 1-D bulk copies (TMA) into shared memory.
+struct PipeRec {
+  int blk_off;      // element offset of the system block ([G_x | G_y | R] or [R]) in the state arrays
+  int blk_elems;    // element count of the block (multiple of 16)
+  int param_off;    // byte offset of the problem's parameter block
+  int param_bytes;  // its size (multiple of 16)
+  int gx_off, gy_off, r_off;  // element offsets inside the block (-1: absent)
+  int sys;          // system index (coefficient block)
+};
+// Header of a parameter block (128 B), followed by dx[M], dy[M] (complex) and the weight tables
+// wX[nX][M], wY[nY][M], wSx[nS][M], wSy[nS][M] (real), the whole block padded to 16 B.
+struct PipeHdr {
+  int M, nX, nY, nS, has_sep, has_r, ntot, pad;
+  int sX[BQ_M1_MAXT], sY[BQ_M1_MAXT], sSx[BQ_M1_MAXT], sSy[BQ_M1_MAXT];
+  int pad2[8];
+};
+#define BQ_PIPE_COEF 16  // complex coefficients per system and stage: X, Y, S terms, C at slot 15
+
+struct PipeArgs {
+  const PipeRec* recs;
+  const unsigned char* params;
+  const void* coef;     // n_sys x BQ_PIPE_COEF complex, this stage
+  const void* u_in;
+  void* u_out;
+  void* y;
+  void* acc;
+  void* comp;
+  unsigned int* ticket;
+  long long* counter;
+  unsigned int* error;  // set when a bounded wait gives up
+  int n_sys, stage, n_slots, pad;
+  int slot_bytes, off_coef, off_u, off_y, off_acc, off_comp, pad2[2];  // shared-memory layout of a slot
+  double dt;
+};
+
+struct CoefArgs {
+  const M1Sys* m1;
+  const SysDesc* sys;
+  const TermDesc* terms;
+  const ChanDesc* chans;
+  const double* chpar;
+  void* coef;
+  const double* tau_base;
+  const long long* counter;
+  double dt, horizon;
+  int n_sys, stage, reverse, pad;
 };
 
 // Arguments of the batched persistent solve (k_solve_m1).
@@ -142,6 +201,27 @@ struct SolveArgs {
   int reverse;
   long long n_steps;
   double dt, tau0, horizon;
+};
+
+// Arguments of one adjoint (transposed) RK4 stage, see k_adj_stage.
+struct AdjArgs {
+  const SysDesc* sys;
+  const TermDesc* terms;
+  const ChanDesc* chans;
+  const double* chpar;
+  const void* wtab;
+  const void* diag;
+  const WorkItem* work;
+  const double2* dc;     // d C / d theta per system (SysDesc::dc_off)
+  const void* b_in;      // b_i; NULL at stage 4 (then b_4 = dt/6 lam)
+  const void* lam;       // cotangent of the state after the step
+  void* lacc;            // cotangent of the state before the step (accumulated over stages)
+  void* b_out;           // b_{i-1} (stages 4..2)
+  const void* u;         // recorded stage input u_i
+  const void* srcred;    // transposed-source reductions, srcred_stride complex per system
+  double* grad;          // gradient slots
+  double tau_step, dt, horizon;
+  int reverse, stage, srcred_stride, pad;
 };
 
 }  // namespace bq

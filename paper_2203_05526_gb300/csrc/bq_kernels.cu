@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
           k = cfma(sc[t], cmul(cscale(gxs[sx], wx), cscale(gys[sy], wy)), k);
         }
       }
+      if (A.rec) reinterpret_cast<C*>(A.rec)[sd.off_r + p] = uc;
       combine(sd.off_r + p, uc, k);
     }
   }
@@ -261,6 +262,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
         const int src = (w != (T)0) ? g + delta : g;
         k = cfma(sc[t], cscale(gs[src], w), k);
       }
+      if (A.rec) reinterpret_cast<C*>(A.rec)[(side == SIDE_X ? sd.off_gx : sd.off_gy) + g] = uc;
       combine((side == SIDE_X ? sd.off_gx : sd.off_gy) + g, uc, k);
     }
   }
@@ -450,6 +452,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage_m1(const StageArgs A, const 
           if (has_sep) v = cadd(v, cmul(gx[r], gy[c]));
           kv = cfma(cS[j], cscale(v, wSx[j * M + kx] * wSy[j * M + ly]), kv);
         }
+      if (A.rec) reinterpret_cast<C*>(A.rec)[s.off_r + p] = uc;
       combine(s.off_r + p, uc, kv);
     }
   }
@@ -469,6 +472,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage_m1(const StageArgs A, const 
         for (int j = 0; j < MY; ++j)
           if (j < nY) kv = cfma(cY[j], cscale(gs[min(max(g + shY[j], 0), M - 1)], wY[j * M + g]), kv);
       }
+      if (A.rec) reinterpret_cast<C*>(A.rec)[(isx ? s.off_gx : s.off_gy) + g] = gs[g];
       combine((isx ? s.off_gx : s.off_gy) + g, gs[g], kv);
     }
   }
@@ -482,6 +486,262 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage_m1(const StageArgs A, const 
         *A.counter = *(volatile long long*)A.counter + 1;
         __threadfence();
       }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Pipelined single-mode stage (the HBM-streaming form of the fused stage).
+//
+// A persistent CTA processes its systems in order; thread 0 keeps n_slots - 1 systems in
+// flight by issuing 1-D bulk copies (TMA, cp.async.bulk with an mbarrier transaction count)
+// of each system's parameter block, stage coefficients, stage input, state, stage sum and
+// compensation into a shared-memory slot, while all threads compute the current system from
+// shared memory and stream the results to HBM with coalesced stores.  Every wait on an
+// mbarrier is bounded; a wait that gives up sets an error word and the CTA returns.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+#define BQ_PIPE_THREADS 256
+#define BQ_WAIT_LIMIT (1 << 22)
+
+// Stage coefficients of every system (X, Y, S terms in program order, C at slot 15).
+template <typename T>
+__global__ void k_coef_m1(const CoefArgs A) {
+  using C = typename C2T<T>::type;
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= A.n_sys * BQ_PIPE_COEF) return;
+  const int si = gi / BQ_PIPE_COEF, q = gi - si * BQ_PIPE_COEF;
+  const M1Sys& m = A.m1[si];
+  C* out = reinterpret_cast<C*>(A.coef) + gi;
+  if (q == BQ_PIPE_COEF - 1) {
+    *out = cmk<C>(m.c_re, m.c_im);
+    return;
+  }
+  const int nt = m.nX + m.nY + m.nS;
+  if (q >= nt) { *out = cmk<C>(0.0, 0.0); return; }
+  const int t = q < m.nX ? m.tX[q] : (q < m.nX + m.nY ? m.tY[q - m.nX] : m.tS[q - m.nX - m.nY]);
+  const TermDesc& td = A.terms[m.term_off + t];
+  double2 c = make_double2(td.c_re, td.c_im);
+  if (td.ch >= 0) {
+    const double ts = A.tau_base[0] + (double)(*A.counter) * A.dt;
+    const ChanDesc cd = A.chans[td.ch];
+    const double tau = (cd.kind == 2) ? ts + 0.5 * A.dt : ts + stage_c(A.stage) * A.dt;
+    double2 e = chan_value_t<T>(cd, A.chpar, A.reverse ? A.horizon - tau : tau);
+    if (td.conj) e.y = -e.y;
+    c = make_double2(c.x * e.x - c.y * e.y, c.x * e.y + c.y * e.x);
+  }
+  *out = cmk<C>(c.x, c.y);
+}
+
+template <typename T, int MX, int MY, int MS>
+__global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A) {
+  using C = typename C2T<T>::type;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long full[4];
+  __shared__ PipeRec recs[2][32];
+  __shared__ int s_fail;
+  const int tid = threadIdx.x;
+  const int G = gridDim.x;
+  const int nj = A.n_sys > (int)blockIdx.x ? (A.n_sys - (int)blockIdx.x + G - 1) / G : 0;
+  const int S = A.n_slots;
+  const int stage = A.stage;
+  const size_t cs = sizeof(C);
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+    s_fail = 0;
+  }
+  auto load_batch = [&](int b) {
+    if (tid < 32) {
+      const int j = b * 32 + tid;
+      if (j < nj) recs[b & 1][tid] = A.recs[blockIdx.x + (size_t)j * G];
+    }
+  };
+  load_batch(0);
+  __syncthreads();
+  auto slot_ptr = [&](int s) { return smem_raw + (size_t)s * A.slot_bytes; };
+  // thread 0: issue the bulk copies of system j into slot j % S
+  auto issue = [&](int j) {
+    const PipeRec r = recs[(j >> 5) & 1][j & 31];
+    unsigned char* sl = slot_ptr(j % S);
+    const unsigned blk = (unsigned)(r.blk_elems * cs);
+    unsigned bytes = (unsigned)r.param_bytes + (unsigned)(BQ_PIPE_COEF * cs) + blk;
+    if (stage > 1) bytes += 2 * blk;
+    if (stage == 4) bytes += blk;
+    fence_proxy_async();
+    unsigned long long* bar = &full[j % S];
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(sl, A.params + r.param_off, (unsigned)r.param_bytes, bar);
+    bulk_g2s(sl + A.off_coef, reinterpret_cast<const C*>(A.coef) + (size_t)r.sys * BQ_PIPE_COEF,
+             (unsigned)(BQ_PIPE_COEF * cs), bar);
+    bulk_g2s(sl + A.off_u, reinterpret_cast<const C*>(A.u_in) + r.blk_off, blk, bar);
+    if (stage > 1) {
+      bulk_g2s(sl + A.off_y, reinterpret_cast<const C*>(A.y) + r.blk_off, blk, bar);
+      bulk_g2s(sl + A.off_acc, reinterpret_cast<const C*>(A.acc) + r.blk_off, blk, bar);
+    }
+    if (stage == 4) bulk_g2s(sl + A.off_comp, reinterpret_cast<const C*>(A.comp) + r.blk_off, blk, bar);
+  };
+  if (tid == 0)
+    for (int j = 0; j < S - 1 && j < nj; ++j) issue(j);
+
+  C* uout = reinterpret_cast<C*>(A.u_out);
+  C* yg = reinterpret_cast<C*>(A.y);
+  C* accg = reinterpret_cast<C*>(A.acc);
+  C* compg = reinterpret_cast<C*>(A.comp);
+  const T dt = (T)A.dt;
+
+  for (int j = 0; j < nj; ++j) {
+    const int jn = j + S - 1;
+    if (jn < nj && (jn & 31) == 0) {
+      load_batch(jn >> 5);
+      __syncthreads();
+    }
+    if (tid == 0 && jn < nj) issue(jn);
+    // wait for system j (bounded)
+    {
+      bool ok = false;
+      for (int it = 0; it < BQ_WAIT_LIMIT; ++it)
+        if (mbar_try_wait(&full[j % S], (unsigned)((j / S) & 1))) { ok = true; break; }
+      if (!ok) atomicOr(&s_fail, 1);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(A.error, 1u);
+        // give the copies in flight a bounded chance to land before the CTA leaves
+        for (int s = 0; s < S; ++s)
+          for (int it = 0; it < BQ_WAIT_LIMIT; ++it)
+            if (mbar_try_wait(&full[s], (unsigned)((j / S) & 1))) break;
+        return;
+      }
+    }
+    const PipeRec r = recs[(j >> 5) & 1][j & 31];
+    unsigned char* sl = slot_ptr(j % S);
+    const PipeHdr& h = *reinterpret_cast<const PipeHdr*>(sl);
+    const int M = h.M, nX = h.nX, nY = h.nY, nS = h.nS, has_sep = h.has_sep;
+    const C* dx = reinterpret_cast<const C*>(sl + sizeof(PipeHdr));
+    const C* dy = dx + M;
+    const T* wX = reinterpret_cast<const T*>(dy + M);
+    const T* wY = wX + nX * M;
+    const T* wSx = wY + nY * M;
+    const T* wSy = wSx + nS * M;
+    const C* cf = reinterpret_cast<const C*>(sl + A.off_coef);
+    const C* u = reinterpret_cast<const C*>(sl + A.off_u);
+    const C* ys = reinterpret_cast<const C*>(sl + A.off_y);
+    const C* as = reinterpret_cast<const C*>(sl + A.off_acc);
+    const C* cps = reinterpret_cast<const C*>(sl + A.off_comp);
+    C cX[MX], cY[MY], cS[MS];
+    int shX[MX], shY[MY], shSx[MS], shSy[MS];
+#pragma unroll
+    for (int q = 0; q < MX; ++q) { cX[q] = cf[min(q, BQ_PIPE_COEF - 1)]; shX[q] = h.sX[q]; }
+#pragma unroll
+    for (int q = 0; q < MY; ++q) { cY[q] = cf[min(nX + q, BQ_PIPE_COEF - 1)]; shY[q] = h.sY[q]; }
+#pragma unroll
+    for (int q = 0; q < MS; ++q) {
+      cS[q] = cf[min(nX + nY + q, BQ_PIPE_COEF - 1)];
+      shSx[q] = h.sSx[q];
+      shSy[q] = h.sSy[q];
+    }
+    const C Cc = cf[BQ_PIPE_COEF - 1];
+    const C* ur = u + r.r_off;
+    const C* ugx = u + r.gx_off;
+    const C* ugy = u + r.gy_off;
+    const int nr = h.has_r ? M * M : 0;
+    const int ntot = h.ntot;
+    const float invM = 1.0f / (float)M;
+    for (int e = tid; e < ntot; e += blockDim.x) {
+      int pos;
+      C uc, kv;
+      if (e < nr) {
+        const int kx = (int)(((float)e + 0.5f) * invM);
+        const int ly = e - kx * M;
+        pos = r.r_off + e;
+        uc = ur[e];
+        kv = cmul(cadd(dx[kx], dy[ly]), uc);
+#pragma unroll
+        for (int q = 0; q < MX; ++q)
+          if (q < nX) kv = cfma(cX[q], cscale(ur[min(max(kx + shX[q], 0), M - 1) * M + ly], wX[q * M + kx]), kv);
+#pragma unroll
+        for (int q = 0; q < MY; ++q)
+          if (q < nY) kv = cfma(cY[q], cscale(ur[kx * M + min(max(ly + shY[q], 0), M - 1)], wY[q * M + ly]), kv);
+#pragma unroll
+        for (int q = 0; q < MS; ++q)
+          if (q < nS) {
+            const int rr = min(max(kx + shSx[q], 0), M - 1);
+            const int cc = min(max(ly + shSy[q], 0), M - 1);
+            C v = ur[rr * M + cc];
+            if (has_sep) v = cadd(v, cmul(ugx[rr], ugy[cc]));
+            kv = cfma(cS[q], cscale(v, wSx[q * M + kx] * wSy[q * M + ly]), kv);
+          }
+      } else {
+        const bool isx = e < nr + M;
+        const int g = isx ? e - nr : e - nr - M;
+        const C* gs = isx ? ugx : ugy;
+        pos = (isx ? r.gx_off : r.gy_off) + g;
+        uc = gs[g];
+        kv = cmul(isx ? cadd(dx[g], Cc) : cadd(dy[g], cmk<C>(-(double)Cc.x, -(double)Cc.y)), uc);
+        if (isx) {
+#pragma unroll
+          for (int q = 0; q < MX; ++q)
+            if (q < nX) kv = cfma(cX[q], cscale(gs[min(max(g + shX[q], 0), M - 1)], wX[q * M + g]), kv);
+        } else {
+#pragma unroll
+          for (int q = 0; q < MY; ++q)
+            if (q < nY) kv = cfma(cY[q], cscale(gs[min(max(g + shY[q], 0), M - 1)], wY[q * M + g]), kv);
+        }
+      }
+      const int64_t gi = (int64_t)r.blk_off + pos;
+      if (stage == 1) {
+        uout[gi] = caxpy(dt * (T)0.5, kv, uc);
+        accg[gi] = kv;
+      } else if (stage == 4) {
+        const C yv = ys[pos];
+        const C sm = cadd(as[pos], kv);
+        const C cv = cps[pos];
+        C d, t, c2;
+        d.x = dt * (T)(1.0 / 6.0) * sm.x - cv.x;
+        d.y = dt * (T)(1.0 / 6.0) * sm.y - cv.y;
+        t.x = yv.x + d.x;
+        t.y = yv.y + d.y;
+        c2.x = (t.x - yv.x) - d.x;
+        c2.y = (t.y - yv.y) - d.y;
+        yg[gi] = t;
+        compg[gi] = c2;
+      } else {
+        const C yv = ys[pos];
+        uout[gi] = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, yv);
+        accg[gi] = caxpy((T)2, kv, as[pos]);
+      }
+    }
+    __syncthreads();
+  }
+  if (stage == 4 && tid == 0) {
+    __threadfence();
+    const unsigned int t = atomicAdd(A.ticket, 1u);
+    if (t == gridDim.x - 1) {
+      *A.ticket = 0u;
+      *A.counter = *(volatile long long*)A.counter + 1;
+      __threadfence();
     }
   }
 }
@@ -688,6 +948,360 @@ __global__ void __launch_bounds__(BLK, 2) k_solve_m1(const SolveArgs A) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Adjoint (backward-in-time) RK4 stage: the exact discrete adjoint of the stage kernels.
+//
+// For stage i of a step with cotangent lam of the state after the step:
+//   q_i = J_i^T b_i, lacc += q_i (lacc = lam + q_4 at stage 4),
+//   b_{i-1} = dt beta_{i-1} lam + c_i dt q_i  (beta = 1/6, 1/3, 1/3; c = 1/2, 1/2, 1 for i = 2, 3, 4),
+//   dl/dtheta += Re <b_i, df/dtheta(u_i)> (bilinear pairing, the system is complex linear).
+// J^T of a stencil term  out[p] += c W(p) u[p + delta]  is the gather
+//   q[p] += c W(p - delta) b[p - delta]  (source point inside the grid),
+// and <b, T_t u> = <T_t^T b, u>, so the parameter sums need u only at the point itself.
+// The transposed separable source uses the reductions of k_adj_src.
+// ---------------------------------------------------------------------------------------
+#define BQ_MAX_GT 16
+
+__device__ __forceinline__ int pwc_segment(const ChanDesc& cd, const double* par, double t) {
+  const double* p = par + cd.par_off;
+  const int n_seg = (cd.n_par - 2) / 2;
+  const double x = floor((t - p[0]) / p[1]);
+  if (!(x >= 0.0) || x >= (double)n_seg) return -1;
+  return (int)x;
+}
+
+template <typename T, int NM>
+__global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
+  using C = typename C2T<T>::type;
+  constexpr int ND = 2 * NM;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* bw = reinterpret_cast<C*>(smem_raw);
+  __shared__ SysDesc sd;
+  __shared__ WorkItem wi;
+  __shared__ TermDesc st[BQ_MAX_TERMS];
+  __shared__ C sc[BQ_MAX_TERMS];
+  __shared__ int gidx[BQ_MAX_TERMS];
+  __shared__ int s_ngt, s_nS;
+  __shared__ int sidx[BQ_MAX_TERMS];       // ordinal of an S term
+  __shared__ double2 red[BQ_MAX_GT + 1][BQ_BLOCK / 32];
+
+  const int tid = threadIdx.x;
+  const int stage = A.stage;
+  if (tid == 0) {
+    wi = A.work[blockIdx.x];
+    sd = A.sys[wi.sys];
+  }
+  __syncthreads();
+  const int nt = sd.n_terms;
+  for (int t = tid; t < nt; t += blockDim.x) {
+    st[t] = A.terms[sd.term_off + t];
+    const double2 c = term_coef(st[t], A.chans, A.chpar, A.tau_step, A.dt, stage, A.horizon, A.reverse);
+    sc[t] = cmk<C>(c.x, c.y);
+  }
+  if (tid == 0) {
+    int g = 0, s = 0;
+    for (int t = 0; t < nt; ++t) {
+      const TermDesc& td = A.terms[sd.term_off + t];
+      gidx[t] = (td.gslot_param >= 0 || td.gslot_pwc >= 0) && g < BQ_MAX_GT ? g++ : -1;
+      sidx[t] = td.side == SIDE_S ? s++ : -1;
+    }
+    s_ngt = g;
+    s_nS = s;
+  }
+  const T dt = (T)A.dt;
+  const T bscale = stage == 4 ? dt * (T)(1.0 / 6.0) : (T)1;
+  const C* bsrc = reinterpret_cast<const C*>(stage == 4 ? A.lam : A.b_in);
+  const int wn = wi.win_hi - wi.win_lo;
+  if (sd.has_r)
+    for (int i = tid; i < wn; i += blockDim.x) bw[i] = cscale(bsrc[sd.off_r + wi.win_lo + i], bscale);
+  C* bgx = bw + wn;
+  C* bgy = bgx + sd.n_g;
+  C* vw = bgy + sd.n_g;  // [nS][2][n_g] source reductions of this system
+  if (sd.has_sep && wi.do_sep) {
+    for (int i = tid; i < sd.n_g; i += blockDim.x) {
+      bgx[i] = cscale(bsrc[sd.off_gx + i], bscale);
+      bgy[i] = cscale(bsrc[sd.off_gy + i], bscale);
+    }
+  }
+  __syncthreads();
+  if (sd.has_sep && wi.do_sep && sd.has_r) {
+    const C* srcr = reinterpret_cast<const C*>(A.srcred) + (int64_t)wi.sys * A.srcred_stride;
+    for (int i = tid; i < 2 * s_nS * sd.n_g; i += blockDim.x) vw[i] = srcr[i];
+  }
+  __syncthreads();
+
+  const T* W = reinterpret_cast<const T*>(A.wtab);
+  const C* D = reinterpret_cast<const C*>(A.diag) + sd.diag_off;
+  const C* U = reinterpret_cast<const C*>(A.u);
+  const C* LAM = reinterpret_cast<const C*>(A.lam);
+  C* LACC = reinterpret_cast<C*>(A.lacc);
+  C* BOUT = reinterpret_cast<C*>(A.b_out);
+  int Md[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) Md[d] = sd.M[d % NM];
+  int doff[ND];
+  {
+    int o = 0;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) { doff[d] = o; o += Md[d]; }
+  }
+  // b_{i-1} = dt beta lam + cq dt q
+  const T beta = stage == 4 ? (T)(1.0 / 3.0) : (stage == 3 ? (T)(1.0 / 3.0) : (T)(1.0 / 6.0));
+  const T cq = stage == 4 ? dt : dt * (T)0.5;
+  double2 gacc[BQ_MAX_GT];
+  double2 dcacc = make_double2(0.0, 0.0);
+#pragma unroll
+  for (int g = 0; g < BQ_MAX_GT; ++g) gacc[g] = make_double2(0.0, 0.0);
+  const int ngt = s_ngt;
+
+  auto finish = [&](int64_t gi, C q) {
+    LACC[gi] = stage == 4 ? cadd(LAM[gi], q) : cadd(LACC[gi], q);
+    if (stage > 1) BOUT[gi] = caxpy(cq, q, cscale(LAM[gi], dt * beta));
+  };
+  auto addg = [&](int t, C ub, C bv, T w) {
+    // accumulate u * (W b_src) for gradient term t
+    const int g = gidx[t];
+    if (g < 0) return;
+    const C v = cmul(ub, cscale(bv, w));
+#pragma unroll
+    for (int q = 0; q < BQ_MAX_GT; ++q)
+      if (q == g) { gacc[q].x += (double)v.x; gacc[q].y += (double)v.y; }
+  };
+
+  if (sd.has_r) {
+    const int ng = sd.n_g;
+    for (int p = wi.start + tid; p < wi.start + wi.len; p += blockDim.x) {
+      int idx[ND];
+      const int kx = p / ng;
+      const int ly = p - kx * ng;
+      {
+        int r = kx;
+#pragma unroll
+        for (int d = NM - 1; d >= 0; --d) { idx[d] = r % Md[d]; r /= Md[d]; }
+        r = ly;
+#pragma unroll
+        for (int d = ND - 1; d >= NM; --d) { idx[d] = r % Md[d]; r /= Md[d]; }
+      }
+      C dg = D[doff[0] + idx[0]];
+#pragma unroll
+      for (int d = 1; d < ND; ++d) dg = cadd(dg, D[doff[d] + idx[d]]);
+      C q = cmul(dg, bw[p - wi.win_lo]);
+      const C up = U[sd.off_r + p];
+      for (int t = 0; t < nt; ++t) {
+        const TermDesc& td = st[t];
+        T w = (T)1;
+        bool ok = true;
+        for (int i = 0; i < td.n_act; ++i) {
+          const int d = td.dim[i];
+          const int s = idx[d] - td.sh[i];
+          ok = ok && (s >= 0) && (s < Md[d]);
+          w *= ok ? W[td.wtab[i] + (ok ? s : 0)] : (T)0;
+        }
+        if (!ok) w = (T)0;
+        const int src = (w != (T)0) ? p - td.deltaR : p;
+        const C bv = bw[src - wi.win_lo];
+        q = cfma(sc[t], cscale(bv, w), q);
+        if (ngt) addg(t, up, bv, w);
+      }
+      finish(sd.off_r + p, q);
+    }
+  }
+  if (sd.has_sep && wi.do_sep) {
+    const int ng = sd.n_g;
+    const C Cc = cmk<C>(sd.c_re, sd.c_im);
+    for (int i = tid; i < 2 * ng; i += blockDim.x) {
+      const int side = i < ng ? SIDE_X : SIDE_Y;
+      const int g = side == SIDE_X ? i : i - ng;
+      const int d0 = side == SIDE_X ? 0 : NM;
+      int idx[ND];
+      {
+        int r = g;
+#pragma unroll
+        for (int d = NM - 1; d >= 0; --d) { idx[d0 + d] = r % Md[d]; r /= Md[d]; }
+      }
+      const C* bs = side == SIDE_X ? bgx : bgy;
+      C dg = side == SIDE_X ? Cc : cmk<C>(-sd.c_re, -sd.c_im);
+#pragma unroll
+      for (int d = 0; d < NM; ++d) dg = cadd(dg, D[doff[d0 + d] + idx[d0 + d]]);
+      C q = cmul(dg, bs[g]);
+      const C up = U[(side == SIDE_X ? sd.off_gx : sd.off_gy) + g];
+      {
+        const C v = cmul(up, bs[g]);
+        if (side == SIDE_X) { dcacc.x += (double)v.x; dcacc.y += (double)v.y; }
+        else { dcacc.x -= (double)v.x; dcacc.y -= (double)v.y; }
+      }
+      for (int t = 0; t < nt; ++t) {
+        const TermDesc& td = st[t];
+        const bool own = td.side == side;
+        const bool src_term = td.side == SIDE_S && sd.has_r;
+        if (!own && !src_term) continue;
+        // weight over the active dims of this side
+        T w = (T)1;
+        bool ok = true;
+        for (int j = 0; j < td.n_act; ++j) {
+          const int d = td.dim[j];
+          if ((d < NM) != (side == SIDE_X)) continue;
+          const int s = idx[d] - td.sh[j];
+          ok = ok && (s >= 0) && (s < Md[d]);
+          w *= ok ? W[td.wtab[j] + (ok ? s : 0)] : (T)0;
+        }
+        if (!ok) w = (T)0;
+        const int delta = side == SIDE_X ? td.deltaGx : td.deltaGy;
+        const int src = (w != (T)0) ? g - delta : g;
+        if (own) {
+          const C bv = bs[src];
+          q = cfma(sc[t], cscale(bv, w), q);
+          if (ngt) addg(t, up, bv, w);
+        } else {
+          // d/dG_x of  c (Wx G_x[.+sx]) (Wy G_y[.+sy]) paired with b_R: c Wx(j-sx) v_t[j-sx]
+          const C* red_t = vw + (sidx[t] * 2 + (side == SIDE_X ? 0 : 1)) * ng;
+          q = cfma(sc[t], cscale(red_t[src], w), q);
+        }
+      }
+      finish((side == SIDE_X ? sd.off_gx : sd.off_gy) + g, q);
+    }
+  }
+
+  // ---- gradient reductions: warp shuffles, then one atomic per term per CTA ----------
+  if (ngt > 0 || (sd.has_sep && wi.do_sep && sd.n_params > 0)) {
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int g = 0; g <= BQ_MAX_GT; ++g) {
+      double2 v = g < BQ_MAX_GT ? gacc[g] : dcacc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+      }
+      if (lane == 0) red[g][warp] = v;
+    }
+    __syncthreads();
+    if (tid < nt) {
+      const int t = tid;
+      const int g = gidx[t];
+      if (g >= 0) {
+        double2 a = make_double2(0.0, 0.0);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a.x += red[g][w].x; a.y += red[g][w].y; }
+        const TermDesc& td = st[t];
+        double2 e = make_double2(1.0, 0.0);
+        double t_phys = 0.0;
+        if (td.ch >= 0) {
+          const ChanDesc cd = A.chans[td.ch];
+          const double tau = (cd.kind == 2) ? A.tau_step + 0.5 * A.dt : A.tau_step + stage_c(stage) * A.dt;
+          t_phys = A.reverse ? A.horizon - tau : tau;
+          e = chan_value(cd, A.chpar, t_phys);
+          if (td.conj) e.y = -e.y;
+        }
+        if (td.gslot_param >= 0) {
+          // d coef / d theta = cb * channel
+          const double cr = td.cb_re * e.x - td.cb_im * e.y, ci = td.cb_re * e.y + td.cb_im * e.x;
+          atomicAdd(A.grad + td.gslot_param, cr * a.x - ci * a.y);
+        }
+        if (td.gslot_pwc >= 0) {
+          const ChanDesc cd = A.chans[td.ch];
+          const int sg = pwc_segment(cd, A.chpar, t_phys);
+          if (sg >= 0) {
+            // d/dRe: c; d/dIm: +i c (channel) or -i c (conjugate channel)
+            const double re = td.c_re * a.x - td.c_im * a.y;
+            const double im = td.c_re * a.y + td.c_im * a.x;
+            atomicAdd(A.grad + td.gslot_pwc + 2 * sg, re);
+            atomicAdd(A.grad + td.gslot_pwc + 2 * sg + 1, td.conj ? im : -im);
+          }
+        }
+      }
+    }
+    if (sd.has_sep && wi.do_sep && tid < sd.n_params) {
+      double2 a = make_double2(0.0, 0.0);
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a.x += red[BQ_MAX_GT][w].x; a.y += red[BQ_MAX_GT][w].y; }
+      const double2 dcv = A.dc[sd.dc_off + tid];
+      atomicAdd(A.grad + sd.grad_off + tid, dcv.x * a.x - dcv.y * a.y);
+    }
+  }
+}
+
+// Transposed separable source: for every system and sandwich term t
+//   v_t[kx] = sum_ly b_R[kx, ly] Wy_t(ly) G_y[ly + sy],   w_t[ly] = sum_kx b_R[kx, ly] Wx_t(kx) G_x[kx + sx]
+// (G_x, G_y of the recorded stage input; b_R = dt/6 lam at stage 4).  grid = (systems, max S terms, 2).
+template <typename T, int NM>
+__global__ void __launch_bounds__(BQ_BLOCK) k_adj_src(const AdjArgs A) {
+  using C = typename C2T<T>::type;
+  const SysDesc& sd = A.sys[blockIdx.x];
+  if (!sd.has_sep || !sd.has_r) return;
+  // find the blockIdx.y-th sandwich term of the system
+  int t = -1, s = 0;
+  for (int q = 0; q < sd.n_terms; ++q)
+    if (A.terms[sd.term_off + q].side == SIDE_S) {
+      if (s == (int)blockIdx.y) { t = q; break; }
+      ++s;
+    }
+  if (t < 0) return;
+  const TermDesc td = A.terms[sd.term_off + t];
+  const int dirx = blockIdx.z == 0;  // 0: v_t over kx (sum over ly), 1: w_t over ly (sum over kx)
+  const int ng = sd.n_g;
+  const T dt = (T)A.dt;
+  const T bscale = A.stage == 4 ? dt * (T)(1.0 / 6.0) : (T)1;
+  const C* bsrc = reinterpret_cast<const C*>(A.stage == 4 ? A.lam : A.b_in) + sd.off_r;
+  const C* U = reinterpret_cast<const C*>(A.u);
+  const C* other = U + (dirx ? sd.off_gy : sd.off_gx);
+  const T* W = reinterpret_cast<const T*>(A.wtab);
+  const int delta = dirx ? td.deltaGy : td.deltaGx;
+  C* out = reinterpret_cast<C*>(const_cast<void*>(A.srcred)) + (int64_t)blockIdx.x * A.srcred_stride +
+           (s * 2 + (dirx ? 0 : 1)) * ng;
+  for (int i = threadIdx.x; i < ng; i += blockDim.x) {
+    C acc = cmk<C>(0.0, 0.0);
+    for (int j = 0; j < ng; ++j) {
+      // j runs over the summed index (ly for v_t, kx for w_t); weight of the other side's part
+      int rem = j;
+      int id[NM];
+#pragma unroll
+      for (int d = NM - 1; d >= 0; --d) { id[d] = rem % sd.M[d]; rem /= sd.M[d]; }
+      T w = (T)1;
+      for (int a = 0; a < td.n_act; ++a) {
+        const int d = td.dim[a];
+        const bool isx = d < NM;
+        if (isx == (bool)dirx) continue;  // only the summed side's dims
+        w *= W[td.wtab[a] + id[isx ? d : d - NM]];
+      }
+      if (w == (T)0) continue;
+      const C b = dirx ? bsrc[(int64_t)i * ng + j] : bsrc[(int64_t)j * ng + i];
+      acc = cfma(cscale(b, w), other[j + delta], acc);
+    }
+    out[i] = cscale(acc, bscale);
+  }
+}
+
+// Cotangent of the final state for l = Re sum_b Tr(rho0_b A_b): one thread per system.
+template <typename T>
+__global__ void k_adj_seed(const SysDesc* __restrict__ sys, const EvalGroup* __restrict__ groups,
+                           const EvalEntry* __restrict__ entries, const void* ystate, void* lam, int n_groups) {
+  using C = typename C2T<T>::type;
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= n_groups) return;
+  const EvalGroup g = groups[gi];
+  const C* y = reinterpret_cast<const C*>(ystate);
+  C* L = reinterpret_cast<C*>(lam);
+  for (int s = 0; s < g.n_sys; ++s) {
+    const SysDesc& sd = sys[g.sys_off + s];
+    for (int e = 0; e < g.n_e; ++e) {
+      const EvalEntry en = entries[g.e_off + e];
+      const double fr = sd.w_re * en.f_re - sd.w_im * en.f_im;
+      const double fi = sd.w_re * en.f_im + sd.w_im * en.f_re;
+      const C f = cmk<C>(fr, fi);
+      if (sd.has_r) {
+        C& r = L[sd.off_r + (int64_t)en.kx * sd.n_g + en.ly];
+        r = cadd(r, f);
+      }
+      if (sd.has_sep) {
+        C& ax = L[sd.off_gx + en.kx];
+        C& ay = L[sd.off_gy + en.ly];
+        const C gx = y[sd.off_gx + en.kx];
+        const C gy = y[sd.off_gy + en.ly];
+        ax = cfma(f, gy, ax);
+        ay = cfma(f, gx, ay);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Observables: one warp per evaluation group, lanes over (initial condition, entry) pairs.
 // ---------------------------------------------------------------------------------------
 template <typename T>
@@ -876,6 +1490,101 @@ cudaError_t launch_solve_m1(const SolveArgs& a, int dtype, int capacity_class, i
   if (capacity_class != 0) return cudaErrorInvalidValue;
   return dtype == 0 ? launch_solve_t<double, 448, 4>(a, smem_bytes, s, grid_out)
                     : launch_solve_t<float, 256, 7>(a, smem_bytes, s, grid_out);
+}
+
+template <typename T, int NM>
+static cudaError_t launch_adj_t(const AdjArgs& a, int n_work, int smem_bytes, int n_sys, int max_s, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_adj_stage<T, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         BQ_MAX_DYN_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  if (max_s > 0) {
+    k_adj_src<T, NM><<<dim3(n_sys, max_s, 2), BQ_BLOCK, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_adj_stage<T, NM><<<n_work, BQ_BLOCK, smem_bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const AdjArgs& a, int dtype, int nm, int n_work, int smem_bytes, int n_sys, int max_s,
+                           cudaStream_t s) {
+  if (dtype == 0) {
+    switch (nm) {
+      case 1: return launch_adj_t<double, 1>(a, n_work, smem_bytes, n_sys, max_s, s);
+      case 2: return launch_adj_t<double, 2>(a, n_work, smem_bytes, n_sys, max_s, s);
+      case 3: return launch_adj_t<double, 3>(a, n_work, smem_bytes, n_sys, max_s, s);
+    }
+  } else {
+    switch (nm) {
+      case 1: return launch_adj_t<float, 1>(a, n_work, smem_bytes, n_sys, max_s, s);
+      case 2: return launch_adj_t<float, 2>(a, n_work, smem_bytes, n_sys, max_s, s);
+      case 3: return launch_adj_t<float, 3>(a, n_work, smem_bytes, n_sys, max_s, s);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adj_seed(const SysDesc* sys, const EvalGroup* groups, const EvalEntry* entries, const void* y,
+                            void* lam, int n_groups, int dtype, cudaStream_t s) {
+  if (n_groups <= 0) return cudaSuccess;
+  const int blocks = (n_groups + 127) / 128;
+  if (dtype == 0)
+    k_adj_seed<double><<<blocks, 128, 0, s>>>(sys, groups, entries, y, lam, n_groups);
+  else
+    k_adj_seed<float><<<blocks, 128, 0, s>>>(sys, groups, entries, y, lam, n_groups);
+  return cudaGetLastError();
+}
+
+static cudaError_t pipe_attrs() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_stage_pipe<double, 2, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, BQ_MAX_DYN_SMEM)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_stage_pipe<double, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, BQ_MAX_DYN_SMEM)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_stage_pipe<float, 2, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, BQ_MAX_DYN_SMEM)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_stage_pipe<float, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, BQ_MAX_DYN_SMEM)) != cudaSuccess) return e;
+  done = true;
+  return cudaSuccess;
+}
+
+template <typename T, int MXYS>
+static cudaError_t launch_pipe_t(const PipeArgs& a, const CoefArgs& c, int grid, int smem_bytes, cudaStream_t s) {
+  auto kern = k_stage_pipe<T, MXYS, MXYS, MXYS>;
+  cudaError_t ea = pipe_attrs();
+  if (ea != cudaSuccess) return ea;
+  const int nc = c.n_sys * BQ_PIPE_COEF;
+  k_coef_m1<T><<<(nc + 255) / 256, 256, 0, s>>>(c);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  kern<<<grid, BQ_PIPE_THREADS, smem_bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage_pipe(const PipeArgs& a, const CoefArgs& c, int variant, int dtype, int grid, int smem_bytes,
+                              cudaStream_t s) {
+  if (dtype == 0)
+    return variant == 0 ? launch_pipe_t<double, 2>(a, c, grid, smem_bytes, s)
+                        : launch_pipe_t<double, BQ_M1_MAXT>(a, c, grid, smem_bytes, s);
+  return variant == 0 ? launch_pipe_t<float, 2>(a, c, grid, smem_bytes, s)
+                      : launch_pipe_t<float, BQ_M1_MAXT>(a, c, grid, smem_bytes, s);
+}
+
+cudaError_t pipe_blocks_per_sm(int dtype, int variant, int smem_bytes, int* out) {
+  cudaError_t ea = pipe_attrs();
+  if (ea != cudaSuccess) return ea;
+  if (dtype == 0)
+    return variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_stage_pipe<double, 2, 2, 2>,
+                                                                         BQ_PIPE_THREADS, smem_bytes)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                              out, k_stage_pipe<double, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>, BQ_PIPE_THREADS, smem_bytes);
+  return variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_stage_pipe<float, 2, 2, 2>,
+                                                                       BQ_PIPE_THREADS, smem_bytes)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            out, k_stage_pipe<float, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>, BQ_PIPE_THREADS, smem_bytes);
 }
 
 cudaError_t launch_stage(const StageArgs& a, int dtype, int nm, int n_work, int smem_bytes, cudaStream_t s) {

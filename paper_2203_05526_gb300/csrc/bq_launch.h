@@ -24,6 +24,15 @@ cudaError_t launch_stage_m1(const StageArgs& a, const M1Sys* m1, int variant, in
 // Batched persistent solve; capacity_class 0 = systems of up to 1792 points.
 cudaError_t launch_solve_m1(const SolveArgs& a, int dtype, int capacity_class, int smem_bytes, cudaStream_t s,
                             int* grid_out);
+// Adjoint RK4 stage (transposed-source pre-pass when max_s > 0, then the stage kernel).
+cudaError_t launch_adjoint(const AdjArgs& a, int dtype, int nm, int n_work, int smem_bytes, int n_sys, int max_s,
+                           cudaStream_t s);
+cudaError_t launch_adj_seed(const SysDesc* sys, const EvalGroup* groups, const EvalEntry* entries, const void* y,
+                            void* lam, int n_groups, int dtype, cudaStream_t s);
+// Pipelined single-mode stage: per-stage coefficient kernel + persistent bulk-copy pipeline.
+cudaError_t launch_stage_pipe(const PipeArgs& a, const CoefArgs& c, int variant, int dtype, int grid, int smem_bytes,
+                              cudaStream_t s);
+cudaError_t pipe_blocks_per_sm(int dtype, int variant, int smem_bytes, int* out);
 cudaError_t launch_eval(const SysDesc* sys, const EvalGroup* groups, const EvalEntry* entries, const void* y,
                         double2* out, int n_groups, int dtype, int small, cudaStream_t s);
 // Device address of the fixed RK4 scratch on the current device (looked up once per device).

@@ -1,0 +1,151 @@
+"""Adjoint gradients on the GPU (bq_grad and the torch.autograd.Function over it) against
+the oracle's discrete adjoint (oracle.grad), central finite differences and each other."""
+
+import copy
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import grad as ograd
+from workloads import configs
+from workloads.spec import Channel
+
+from parity import gpu_state
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "control_golden.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    from paper_2203_05526_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _small_control(n_modes=1, N=5, n_seg=4, steps_per_seg=6, seed=3):
+    rng = np.random.default_rng(seed)
+    if n_modes == 1:
+        p = configs.kerr_driven(N=N, dt=0.01, T=0.24, n_th=0.1)
+        p.h_terms = (configs.kerr_mode_terms(1, 0, 0.0, 0.0, delta_param=0, kerr_param=1)
+                     + configs.gauss_drive_terms(1, 0, 0))
+        p.params = [0.3, -1.1]
+        p.measured = {((1,), (1,)): 1.0, ((0,), (1,)): 0.3 + 0.2j, ((1,), (0,)): 0.3 - 0.2j}
+    else:
+        p = configs.two_mode_control(n_seg=n_seg, T=0.24, steps_per_seg=steps_per_seg, N=N)
+    seg_len = p.T / n_seg
+    vals = []
+    for _ in range(n_seg):
+        vals += [float(rng.normal(0, 0.5)), float(rng.normal(0, 0.5))]
+    p.channels = [Channel("pwc", (0.0, seg_len, *vals))]
+    p.dt = seg_len / steps_per_seg
+    p.rho0 = {((0,) * n_modes, (0,) * n_modes): 0.7,
+              ((1,) + (0,) * (n_modes - 1), (1,) + (0,) * (n_modes - 1)): 0.3}
+    return p
+
+
+def _flat_oracle(gt, gp):
+    return np.concatenate([gt, gp[0].reshape(-1)])
+
+
+@pytest.mark.parametrize("n_modes,N,ck", [(1, 5, 7), (2, 3, 5), (2, 4, 24)])
+def test_grad_matches_oracle_adjoint(n_modes, N, ck):
+    p = _small_control(n_modes=n_modes, N=N)
+    loss_o, gt, gp = ograd.loss_and_grad(p, checkpoint_every=ck)
+    st = gpu_state(p)
+    loss, g = st.grad(p.dt, p.n_steps, ck)
+    ref = _flat_oracle(gt, gp)
+    assert abs(loss[0] - loss_o) <= 1e-12 * max(1.0, abs(loss_o))
+    assert np.max(np.abs(g - ref)) <= 1e-10 * np.max(np.abs(ref)), (g, ref)
+    assert abs(st.time()) == 0.0  # the state is left as it was
+
+
+def test_grad_direct_method_matches_finite_differences():
+    p = _small_control(n_modes=1, N=5)
+    st = gpu_state(p, method="direct")
+    loss, g = st.grad(p.dt, p.n_steps, 6)
+    h = 1e-6
+
+    def loss_at(q):
+        s = gpu_state(q, method="direct")
+        s.step(q.dt, q.n_steps)
+        return s.evaluate()[0].real
+
+    fd = []
+    for i in range(len(p.params)):
+        a, b = copy.deepcopy(p), copy.deepcopy(p)
+        a.params[i] += h
+        b.params[i] -= h
+        fd.append((loss_at(a) - loss_at(b)) / (2 * h))
+    ch = p.channels[0]
+    for j in range(len(ch.params) - 2):
+        a, b = copy.deepcopy(p), copy.deepcopy(p)
+        pa, pb = list(ch.params), list(ch.params)
+        pa[2 + j] += h
+        pb[2 + j] -= h
+        a.channels = [Channel("pwc", tuple(pa))]
+        b.channels = [Channel("pwc", tuple(pb))]
+        fd.append((loss_at(a) - loss_at(b)) / (2 * h))
+    fd = np.array(fd)
+    err = float(np.max(np.abs(g - fd)) / np.max(np.abs(fd)))
+    print("direct adjoint", g.tolist(), "fd", fd.tolist(), "rel err", err)
+    assert err <= 1e-7
+
+
+def test_checkpoint_interval_and_autograd():
+    import torch
+    from paper_2203_05526_gb300.autograd import measured_probability
+    p = _small_control(n_modes=2, N=3)
+    st = gpu_state(p)
+    _, g1 = st.grad(p.dt, p.n_steps, 1)
+    _, g2 = st.grad(p.dt, p.n_steps, 1000)
+    assert np.max(np.abs(g1 - g2)) <= 1e-13 * np.max(np.abs(g1))
+    theta = torch.tensor(p.params, dtype=torch.float64, requires_grad=True)
+    ch = p.channels[0]
+    pwc = torch.tensor(np.array(ch.params[2:]).reshape(-1, 2), dtype=torch.float64, requires_grad=True)
+    l = measured_probability(p, theta, pwc, checkpoint_every=5)
+    l.backward()
+    P = len(p.params)
+    assert np.max(np.abs(theta.grad.numpy() - g1[:P])) <= 1e-13 * np.max(np.abs(g1))
+    assert np.max(np.abs(pwc.grad.numpy().reshape(-1) - g1[P:])) <= 1e-13 * np.max(np.abs(g1))
+
+
+def test_control_problem_full_size():
+    """Two-mode control problem at full size: 64 segments, 20 480 steps, checkpoint every 160
+    steps; against the oracle's adjoint (golden file) and central differences (h = 1e-6) on
+    sampled parameters."""
+    p = configs.two_mode_control()
+    st = gpu_state(p)
+    loss, g = st.grad(p.dt, p.n_steps, 160)
+    assert np.all(np.isfinite(g)) and g.shape == (3 + 128,)
+    if os.path.exists(GOLDEN):
+        gold = json.load(open(GOLDEN))
+        ref = np.concatenate([gold["grad_theta"], np.array(gold["grad_pwc"]).reshape(-1)])
+        assert abs(loss[0] - gold["loss"]) <= 1e-10 * max(1.0, abs(gold["loss"]))
+        assert np.max(np.abs(g - ref)) <= 1e-8 * np.max(np.abs(ref))
+    h = 1e-6
+
+    def loss_at(q):
+        s = gpu_state(q)
+        s.step(q.dt, q.n_steps)
+        return s.evaluate()[0].real
+
+    for i in (0, 2):  # K_1 and g
+        a, b = copy.deepcopy(p), copy.deepcopy(p)
+        a.params[i] += h
+        b.params[i] -= h
+        fd = (loss_at(a) - loss_at(b)) / (2 * h)
+        assert abs(g[i] - fd) <= 1e-5 * max(abs(fd), 1e-3 * np.max(np.abs(g)))
+    ch = p.channels[0]
+    for j in (0, 77):  # Re of segment 0, Im of segment 38
+        a, b = copy.deepcopy(p), copy.deepcopy(p)
+        pa, pb = list(ch.params), list(ch.params)
+        pa[2 + j] += h
+        pb[2 + j] -= h
+        a.channels = [Channel("pwc", tuple(pa))]
+        b.channels = [Channel("pwc", tuple(pb))]
+        fd = (loss_at(a) - loss_at(b)) / (2 * h)
+        assert abs(g[3 + j] - fd) <= 1e-5 * max(abs(fd), 1e-3 * np.max(np.abs(g)))

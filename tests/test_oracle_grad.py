@@ -1,0 +1,72 @@
+"""Pins for O3 (discrete adjoint of the mapped RK4 solve) against central finite
+differences of the oracle's forward solve (oracle.mapping)."""
+
+import copy
+
+import numpy as np
+import pytest
+
+from oracle import grad
+from workloads import configs
+from workloads.spec import Channel, HTerm, Problem
+
+
+def _small_control(n_modes=1, N=5, n_seg=4, steps_per_seg=6, seed=3):
+    rng = np.random.default_rng(seed)
+    if n_modes == 1:
+        p = configs.kerr_driven(N=N, dt=0.01, T=0.24, n_th=0.1)
+        p.h_terms = (configs.kerr_mode_terms(1, 0, 0.0, 0.0, delta_param=0, kerr_param=1)
+                     + configs.gauss_drive_terms(1, 0, 0))
+        p.params = [0.3, -1.1]
+        p.measured = {((1,), (1,)): 1.0, ((0,), (1,)): 0.3 + 0.2j, ((1,), (0,)): 0.3 - 0.2j}
+    else:
+        p = configs.two_mode_control(n_seg=n_seg, T=0.24, steps_per_seg=steps_per_seg, N=N)
+    seg_len = p.T / n_seg
+    vals = []
+    for _ in range(n_seg):
+        vals += [float(rng.normal(0, 0.5)), float(rng.normal(0, 0.5))]
+    p.channels = [Channel("pwc", (0.0, seg_len, *vals))]
+    p.dt = seg_len / steps_per_seg
+    p.rho0 = {((0,) * n_modes, (0,) * n_modes): 0.7, ((1,) + (0,) * (n_modes - 1), (1,) + (0,) * (n_modes - 1)): 0.3}
+    return p
+
+
+def _fd(p, h=1e-6):
+    gt = []
+    for i in range(len(p.params)):
+        a, b = copy.deepcopy(p), copy.deepcopy(p)
+        a.params[i] += h
+        b.params[i] -= h
+        gt.append((grad.loss_only(a) - grad.loss_only(b)) / (2 * h))
+    ch = p.channels[0]
+    n_seg = (len(ch.params) - 2) // 2
+    gp = np.zeros((n_seg, 2))
+    for s in range(n_seg):
+        for r in range(2):
+            a, b = copy.deepcopy(p), copy.deepcopy(p)
+            pa, pb = list(ch.params), list(ch.params)
+            pa[2 + 2 * s + r] += h
+            pb[2 + 2 * s + r] -= h
+            a.channels = [Channel("pwc", tuple(pa))]
+            b.channels = [Channel("pwc", tuple(pb))]
+            gp[s, r] = (grad.loss_only(a) - grad.loss_only(b)) / (2 * h)
+    return np.array(gt), gp
+
+
+@pytest.mark.parametrize("n_modes,N,ck", [(1, 5, 7), (2, 3, 5)])
+def test_adjoint_matches_central_differences(n_modes, N, ck):
+    p = _small_control(n_modes=n_modes, N=N)
+    loss, gt, gp = grad.loss_and_grad(p, checkpoint_every=ck)
+    assert abs(loss - grad.loss_only(p)) < 1e-13
+    ft, fp = _fd(p)
+    scale = max(np.max(np.abs(ft)), np.max(np.abs(fp)))
+    assert np.max(np.abs(gt - ft)) < 1e-7 * scale, (gt, ft)
+    assert np.max(np.abs(gp[0] - fp)) < 1e-7 * scale, (gp[0], fp)
+
+
+def test_checkpoint_interval_does_not_change_gradient():
+    p = _small_control()
+    a = grad.loss_and_grad(p, checkpoint_every=1)
+    b = grad.loss_and_grad(p, checkpoint_every=100)
+    assert np.max(np.abs(a[1] - b[1])) < 1e-14
+    assert np.max(np.abs(a[2][0] - b[2][0])) < 1e-14
