@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-instance full-solve leg")
+    ap.add_argument("--no-grads", action="store_true", help="skip the adjoint-gradient leg")
     ap.add_argument("--only-solve", action="store_true",
                     help="profiling aid: only the persistent batched solve of --instances for --solve-steps steps")
     ap.add_argument("--solve-steps", type=int, default=2000)
@@ -209,6 +210,28 @@ def batched_leg(world: int):
     return out
 
 
+def grads_leg():
+    """Gradient of P(|1,0>) at T = 200 ns for the two-mode control problem (64 complex
+    piecewise-constant drive segments, K_1, K_2, g: 131 real parameters; 20 480 RK4 steps,
+    complex FP64, checkpoint every 160 steps) by the discrete adjoint kernels (bq_grad)."""
+    import numpy as np
+    import torch
+
+    import paper_2203_05526_gb300 as bq
+    from workloads import configs
+    p = configs.two_mode_control()
+    st = bq.State([bq.problem_from_spec(p)], bq.map_opts(dtype="f64", horizon=p.T, dt=p.dt))
+    st.grad(p.dt, 320, 160)  # warm-up (modules, workspace)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss, g = st.grad(p.dt, p.n_steps, 160)
+    el = time.perf_counter() - t0
+    return {"workload": "two_mode_control: 2 modes x M=12, 64 pwc segments, 131 parameters, 20480 RK4 steps, "
+                        "checkpoint every 160, complex FP64",
+            "seconds_per_gradient": el, "grads_per_s": 1.0 / el, "loss": float(loss[0]),
+            "grad_norm": float(np.linalg.norm(g)), "n_params": int(g.size)}
+
+
 def run_reference(args, rank, world):
     """Oracle arm: rank 0 only, bounded samples of the same workload on the host cores."""
     if rank != 0:
@@ -362,6 +385,9 @@ def main():
     batched = None
     if not args.no_batched:
         batched = batched_leg(world)
+    grads = None
+    if not args.no_grads and rank == 0:
+        grads = grads_leg()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -378,7 +404,7 @@ def main():
                            "instances_per_gpu": args.instances, "grid_points_per_gpu": pts,
                            "state_bytes_per_array": nbytes, "l2": "inputs larger than L2 (4 arrays x "
                            f"{nbytes / 1e6:.0f} MB vs 129 MB)", "parallelism": f"replicas x{world}"},
-                "roofline": roof, "e2e": e2e, "batched": batched, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches}
+                "roofline": roof, "e2e": e2e, "batched": batched, "grads": grads, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -594,7 +594,7 @@ struct Layout {
 struct bq_state {
   int B = 0, nm = 0, dtype = 0, method = 0, basis = 0, n_sys = 0, n_work = 0, smem_bytes = 0, use_m1 = 0, m1_variant = 0;
   int trace_small = 0, block_small = 0;
-  int solve_ok = 0, solve_smem = 0, last_solve_grid = 0;
+  int solve_ok = 0, solve_smem = 0, last_solve_grid = 0, solve_mg = 0, solve_mg_smem = 0;
   int use_pipe = 0, pipe_off_coef = 0, pipe_off_u = 0, pipe_off_y = 0, pipe_off_acc = 0, pipe_off_comp = 0;
   int pipe_slot[3] = {0, 0, 0}, pipe_nslots[3] = {2, 2, 2}, pipe_grid[3] = {1, 1, 1};
   int grad_size = 0, adj_smem = 0, srcred_stride = 0, max_s = 0;
@@ -643,6 +643,7 @@ struct Plan {
   std::vector<unsigned char> pparams;
   std::vector<bq::PipeRec> precs;
   int solve_smem = 0;
+  int solve_mg = 0, solve_mg_smem = 0;  // merged-stencil persistent solve
   int adj_smem = 0;  // shared memory of the adjoint stage kernel
   int srcred_stride = 0, max_s = 0;
   std::vector<int> wbase;  // per problem: offset of its weight tables in the pool
@@ -837,6 +838,14 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
           hd.M = M; hd.nX = m.nX; hd.nY = m.nY; hd.nS = m.nS; hd.has_sep = C.has_sep; hd.has_r = C.has_r;
           hd.ntot = (C.has_r ? M * M : 0) + (C.has_sep ? 2 * M : 0);
           for (int q = 0; q < BQ_M1_MAXT; ++q) { hd.sX[q] = m.sX[q]; hd.sY[q] = m.sY[q]; hd.sSx[q] = m.sSx[q]; hd.sSy[q] = m.sSy[q]; }
+          {
+            bool mg = M <= 64 && m.nS <= 2 && (P.m1_variant == 0 || m.nS <= 2);
+            for (int q = 0; q < m.nX; ++q) mg = mg && std::abs(m.sX[q]) <= 1;
+            for (int q = 0; q < m.nY; ++q) mg = mg && std::abs(m.sY[q]) <= 1;
+            for (int q = 0; q < m.nS; ++q) mg = mg && std::abs(m.sSx[q]) <= 1 && std::abs(m.sSy[q]) <= 1;
+            // the merged path stores MS = 2 (variant 0) or BQ_M1_MAXT (variant 1) sandwich vectors
+            hd.merged = mg ? 1 : 0;
+          }
           std::vector<unsigned char> blk(sizeof(hd));
           std::memcpy(blk.data(), &hd, sizeof(hd));
           auto put_c = [&](cplx v) {
@@ -884,15 +893,31 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
         P.pipe_off_y = P.pipe_off_u + blkb;
         P.pipe_off_acc = P.pipe_off_y + blkb;
         P.pipe_off_comp = P.pipe_off_acc + blkb;
-        P.pipe_slot[0] = P.pipe_off_y;          // stage 1: parameters, coefficients, input
-        P.pipe_slot[1] = P.pipe_off_comp;       // stages 2-3: + state, stage sum
-        P.pipe_slot[2] = P.pipe_off_comp + blkb;  // stage 4: + compensation
+        // a slot holds the parameter block, the stage coefficients and the stage input; the
+        // state, stage sum and compensation are streamed with coalesced loads
+        P.pipe_slot[0] = P.pipe_slot[1] = P.pipe_slot[2] = P.pipe_off_y;
         P.use_pipe = 2 * (size_t)P.pipe_slot[2] <= 200 * 1024 ? 1 : 0;
       }
       if (solve_ok && solve_max <= 160 * 1024) {
         std::stable_sort(sz.begin(), sz.end());
         for (auto& e : sz) P.order.push_back(e.second);
         P.solve_smem = (int)solve_max;
+        // merged-stencil persistent solve: shifts in {-1, 0, 1}, <= 2 sandwich terms,
+        // column strips of at most 8 rows with 256 threads (M <= 45)
+        bool mg = true;
+        size_t mg_max = 0;
+        for (int i = 0; i < (int)P.m1.size() && mg; ++i) {
+          const bq::M1Sys& m = P.m1[i];
+          const int M = m.M;
+          const int nb = std::min(256 / M, M);
+          mg = mg && M >= 1 && nb >= 1 && (M + nb - 1) / nb <= 8 && m.nS <= 2;
+          for (int q = 0; q < m.nX; ++q) mg = mg && std::abs(m.sX[q]) <= 1;
+          for (int q = 0; q < m.nY; ++q) mg = mg && std::abs(m.sY[q]) <= 1;
+          for (int q = 0; q < m.nS; ++q) mg = mg && std::abs(m.sSx[q]) <= 1 && std::abs(m.sSy[q]) <= 1;
+          const int ntot = (m.has_r ? M * M : 0) + (m.has_sep ? 2 * M : 0);
+          mg_max = std::max(mg_max, (size_t)(2 * ntot + 2 * M + 2 * 8 * M) * cs + (size_t)(m.nX + m.nY + 2 * m.nS) * M * rs);
+        }
+        if (mg && mg_max <= 160 * 1024) { P.solve_mg = 1; P.solve_mg_smem = (int)mg_max; }
       }
     }
   }
@@ -915,8 +940,15 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
       smem_max = std::max(smem_max, sd.n_r + sep);
       continue;
     }
-    const int tl = budget - sep - sd.halo_lo - sd.halo_hi;
-    if (tl < 256) return fail(BQ_EUNSUPPORTED, "stencil halo too large for a shared-memory tile");
+    int tl = budget - sep - sd.halo_lo - sd.halo_hi;
+    if (tl < 64) return fail(BQ_EUNSUPPORTED, "stencil halo too large for a shared-memory tile");
+    // enough CTAs per launch to occupy every SM twice (the multi-mode kernels are ALU-bound
+    // in FP64, so the larger halo share of small tiles costs L2 bandwidth, not time)
+    {
+      const int want_tiles = std::max(1, (2 * 152 + (int)P.sys.size() - 1) / (int)P.sys.size());
+      const int tl_par = std::max(64, (sd.n_r + want_tiles - 1) / want_tiles);
+      tl = std::min(tl, tl_par);
+    }
     for (int s = 0; s < sd.n_r; s += tl) {
       WorkItem w;
       w.sys = i; w.start = s; w.len = std::min(tl, sd.n_r - s); w.do_sep = (s == 0) ? sd.has_sep : 0;
@@ -1070,7 +1102,7 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     for (int q = 0; q < 3; ++q) {
       const int slot = st->pipe_slot[q];
-      const int nsl = std::max(2, std::min(4, (200 * 1024) / std::max(1, slot)));
+      const int nsl = std::max(2, std::min(3, (200 * 1024) / std::max(1, slot)));
       st->pipe_nslots[q] = nsl;
       int per_sm = 0;
       CUDA_TRY(bq::pipe_blocks_per_sm(o->dtype, P.m1_variant, nsl * slot, &per_sm));
@@ -1087,6 +1119,8 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   st->chpar_host = P.chpar;
   st->work_host = P.work;
   st->solve_smem = P.solve_smem;
+  st->solve_mg = P.solve_mg;
+  st->solve_mg_smem = P.solve_mg_smem;
   st->n_trace_groups = P.n_trace_groups; st->n_block_groups = P.n_block_groups; st->block_dim = P.block_dim;
   st->total_elems = P.total_elems; st->dt_max = dt_max; st->horizon = o->horizon; st->reverse = o->reverse_time;
   st->pool = base; st->L = L; st->sys = P.sys;
@@ -1291,7 +1325,10 @@ extern "C" int bq_solve(bq_state* s, double dt, int64_t n_steps, void* stream) {
   a.dt = dt;
   a.tau0 = s->tau;
   a.horizon = s->horizon;
-  CUDA_TRY(bq::launch_solve_m1(a, s->dtype, 0, s->solve_smem, st, &s->last_solve_grid));
+  if (s->solve_mg)
+    CUDA_TRY(bq::launch_solve_mg(a, s->dtype, s->solve_mg_smem, st, &s->last_solve_grid));
+  else
+    CUDA_TRY(bq::launch_solve_m1(a, s->dtype, 0, s->solve_smem, st, &s->last_solve_grid));
   g_launches++;
   s->tau += (double)n_steps * dt;
   return BQ_OK;

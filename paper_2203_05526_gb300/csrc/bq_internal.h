@@ -149,7 +149,7 @@ struct PipeRec {
 // Header of a parameter block (128 B), followed by dx[M], dy[M] (complex) and the weight tables
 // wX[nX][M], wY[nY][M], wSx[nS][M], wSy[nS][M] (real), the whole block padded to 16 B.
 struct PipeHdr {
-  int M, nX, nY, nS, has_sep, has_r, ntot, pad;
+  int M, nX, nY, nS, has_sep, has_r, ntot, merged;  // merged: all shifts in {-1,0,1}, nS <= 2, M <= 64
   int sX[BQ_M1_MAXT], sY[BQ_M1_MAXT], sSx[BQ_M1_MAXT], sSy[BQ_M1_MAXT];
   int pad2[8];
 };

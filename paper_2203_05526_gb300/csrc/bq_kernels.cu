@@ -526,6 +526,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 #define BQ_PIPE_THREADS 256
+#define BQ_MERGED_MAXM 64
 #define BQ_WAIT_LIMIT (1 << 22)
 
 // Stage coefficients of every system (X, Y, S terms in program order, C at slot 15).
@@ -564,6 +565,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
   __shared__ __align__(8) unsigned long long full[4];
   __shared__ PipeRec recs[2][32];
   __shared__ int s_fail;
+  __shared__ C mv[(6 + 4 * MS) * BQ_MERGED_MAXM];  // merged coefficient vectors of the current system
   const int tid = threadIdx.x;
   const int G = gridDim.x;
   const int nj = A.n_sys > (int)blockIdx.x ? (A.n_sys - (int)blockIdx.x + G - 1) / G : 0;
@@ -588,9 +590,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
     const PipeRec r = recs[(j >> 5) & 1][j & 31];
     unsigned char* sl = slot_ptr(j % S);
     const unsigned blk = (unsigned)(r.blk_elems * cs);
-    unsigned bytes = (unsigned)r.param_bytes + (unsigned)(BQ_PIPE_COEF * cs) + blk;
-    if (stage > 1) bytes += 2 * blk;
-    if (stage == 4) bytes += blk;
+    const unsigned bytes = (unsigned)r.param_bytes + (unsigned)(BQ_PIPE_COEF * cs) + blk;
     fence_proxy_async();
     unsigned long long* bar = &full[j % S];
     mbar_expect_tx(bar, bytes);
@@ -598,11 +598,6 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
     bulk_g2s(sl + A.off_coef, reinterpret_cast<const C*>(A.coef) + (size_t)r.sys * BQ_PIPE_COEF,
              (unsigned)(BQ_PIPE_COEF * cs), bar);
     bulk_g2s(sl + A.off_u, reinterpret_cast<const C*>(A.u_in) + r.blk_off, blk, bar);
-    if (stage > 1) {
-      bulk_g2s(sl + A.off_y, reinterpret_cast<const C*>(A.y) + r.blk_off, blk, bar);
-      bulk_g2s(sl + A.off_acc, reinterpret_cast<const C*>(A.acc) + r.blk_off, blk, bar);
-    }
-    if (stage == 4) bulk_g2s(sl + A.off_comp, reinterpret_cast<const C*>(A.comp) + r.blk_off, blk, bar);
   };
   if (tid == 0)
     for (int j = 0; j < S - 1 && j < nj; ++j) issue(j);
@@ -647,9 +642,151 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
     const T* wSy = wSx + nS * M;
     const C* cf = reinterpret_cast<const C*>(sl + A.off_coef);
     const C* u = reinterpret_cast<const C*>(sl + A.off_u);
-    const C* ys = reinterpret_cast<const C*>(sl + A.off_y);
-    const C* as = reinterpret_cast<const C*>(sl + A.off_acc);
-    const C* cps = reinterpret_cast<const C*>(sl + A.off_comp);
+    const C Cc = cf[BQ_PIPE_COEF - 1];
+    const C* ur = u + r.r_off;
+    const C* ugx = u + r.gx_off;
+    const C* ugy = u + r.gy_off;
+    const int nr = h.has_r ? M * M : 0;
+
+    // RK4 combine of one element (position pos inside the system block)
+    auto combine_at = [&](int pos, C uc, C kv) {
+      const int64_t gi = (int64_t)r.blk_off + pos;
+      if (stage == 1) {
+        uout[gi] = caxpy(dt * (T)0.5, kv, uc);
+        accg[gi] = kv;
+      } else if (stage == 4) {
+        const C yv = yg[gi];
+        const C sm = cadd(accg[gi], kv);
+        const C cv = compg[gi];
+        C d, t, c2;
+        d.x = dt * (T)(1.0 / 6.0) * sm.x - cv.x;
+        d.y = dt * (T)(1.0 / 6.0) * sm.y - cv.y;
+        t.x = yv.x + d.x;
+        t.y = yv.y + d.y;
+        c2.x = (t.x - yv.x) - d.x;
+        c2.y = (t.y - yv.y) - d.y;
+        yg[gi] = t;
+        compg[gi] = c2;
+      } else {
+        const C yv = yg[gi];
+        uout[gi] = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, yv);
+        accg[gi] = caxpy((T)2, kv, accg[gi]);
+      }
+    };
+
+    if (h.merged) {
+      // ---- merged stencil: per-row / per-column coefficient vectors, 3x3 register window ----
+      // row vectors: A0 (diagonal + shift-0 X terms), Am (shift -1), Ap (shift +1);
+      // column vectors B0, Bm, Bp likewise for the Y terms; per sandwich term t with shifts
+      // (sx, sy): SX_t[k] = c_t Wx_t[k], SY_t[l] = Wy_t[l], GX_t[k] = G_x[k+sx], GY_t[l] = Wy_t[l] G_y[l+sy].
+      C* A0 = mv;
+      C* Am = A0 + M;
+      C* Ap = Am + M;
+      C* B0 = Ap + M;
+      C* Bm = B0 + M;
+      C* Bp = Bm + M;
+      C* SXv = Bp + M;        // [MS][M]
+      C* GXv = SXv + MS * M;  // [MS][M]
+      C* SYv = GXv + MS * M;  // [MS][M] (real part used)
+      C* GYv = SYv + MS * M;  // [MS][M]
+      for (int i = tid; i < M; i += blockDim.x) {
+        C a0 = dx[i], am = cmk<C>(0.0, 0.0), ap = am;
+        C b0 = dy[i], bm = am, bp = am;
+#pragma unroll
+        for (int q = 0; q < MX; ++q)
+          if (q < nX) {
+            const C v = cscale(cf[q], wX[q * M + i]);
+            if (h.sX[q] == 0) a0 = cadd(a0, v); else if (h.sX[q] < 0) am = cadd(am, v); else ap = cadd(ap, v);
+          }
+#pragma unroll
+        for (int q = 0; q < MY; ++q)
+          if (q < nY) {
+            const C v = cscale(cf[nX + q], wY[q * M + i]);
+            if (h.sY[q] == 0) b0 = cadd(b0, v); else if (h.sY[q] < 0) bm = cadd(bm, v); else bp = cadd(bp, v);
+          }
+        A0[i] = a0; Am[i] = am; Ap[i] = ap;
+        B0[i] = b0; Bm[i] = bm; Bp[i] = bp;
+#pragma unroll
+        for (int q = 0; q < MS; ++q)
+          if (q < nS) {
+            const int xs = i + h.sSx[q], ysh = i + h.sSy[q];
+            SXv[q * M + i] = cscale(cf[nX + nY + q], wSx[q * M + i]);
+            SYv[q * M + i] = cmk<C>((double)wSy[q * M + i], 0.0);
+            GXv[q * M + i] = (has_sep && xs >= 0 && xs < M) ? ugx[xs] : cmk<C>(0.0, 0.0);
+            GYv[q * M + i] = (has_sep && ysh >= 0 && ysh < M) ? cscale(ugy[ysh], wSy[q * M + i]) : cmk<C>(0.0, 0.0);
+          }
+      }
+      __syncthreads();
+      if (nr) {
+        const int nb = min((int)blockDim.x / M, M);
+        const int rb = (M + nb - 1) / nb;
+        const int l = tid % M, bk = tid / M;
+        if (bk < nb) {
+          const int k0 = bk * rb, k1 = min(M, k0 + rb);
+          const C b0 = B0[l], bm = Bm[l], bp = Bp[l];
+          T sy[MS];
+          C gy[MS];
+          int ssx[MS], ssy[MS];
+#pragma unroll
+          for (int q = 0; q < MS; ++q) {
+            sy[q] = q < nS ? SYv[q * M + l].x : (T)0;
+            gy[q] = q < nS ? GYv[q * M + l] : cmk<C>(0.0, 0.0);
+            ssx[q] = h.sSx[q];
+            ssy[q] = h.sSy[q];
+          }
+          const C zero = cmk<C>(0.0, 0.0);
+          auto ld = [&](int kk, int ll) { return (kk >= 0 && kk < M && ll >= 0 && ll < M) ? ur[kk * M + ll] : zero; };
+          C w0[3], w1[3], w2[3];  // rows k-1, k, k+1 at columns l-1, l, l+1
+#pragma unroll
+          for (int c = 0; c < 3; ++c) { w0[c] = ld(k0 - 1, l - 1 + c); w1[c] = ld(k0, l - 1 + c); }
+          for (int kk = k0; kk < k1; ++kk) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) w2[c] = ld(kk + 1, l - 1 + c);
+            const C uc = w1[1];
+            C kv = cmul(cadd(A0[kk], b0), uc);
+            kv = cfma(Am[kk], w0[1], kv);
+            kv = cfma(Ap[kk], w2[1], kv);
+            kv = cfma(bm, w1[0], kv);
+            kv = cfma(bp, w1[2], kv);
+#pragma unroll
+            for (int q = 0; q < MS; ++q)
+              if (q < nS) {
+                const C* rowp = ssx[q] < 0 ? w0 : (ssx[q] > 0 ? w2 : w1);
+                const C v = ssy[q] < 0 ? rowp[0] : (ssy[q] > 0 ? rowp[2] : rowp[1]);
+                kv = cfma(SXv[q * M + kk], cadd(cscale(v, sy[q]), cmul(GXv[q * M + kk], gy[q])), kv);
+              }
+            combine_at(r.r_off + kk * M + l, uc, kv);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { w0[c] = w1[c]; w1[c] = w2[c]; }
+          }
+        }
+      }
+      if (has_sep) {
+        for (int i = tid; i < 2 * M; i += blockDim.x) {
+          const bool isx = i < M;
+          const int g = isx ? i : i - M;
+          const C* gs = isx ? ugx : ugy;
+          const C uc = gs[g];
+          const C zero = cmk<C>(0.0, 0.0);
+          const C lo = g > 0 ? gs[g - 1] : zero, hi = g + 1 < M ? gs[g + 1] : zero;
+          C kv;
+          if (isx) {
+            kv = cmul(cadd(A0[g], Cc), uc);
+            kv = cfma(Am[g], lo, kv);
+            kv = cfma(Ap[g], hi, kv);
+          } else {
+            kv = cmul(cadd(B0[g], cmk<C>(-(double)Cc.x, -(double)Cc.y)), uc);
+            kv = cfma(Bm[g], lo, kv);
+            kv = cfma(Bp[g], hi, kv);
+          }
+          combine_at((isx ? r.gx_off : r.gy_off) + g, uc, kv);
+        }
+      }
+      __syncthreads();
+      continue;
+    }
+
+    // ---- general term program (any shifts) ----------------------------------------------
     C cX[MX], cY[MY], cS[MS];
     int shX[MX], shY[MY], shSx[MS], shSy[MS];
 #pragma unroll
@@ -662,11 +799,6 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
       shSx[q] = h.sSx[q];
       shSy[q] = h.sSy[q];
     }
-    const C Cc = cf[BQ_PIPE_COEF - 1];
-    const C* ur = u + r.r_off;
-    const C* ugx = u + r.gx_off;
-    const C* ugy = u + r.gy_off;
-    const int nr = h.has_r ? M * M : 0;
     const int ntot = h.ntot;
     const float invM = 1.0f / (float)M;
     for (int e = tid; e < ntot; e += blockDim.x) {
@@ -710,28 +842,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
             if (q < nY) kv = cfma(cY[q], cscale(gs[min(max(g + shY[q], 0), M - 1)], wY[q * M + g]), kv);
         }
       }
-      const int64_t gi = (int64_t)r.blk_off + pos;
-      if (stage == 1) {
-        uout[gi] = caxpy(dt * (T)0.5, kv, uc);
-        accg[gi] = kv;
-      } else if (stage == 4) {
-        const C yv = ys[pos];
-        const C sm = cadd(as[pos], kv);
-        const C cv = cps[pos];
-        C d, t, c2;
-        d.x = dt * (T)(1.0 / 6.0) * sm.x - cv.x;
-        d.y = dt * (T)(1.0 / 6.0) * sm.y - cv.y;
-        t.x = yv.x + d.x;
-        t.y = yv.y + d.y;
-        c2.x = (t.x - yv.x) - d.x;
-        c2.y = (t.y - yv.y) - d.y;
-        yg[gi] = t;
-        compg[gi] = c2;
-      } else {
-        const C yv = ys[pos];
-        uout[gi] = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, yv);
-        accg[gi] = caxpy((T)2, kv, as[pos]);
-      }
+      combine_at(pos, uc, kv);
     }
     __syncthreads();
   }
@@ -1058,13 +1169,20 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
     if (stage > 1) BOUT[gi] = caxpy(cq, q, cscale(LAM[gi], dt * beta));
   };
   auto addg = [&](int t, C ub, C bv, T w) {
-    // accumulate u * (W b_src) for gradient term t
+    // accumulate u * (W b_src) for gradient term t (g is uniform across the warp: a jump
+    // to one register accumulator, not a scan over all of them)
     const int g = gidx[t];
     if (g < 0) return;
     const C v = cmul(ub, cscale(bv, w));
-#pragma unroll
-    for (int q = 0; q < BQ_MAX_GT; ++q)
-      if (q == g) { gacc[q].x += (double)v.x; gacc[q].y += (double)v.y; }
+    const double vx = (double)v.x, vy = (double)v.y;
+    switch (g) {
+#define BQ_GACC_CASE(q) case q: gacc[q].x += vx; gacc[q].y += vy; break;
+      BQ_GACC_CASE(0) BQ_GACC_CASE(1) BQ_GACC_CASE(2) BQ_GACC_CASE(3) BQ_GACC_CASE(4) BQ_GACC_CASE(5)
+      BQ_GACC_CASE(6) BQ_GACC_CASE(7) BQ_GACC_CASE(8) BQ_GACC_CASE(9) BQ_GACC_CASE(10) BQ_GACC_CASE(11)
+      BQ_GACC_CASE(12) BQ_GACC_CASE(13) BQ_GACC_CASE(14) BQ_GACC_CASE(15)
+#undef BQ_GACC_CASE
+      default: break;
+    }
   };
 
   if (sd.has_r) {
@@ -1302,6 +1420,289 @@ __global__ void k_adj_seed(const SysDesc* __restrict__ sys, const EvalGroup* __r
 }
 
 // ---------------------------------------------------------------------------------------
+// Batched persistent solve, merged-stencil form (single mode, every shift in {-1, 0, 1}):
+// the solve of k_solve_m1 with the per-term stencil replaced by per-row / per-column
+// coefficient vectors (rebuilt for the next stage while the current one is computed) and a
+// column-strip thread mapping with a 3x3 register window of the stage input.  Thread (l, b)
+// owns column l, rows [b rb, (b+1) rb); its state, stage sum and compensation stay in
+// registers for the whole solve.  One barrier per stage; coefficients are evaluated two
+// stages ahead (triple buffered), the merged vectors one stage ahead (double buffered).
+// ---------------------------------------------------------------------------------------
+template <typename T, int BLK, int RB, int MX, int MY, int MS>
+__global__ void __launch_bounds__(BLK) k_solve_mg(const SolveArgs A) {
+  using C = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ M1Sys s;
+  __shared__ C coef[3][3 * BQ_M1_MAXT];
+  __shared__ int s_next;
+  const int tid = threadIdx.x;
+  C* y_g = reinterpret_cast<C*>(A.y);
+  C* comp_g = reinterpret_cast<C*>(A.comp);
+  const C zero = cmk<C>(0.0, 0.0);
+
+  for (;;) {
+    if (tid == 0) s_next = (int)atomicAdd(A.queue, 1u);
+    __syncthreads();
+    const int qi = s_next;
+    if (qi >= A.n_sys) return;
+    {
+      const int* src = reinterpret_cast<const int*>(A.m1 + A.order[qi]);
+      int* dst = reinterpret_cast<int*>(&s);
+      for (int i = tid; i < (int)(sizeof(M1Sys) / sizeof(int)); i += BLK) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int M = s.M, nX = s.nX, nY = s.nY, nS = s.nS;
+    const int has_r = s.has_r, has_sep = s.has_sep;
+    const int nr = has_r ? M * M : 0;
+    const int ntot = nr + (has_sep ? 2 * M : 0);
+    // shared: B0[ntot] | B1[ntot] | dx[M] dy[M] | MV[2][(6 + MS) M] | wX wY wSx wSy (real)
+    C* B0 = reinterpret_cast<C*>(smem_raw);
+    C* B1 = B0 + ntot;
+    C* dx = B1 + ntot;
+    C* dy = dx + M;
+    C* MV = dy + M;
+    const int mvs = (6 + MS) * M;
+    T* wX = reinterpret_cast<T*>(MV + 2 * mvs);
+    T* wY = wX + nX * M;
+    T* wSx = wY + nY * M;
+    T* wSy = wSx + nS * M;
+    const int nt = nX + nY + nS;
+    auto eval_coef = [&](int buf, int64_t step, int stage) {
+      if (tid < nt) {
+        const int t = tid < nX ? s.tX[tid] : (tid < nX + nY ? s.tY[tid - nX] : s.tS[tid - nX - nY]);
+        const TermDesc& td = A.terms[s.term_off + t];
+        double2 c = make_double2(td.c_re, td.c_im);
+        if (td.ch >= 0) {
+          const ChanDesc cd = A.chans[td.ch];
+          const double ts = A.tau0 + (double)step * A.dt;
+          const double tau = (cd.kind == 2) ? ts + 0.5 * A.dt : ts + stage_c(stage) * A.dt;
+          double2 e = chan_value_t<T>(cd, A.chpar, A.reverse ? A.horizon - tau : tau);
+          if (td.conj) e.y = -e.y;
+          c = make_double2(c.x * e.x - c.y * e.y, c.x * e.y + c.y * e.x);
+        }
+        coef[buf][tid] = cmk<C>(c.x, c.y);
+      }
+    };
+    // merged vectors from coef[cb] into MV half mb: A0 Am Ap (rows) B0 Bm Bp (columns) SX_t
+    auto build_mv = [&](int cb, int mb) {
+      C* V = MV + mb * mvs;
+      for (int i = tid; i < M; i += BLK) {
+        C a0 = dx[i], am = zero, ap = zero, b0 = dy[i], bm = zero, bp = zero;
+#pragma unroll
+        for (int q = 0; q < MX; ++q)
+          if (q < nX) {
+            const C v = cscale(coef[cb][q], wX[q * M + i]);
+            if (s.sX[q] == 0) a0 = cadd(a0, v); else if (s.sX[q] < 0) am = cadd(am, v); else ap = cadd(ap, v);
+          }
+#pragma unroll
+        for (int q = 0; q < MY; ++q)
+          if (q < nY) {
+            const C v = cscale(coef[cb][nX + q], wY[q * M + i]);
+            if (s.sY[q] == 0) b0 = cadd(b0, v); else if (s.sY[q] < 0) bm = cadd(bm, v); else bp = cadd(bp, v);
+          }
+        V[i] = a0; V[M + i] = am; V[2 * M + i] = ap;
+        V[3 * M + i] = b0; V[4 * M + i] = bm; V[5 * M + i] = bp;
+#pragma unroll
+        for (int q = 0; q < MS; ++q)
+          if (q < nS) V[(6 + q) * M + i] = cscale(coef[cb][nX + nY + q], wSx[q * M + i]);
+      }
+    };
+    // ---- load: state, tables; coefficients of stages (0,1) and (0,2); vectors of (0,1) ----
+    const int nb = min(BLK / M, M);
+    const int rb = (M + nb - 1) / nb;
+    const int cl = tid % M, cbk = tid / M;
+    const bool owner = has_r && cbk < nb;
+    const int k0 = cbk * rb, k1 = owner ? min(M, k0 + rb) : k0;
+    C yv[RB], av[RB], cv[RB];
+    auto gidx_r = [&](int kk) { return s.off_r + (int64_t)kk * M + cl; };
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      const int kk = k0 + j;
+      if (kk < k1) {
+        yv[j] = y_g[gidx_r(kk)];
+        cv[j] = comp_g[gidx_r(kk)];
+        B0[kk * M + cl] = yv[j];
+      } else {
+        yv[j] = zero; cv[j] = zero;
+      }
+      av[j] = zero;
+    }
+    // G_x, G_y (elements nr .. nr + 2M): thread tid < 2M owns one
+    const bool gown = has_sep && tid < 2 * M;
+    C gy_v = zero, ga_v = zero, gc_v = zero;
+    const int64_t g_gi = gown ? (tid < M ? s.off_gx + tid : s.off_gy + (tid - M)) : 0;
+    if (gown) {
+      gy_v = y_g[g_gi];
+      gc_v = comp_g[g_gi];
+      B0[nr + tid] = gy_v;
+    }
+    {
+      const C* Dg = reinterpret_cast<const C*>(A.diag) + s.diag_off;
+      const T* W = reinterpret_cast<const T*>(A.wtab);
+      for (int i = tid; i < M; i += BLK) {
+        dx[i] = Dg[i];
+        dy[i] = Dg[M + i];
+#pragma unroll
+        for (int j = 0; j < MX; ++j) if (j < nX) wX[j * M + i] = s.wX[j] >= 0 ? W[s.wX[j] + i] : (T)1;
+#pragma unroll
+        for (int j = 0; j < MY; ++j) if (j < nY) wY[j * M + i] = s.wY[j] >= 0 ? W[s.wY[j] + i] : (T)1;
+#pragma unroll
+        for (int j = 0; j < MS; ++j)
+          if (j < nS) {
+            wSx[j * M + i] = s.wSx[j] >= 0 ? W[s.wSx[j] + i] : (T)1;
+            wSy[j * M + i] = s.wSy[j] >= 0 ? W[s.wSy[j] + i] : (T)1;
+          }
+      }
+    }
+    eval_coef(0, 0, 1);
+    eval_coef(1, 0, 2);
+    __syncthreads();
+    build_mv(0, 0);
+    __syncthreads();
+    const C Cc = cmk<C>(s.c_re, s.c_im);
+    const C mCc = cmk<C>(-s.c_re, -s.c_im);
+    const T dt = (T)A.dt;
+    int ssx[MS], ssy[MS];
+#pragma unroll
+    for (int q = 0; q < MS; ++q) { ssx[q] = s.sSx[q]; ssy[q] = s.sSy[q]; }
+
+    int cbuf = 0;  // coef buffer of the current stage; +1 (mod 3) is the next stage's
+    int mbuf = 0;  // MV half of the current stage
+    for (int64_t step = 0; step < A.n_steps; ++step) {
+#pragma unroll 1
+      for (int stage = 1; stage <= 4; ++stage) {
+        const C* uin = (stage & 1) ? B0 : B1;
+        C* uout = (stage & 1) ? B1 : B0;
+        const C* V = MV + mbuf * mvs;
+        const C* gxi = uin + nr;
+        const C* gyi = gxi + M;
+        // coefficients two stages ahead (stage + 2)
+        {
+          int st2 = stage + 2;
+          int64_t sp2 = step;
+          if (st2 > 4) { st2 -= 4; ++sp2; }
+          eval_coef((cbuf + 2) % 3, sp2, st2);
+        }
+        if (owner) {
+          const C b0 = V[3 * M + cl], bm = V[4 * M + cl], bp = V[5 * M + cl];
+          T sy[MS];
+          C gyp[MS];
+#pragma unroll
+          for (int q = 0; q < MS; ++q) {
+            sy[q] = q < nS ? wSy[q * M + cl] : (T)0;
+            const int yy = cl + ssy[q];
+            gyp[q] = (q < nS && has_sep && yy >= 0 && yy < M) ? cscale(gyi[yy], sy[q]) : zero;
+          }
+          auto ld = [&](int kk, int ll) { return (kk >= 0 && kk < M && ll >= 0 && ll < M) ? uin[kk * M + ll] : zero; };
+          C w0[3], w1[3], w2[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) { w0[c] = ld(k0 - 1, cl - 1 + c); w1[c] = ld(k0, cl - 1 + c); }
+#pragma unroll
+          for (int j = 0; j < RB; ++j) {
+            const int kk = k0 + j;
+            if (kk < k1) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) w2[c] = ld(kk + 1, cl - 1 + c);
+              C kv = cmul(cadd(V[kk], b0), w1[1]);
+              kv = cfma(V[M + kk], w0[1], kv);
+              kv = cfma(V[2 * M + kk], w2[1], kv);
+              kv = cfma(bm, w1[0], kv);
+              kv = cfma(bp, w1[2], kv);
+#pragma unroll
+              for (int q = 0; q < MS; ++q)
+                if (q < nS) {
+                  const C* rowp = ssx[q] < 0 ? w0 : (ssx[q] > 0 ? w2 : w1);
+                  const C v = ssy[q] < 0 ? rowp[0] : (ssy[q] > 0 ? rowp[2] : rowp[1]);
+                  const int xx = kk + ssx[q];
+                  const C gxv = (has_sep && xx >= 0 && xx < M) ? gxi[xx] : zero;
+                  kv = cfma(V[(6 + q) * M + kk], cadd(cscale(v, sy[q]), cmul(gxv, gyp[q])), kv);
+                }
+              // RK4 combine (stage sum + compensated state update)
+              C outv;
+              if (stage == 1) {
+                outv = caxpy(dt * (T)0.5, kv, yv[j]);
+                av[j] = kv;
+              } else if (stage == 4) {
+                const C sm = cadd(av[j], kv);
+                C d, t;
+                d.x = dt * (T)(1.0 / 6.0) * sm.x - cv[j].x;
+                d.y = dt * (T)(1.0 / 6.0) * sm.y - cv[j].y;
+                t.x = yv[j].x + d.x;
+                t.y = yv[j].y + d.y;
+                cv[j].x = (t.x - yv[j].x) - d.x;
+                cv[j].y = (t.y - yv[j].y) - d.y;
+                yv[j] = t;
+                outv = t;
+              } else {
+                outv = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, yv[j]);
+                av[j] = caxpy((T)2, kv, av[j]);
+              }
+              uout[kk * M + cl] = outv;
+#pragma unroll
+              for (int c = 0; c < 3; ++c) { w0[c] = w1[c]; w1[c] = w2[c]; }
+            }
+          }
+        }
+        if (gown) {
+          const bool isx = tid < M;
+          const int g = isx ? tid : tid - M;
+          const C* gs = isx ? gxi : gyi;
+          const C lo = g > 0 ? gs[g - 1] : zero, hi = g + 1 < M ? gs[g + 1] : zero;
+          C kv;
+          if (isx) {
+            kv = cmul(cadd(V[g], Cc), gs[g]);
+            kv = cfma(V[M + g], lo, kv);
+            kv = cfma(V[2 * M + g], hi, kv);
+          } else {
+            kv = cmul(cadd(V[3 * M + g], mCc), gs[g]);
+            kv = cfma(V[4 * M + g], lo, kv);
+            kv = cfma(V[5 * M + g], hi, kv);
+          }
+          C outv;
+          if (stage == 1) {
+            outv = caxpy(dt * (T)0.5, kv, gy_v);
+            ga_v = kv;
+          } else if (stage == 4) {
+            const C sm = cadd(ga_v, kv);
+            C d, t;
+            d.x = dt * (T)(1.0 / 6.0) * sm.x - gc_v.x;
+            d.y = dt * (T)(1.0 / 6.0) * sm.y - gc_v.y;
+            t.x = gy_v.x + d.x;
+            t.y = gy_v.y + d.y;
+            gc_v.x = (t.x - gy_v.x) - d.x;
+            gc_v.y = (t.y - gy_v.y) - d.y;
+            gy_v = t;
+            outv = t;
+          } else {
+            outv = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, gy_v);
+            ga_v = caxpy((T)2, kv, ga_v);
+          }
+          uout[nr + tid] = outv;
+        }
+        // merged vectors of the next stage (its coefficients were evaluated two stages ago)
+        build_mv((cbuf + 1) % 3, mbuf ^ 1);
+        cbuf = (cbuf + 1) % 3;
+        mbuf ^= 1;
+        __syncthreads();
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      const int kk = k0 + j;
+      if (kk < k1) {
+        y_g[gidx_r(kk)] = yv[j];
+        comp_g[gidx_r(kk)] = cv[j];
+      }
+    }
+    if (gown) {
+      y_g[g_gi] = gy_v;
+      comp_g[g_gi] = gc_v;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Observables: one warp per evaluation group, lanes over (initial condition, entry) pairs.
 // ---------------------------------------------------------------------------------------
 template <typename T>
@@ -1482,6 +1883,35 @@ static cudaError_t launch_solve_t(const SolveArgs& a, int smem_bytes, cudaStream
   *grid_out = grid;
   kern<<<grid, BLK, smem_bytes, s>>>(a);
   return cudaGetLastError();
+}
+
+template <typename T, int BLK, int RB>
+static cudaError_t launch_solve_mg_t(const SolveArgs& a, int smem_bytes, cudaStream_t s, int* grid_out) {
+  auto kern = k_solve_mg<T, BLK, RB, BQ_M1_MAXT, BQ_M1_MAXT, 2>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, BQ_MAX_DYN_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLK, smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = std::min(a.n_sys, per_sm * nsm);
+  *grid_out = grid;
+  kern<<<grid, BLK, smem_bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_mg(const SolveArgs& a, int dtype, int smem_bytes, cudaStream_t s, int* grid_out) {
+  // 256 threads; column strips of at most 8 rows (M <= 45)
+  return dtype == 0 ? launch_solve_mg_t<double, 256, 8>(a, smem_bytes, s, grid_out)
+                    : launch_solve_mg_t<float, 256, 8>(a, smem_bytes, s, grid_out);
 }
 
 cudaError_t launch_solve_m1(const SolveArgs& a, int dtype, int capacity_class, int smem_bytes, cudaStream_t s,

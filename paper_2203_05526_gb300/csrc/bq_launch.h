@@ -33,6 +33,8 @@ cudaError_t launch_adj_seed(const SysDesc* sys, const EvalGroup* groups, const E
 cudaError_t launch_stage_pipe(const PipeArgs& a, const CoefArgs& c, int variant, int dtype, int grid, int smem_bytes,
                               cudaStream_t s);
 cudaError_t pipe_blocks_per_sm(int dtype, int variant, int smem_bytes, int* out);
+// Batched persistent solve, merged-stencil form (256 threads, M <= 45, shifts in {-1,0,1}).
+cudaError_t launch_solve_mg(const SolveArgs& a, int dtype, int smem_bytes, cudaStream_t s, int* grid_out);
 cudaError_t launch_eval(const SysDesc* sys, const EvalGroup* groups, const EvalEntry* entries, const void* y,
                         double2* out, int n_groups, int dtype, int small, cudaStream_t s);
 // Device address of the fixed RK4 scratch on the current device (looked up once per device).
