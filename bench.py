@@ -64,11 +64,29 @@ def dist_env():
     return rank, world, local
 
 
+def shard_range(n_inst: int, rank: int):
+    """Indices of the seeded kerr_batch stream solved by this rank (rank-major shards of
+    n_inst instances: replicas with no exchange between ranks)."""
+    return range(n_inst * rank, n_inst * (rank + 1))
+
+
 def workload(n_inst: int, rank: int):
     """Instances of this rank: the seeded stream of kerr_batch, rank-major shards."""
     from workloads import configs
-    allp = configs.kerr_batch(B=n_inst * (rank + 1), T=HORIZON, dt=DT)
-    return allp[n_inst * rank:]
+    r = shard_range(n_inst, rank)
+    allp = configs.kerr_batch(B=r.stop, T=HORIZON, dt=DT)
+    return allp[r.start:r.stop]
+
+
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """Slowest rank's time (the job's time); a no-op for one rank."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def configs_batch(n: int):
@@ -332,11 +350,7 @@ def main():
     clocks = clk.stop()
     ms = t0.elapsed_time(t1)
     stage_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, world, device="cuda")
     assert np.all(np.isfinite(obs))
     upd_per_step = 4 * pts
     value = world * upd_per_step * args.steps / (ms / 1e3)
@@ -382,11 +396,12 @@ def main():
     e2e = {"value": world * upd_per_step * args.steps / (e2e_ms / 1e3), "unit": METRIC,
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 16 * len(specs)}
 
+    # the 4096-instance full solves and the gradient are single-GPU legs (rank 0 of a 1-GPU run)
     batched = None
-    if not args.no_batched:
+    if not args.no_batched and world == 1:
         batched = batched_leg(world)
     grads = None
-    if not args.no_grads and rank == 0:
+    if not args.no_grads and world == 1:
         grads = grads_leg()
 
     cpu = None

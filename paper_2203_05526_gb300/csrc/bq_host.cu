@@ -596,7 +596,7 @@ struct bq_state {
   int trace_small = 0, block_small = 0;
   int solve_ok = 0, solve_smem = 0, last_solve_grid = 0, solve_mg = 0, solve_mg_smem = 0;
   int use_pipe = 0, pipe_off_coef = 0, pipe_off_u = 0, pipe_off_y = 0, pipe_off_acc = 0, pipe_off_comp = 0;
-  int pipe_slot[3] = {0, 0, 0}, pipe_nslots[3] = {2, 2, 2}, pipe_grid[3] = {1, 1, 1};
+  int pipe_slot[3] = {0, 0, 0}, pipe_nslots[3] = {2, 2, 2}, pipe_grid[3] = {1, 1, 1}, pipe_mv_bytes = 0;
   int grad_size = 0, adj_smem = 0, srcred_stride = 0, max_s = 0;
   std::vector<TermDesc> terms_host;
   std::vector<ChanDesc> chans_host;
@@ -1096,16 +1096,22 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   st->pipe_off_coef = P.pipe_off_coef; st->pipe_off_u = P.pipe_off_u; st->pipe_off_y = P.pipe_off_y;
   st->pipe_off_acc = P.pipe_off_acc; st->pipe_off_comp = P.pipe_off_comp;
   for (int q = 0; q < 3; ++q) st->pipe_slot[q] = P.pipe_slot[q];
+  {
+    int mmax = 1;
+    for (auto& m : P.m1) mmax = std::max(mmax, m.M);
+    const int ms = P.m1_variant == 0 ? 2 : BQ_M1_MAXT;
+    st->pipe_mv_bytes = (int)(((size_t)(6 + 4 * ms) * mmax * (o->dtype == BQ_F64 ? 16 : 8) + 127) & ~(size_t)127);
+  }
   if (st->use_pipe) {
     int dev = 0, nsm = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     for (int q = 0; q < 3; ++q) {
       const int slot = st->pipe_slot[q];
-      const int nsl = std::max(2, std::min(3, (200 * 1024) / std::max(1, slot)));
+      const int nsl = 2;  // double buffering; more CTAs per SM keep more systems in flight
       st->pipe_nslots[q] = nsl;
       int per_sm = 0;
-      CUDA_TRY(bq::pipe_blocks_per_sm(o->dtype, P.m1_variant, nsl * slot, &per_sm));
+      CUDA_TRY(bq::pipe_blocks_per_sm(o->dtype, P.m1_variant, nsl * slot + st->pipe_mv_bytes, &per_sm));
       if (per_sm < 1) { st->use_pipe = 0; break; }
       st->pipe_grid[q] = std::min((int)P.sys.size(), per_sm * nsm);
     }
@@ -1196,7 +1202,8 @@ static cudaError_t launch_any_stage(bq_state* s, const bq::StageArgs& a, cudaStr
     ca.coef = b + L.off_pcoef;
     ca.tau_base = a.tau_base; ca.counter = a.counter;
     ca.dt = a.dt; ca.horizon = a.horizon; ca.n_sys = s->n_sys; ca.stage = a.stage; ca.reverse = a.reverse;
-    return bq::launch_stage_pipe(pa, ca, s->m1_variant, s->dtype, s->pipe_grid[q], pa.n_slots * pa.slot_bytes, st);
+    return bq::launch_stage_pipe(pa, ca, s->m1_variant, s->dtype, s->pipe_grid[q], pa.n_slots * pa.slot_bytes + s->pipe_mv_bytes,
+                                 st);
   }
   if (s->use_m1)
     return bq::launch_stage_m1(a, (const bq::M1Sys*)(s->pool + s->L.off_m1), s->m1_variant, s->dtype, s->n_work,

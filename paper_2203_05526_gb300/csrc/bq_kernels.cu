@@ -500,6 +500,16 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage_m1(const StageArgs A, const 
 // shared memory and stream the results to HBM with coalesced stores.  Every wait on an
 // mbarrier is bounded; a wait that gives up sets an error word and the CTA returns.
 // ---------------------------------------------------------------------------------------
+// Element (1 + sx, 1 + sy) of a 3x3 register window, selected without taking addresses (so
+// the window stays in registers).
+template <typename C>
+__device__ __forceinline__ C pick9(const C (&w0)[3], const C (&w1)[3], const C (&w2)[3], int sx, int sy) {
+  const C a = sy < 0 ? w0[0] : (sy > 0 ? w0[2] : w0[1]);
+  const C b = sy < 0 ? w1[0] : (sy > 0 ? w1[2] : w1[1]);
+  const C c = sy < 0 ? w2[0] : (sy > 0 ? w2[2] : w2[1]);
+  return sx < 0 ? a : (sx > 0 ? c : b);
+}
+
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
@@ -525,7 +535,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-#define BQ_PIPE_THREADS 256
+#define BQ_PIPE_THREADS 128
 #define BQ_MERGED_MAXM 64
 #define BQ_WAIT_LIMIT (1 << 22)
 
@@ -565,7 +575,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
   __shared__ __align__(8) unsigned long long full[4];
   __shared__ PipeRec recs[2][32];
   __shared__ int s_fail;
-  __shared__ C mv[(6 + 4 * MS) * BQ_MERGED_MAXM];  // merged coefficient vectors of the current system
+
   const int tid = threadIdx.x;
   const int G = gridDim.x;
   const int nj = A.n_sys > (int)blockIdx.x ? (A.n_sys - (int)blockIdx.x + G - 1) / G : 0;
@@ -585,6 +595,8 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
   load_batch(0);
   __syncthreads();
   auto slot_ptr = [&](int s) { return smem_raw + (size_t)s * A.slot_bytes; };
+  // merged coefficient vectors of the current system: after the slots, (6 + 4 MS) Mmax complex
+  C* mv = reinterpret_cast<C*>(smem_raw + (size_t)S * A.slot_bytes);
   // thread 0: issue the bulk copies of system j into slot j % S
   auto issue = [&](int j) {
     const PipeRec r = recs[(j >> 5) & 1][j & 31];
@@ -615,12 +627,15 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
       __syncthreads();
     }
     if (tid == 0 && jn < nj) issue(jn);
-    // wait for system j (bounded)
+    // wait for system j (bounded): one thread polls the mbarrier, the others wait at the
+    // barrier without issuing; the completed phase also makes the bulk-copied data visible
     {
-      bool ok = false;
-      for (int it = 0; it < BQ_WAIT_LIMIT; ++it)
-        if (mbar_try_wait(&full[j % S], (unsigned)((j / S) & 1))) { ok = true; break; }
-      if (!ok) atomicOr(&s_fail, 1);
+      bool ok = true;
+      if (tid == 0) {
+        ok = false;
+        for (int it = 0; it < BQ_WAIT_LIMIT; ++it)
+          if (mbar_try_wait(&full[j % S], (unsigned)((j / S) & 1))) { ok = true; break; }
+      }
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicOr(A.error, 1u);
         // give the copies in flight a bounded chance to land before the CTA leaves
@@ -723,41 +738,76 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
         const int l = tid % M, bk = tid / M;
         if (bk < nb) {
           const int k0 = bk * rb, k1 = min(M, k0 + rb);
+          const C zero = cmk<C>(0.0, 0.0);
           const C b0 = B0[l], bm = Bm[l], bp = Bp[l];
+          const bool cm = l > 0, cp = l + 1 < M;  // column neighbours exist
           T sy[MS];
           C gy[MS];
-          int ssx[MS], ssy[MS];
+          int ssx[MS], soff[MS];
+          bool scol[MS];
 #pragma unroll
           for (int q = 0; q < MS; ++q) {
             sy[q] = q < nS ? SYv[q * M + l].x : (T)0;
-            gy[q] = q < nS ? GYv[q * M + l] : cmk<C>(0.0, 0.0);
+            gy[q] = q < nS ? GYv[q * M + l] : zero;
             ssx[q] = h.sSx[q];
-            ssy[q] = h.sSy[q];
+            soff[q] = h.sSx[q] * M + h.sSy[q];
+            scol[q] = q < nS && l + h.sSy[q] >= 0 && l + h.sSy[q] < M;
           }
-          const C zero = cmk<C>(0.0, 0.0);
-          auto ld = [&](int kk, int ll) { return (kk >= 0 && kk < M && ll >= 0 && ll < M) ? ur[kk * M + ll] : zero; };
-          C w0[3], w1[3], w2[3];  // rows k-1, k, k+1 at columns l-1, l, l+1
-#pragma unroll
-          for (int c = 0; c < 3; ++c) { w0[c] = ld(k0 - 1, l - 1 + c); w1[c] = ld(k0, l - 1 + c); }
+          C um = k0 > 0 ? ur[(k0 - 1) * M + l] : zero;  // u(k-1, l)
+          C uc = ur[k0 * M + l];                          // u(k, l)
+          // state / stage sum / compensation, loaded two rows ahead of use (register ring)
+          const int64_t g0 = (int64_t)r.blk_off + r.r_off + l;
+          C y0 = zero, a0v = zero, c0 = zero, y1 = zero, a1 = zero, c1 = zero;
+          if (stage > 1) {
+            if (k0 < k1) { y0 = yg[g0 + k0 * M]; a0v = accg[g0 + k0 * M]; if (stage == 4) c0 = compg[g0 + k0 * M]; }
+            if (k0 + 1 < k1) { y1 = yg[g0 + (k0 + 1) * M]; a1 = accg[g0 + (k0 + 1) * M]; if (stage == 4) c1 = compg[g0 + (k0 + 1) * M]; }
+          }
           for (int kk = k0; kk < k1; ++kk) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) w2[c] = ld(kk + 1, l - 1 + c);
-            const C uc = w1[1];
+            const int pos = r.r_off + kk * M + l;
+            const int64_t gi = (int64_t)r.blk_off + pos;
+            const C yv = y0, av = a0v, cv = c0;
+            y0 = y1; a0v = a1; c0 = c1;
+            if (stage > 1 && kk + 2 < k1) {
+              y1 = yg[gi + 2 * M];
+              a1 = accg[gi + 2 * M];
+              if (stage == 4) c1 = compg[gi + 2 * M];
+            }
+            const int c = kk * M + l;
+            const C up = kk + 1 < M ? ur[c + M] : zero;
+            const C ul = cm ? ur[c - 1] : zero;
+            const C urr = cp ? ur[c + 1] : zero;
             C kv = cmul(cadd(A0[kk], b0), uc);
-            kv = cfma(Am[kk], w0[1], kv);
-            kv = cfma(Ap[kk], w2[1], kv);
-            kv = cfma(bm, w1[0], kv);
-            kv = cfma(bp, w1[2], kv);
+            kv = cfma(Am[kk], um, kv);
+            kv = cfma(Ap[kk], up, kv);
+            kv = cfma(bm, ul, kv);
+            kv = cfma(bp, urr, kv);
 #pragma unroll
             for (int q = 0; q < MS; ++q)
               if (q < nS) {
-                const C* rowp = ssx[q] < 0 ? w0 : (ssx[q] > 0 ? w2 : w1);
-                const C v = ssy[q] < 0 ? rowp[0] : (ssy[q] > 0 ? rowp[2] : rowp[1]);
+                const int xx = kk + ssx[q];
+                const C v = (scol[q] && xx >= 0 && xx < M) ? ur[c + soff[q]] : zero;
                 kv = cfma(SXv[q * M + kk], cadd(cscale(v, sy[q]), cmul(GXv[q * M + kk], gy[q])), kv);
               }
-            combine_at(r.r_off + kk * M + l, uc, kv);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) { w0[c] = w1[c]; w1[c] = w2[c]; }
+            if (stage == 1) {
+              uout[gi] = caxpy(dt * (T)0.5, kv, uc);
+              accg[gi] = kv;
+            } else if (stage == 4) {
+              const C sm = cadd(av, kv);
+              C d, t, c2;
+              d.x = dt * (T)(1.0 / 6.0) * sm.x - cv.x;
+              d.y = dt * (T)(1.0 / 6.0) * sm.y - cv.y;
+              t.x = yv.x + d.x;
+              t.y = yv.y + d.y;
+              c2.x = (t.x - yv.x) - d.x;
+              c2.y = (t.y - yv.y) - d.y;
+              yg[gi] = t;
+              compg[gi] = c2;
+            } else {
+              uout[gi] = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, yv);
+              accg[gi] = caxpy((T)2, kv, av);
+            }
+            um = uc;
+            uc = up;
           }
         }
       }
@@ -1593,27 +1643,34 @@ __global__ void __launch_bounds__(BLK) k_solve_mg(const SolveArgs A) {
             const int yy = cl + ssy[q];
             gyp[q] = (q < nS && has_sep && yy >= 0 && yy < M) ? cscale(gyi[yy], sy[q]) : zero;
           }
-          auto ld = [&](int kk, int ll) { return (kk >= 0 && kk < M && ll >= 0 && ll < M) ? uin[kk * M + ll] : zero; };
-          C w0[3], w1[3], w2[3];
+          const bool cm = cl > 0, cp = cl + 1 < M;
+          int soff[MS];
+          bool scol[MS];
 #pragma unroll
-          for (int c = 0; c < 3; ++c) { w0[c] = ld(k0 - 1, cl - 1 + c); w1[c] = ld(k0, cl - 1 + c); }
+          for (int q = 0; q < MS; ++q) {
+            soff[q] = ssx[q] * M + ssy[q];
+            scol[q] = q < nS && cl + ssy[q] >= 0 && cl + ssy[q] < M;
+          }
+          C um = k0 > 0 ? uin[(k0 - 1) * M + cl] : zero;
+          C ucn = uin[k0 * M + cl];
 #pragma unroll
           for (int j = 0; j < RB; ++j) {
             const int kk = k0 + j;
             if (kk < k1) {
-#pragma unroll
-              for (int c = 0; c < 3; ++c) w2[c] = ld(kk + 1, cl - 1 + c);
-              C kv = cmul(cadd(V[kk], b0), w1[1]);
-              kv = cfma(V[M + kk], w0[1], kv);
-              kv = cfma(V[2 * M + kk], w2[1], kv);
-              kv = cfma(bm, w1[0], kv);
-              kv = cfma(bp, w1[2], kv);
+              const int c = kk * M + cl;
+              const C up = kk + 1 < M ? uin[c + M] : zero;
+              const C ul = cm ? uin[c - 1] : zero;
+              const C urr = cp ? uin[c + 1] : zero;
+              C kv = cmul(cadd(V[kk], b0), ucn);
+              kv = cfma(V[M + kk], um, kv);
+              kv = cfma(V[2 * M + kk], up, kv);
+              kv = cfma(bm, ul, kv);
+              kv = cfma(bp, urr, kv);
 #pragma unroll
               for (int q = 0; q < MS; ++q)
                 if (q < nS) {
-                  const C* rowp = ssx[q] < 0 ? w0 : (ssx[q] > 0 ? w2 : w1);
-                  const C v = ssy[q] < 0 ? rowp[0] : (ssy[q] > 0 ? rowp[2] : rowp[1]);
                   const int xx = kk + ssx[q];
+                  const C v = (scol[q] && xx >= 0 && xx < M) ? uin[c + soff[q]] : zero;
                   const C gxv = (has_sep && xx >= 0 && xx < M) ? gxi[xx] : zero;
                   kv = cfma(V[(6 + q) * M + kk], cadd(cscale(v, sy[q]), cmul(gxv, gyp[q])), kv);
                 }
@@ -1638,8 +1695,8 @@ __global__ void __launch_bounds__(BLK) k_solve_mg(const SolveArgs A) {
                 av[j] = caxpy((T)2, kv, av[j]);
               }
               uout[kk * M + cl] = outv;
-#pragma unroll
-              for (int c = 0; c < 3; ++c) { w0[c] = w1[c]; w1[c] = w2[c]; }
+              um = ucn;
+              ucn = up;
             }
           }
         }
