@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--only-solve", action="store_true",
                     help="profiling aid: only the persistent batched solve of --instances for --solve-steps steps")
     ap.add_argument("--solve-steps", type=int, default=2000)
+    ap.add_argument("--only-grad", action="store_true",
+                    help="profiling aid: only the adjoint gradient of the control problem for --grad-steps steps")
+    ap.add_argument("--grad-steps", type=int, default=None)
     return ap.parse_args()
 
 
@@ -228,7 +231,7 @@ def batched_leg(world: int):
     return out
 
 
-def grads_leg():
+def grads_leg(n_steps=None):
     """Gradient of P(|1,0>) at T = 200 ns for the two-mode control problem (64 complex
     piecewise-constant drive segments, K_1, K_2, g: 131 real parameters; 20 480 RK4 steps,
     complex FP64, checkpoint every 160 steps) by the discrete adjoint kernels (bq_grad)."""
@@ -241,10 +244,11 @@ def grads_leg():
     st = bq.State([bq.problem_from_spec(p)], bq.map_opts(dtype="f64", horizon=p.T, dt=p.dt))
     st.grad(p.dt, 320, 160)  # warm-up (modules, workspace)
     torch.cuda.synchronize()
+    steps = p.n_steps if n_steps is None else n_steps
     t0 = time.perf_counter()
-    loss, g = st.grad(p.dt, p.n_steps, 160)
+    loss, g = st.grad(p.dt, steps, 160)
     el = time.perf_counter() - t0
-    return {"workload": "two_mode_control: 2 modes x M=12, 64 pwc segments, 131 parameters, 20480 RK4 steps, "
+    return {"workload": f"two_mode_control: 2 modes x M=12, 64 pwc segments, 131 parameters, {steps} RK4 steps, "
                         "checkpoint every 160, complex FP64",
             "seconds_per_gradient": el, "grads_per_s": 1.0 / el, "loss": float(loss[0]),
             "grad_norm": float(np.linalg.norm(g)), "n_params": int(g.size)}
@@ -302,6 +306,9 @@ def main():
     import paper_2203_05526_gb300 as bq
     from paper_2203_05526_gb300 import build
     build.build()
+    if args.only_grad:
+        print(json.dumps({"only_grad": True, **grads_leg(args.grad_steps)}))
+        return
     if args.only_solve:
         specs = configs_batch(args.instances)
         st = bq.State([bq.problem_from_spec(p) for p in specs], bq.map_opts(dtype=args.dtype, horizon=HORIZON, dt=DT))

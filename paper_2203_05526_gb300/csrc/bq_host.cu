@@ -1073,6 +1073,11 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   const size_t cs = o->dtype == BQ_F64 ? 16 : 8;
   CUDA_TRY(cudaMemsetAsync(base + L.off_y, 0, (size_t)P.total_elems * cs, s));
   CUDA_TRY(cudaMemsetAsync(base + L.off_comp, 0, (size_t)P.total_elems * cs, s));
+  // stage scratch too, so that the padding between a system's blocks (never written by the
+  // stage kernels) holds defined values in every buffer the bulk copies move
+  CUDA_TRY(cudaMemsetAsync(base + L.off_ua, 0, (size_t)P.total_elems * cs, s));
+  CUDA_TRY(cudaMemsetAsync(base + L.off_ub, 0, (size_t)P.total_elems * cs, s));
+  CUDA_TRY(cudaMemsetAsync(base + L.off_acc, 0, (size_t)P.total_elems * cs, s));
   CUDA_TRY(bq::launch_scatter((const InitEntry*)(base + L.off_init), (int)P.init.size(), base + L.off_y, o->dtype, s));
   g_launches++;
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -1176,6 +1181,9 @@ static bq::StageArgs stage_args(bq_state* s, int stage, double dt) {
   return a;
 }
 
+// kernels enqueued by one stage: the pipelined path adds the per-stage coefficient kernel
+static int kernels_per_stage(const bq_state* s, bool recording) { return (s->use_pipe && !recording) ? 2 : 1; }
+
 static cudaError_t launch_any_stage(bq_state* s, const bq::StageArgs& a, cudaStream_t st) {
   if (s->use_pipe && !a.rec) {
     char* b = s->pool;
@@ -1252,13 +1260,13 @@ extern "C" int bq_step(bq_state* s, double dt, int64_t n_steps, void* stream) {
     }
     while (left >= kGraphSteps) {
       CUDA_TRY(cudaGraphLaunch(s->graph, st));
-      g_launches += 4 * kGraphSteps;
+      g_launches += 4 * kGraphSteps * kernels_per_stage(s, false);
       left -= kGraphSteps;
     }
   }
   if (left > 0) {
     CUDA_TRY(enqueue_steps(s, dt, left, st));
-    g_launches += 4 * left;
+    g_launches += 4 * left * kernels_per_stage(s, false);
   }
   s->tau += (double)n_steps * dt;
   return BQ_OK;
@@ -1296,7 +1304,7 @@ extern "C" int bq_step_fixed_scratch(bq_state* s, double dt, int64_t n_steps, vo
       a.u_out = stage == 1 ? (void*)ua : (stage == 2 ? (void*)ub : (stage == 3 ? (void*)ua : nullptr));
       a.acc = acc;
       CUDA_TRY(launch_any_stage(s, a, st));
-      g_launches++;
+      g_launches += kernels_per_stage(s, false);
     }
   s->tau += (double)n_steps * dt;
   return BQ_OK;
@@ -1402,7 +1410,7 @@ static cudaError_t enqueue_steps_rec(bq_state* s, double dt, int64_t n, cudaStre
       a.rec = rec ? rec + ((size_t)i * 4 + stage - 1) * arr : nullptr;
       cudaError_t e = launch_any_stage(s, a, st);
       if (e != cudaSuccess) return e;
-      g_launches++;
+      g_launches += kernels_per_stage(s, a.rec != nullptr);
     }
   return cudaSuccess;
 }
