@@ -827,7 +827,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
       }
       // pipelined stage kernel: parameter blocks per problem, records per system
       {
-        std::vector<int> poff(B, -1), pbytes(B, 0);
+        std::vector<int> poff(B, -1), pbytes(B, 0), pmerged(B, 0);
         size_t blk_max = 0, par_max = 0;
         for (int b = 0; b < B; ++b) {
           const Compiled& C = P.comp[b];
@@ -845,6 +845,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
             for (int q = 0; q < m.nS; ++q) mg = mg && std::abs(m.sSx[q]) <= 1 && std::abs(m.sSy[q]) <= 1;
             // the merged path stores MS = 2 (variant 0) or BQ_M1_MAXT (variant 1) sandwich vectors
             hd.merged = mg ? 1 : 0;
+            pmerged[b] = hd.merged;
           }
           std::vector<unsigned char> blk(sizeof(hd));
           std::memcpy(blk.data(), &hd, sizeof(hd));
@@ -883,6 +884,11 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
           r.gy_off = sd.has_sep ? pg : -1;
           r.r_off = sd.has_r ? (sd.has_sep ? 2 * pg : 0) : -1;
           r.sys = i;
+          r.M = P.comp[sd.prob].M[0];
+          r.merged = pmerged[sd.prob];
+          r.nb = std::max(1, std::min(BQ_PIPE_THREADS / r.M, r.M));
+          r.rb = (r.M + r.nb - 1) / r.nb;
+          r.inv_m = 1.0f / (float)r.M;
           P.precs.push_back(r);
           blk_max = std::max(blk_max, (size_t)r.blk_elems);
         }

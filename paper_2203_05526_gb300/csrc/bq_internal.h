@@ -138,13 +138,17 @@ struct StageArgs {
 
 // Pipelined single-mode stage kernel (k_stage_pipe): one record per system and one
 // parameter block per problem, both fetched with 1-D bulk copies (TMA) into shared memory.
-struct PipeRec {
+struct __align__(16) PipeRec {
   int blk_off;      // element offset of the system block ([G_x | G_y | R] or [R]) in the state arrays
   int blk_elems;    // element count of the block (multiple of 16)
   int param_off;    // byte offset of the problem's parameter block
   int param_bytes;  // its size (multiple of 16)
   int gx_off, gy_off, r_off;  // element offsets inside the block (-1: absent)
   int sys;          // system index (coefficient block)
+  int M;            // grid size of the mode
+  int merged;       // 1: merged-stencil path (every shift in {-1, 0, 1}, M <= 64)
+  int nb, rb;       // merged path: nb column strips of rb rows (thread t: column t % M, strip t / M)
+  float inv_m;      // 1 / M (strip index without an integer division)
 };
 // Header of a parameter block (128 B), followed by dx[M], dy[M] (complex) and the weight tables
 // wX[nX][M], wY[nY][M], wSx[nS][M], wSy[nS][M] (real), the whole block padded to 16 B.
@@ -153,6 +157,7 @@ struct PipeHdr {
   int sX[BQ_M1_MAXT], sY[BQ_M1_MAXT], sSx[BQ_M1_MAXT], sSy[BQ_M1_MAXT];
   int pad2[8];
 };
+#define BQ_PIPE_THREADS 128  // threads of a pipelined stage CTA
 #define BQ_PIPE_COEF 16  // complex coefficients per system and stage: X, Y, S terms, C at slot 15
 
 struct PipeArgs {

@@ -535,8 +535,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-#define BQ_PIPE_THREADS 128
 #define BQ_MERGED_MAXM 64
+#define BQ_PIPE_RB 16  // system records per batch (power of two)
 #define BQ_WAIT_LIMIT (1 << 22)
 
 // Stage coefficients of every system (X, Y, S terms in program order, C at slot 15).
@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
   using C = typename C2T<T>::type;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long full[4];
-  __shared__ PipeRec recs[2][32];
+  __shared__ PipeRec recs[2][BQ_PIPE_RB];  // records of two batches of systems
   __shared__ int s_fail;
 
   const int tid = threadIdx.x;
@@ -587,8 +587,8 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
     s_fail = 0;
   }
   auto load_batch = [&](int b) {
-    if (tid < 32) {
-      const int j = b * 32 + tid;
+    if (tid < BQ_PIPE_RB) {
+      const int j = b * BQ_PIPE_RB + tid;
       if (j < nj) recs[b & 1][tid] = A.recs[blockIdx.x + (size_t)j * G];
     }
   };
@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
   C* mv = reinterpret_cast<C*>(smem_raw + (size_t)S * A.slot_bytes);
   // thread 0: issue the bulk copies of system j into slot j % S
   auto issue = [&](int j) {
-    const PipeRec r = recs[(j >> 5) & 1][j & 31];
+    const PipeRec r = recs[(j / BQ_PIPE_RB) & 1][j % BQ_PIPE_RB];
     unsigned char* sl = slot_ptr(j % S);
     const unsigned blk = (unsigned)(r.blk_elems * cs);
     const unsigned bytes = (unsigned)r.param_bytes + (unsigned)(BQ_PIPE_COEF * cs) + blk;
@@ -619,14 +619,53 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
   C* accg = reinterpret_cast<C*>(A.acc);
   C* compg = reinterpret_cast<C*>(A.comp);
   const T dt = (T)A.dt;
+  const C zero = cmk<C>(0.0, 0.0);
 
   for (int j = 0; j < nj; ++j) {
     const int jn = j + S - 1;
-    if (jn < nj && (jn & 31) == 0) {
-      load_batch(jn >> 5);
+    if (jn < nj && jn % BQ_PIPE_RB == 0) {
+      load_batch(jn / BQ_PIPE_RB);
       __syncthreads();
     }
-    if (tid == 0 && jn < nj) issue(jn);
+    const PipeRec r = recs[(j / BQ_PIPE_RB) & 1][j % BQ_PIPE_RB];
+    // Merged path: this thread's column strip (column l, rows k0..k1-1 of R) and its G item
+    // (index gq of [G_x | G_y], handed out from the last thread down, where the strips are
+    // shortest or absent).  The state, stage sum and compensation of the strip's first two
+    // rows and of the G item are loaded before the wait for the stage input, so that their
+    // latency overlaps the wait and the coefficient set-up.
+    int l = 0, k0 = 0, k1 = 0, gq = -1;
+    C y0 = zero, a0v = zero, c0 = zero, y1 = zero, a1 = zero, c1 = zero;
+    C gyv = zero, gav = zero, gcv = zero;
+    if (r.merged) {
+      const int M = r.M;
+      const int bk = (int)(((float)tid + 0.5f) * r.inv_m);
+      l = tid - bk * M;
+      if (r.r_off >= 0 && bk < r.nb) {
+        k0 = bk * r.rb;
+        k1 = min(M, k0 + r.rb);
+      }
+      const int gi_ = BQ_PIPE_THREADS - 1 - tid;
+      if (r.gx_off >= 0 && gi_ < 2 * M) gq = gi_;
+      if (stage > 1) {
+        const int64_t g0 = (int64_t)r.blk_off + r.r_off + l;
+        if (k0 < k1) {
+          y0 = yg[g0 + k0 * M];
+          a0v = accg[g0 + k0 * M];
+          if (stage == 4) c0 = compg[g0 + k0 * M];
+        }
+        if (k0 + 1 < k1) {
+          y1 = yg[g0 + (k0 + 1) * M];
+          a1 = accg[g0 + (k0 + 1) * M];
+          if (stage == 4) c1 = compg[g0 + (k0 + 1) * M];
+        }
+        if (gq >= 0) {
+          const int64_t gg = (int64_t)r.blk_off + (gq < M ? r.gx_off + gq : r.gy_off + gq - M);
+          gyv = yg[gg];
+          gav = accg[gg];
+          if (stage == 4) gcv = compg[gg];
+        }
+      }
+    }
     // wait for system j (bounded): one thread polls the mbarrier, the others wait at the
     // barrier without issuing; the completed phase also makes the bulk-copied data visible
     {
@@ -645,7 +684,9 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
         return;
       }
     }
-    const PipeRec r = recs[(j >> 5) & 1][j & 31];
+    // every thread is past system j - 1: its slot ((j + S - 1) % S) and the coefficient
+    // vectors are free, so the next copy can start now
+    if (tid == 0 && jn < nj) issue(jn);
     unsigned char* sl = slot_ptr(j % S);
     const PipeHdr& h = *reinterpret_cast<const PipeHdr*>(sl);
     const int M = h.M, nX = h.nX, nY = h.nY, nS = h.nS, has_sep = h.has_sep;
@@ -688,12 +729,35 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
         accg[gi] = caxpy((T)2, kv, accg[gi]);
       }
     };
+    // RK4 combine of one element whose state, stage sum and compensation are in registers
+    auto combine_reg = [&](int64_t gi, C uc, C kv, C yv, C av, C cv) {
+      if (stage == 1) {
+        uout[gi] = caxpy(dt * (T)0.5, kv, uc);
+        accg[gi] = kv;
+      } else if (stage == 4) {
+        const C sm = cadd(av, kv);
+        C d, t, c2;
+        d.x = dt * (T)(1.0 / 6.0) * sm.x - cv.x;
+        d.y = dt * (T)(1.0 / 6.0) * sm.y - cv.y;
+        t.x = yv.x + d.x;
+        t.y = yv.y + d.y;
+        c2.x = (t.x - yv.x) - d.x;
+        c2.y = (t.y - yv.y) - d.y;
+        yg[gi] = t;
+        compg[gi] = c2;
+      } else {
+        uout[gi] = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, yv);
+        accg[gi] = caxpy((T)2, kv, av);
+      }
+    };
 
-    if (h.merged) {
+    if (r.merged) {
       // ---- merged stencil: per-row / per-column coefficient vectors, 3x3 register window ----
       // row vectors: A0 (diagonal + shift-0 X terms), Am (shift -1), Ap (shift +1);
       // column vectors B0, Bm, Bp likewise for the Y terms; per sandwich term t with shifts
       // (sx, sy): SX_t[k] = c_t Wx_t[k], SY_t[l] = Wy_t[l], GX_t[k] = G_x[k+sx], GY_t[l] = Wy_t[l] G_y[l+sy].
+      // The row vectors are built by threads 0..M-1, the column vectors by threads
+      // BQ_MERGED_MAXM..BQ_MERGED_MAXM+M-1 (other warps), concurrently.
       C* A0 = mv;
       C* Am = A0 + M;
       C* Ap = Am + M;
@@ -704,135 +768,111 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
       C* GXv = SXv + MS * M;  // [MS][M]
       C* SYv = GXv + MS * M;  // [MS][M] (real part used)
       C* GYv = SYv + MS * M;  // [MS][M]
-      for (int i = tid; i < M; i += blockDim.x) {
-        C a0 = dx[i], am = cmk<C>(0.0, 0.0), ap = am;
-        C b0 = dy[i], bm = am, bp = am;
+      if (tid < M) {
+        const int i = tid;
+        C a0 = dx[i], am = zero, ap = zero;
 #pragma unroll
         for (int q = 0; q < MX; ++q)
           if (q < nX) {
             const C v = cscale(cf[q], wX[q * M + i]);
             if (h.sX[q] == 0) a0 = cadd(a0, v); else if (h.sX[q] < 0) am = cadd(am, v); else ap = cadd(ap, v);
           }
+        A0[i] = a0; Am[i] = am; Ap[i] = ap;
+#pragma unroll
+        for (int q = 0; q < MS; ++q)
+          if (q < nS) {
+            const int xs = i + h.sSx[q];
+            SXv[q * M + i] = cscale(cf[nX + nY + q], wSx[q * M + i]);
+            GXv[q * M + i] = (has_sep && xs >= 0 && xs < M) ? ugx[xs] : zero;
+          }
+      } else if (tid >= BQ_MERGED_MAXM && tid - BQ_MERGED_MAXM < M) {
+        const int i = tid - BQ_MERGED_MAXM;
+        C b0 = dy[i], bm = zero, bp = zero;
 #pragma unroll
         for (int q = 0; q < MY; ++q)
           if (q < nY) {
             const C v = cscale(cf[nX + q], wY[q * M + i]);
             if (h.sY[q] == 0) b0 = cadd(b0, v); else if (h.sY[q] < 0) bm = cadd(bm, v); else bp = cadd(bp, v);
           }
-        A0[i] = a0; Am[i] = am; Ap[i] = ap;
         B0[i] = b0; Bm[i] = bm; Bp[i] = bp;
 #pragma unroll
         for (int q = 0; q < MS; ++q)
           if (q < nS) {
-            const int xs = i + h.sSx[q], ysh = i + h.sSy[q];
-            SXv[q * M + i] = cscale(cf[nX + nY + q], wSx[q * M + i]);
+            const int ysh = i + h.sSy[q];
             SYv[q * M + i] = cmk<C>((double)wSy[q * M + i], 0.0);
-            GXv[q * M + i] = (has_sep && xs >= 0 && xs < M) ? ugx[xs] : cmk<C>(0.0, 0.0);
-            GYv[q * M + i] = (has_sep && ysh >= 0 && ysh < M) ? cscale(ugy[ysh], wSy[q * M + i]) : cmk<C>(0.0, 0.0);
+            GYv[q * M + i] = (has_sep && ysh >= 0 && ysh < M) ? cscale(ugy[ysh], wSy[q * M + i]) : zero;
           }
       }
       __syncthreads();
-      if (nr) {
-        const int nb = min((int)blockDim.x / M, M);
-        const int rb = (M + nb - 1) / nb;
-        const int l = tid % M, bk = tid / M;
-        if (bk < nb) {
-          const int k0 = bk * rb, k1 = min(M, k0 + rb);
-          const C zero = cmk<C>(0.0, 0.0);
-          const C b0 = B0[l], bm = Bm[l], bp = Bp[l];
-          const bool cm = l > 0, cp = l + 1 < M;  // column neighbours exist
-          T sy[MS];
-          C gy[MS];
-          int ssx[MS], soff[MS];
-          bool scol[MS];
+      if (k0 < k1) {
+        const C b0 = B0[l], bm = Bm[l], bp = Bp[l];
+        const bool cm = l > 0, cp = l + 1 < M;  // column neighbours exist
+        T sy[MS];
+        C gy[MS];
+        int ssx[MS], soff[MS];
+        bool scol[MS];
 #pragma unroll
-          for (int q = 0; q < MS; ++q) {
-            sy[q] = q < nS ? SYv[q * M + l].x : (T)0;
-            gy[q] = q < nS ? GYv[q * M + l] : zero;
-            ssx[q] = h.sSx[q];
-            soff[q] = h.sSx[q] * M + h.sSy[q];
-            scol[q] = q < nS && l + h.sSy[q] >= 0 && l + h.sSy[q] < M;
+        for (int q = 0; q < MS; ++q) {
+          sy[q] = q < nS ? SYv[q * M + l].x : (T)0;
+          gy[q] = q < nS ? GYv[q * M + l] : zero;
+          ssx[q] = h.sSx[q];
+          soff[q] = h.sSx[q] * M + h.sSy[q];
+          scol[q] = q < nS && l + h.sSy[q] >= 0 && l + h.sSy[q] < M;
+        }
+        C um = k0 > 0 ? ur[(k0 - 1) * M + l] : zero;  // u(k-1, l)
+        C uc = ur[k0 * M + l];                          // u(k, l)
+        // state / stage sum / compensation: a register ring two rows ahead of use
+        for (int kk = k0; kk < k1; ++kk) {
+          const int pos = r.r_off + kk * M + l;
+          const int64_t gi = (int64_t)r.blk_off + pos;
+          const C yv = y0, av = a0v, cv = c0;
+          y0 = y1; a0v = a1; c0 = c1;
+          if (stage > 1 && kk + 2 < k1) {
+            y1 = yg[gi + 2 * M];
+            a1 = accg[gi + 2 * M];
+            if (stage == 4) c1 = compg[gi + 2 * M];
           }
-          C um = k0 > 0 ? ur[(k0 - 1) * M + l] : zero;  // u(k-1, l)
-          C uc = ur[k0 * M + l];                          // u(k, l)
-          // state / stage sum / compensation, loaded two rows ahead of use (register ring)
-          const int64_t g0 = (int64_t)r.blk_off + r.r_off + l;
-          C y0 = zero, a0v = zero, c0 = zero, y1 = zero, a1 = zero, c1 = zero;
-          if (stage > 1) {
-            if (k0 < k1) { y0 = yg[g0 + k0 * M]; a0v = accg[g0 + k0 * M]; if (stage == 4) c0 = compg[g0 + k0 * M]; }
-            if (k0 + 1 < k1) { y1 = yg[g0 + (k0 + 1) * M]; a1 = accg[g0 + (k0 + 1) * M]; if (stage == 4) c1 = compg[g0 + (k0 + 1) * M]; }
-          }
-          for (int kk = k0; kk < k1; ++kk) {
-            const int pos = r.r_off + kk * M + l;
-            const int64_t gi = (int64_t)r.blk_off + pos;
-            const C yv = y0, av = a0v, cv = c0;
-            y0 = y1; a0v = a1; c0 = c1;
-            if (stage > 1 && kk + 2 < k1) {
-              y1 = yg[gi + 2 * M];
-              a1 = accg[gi + 2 * M];
-              if (stage == 4) c1 = compg[gi + 2 * M];
-            }
-            const int c = kk * M + l;
-            const C up = kk + 1 < M ? ur[c + M] : zero;
-            const C ul = cm ? ur[c - 1] : zero;
-            const C urr = cp ? ur[c + 1] : zero;
-            C kv = cmul(cadd(A0[kk], b0), uc);
-            kv = cfma(Am[kk], um, kv);
-            kv = cfma(Ap[kk], up, kv);
-            kv = cfma(bm, ul, kv);
-            kv = cfma(bp, urr, kv);
+          const int c = kk * M + l;
+          const C up = kk + 1 < M ? ur[c + M] : zero;
+          const C ul = cm ? ur[c - 1] : zero;
+          const C urr = cp ? ur[c + 1] : zero;
+          C kv = cmul(cadd(A0[kk], b0), uc);
+          kv = cfma(Am[kk], um, kv);
+          kv = cfma(Ap[kk], up, kv);
+          kv = cfma(bm, ul, kv);
+          kv = cfma(bp, urr, kv);
 #pragma unroll
-            for (int q = 0; q < MS; ++q)
-              if (q < nS) {
-                const int xx = kk + ssx[q];
-                const C v = (scol[q] && xx >= 0 && xx < M) ? ur[c + soff[q]] : zero;
-                kv = cfma(SXv[q * M + kk], cadd(cscale(v, sy[q]), cmul(GXv[q * M + kk], gy[q])), kv);
-              }
-            if (stage == 1) {
-              uout[gi] = caxpy(dt * (T)0.5, kv, uc);
-              accg[gi] = kv;
-            } else if (stage == 4) {
-              const C sm = cadd(av, kv);
-              C d, t, c2;
-              d.x = dt * (T)(1.0 / 6.0) * sm.x - cv.x;
-              d.y = dt * (T)(1.0 / 6.0) * sm.y - cv.y;
-              t.x = yv.x + d.x;
-              t.y = yv.y + d.y;
-              c2.x = (t.x - yv.x) - d.x;
-              c2.y = (t.y - yv.y) - d.y;
-              yg[gi] = t;
-              compg[gi] = c2;
-            } else {
-              uout[gi] = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, yv);
-              accg[gi] = caxpy((T)2, kv, av);
+          for (int q = 0; q < MS; ++q)
+            if (q < nS) {
+              const int xx = kk + ssx[q];
+              const C v = (scol[q] && xx >= 0 && xx < M) ? ur[c + soff[q]] : zero;
+              kv = cfma(SXv[q * M + kk], cadd(cscale(v, sy[q]), cmul(GXv[q * M + kk], gy[q])), kv);
             }
-            um = uc;
-            uc = up;
-          }
+          combine_reg(gi, uc, kv, yv, av, cv);
+          um = uc;
+          uc = up;
         }
       }
-      if (has_sep) {
-        for (int i = tid; i < 2 * M; i += blockDim.x) {
-          const bool isx = i < M;
-          const int g = isx ? i : i - M;
-          const C* gs = isx ? ugx : ugy;
-          const C uc = gs[g];
-          const C zero = cmk<C>(0.0, 0.0);
-          const C lo = g > 0 ? gs[g - 1] : zero, hi = g + 1 < M ? gs[g + 1] : zero;
-          C kv;
-          if (isx) {
-            kv = cmul(cadd(A0[g], Cc), uc);
-            kv = cfma(Am[g], lo, kv);
-            kv = cfma(Ap[g], hi, kv);
-          } else {
-            kv = cmul(cadd(B0[g], cmk<C>(-(double)Cc.x, -(double)Cc.y)), uc);
-            kv = cfma(Bm[g], lo, kv);
-            kv = cfma(Bp[g], hi, kv);
-          }
-          combine_at((isx ? r.gx_off : r.gy_off) + g, uc, kv);
+      if (gq >= 0) {
+        const bool isx = gq < M;
+        const int g = isx ? gq : gq - M;
+        const C* gs = isx ? ugx : ugy;
+        const C uc = gs[g];
+        const C lo = g > 0 ? gs[g - 1] : zero, hi = g + 1 < M ? gs[g + 1] : zero;
+        C kv;
+        if (isx) {
+          kv = cmul(cadd(A0[g], Cc), uc);
+          kv = cfma(Am[g], lo, kv);
+          kv = cfma(Ap[g], hi, kv);
+        } else {
+          kv = cmul(cadd(B0[g], cmk<C>(-(double)Cc.x, -(double)Cc.y)), uc);
+          kv = cfma(Bm[g], lo, kv);
+          kv = cfma(Bp[g], hi, kv);
         }
+        combine_reg((int64_t)r.blk_off + (isx ? r.gx_off : r.gy_off) + g, uc, kv, gyv, gav, gcv);
       }
-      __syncthreads();
+      // no barrier here: the wait at the top of the next system orders the reuse of the
+      // slot and of the coefficient vectors
       continue;
     }
 
@@ -894,8 +934,8 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
       }
       combine_at(pos, uc, kv);
     }
-    __syncthreads();
   }
+  __syncthreads();  // every system of this CTA is written before it takes its ticket
   if (stage == 4 && tid == 0) {
     __threadfence();
     const unsigned int t = atomicAdd(A.ticket, 1u);
