@@ -527,6 +527,17 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return done != 0;
 }
+// try_wait with a suspend-time hint (ns): the thread sleeps until the phase completes or the
+// hint elapses instead of spinning through short polls
+__device__ __forceinline__ bool mbar_try_wait_for(unsigned long long* bar, unsigned parity, unsigned ns) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return done != 0;
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    smem_u32(dst)),
@@ -538,6 +549,8 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 #define BQ_MERGED_MAXM 64
 #define BQ_PIPE_RB 16  // system records per batch (power of two)
 #define BQ_WAIT_LIMIT (1 << 22)
+#define BQ_WAIT_SUSPENDS (1 << 16)  // suspended polls of at most BQ_WAIT_HINT_NS each (< 1 s in all)
+#define BQ_WAIT_HINT_NS 10000u
 
 // Stage coefficients of every system (X, Y, S terms in program order, C at slot 15).
 template <typename T>
@@ -672,8 +685,8 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
       bool ok = true;
       if (tid == 0) {
         ok = false;
-        for (int it = 0; it < BQ_WAIT_LIMIT; ++it)
-          if (mbar_try_wait(&full[j % S], (unsigned)((j / S) & 1))) { ok = true; break; }
+        for (int it = 0; it < BQ_WAIT_SUSPENDS; ++it)
+          if (mbar_try_wait_for(&full[j % S], (unsigned)((j / S) & 1), BQ_WAIT_HINT_NS)) { ok = true; break; }
       }
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicOr(A.error, 1u);
