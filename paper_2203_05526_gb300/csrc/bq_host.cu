@@ -587,7 +587,7 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
 // State.
 // ---------------------------------------------------------------------------------------
 struct Layout {
-  size_t off_sys, off_terms, off_chans, off_chpar, off_work, off_m1, off_order, off_dc, off_pparams, off_precs, off_pcoef, off_groups, off_entries, off_out, off_wtab, off_diag,
+  size_t off_sys, off_terms, off_chans, off_chpar, off_work, off_m1, off_order, off_dc, off_pparams, off_precs, off_pcoef, off_pcdyn, off_groups, off_entries, off_out, off_wtab, off_diag,
       off_ctrl, off_init, off_y, off_comp, off_ua, off_ub, off_acc, total;
 };
 
@@ -597,6 +597,7 @@ struct bq_state {
   int solve_ok = 0, solve_smem = 0, last_solve_grid = 0, solve_mg = 0, solve_mg_smem = 0;
   int use_pipe = 0, pipe_off_coef = 0, pipe_off_u = 0, pipe_off_y = 0, pipe_off_acc = 0, pipe_off_comp = 0;
   int pipe_slot[3] = {0, 0, 0}, pipe_nslots[3] = {2, 2, 2}, pipe_grid[3] = {1, 1, 1}, pipe_mv_bytes = 0;
+  int n_coef_dyn = 0;  // time-dependent stage coefficients (k_coef_dyn entries)
   int grad_size = 0, adj_smem = 0, srcred_stride = 0, max_s = 0;
   std::vector<TermDesc> terms_host;
   std::vector<ChanDesc> chans_host;
@@ -642,6 +643,8 @@ struct Plan {
   int pipe_slot[3] = {0, 0, 0};
   std::vector<unsigned char> pparams;
   std::vector<bq::PipeRec> precs;
+  std::vector<cplx> pcoef;           // stage coefficients that do not depend on time (n_sys x BQ_PIPE_COEF)
+  std::vector<bq::CoefDyn> pcdyn;    // and the entries that do
   int solve_smem = 0;
   int solve_mg = 0, solve_mg_smem = 0;  // merged-stencil persistent solve
   int adj_smem = 0;  // shared memory of the adjoint stage kernel
@@ -892,6 +895,27 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
           P.precs.push_back(r);
           blk_max = std::max(blk_max, (size_t)r.blk_elems);
         }
+        // stage coefficients: X, Y, S terms in program order, the separation constant C at the
+        // last position; static ones now, drive-dependent ones per stage on the device
+        P.pcoef.assign(P.sys.size() * BQ_PIPE_COEF, cplx(0.0, 0.0));
+        for (int i = 0; i < (int)P.m1.size(); ++i) {
+          const bq::M1Sys& m = P.m1[i];
+          P.pcoef[(size_t)i * BQ_PIPE_COEF + BQ_PIPE_COEF - 1] = cplx(m.c_re, m.c_im);
+          const int nt = m.nX + m.nY + m.nS;
+          for (int q = 0; q < nt && q < BQ_PIPE_COEF - 1; ++q) {
+            const int t = q < m.nX ? m.tX[q] : (q < m.nX + m.nY ? m.tY[q - m.nX] : m.tS[q - m.nX - m.nY]);
+            const TermDesc& td = P.terms[m.term_off + t];
+            if (td.ch < 0) {
+              P.pcoef[(size_t)i * BQ_PIPE_COEF + q] = cplx(td.c_re, td.c_im);
+            } else {
+              bq::CoefDyn d;
+              std::memset(&d, 0, sizeof(d));
+              d.slot = i * BQ_PIPE_COEF + q;
+              d.ch = td.ch; d.conj = td.conj; d.c_re = td.c_re; d.c_im = td.c_im;
+              P.pcdyn.push_back(d);
+            }
+          }
+        }
         auto a128 = [](size_t x) { return (x + 127) & ~(size_t)127; };
         P.pipe_off_coef = (int)a128(par_max);
         P.pipe_off_u = P.pipe_off_coef + (int)a128(BQ_PIPE_COEF * cs);
@@ -999,6 +1023,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
   L.off_pparams = seg(P.pparams.size());
   L.off_precs = seg(P.precs.size() * sizeof(bq::PipeRec));
   L.off_pcoef = seg(P.use_pipe ? (size_t)P.sys.size() * BQ_PIPE_COEF * cs : 0);
+  L.off_pcdyn = seg(P.use_pipe ? P.pcdyn.size() * sizeof(bq::CoefDyn) : 0);
   L.off_dc = seg(P.dc.size() * sizeof(double2));
   L.off_groups = seg(P.groups.size() * sizeof(EvalGroup));
   L.off_entries = seg(P.entries.size() * sizeof(EvalEntry));
@@ -1055,6 +1080,18 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   CUDA_TRY(up(L.off_order, P.order.data(), P.order.size() * sizeof(int)));
   CUDA_TRY(up(L.off_pparams, P.pparams.data(), P.pparams.size()));
   CUDA_TRY(up(L.off_precs, P.precs.data(), P.precs.size() * sizeof(bq::PipeRec)));
+  if (P.use_pipe) {
+    CUDA_TRY(up(L.off_pcdyn, P.pcdyn.data(), P.pcdyn.size() * sizeof(bq::CoefDyn)));
+    if (o->dtype == BQ_F64) {
+      std::vector<double2> c(P.pcoef.size());
+      for (size_t i = 0; i < c.size(); ++i) c[i] = make_double2(P.pcoef[i].real(), P.pcoef[i].imag());
+      CUDA_TRY(up(L.off_pcoef, c.data(), c.size() * sizeof(double2)));
+    } else {
+      std::vector<float2> c(P.pcoef.size());
+      for (size_t i = 0; i < c.size(); ++i) c[i] = make_float2((float)P.pcoef[i].real(), (float)P.pcoef[i].imag());
+      CUDA_TRY(up(L.off_pcoef, c.data(), c.size() * sizeof(float2)));
+    }
+  }
   {
     std::vector<double2> dcv(P.dc.size());
     for (size_t i = 0; i < dcv.size(); ++i) dcv[i] = make_double2(P.dc[i].real(), P.dc[i].imag());
@@ -1104,6 +1141,7 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   st->m1_variant = P.m1_variant;
   st->solve_ok = P.order.empty() ? 0 : 1;
   st->use_pipe = P.use_pipe;
+  st->n_coef_dyn = (int)P.pcdyn.size();
   st->pipe_off_coef = P.pipe_off_coef; st->pipe_off_u = P.pipe_off_u; st->pipe_off_y = P.pipe_off_y;
   st->pipe_off_acc = P.pipe_off_acc; st->pipe_off_comp = P.pipe_off_comp;
   for (int q = 0; q < 3; ++q) st->pipe_slot[q] = P.pipe_slot[q];
@@ -1187,8 +1225,11 @@ static bq::StageArgs stage_args(bq_state* s, int stage, double dt) {
   return a;
 }
 
-// kernels enqueued by one stage: the pipelined path adds the per-stage coefficient kernel
-static int kernels_per_stage(const bq_state* s, bool recording) { return (s->use_pipe && !recording) ? 2 : 1; }
+// kernels enqueued by one stage: the pipelined path adds the coefficient kernel when some
+// coefficient depends on time
+static int kernels_per_stage(const bq_state* s, bool recording) {
+  return (s->use_pipe && !recording && s->n_coef_dyn > 0) ? 2 : 1;
+}
 
 static cudaError_t launch_any_stage(bq_state* s, const bq::StageArgs& a, cudaStream_t st) {
   if (s->use_pipe && !a.rec) {
@@ -1211,11 +1252,12 @@ static cudaError_t launch_any_stage(bq_state* s, const bq::StageArgs& a, cudaStr
     pa.dt = a.dt;
     bq::CoefArgs ca;
     std::memset(&ca, 0, sizeof(ca));
-    ca.m1 = (const bq::M1Sys*)(b + L.off_m1);
-    ca.sys = a.sys; ca.terms = a.terms; ca.chans = a.chans; ca.chpar = a.chpar;
+    ca.dyn = (const bq::CoefDyn*)(b + L.off_pcdyn);
+    ca.n_dyn = s->n_coef_dyn;
+    ca.chans = a.chans; ca.chpar = a.chpar;
     ca.coef = b + L.off_pcoef;
     ca.tau_base = a.tau_base; ca.counter = a.counter;
-    ca.dt = a.dt; ca.horizon = a.horizon; ca.n_sys = s->n_sys; ca.stage = a.stage; ca.reverse = a.reverse;
+    ca.dt = a.dt; ca.horizon = a.horizon; ca.stage = a.stage; ca.reverse = a.reverse;
     return bq::launch_stage_pipe(pa, ca, s->m1_variant, s->dtype, s->pipe_grid[q], pa.n_slots * pa.slot_bytes + s->pipe_mv_bytes,
                                  st);
   }

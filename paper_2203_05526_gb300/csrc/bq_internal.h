@@ -177,17 +177,23 @@ struct PipeArgs {
   double dt;
 };
 
+// A stage coefficient that depends on time: slot `slot` of the coefficient array (system
+// * BQ_PIPE_COEF + position) = c * chan(tau) (or c * conj(chan(tau))).  Static slots are
+// written once when the problem is mapped.
+struct CoefDyn {
+  int slot, ch, conj, pad;
+  double c_re, c_im;
+};
+
 struct CoefArgs {
-  const M1Sys* m1;
-  const SysDesc* sys;
-  const TermDesc* terms;
+  const CoefDyn* dyn;
   const ChanDesc* chans;
   const double* chpar;
   void* coef;
   const double* tau_base;
   const long long* counter;
   double dt, horizon;
-  int n_sys, stage, reverse, pad;
+  int n_dyn, stage, reverse, pad;
 };
 
 // Arguments of the batched persistent solve (k_solve_m1).

@@ -552,33 +552,20 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 #define BQ_WAIT_SUSPENDS (1 << 16)  // suspended polls of at most BQ_WAIT_HINT_NS each (< 1 s in all)
 #define BQ_WAIT_HINT_NS 10000u
 
-// Stage coefficients of every system (X, Y, S terms in program order, C at slot 15).
+// Time-dependent stage coefficients (drive envelopes at the stage time; a piecewise-constant
+// envelope at the step midpoint): one thread per entry.
 template <typename T>
-__global__ void k_coef_m1(const CoefArgs A) {
+__global__ void k_coef_dyn(const CoefArgs A) {
   using C = typename C2T<T>::type;
-  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gi >= A.n_sys * BQ_PIPE_COEF) return;
-  const int si = gi / BQ_PIPE_COEF, q = gi - si * BQ_PIPE_COEF;
-  const M1Sys& m = A.m1[si];
-  C* out = reinterpret_cast<C*>(A.coef) + gi;
-  if (q == BQ_PIPE_COEF - 1) {
-    *out = cmk<C>(m.c_re, m.c_im);
-    return;
-  }
-  const int nt = m.nX + m.nY + m.nS;
-  if (q >= nt) { *out = cmk<C>(0.0, 0.0); return; }
-  const int t = q < m.nX ? m.tX[q] : (q < m.nX + m.nY ? m.tY[q - m.nX] : m.tS[q - m.nX - m.nY]);
-  const TermDesc& td = A.terms[m.term_off + t];
-  double2 c = make_double2(td.c_re, td.c_im);
-  if (td.ch >= 0) {
-    const double ts = A.tau_base[0] + (double)(*A.counter) * A.dt;
-    const ChanDesc cd = A.chans[td.ch];
-    const double tau = (cd.kind == 2) ? ts + 0.5 * A.dt : ts + stage_c(A.stage) * A.dt;
-    double2 e = chan_value_t<T>(cd, A.chpar, A.reverse ? A.horizon - tau : tau);
-    if (td.conj) e.y = -e.y;
-    c = make_double2(c.x * e.x - c.y * e.y, c.x * e.y + c.y * e.x);
-  }
-  *out = cmk<C>(c.x, c.y);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n_dyn) return;
+  const CoefDyn d = A.dyn[i];
+  const double ts = A.tau_base[0] + (double)(*A.counter) * A.dt;
+  const ChanDesc cd = A.chans[d.ch];
+  const double tau = (cd.kind == 2) ? ts + 0.5 * A.dt : ts + stage_c(A.stage) * A.dt;
+  double2 e = chan_value_t<T>(cd, A.chpar, A.reverse ? A.horizon - tau : tau);
+  if (d.conj) e.y = -e.y;
+  reinterpret_cast<C*>(A.coef)[d.slot] = cmk<C>(d.c_re * e.x - d.c_im * e.y, d.c_re * e.y + d.c_im * e.x);
 }
 
 template <typename T, int MX, int MY, int MS>
@@ -2096,10 +2083,11 @@ static cudaError_t launch_pipe_t(const PipeArgs& a, const CoefArgs& c, int grid,
   auto kern = k_stage_pipe<T, MXYS, MXYS, MXYS>;
   cudaError_t ea = pipe_attrs();
   if (ea != cudaSuccess) return ea;
-  const int nc = c.n_sys * BQ_PIPE_COEF;
-  k_coef_m1<T><<<(nc + 255) / 256, 256, 0, s>>>(c);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (c.n_dyn > 0) {
+    k_coef_dyn<T><<<(c.n_dyn + 255) / 256, 256, 0, s>>>(c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   kern<<<grid, BQ_PIPE_THREADS, smem_bytes, s>>>(a);
   return cudaGetLastError();
 }
