@@ -544,6 +544,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// L2 prefetch of a contiguous global range (16-byte aligned start, size a multiple of 16)
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 #define BQ_MERGED_MAXM 64
@@ -610,6 +614,13 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
     bulk_g2s(sl + A.off_coef, reinterpret_cast<const C*>(A.coef) + (size_t)r.sys * BQ_PIPE_COEF,
              (unsigned)(BQ_PIPE_COEF * cs), bar);
     bulk_g2s(sl + A.off_u, reinterpret_cast<const C*>(A.u_in) + r.blk_off, blk, bar);
+    // the state, stage sum and compensation of that system are read with per-thread loads:
+    // bring them into L2 now, one system ahead of use
+    if (stage > 1) {
+      bulk_prefetch_l2(reinterpret_cast<const C*>(A.y) + r.blk_off, blk);
+      bulk_prefetch_l2(reinterpret_cast<const C*>(A.acc) + r.blk_off, blk);
+      if (stage == 4) bulk_prefetch_l2(reinterpret_cast<const C*>(A.comp) + r.blk_off, blk);
+    }
   };
   if (tid == 0)
     for (int j = 0; j < S - 1 && j < nj; ++j) issue(j);
