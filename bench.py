@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--only-grad", action="store_true",
                     help="profiling aid: only the adjoint gradient of the control problem for --grad-steps steps")
     ap.add_argument("--grad-steps", type=int, default=None)
+    ap.add_argument("--n-range", type=int, nargs=2, default=(10, 40), metavar=("LO", "HI"),
+                    help="profiling aid: Fock truncation range of the kerr_batch instances (default 10 40)")
     return ap.parse_args()
 
 
@@ -73,11 +75,32 @@ def shard_range(n_inst: int, rank: int):
     return range(n_inst * rank, n_inst * (rank + 1))
 
 
+N_RANGE = (10, 40)  # Fock truncation range of the instances (--n-range)
+
+# DRAM traffic of the stage kernel per launch (mean over the four RK4 stages), from one ncu
+# capture of dram__bytes_read.sum + dram__bytes_write.sum on the default workload (65 536
+# instances, N 10..40, complex FP32); reported only while the kernel source is the one that
+# was measured and the workload is the default one.
+STAGE_TRAFFIC = {"kernel_sha256": "2dddec0473b926e8464afbe68f639129d36ef6018e5a4811dd7c75d9dad02d3a",
+                 "instances": 65536, "n_range": (10, 40), "dtype": "f32", "bytes_per_launch": 1.9689e9}
+
+
+def measured_traffic(instances: int, dtype: str):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2203_05526_gb300", "csrc", "bq_kernels.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    t = STAGE_TRAFFIC
+    if sha != t["kernel_sha256"] or instances != t["instances"] or tuple(N_RANGE) != t["n_range"] or dtype != t["dtype"]:
+        return None
+    return t["bytes_per_launch"]
+
+
 def workload(n_inst: int, rank: int):
     """Instances of this rank: the seeded stream of kerr_batch, rank-major shards."""
     from workloads import configs
     r = shard_range(n_inst, rank)
-    allp = configs.kerr_batch(B=r.stop, T=HORIZON, dt=DT)
+    allp = configs.kerr_batch(B=r.stop, T=HORIZON, dt=DT, n_min=N_RANGE[0], n_max=N_RANGE[1])
     return allp[r.start:r.stop]
 
 
@@ -94,7 +117,7 @@ def max_over_ranks(ms: float, world: int, device=None) -> float:
 
 def configs_batch(n: int):
     from workloads import configs
-    return configs.kerr_batch(B=n, T=HORIZON, dt=DT)
+    return configs.kerr_batch(B=n, T=HORIZON, dt=DT, n_min=N_RANGE[0], n_max=N_RANGE[1])
 
 
 def points_of(specs):
@@ -290,7 +313,9 @@ def run_reference(args, rank, world):
 
 
 def main():
+    global N_RANGE
     args = parse()
+    N_RANGE = (int(args.n_range[0]), int(args.n_range[1]))
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -376,7 +401,7 @@ def main():
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": {"pipelined": "bq::k_stage_pipe", "single_mode": "bq::k_stage_m1",
+            "traffic": measured_traffic(args.instances, args.dtype), "kernel": {"pipelined": "bq::k_stage_pipe", "single_mode": "bq::k_stage_m1",
                                                "generic": "bq::k_stage"}[state.stage_variant()], "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "bytes_per_launch": bytes_per_launch, "avg_launch_us": launch_s * 1e6}
 
@@ -423,7 +448,7 @@ def main():
                 "config": {"workload": f"kerr_batch x{args.instances}: driven damped Kerr oscillators, "
                                        f"mapped method (G_x, G_y, full R), one RK4 step of dt={DT} ns + "
                                        "Tr(rho0 A) per instance per step",
-                           "instances_per_gpu": args.instances, "grid_points_per_gpu": pts,
+                           "instances_per_gpu": args.instances, "n_range": list(N_RANGE), "grid_points_per_gpu": pts,
                            "state_bytes_per_array": nbytes, "l2": "inputs larger than L2 (4 arrays x "
                            f"{nbytes / 1e6:.0f} MB vs 129 MB)", "parallelism": f"replicas x{world}"},
                 "roofline": roof, "e2e": e2e, "batched": batched, "grads": grads, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches}

@@ -598,6 +598,7 @@ struct bq_state {
   int use_pipe = 0, pipe_off_coef = 0, pipe_off_u = 0, pipe_off_y = 0, pipe_off_acc = 0, pipe_off_comp = 0;
   int pipe_slot[3] = {0, 0, 0}, pipe_nslots[3] = {2, 2, 2}, pipe_grid[3] = {1, 1, 1}, pipe_mv_bytes = 0;
   int n_coef_dyn = 0;  // time-dependent stage coefficients (k_coef_dyn entries)
+  int ng_max = 0;      // largest G_x / G_y point count over the systems
   int grad_size = 0, adj_smem = 0, srcred_stride = 0, max_s = 0;
   std::vector<TermDesc> terms_host;
   std::vector<ChanDesc> chans_host;
@@ -1168,6 +1169,7 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   st->grad_size = P.grad_size;
   st->adj_smem = P.adj_smem;
   st->srcred_stride = P.srcred_stride;
+  for (const SysDesc& sd : P.sys) st->ng_max = std::max(st->ng_max, sd.n_g);
   st->max_s = P.max_s;
   st->terms_host = P.terms;
   st->chans_host = P.chans;
@@ -1528,6 +1530,7 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
   a.horizon = s->horizon;
   a.reverse = s->reverse;
   a.srcred_stride = s->srcred_stride;
+  a.ng_max = s->ng_max;
   for (int64_t c = G.n_ckpt - 1; c >= 0; --c) {
     const int64_t n0 = c * k, n1 = std::min<int64_t>(n_steps, n0 + k);
     // recompute the segment from its checkpoint, recording every stage input

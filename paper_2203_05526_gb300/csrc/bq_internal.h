@@ -232,7 +232,8 @@ struct AdjArgs {
   const void* srcred;    // transposed-source reductions, srcred_stride complex per system
   double* grad;          // gradient slots
   double tau_step, dt, horizon;
-  int reverse, stage, srcred_stride, pad;
+  int reverse, stage, srcred_stride;
+  int ng_max;            // largest n_g (G_x / G_y points) over the systems
 };
 
 }  // namespace bq

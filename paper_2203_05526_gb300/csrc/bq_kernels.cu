@@ -1439,12 +1439,17 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
 // Transposed separable source: for every system and sandwich term t
 //   v_t[kx] = sum_ly b_R[kx, ly] Wy_t(ly) G_y[ly + sy],   w_t[ly] = sum_kx b_R[kx, ly] Wx_t(kx) G_x[kx + sx]
 // (G_x, G_y of the recorded stage input; b_R = dt/6 lam at stage 4).  grid = (systems, max S terms, 2).
+#define BQ_SRC_THREADS 256
+#define BQ_SRC_TILE 32     // outputs per CTA
+#define BQ_SRC_ZCH 1024    // summed-index chunk held in shared memory
 template <typename T, int NM>
-__global__ void __launch_bounds__(BQ_BLOCK) k_adj_src(const AdjArgs A) {
+__global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
   using C = typename C2T<T>::type;
+  __shared__ C z[BQ_SRC_ZCH];
+  __shared__ C red[BQ_SRC_THREADS / 32][BQ_SRC_TILE];
   const SysDesc& sd = A.sys[blockIdx.x];
   if (!sd.has_sep || !sd.has_r) return;
-  // find the blockIdx.y-th sandwich term of the system
+  // the blockIdx.y-th sandwich term of the system
   int t = -1, s = 0;
   for (int q = 0; q < sd.n_terms; ++q)
     if (A.terms[sd.term_off + q].side == SIDE_S) {
@@ -1453,8 +1458,11 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_src(const AdjArgs A) {
     }
   if (t < 0) return;
   const TermDesc td = A.terms[sd.term_off + t];
-  const int dirx = blockIdx.z == 0;  // 0: v_t over kx (sum over ly), 1: w_t over ly (sum over kx)
+  const int dirx = (blockIdx.z & 1) == 0;  // 1: v_t over kx (sum over ly), 0: w_t over ly (sum over kx)
+  const int i0 = (int)(blockIdx.z >> 1) * BQ_SRC_TILE;
   const int ng = sd.n_g;
+  if (i0 >= ng) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T dt = (T)A.dt;
   const T bscale = A.stage == 4 ? dt * (T)(1.0 / 6.0) : (T)1;
   const C* bsrc = reinterpret_cast<const C*>(A.stage == 4 ? A.lam : A.b_in) + sd.off_r;
@@ -1462,12 +1470,18 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_src(const AdjArgs A) {
   const C* other = U + (dirx ? sd.off_gy : sd.off_gx);
   const T* W = reinterpret_cast<const T*>(A.wtab);
   const int delta = dirx ? td.deltaGy : td.deltaGx;
-  C* out = reinterpret_cast<C*>(const_cast<void*>(A.srcred)) + (int64_t)blockIdx.x * A.srcred_stride +
-           (s * 2 + (dirx ? 0 : 1)) * ng;
-  for (int i = threadIdx.x; i < ng; i += blockDim.x) {
-    C acc = cmk<C>(0.0, 0.0);
-    for (int j = 0; j < ng; ++j) {
-      // j runs over the summed index (ly for v_t, kx for w_t); weight of the other side's part
+  // out[i] = bscale sum_j B(i, j) z[j], z[j] = w(j) other[j + delta], with B(i, j) the R
+  // cotangent at (i, j) (dirx) or (j, i), and w(j) the product of the term's weights on the
+  // summed side.  Chunks of z go through shared memory; the sums run in a fixed order.
+  C acc[BQ_SRC_TILE / (BQ_SRC_THREADS / 32)];
+#pragma unroll
+  for (int r = 0; r < BQ_SRC_TILE / (BQ_SRC_THREADS / 32); ++r) acc[r] = cmk<C>(0.0, 0.0);
+  C accc = cmk<C>(0.0, 0.0);
+  for (int jc = 0; jc < ng; jc += BQ_SRC_ZCH) {
+    const int nj = min(BQ_SRC_ZCH, ng - jc);
+    __syncthreads();  // the previous chunk is consumed
+    for (int jj = tid; jj < nj; jj += BQ_SRC_THREADS) {
+      const int j = jc + jj;
       int rem = j;
       int id[NM];
 #pragma unroll
@@ -1479,11 +1493,50 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_src(const AdjArgs A) {
         if (isx == (bool)dirx) continue;  // only the summed side's dims
         w *= W[td.wtab[a] + id[isx ? d : d - NM]];
       }
-      if (w == (T)0) continue;
-      const C b = dirx ? bsrc[(int64_t)i * ng + j] : bsrc[(int64_t)j * ng + i];
-      acc = cfma(cscale(b, w), other[j + delta], acc);
+      z[jj] = w == (T)0 ? cmk<C>(0.0, 0.0) : cscale(other[j + delta], w);
     }
-    out[i] = cscale(acc, bscale);
+    __syncthreads();
+    if (dirx) {
+      // rows i0 + warp * R + r: lanes stride over j (coalesced along the row)
+#pragma unroll
+      for (int r = 0; r < BQ_SRC_TILE / (BQ_SRC_THREADS / 32); ++r) {
+        const int i = i0 + warp * (BQ_SRC_TILE / (BQ_SRC_THREADS / 32)) + r;
+        if (i < ng) {
+          const C* row = bsrc + (int64_t)i * ng + jc;
+          for (int jj = lane; jj < nj; jj += 32) acc[r] = cfma(row[jj], z[jj], acc[r]);
+        }
+      }
+    } else {
+      // column i0 + lane: warps split j (coalesced across lanes)
+      const int i = i0 + lane;
+      if (i < ng)
+        for (int jj = warp; jj < nj; jj += BQ_SRC_THREADS / 32)
+          accc = cfma(bsrc[(int64_t)(jc + jj) * ng + i], z[jj], accc);
+    }
+  }
+  C* out = reinterpret_cast<C*>(const_cast<void*>(A.srcred)) + (int64_t)blockIdx.x * A.srcred_stride +
+           (s * 2 + (dirx ? 0 : 1)) * ng;
+  if (dirx) {
+#pragma unroll
+    for (int r = 0; r < BQ_SRC_TILE / (BQ_SRC_THREADS / 32); ++r) {
+      C v = acc[r];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+      }
+      const int i = i0 + warp * (BQ_SRC_TILE / (BQ_SRC_THREADS / 32)) + r;
+      if (lane == 0 && i < ng) out[i] = cscale(v, bscale);
+    }
+  } else {
+    red[warp][lane] = accc;
+    __syncthreads();
+    if (warp == 0) {
+      C v = red[0][lane];
+      for (int w2 = 1; w2 < BQ_SRC_THREADS / 32; ++w2) v = cadd(v, red[w2][lane]);
+      const int i = i0 + lane;
+      if (i < ng) out[i] = cscale(v, bscale);
+    }
   }
 }
 
@@ -2040,7 +2093,8 @@ static cudaError_t launch_adj_t(const AdjArgs& a, int n_work, int smem_bytes, in
     attr_set = true;
   }
   if (max_s > 0) {
-    k_adj_src<T, NM><<<dim3(n_sys, max_s, 2), BQ_BLOCK, 0, s>>>(a);
+    const int tiles = (a.ng_max + BQ_SRC_TILE - 1) / BQ_SRC_TILE;
+    k_adj_src<T, NM><<<dim3(n_sys, max_s, 2 * tiles), BQ_SRC_THREADS, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
