@@ -155,6 +155,51 @@ int bq_stage_variant(const bq_state* s, int* variant);
 /* *eligible = 1 if bq_solve runs the persistent kernel for this state, 0 if it falls back. */
 int bq_solve_eligible(const bq_state* s, int* eligible);
 
+/* ---- schedule selection (autotuner) -------------------------------------------------- *
+ * The paper leaves the parallel schedule open (independent initial conditions processed
+ * "in an ideal fashion", main text after Eq. 13).  A state carries a schedule for bq_step
+ * and one for bq_solve; bq_map picks defaults from occupancy, bq_autotune measures the
+ * candidates on the state itself and keeps the fastest.  Changing a schedule never changes
+ * the arithmetic: every candidate computes the same RK4 step in the same order per point. */
+#define BQ_PATH_TILED 0    /* generic kernel, tiles of R with halo windows (any mode count) */
+#define BQ_PATH_SYSTEM 1   /* single mode, one CTA per system */
+#define BQ_PATH_PIPE 2     /* single mode, persistent CTAs with bulk-copy prefetch */
+#define BQ_SOLVE_PROGRAM 0 /* persistent solve, per-term stencil programs */
+#define BQ_SOLVE_MERGED 1  /* persistent solve, merged per-row / per-column coefficients */
+
+typedef struct bq_tune {
+  int stage_path;        /* BQ_PATH_* used by bq_step */
+  int pipe_slots;        /* BQ_PATH_PIPE: shared-memory slots per CTA (2..4) */
+  int pipe_ctas_per_sm;  /* BQ_PATH_PIPE: resident CTAs per SM (0 = occupancy limit) */
+  int solve_kernel;      /* BQ_SOLVE_* used by bq_solve (-1: bq_solve falls back to bq_step) */
+  int solve_ctas_per_sm; /* persistent solve: resident CTAs per SM (0 = occupancy limit) */
+  int n_candidates;      /* bq_autotune: schedules measured */
+  double step_us;        /* bq_autotune: device time of one RK4 step with bq_step's schedule */
+  double solve_us;       /* bq_autotune: device time per RK4 step with bq_solve's schedule */
+} bq_tune;
+
+/* Current schedules of the state (step_us / solve_us: last bq_autotune result, else 0). */
+int bq_get_tune(const bq_state* s, bq_tune* out);
+
+/* Sets the schedules.  BQ_EUNSUPPORTED if a path or kernel is not available for this state
+ * (BQ_PATH_PIPE / BQ_PATH_SYSTEM need a single-mode state; BQ_SOLVE_MERGED needs every
+ * stencil shift in {-1, 0, 1}; pipe_slots must fit in shared memory). */
+int bq_set_tune(bq_state* s, const bq_tune* t);
+
+/* Device bytes of the scratch buffer bq_autotune needs: a copy of the state and its
+ * rounding compensation (2 x bq_state_bytes). */
+int bq_autotune_scratch_bytes(const bq_state* s, size_t* out);
+
+/* Measures every available schedule on the state itself: for bq_step the available paths x
+ * slot counts x CTAs per SM, for bq_solve the available kernels x CTAs per SM, each over
+ * trial_steps RK4 steps of size dt after one warm-up step (CUDA events on stream), and sets
+ * the fastest.  The state, its compensation and its time are saved into the caller-owned
+ * device buffer scratch (scratch_bytes >= bq_autotune_scratch_bytes) first and restored
+ * after every trial, so the state is unchanged on return.  Synchronises stream.  out (may
+ * be NULL) receives the chosen schedules and their times. */
+int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratch, size_t scratch_bytes, void* stream,
+                bq_tune* out);
+
 /* ---- gradients (discrete adjoint of the RK4 solve) ----------------------------------- */
 
 /* Number of gradient slots of the state: for every problem b in order, its parameters

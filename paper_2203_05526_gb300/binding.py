@@ -35,6 +35,16 @@ C_MODE = {"eq304": 0, "zero": 1}
 MAX_MODES = 3
 
 
+PATH = {0: "tiled", 1: "system", 2: "pipe"}
+SOLVE_KERNEL = {-1: None, 0: "program", 1: "merged"}
+
+
+class bq_tune(C.Structure):
+    _fields_ = [("stage_path", C.c_int), ("pipe_slots", C.c_int), ("pipe_ctas_per_sm", C.c_int),
+                ("solve_kernel", C.c_int), ("solve_ctas_per_sm", C.c_int), ("n_candidates", C.c_int),
+                ("step_us", C.c_double), ("solve_us", C.c_double)]
+
+
 class BQError(RuntimeError):
     def __init__(self, status: int, detail: str):
         super().__init__(f"bq status {status}: {detail}")
@@ -77,6 +87,10 @@ def lib() -> C.CDLL:
         "bq_grad_required_bytes": (C.c_int, [vp, i64, C.c_int, C.POINTER(C.c_size_t)]),
         "bq_grad": (C.c_int, [vp, C.c_double, i64, C.c_int, vp, C.c_size_t, dp, dp, vp]),
         "bq_solve_eligible": (C.c_int, [vp, ip]),
+        "bq_get_tune": (C.c_int, [vp, C.POINTER(bq_tune)]),
+        "bq_set_tune": (C.c_int, [vp, C.POINTER(bq_tune)]),
+        "bq_autotune_scratch_bytes": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
+        "bq_autotune": (C.c_int, [vp, C.c_double, C.c_int, vp, C.c_size_t, vp, C.POINTER(bq_tune)]),
         "bq_stage_variant": (C.c_int, [vp, ip]),
         "bq_time": (C.c_int, [vp, dp]),
         "bq_evaluate": (C.c_int, [vp, dp, vp]),
@@ -263,6 +277,43 @@ class State:
         e = C.c_int()
         check(lib().bq_solve_eligible(self.ptr, C.byref(e)))
         return bool(e.value)
+
+    @staticmethod
+    def _tune_dict(t: "bq_tune") -> dict:
+        return dict(stage_path=PATH[t.stage_path], pipe_slots=t.pipe_slots, pipe_ctas_per_sm=t.pipe_ctas_per_sm,
+                    solve_kernel=SOLVE_KERNEL[t.solve_kernel], solve_ctas_per_sm=t.solve_ctas_per_sm,
+                    n_candidates=t.n_candidates, step_us=t.step_us, solve_us=t.solve_us)
+
+    def get_tune(self) -> dict:
+        t = bq_tune()
+        check(lib().bq_get_tune(self.ptr, C.byref(t)))
+        return self._tune_dict(t)
+
+    def set_tune(self, **kw):
+        """Sets schedules (keys of get_tune(); unspecified keys keep their current value)."""
+        t = bq_tune()
+        check(lib().bq_get_tune(self.ptr, C.byref(t)))
+        inv_path = {v: k for k, v in PATH.items()}
+        inv_solve = {v: k for k, v in SOLVE_KERNEL.items()}
+        for k, v in kw.items():
+            if k == "stage_path":
+                v = inv_path[v]
+            elif k == "solve_kernel":
+                v = inv_solve[v]
+            setattr(t, k, v)
+        check(lib().bq_set_tune(self.ptr, C.byref(t)))
+
+    def autotune(self, dt: float, trial_steps: int = 8, stream=None) -> dict:
+        """Measures the available schedules on this state (restored afterwards) and keeps the
+        fastest (bq_autotune); returns the chosen schedules and their per-step times."""
+        import torch
+        nb = C.c_size_t()
+        check(lib().bq_autotune_scratch_bytes(self.ptr, C.byref(nb)))
+        scratch = torch.empty(nb.value, dtype=torch.uint8, device=self.pool.device)
+        t = bq_tune()
+        check(lib().bq_autotune(self.ptr, float(dt), int(trial_steps), C.c_void_p(scratch.data_ptr()), nb.value,
+                                _stream_ptr(stream), C.byref(t)))
+        return self._tune_dict(t)
 
     def step_fixed_scratch(self, dt: float, n_steps: int, stream=None):
         """bq_step with the RK4 scratch in the library's fixed device array (no allocation)."""

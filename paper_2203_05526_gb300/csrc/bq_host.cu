@@ -599,6 +599,13 @@ struct bq_state {
   int pipe_slot[3] = {0, 0, 0}, pipe_nslots[3] = {2, 2, 2}, pipe_grid[3] = {1, 1, 1}, pipe_mv_bytes = 0;
   int n_coef_dyn = 0;  // time-dependent stage coefficients (k_coef_dyn entries)
   int ng_max = 0;      // largest G_x / G_y point count over the systems
+  // schedules (bq_get_tune / bq_set_tune / bq_autotune)
+  int pipe_ok = 0;      // the pipelined path is available (single mode, two slots fit)
+  int pipe_cap = 0;     // resident pipelined CTAs per SM (0 = occupancy limit)
+  int solve_mg_ok = 0;  // the merged-stencil persistent solve is available
+  int solve_cap = 0;    // resident persistent-solve CTAs per SM (0 = occupancy limit)
+  int tune_n = 0;
+  double tune_step_us = 0.0, tune_solve_us = 0.0;
   int grad_size = 0, adj_smem = 0, srcred_stride = 0, max_s = 0;
   std::vector<TermDesc> terms_host;
   std::vector<ChanDesc> chans_host;
@@ -1043,6 +1050,29 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
   return BQ_OK;
 }
 
+// Slots and grid of the pipelined stage kernel for `slots` shared-memory slots per CTA and
+// at most `cap` resident CTAs per SM (0: the occupancy limit).  BQ_EUNSUPPORTED when the
+// slots do not fit.
+static int pipe_configure(bq_state* st, int slots, int cap) {
+  if (slots < 2 || slots > 4) return fail(BQ_EUNSUPPORTED, "pipe_slots must be 2..4");
+  int dev = 0, nsm = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int grid[3];
+  for (int q = 0; q < 3; ++q) {
+    const size_t smem = (size_t)slots * st->pipe_slot[q] + st->pipe_mv_bytes;
+    if (smem > BQ_MAX_DYN_SMEM) return fail(BQ_EUNSUPPORTED, "%d slots need %zu bytes of shared memory", slots, smem);
+    int per_sm = 0;
+    CUDA_TRY(bq::pipe_blocks_per_sm(st->dtype, st->m1_variant, (int)smem, &per_sm));
+    if (per_sm < 1) return fail(BQ_EUNSUPPORTED, "%d slots do not fit on an SM", slots);
+    if (cap > 0) per_sm = std::min(per_sm, cap);
+    grid[q] = std::min(st->n_sys, per_sm * nsm);
+  }
+  for (int q = 0; q < 3; ++q) { st->pipe_nslots[q] = slots; st->pipe_grid[q] = grid[q]; }
+  st->pipe_cap = cap;
+  return BQ_OK;
+}
+
 extern "C" int bq_required_bytes(const bq_problem* const* probs, int B, const bq_map_opts* opts, size_t* out) {
   if (!out) return fail(BQ_EINVAL, "out is NULL");
   Plan P;
@@ -1153,19 +1183,12 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
     st->pipe_mv_bytes = (int)(((size_t)(6 + 4 * ms) * mmax * (o->dtype == BQ_F64 ? 16 : 8) + 127) & ~(size_t)127);
   }
   if (st->use_pipe) {
-    int dev = 0, nsm = 0;
-    CUDA_TRY(cudaGetDevice(&dev));
-    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    for (int q = 0; q < 3; ++q) {
-      const int slot = st->pipe_slot[q];
-      const int nsl = 2;  // double buffering; more CTAs per SM keep more systems in flight
-      st->pipe_nslots[q] = nsl;
-      int per_sm = 0;
-      CUDA_TRY(bq::pipe_blocks_per_sm(o->dtype, P.m1_variant, nsl * slot + st->pipe_mv_bytes, &per_sm));
-      if (per_sm < 1) { st->use_pipe = 0; break; }
-      st->pipe_grid[q] = std::min((int)P.sys.size(), per_sm * nsm);
-    }
+    // double buffering at the occupancy limit; bq_autotune may pick another schedule
+    int rc = pipe_configure(st, 2, 0);
+    if (rc == BQ_ECUDA) return rc;
+    st->use_pipe = rc == BQ_OK ? 1 : 0;
   }
+  st->pipe_ok = st->use_pipe;
   st->grad_size = P.grad_size;
   st->adj_smem = P.adj_smem;
   st->srcred_stride = P.srcred_stride;
@@ -1177,6 +1200,7 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   st->work_host = P.work;
   st->solve_smem = P.solve_smem;
   st->solve_mg = P.solve_mg;
+  st->solve_mg_ok = P.solve_mg;
   st->solve_mg_smem = P.solve_mg_smem;
   st->n_trace_groups = P.n_trace_groups; st->n_block_groups = P.n_block_groups; st->block_dim = P.block_dim;
   st->total_elems = P.total_elems; st->dt_max = dt_max; st->horizon = o->horizon; st->reverse = o->reverse_time;
@@ -1360,6 +1384,8 @@ extern "C" int bq_step_fixed_scratch(bq_state* s, double dt, int64_t n_steps, vo
   return BQ_OK;
 }
 
+static cudaError_t enqueue_solve(bq_state* s, double dt, int64_t n_steps, cudaStream_t st);
+
 extern "C" int bq_solve(bq_state* s, double dt, int64_t n_steps, void* stream) {
   if (!s) return fail(BQ_EINVAL, "state is NULL");
   if (!s->solve_ok) return bq_step(s, dt, n_steps, stream);
@@ -1368,10 +1394,18 @@ extern "C" int bq_solve(bq_state* s, double dt, int64_t n_steps, void* stream) {
   if (dt > s->dt_max * (1.0 + 1e-12))
     return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 stability bound %g", dt, s->dt_max);
   if (n_steps == 0) return BQ_OK;
-  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(enqueue_solve(s, dt, n_steps, (cudaStream_t)stream));
+  g_launches++;
+  s->tau += (double)n_steps * dt;
+  return BQ_OK;
+}
+
+// One persistent-solve launch of n_steps steps from s->tau with the state's schedule.
+static cudaError_t enqueue_solve(bq_state* s, double dt, int64_t n_steps, cudaStream_t st) {
   char* b = s->pool;
   const Layout& L = s->L;
-  CUDA_TRY(cudaMemsetAsync(b + L.off_ctrl + 24, 0, 8, st));
+  cudaError_t e = cudaMemsetAsync(b + L.off_ctrl + 24, 0, 8, st);
+  if (e != cudaSuccess) return e;
   bq::SolveArgs a;
   std::memset(&a, 0, sizeof(a));
   a.m1 = (const bq::M1Sys*)(b + L.off_m1);
@@ -1390,13 +1424,8 @@ extern "C" int bq_solve(bq_state* s, double dt, int64_t n_steps, void* stream) {
   a.dt = dt;
   a.tau0 = s->tau;
   a.horizon = s->horizon;
-  if (s->solve_mg)
-    CUDA_TRY(bq::launch_solve_mg(a, s->dtype, s->solve_mg_smem, st, &s->last_solve_grid));
-  else
-    CUDA_TRY(bq::launch_solve_m1(a, s->dtype, 0, s->solve_smem, st, &s->last_solve_grid));
-  g_launches++;
-  s->tau += (double)n_steps * dt;
-  return BQ_OK;
+  if (s->solve_mg) return bq::launch_solve_mg(a, s->dtype, s->solve_mg_smem, s->solve_cap, st, &s->last_solve_grid);
+  return bq::launch_solve_m1(a, s->dtype, 0, s->solve_smem, s->solve_cap, st, &s->last_solve_grid);
 }
 
 extern "C" int bq_stage_variant(const bq_state* s, int* variant) {
@@ -1408,6 +1437,196 @@ extern "C" int bq_stage_variant(const bq_state* s, int* variant) {
 extern "C" int bq_solve_eligible(const bq_state* s, int* eligible) {
   if (!s || !eligible) return fail(BQ_EINVAL, "NULL argument");
   *eligible = s->solve_ok;
+  return BQ_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Schedules and the autotuner.
+// ---------------------------------------------------------------------------------------
+static void drop_graph(bq_state* s) {
+  if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
+}
+
+extern "C" int bq_get_tune(const bq_state* s, bq_tune* out) {
+  if (!s || !out) return fail(BQ_EINVAL, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  out->stage_path = s->use_pipe ? BQ_PATH_PIPE : (s->use_m1 ? BQ_PATH_SYSTEM : BQ_PATH_TILED);
+  out->pipe_slots = s->pipe_nslots[0];
+  out->pipe_ctas_per_sm = s->pipe_cap;
+  out->solve_kernel = s->solve_ok ? (s->solve_mg ? BQ_SOLVE_MERGED : BQ_SOLVE_PROGRAM) : -1;
+  out->solve_ctas_per_sm = s->solve_cap;
+  out->n_candidates = s->tune_n;
+  out->step_us = s->tune_step_us;
+  out->solve_us = s->tune_solve_us;
+  return BQ_OK;
+}
+
+extern "C" int bq_set_tune(bq_state* s, const bq_tune* t) {
+  if (!s || !t) return fail(BQ_EINVAL, "NULL argument");
+  if (t->pipe_ctas_per_sm < 0 || t->solve_ctas_per_sm < 0) return fail(BQ_EINVAL, "negative CTA count");
+  switch (t->stage_path) {
+    case BQ_PATH_PIPE: {
+      if (!s->pipe_ok) return fail(BQ_EUNSUPPORTED, "the pipelined path is not available for this state");
+      const int rc = pipe_configure(s, t->pipe_slots, t->pipe_ctas_per_sm);
+      if (rc != BQ_OK) return rc;
+      s->use_pipe = 1;
+      break;
+    }
+    case BQ_PATH_SYSTEM:
+      if (!s->use_m1) return fail(BQ_EUNSUPPORTED, "the one-CTA-per-system path needs a single-mode state");
+      s->use_pipe = 0;
+      break;
+    case BQ_PATH_TILED:
+      if (s->use_m1) return fail(BQ_EUNSUPPORTED, "single-mode states have no tiled work items");
+      break;
+    default:
+      return fail(BQ_EINVAL, "unknown stage path %d", t->stage_path);
+  }
+  if (s->solve_ok) {
+    if (t->solve_kernel == BQ_SOLVE_MERGED) {
+      if (!s->solve_mg_ok) return fail(BQ_EUNSUPPORTED, "the merged persistent solve is not available");
+      s->solve_mg = 1;
+    } else if (t->solve_kernel == BQ_SOLVE_PROGRAM) {
+      s->solve_mg = 0;
+    } else {
+      return fail(BQ_EINVAL, "unknown solve kernel %d", t->solve_kernel);
+    }
+    s->solve_cap = t->solve_ctas_per_sm;
+  }
+  drop_graph(s);
+  return BQ_OK;
+}
+
+extern "C" int bq_autotune_scratch_bytes(const bq_state* s, size_t* out) {
+  if (!s || !out) return fail(BQ_EINVAL, "NULL argument");
+  *out = 2 * (size_t)s->total_elems * (s->dtype == BQ_F64 ? 16 : 8);
+  return BQ_OK;
+}
+
+extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratch, size_t scratch_bytes, void* stream,
+                           bq_tune* out) {
+  if (!s || !scratch) return fail(BQ_EINVAL, "NULL argument");
+  if (trial_steps < 1) return fail(BQ_EINVAL, "trial_steps < 1");
+  if (!(dt > 0.0)) return fail(BQ_EINVAL, "dt must be > 0");
+  if (dt > s->dt_max * (1.0 + 1e-12))
+    return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 stability bound %g", dt, s->dt_max);
+  const size_t n = (size_t)s->total_elems * (s->dtype == BQ_F64 ? 16 : 8);
+  if (scratch_bytes < 2 * n) return fail(BQ_ENOMEM, "scratch has %zu bytes, needs %zu", scratch_bytes, 2 * n);
+  cudaStream_t st = (cudaStream_t)stream;
+  char* b = s->pool;
+  char* sc = (char*)scratch;
+  const double tau0 = s->tau;
+  CUDA_TRY(cudaMemcpyAsync(sc, b + s->L.off_y, n, cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(sc + n, b + s->L.off_comp, n, cudaMemcpyDeviceToDevice, st));
+  auto restore = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(b + s->L.off_y, sc, n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + s->L.off_comp, sc + n, n, cudaMemcpyDeviceToDevice, st);
+    s->tau = tau0;
+    s->tau_base_host = tau0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + s->L.off_ctrl, &s->tau_base_host, sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b + s->L.off_ctrl + 8, 0, 16, st);
+    return e;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  // device time per RK4 step of `run` (after one warm-up step), with the state restored
+  // before and after
+  auto measure = [&](bool solve, double* us) -> int {
+    for (int rep = 0; rep < 2; ++rep) {
+      CUDA_TRY(restore());
+      if (rep == 1) CUDA_TRY(cudaEventRecord(e0, st));
+      const int64_t ns = rep == 0 ? 1 : trial_steps;
+      CUDA_TRY(solve ? enqueue_solve(s, dt, ns, st) : enqueue_steps(s, dt, ns, st));
+      g_launches += solve ? 1 : 4 * ns * kernels_per_stage(s, false);
+      if (rep == 1) CUDA_TRY(cudaEventRecord(e1, st));
+    }
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    unsigned int err = 0;
+    CUDA_TRY(cudaMemcpy(&err, b + s->L.off_ctrl + 32, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err) return fail(BQ_ETIMEOUT, "a bounded device wait gave up during tuning");
+    *us = 1000.0 * ms / trial_steps;
+    return BQ_OK;
+  };
+  int rc = BQ_OK;
+  int ntried = 0;
+  // ---- bq_step schedules --------------------------------------------------------------
+  bq_tune best;
+  bq_get_tune(s, &best);
+  double best_step = 1e300;
+  {
+    struct Cand { int path, slots, cap; };
+    std::vector<Cand> cands;
+    if (s->pipe_ok) {
+      for (int slots = 2; slots <= 4; ++slots) {
+        if (pipe_configure(s, slots, 0) != BQ_OK) break;
+        // the occupancy limit and one CTA per SM fewer (less shared-memory and L2 pressure)
+        int dev = 0, nsm = 0;
+        CUDA_TRY(cudaGetDevice(&dev));
+        CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const int per_sm = (s->pipe_grid[1] + nsm - 1) / nsm;
+        cands.push_back({BQ_PATH_PIPE, slots, 0});
+        if (per_sm > 2 && s->n_sys > per_sm * nsm) cands.push_back({BQ_PATH_PIPE, slots, per_sm - 1});
+      }
+    }
+    if (s->use_m1) cands.push_back({BQ_PATH_SYSTEM, 0, 0});
+    else cands.push_back({BQ_PATH_TILED, 0, 0});
+    for (const Cand& c : cands) {
+      if (c.path == BQ_PATH_PIPE) {
+        if ((rc = pipe_configure(s, c.slots, c.cap)) != BQ_OK) break;
+        s->use_pipe = 1;
+      } else {
+        s->use_pipe = 0;
+      }
+      double us = 0.0;
+      if ((rc = measure(false, &us)) != BQ_OK) break;
+      ++ntried;
+      if (us < best_step) {
+        best_step = us;
+        best.stage_path = c.path;
+        best.pipe_slots = c.path == BQ_PATH_PIPE ? c.slots : 2;
+        best.pipe_ctas_per_sm = c.cap;
+      }
+    }
+  }
+  // ---- bq_solve schedules -------------------------------------------------------------
+  double best_solve = 0.0;
+  if (rc == BQ_OK && s->solve_ok) {
+    best_solve = 1e300;
+    const int kinds[2] = {BQ_SOLVE_MERGED, BQ_SOLVE_PROGRAM};
+    for (int kind : kinds) {
+      if (kind == BQ_SOLVE_MERGED && !s->solve_mg_ok) continue;
+      s->solve_mg = kind == BQ_SOLVE_MERGED;
+      int per_sm = 0;
+      CUDA_TRY(bq::solve_blocks_per_sm(s->dtype, s->solve_mg, s->solve_mg ? s->solve_mg_smem : s->solve_smem, &per_sm));
+      for (int cap : {0, per_sm - 1}) {
+        if (cap < 0 || (cap == 0 && per_sm < 1) || (cap > 0 && cap >= per_sm)) continue;
+        s->solve_cap = cap;
+        double us = 0.0;
+        if ((rc = measure(true, &us)) != BQ_OK) break;
+        ++ntried;
+        if (us < best_solve) {
+          best_solve = us;
+          best.solve_kernel = kind;
+          best.solve_ctas_per_sm = cap;
+        }
+      }
+      if (rc != BQ_OK) break;
+    }
+  }
+  cudaError_t er = restore();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != BQ_OK) return rc;
+  if (er != cudaSuccess) return fail(BQ_ECUDA, "restore: %s", cudaGetErrorString(er));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if ((rc = bq_set_tune(s, &best)) != BQ_OK) return rc;
+  s->tune_n = ntried;
+  s->tune_step_us = best_step;
+  s->tune_solve_us = best_solve;
+  if (out) bq_get_tune(s, out);
   return BQ_OK;
 }
 

@@ -2024,7 +2024,7 @@ cudaError_t launch_stage_m1(const StageArgs& a, const M1Sys* m1, int variant, in
 }
 
 template <typename T, int BLK, int PPT>
-static cudaError_t launch_solve_t(const SolveArgs& a, int smem_bytes, cudaStream_t s, int* grid_out) {
+static cudaError_t launch_solve_t(const SolveArgs& a, int smem_bytes, int cap_per_sm, cudaStream_t s, int* grid_out) {
   auto kern = k_solve_m1<T, BLK, PPT, 2, 2, 2>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -2040,6 +2040,7 @@ static cudaError_t launch_solve_t(const SolveArgs& a, int smem_bytes, cudaStream
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLK, smem_bytes);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if (cap_per_sm > 0) per_sm = std::min(per_sm, cap_per_sm);
   const int grid = std::min(a.n_sys, per_sm * nsm);
   *grid_out = grid;
   kern<<<grid, BLK, smem_bytes, s>>>(a);
@@ -2047,7 +2048,7 @@ static cudaError_t launch_solve_t(const SolveArgs& a, int smem_bytes, cudaStream
 }
 
 template <typename T, int BLK, int RB>
-static cudaError_t launch_solve_mg_t(const SolveArgs& a, int smem_bytes, cudaStream_t s, int* grid_out) {
+static cudaError_t launch_solve_mg_t(const SolveArgs& a, int smem_bytes, int cap_per_sm, cudaStream_t s, int* grid_out) {
   auto kern = k_solve_mg<T, BLK, RB, BQ_M1_MAXT, BQ_M1_MAXT, 2>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -2063,24 +2064,26 @@ static cudaError_t launch_solve_mg_t(const SolveArgs& a, int smem_bytes, cudaStr
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLK, smem_bytes);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if (cap_per_sm > 0) per_sm = std::min(per_sm, cap_per_sm);
   const int grid = std::min(a.n_sys, per_sm * nsm);
   *grid_out = grid;
   kern<<<grid, BLK, smem_bytes, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve_mg(const SolveArgs& a, int dtype, int smem_bytes, cudaStream_t s, int* grid_out) {
+cudaError_t launch_solve_mg(const SolveArgs& a, int dtype, int smem_bytes, int cap_per_sm, cudaStream_t s,
+                            int* grid_out) {
   // 256 threads; column strips of at most 8 rows (M <= 45)
-  return dtype == 0 ? launch_solve_mg_t<double, 256, 8>(a, smem_bytes, s, grid_out)
-                    : launch_solve_mg_t<float, 256, 8>(a, smem_bytes, s, grid_out);
+  return dtype == 0 ? launch_solve_mg_t<double, 256, 8>(a, smem_bytes, cap_per_sm, s, grid_out)
+                    : launch_solve_mg_t<float, 256, 8>(a, smem_bytes, cap_per_sm, s, grid_out);
 }
 
-cudaError_t launch_solve_m1(const SolveArgs& a, int dtype, int capacity_class, int smem_bytes, cudaStream_t s,
-                            int* grid_out) {
+cudaError_t launch_solve_m1(const SolveArgs& a, int dtype, int capacity_class, int smem_bytes, int cap_per_sm,
+                            cudaStream_t s, int* grid_out) {
   // capacity: FP32 256 threads x 7 points = 1792, FP64 448 threads x 4 points = 1792 points per system
   if (capacity_class != 0) return cudaErrorInvalidValue;
-  return dtype == 0 ? launch_solve_t<double, 448, 4>(a, smem_bytes, s, grid_out)
-                    : launch_solve_t<float, 256, 7>(a, smem_bytes, s, grid_out);
+  return dtype == 0 ? launch_solve_t<double, 448, 4>(a, smem_bytes, cap_per_sm, s, grid_out)
+                    : launch_solve_t<float, 256, 7>(a, smem_bytes, cap_per_sm, s, grid_out);
 }
 
 template <typename T, int NM>
@@ -2178,6 +2181,21 @@ cudaError_t pipe_blocks_per_sm(int dtype, int variant, int smem_bytes, int* out)
                                                                        BQ_PIPE_THREADS, smem_bytes)
                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                             out, k_stage_pipe<float, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>, BQ_PIPE_THREADS, smem_bytes);
+}
+
+template <typename K>
+static cudaError_t occupancy_with_smem(K kern, int threads, int smem_bytes, int* out) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, BQ_MAX_DYN_SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kern, threads, smem_bytes);
+}
+
+cudaError_t solve_blocks_per_sm(int dtype, int merged, int smem_bytes, int* out) {
+  if (merged)
+    return dtype == 0 ? occupancy_with_smem(k_solve_mg<double, 256, 8, BQ_M1_MAXT, BQ_M1_MAXT, 2>, 256, smem_bytes, out)
+                      : occupancy_with_smem(k_solve_mg<float, 256, 8, BQ_M1_MAXT, BQ_M1_MAXT, 2>, 256, smem_bytes, out);
+  return dtype == 0 ? occupancy_with_smem(k_solve_m1<double, 448, 4, 2, 2, 2>, 448, smem_bytes, out)
+                    : occupancy_with_smem(k_solve_m1<float, 256, 7, 2, 2, 2>, 256, smem_bytes, out);
 }
 
 cudaError_t launch_stage(const StageArgs& a, int dtype, int nm, int n_work, int smem_bytes, cudaStream_t s) {

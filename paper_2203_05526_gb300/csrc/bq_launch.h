@@ -21,9 +21,10 @@ cudaError_t launch_stage(const StageArgs& a, int dtype, int nm, int n_work, int 
 // checks bq_m1_eligible().
 cudaError_t launch_stage_m1(const StageArgs& a, const M1Sys* m1, int variant, int dtype, int n_work, int smem_bytes,
                             cudaStream_t s);
-// Batched persistent solve; capacity_class 0 = systems of up to 1792 points.
-cudaError_t launch_solve_m1(const SolveArgs& a, int dtype, int capacity_class, int smem_bytes, cudaStream_t s,
-                            int* grid_out);
+// Batched persistent solve; capacity_class 0 = systems of up to 1792 points; at most
+// cap_per_sm resident CTAs per SM (0: the occupancy limit).
+cudaError_t launch_solve_m1(const SolveArgs& a, int dtype, int capacity_class, int smem_bytes, int cap_per_sm,
+                            cudaStream_t s, int* grid_out);
 // Adjoint RK4 stage (transposed-source pre-pass when max_s > 0, then the stage kernel).
 cudaError_t launch_adjoint(const AdjArgs& a, int dtype, int nm, int n_work, int smem_bytes, int n_sys, int max_s,
                            cudaStream_t s);
@@ -34,7 +35,10 @@ cudaError_t launch_stage_pipe(const PipeArgs& a, const CoefArgs& c, int variant,
                               cudaStream_t s);
 cudaError_t pipe_blocks_per_sm(int dtype, int variant, int smem_bytes, int* out);
 // Batched persistent solve, merged-stencil form (256 threads, M <= 45, shifts in {-1,0,1}).
-cudaError_t launch_solve_mg(const SolveArgs& a, int dtype, int smem_bytes, cudaStream_t s, int* grid_out);
+cudaError_t launch_solve_mg(const SolveArgs& a, int dtype, int smem_bytes, int cap_per_sm, cudaStream_t s,
+                            int* grid_out);
+// Occupancy (CTAs per SM) of the persistent solve kernels at the given shared memory.
+cudaError_t solve_blocks_per_sm(int dtype, int merged, int smem_bytes, int* out);
 cudaError_t launch_eval(const SysDesc* sys, const EvalGroup* groups, const EvalEntry* entries, const void* y,
                         double2* out, int n_groups, int dtype, int small, cudaStream_t s);
 // Device address of the fixed RK4 scratch on the current device (looked up once per device).

@@ -1,0 +1,123 @@
+"""Schedule selection (bq_get_tune / bq_set_tune / bq_autotune): the autotuner leaves the
+state untouched, every schedule computes the same RK4 step, and requests for schedules a
+state cannot run are refused."""
+
+import numpy as np
+import pytest
+
+import paper_2203_05526_gb300 as bq
+from paper_2203_05526_gb300.binding import BQ_EUNSUPPORTED
+from oracle import mapping
+from workloads import configs
+
+from parity import compare_mapped_systems, gpu_state, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    from paper_2203_05526_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def _snapshot(st):
+    import torch
+    host = torch.empty(st.state_bytes(), dtype=torch.uint8, pin_memory=True)
+    st.store_state(host.data_ptr())
+    _sync()
+    return host.numpy().copy()
+
+
+def _batch(n=300, dt=0.002, steps=12):
+    return configs.kerr_batch(B=n, T=steps * dt, dt=dt, n_min=10, n_max=40)
+
+
+def test_autotune_restores_state_and_time():
+    ps = _batch()
+    st = gpu_state(ps, dtype="f32")
+    st.step(ps[0].dt, 3)
+    _sync()
+    before, t0 = _snapshot(st), st.time()
+    tune = st.autotune(ps[0].dt, trial_steps=4)
+    after, t1 = _snapshot(st), st.time()
+    assert np.array_equal(before, after)
+    assert t0 == t1
+    assert tune["n_candidates"] >= 3  # pipe schedules + one CTA per system + solve kernels
+    assert tune["step_us"] > 0 and tune["solve_us"] > 0
+    assert st.get_tune() == tune
+
+
+def test_every_step_schedule_computes_the_same_step():
+    """Pipelined schedules (slots, CTAs per SM) run the same kernel: bitwise equal results.
+    The one-CTA-per-system path evaluates the same stencil from per-term programs: equal to
+    FP32 rounding, and both match the FP64 oracle."""
+    ps = _batch(n=64)
+    dt, n = ps[0].dt, 12
+    ref = gpu_state(ps, dtype="f32")
+    assert ref.get_tune()["stage_path"] == "pipe"
+    ref.step(dt, n)
+    base = _snapshot(ref)
+    for slots, cap in ((3, 0), (2, 1), (4, 2)):
+        st = gpu_state(ps, dtype="f32")
+        st.set_tune(stage_path="pipe", pipe_slots=slots, pipe_ctas_per_sm=cap)
+        st.step(dt, n)
+        assert np.array_equal(_snapshot(st), base), (slots, cap)
+    st = gpu_state(ps, dtype="f32")
+    st.set_tune(stage_path="system")
+    st.step(dt, n)
+    _sync()
+    for i in (0, 17, 63):
+        run = mapping.rk4_mapped(ps[i])
+        compare_mapped_systems(st, run, 1e-5, sys_offset=i, n_sys=i + 1)
+        compare_mapped_systems(ref, run, 1e-5, sys_offset=i, n_sys=i + 1)
+
+
+def test_solve_kernels_agree_and_tuned_solve_matches_streaming():
+    ps = _batch(n=96)
+    dt, n = ps[0].dt, 12
+    streamed = gpu_state(ps, dtype="f64")
+    streamed.step(dt, n)
+    _sync()
+    for kernel in ("merged", "program"):
+        for cap in (0, 1):
+            st = gpu_state(ps, dtype="f64")
+            st.set_tune(solve_kernel=kernel, solve_ctas_per_sm=cap)
+            st.solve(dt, n)
+            _sync()
+            for i in (0, 41, 95):
+                for x, y in zip(st.read_system(i)[1:], streamed.read_system(i)[1:]):
+                    if x is not None:
+                        assert rel_err(x, y) <= 1e-10, (kernel, cap, i)
+    st = gpu_state(ps, dtype="f64")
+    st.autotune(dt, trial_steps=3)
+    st.solve(dt, n)
+    _sync()
+    for x, y in zip(st.read_system(5)[1:], streamed.read_system(5)[1:]):
+        if x is not None:
+            assert rel_err(x, y) <= 1e-10
+
+
+def test_unavailable_schedules_are_refused():
+    two = configs.two_mode(N=4)
+    st = gpu_state(two)  # two modes: tiled path only, no persistent solve
+    assert st.get_tune()["stage_path"] == "tiled"
+    with pytest.raises(bq.BQError) as e:
+        st.set_tune(stage_path="pipe")
+    assert e.value.args[0].startswith(f"bq status {BQ_EUNSUPPORTED}")
+    with pytest.raises(bq.BQError):
+        st.set_tune(stage_path="system")
+    one = gpu_state(_batch(n=4))
+    with pytest.raises(bq.BQError):
+        one.set_tune(stage_path="pipe", pipe_slots=9)
+    with pytest.raises(bq.BQError):
+        one.set_tune(stage_path="tiled")
+    tune = st.autotune(two.dt, trial_steps=2)
+    assert tune["stage_path"] == "tiled" and tune["solve_kernel"] is None
