@@ -13,7 +13,12 @@ Other keys: ``roofline`` (the stage kernel against the measured HBM copy bandwid
 ``e2e`` (the same step through the C ABI with the state loaded from pinned host memory
 and the observables read back every step), ``cpu_baseline`` (the FP64 oracle timed on a
 bounded sample of the same workload on the host cores), ``clocks`` (nvidia-smi sampled
-during the timed region), ``gpu_launches`` (library kernel launches in the timed region).
+during the timed region), ``gpu_launches`` (library kernel launches in the timed region),
+``batched`` (4096 full-horizon solves: one persistent launch vs streamed stage kernels vs
+one instance per launch), ``grads`` (the 131-parameter control gradient, and 16 control
+problems batched in one state vs one problem per state), ``methods`` (memory and time per
+step of the conventional number-basis method vs the mapping with full R and with R = 0),
+and ``config.schedule`` (the schedule bq_autotune picked for the timed state).
 
 ``--impl reference`` times the oracle (the plain FP64 CPU implementation) on the same
 workload, each step a bounded sample.  Multi-GPU: every rank solves its own shard of
@@ -283,10 +288,81 @@ def grads_leg(n_steps=None):
     t0 = time.perf_counter()
     loss, g = st.grad(p.dt, steps, 160)
     el = time.perf_counter() - t0
-    return {"workload": f"two_mode_control: 2 modes x M=12, 64 pwc segments, 131 parameters, {steps} RK4 steps, "
+    out = {"workload": f"two_mode_control: 2 modes x M=12, 64 pwc segments, 131 parameters, {steps} RK4 steps, "
+                       "checkpoint every 160, complex FP64",
+           "seconds_per_gradient": el, "grads_per_s": 1.0 / el, "loss": float(loss[0]),
+           "grad_norm": float(np.linalg.norm(g)), "n_params": int(g.size)}
+    if n_steps is None:
+        out["batched"] = grads_batched_leg()
+    return out
+
+
+def grads_batched_leg(B: int = 16, steps: int = 1280):
+    """Gradients of B control problems (drive amplitudes from seeds 5526 + b) in one state
+    (one set of adjoint launches for the whole batch) against one problem per state (the
+    plain one-instance-per-launch path), over the first `steps` RK4 steps, same arithmetic."""
+    import numpy as np
+    import torch
+
+    import paper_2203_05526_gb300 as bq
+    from workloads import configs
+    probs = [configs.two_mode_control(seed=5526 + b) for b in range(B)]
+    dt = probs[0].dt
+    opts = bq.map_opts(dtype="f64", horizon=probs[0].T, dt=dt)
+    stB = bq.State([bq.problem_from_spec(q) for q in probs], opts)
+    stB.grad(dt, 160, 160)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lossB, gB = stB.grad(dt, steps, 160)
+    tB = time.perf_counter() - t0
+    t1 = 0.0
+    worst = 0.0
+    n_per = gB.size // B
+    for b, q in enumerate(probs):
+        st1 = bq.State([bq.problem_from_spec(q)], opts)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        l1, g1 = st1.grad(dt, steps, 160)
+        t1 += time.perf_counter() - t0
+        ref = gB[b * n_per:(b + 1) * n_per]
+        worst = max(worst, float(np.max(np.abs(g1 - ref)) / max(float(np.max(np.abs(ref))), 1e-300)))
+    return {"workload": f"{B} two_mode_control problems (seeds 5526..{5526 + B - 1}), first {steps} RK4 steps, "
                         "checkpoint every 160, complex FP64",
-            "seconds_per_gradient": el, "grads_per_s": 1.0 / el, "loss": float(loss[0]),
-            "grad_norm": float(np.linalg.norm(g)), "n_params": int(g.size)}
+            "batched_grads_per_s": B / tB, "one_instance_per_launch_grads_per_s": B / t1,
+            "batched_vs_one_per_launch": t1 / tB, "max_rel_diff_batched_vs_single": worst}
+
+
+def methods_leg(B: int = 1024, Ns=(10, 20, 40), steps: int = 100):
+    """The paper's memory and time comparison on this GPU: B driven damped Kerr oscillators
+    with truncation N, integrated by the conventional number-basis method (N^2 elements per
+    instance), the mapping with the full residual R (2N + N^2) and the mapping with R = 0
+    (2N, the regime the paper's memory claim refers to; an approximation for kappa t << 1).
+    Complex FP32, schedules autotuned; device time per RK4 step."""
+    import torch
+
+    import paper_2203_05526_gb300 as bq
+    from workloads import configs
+    rows = []
+    for N in Ns:
+        specs = configs.kerr_batch(B=B, T=HORIZON, dt=DT, n_min=N, n_max=N)
+        handles = [bq.problem_from_spec(p) for p in specs]
+        for name, kw in (("direct", dict(method="direct")), ("mapped_full_R", dict(method="mapped")),
+                         ("mapped_R_off", dict(method="mapped", r_layout="off"))):
+            st = bq.State(handles, bq.map_opts(dtype="f32", horizon=HORIZON, dt=DT, **kw))
+            st.autotune(DT, trial_steps=4)
+            st.step(DT, 8)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st.step(DT, steps)
+            e1.record()
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / steps
+            elems = st.state_bytes() // 8
+            rows.append({"N": N, "method": name, "elements_per_instance": elems / B, "state_bytes": st.state_bytes(),
+                         "us_per_step": us, "ns_per_instance_step": 1e3 * us / B})
+    return {"workload": f"{B} driven damped Kerr instances per N (kerr_batch distribution at fixed N), complex FP32, "
+                        f"{steps} RK4 steps of dt={DT} ns", "rows": rows}
 
 
 def run_reference(args, rank, world):
@@ -448,6 +524,9 @@ def main():
     grads = None
     if not args.no_grads and world == 1:
         grads = grads_leg()
+    methods = None
+    if not args.no_batched and world == 1:
+        methods = methods_leg()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -466,7 +545,7 @@ def main():
                                                                  "n_candidates", "step_us")},
                            "state_bytes_per_array": nbytes, "l2": "inputs larger than L2 (4 arrays x "
                            f"{nbytes / 1e6:.0f} MB vs 129 MB)", "parallelism": f"replicas x{world}"},
-                "roofline": roof, "e2e": e2e, "batched": batched, "grads": grads, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches}
+                "roofline": roof, "e2e": e2e, "batched": batched, "grads": grads, "methods": methods, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -63,6 +63,25 @@ def test_grad_matches_oracle_adjoint(n_modes, N, ck):
     assert abs(st.time()) == 0.0  # the state is left as it was
 
 
+def test_batched_gradients_equal_single_problem_gradients():
+    """Three problems with different drives, parameters and measured operators in one state:
+    per-problem losses and gradient slots equal those of one problem per state, and the first
+    problem's against the oracle."""
+    ps = [_small_control(n_modes=2, N=3, seed=s) for s in (3, 4, 5)]
+    ps[1].params = [p * 1.1 for p in ps[1].params]
+    ps[2].measured = {((0, 1), (0, 1)): 1.0}
+    st = gpu_state(ps)
+    loss, g = st.grad(ps[0].dt, ps[0].n_steps, 5)
+    n_per = g.size // 3
+    for b, p in enumerate(ps):
+        l1, g1 = gpu_state(p).grad(p.dt, p.n_steps, 5)
+        assert abs(loss[b] - l1[0]) <= 1e-13 * max(1.0, abs(l1[0]))
+        assert np.max(np.abs(g[b * n_per:(b + 1) * n_per] - g1)) <= 1e-12 * np.max(np.abs(g1))
+    loss_o, gt, gp = ograd.loss_and_grad(ps[0], checkpoint_every=5)
+    ref = _flat_oracle(gt, gp)
+    assert np.max(np.abs(g[:n_per] - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
 def test_grad_direct_method_matches_finite_differences():
     p = _small_control(n_modes=1, N=5)
     st = gpu_state(p, method="direct")
