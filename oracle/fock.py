@@ -11,6 +11,15 @@ enters through its exact matrix elements in that span.  The matrices are therefo
 at a padded size and restricted, so that e.g. L^dag L for L = a^dag is diag(1..N), the
 same as its normal-ordered form a^dag a + 1.
 
+Secular dissipator (the paper's proper dissipator, Eq. 203 / Eq. S9, per damped mode j with
+rate kappa and transition occupations nbar_n): with K_n = |n><n+1|_j (identity on the other
+modes) and P_n = |n><n|_j,
+    Schroedinger:  kappa/2 sum_n (nbar_n + 1)(n + 1) [2 K_n rho K_n^dag - {P_{n+1}, rho}]
+                 + kappa/2 sum_n nbar_n (n + 1) [2 K_n^dag rho K_n - {P_n, rho}],
+    adjoint:       the same with K_n rho K_n^dag -> K_n^dag A K_n and K_n^dag rho K_n -> K_n A K_n^dag.
+Both are evaluated on A (rho) zero-padded by one level per mode and then restricted, the
+same compression reading as for H and the jump operators.
+
 Parity status (all pinned in tests/test_oracle_fock.py):
   * generator + RK4:      pinned by the damped-oscillator closed forms <a>(t), <a^dag a>(t);
                           by the binomial closed form for |m><m| under Kerr + damping;
@@ -19,6 +28,12 @@ Parity status (all pinned in tests/test_oracle_fock.py):
                           by the dense Liouvillian exponential (scipy.linalg.expm);
                           by unitary evolution U^dag A U for closed systems.
   * schrodinger_rk4:      pinned by the same duality and by trace preservation.
+  * secular dissipator:   pinned (tests/test_oracle_secular.py) by equality with the
+                          conventional dissipator on diagonal operators at zero temperature;
+                          by the closed form A_{k,k+1}(t) = sqrt(k+1) exp(-(i Delta +
+                          kappa (2k+1)/2) t) for A(0) = a; by adjoint / Schroedinger duality at
+                          finite temperature with a drive; by unitality; by stationarity of
+                          the thermal state rho_{n+1,n+1}/rho_{n,n} = nbar_n/(1 + nbar_n).
 """
 
 from __future__ import annotations
@@ -106,6 +121,62 @@ class FockModel:
             LdL = r(L_big.conj().T @ L_big)
             L = r(L_big)
             self.jumps.append((j.rate, L, L.conj().T, LdL))
+        # secular dissipators: K_n, P_n, P_{n+1} on a space padded by one level per mode
+        # (enough: they change a mode's level by at most one), with their weights
+        sbig = tuple(n + 1 for n in self.N)
+        self.big = sbig
+        self.secular = []  # (kappa, [(w_down, w_up, K_n, P_n, P_n+1)])
+        for sd in getattr(problem, "secular", []):
+            ops = []
+            for n in range(sbig[sd.mode] - 1):
+                e = [np.eye(b, dtype=np.complex128) for b in sbig]
+                kn = np.zeros((sbig[sd.mode], sbig[sd.mode]), dtype=np.complex128)
+                kn[n, n + 1] = 1.0
+                pn = np.zeros_like(kn)
+                pn[n, n] = 1.0
+                pn1 = np.zeros_like(kn)
+                pn1[n + 1, n + 1] = 1.0
+
+                def on_mode(m, e=e, j=sd.mode):
+                    f = list(e)
+                    f[j] = m
+                    return reduce(np.kron, f)
+                nb = sd.nbar_at(n)
+                ops.append(((nb + 1.0) * (n + 1), nb * (n + 1), on_mode(kn), on_mode(pn), on_mode(pn1)))
+            self.secular.append((sd.kappa, ops))
+        self._ri = restriction_indices(sbig, self.N) if self.secular else None
+
+    def _pad(self, X: np.ndarray) -> np.ndarray:
+        d = int(np.prod(self.big))
+        out = np.zeros((d, d), dtype=np.complex128)
+        out[np.ix_(self._ri, self._ri)] = X
+        return out
+
+    def secular_adjoint(self, A: np.ndarray) -> np.ndarray:
+        """Adjoint of the secular dissipators applied to A (padded, then restricted)."""
+        if not self.secular:
+            return np.zeros_like(A)
+        Ab = self._pad(A)
+        out = np.zeros_like(Ab)
+        for kappa, ops in self.secular:
+            for wd, wu, K, P, P1 in ops:
+                Kd = K.conj().T
+                out += 0.5 * kappa * wd * (2.0 * (Kd @ Ab @ K) - (P1 @ Ab + Ab @ P1))
+                out += 0.5 * kappa * wu * (2.0 * (K @ Ab @ Kd) - (P @ Ab + Ab @ P))
+        return out[np.ix_(self._ri, self._ri)]
+
+    def secular_schrodinger(self, rho: np.ndarray) -> np.ndarray:
+        """The secular dissipators of Eq. S9 applied to rho (padded, then restricted)."""
+        if not self.secular:
+            return np.zeros_like(rho)
+        rb = self._pad(rho)
+        out = np.zeros_like(rb)
+        for kappa, ops in self.secular:
+            for wd, wu, K, P, P1 in ops:
+                Kd = K.conj().T
+                out += 0.5 * kappa * wd * (2.0 * (K @ rb @ Kd) - (P1 @ rb + rb @ P1))
+                out += 0.5 * kappa * wu * (2.0 * (Kd @ rb @ K) - (P @ rb + rb @ P))
+        return out[np.ix_(self._ri, self._ri)]
 
     def hamiltonian(self, tau_step: float, c: float, dt: float) -> np.ndarray:
         p = self.p
@@ -120,6 +191,8 @@ class FockModel:
         out = 1j * (H @ A - A @ H)
         for rate, L, Ld, LdL in self.jumps:
             out += rate * (Ld @ A @ L - 0.5 * (LdL @ A + A @ LdL))
+        if self.secular:
+            out += self.secular_adjoint(A)
         return out
 
     def schrodinger_generator(self, rho: np.ndarray, H: np.ndarray) -> np.ndarray:
@@ -127,6 +200,8 @@ class FockModel:
         out = -1j * (H @ rho - rho @ H)
         for rate, L, Ld, LdL in self.jumps:
             out += rate * (L @ rho @ Ld - 0.5 * (LdL @ rho + rho @ LdL))
+        if self.secular:
+            out += self.secular_schrodinger(rho)
         return out
 
 
@@ -202,6 +277,11 @@ def adjoint_liouvillian(problem: Problem, H: np.ndarray, N: Optional[Sequence[in
     Lsup = 1j * (np.kron(H, I) - np.kron(I, H.T))
     for rate, L, Ld, LdL in model.jumps:
         Lsup += rate * (np.kron(Ld, L.T) - 0.5 * (np.kron(LdL, I) + np.kron(I, LdL.T)))
+    if model.secular:  # column by column: the secular dissipators applied to every E_{ij}
+        for c in range(d * d):
+            E = np.zeros((d, d), dtype=np.complex128)
+            E.reshape(-1)[c] = 1.0
+            Lsup[:, c] += model.secular_adjoint(E).reshape(-1)
     return Lsup
 
 

@@ -91,6 +91,8 @@ class _Derivs:
 
 def loss_and_grad(problem: Problem, M: Optional[Sequence[int]] = None, checkpoint_every: int = 64):
     """Returns (loss, dl/dtheta (len P), {channel: dl/d(Re, Im) of each segment (n_seg, 2)})."""
+    if getattr(problem, "secular", None):
+        raise NotImplementedError("gradients with secular dissipators are not implemented")
     model = MappedModel(problem, M)
     M = model.M
     der = _Derivs(problem, model)

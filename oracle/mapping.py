@@ -20,6 +20,14 @@ Steps, in the paper's order (single mode in the main text, multimode in Sec. S1)
      and then truncated (the same compression as O1's);
   6. reconstruction of f(t) by Eq. 11 and of A(t)'s number-basis elements by Eq. 2.
 
+Secular dissipator (Eq. 203 / Eq. S9; Eq. S15 is its zero-temperature mapped form
+G' = kappa/2 (2P - x d/dx - y d/dy) G): in g_{k,l} = <k|A|l>/sqrt(k! l!) its adjoint acts as
+a decay -kappa/2 [a_j(k_j) + a_j(l_j)], a_j(m) = m (1 + nbar_{m-1}) + (m + 1) nbar_m, which is
+separable and joins O_x and O_y, plus the projector term P of Eq. 302c generalised to
+nbar != 0, which acts only on diagonal pairs k_j = l_j of mode j:
+    (P G)_{..m..,..m..} = kappa (1 + nbar_{m-1}) g_{..m-1..,..m-1..} + kappa (m+1)^2 nbar_m g_{..m+1..,..m+1..};
+P is not separable, so it acts on R and as a source on G_x G_y (Eq. 303c).
+
 Parity status (tests/test_oracle_mapping.py):
   * f_from_fock / g_from_f / f_from_g / fock_from_f: pinned by brute force against
     explicit matrix products of (a^dag)^k a^l and by the identity T_{k,l} = sqrt(k! l!)|k><l|
@@ -276,7 +284,44 @@ class MappedModel:
             # A L^dag L = (A L^dag) L: apply [L^dag]_right first, then [L]_right
             self.Oy += -0.5 * jmp.rate * r(L_right @ Ld_right)
             self.sandwich.append((jmp.rate, r(Ld_left), r(L_right)))
+        # secular dissipators: separable decay into O_x / O_y, projector weights for P
+        self.secular = []  # (mode, w_down[m] (source m-1), w_up[m] (source m+1))
+        grids = np.meshgrid(*[np.arange(m) for m in self.M], indexing="ij")
+        for sd in getattr(problem, "secular", []):
+            j, Mj = sd.mode, self.M[sd.mode]
+            a = np.array([m * (1.0 + sd.nbar_at(m - 1)) + (m + 1) * sd.nbar_at(m) for m in range(Mj)])
+            decay = (-0.5 * sd.kappa * a[grids[j]]).reshape(-1)
+            self.Ox += np.diag(decay)
+            self.Oy += np.diag(decay)
+            w_down = np.array([sd.kappa * (1.0 + sd.nbar_at(m - 1)) if m >= 1 else 0.0 for m in range(Mj)])
+            w_up = np.array([sd.kappa * (m + 1) ** 2 * sd.nbar_at(m) if m + 1 < Mj else 0.0 for m in range(Mj)])
+            self.secular.append((j, w_down, w_up))
         del n
+
+    def secular_projector(self, F: np.ndarray) -> np.ndarray:
+        """sum over secular dissipators of their P term applied to F (x index, y index)."""
+        n = self.p.n_modes
+        out = np.zeros_like(F)
+        if not self.secular:
+            return out
+        Fr = F.reshape(self.M + self.M)
+        Or = out.reshape(self.M + self.M)
+        for j, w_down, w_up in self.secular:
+            for m in range(self.M[j]):
+                dst = [slice(None)] * (2 * n)
+                dst[j] = m
+                dst[n + j] = m
+                if m >= 1 and w_down[m] != 0.0:
+                    src = list(dst)
+                    src[j] = m - 1
+                    src[n + j] = m - 1
+                    Or[tuple(dst)] += w_down[m] * Fr[tuple(src)]
+                if w_up[m] != 0.0:
+                    src = list(dst)
+                    src[j] = m + 1
+                    src[n + j] = m + 1
+                    Or[tuple(dst)] += w_up[m] * Fr[tuple(src)]
+        return out
 
     def operators(self, tau_step: float, c: float, dt: float):
         p = self.p
@@ -298,6 +343,8 @@ class MappedModel:
         for kappa, Ld_l, L_r in self.sandwich:
             dR += kappa * (Ld_l @ R @ L_r.T)
             dR += kappa * np.outer(Ld_l @ Gx, L_r @ Gy)
+        if self.secular:
+            dR += self.secular_projector(R + np.outer(Gx, Gy))
         return dGx, dGy, dR
 
 

@@ -30,7 +30,7 @@ from typing import List, Sequence
 
 import numpy as np
 
-from .spec import Channel, HTerm, Jump, Problem
+from .spec import Channel, HTerm, Jump, Problem, SecularDamping
 
 TWO_PI = 2.0 * math.pi
 
@@ -232,3 +232,60 @@ def random_problem(seed: int, n_modes: int = 1, N: int = 6, n_steps: int = 20,
     return Problem(n_modes=n_modes, N=(N,) * n_modes, h_terms=terms, jumps=jumps,
                    measured=meas, channels=chans, T=n_steps * dt, dt=dt,
                    name=f"random[{seed}]")
+
+
+# ---- secular ("proper") dissipator, Eq. 203 / Eq. S9 -----------------------------------
+def thermal_nbar(omega: float, eta: float, kT: float, n_levels: int) -> tuple:
+    """Eq. S10: occupation of the bath mode at the n <-> n+1 transition frequency
+    omega + 2 eta n, nbar_n = 1 / (exp((omega + 2 eta n) / kT) - 1), kT = k_B T_E / hbar in
+    rad/ns; kT = 0 gives the zero-temperature case.  Every transition frequency must be
+    positive (a lab-frame omega well above 2 |eta| n_levels)."""
+    if kT <= 0.0:
+        return ()
+    if any(omega + 2.0 * eta * n <= 0.0 for n in range(n_levels)):
+        raise ValueError("transition frequency omega + 2 eta n <= 0 inside the truncation")
+    return tuple(1.0 / math.expm1((omega + 2.0 * eta * n) / kT) for n in range(n_levels))
+
+
+def kerr_secular(N: int = 12, T: float = 20.0, dt: float = 0.005, kappa: float = 0.05, kT: float = 0.0,
+                 omega_q: float = TWO_PI * 5.0, drive_peak: float = TWO_PI * 0.05,
+                 measured=None) -> Problem:
+    """A driven Kerr oscillator (Delta = 0, K = -2pi 0.2 in the rotating frame) damped by the
+    secular dissipator at rate kappa; thermal occupations from Eq. S10 at the lab-frame
+    transition frequencies omega_q + 2 eta n (eta = K/2)."""
+    kerr = -TWO_PI * 0.2
+    nbar = thermal_nbar(omega_q, 0.5 * kerr, kT, N - 1)
+    return Problem(
+        n_modes=1, N=(N,),
+        h_terms=kerr_mode_terms(1, 0, 0.0, kerr) + gauss_drive_terms(1, 0, 0),
+        jumps=[], secular=[SecularDamping(0, kappa, nbar)],
+        measured=measured if measured is not None else projector(1, (1,)),
+        channels=[Channel("gauss", (drive_peak, 0.0, T / 2.0, T / 6.0))],
+        T=T, dt=dt, name="kerr_secular")
+
+
+def two_mode_secular(N: int = 5, T: float = 4.0, dt: float = 0.01, kappa: float = 0.1, kT: float = 0.0) -> Problem:
+    """The two exchange-coupled Kerr modes with the secular dissipator on each mode and a
+    Gaussian drive on mode 1."""
+    p = two_mode(N=N, T=T, dt=dt)
+    p.jumps = []
+    p.secular = [SecularDamping(j, kappa, thermal_nbar(TWO_PI * (5.0 + 0.1 * j), -TWO_PI * 0.1, kT, N - 1))
+                 for j in range(2)]
+    p.channels = [Channel("gauss", (TWO_PI * 0.05, 0.0, T / 2.0, T / 6.0))]
+    p.h_terms = p.h_terms + gauss_drive_terms(2, 0, 0)
+    p.name = "two_mode_secular"
+    return p
+
+
+def secular_batch(B: int = 4096, seed: int = 20220311, T: float = 100.0, dt: float = 0.002,
+                  n_min: int = 10, n_max: int = 40) -> List[Problem]:
+    """kerr_batch's instances (same draws) with the secular dissipator in place of the
+    conventional one, at zero temperature."""
+    out = []
+    for p in kerr_batch(B=B, seed=seed, T=T, dt=dt, n_min=n_min, n_max=n_max):
+        gamma = p.jumps[0].rate
+        p.jumps = []
+        p.secular = [SecularDamping(0, gamma, ())]
+        p.name = p.name.replace("kerr_batch", "secular_batch")
+        out.append(p)
+    return out

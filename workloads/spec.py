@@ -19,6 +19,11 @@ channel's value (so ``eps(t) a^dag + eps(t)^* a`` is two terms on one channel). 
 with ``param >= 0`` has coefficient ``coef * params[param]``; these real parameters, and
 the segment values of ``pwc`` channels, are what gradients are taken with respect to.
 
+A *secular damping* entry is the paper's proper (secular) dissipator of one anharmonic mode
+(Eq. 203 / Eq. S9): rate ``kappa`` and, per transition n <-> n+1, the thermal occupation
+``nbar[n]`` (Eq. S10: the bath occupation at the transition frequency omega + 2 eta n;
+entries beyond the tuple are 0, an empty tuple is the zero-temperature case).
+
 Only data lives here; the envelopes are evaluated separately by each consumer.
 """
 
@@ -58,6 +63,16 @@ class Jump:
     terms: Tuple[Tuple[complex, Index, Index], ...]  # (c_t, u_t, v_t)
 
 
+@dataclass(frozen=True)
+class SecularDamping:
+    mode: int
+    kappa: float
+    nbar: Tuple[float, ...] = ()
+
+    def nbar_at(self, n: int) -> float:
+        return float(self.nbar[n]) if 0 <= n < len(self.nbar) else 0.0
+
+
 @dataclass
 class Problem:
     n_modes: int
@@ -72,6 +87,7 @@ class Problem:
     rho0: Optional[Dict[Tuple[Index, Index], complex]] = None  # None: vacuum
     reverse_time: bool = True  # Heisenberg reading: integrate tau in [0, T] with t = T - tau
     name: str = ""
+    secular: List[SecularDamping] = field(default_factory=list)
 
     @property
     def n_steps(self) -> int:
