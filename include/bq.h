@@ -107,6 +107,15 @@ int bq_problem_set_params(bq_problem* p, const double* values, int n);
 int bq_problem_add_jump(bq_problem* p, double kappa, int n_terms, const double* c_re,
                         const double* c_im, const int* u, const int* v);
 
+/* Adds the secular ("proper") dissipator of Eq. 203 / Eq. S9 to mode `mode`: rate kappa >= 0
+ * and, for n = 0..n_nbar-1, the thermal occupation nbar[n] >= 0 of the bath at the n <-> n+1
+ * transition frequency (Eq. S10; n >= n_nbar: 0; n_nbar = 0 is zero temperature).  In the
+ * mapped representation it is a separable decay plus the projector term P of Eq. 302c /
+ * Eq. S15, which acts only where the x and y indices of the mode agree; states with such a
+ * term are stepped by the tiled stage kernel (any mode count) and bq_grad returns
+ * BQ_EUNSUPPORTED for them.  BQ_EINVAL for a bad mode, rate or occupation. */
+int bq_problem_add_secular(bq_problem* p, int mode, double kappa, int n_nbar, const double* nbar);
+
 /* Measured operator A(0) by number-basis elements <k|A|l> = re + i im; k, l are n x n_modes
  * row-major.  Repeated (k, l) pairs add up. */
 int bq_problem_set_measured(bq_problem* p, int n, const int* k, const int* l, const double* re,

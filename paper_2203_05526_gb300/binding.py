@@ -76,6 +76,7 @@ def lib() -> C.CDLL:
         "bq_problem_add_h_term": (C.c_int, [vp, C.c_double, C.c_double, ip, ip, C.c_int, C.c_int, C.c_int]),
         "bq_problem_set_params": (C.c_int, [vp, dp, C.c_int]),
         "bq_problem_add_jump": (C.c_int, [vp, C.c_double, C.c_int, dp, dp, ip, ip]),
+        "bq_problem_add_secular": (C.c_int, [vp, C.c_int, C.c_double, C.c_int, dp]),
         "bq_problem_set_measured": (C.c_int, [vp, C.c_int, ip, ip, dp, dp]),
         "bq_problem_set_rho0": (C.c_int, [vp, C.c_int, ip, ip, dp, dp]),
         "bq_required_bytes": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(bq_map_opts), C.POINTER(C.c_size_t)]),
@@ -175,6 +176,11 @@ class ProblemHandle:
         v = [x for _, _, vv in terms for x in vv]
         check(lib().bq_problem_add_jump(self.ptr, rate, len(terms), _darr(cre), _darr(cim), _iarr(u), _iarr(v)))
 
+    def add_secular(self, mode: int, kappa: float, nbar=()):
+        nbar = [float(x) for x in nbar]
+        check(lib().bq_problem_add_secular(self.ptr, int(mode), float(kappa), len(nbar),
+                                           _darr(nbar) if nbar else None))
+
     def _elems(self, fn, elems):
         items = list(elems.items())
         k = [x for (kk, _), _ in items for x in kk]
@@ -201,6 +207,8 @@ def problem_from_spec(spec) -> ProblemHandle:
         h.add_h_term(complex(t.coef), t.u, t.v, t.channel, t.conj, t.param)
     for j in spec.jumps:
         h.add_jump(j.rate, j.terms)
+    for sd in getattr(spec, "secular", []):
+        h.add_secular(sd.mode, sd.kappa, sd.nbar)
     h.set_measured(spec.measured)
     if spec.rho0 is not None:
         h.set_rho0(spec.rho0)

@@ -68,6 +68,12 @@ struct ChannelH {
   int kind;
   std::vector<double> par;
 };
+struct SecularH {  // secular dissipator of one mode (Eq. 203 / Eq. S9)
+  int mode;
+  double kappa;
+  std::vector<double> nbar;  // nbar[n]: occupation at the n <-> n+1 transition; 0 beyond
+  double nb(int n) const { return n >= 0 && n < (int)nbar.size() ? nbar[n] : 0.0; }
+};
 using Key = std::pair<std::vector<int>, std::vector<int>>;
 
 struct bq_problem {
@@ -75,6 +81,7 @@ struct bq_problem {
   std::vector<int> N;
   std::vector<HTermH> h;
   std::vector<JumpH> jumps;
+  std::vector<SecularH> sec;
   std::vector<ChannelH> ch;
   std::vector<double> params;
   std::map<Key, cplx> measured, rho0;
@@ -146,6 +153,17 @@ extern "C" int bq_problem_add_jump(bq_problem* p, double kappa, int n_terms, con
     j.v.emplace_back(v + t * p->nm, v + (t + 1) * p->nm);
   }
   p->jumps.push_back(std::move(j));
+  return BQ_OK;
+}
+
+extern "C" int bq_problem_add_secular(bq_problem* p, int mode, double kappa, int n_nbar, const double* nbar) {
+  if (!p) return fail(BQ_EINVAL, "problem is NULL");
+  if (mode < 0 || mode >= p->nm) return fail(BQ_EINVAL, "mode %d outside 0..%d", mode, p->nm - 1);
+  if (!(kappa >= 0.0)) return fail(BQ_EINVAL, "secular rate must be >= 0");
+  if (n_nbar < 0 || (n_nbar > 0 && !nbar)) return fail(BQ_EINVAL, "bad nbar arguments");
+  for (int n = 0; n < n_nbar; ++n)
+    if (!(nbar[n] >= 0.0) || !std::isfinite(nbar[n])) return fail(BQ_EINVAL, "nbar[%d] must be finite and >= 0", n);
+  p->sec.push_back({mode, kappa, std::vector<double>(nbar, nbar + n_nbar)});
   return BQ_OK;
 }
 
@@ -443,6 +461,53 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
     rho_terms += std::abs(c) * (ch >= 0 ? chan_max(p->ch[ch]) : 1.0) * wmax_num;
   }
 
+  // ---- secular dissipators (Eq. 203 / Eq. S9) ---------------------------------------
+  // In g_{k,l} the adjoint is a separable decay -kappa/2 [a(k_j) + a(l_j)],
+  // a(m) = m (1 + nbar_{m-1}) + (m + 1) nbar_m, which joins the diagonal tables, plus two
+  // jump terms restricted to k_j = l_j: g_{m,m} += kappa (1 + nbar_{m-1}) g_{m-1,m-1} and
+  // g_{m,m} += kappa (m+1)^2 nbar_m g_{m+1,m+1} (the projector P of Eq. 302c / Eq. S15),
+  // written as x y and d_x d_y stencils with diagonal-restricted sandwich terms.
+  for (const SecularH& sh : p->sec) {
+    if (sh.kappa == 0.0) continue;
+    const int j = sh.mode, Mj = C.M[j];
+    for (int m = 0; m < Mj; ++m) {
+      const double a = m * (1.0 + sh.nb(m - 1)) + (m + 1) * sh.nb(m);
+      C.diag[doff[j] + m] += -0.5 * sh.kappa * a;
+      C.diag[doff[nm + j] + m] += -0.5 * sh.kappa * a;
+    }
+    if (!C.has_r) continue;
+    bool any_up = false;
+    for (int m = 0; m + 1 < Mj; ++m) any_up = any_up || sh.nb(m) > 0.0;
+    for (int dir = 0; dir < (any_up ? 2 : 1); ++dir) {  // 0: source m-1 (x y), 1: source m+1 (d_x d_y)
+      const int a = dir == 0 ? 1 : 0, b = dir == 0 ? 0 : 1;
+      TermDesc td;
+      std::memset(&td, 0, sizeof(td));
+      td.c_re = 1.0; td.cb_re = 1.0; td.ch = -1; td.side = bq::SIDE_S; td.param = -1;
+      td.gslot_param = -1; td.gslot_pwc = -1;
+      td.n_act = 2;
+      td.diagp1 = (int8_t)(j + 1);
+      td.dim[0] = (int8_t)j; td.dim[1] = (int8_t)(nm + j);
+      td.sh[0] = td.sh[1] = (int8_t)(b - a);
+      double wmax = 0.0;
+      td.wtab[0] = (int)C.wtab.size();
+      for (int m = 0; m < Mj; ++m) {
+        const double rate = dir == 0 ? sh.kappa * (1.0 + sh.nb(m - 1)) : sh.kappa * sh.nb(m);
+        C.wtab.push_back(rate * weight(a, b, m, Mj, C.basis));
+        wmax = std::max(wmax, rate * weight(a, b, m, Mj, BQ_BASIS_NUMBER) * weight(a, b, m, Mj, BQ_BASIS_NUMBER));
+      }
+      td.wtab[1] = (int)C.wtab.size();
+      for (int l = 0; l < Mj; ++l) C.wtab.push_back(weight(a, b, l, Mj, C.basis));
+      td.deltaR = (b - a) * (stR[j] + stR[nm + j]);
+      td.deltaGx = (b - a) * stG[j];
+      td.deltaGy = (b - a) * stG[j];
+      C.halo_lo = std::max(C.halo_lo, std::abs(td.deltaR));
+      C.halo_hi = C.halo_lo;
+      C.terms.push_back(td);
+      rho_terms += wmax;
+    }
+  }
+  if ((int)C.terms.size() > BQ_MAX_TERMS) return fail(BQ_EUNSUPPORTED, "%zu stencil terms > %d", C.terms.size(), BQ_MAX_TERMS);
+
   // ---- stability bound: max |diag| over the grid + sum of off-diagonal magnitudes ----
   {
     double dmax = 0.0;
@@ -598,6 +663,7 @@ struct bq_state {
   int use_pipe = 0, pipe_off_coef = 0, pipe_off_u = 0, pipe_off_y = 0, pipe_off_acc = 0, pipe_off_comp = 0;
   int pipe_slot[3] = {0, 0, 0}, pipe_nslots[3] = {2, 2, 2}, pipe_grid[3] = {1, 1, 1}, pipe_mv_bytes = 0;
   int n_coef_dyn = 0;  // time-dependent stage coefficients (k_coef_dyn entries)
+  int has_diag = 0;     // some term acts only on diagonal index pairs (secular dissipator)
   int ng_max = 0;      // largest G_x / G_y point count over the systems
   // schedules (bq_get_tune / bq_set_tune / bq_autotune)
   int pipe_ok = 0;      // the pipelined path is available (single mode, two slots fit)
@@ -788,6 +854,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
       m.M = M; m.has_sep = C.has_sep; m.has_r = C.has_r;
       for (int t = 0; t < (int)C.terms.size() && ok; ++t) {
         const TermDesc& td = C.terms[t];
+        if (td.diagp1) { ok = false; break; }  // diagonal-restricted terms: tiled kernel only
         const int woff = P.wbase[b];
         if (td.side == bq::SIDE_X) {
           if (m.nX == BQ_M1_MAXT) { ok = false; break; }
@@ -1173,6 +1240,7 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   st->solve_ok = P.order.empty() ? 0 : 1;
   st->use_pipe = P.use_pipe;
   st->n_coef_dyn = (int)P.pcdyn.size();
+  for (const TermDesc& td : P.terms) st->has_diag = st->has_diag || td.diagp1 != 0;
   st->pipe_off_coef = P.pipe_off_coef; st->pipe_off_u = P.pipe_off_u; st->pipe_off_y = P.pipe_off_y;
   st->pipe_off_acc = P.pipe_off_acc; st->pipe_off_comp = P.pipe_off_comp;
   for (int q = 0; q < 3; ++q) st->pipe_slot[q] = P.pipe_slot[q];
@@ -1695,6 +1763,7 @@ static int set_tau(bq_state* s, double tau, cudaStream_t st) {
 
 extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_every, void* work, size_t work_bytes,
                        double* loss_out, double* grad_out, void* stream) {
+  if (s && s->has_diag) return fail(BQ_EUNSUPPORTED, "gradients with secular dissipators are not implemented");
   if (!s || !work || !loss_out || !grad_out) return fail(BQ_EINVAL, "NULL argument");
   if (n_steps < 1 || checkpoint_every < 1 || !(dt > 0.0)) return fail(BQ_EINVAL, "bad step arguments");
   if (dt > s->dt_max * (1.0 + 1e-12)) return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 bound %g", dt, s->dt_max);

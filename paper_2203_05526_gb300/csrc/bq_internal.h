@@ -32,7 +32,8 @@ struct TermDesc {
   int deltaGy;         // linear source offset in G_y (SIDE_Y, SIDE_S y-part)
   int param;           // gradient parameter index or -1 (coefficient = theta * c)
   int8_t dim[BQ_MAXD];
-  int8_t pad8[2];
+  int8_t diagp1;       // 0: everywhere; j + 1: only where the x and y indices of mode j agree
+  int8_t pad8;
   int wtab[BQ_MAXD];   // element offsets of the weight tables (length M_dim each)
   // gradient metadata
   double cb_re, cb_im; // coefficient with the parameter value set to 1

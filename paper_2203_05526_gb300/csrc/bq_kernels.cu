@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
       C k = cmul(dg, uc);
       for (int t = 0; t < nt; ++t) {
         const TermDesc& td = st[t];
+        if (td.diagp1 && idx[td.diagp1 - 1] != idx[NM + td.diagp1 - 1]) continue;  // projector P
         T wx = (T)1, wy = (T)1;
         for (int i = 0; i < td.n_act; ++i) {
           const int d = td.dim[i];

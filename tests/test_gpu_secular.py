@@ -1,0 +1,112 @@
+"""The secular dissipator (Eq. 203 / Eq. S9) on the GPU: the diagonal-restricted projector
+term of the tiled stage kernel against the oracles, element by element."""
+
+import math
+
+import numpy as np
+import pytest
+
+import paper_2203_05526_gb300 as bq
+from paper_2203_05526_gb300.binding import BQ_EUNSUPPORTED
+from oracle import fock, mapping
+from workloads import configs
+
+from parity import compare_mapped_systems, gpu_state, rel_err
+
+pytestmark = pytest.mark.gpu
+TWO_PI = 2.0 * math.pi
+TOL64, TOL32 = 1e-10, 1e-5
+KT = TWO_PI * 1.64  # nbar_0 ~ 0.05 at 5 GHz
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    from paper_2203_05526_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def _single(N=9, T=0.6, dt=0.005, kT=KT, dense=True, drive=TWO_PI * 0.3):
+    meas = ({((1,), (2,)): 0.4 + 0.1j, ((2,), (1,)): 0.4 - 0.1j, ((3,), (3,)): 1.0, ((0,), (0,)): 0.2}
+            if dense else None)
+    return configs.kerr_secular(N=N, T=T, dt=dt, kappa=0.4, kT=kT, measured=meas, drive_peak=drive)
+
+
+@pytest.mark.parametrize("kT", [0.0, KT])
+def test_single_mode_mapped_f64_matches_oracle(kT):
+    p = _single(kT=kT)
+    st = gpu_state(p)
+    assert st.stage_variant() == "generic"
+    st.step(p.dt, p.n_steps)
+    _sync()
+    compare_mapped_systems(st, mapping.rk4_mapped(p), TOL64)
+
+
+def test_single_mode_mapped_f32_matches_oracle():
+    p = _single(N=12, T=0.6)
+    st = gpu_state(p, dtype="f32")
+    st.step(p.dt, p.n_steps)
+    _sync()
+    compare_mapped_systems(st, mapping.rk4_mapped(p), TOL32)
+
+
+def test_direct_method_matches_number_basis_oracle():
+    p = _single(N=10)
+    st = gpu_state(p, method="direct")
+    st.step(p.dt, p.n_steps)
+    _sync()
+    A = fock.rk4_adjoint(p)
+    _, _, _, r = st.read_system(0)
+    assert rel_err(r, A.reshape(-1)) <= TOL64
+
+
+def test_two_modes_match_oracle():
+    p = configs.two_mode_secular(N=4, T=0.4, dt=0.01, kappa=0.3, kT=KT)
+    p.measured = {((1, 0), (0, 1)): 1.0 + 0.5j, ((0, 1), (1, 0)): 1.0 - 0.5j, ((1, 1), (1, 1)): 0.3}
+    st = gpu_state(p)
+    st.step(p.dt, p.n_steps)
+    _sync()
+    compare_mapped_systems(st, mapping.rk4_mapped(p), TOL64)
+    d = gpu_state(p, method="direct")
+    d.step(p.dt, p.n_steps)
+    _sync()
+    _, _, _, r = d.read_system(0)
+    assert rel_err(r, fock.rk4_adjoint(p).reshape(-1)) <= TOL64
+
+
+def test_projector_never_sources_off_diagonal_products():
+    """A(0) = a without drive at T_E = 0: every G_x G_y product is off-diagonal, so the
+    residual stays exactly zero on the GPU too (a missing diagonal restriction would
+    source it at every point)."""
+    N = 8
+    meas = {((k,), (k + 1,)): math.sqrt(k + 1) for k in range(N - 1)}
+    p = configs.kerr_secular(N=N, T=0.5, dt=0.005, kappa=0.4, kT=0.0, measured=meas, drive_peak=0.0)
+    st = gpu_state(p)
+    st.step(p.dt, p.n_steps)
+    _sync()
+    for s in range(st.n_systems()):
+        _, gx, gy, r = st.read_system(s)
+        assert np.max(np.abs(r)) == 0.0
+        assert np.max(np.abs(gx)) > 0.0
+    compare_mapped_systems(st, mapping.rk4_mapped(p), TOL64)
+
+
+def test_batch_schedules_and_refusals():
+    ps = configs.secular_batch(B=48, T=0.2, dt=0.002, n_min=10, n_max=20)
+    st = gpu_state(ps, dtype="f32")
+    assert st.stage_variant() == "generic" and not st.solve_eligible()
+    tune = st.autotune(ps[0].dt, trial_steps=2)
+    assert tune["stage_path"] == "tiled" and tune["solve_kernel"] is None
+    st.solve(ps[0].dt, ps[0].n_steps)  # falls back to stepping
+    _sync()
+    for i in (0, 23, 47):
+        compare_mapped_systems(st, mapping.rk4_mapped(ps[i]), TOL32, sys_offset=i, n_sys=i + 1)
+    with pytest.raises(bq.BQError) as e:
+        gpu_state(_single()).grad(0.005, 10, 5)
+    assert e.value.args[0].startswith(f"bq status {BQ_EUNSUPPORTED}")
