@@ -18,6 +18,7 @@ during the timed region), ``gpu_launches`` (library kernel launches in the timed
 one instance per launch), ``grads`` (the 131-parameter control gradient, and 16 control
 problems batched in one state vs one problem per state), ``methods`` (memory and time per
 step of the conventional number-basis method vs the mapping with full R and with R = 0),
+``secular`` (the paper's secular dissipator on the same instances: updates/s and HBM GB/s),
 and ``config.schedule`` (the schedule bq_autotune picked for the timed state).
 
 ``--impl reference`` times the oracle (the plain FP64 CPU implementation) on the same
@@ -365,6 +366,35 @@ def methods_leg(B: int = 1024, Ns=(10, 20, 40), steps: int = 100):
                         f"{steps} RK4 steps of dt={DT} ns", "rows": rows}
 
 
+def secular_leg(B: int = 32768, steps: int = 20):
+    """The paper's secular dissipator (Eq. 203 / Eq. S9, zero temperature) on kerr_batch's
+    instances (secular_batch: same draws, complex FP32): grid-point RK-stage updates/s of the
+    tiled stage kernel (the projector term is restricted to diagonal index pairs) and its HBM
+    bandwidth for the same 19/4 array transfers per point and stage."""
+    import torch
+
+    import paper_2203_05526_gb300 as bq
+    from workloads import configs
+    specs = configs.secular_batch(B=B, T=HORIZON, dt=DT, n_min=N_RANGE[0], n_max=N_RANGE[1])
+    st = bq.State([bq.problem_from_spec(p) for p in specs], bq.map_opts(dtype="f32", horizon=HORIZON, dt=DT))
+    st.step(DT, 3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st.step(DT, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    s_step = e0.elapsed_time(e1) / 1e3 / steps
+    pts = points_of(specs)
+    achieved = 19 * 8 * pts / 4 / (s_step / 4) / 1e9
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    return {"workload": f"secular_batch x{B} (kerr_batch draws, secular dissipator, T_E = 0), complex FP32, "
+                        f"{steps} RK4 steps", "kernel": "bq::k_stage (tiled, " + st.stage_variant() + ")",
+            "updates_per_s": 4 * pts / s_step, "ms_per_step": 1e3 * s_step,
+            "achieved_gbs": achieved, "frac_of_measured_hbm": achieved / peak}
+
+
 def run_reference(args, rank, world):
     """Oracle arm: rank 0 only, bounded samples of the same workload on the host cores."""
     if rank != 0:
@@ -525,8 +555,10 @@ def main():
     if not args.no_grads and world == 1:
         grads = grads_leg()
     methods = None
+    secular = None
     if not args.no_batched and world == 1:
         methods = methods_leg()
+        secular = secular_leg()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -545,7 +577,7 @@ def main():
                                                                  "n_candidates", "step_us")},
                            "state_bytes_per_array": nbytes, "l2": "inputs larger than L2 (4 arrays x "
                            f"{nbytes / 1e6:.0f} MB vs 129 MB)", "parallelism": f"replicas x{world}"},
-                "roofline": roof, "e2e": e2e, "batched": batched, "grads": grads, "methods": methods, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches}
+                "roofline": roof, "e2e": e2e, "batched": batched, "grads": grads, "methods": methods, "secular": secular, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
