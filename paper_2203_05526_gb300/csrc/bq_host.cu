@@ -854,7 +854,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
       m.M = M; m.has_sep = C.has_sep; m.has_r = C.has_r;
       for (int t = 0; t < (int)C.terms.size() && ok; ++t) {
         const TermDesc& td = C.terms[t];
-        if (td.diagp1) { ok = false; break; }  // diagonal-restricted terms: tiled kernel only
+        if (td.diagp1 && td.side != bq::SIDE_S) { ok = false; break; }
         const int woff = P.wbase[b];
         if (td.side == bq::SIDE_X) {
           if (m.nX == BQ_M1_MAXT) { ok = false; break; }
@@ -864,6 +864,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
           m.sY[m.nY] = td.deltaGy; m.wY[m.nY] = td.n_act ? td.wtab[0] + woff : -1; m.tY[m.nY++] = t;
         } else {
           if (m.nS == BQ_M1_MAXT) { ok = false; break; }
+          if (td.diagp1) m.sdiag |= 1 << m.nS;  // single mode: only where k = l
           m.sSx[m.nS] = td.deltaGx; m.sSy[m.nS] = td.deltaGy; m.wSx[m.nS] = -1; m.wSy[m.nS] = -1;
           for (int a = 0; a < td.n_act; ++a) {
             if (td.dim[a] == 0) m.wSx[m.nS] = td.wtab[a] + woff; else m.wSy[m.nS] = td.wtab[a] + woff;
@@ -899,6 +900,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
         const bq::M1Sys& m = P.m1[i];
         const int ntot = (m.has_r ? m.M * m.M : 0) + (m.has_sep ? 2 * m.M : 0);
         if (ntot > 1792) solve_ok = false;
+        if (m.sdiag) solve_ok = false;  // the persistent solve has no diagonal-restricted terms
         const size_t bytes = (size_t)(2 * ntot + 2 * m.M) * cs + (size_t)(m.nX + m.nY + 2 * m.nS) * m.M * rs;
         solve_max = std::max(solve_max, bytes);
         sz.push_back({-ntot, i});
@@ -914,6 +916,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
           bq::PipeHdr hd;
           std::memset(&hd, 0, sizeof(hd));
           hd.M = M; hd.nX = m.nX; hd.nY = m.nY; hd.nS = m.nS; hd.has_sep = C.has_sep; hd.has_r = C.has_r;
+          hd.sdiag = m.sdiag;
           hd.ntot = (C.has_r ? M * M : 0) + (C.has_sep ? 2 * M : 0);
           for (int q = 0; q < BQ_M1_MAXT; ++q) { hd.sX[q] = m.sX[q]; hd.sY[q] = m.sY[q]; hd.sSx[q] = m.sSx[q]; hd.sSy[q] = m.sSy[q]; }
           {

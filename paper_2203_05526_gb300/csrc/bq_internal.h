@@ -108,7 +108,8 @@ struct M1Sys {
   int sX[BQ_M1_MAXT], sY[BQ_M1_MAXT], sSx[BQ_M1_MAXT], sSy[BQ_M1_MAXT];
   int wX[BQ_M1_MAXT], wY[BQ_M1_MAXT], wSx[BQ_M1_MAXT], wSy[BQ_M1_MAXT];  // -1: weight 1
   int tX[BQ_M1_MAXT], tY[BQ_M1_MAXT], tS[BQ_M1_MAXT];
-  int pad[4];
+  int sdiag;  // bit q: sandwich term q acts only where k = l (secular projector)
+  int pad[3];
   int64_t off_gx, off_gy, off_r;
   int64_t pad64;
   double c_re, c_im;
@@ -156,7 +157,8 @@ struct __align__(16) PipeRec {
 struct PipeHdr {
   int M, nX, nY, nS, has_sep, has_r, ntot, merged;  // merged: all shifts in {-1,0,1}, nS <= 2, M <= 64
   int sX[BQ_M1_MAXT], sY[BQ_M1_MAXT], sSx[BQ_M1_MAXT], sSy[BQ_M1_MAXT];
-  int pad2[8];
+  int sdiag;  // bit q: sandwich term q acts only where k = l (secular projector)
+  int pad2[7];
 };
 #define BQ_PIPE_THREADS 128  // threads of a pipelined stage CTA
 #define BQ_PIPE_COEF 16  // complex coefficients per system and stage: X, Y, S terms, C at slot 15

@@ -11,6 +11,7 @@
 // per point, so it never touches the tensor cores.  Loads of the stage input are staged
 // once per CTA in shared memory (halo re-reads come from there), the state, stage output
 // and accumulator are streamed with coalesced accesses.
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -446,7 +447,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage_m1(const StageArgs A, const 
         }
 #pragma unroll
       for (int j = 0; j < MS; ++j)
-        if (j < nS) {
+        if (j < nS && (!((s.sdiag >> j) & 1) || kx == ly)) {  // secular projector: k = l only
           const int r = min(max(kx + shSx[j], 0), M - 1);
           const int c = min(max(ly + shSy[j], 0), M - 1);
           C v = u[r * M + c];
@@ -702,6 +703,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
     unsigned char* sl = slot_ptr(j % S);
     const PipeHdr& h = *reinterpret_cast<const PipeHdr*>(sl);
     const int M = h.M, nX = h.nX, nY = h.nY, nS = h.nS, has_sep = h.has_sep;
+    const int sdiag = h.sdiag;  // bit q: sandwich term q acts only where k = l
     const C* dx = reinterpret_cast<const C*>(sl + sizeof(PipeHdr));
     const C* dy = dx + M;
     const T* wX = reinterpret_cast<const T*>(dy + M);
@@ -833,37 +835,43 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
         }
         C um = k0 > 0 ? ur[(k0 - 1) * M + l] : zero;  // u(k-1, l)
         C uc = ur[k0 * M + l];                          // u(k, l)
-        // state / stage sum / compensation: a register ring two rows ahead of use
-        for (int kk = k0; kk < k1; ++kk) {
-          const int pos = r.r_off + kk * M + l;
-          const int64_t gi = (int64_t)r.blk_off + pos;
-          const C yv = y0, av = a0v, cv = c0;
-          y0 = y1; a0v = a1; c0 = c1;
-          if (stage > 1 && kk + 2 < k1) {
-            y1 = yg[gi + 2 * M];
-            a1 = accg[gi + 2 * M];
-            if (stage == 4) c1 = compg[gi + 2 * M];
-          }
-          const int c = kk * M + l;
-          const C up = kk + 1 < M ? ur[c + M] : zero;
-          const C ul = cm ? ur[c - 1] : zero;
-          const C urr = cp ? ur[c + 1] : zero;
-          C kv = cmul(cadd(A0[kk], b0), uc);
-          kv = cfma(Am[kk], um, kv);
-          kv = cfma(Ap[kk], up, kv);
-          kv = cfma(bm, ul, kv);
-          kv = cfma(bp, urr, kv);
-#pragma unroll
-          for (int q = 0; q < MS; ++q)
-            if (q < nS) {
-              const int xx = kk + ssx[q];
-              const C v = (scol[q] && xx >= 0 && xx < M) ? ur[c + soff[q]] : zero;
-              kv = cfma(SXv[q * M + kk], cadd(cscale(v, sy[q]), cmul(GXv[q * M + kk], gy[q])), kv);
+        // state / stage sum / compensation: a register ring two rows ahead of use.  The
+        // diagonal restriction of a secular projector term costs a test per row and term,
+        // so only systems that have one run the tested form of the row loop.
+        auto rows = [&](auto diag_tag) {
+          constexpr bool DIAG = decltype(diag_tag)::value;
+          for (int kk = k0; kk < k1; ++kk) {
+            const int pos = r.r_off + kk * M + l;
+            const int64_t gi = (int64_t)r.blk_off + pos;
+            const C yv = y0, av = a0v, cv = c0;
+            y0 = y1; a0v = a1; c0 = c1;
+            if (stage > 1 && kk + 2 < k1) {
+              y1 = yg[gi + 2 * M];
+              a1 = accg[gi + 2 * M];
+              if (stage == 4) c1 = compg[gi + 2 * M];
             }
-          combine_reg(gi, uc, kv, yv, av, cv);
-          um = uc;
-          uc = up;
-        }
+            const int c = kk * M + l;
+            const C up = kk + 1 < M ? ur[c + M] : zero;
+            const C ul = cm ? ur[c - 1] : zero;
+            const C urr = cp ? ur[c + 1] : zero;
+            C kv = cmul(cadd(A0[kk], b0), uc);
+            kv = cfma(Am[kk], um, kv);
+            kv = cfma(Ap[kk], up, kv);
+            kv = cfma(bm, ul, kv);
+            kv = cfma(bp, urr, kv);
+#pragma unroll
+            for (int q = 0; q < MS; ++q)
+              if (q < nS && (!DIAG || !((sdiag >> q) & 1) || kk == l)) {  // secular projector: k = l only
+                const int xx = kk + ssx[q];
+                const C v = (scol[q] && xx >= 0 && xx < M) ? ur[c + soff[q]] : zero;
+                kv = cfma(SXv[q * M + kk], cadd(cscale(v, sy[q]), cmul(GXv[q * M + kk], gy[q])), kv);
+              }
+            combine_reg(gi, uc, kv, yv, av, cv);
+            um = uc;
+            uc = up;
+          }
+        };
+        if (sdiag) rows(std::true_type{}); else rows(std::false_type{});
       }
       if (gq >= 0) {
         const bool isx = gq < M;
@@ -920,7 +928,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
           if (q < nY) kv = cfma(cY[q], cscale(ur[kx * M + min(max(ly + shY[q], 0), M - 1)], wY[q * M + ly]), kv);
 #pragma unroll
         for (int q = 0; q < MS; ++q)
-          if (q < nS) {
+          if (q < nS && (!((sdiag >> q) & 1) || kx == ly)) {  // secular projector: k = l only
             const int rr = min(max(kx + shSx[q], 0), M - 1);
             const int cc = min(max(ly + shSy[q], 0), M - 1);
             C v = ur[rr * M + cc];

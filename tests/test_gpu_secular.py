@@ -1,5 +1,6 @@
 """The secular dissipator (Eq. 203 / Eq. S9) on the GPU: the diagonal-restricted projector
-term of the tiled stage kernel against the oracles, element by element."""
+term in every stage kernel that runs it (pipelined, one CTA per system, tiled) against the
+oracles, element by element."""
 
 import math
 
@@ -41,8 +42,27 @@ def _single(N=9, T=0.6, dt=0.005, kT=KT, dense=True, drive=TWO_PI * 0.3):
 @pytest.mark.parametrize("kT", [0.0, KT])
 def test_single_mode_mapped_f64_matches_oracle(kT):
     p = _single(kT=kT)
+    run = mapping.rk4_mapped(p)
     st = gpu_state(p)
-    assert st.stage_variant() == "generic"
+    assert st.stage_variant() == "pipelined"
+    st.step(p.dt, p.n_steps)
+    _sync()
+    compare_mapped_systems(st, run, TOL64)
+    st = gpu_state(p)
+    st.set_tune(stage_path="system")  # one CTA per system, per-term programs
+    st.step(p.dt, p.n_steps)
+    _sync()
+    compare_mapped_systems(st, run, TOL64)
+
+
+def test_general_pipelined_path_with_mixed_dissipators():
+    """Secular damping at finite temperature (two diagonal-restricted terms) plus a
+    conventional thermal jump pair: three sandwich terms take the pipelined kernel's
+    per-term loop instead of the merged one."""
+    p = _single(N=8)
+    p.jumps = configs.damping_jumps(1, 0, 0.1, 0.2)
+    st = gpu_state(p)
+    assert st.stage_variant() == "pipelined"
     st.step(p.dt, p.n_steps)
     _sync()
     compare_mapped_systems(st, mapping.rk4_mapped(p), TOL64)
@@ -100,9 +120,9 @@ def test_projector_never_sources_off_diagonal_products():
 def test_batch_schedules_and_refusals():
     ps = configs.secular_batch(B=48, T=0.2, dt=0.002, n_min=10, n_max=20)
     st = gpu_state(ps, dtype="f32")
-    assert st.stage_variant() == "generic" and not st.solve_eligible()
+    assert st.stage_variant() == "pipelined" and not st.solve_eligible()
     tune = st.autotune(ps[0].dt, trial_steps=2)
-    assert tune["stage_path"] == "tiled" and tune["solve_kernel"] is None
+    assert tune["stage_path"] in ("pipe", "system") and tune["solve_kernel"] is None
     st.solve(ps[0].dt, ps[0].n_steps)  # falls back to stepping
     _sync()
     for i in (0, 23, 47):
