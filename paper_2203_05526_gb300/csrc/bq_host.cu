@@ -900,7 +900,6 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
         const bq::M1Sys& m = P.m1[i];
         const int ntot = (m.has_r ? m.M * m.M : 0) + (m.has_sep ? 2 * m.M : 0);
         if (ntot > 1792) solve_ok = false;
-        if (m.sdiag) solve_ok = false;  // the persistent solve has no diagonal-restricted terms
         const size_t bytes = (size_t)(2 * ntot + 2 * m.M) * cs + (size_t)(m.nX + m.nY + 2 * m.nS) * m.M * rs;
         solve_max = std::max(solve_max, bytes);
         sz.push_back({-ntot, i});
@@ -1491,6 +1490,7 @@ static cudaError_t enqueue_solve(bq_state* s, double dt, int64_t n_steps, cudaSt
   a.queue = (unsigned int*)(b + L.off_ctrl + 24);
   a.n_sys = s->n_sys;
   a.reverse = s->reverse;
+  a.has_diag = s->has_diag;
   a.n_steps = n_steps;
   a.dt = dt;
   a.tau0 = s->tau;

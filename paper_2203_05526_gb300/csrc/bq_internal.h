@@ -213,6 +213,8 @@ struct SolveArgs {
   unsigned int* queue;     // device: next queue position (zeroed before the launch)
   int n_sys;
   int reverse;
+  int has_diag;            // some system has a diagonal-restricted (secular) sandwich term
+  int pad_sa;
   long long n_steps;
   double dt, tau0, horizon;
 };

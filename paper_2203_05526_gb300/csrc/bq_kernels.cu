@@ -327,6 +327,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage_m1(const StageArgs A, const 
   }
   __syncthreads();
   const int M = s.M, nX = s.nX, nY = s.nY, nS = s.nS;
+  const int sdiag = s.sdiag;  // bit q: sandwich term q acts only where k = l
   const int has_r = s.has_r, has_sep = s.has_sep;
   const int nr = has_r ? M * M : 0;
   // shared layout: u[M*M] | gx[M] | gy[M] | dx[M] | dy[M] | wX[nX*M] wY[nY*M] wSx[nS*M] wSy[nS*M] (real)
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage_m1(const StageArgs A, const 
         }
 #pragma unroll
       for (int j = 0; j < MS; ++j)
-        if (j < nS && (!((s.sdiag >> j) & 1) || kx == ly)) {  // secular projector: k = l only
+        if (j < nS && (!((sdiag >> j) & 1) || kx == ly)) {  // secular projector: k = l only
           const int r = min(max(kx + shSx[j], 0), M - 1);
           const int c = min(max(ly + shSy[j], 0), M - 1);
           C v = u[r * M + c];
@@ -975,7 +976,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
 // barrier per stage.  Drive coefficients of the next stage are evaluated by a few threads
 // while the others compute.  There is no inter-CTA waiting of any kind.
 // ---------------------------------------------------------------------------------------
-template <typename T, int BLK, int PPT, int MX, int MY, int MS>
+template <typename T, int BLK, int PPT, int MX, int MY, int MS, bool DIAG>
 __global__ void __launch_bounds__(BLK, 2) k_solve_m1(const SolveArgs A) {
   using C = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -998,6 +999,7 @@ __global__ void __launch_bounds__(BLK, 2) k_solve_m1(const SolveArgs A) {
     }
     __syncthreads();
     const int M = s.M, nX = s.nX, nY = s.nY, nS = s.nS;
+    const int sdiag = s.sdiag;  // bit q: sandwich term q acts only where k = l
     const int has_r = s.has_r, has_sep = s.has_sep;
     const int nr = has_r ? M * M : 0;
     const int ntot = nr + (has_sep ? 2 * M : 0);
@@ -1106,7 +1108,7 @@ __global__ void __launch_bounds__(BLK, 2) k_solve_m1(const SolveArgs A) {
               if (q < nY) kv = cfma(cY[q], cscale(uin[kx * M + min(max(ly + shY[q], 0), M - 1)], wY[q * M + ly]), kv);
 #pragma unroll
             for (int q = 0; q < MS; ++q)
-              if (q < nS) {
+              if (q < nS && (!DIAG || !((sdiag >> q) & 1) || kx == ly)) {  // secular projector: k = l only
                 const int r = min(max(kx + shSx[q], 0), M - 1);
                 const int c = min(max(ly + shSy[q], 0), M - 1);
                 C v = uin[r * M + c];
@@ -1591,7 +1593,7 @@ __global__ void k_adj_seed(const SysDesc* __restrict__ sys, const EvalGroup* __r
 // registers for the whole solve.  One barrier per stage; coefficients are evaluated two
 // stages ahead (triple buffered), the merged vectors one stage ahead (double buffered).
 // ---------------------------------------------------------------------------------------
-template <typename T, int BLK, int RB, int MX, int MY, int MS>
+template <typename T, int BLK, int RB, int MX, int MY, int MS, bool DIAG>
 __global__ void __launch_bounds__(BLK) k_solve_mg(const SolveArgs A) {
   using C = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1615,6 +1617,7 @@ __global__ void __launch_bounds__(BLK) k_solve_mg(const SolveArgs A) {
     }
     __syncthreads();
     const int M = s.M, nX = s.nX, nY = s.nY, nS = s.nS;
+    const int sdiag = s.sdiag;  // bit q: sandwich term q acts only where k = l
     const int has_r = s.has_r, has_sep = s.has_sep;
     const int nr = has_r ? M * M : 0;
     const int ntot = nr + (has_sep ? 2 * M : 0);
@@ -1781,7 +1784,7 @@ __global__ void __launch_bounds__(BLK) k_solve_mg(const SolveArgs A) {
               kv = cfma(bp, urr, kv);
 #pragma unroll
               for (int q = 0; q < MS; ++q)
-                if (q < nS) {
+                if (q < nS && (!DIAG || !((sdiag >> q) & 1) || kk == cl)) {  // secular projector: k = l only
                   const int xx = kk + ssx[q];
                   const C v = (scol[q] && xx >= 0 && xx < M) ? uin[c + soff[q]] : zero;
                   const C gxv = (has_sep && xx >= 0 && xx < M) ? gxi[xx] : zero;
@@ -2034,12 +2037,10 @@ cudaError_t launch_stage_m1(const StageArgs& a, const M1Sys* m1, int variant, in
 
 template <typename T, int BLK, int PPT>
 static cudaError_t launch_solve_t(const SolveArgs& a, int smem_bytes, int cap_per_sm, cudaStream_t s, int* grid_out) {
-  auto kern = k_solve_m1<T, BLK, PPT, 2, 2, 2>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  auto kern = a.has_diag ? k_solve_m1<T, BLK, PPT, 2, 2, 2, true> : k_solve_m1<T, BLK, PPT, 2, 2, 2, false>;
+  {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, BQ_MAX_DYN_SMEM);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   int dev = 0, nsm = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -2058,12 +2059,11 @@ static cudaError_t launch_solve_t(const SolveArgs& a, int smem_bytes, int cap_pe
 
 template <typename T, int BLK, int RB>
 static cudaError_t launch_solve_mg_t(const SolveArgs& a, int smem_bytes, int cap_per_sm, cudaStream_t s, int* grid_out) {
-  auto kern = k_solve_mg<T, BLK, RB, BQ_M1_MAXT, BQ_M1_MAXT, 2>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  auto kern = a.has_diag ? k_solve_mg<T, BLK, RB, BQ_M1_MAXT, BQ_M1_MAXT, 2, true>
+                         : k_solve_mg<T, BLK, RB, BQ_M1_MAXT, BQ_M1_MAXT, 2, false>;
+  {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, BQ_MAX_DYN_SMEM);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   int dev = 0, nsm = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -2201,10 +2201,10 @@ static cudaError_t occupancy_with_smem(K kern, int threads, int smem_bytes, int*
 
 cudaError_t solve_blocks_per_sm(int dtype, int merged, int smem_bytes, int* out) {
   if (merged)
-    return dtype == 0 ? occupancy_with_smem(k_solve_mg<double, 256, 8, BQ_M1_MAXT, BQ_M1_MAXT, 2>, 256, smem_bytes, out)
-                      : occupancy_with_smem(k_solve_mg<float, 256, 8, BQ_M1_MAXT, BQ_M1_MAXT, 2>, 256, smem_bytes, out);
-  return dtype == 0 ? occupancy_with_smem(k_solve_m1<double, 448, 4, 2, 2, 2>, 448, smem_bytes, out)
-                    : occupancy_with_smem(k_solve_m1<float, 256, 7, 2, 2, 2>, 256, smem_bytes, out);
+    return dtype == 0 ? occupancy_with_smem(k_solve_mg<double, 256, 8, BQ_M1_MAXT, BQ_M1_MAXT, 2, false>, 256, smem_bytes, out)
+                      : occupancy_with_smem(k_solve_mg<float, 256, 8, BQ_M1_MAXT, BQ_M1_MAXT, 2, false>, 256, smem_bytes, out);
+  return dtype == 0 ? occupancy_with_smem(k_solve_m1<double, 448, 4, 2, 2, 2, false>, 448, smem_bytes, out)
+                    : occupancy_with_smem(k_solve_m1<float, 256, 7, 2, 2, 2, false>, 256, smem_bytes, out);
 }
 
 cudaError_t launch_stage(const StageArgs& a, int dtype, int nm, int n_work, int smem_bytes, cudaStream_t s) {

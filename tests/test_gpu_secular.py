@@ -120,13 +120,29 @@ def test_projector_never_sources_off_diagonal_products():
 def test_batch_schedules_and_refusals():
     ps = configs.secular_batch(B=48, T=0.2, dt=0.002, n_min=10, n_max=20)
     st = gpu_state(ps, dtype="f32")
-    assert st.stage_variant() == "pipelined" and not st.solve_eligible()
+    assert st.stage_variant() == "pipelined" and st.solve_eligible()
     tune = st.autotune(ps[0].dt, trial_steps=2)
-    assert tune["stage_path"] in ("pipe", "system") and tune["solve_kernel"] is None
-    st.solve(ps[0].dt, ps[0].n_steps)  # falls back to stepping
+    assert tune["stage_path"] in ("pipe", "system") and tune["solve_kernel"] in ("merged", "program")
+    st.solve(ps[0].dt, ps[0].n_steps)  # one persistent launch
     _sync()
     for i in (0, 23, 47):
         compare_mapped_systems(st, mapping.rk4_mapped(ps[i]), TOL32, sys_offset=i, n_sys=i + 1)
+    # both persistent-solve kernels against streamed stepping, FP64
+    ps64 = configs.secular_batch(B=24, T=0.1, dt=0.002, n_min=8, n_max=30)
+    for p in ps64[::5]:
+        p.secular = [configs.SecularDamping(0, 0.3, (0.05, 0.06, 0.07))]
+    ref = gpu_state(ps64)
+    ref.step(ps64[0].dt, ps64[0].n_steps)
+    _sync()
+    for kernel in ("merged", "program"):
+        sv = gpu_state(ps64)
+        sv.set_tune(solve_kernel=kernel)
+        sv.solve(ps64[0].dt, ps64[0].n_steps)
+        _sync()
+        for i in range(0, 24, 5):
+            for x, y in zip(sv.read_system(i)[1:], ref.read_system(i)[1:]):
+                if x is not None:
+                    assert rel_err(x, y) <= 1e-10, (kernel, i)
     with pytest.raises(bq.BQError) as e:
         gpu_state(_single()).grad(0.005, 10, 5)
     assert e.value.args[0].startswith(f"bq status {BQ_EUNSUPPORTED}")
