@@ -179,3 +179,46 @@ def test_off_diagonal_operator_keeps_zero_residual_without_drive():
     assert all(np.max(np.abs(ic[6])) == 0.0 for ic in run.ics)
     run_c = mapping.rk4_mapped(_osc(6, 0.3, meas, delta=0.5, kerr=-0.7, T=0.5, dt=0.01, standard=True))
     assert max(np.max(np.abs(ic[6])) for ic in run_c.ics) > 1e-3
+
+
+# ---- diagonal residual layout (R as a function of x_j y_j only) --------------------------
+@pytest.mark.parametrize("which", ["single_secular", "single_conventional", "two_uncoupled"])
+def test_diag_layout_exact_when_dynamics_keep_diagonality(which):
+    """With a diagonal measured operator, a diagonal Hamiltonian (Kerr, detuning) and either
+    dissipator, every term maps diagonal to diagonal, so the full residual R stays diagonal
+    and the diagonal layout must reproduce the full run to rounding."""
+    if which == "two_uncoupled":
+        p = configs.two_mode_secular(N=4, T=0.5, dt=0.01, kappa=0.3, kT=TWO_PI * 1.64)
+        p.h_terms = [t for t in p.h_terms if sum(t.u) == sum(t.v) and all(a == b for a, b in zip(t.u, t.v))]
+        p.channels = []
+        p.measured = {((1, 0), (1, 0)): 1.0, ((2, 1), (2, 1)): 0.5, ((0, 0), (0, 0)): 0.2}
+    else:
+        meas = {((1,), (1,)): 1.0, ((3,), (3,)): -0.4}
+        p = _osc(8, 0.3, meas, delta=0.4, kerr=-1.1, standard=(which == "single_conventional"),
+                 nbar=(0.05, 0.06, 0.07), T=0.5, dt=0.01)
+    full = mapping.rk4_mapped(p)
+    for ic in full.ics:
+        R = ic[6]
+        assert np.max(np.abs(R - np.diag(np.diag(R)))) == 0.0
+    diag = mapping.rk4_mapped(p, r_layout="diag")
+    A, B = full.fock_matrix(), diag.fock_matrix()
+    assert np.max(np.abs(A - B)) < 1e-14 * np.max(np.abs(A))
+    assert np.max(np.abs(B - fock.rk4_adjoint(p))) < 1e-6  # the separated run vs O1 (RK4 error)
+
+
+def test_diag_layout_approximation_is_first_order_in_kappa_t():
+    """With a drive the residual is not diagonal; keeping its x y part is an approximation
+    (the paper's observation) whose error grows like kappa t and stays well below that of
+    dropping R altogether (R = 0)."""
+    meas = {((k,), (k + 1,)): math.sqrt(k + 1) for k in range(7)}
+    errs = {}
+    for kappa in (0.002, 0.01):
+        p = configs.kerr_secular(N=8, T=5.0, dt=0.01, kappa=kappa, kT=0.0, drive_peak=TWO_PI * 0.05, measured=meas)
+        blk = lambda X: fock.low_block(X, (8,), 3)
+        full = blk(mapping.rk4_mapped(p).fock_matrix())
+        errs[kappa] = tuple(fock.eps_r(blk(mapping.rk4_mapped(p, r_layout=lay).fock_matrix()), full)
+                            for lay in ("diag", "off"))
+    for kappa, (e_diag, e_off) in errs.items():
+        assert e_diag < 0.5 * e_off
+    ratio = errs[0.01][0] / errs[0.002][0]
+    assert 3.5 < ratio < 6.5, ratio
