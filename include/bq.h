@@ -58,7 +58,7 @@ enum { BQ_CH_CONST = 0, BQ_CH_GAUSS = 1, BQ_CH_PWC = 2, BQ_CH_CEXP = 3 };
 
 enum { BQ_METHOD_MAPPED = 0, BQ_METHOD_DIRECT = 1 };
 enum { BQ_F64 = 0, BQ_F32 = 1 };
-enum { BQ_R_FULL = 0, BQ_R_OFF = 1 };
+enum { BQ_R_FULL = 0, BQ_R_OFF = 1, BQ_R_DIAG = 2 };
 /* Storage basis of the coefficients: MONOMIAL stores g_{k,l} as in Eq. 6; NUMBER stores
  * sqrt(k! l!) g_{k,l} (a diagonal similarity, exact in exact arithmetic; keeps FP32 in
  * range for large truncations).  AUTO = MONOMIAL for F64 mapped, NUMBER otherwise. */
@@ -73,7 +73,12 @@ typedef struct bq_state bq_state;
 typedef struct bq_map_opts {
   int method;        /* BQ_METHOD_*                                                     */
   int dtype;         /* BQ_F64 | BQ_F32: arithmetic and storage type of the state       */
-  int r_layout;      /* BQ_R_FULL | BQ_R_OFF (R ~ 0 when kappa t << 1, main text after Eq. 9) */
+  int r_layout;      /* BQ_R_FULL | BQ_R_OFF (R ~ 0 when kappa t << 1, main text after Eq. 9) |
+                      * BQ_R_DIAG (R kept only where k = l, i.e. as a function of the products
+                      * x_j y_j, the paper's observation with Fig. 2; Eq. 303c projected onto
+                      * those entries: exact when the dynamics keep R diagonal, an
+                      * approximation of order kappa t otherwise; mapped method, tiled stage
+                      * kernel, no gradients).  bq_read_system returns R expanded to n_g x n_g. */
   int basis;         /* BQ_BASIS_*                                                      */
   int c_mode;        /* BQ_C_EQ304 | BQ_C_ZERO: separation constant                     */
   int reverse_time;  /* 1: t = horizon - tau                                            */

@@ -29,7 +29,7 @@ BQ_EUNSUPPORTED = -7
 CH_KIND = {"const": 0, "gauss": 1, "pwc": 2, "cexp": 3}
 METHOD = {"mapped": 0, "direct": 1}
 DTYPE = {"f64": 0, "f32": 1}
-R_LAYOUT = {"full": 0, "off": 1}
+R_LAYOUT = {"full": 0, "off": 1, "diag": 2}
 BASIS = {"auto": 0, "monomial": 1, "number": 2}
 C_MODE = {"eq304": 0, "zero": 1}
 MAX_MODES = 3

@@ -243,7 +243,7 @@ struct RawTerm {
 };
 
 struct Compiled {
-  int nm, M[3], method, basis, has_sep, has_r;
+  int nm, M[3], method, basis, has_sep, has_r, r_diag = 0;
   int n_g, n_r;
   std::vector<TermDesc> terms;         // wtab offsets relative to this problem's weight block
   std::vector<double> wtab;            // weight tables
@@ -332,7 +332,10 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
   C.n_g = (int)ng;
   C.n_r = (int)(ng * ng);
   C.has_sep = o.method == BQ_METHOD_MAPPED ? 1 : 0;
-  C.has_r = (o.method == BQ_METHOD_DIRECT || o.r_layout == BQ_R_FULL) ? 1 : 0;
+  C.has_r = (o.method == BQ_METHOD_DIRECT || o.r_layout == BQ_R_FULL || o.r_layout == BQ_R_DIAG) ? 1 : 0;
+  C.r_diag = (o.method == BQ_METHOD_MAPPED && o.r_layout == BQ_R_DIAG) ? 1 : 0;
+  if (o.method == BQ_METHOD_DIRECT && o.r_layout == BQ_R_DIAG)
+    return fail(BQ_EINVAL, "the diagonal residual layout applies to the mapped method only");
   for (auto& t : p->h)
     if (t.param >= (int)p->params.size()) return fail(BQ_EINVAL, "H term uses param %d but only %zu set", t.param, p->params.size());
   int r = check_hermitian(p);
@@ -528,6 +531,15 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
     }
     C.rho = dmax + rho_terms;
   }
+  // diagonal residual layout: R holds its k = l entries only (index = flat k); a term
+  // contributes an R source only if it shifts x and y alike, at offset deltaGx
+  if (C.r_diag) {
+    C.n_r = C.n_g;
+    C.halo_lo = 0;
+    for (const TermDesc& td : C.terms)
+      if (td.deltaGx == td.deltaGy) C.halo_lo = std::max(C.halo_lo, std::abs(td.deltaGx));
+    C.halo_hi = C.halo_lo;
+  }
 
   C.n_params = (int)p->params.size();
   // ---- channels ----------------------------------------------------------------------
@@ -664,6 +676,7 @@ struct bq_state {
   int pipe_slot[3] = {0, 0, 0}, pipe_nslots[3] = {2, 2, 2}, pipe_grid[3] = {1, 1, 1}, pipe_mv_bytes = 0;
   int n_coef_dyn = 0;  // time-dependent stage coefficients (k_coef_dyn entries)
   int has_diag = 0;     // some term acts only on diagonal index pairs (secular dissipator)
+  int r_diag = 0;       // diagonal residual layout
   int ng_max = 0;      // largest G_x / G_y point count over the systems
   // schedules (bq_get_tune / bq_set_tune / bq_autotune)
   int pipe_ok = 0;      // the pipelined path is available (single mode, two slots fit)
@@ -736,7 +749,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
   if (!probs || B < 1 || !o) return fail(BQ_EINVAL, "bad map arguments");
   if (o->method != BQ_METHOD_MAPPED && o->method != BQ_METHOD_DIRECT) return fail(BQ_EINVAL, "method");
   if (o->dtype != BQ_F64 && o->dtype != BQ_F32) return fail(BQ_EINVAL, "dtype");
-  if (o->r_layout != BQ_R_FULL && o->r_layout != BQ_R_OFF) return fail(BQ_EINVAL, "r_layout");
+  if (o->r_layout != BQ_R_FULL && o->r_layout != BQ_R_OFF && o->r_layout != BQ_R_DIAG) return fail(BQ_EINVAL, "r_layout");
   const int nm = probs[0] ? probs[0]->nm : 0;
   const size_t cs = o->dtype == BQ_F64 ? 16 : 8;  // complex element size
   const size_t rs = cs / 2;
@@ -781,7 +794,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
       std::memset(&sd, 0, sizeof(sd));
       sd.prob = b; sd.nm = nm;
       for (int j = 0; j < 3; ++j) sd.M[j] = C.M[j];
-      sd.has_sep = C.has_sep; sd.has_r = C.has_r; sd.n_g = C.n_g; sd.n_r = C.n_r;
+      sd.has_sep = C.has_sep; sd.has_r = C.has_r; sd.n_g = C.n_g; sd.n_r = C.n_r; sd.r_diag = C.r_diag;
       sd.term_off = term_off; sd.n_terms = (int)C.terms.size(); sd.diag_off = diag_off;
       sd.halo_lo = C.halo_lo; sd.halo_hi = C.halo_hi; sd.p_flat = s.p_flat; sd.q_flat = s.q_flat;
       int stG[3] = {1, 1, 1};
@@ -851,6 +864,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
       bq::M1Sys m;
       std::memset(&m, 0, sizeof(m));
       const int M = C.M[0];
+      if (C.r_diag) { ok = false; break; }  // diagonal residual layout: tiled kernel only
       m.M = M; m.has_sep = C.has_sep; m.has_r = C.has_r;
       for (int t = 0; t < (int)C.terms.size() && ok; ++t) {
         const TermDesc& td = C.terms[t];
@@ -1243,6 +1257,7 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   st->use_pipe = P.use_pipe;
   st->n_coef_dyn = (int)P.pcdyn.size();
   for (const TermDesc& td : P.terms) st->has_diag = st->has_diag || td.diagp1 != 0;
+  for (const SysDesc& sd : P.sys) st->r_diag = st->r_diag || sd.r_diag;
   st->pipe_off_coef = P.pipe_off_coef; st->pipe_off_u = P.pipe_off_u; st->pipe_off_y = P.pipe_off_y;
   st->pipe_off_acc = P.pipe_off_acc; st->pipe_off_comp = P.pipe_off_comp;
   for (int q = 0; q < 3; ++q) st->pipe_slot[q] = P.pipe_slot[q];
@@ -1767,6 +1782,7 @@ static int set_tau(bq_state* s, double tau, cudaStream_t st) {
 extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_every, void* work, size_t work_bytes,
                        double* loss_out, double* grad_out, void* stream) {
   if (s && s->has_diag) return fail(BQ_EUNSUPPORTED, "gradients with secular dissipators are not implemented");
+  if (s && s->r_diag) return fail(BQ_EUNSUPPORTED, "gradients with the diagonal residual layout are not implemented");
   if (!s || !work || !loss_out || !grad_out) return fail(BQ_EINVAL, "NULL argument");
   if (n_steps < 1 || checkpoint_every < 1 || !(dt > 0.0)) return fail(BQ_EINVAL, "bad step arguments");
   if (dt > s->dt_max * (1.0 + 1e-12)) return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 bound %g", dt, s->dt_max);
@@ -1911,7 +1927,7 @@ extern "C" int bq_system_info(const bq_state* s, int sys, int* problem, int* p_i
   if (q_idx) *q_idx = sd.q_flat;
   if (n_gx) *n_gx = sd.has_sep ? sd.n_g : 0;
   if (n_gy) *n_gy = sd.has_sep ? sd.n_g : 0;
-  if (n_r) *n_r = sd.has_r ? sd.n_r : 0;
+  if (n_r) *n_r = sd.has_r ? (sd.r_diag ? (int64_t)sd.n_g * sd.n_g : sd.n_r) : 0;  // expanded view
   if (w) { w[0] = sd.w_re; w[1] = sd.w_im; }
   if (c) { c[0] = sd.c_re; c[1] = sd.c_im; }
   return BQ_OK;
@@ -1950,7 +1966,18 @@ extern "C" int bq_read_system(bq_state* s, int sys, double* gx, double* gy, doub
   int rc;
   if (gx && sd.has_sep && (rc = fetch(sd.off_gx, sd.n_g, gx, false)) != BQ_OK) return rc;
   if (gy && sd.has_sep && (rc = fetch(sd.off_gy, sd.n_g, gy, false)) != BQ_OK) return rc;
-  if (r && sd.has_r && (rc = fetch(sd.off_r, sd.n_r, r, true)) != BQ_OK) return rc;
+  if (r && sd.has_r && sd.r_diag) {  // expand the k = l entries to the n_g x n_g matrix
+    std::vector<double> d(2 * (size_t)sd.n_g);
+    if ((rc = fetch(sd.off_r, sd.n_g, d.data(), false)) != BQ_OK) return rc;
+    std::fill(r, r + 2 * (size_t)sd.n_g * sd.n_g, 0.0);
+    for (int i = 0; i < sd.n_g; ++i) {
+      const double sc = s->method == BQ_METHOD_MAPPED ? sflat(i) : 1.0;  // second factor of s(k) s(l)
+      r[2 * ((size_t)i * sd.n_g + i)] = d[2 * i] / sc;
+      r[2 * ((size_t)i * sd.n_g + i) + 1] = d[2 * i + 1] / sc;
+    }
+  } else if (r && sd.has_r && (rc = fetch(sd.off_r, sd.n_r, r, true)) != BQ_OK) {
+    return rc;
+  }
   return BQ_OK;
 }
 

@@ -72,7 +72,8 @@ struct SysDesc {
   double w_re, w_im;    // weight g_{p,q}(0) of the initial condition
   int n_params;         // parameters of the problem
   int grad_off;         // gradient slot of the problem's first parameter
-  int pad2[2];
+  int r_diag;           // R stored only at k = l (n_r = n_g entries, index = flat k)
+  int pad2;
 };
 
 // A CTA's share of one stage: a tile of R points of one system (plus G_x, G_y if sep).

@@ -197,8 +197,8 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
     const int ng = sd.n_g;
     for (int p = wi.start + tid; p < wi.start + wi.len; p += blockDim.x) {
       int idx[ND];
-      const int kx = p / ng;
-      const int ly = p - kx * ng;
+      const int kx = sd.r_diag ? p : p / ng;  // diagonal residual layout: point p is (p, p)
+      const int ly = sd.r_diag ? p : p - kx * ng;
       {
         int r = kx;
 #pragma unroll
@@ -222,8 +222,10 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
           if (d < NM) wx *= wv; else wy *= wv;
         }
         const T w = wx * wy;
-        const int src = (w != (T)0) ? p + td.deltaR : p;
-        k = cfma(sc[t], cscale(win[src - wi.win_lo], w), k);
+        // diagonal layout: only terms that shift x and y alike have an R source, at deltaGx
+        const bool rsrc = !sd.r_diag || td.deltaGx == td.deltaGy;
+        const int src = (w != (T)0 && rsrc) ? p + (sd.r_diag ? td.deltaGx : td.deltaR) : p;
+        if (rsrc) k = cfma(sc[t], cscale(win[src - wi.win_lo], w), k);
         if (td.side == SIDE_S && sd.has_sep) {
           const int sx = (wx != (T)0) ? kx + td.deltaGx : kx;
           const int sy = (wy != (T)0) ? ly + td.deltaGy : ly;
@@ -1903,7 +1905,8 @@ __global__ void k_eval(const SysDesc* __restrict__ sys, const EvalGroup* __restr
       vi += (double)a.x * (double)b.y + (double)a.y * (double)b.x;
     }
     if (sd.has_r) {
-      const C r = y[sd.off_r + (int64_t)en.kx * sd.n_g + en.ly];
+      const C r = sd.r_diag ? (en.kx == en.ly ? y[sd.off_r + en.kx] : cmk<C>(0.0, 0.0))
+                            : y[sd.off_r + (int64_t)en.kx * sd.n_g + en.ly];
       vr += (double)r.x;
       vi += (double)r.y;
     }
@@ -1946,7 +1949,8 @@ __global__ void k_eval_small(const SysDesc* __restrict__ sys, const EvalGroup* _
         vi += (double)a.x * (double)b.y + (double)a.y * (double)b.x;
       }
       if (hr) {
-        const C r = y[orr + (int64_t)en.kx * ng + en.ly];
+        const C r = sd.r_diag ? (en.kx == en.ly ? y[orr + en.kx] : cmk<C>(0.0, 0.0))
+                              : y[orr + (int64_t)en.kx * ng + en.ly];
         vr += (double)r.x;
         vi += (double)r.y;
       }
