@@ -17,7 +17,8 @@ during the timed region), ``gpu_launches`` (library kernel launches in the timed
 ``batched`` (4096 full-horizon solves: one persistent launch vs streamed stage kernels vs
 one instance per launch), ``grads`` (the 131-parameter control gradient, and 16 control
 problems batched in one state vs one problem per state), ``methods`` (memory and time per
-step of the conventional number-basis method vs the mapping with full R and with R = 0),
+step, and accuracy, of the conventional number-basis method vs the mapping with full R, with
+R kept at k = l and with R = 0, on secular-dissipator instances),
 ``secular`` (the paper's secular dissipator on the same instances: updates/s and HBM GB/s),
 and ``config.schedule`` (the schedule bq_autotune picked for the timed state).
 
@@ -335,22 +336,35 @@ def grads_batched_leg(B: int = 16, steps: int = 1280):
             "batched_vs_one_per_launch": t1 / tB, "max_rel_diff_batched_vs_single": worst}
 
 
-def methods_leg(B: int = 1024, Ns=(10, 20, 40), steps: int = 100):
-    """The paper's memory and time comparison on this GPU: B driven damped Kerr oscillators
-    with truncation N, integrated by the conventional number-basis method (N^2 elements per
-    instance), the mapping with the full residual R (2N + N^2) and the mapping with R = 0
-    (2N, the regime the paper's memory claim refers to; an approximation for kappa t << 1).
-    Complex FP32, schedules autotuned; device time per RK4 step."""
+def methods_leg(B: int = 1024, Ns=(10, 20, 40), steps: int = 100, acc_steps: int = 50000):
+    """The paper's memory, time and accuracy comparison (Fig. 2's quantities) on this GPU:
+    B driven Kerr oscillators with the secular dissipator (secular_batch draws at truncation
+    N) integrated by the conventional number-basis method (N^2 elements per instance), the
+    mapping with the full residual R (2N + N^2), with the residual kept as a function of x y
+    only (R diagonal: 3N; the paper's observation) and with R = 0 (2N).  Complex FP32,
+    schedules autotuned; device time per RK4 step of the whole batch; epsilon_r (the paper's
+    relative error on the three-level block) of instance 0 after acc_steps steps against the
+    conventional method at truncation N + 8 with half the time step in FP64."""
+    import numpy as np
     import torch
 
     import paper_2203_05526_gb300 as bq
     from workloads import configs
+    methods = (("direct", dict(method="direct")), ("mapped_full_R", dict(method="mapped")),
+               ("mapped_R_diag", dict(method="mapped", r_layout="diag")),
+               ("mapped_R_off", dict(method="mapped", r_layout="off")))
     rows = []
     for N in Ns:
-        specs = configs.kerr_batch(B=B, T=HORIZON, dt=DT, n_min=N, n_max=N)
+        specs = configs.secular_batch(B=B, T=HORIZON, dt=DT, n_min=N, n_max=N)
         handles = [bq.problem_from_spec(p) for p in specs]
-        for name, kw in (("direct", dict(method="direct")), ("mapped_full_R", dict(method="mapped")),
-                         ("mapped_R_off", dict(method="mapped", r_layout="off"))):
+        # reference block of instance 0: conventional method, N + 8, dt / 2, FP64
+        ref_spec = configs.secular_batch(B=1, T=HORIZON, dt=DT, n_min=N + 8, n_max=N + 8)[0]
+        ref_spec.N = (N + 8,)
+        ref = bq.State([bq.problem_from_spec(ref_spec)], bq.map_opts(method="direct", dtype="f64",
+                                                                       horizon=HORIZON, dt=DT / 2))
+        ref.step(DT / 2, 2 * acc_steps)
+        bref = ref.fock_block(3, dim=3)[0]
+        for name, kw in methods:
             st = bq.State(handles, bq.map_opts(dtype="f32", horizon=HORIZON, dt=DT, **kw))
             st.autotune(DT, trial_steps=4)
             st.step(DT, 8)
@@ -361,11 +375,17 @@ def methods_leg(B: int = 1024, Ns=(10, 20, 40), steps: int = 100):
             e1.record()
             torch.cuda.synchronize()
             us = e0.elapsed_time(e1) * 1e3 / steps
-            elems = st.state_bytes() // 8
-            rows.append({"N": N, "method": name, "elements_per_instance": elems / B, "state_bytes": st.state_bytes(),
-                         "us_per_step": us, "ns_per_instance_step": 1e3 * us / B})
-    return {"workload": f"{B} driven damped Kerr instances per N (kerr_batch distribution at fixed N), complex FP32, "
-                        f"{steps} RK4 steps of dt={DT} ns", "rows": rows}
+            one = bq.State([handles[0]], bq.map_opts(dtype="f32", horizon=HORIZON, dt=DT, **kw))
+            one.step(DT, acc_steps)
+            blk = one.fock_block(3, dim=3)[0]
+            eps = float(np.linalg.norm(blk - bref) / np.linalg.norm(bref))
+            rows.append({"N": N, "method": name, "elements_per_instance": st.state_bytes() / 8 / B,
+                         "state_bytes": st.state_bytes(), "us_per_step": us, "ns_per_instance_step": 1e3 * us / B,
+                         "eps_r_instance0": eps})
+    return {"workload": f"{B} secular_batch instances per N (kerr_batch draws with the secular dissipator, "
+                        f"fixed N), complex FP32, {steps} timed RK4 steps of dt={DT} ns; eps_r of instance 0 "
+                        f"after {acc_steps} steps vs the conventional method at N + 8, dt/2, FP64",
+            "rows": rows}
 
 
 def secular_leg(B: int = 32768, steps: int = 20):
