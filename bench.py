@@ -391,7 +391,7 @@ def methods_leg(B: int = 1024, Ns=(10, 20, 40), steps: int = 100, acc_steps: int
 def secular_leg(B: int = 32768, steps: int = 20):
     """The paper's secular dissipator (Eq. 203 / Eq. S9, zero temperature) on kerr_batch's
     instances (secular_batch: same draws, complex FP32): grid-point RK-stage updates/s of the
-    tiled stage kernel (the projector term is restricted to diagonal index pairs) and its HBM
+    stage kernel (the projector term is restricted to diagonal index pairs) and its HBM
     bandwidth for the same 19/4 array transfers per point and stage."""
     import torch
 
@@ -412,7 +412,8 @@ def secular_leg(B: int = 32768, steps: int = 20):
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
     return {"workload": f"secular_batch x{B} (kerr_batch draws, secular dissipator, T_E = 0), complex FP32, "
-                        f"{steps} RK4 steps", "kernel": "bq::k_stage (tiled, " + st.stage_variant() + ")",
+                        f"{steps} RK4 steps", "kernel": {"pipelined": "bq::k_stage_pipe", "single_mode": "bq::k_stage_m1",
+                                               "generic": "bq::k_stage"}[st.stage_variant()],
             "updates_per_s": 4 * pts / s_step, "ms_per_step": 1e3 * s_step,
             "achieved_gbs": achieved, "frac_of_measured_hbm": achieved / peak}
 
