@@ -38,6 +38,9 @@ Parity status (tests/test_oracle_mapping.py):
   * f_from_fock / g_from_f / f_from_g / fock_from_f: pinned by brute force against
     explicit matrix products of (a^dag)^k a^l and by the identity T_{k,l} = sqrt(k! l!)|k><l|
     checked numerically at N <= 8 (Eq. 8 summed with a padded truncation).
+  * initial_conditions_svd: pinned by exact reconstruction of g(0) and by the exact equality
+    of SVD and monomial runs at equal separation constants (every step is linear in each
+    IC's tensor product G_x(0) (x) G_y(0), so only their sum, g(0), matters).
   * separation_constant: pinned against a direct numerical minimisation of the functional
     quoted with Eq. 304 for the uncoupled oscillator.
   * left/right/sandwich operators + RK4: pinned by (a) the exact G(x,y,t) of a damped
@@ -222,6 +225,19 @@ def initial_conditions(g0: np.ndarray, n_modes: int, rel_tol: float = 1e-12):
     return out
 
 
+def initial_conditions_svd(g0: np.ndarray, n_modes: int, rel_tol: float = 1e-12):
+    """Separable initial conditions from a singular value decomposition of g(0) seen as a
+    (prod M) x (prod M) matrix, g(0) = sum_i s_i u_i v_i^H: one IC per singular value above
+    rel_tol * s_max, with G_x(0) = s_i u_i and G_y(0) = conj(v_i) (the option the method
+    leaves open for operators with many non-negligible g_{p,q}(0): at most prod M ICs instead
+    of one per non-zero element).  Returns [(G_x(0), G_y(0))]."""
+    d = int(round(math.sqrt(g0.size)))
+    U, S, Vh = np.linalg.svd(g0.reshape(d, d))
+    if S.size == 0 or S[0] == 0.0:
+        return []
+    return [(U[:, i] * S[i], Vh[i, :].copy()) for i in range(S.size) if S[i] > rel_tol * S[0]]
+
+
 def omega_eta(problem: Problem) -> Tuple[List[float], List[float]]:
     """omega_j (static coefficient of a_j^dag a_j) and eta_j (of a_j^dag^2 a_j^2) of H."""
     n = problem.n_modes
@@ -393,19 +409,28 @@ def map_initial(problem: Problem, M: Optional[Sequence[int]] = None):
 
 
 def rk4_mapped(problem: Problem, M: Optional[Sequence[int]] = None, n_steps: Optional[int] = None,
-               r_layout: str = "full", C_override=None, all_in_R: bool = False) -> MappedRun:
+               r_layout: str = "full", C_override=None, all_in_R: bool = False,
+               ic_mode: str = "monomial") -> MappedRun:
     """Integrate Eqs. 9a-c for every initial condition with classical RK4.
 
     ``r_layout``:   "full" (Eq. 303c as printed), "off" (R = 0) or "diag" (R restricted to
                     k = l, the x_j y_j-only residual).
     ``C_override``: use this separation constant for every IC instead of Eq. 304.
-    ``all_in_R``:   start from G_x = G_y = 0, R = x^p y^q (a pin: then the run is RK4 on G)."""
+    ``all_in_R``:   start from G_x = G_y = 0, R = x^p y^q (a pin: then the run is RK4 on G).
+    ``ic_mode``:    "monomial" (one IC x^p y^q per non-negligible g_{p,q}(0), Eqs. 10 / 13) or
+                    "svd" (``initial_conditions_svd``; weight 1, C = 0 or ``C_override``)."""
     model = MappedModel(problem, M)
     g0, ics0 = map_initial(problem, model.M)
     d = model.dim
     dt = problem.dt
     steps = problem.n_steps if n_steps is None else n_steps
     states = []
+    if ic_mode == "svd":
+        C = 0j if C_override is None else complex(C_override)
+        for gx0, gy0 in initial_conditions_svd(g0, problem.n_modes):
+            states.append([None, None, 1.0 + 0j, C, gx0.astype(np.complex128), gy0.astype(np.complex128),
+                           np.zeros((d, d), dtype=np.complex128)])
+        ics0 = []
     for p, q, w in ics0:
         C = separation_constant(problem, p, q) if C_override is None else complex(C_override)
         ip = int(np.ravel_multi_index(p, model.M))

@@ -242,3 +242,34 @@ def test_r_layout_off_exact_without_dissipation():
     a = mapping.rk4_mapped(p, r_layout="full").fock_matrix()
     b = mapping.rk4_mapped(p, r_layout="off").fock_matrix()
     assert np.max(np.abs(a - b)) == 0.0
+
+
+# ---- SVD initial conditions ----------------------------------------------------------------
+def _dense_problem(seed=41, n_modes=1, N=6, steps=30):
+    return configs.random_problem(seed, n_modes=n_modes, N=N, n_steps=steps, dt=0.01, dense_measured=True)
+
+
+@pytest.mark.parametrize("n_modes,N", [(1, 7), (2, 3)])
+def test_svd_initial_conditions_reconstruct_g0_with_fewer_systems(n_modes, N):
+    p = _dense_problem(n_modes=n_modes, N=N)
+    g0, ics = mapping.map_initial(p)
+    svd = mapping.initial_conditions_svd(g0, n_modes)
+    d = int(np.prod(p.N))
+    G = sum(np.outer(gx, gy) for gx, gy in svd)
+    assert np.max(np.abs(G - g0.reshape(d, d))) < 1e-13 * np.max(np.abs(g0))
+    assert len(svd) <= d < len(ics)
+
+
+@pytest.mark.parametrize("n_modes,N", [(1, 7), (2, 3)])
+def test_svd_run_equals_monomial_run_for_equal_separation_constant(n_modes, N):
+    """Every step of Eqs. 9a-c is linear in the tensor product G_x(0) (x) G_y(0) of an IC
+    (the source S(G_x G_y) is bilinear in the factors), so with the same C for all ICs the
+    summed result depends only on sum_i G_x^i(0) (x) G_y^i(0) = g(0): the SVD and the
+    monomial decompositions must agree to rounding, with dissipation and drive."""
+    p = _dense_problem(n_modes=n_modes, N=N)
+    a = mapping.rk4_mapped(p, C_override=0.0).fock_matrix()
+    b = mapping.rk4_mapped(p, C_override=0.0, ic_mode="svd").fock_matrix()
+    assert np.max(np.abs(a - b)) < 1e-12 * np.max(np.abs(a))
+    # with Eq. 304's per-IC constants the two differ only at the RK4-error level
+    c = mapping.rk4_mapped(p).fock_matrix()
+    assert np.max(np.abs(c - b)) < 1e-6 * np.max(np.abs(a))
