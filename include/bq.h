@@ -64,6 +64,12 @@ enum { BQ_R_FULL = 0, BQ_R_OFF = 1, BQ_R_DIAG = 2 };
  * range for large truncations).  AUTO = MONOMIAL for F64 mapped, NUMBER otherwise. */
 enum { BQ_BASIS_AUTO = 0, BQ_BASIS_MONOMIAL = 1, BQ_BASIS_NUMBER = 2 };
 enum { BQ_C_EQ304 = 0, BQ_C_ZERO = 1 };
+/* Separable initial conditions of the mapped method: MONOMIAL = one system x^p y^q per
+ * non-zero element of A(0) (Eqs. 10 / 13, weight g_{p,q}(0), C of Eq. 304); SVD = one
+ * system per singular value of g(0) seen as a (prod M) x (prod M) matrix above 1e-12 of the
+ * largest, G_x(0) = s_i u_i, G_y(0) = conj(v_i), weight 1, C = 0 (at most prod M systems;
+ * the summed result equals the monomial one up to the RK4 error of the different C). */
+enum { BQ_IC_MONOMIAL = 0, BQ_IC_SVD = 1 };
 
 #define BQ_MAX_MODES 3
 
@@ -85,6 +91,8 @@ typedef struct bq_map_opts {
   int grid[BQ_MAX_MODES]; /* coefficient truncation M per mode; 0 = the Fock truncation */
   double horizon;    /* T, physical end time                                            */
   double dt;         /* time step the state will be stepped with (stability check)      */
+  int ic_mode;       /* BQ_IC_MONOMIAL | BQ_IC_SVD (mapped method; prod M <= 1024 for SVD) */
+  int pad;
 } bq_map_opts;
 
 /* ---- problem construction (host only; Eqs. 1-3, S1-S2) ---------------------------- */

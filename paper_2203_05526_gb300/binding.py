@@ -32,6 +32,7 @@ DTYPE = {"f64": 0, "f32": 1}
 R_LAYOUT = {"full": 0, "off": 1, "diag": 2}
 BASIS = {"auto": 0, "monomial": 1, "number": 2}
 C_MODE = {"eq304": 0, "zero": 1}
+IC_MODE = {"monomial": 0, "svd": 1}
 MAX_MODES = 3
 
 
@@ -54,7 +55,7 @@ class BQError(RuntimeError):
 class bq_map_opts(C.Structure):
     _fields_ = [("method", C.c_int), ("dtype", C.c_int), ("r_layout", C.c_int), ("basis", C.c_int),
                 ("c_mode", C.c_int), ("reverse_time", C.c_int), ("grid", C.c_int * MAX_MODES),
-                ("horizon", C.c_double), ("dt", C.c_double)]
+                ("horizon", C.c_double), ("dt", C.c_double), ("ic_mode", C.c_int), ("pad", C.c_int)]
 
 
 _lib: Optional[C.CDLL] = None
@@ -216,7 +217,8 @@ def problem_from_spec(spec) -> ProblemHandle:
 
 
 def map_opts(method="mapped", dtype="f64", r_layout="full", basis="auto", c_mode="eq304", reverse_time=True,
-             grid: Optional[Sequence[int]] = None, horizon: float = 0.0, dt: float = 0.0) -> bq_map_opts:
+             grid: Optional[Sequence[int]] = None, horizon: float = 0.0, dt: float = 0.0,
+             ic_mode: str = "monomial") -> bq_map_opts:
     o = bq_map_opts()
     o.method, o.dtype, o.r_layout = METHOD[method], DTYPE[dtype], R_LAYOUT[r_layout]
     o.basis, o.c_mode, o.reverse_time = BASIS[basis], C_MODE[c_mode], 1 if reverse_time else 0
@@ -224,6 +226,7 @@ def map_opts(method="mapped", dtype="f64", r_layout="full", basis="auto", c_mode
     for j in range(MAX_MODES):
         o.grid[j] = int(g[j]) if j < len(g) else 0
     o.horizon, o.dt = float(horizon), float(dt)
+    o.ic_mode = IC_MODE[ic_mode]
     return o
 
 

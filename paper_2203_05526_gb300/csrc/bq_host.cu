@@ -252,6 +252,7 @@ struct Compiled {
     int p_flat, q_flat;
     cplx w, C;
     double gx0, gy0;          // stored values of x^p, y^q
+    std::vector<cplx> vx, vy; // SVD initial conditions: stored G_x(0), G_y(0) (empty: monomial)
     std::vector<cplx> dC;     // d C / d theta_p (Eq. 304)
   };
   int n_params = 0;
@@ -312,6 +313,49 @@ static int check_hermitian(const bq_problem* p) {
       return fail(BQ_EINVAL, "Hamiltonian is not Hermitian: add the conjugate of every term (swap u/v, conj channel)");
   }
   return BQ_OK;
+}
+
+// One-sided (Hestenes) Jacobi SVD of the n x n complex matrix W (column-major, overwritten):
+// column rotations make W's columns orthogonal, W <- W V with V unitary (returned,
+// column-major), so that the input equals W V^H and sigma_i = |W column i|.
+static void jacobi_svd(int n, std::vector<cplx>& W, std::vector<cplx>& V) {
+  V.assign((size_t)n * n, cplx(0, 0));
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 80; ++sweep) {
+    double off = 0.0;
+    for (int pc = 0; pc < n; ++pc)
+      for (int qc = pc + 1; qc < n; ++qc) {
+        cplx* a = &W[(size_t)pc * n];
+        cplx* b = &W[(size_t)qc * n];
+        double alpha = 0.0, beta = 0.0;
+        cplx gamma(0, 0);
+        for (int i = 0; i < n; ++i) {
+          alpha += std::norm(a[i]);
+          beta += std::norm(b[i]);
+          gamma += std::conj(a[i]) * b[i];
+        }
+        const double g = std::abs(gamma);
+        if (g == 0.0 || g <= 1e-15 * std::sqrt(alpha * beta)) continue;
+        off = std::max(off, g / std::sqrt(alpha * beta));
+        const cplx ph = std::conj(gamma / g);  // column q times ph makes a^H b real, = g
+        const double zeta = (beta - alpha) / (2.0 * g);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (std::abs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+        for (int i = 0; i < n; ++i) {
+          const cplx ap = a[i], bq = b[i] * ph;
+          a[i] = c * ap - sn * bq;
+          b[i] = sn * ap + c * bq;
+        }
+        cplx* va = &V[(size_t)pc * n];
+        cplx* vb = &V[(size_t)qc * n];
+        for (int i = 0; i < n; ++i) {
+          const cplx ap = va[i], bq = vb[i] * ph;
+          va[i] = c * ap - sn * bq;
+          vb[i] = sn * ap + c * bq;
+        }
+      }
+    if (off < 1e-15) break;
+  }
 }
 
 static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& C) {
@@ -583,6 +627,40 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
     for (auto& [kl, v] : p->measured)
       if (in_grid(kl.first) && in_grid(kl.second) && v != cplx(0, 0))
         C.init.push_back({(long long)flat_index(kl.first, C.M, nm) * C.n_g + flat_index(kl.second, C.M, nm), v});
+  } else if (o.ic_mode == BQ_IC_SVD) {
+    // g(0) in the storage basis (stored value s(p) s(q) <p|A|q> / sqrt(p! q!)), factored as
+    // sum_i sigma_i u_i v_i^H; one system per sigma_i > 1e-12 sigma_max
+    const int n = C.n_g;
+    if (n > 1024) return fail(BQ_EUNSUPPORTED, "SVD initial conditions need prod M <= 1024 (%d)", n);
+    std::vector<cplx> W((size_t)n * n, cplx(0, 0)), V;
+    for (auto& [kl, v] : p->measured) {
+      if (!in_grid(kl.first) || !in_grid(kl.second) || v == cplx(0, 0)) continue;
+      const int pf = flat_index(kl.first, C.M, nm), qf = flat_index(kl.second, C.M, nm);
+      W[(size_t)qf * n + pf] += v / sqfact(kl.first) / sqfact(kl.second) * sfl(kl.first) * sfl(kl.second);
+    }
+    jacobi_svd(n, W, V);
+    std::vector<std::pair<double, int>> sig;
+    double smax = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double s2 = 0.0;
+      for (int k = 0; k < n; ++k) s2 += std::norm(W[(size_t)i * n + k]);
+      sig.push_back({-std::sqrt(s2), i});
+      smax = std::max(smax, std::sqrt(s2));
+    }
+    std::sort(sig.begin(), sig.end());
+    for (auto& [ns, i] : sig) {
+      if (!(-ns > 1e-12 * smax)) break;
+      Compiled::Sys s;
+      s.p_flat = -1; s.q_flat = -1;
+      s.w = cplx(1, 0);
+      s.C = cplx(0, 0);
+      s.dC.assign(p->params.size(), cplx(0, 0));
+      s.gx0 = s.gy0 = 0.0;
+      s.vx.assign(W.begin() + (size_t)i * n, W.begin() + (size_t)(i + 1) * n);
+      s.vy.resize(n);
+      for (int k = 0; k < n; ++k) s.vy[k] = std::conj(V[(size_t)i * n + k]);
+      C.sys.push_back(s);
+    }
   } else {
     for (auto& [kl, v] : p->measured) {
       if (!in_grid(kl.first) || !in_grid(kl.second) || v == cplx(0, 0)) continue;
@@ -750,6 +828,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
   if (o->method != BQ_METHOD_MAPPED && o->method != BQ_METHOD_DIRECT) return fail(BQ_EINVAL, "method");
   if (o->dtype != BQ_F64 && o->dtype != BQ_F32) return fail(BQ_EINVAL, "dtype");
   if (o->r_layout != BQ_R_FULL && o->r_layout != BQ_R_OFF && o->r_layout != BQ_R_DIAG) return fail(BQ_EINVAL, "r_layout");
+  if (o->ic_mode != BQ_IC_MONOMIAL && o->ic_mode != BQ_IC_SVD) return fail(BQ_EINVAL, "ic_mode");
   const int nm = probs[0] ? probs[0]->nm : 0;
   const size_t cs = o->dtype == BQ_F64 ? 16 : 8;  // complex element size
   const size_t rs = cs / 2;
@@ -818,8 +897,16 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
     } else {
       for (size_t i = 0; i < C.sys.size(); ++i) {
         const SysDesc& sd = P.sys[sys_off + i];
-        P.init.push_back({sd.off_gx + C.sys[i].p_flat, C.sys[i].gx0, 0.0});
-        P.init.push_back({sd.off_gy + C.sys[i].q_flat, C.sys[i].gy0, 0.0});
+        if (!C.sys[i].vx.empty()) {  // SVD initial condition: whole vectors
+          for (int k = 0; k < C.n_g; ++k) {
+            const cplx a = C.sys[i].vx[k], b = C.sys[i].vy[k];
+            if (a != cplx(0, 0)) P.init.push_back({sd.off_gx + k, a.real(), a.imag()});
+            if (b != cplx(0, 0)) P.init.push_back({sd.off_gy + k, b.real(), b.imag()});
+          }
+        } else {
+          P.init.push_back({sd.off_gx + C.sys[i].p_flat, C.sys[i].gx0, 0.0});
+          P.init.push_back({sd.off_gy + C.sys[i].q_flat, C.sys[i].gy0, 0.0});
+        }
       }
     }
     // evaluation groups: trace group b, then block groups appended later

@@ -9,13 +9,14 @@ import paper_2203_05526_gb300 as bq
 from oracle import fock, mapping
 
 
-def gpu_state(specs, method="mapped", dtype="f64", grid=None, r_layout="full", c_mode="eq304", basis="auto"):
+def gpu_state(specs, method="mapped", dtype="f64", grid=None, r_layout="full", c_mode="eq304", basis="auto",
+              ic_mode="monomial"):
     if not isinstance(specs, (list, tuple)):
         specs = [specs]
     s0 = specs[0]
     handles = [bq.problem_from_spec(s) for s in specs]
     opts = bq.map_opts(method=method, dtype=dtype, grid=grid, r_layout=r_layout, c_mode=c_mode, basis=basis,
-                       reverse_time=s0.reverse_time, horizon=s0.T, dt=s0.dt)
+                       reverse_time=s0.reverse_time, horizon=s0.T, dt=s0.dt, ic_mode=ic_mode)
     return bq.State(handles, opts)
 
 
