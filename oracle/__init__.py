@@ -17,6 +17,12 @@ Modules
                 monomial basis, classical RK4, reconstruction (Eq. 11).
 * ``grad``      O3: reverse-mode (discrete adjoint) gradients of the RK4 trajectory of
                 O2, and central finite differences.
+* ``entropy``   O4: entropy production rate of the anharmonic oscillator under the
+                conventional and the secular master equations (the supplement's
+                entropy-production section), a validation workload of the two dissipators.
+
+O1 and O2 also carry the secular dissipator (Eq. 203 / Eq. S9), O2 the diagonal residual
+layout and SVD initial conditions.
 
 Parity status of every function is listed in each module's header.
 """
