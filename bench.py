@@ -388,6 +388,63 @@ def methods_leg(B: int = 1024, Ns=(10, 20, 40), steps: int = 100, acc_steps: int
             "rows": rows}
 
 
+def fig2_leg(modes=(1, 2, 3), target: float = 1e-4, steps: int = 2000, n_max: int = 12):
+    """The paper's Fig. 2 (right panels) on this GPU: the Table I network of n coupled
+    driven anharmonic oscillators in the lab frame (secular dissipator, A(0) = a_1 (x) ... (x)
+    a_n) at the scaled time omega_q t / pi = 10.  For each method the smallest truncation
+    whose epsilon_r (three-level block) against a reference (conventional method, larger
+    truncation, half the time step, FP64) is at most `target`; then its stored elements
+    (conventional: N^(2n); mapping: per initial condition and in total) and its device time
+    per RK4 step (FP64)."""
+    import numpy as np
+    import torch
+
+    import paper_2203_05526_gb300 as bq
+    from workloads import configs
+    ref_n = {1: 14, 2: 10, 3: 8}
+    rows = []
+
+    def run(p, dt, n, **kw):
+        st = bq.State([bq.problem_from_spec(p)], bq.map_opts(dtype="f64", horizon=p.T, dt=dt, **kw))
+        st.step(dt, n)
+        torch.cuda.synchronize()
+        return st
+
+    for nm in modes:
+        pr = configs.table_one_network(nm, ref_n[nm], steps=2 * steps)
+        ref = run(pr, pr.dt, 2 * steps, method="direct").fock_block(3, dim=3 ** nm)[0]
+        for name, kw in (("conventional", dict(method="direct")), ("mapping_R_diag", dict(r_layout="diag")),
+                         ("mapping_R_off", dict(r_layout="off"))):
+            found = None
+            for N in range(3, n_max + 1):
+                if N >= ref_n[nm]:
+                    break
+                p = configs.table_one_network(nm, N, steps=steps)
+                st = run(p, p.dt, steps, **kw)
+                blk = st.fock_block(3, dim=3 ** nm)[0]
+                eps = float(np.linalg.norm(blk - ref) / np.linalg.norm(ref))
+                if eps <= target:
+                    found = (N, p, st, eps)
+                    break
+            if found is None:
+                rows.append({"modes": nm, "method": name, "truncation": None})
+                continue
+            N, p, st, eps = found
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st.step(p.dt, 200)
+            e1.record()
+            torch.cuda.synchronize()
+            n_sys = st.n_systems()
+            per_sys = st.state_bytes() / 16 / n_sys
+            rows.append({"modes": nm, "method": name, "truncation": N, "eps_r": eps, "systems": n_sys,
+                         "elements_per_system": per_sys, "elements_total": st.state_bytes() / 16,
+                         "conventional_elements": N ** (2 * nm), "us_per_step": e0.elapsed_time(e1) * 1e3 / 200})
+    return {"workload": f"Table I network, lab frame, secular dissipator at T_E = 0, A(0) = a_1 x ... x a_n, "
+                        f"omega_q t / pi = 10 in {steps} RK4 steps, complex FP64; truncation tuned to "
+                        f"eps_r <= {target:g}", "rows": rows}
+
+
 def secular_leg(B: int = 32768, steps: int = 20):
     """The paper's secular dissipator (Eq. 203 / Eq. S9, zero temperature) on kerr_batch's
     instances (secular_batch: same draws, complex FP32): grid-point RK-stage updates/s of the
@@ -580,9 +637,11 @@ def main():
         grads = grads_leg()
     methods = None
     secular = None
+    fig2 = None
     if not args.no_batched and world == 1:
         methods = methods_leg()
         secular = secular_leg()
+        fig2 = fig2_leg()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -601,7 +660,7 @@ def main():
                                                                  "n_candidates", "step_us")},
                            "state_bytes_per_array": nbytes, "l2": "inputs larger than L2 (4 arrays x "
                            f"{nbytes / 1e6:.0f} MB vs 129 MB)", "parallelism": f"replicas x{world}"},
-                "roofline": roof, "e2e": e2e, "batched": batched, "grads": grads, "methods": methods, "secular": secular, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches}
+                "roofline": roof, "e2e": e2e, "batched": batched, "grads": grads, "methods": methods, "secular": secular, "fig2": fig2, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -755,6 +755,7 @@ struct bq_state {
   int n_coef_dyn = 0;  // time-dependent stage coefficients (k_coef_dyn entries)
   int has_diag = 0;     // some term acts only on diagonal index pairs (secular dissipator)
   int r_diag = 0;       // diagonal residual layout
+  int has_gread = 0;    // some work item reads its R sources from global memory
   int ng_max = 0;      // largest G_x / G_y point count over the systems
   // schedules (bq_get_tune / bq_set_tune / bq_autotune)
   int pipe_ok = 0;      // the pipelined path is available (single mode, two slots fit)
@@ -1142,27 +1143,31 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
       smem_max = std::max(smem_max, sep);
       continue;
     }
-    if (sd.n_r + sep <= budget) {
+    // a system that fits in one tile takes one CTA, unless the batch is too small to fill the
+    // GPU that way (then it is split like a large one)
+    const bool few = (int)P.sys.size() < 2 * 152 && sd.n_r >= 2 * 256;
+    if (sd.n_r + sep <= budget && !few) {
       WorkItem w{i, 0, sd.n_r, sd.has_sep, 0, sd.n_r, sd.n_r + sep, 0};
       P.work.push_back(w);
       smem_max = std::max(smem_max, sd.n_r + sep);
       continue;
     }
     int tl = budget - sep - sd.halo_lo - sd.halo_hi;
-    if (tl < 64) return fail(BQ_EUNSUPPORTED, "stencil halo too large for a shared-memory tile");
+    const int gread = tl < 64 ? 1 : 0;  // the halo does not fit next to a tile: read R from global memory
+    if (gread) tl = 1 << 30;
     // enough CTAs per launch to occupy every SM twice (the multi-mode kernels are ALU-bound
     // in FP64, so the larger halo share of small tiles costs L2 bandwidth, not time)
     {
       const int want_tiles = std::max(1, (2 * 152 + (int)P.sys.size() - 1) / (int)P.sys.size());
-      const int tl_par = std::max(64, (sd.n_r + want_tiles - 1) / want_tiles);
+      const int tl_par = std::max(few ? 256 : 64, (sd.n_r + want_tiles - 1) / want_tiles);
       tl = std::min(tl, tl_par);
     }
     for (int s = 0; s < sd.n_r; s += tl) {
       WorkItem w;
       w.sys = i; w.start = s; w.len = std::min(tl, sd.n_r - s); w.do_sep = (s == 0) ? sd.has_sep : 0;
-      w.win_lo = std::max(0, s - sd.halo_lo);
-      w.win_hi = std::min(sd.n_r, s + w.len + sd.halo_hi);
-      w.smem_elems = (w.win_hi - w.win_lo) + sep; w.pad = 0;
+      w.win_lo = gread ? s : std::max(0, s - sd.halo_lo);
+      w.win_hi = gread ? s : std::min(sd.n_r, s + w.len + sd.halo_hi);
+      w.smem_elems = (w.win_hi - w.win_lo) + sep; w.gread = gread;
       smem_max = std::max(smem_max, w.smem_elems);
       P.work.push_back(w);
     }
@@ -1345,6 +1350,7 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   st->n_coef_dyn = (int)P.pcdyn.size();
   for (const TermDesc& td : P.terms) st->has_diag = st->has_diag || td.diagp1 != 0;
   for (const SysDesc& sd : P.sys) st->r_diag = st->r_diag || sd.r_diag;
+  for (const WorkItem& w : P.work) st->has_gread = st->has_gread || w.gread;
   st->pipe_off_coef = P.pipe_off_coef; st->pipe_off_u = P.pipe_off_u; st->pipe_off_y = P.pipe_off_y;
   st->pipe_off_acc = P.pipe_off_acc; st->pipe_off_comp = P.pipe_off_comp;
   for (int q = 0; q < 3; ++q) st->pipe_slot[q] = P.pipe_slot[q];
@@ -1870,6 +1876,8 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
                        double* loss_out, double* grad_out, void* stream) {
   if (s && s->has_diag) return fail(BQ_EUNSUPPORTED, "gradients with secular dissipators are not implemented");
   if (s && s->r_diag) return fail(BQ_EUNSUPPORTED, "gradients with the diagonal residual layout are not implemented");
+  if (s && s->has_gread)
+    return fail(BQ_EUNSUPPORTED, "gradients of systems whose stencil halo exceeds a shared-memory tile are not implemented");
   if (!s || !work || !loss_out || !grad_out) return fail(BQ_EINVAL, "NULL argument");
   if (n_steps < 1 || checkpoint_every < 1 || !(dt > 0.0)) return fail(BQ_EINVAL, "bad step arguments");
   if (dt > s->dt_max * (1.0 + 1e-12)) return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 bound %g", dt, s->dt_max);

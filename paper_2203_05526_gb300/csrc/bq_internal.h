@@ -83,7 +83,7 @@ struct WorkItem {
   int do_sep;           // this CTA also updates G_x and G_y
   int win_lo, win_hi;   // R window staged in shared memory
   int smem_elems;       // complex elements of shared memory this item needs
-  int pad;
+  int gread;            // 1: no R window (the halo does not fit); sources are read from global memory
 };
 
 // Evaluation: out[g] = sum_{IC of problem} w_IC * sum_{e in group} f_e * G_IC(k_e, l_e)

@@ -129,10 +129,14 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
   // Stage the R window and (for the separable part) G_x, G_y of the stage input.
   const C* uin = reinterpret_cast<const C*>(A.u_in);
   const int wn = wi.win_hi - wi.win_lo;
-  if (sd.has_r) {
+  if (sd.has_r && !wi.gread) {
     const C* src = uin + sd.off_r + wi.win_lo;
     for (int i = tid; i < wn; i += blockDim.x) win[i] = src[i];
   }
+  // R source at flat index i of the system: the staged window, or global memory for tiles
+  // whose halo does not fit in shared memory
+  const C* urg = uin + (sd.has_r ? sd.off_r : 0);
+  auto rsrc_at = [&](int i) { return wi.gread ? urg[i] : win[i - wi.win_lo]; };
   C* gxs = win + wn;
   C* gys = gxs + sd.n_g;
   if (sd.has_sep && (wi.do_sep || sd.has_r)) {
@@ -207,7 +211,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
 #pragma unroll
         for (int d = ND - 1; d >= NM; --d) { idx[d] = r % Md[d]; r /= Md[d]; }
       }
-      const C uc = win[p - wi.win_lo];
+      const C uc = rsrc_at(p);
       C dg = D[doff[0] + idx[0]];
 #pragma unroll
       for (int d = 1; d < ND; ++d) dg = cadd(dg, D[doff[d] + idx[d]]);
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
         // diagonal layout: only terms that shift x and y alike have an R source, at deltaGx
         const bool rsrc = !sd.r_diag || td.deltaGx == td.deltaGy;
         const int src = (w != (T)0 && rsrc) ? p + (sd.r_diag ? td.deltaGx : td.deltaR) : p;
-        if (rsrc) k = cfma(sc[t], cscale(win[src - wi.win_lo], w), k);
+        if (rsrc) k = cfma(sc[t], cscale(rsrc_at(src), w), k);
         if (td.side == SIDE_S && sd.has_sep) {
           const int sx = (wx != (T)0) ? kx + td.deltaGx : kx;
           const int sy = (wy != (T)0) ? ly + td.deltaGy : ly;

@@ -289,3 +289,40 @@ def secular_batch(B: int = 4096, seed: int = 20220311, T: float = 100.0, dt: flo
         p.name = p.name.replace("kerr_batch", "secular_batch")
         out.append(p)
     return out
+
+
+# ---- Table I network (lab frame), the paper's Fig. 2 workload ------------------------------
+TABLE_ONE = dict(omega_q=TWO_PI * 3.5, omega_d=TWO_PI * 3.5, eta=TWO_PI * 0.25, Omega_1=TWO_PI * 0.125,
+                 kappa=2e-5, J=TWO_PI * 0.01)  # rad/ns and 1/ns (Table I, in 2 pi x MHz there)
+
+
+def table_one_network(n_modes: int, N: int, scaled_time: float = 10.0, steps: int = 2000) -> Problem:
+    """The network of Eq. 301 with Table I's parameters in the lab frame: n_modes coupled
+    anharmonic oscillators (omega_q a^dag a + eta (a^dag)^2 a^2, exchange J between every
+    pair), mode 1 driven by i Omega_1 a e^(i omega_d t) + H.c., each damped by the secular
+    dissipator at T_E = 0 with rate kappa; A(0) = a_1 (x) ... (x) a_n; evolved to the scaled
+    time omega_q t / pi = scaled_time in `steps` RK4 steps."""
+    p = TABLE_ONE
+    z = _zero(n_modes)
+    h: List[HTerm] = []
+    for j in range(n_modes):
+        a = _unit(n_modes, j, 1)
+        a2 = _unit(n_modes, j, 2)
+        h.append(HTerm(p["omega_q"] + 0j, a, a))
+        h.append(HTerm(p["eta"] + 0j, a2, a2))
+        for k in range(j + 1, n_modes):
+            ak = _unit(n_modes, k, 1)
+            h.append(HTerm(p["J"] + 0j, ak, a))  # J a_j a_k^dag
+            h.append(HTerm(p["J"] + 0j, a, ak))  # + H.c.
+    a1 = _unit(n_modes, 0, 1)
+    h.append(HTerm(1j * p["Omega_1"], z, a1, channel=0))               # i Omega a e^{i omega_d t}
+    h.append(HTerm(-1j * p["Omega_1"], a1, z, channel=0, conj=True))  # H.c.
+    meas = {}
+    for k in np.ndindex(*([N - 1] * n_modes)):
+        meas[(tuple(int(x) for x in k), tuple(int(x) + 1 for x in k))] = complex(
+            math.prod(math.sqrt(x + 1) for x in k))
+    T = scaled_time * math.pi / p["omega_q"]
+    return Problem(n_modes=n_modes, N=(N,) * n_modes, h_terms=h, jumps=[],
+                   secular=[SecularDamping(j, p["kappa"], ()) for j in range(n_modes)],
+                   measured=meas, channels=[Channel("cexp", (1.0, 0.0, p["omega_d"]))],
+                   T=T, dt=T / steps, name=f"table_one_{n_modes}")
