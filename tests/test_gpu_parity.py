@@ -7,6 +7,8 @@ import math
 import numpy as np
 import pytest
 
+import paper_2203_05526_gb300 as bq
+
 from oracle import fock, mapping
 from workloads import configs
 from workloads.spec import Problem
@@ -172,3 +174,24 @@ def test_two_mode_multi_tile_matches_oracle():
     _, _, _, r = d.read_system(0)
     A = fock.rk4_adjoint(p)
     assert rel_err(r, A.reshape(-1)) <= TOL64
+
+
+def test_three_modes_with_halo_beyond_shared_memory():
+    """Three coupled modes at N = 6: the stencil's outermost stride (6^5 points) does not fit
+    beside a tile in shared memory, so the stage kernel reads R from global memory; direct
+    and mapped methods against O1 / O2."""
+    p = configs.table_one_network(3, 6, steps=4000)
+    p = Problem(**{**p.__dict__, "T": 10 * p.dt,  # the first 10 steps, two initial conditions
+                   "measured": {((1, 0, 1), (0, 1, 1)): 1.0 + 0.3j, ((0, 1, 1), (1, 0, 1)): 1.0 - 0.3j}})
+    d = gpu_state(p, method="direct")
+    d.step(p.dt, p.n_steps)
+    _sync()
+    A = fock.rk4_adjoint(p)
+    _, _, _, r = d.read_system(0)
+    assert rel_err(r, A.reshape(-1)) <= TOL64
+    m = gpu_state(p)
+    m.step(p.dt, p.n_steps)
+    _sync()
+    compare_mapped_systems(m, mapping.rk4_mapped(p), TOL64)
+    with pytest.raises(bq.BQError):
+        d.grad(p.dt, 4, 2)
