@@ -10,7 +10,8 @@ through omega_j, eta_j) and the real and imaginary parts of every segment of eve
 piecewise-constant channel.
 
 Method: the exact discrete adjoint of classical RK4 applied to the separated system of
-Eqs. 9a-c.  With stage inputs u_i, stage derivatives k_i = f(u_i, t_i) and
+Eqs. 9a-c (with the secular dissipator's projector P of Eq. 302c where the problem has one:
+P^T acts on b_R and, through the source P(G_x G_y), on G_x and G_y).  With stage inputs u_i, stage derivatives k_i = f(u_i, t_i) and
 z' = z + h/6 (k1 + 2 k2 + 2 k3 + k4), the cotangent lam' of z' is pulled back as
     b4 = h/6 lam',  q_i = J_i^T b_i,  b3 = h/3 lam' + h q4,  b2 = h/3 lam' + h/2 q3,
     b1 = h/6 lam' + h/2 q2,  lam = lam' + q1 + q2 + q3 + q4,
@@ -20,7 +21,8 @@ J^T of the bilinear source S(G_x G_y) contributes to G_x and G_y.  Forward state
 checkpointed every ``checkpoint_every`` steps and each segment is recomputed once.
 
 Parity status: pinned by central finite differences of oracle.mapping.rk4_mapped
-(tests/test_oracle_grad.py).
+(tests/test_oracle_grad.py), with conventional jump operators and with the secular
+dissipator (one and two modes, finite temperature).
 """
 
 from __future__ import annotations
@@ -91,8 +93,6 @@ class _Derivs:
 
 def loss_and_grad(problem: Problem, M: Optional[Sequence[int]] = None, checkpoint_every: int = 64):
     """Returns (loss, dl/dtheta (len P), {channel: dl/d(Re, Im) of each segment (n_seg, 2)})."""
-    if getattr(problem, "secular", None):
-        raise NotImplementedError("gradients with secular dissipators are not implemented")
     model = MappedModel(problem, M)
     M = model.M
     der = _Derivs(problem, model)
@@ -127,6 +127,12 @@ def loss_and_grad(problem: Problem, M: Optional[Sequence[int]] = None, checkpoin
             # source kappa (Ld_l gx) (L_r gy)^T: derivative wrt gx and gy
             qx += kappa * (Ld_l.T @ (bR @ (L_r @ u[1])))
             qy += kappa * (L_r.T @ (bR.T @ (Ld_l @ u[0])))
+        if model.secular:
+            # secular projector P on R and on the source P(G_x G_y) (Eq. 303c with Eq. 302c)
+            PT = model.secular_projector_T(bR)
+            qR += PT
+            qx += PT @ u[1]
+            qy += PT.T @ u[0]
         return qx, qy, qR
 
     def param_dot(b, u, tau_step, c, C_derivs):

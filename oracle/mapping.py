@@ -320,6 +320,32 @@ class MappedModel:
             self.secular.append((j, w_down, w_up))
         del n
 
+    def secular_projector_T(self, B: np.ndarray) -> np.ndarray:
+        """Transpose of ``secular_projector``: each weight moves B's diagonal entry back to
+        the entry it was taken from."""
+        n = self.p.n_modes
+        out = np.zeros_like(B)
+        if not self.secular:
+            return out
+        Br = B.reshape(self.M + self.M)
+        Or = out.reshape(self.M + self.M)
+        for j, w_down, w_up in self.secular:
+            for m in range(self.M[j]):
+                src = [slice(None)] * (2 * n)
+                src[j] = m
+                src[n + j] = m
+                if m >= 1 and w_down[m] != 0.0:
+                    dst = list(src)
+                    dst[j] = m - 1
+                    dst[n + j] = m - 1
+                    Or[tuple(dst)] += w_down[m] * Br[tuple(src)]
+                if w_up[m] != 0.0:
+                    dst = list(src)
+                    dst[j] = m + 1
+                    dst[n + j] = m + 1
+                    Or[tuple(dst)] += w_up[m] * Br[tuple(src)]
+        return out
+
     def secular_projector(self, F: np.ndarray) -> np.ndarray:
         """sum over secular dissipators of their P term applied to F (x index, y index)."""
         n = self.p.n_modes

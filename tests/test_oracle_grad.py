@@ -70,3 +70,21 @@ def test_checkpoint_interval_does_not_change_gradient():
     b = grad.loss_and_grad(p, checkpoint_every=100)
     assert np.max(np.abs(a[1] - b[1])) < 1e-14
     assert np.max(np.abs(a[2][0] - b[2][0])) < 1e-14
+
+
+@pytest.mark.parametrize("n_modes,N", [(1, 5), (2, 3)])
+def test_adjoint_with_secular_dissipator_matches_central_differences(n_modes, N):
+    """The secular dissipator (Eq. 203 / Eq. S9 at finite temperature) in place of the jump
+    operators: the transposed projector P^T on b_R and on the separable source."""
+    from workloads.spec import SecularDamping
+    p = _small_control(n_modes=n_modes, N=N)
+    p.jumps = []
+    p.secular = [SecularDamping(j, 0.6 + 0.2 * j, (0.1, 0.15, 0.2)) for j in range(n_modes)]
+    p.measured = ({((1,), (1,)): 1.0, ((0,), (1,)): 0.3 + 0.2j, ((1,), (0,)): 0.3 - 0.2j} if n_modes == 1 else
+                  {((1, 0), (1, 0)): 1.0, ((0, 1), (1, 0)): 0.4 + 0.1j, ((1, 0), (0, 1)): 0.4 - 0.1j})
+    loss, gt, gp = grad.loss_and_grad(p, checkpoint_every=5)
+    assert abs(loss - grad.loss_only(p)) < 1e-13
+    ft, fp = _fd(p)
+    scale = max(np.max(np.abs(ft)), np.max(np.abs(fp)))
+    assert np.max(np.abs(gt - ft)) < 1e-7 * scale, (gt, ft)
+    assert np.max(np.abs(gp[0] - fp)) < 1e-7 * scale, (gp[0], fp)
