@@ -124,9 +124,9 @@ int bq_problem_add_jump(bq_problem* p, double kappa, int n_terms, const double* 
  * and, for n = 0..n_nbar-1, the thermal occupation nbar[n] >= 0 of the bath at the n <-> n+1
  * transition frequency (Eq. S10; n >= n_nbar: 0; n_nbar = 0 is zero temperature).  In the
  * mapped representation it is a separable decay plus the projector term P of Eq. 302c /
- * Eq. S15, which acts only where the x and y indices of the mode agree; states with such a
- * term are stepped by the tiled stage kernel (any mode count) and bq_grad returns
- * BQ_EUNSUPPORTED for them.  BQ_EINVAL for a bad mode, rate or occupation. */
+ * Eq. S15, which acts only where the x and y indices of the mode agree (every stage,
+ * persistent-solve and adjoint kernel restricts it there).  BQ_EINVAL for a bad mode, rate
+ * or occupation. */
 int bq_problem_add_secular(bq_problem* p, int mode, double kappa, int n_nbar, const double* nbar);
 
 /* Measured operator A(0) by number-basis elements <k|A|l> = re + i im; k, l are n x n_modes

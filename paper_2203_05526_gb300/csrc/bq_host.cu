@@ -1874,7 +1874,6 @@ static int set_tau(bq_state* s, double tau, cudaStream_t st) {
 
 extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_every, void* work, size_t work_bytes,
                        double* loss_out, double* grad_out, void* stream) {
-  if (s && s->has_diag) return fail(BQ_EUNSUPPORTED, "gradients with secular dissipators are not implemented");
   if (s && s->r_diag) return fail(BQ_EUNSUPPORTED, "gradients with the diagonal residual layout are not implemented");
   if (s && s->has_gread)
     return fail(BQ_EUNSUPPORTED, "gradients of systems whose stencil halo exceeds a shared-memory tile are not implemented");

@@ -1324,6 +1324,9 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
       const C up = U[sd.off_r + p];
       for (int t = 0; t < nt; ++t) {
         const TermDesc& td = st[t];
+        // secular projector term: it shifts x and y alike, so its source p - delta lies on the
+        // diagonal of its mode exactly when p does
+        if (td.diagp1 && idx[td.diagp1 - 1] != idx[NM + td.diagp1 - 1]) continue;
         T w = (T)1;
         bool ok = true;
         for (int i = 0; i < td.n_act; ++i) {
@@ -1487,6 +1490,9 @@ __global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
   const C* other = U + (dirx ? sd.off_gy : sd.off_gx);
   const T* W = reinterpret_cast<const T*>(A.wtab);
   const int delta = dirx ? td.deltaGy : td.deltaGx;
+  // secular projector term: only pairs whose indices of mode dm agree contribute
+  const int dm = td.diagp1 - 1;
+  auto midx = [&](int f) { return dm >= 0 ? (f / sd.stG[dm]) % sd.M[dm] : 0; };
   // out[i] = bscale sum_j B(i, j) z[j], z[j] = w(j) other[j + delta], with B(i, j) the R
   // cotangent at (i, j) (dirx) or (j, i), and w(j) the product of the term's weights on the
   // summed side.  Chunks of z go through shared memory; the sums run in a fixed order.
@@ -1520,15 +1526,18 @@ __global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
         const int i = i0 + warp * (BQ_SRC_TILE / (BQ_SRC_THREADS / 32)) + r;
         if (i < ng) {
           const C* row = bsrc + (int64_t)i * ng + jc;
-          for (int jj = lane; jj < nj; jj += 32) acc[r] = cfma(row[jj], z[jj], acc[r]);
+          const int mi = midx(i);
+          for (int jj = lane; jj < nj; jj += 32)
+            if (dm < 0 || midx(jc + jj) == mi) acc[r] = cfma(row[jj], z[jj], acc[r]);
         }
       }
     } else {
       // column i0 + lane: warps split j (coalesced across lanes)
       const int i = i0 + lane;
+      const int mi = midx(i);
       if (i < ng)
         for (int jj = warp; jj < nj; jj += BQ_SRC_THREADS / 32)
-          accc = cfma(bsrc[(int64_t)(jc + jj) * ng + i], z[jj], accc);
+          if (dm < 0 || midx(jc + jj) == mi) accc = cfma(bsrc[(int64_t)(jc + jj) * ng + i], z[jj], accc);
     }
   }
   C* out = reinterpret_cast<C*>(const_cast<void*>(A.srcred)) + (int64_t)blockIdx.x * A.srcred_stride +

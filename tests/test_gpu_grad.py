@@ -82,6 +82,22 @@ def test_batched_gradients_equal_single_problem_gradients():
     assert np.max(np.abs(g[:n_per] - ref)) <= 1e-10 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("n_modes,N,ck", [(1, 5, 7), (2, 3, 5)])
+def test_grad_with_secular_dissipator_matches_oracle_adjoint(n_modes, N, ck):
+    """The secular dissipator at finite temperature in place of the jump operators: the
+    adjoint kernels apply the transposed projector only on diagonal index pairs."""
+    from workloads.spec import SecularDamping
+    p = _small_control(n_modes=n_modes, N=N)
+    p.jumps = []
+    p.secular = [SecularDamping(j, 0.6 + 0.2 * j, (0.1, 0.15, 0.2)) for j in range(n_modes)]
+    loss_o, gt, gp = ograd.loss_and_grad(p, checkpoint_every=ck)
+    st = gpu_state(p)
+    loss, g = st.grad(p.dt, p.n_steps, ck)
+    ref = _flat_oracle(gt, gp)
+    assert abs(loss[0] - loss_o) <= 1e-12 * max(1.0, abs(loss_o))
+    assert np.max(np.abs(g - ref)) <= 1e-10 * np.max(np.abs(ref)), (g, ref)
+
+
 def test_grad_direct_method_matches_finite_differences():
     p = _small_control(n_modes=1, N=5)
     st = gpu_state(p, method="direct")

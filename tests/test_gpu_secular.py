@@ -7,8 +7,6 @@ import math
 import numpy as np
 import pytest
 
-import paper_2203_05526_gb300 as bq
-from paper_2203_05526_gb300.binding import BQ_EUNSUPPORTED
 from oracle import fock, mapping
 from workloads import configs
 
@@ -117,7 +115,7 @@ def test_projector_never_sources_off_diagonal_products():
     compare_mapped_systems(st, mapping.rk4_mapped(p), TOL64)
 
 
-def test_batch_schedules_and_refusals():
+def test_batch_schedules_and_persistent_solves():
     ps = configs.secular_batch(B=48, T=0.2, dt=0.002, n_min=10, n_max=20)
     st = gpu_state(ps, dtype="f32")
     assert st.stage_variant() == "pipelined" and st.solve_eligible()
@@ -143,6 +141,3 @@ def test_batch_schedules_and_refusals():
             for x, y in zip(sv.read_system(i)[1:], ref.read_system(i)[1:]):
                 if x is not None:
                     assert rel_err(x, y) <= 1e-10, (kernel, i)
-    with pytest.raises(bq.BQError) as e:
-        gpu_state(_single()).grad(0.005, 10, 5)
-    assert e.value.args[0].startswith(f"bq status {BQ_EUNSUPPORTED}")
