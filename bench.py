@@ -286,6 +286,7 @@ def grads_leg(n_steps=None):
     from workloads import configs
     p = configs.two_mode_control()
     st = bq.State([bq.problem_from_spec(p)], bq.map_opts(dtype="f64", horizon=p.T, dt=p.dt))
+    tune = st.autotune(p.dt, trial_steps=16)  # tile length of the tiled kernels
     st.grad(p.dt, 320, 160)  # warm-up (modules, workspace)
     torch.cuda.synchronize()
     steps = p.n_steps if n_steps is None else n_steps
@@ -295,7 +296,7 @@ def grads_leg(n_steps=None):
     out = {"workload": f"two_mode_control: 2 modes x M=12, 64 pwc segments, 131 parameters, {steps} RK4 steps, "
                        "checkpoint every 160, complex FP64",
            "seconds_per_gradient": el, "grads_per_s": 1.0 / el, "loss": float(loss[0]),
-           "grad_norm": float(np.linalg.norm(g)), "n_params": int(g.size)}
+           "grad_norm": float(np.linalg.norm(g)), "n_params": int(g.size), "tile": tune["tile"]}
     if n_steps is None:
         out["batched"] = grads_batched_leg()
     return out
@@ -314,6 +315,7 @@ def grads_batched_leg(B: int = 16, steps: int = 1280):
     dt = probs[0].dt
     opts = bq.map_opts(dtype="f64", horizon=probs[0].T, dt=dt)
     stB = bq.State([bq.problem_from_spec(q) for q in probs], opts)
+    tile = stB.autotune(dt, trial_steps=8)["tile"]
     stB.grad(dt, 160, 160)  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -324,6 +326,7 @@ def grads_batched_leg(B: int = 16, steps: int = 1280):
     n_per = gB.size // B
     for b, q in enumerate(probs):
         st1 = bq.State([bq.problem_from_spec(q)], opts)
+        st1.autotune(dt, trial_steps=8)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         l1, g1 = st1.grad(dt, steps, 160)
@@ -333,7 +336,7 @@ def grads_batched_leg(B: int = 16, steps: int = 1280):
     return {"workload": f"{B} two_mode_control problems (seeds 5526..{5526 + B - 1}), first {steps} RK4 steps, "
                         "checkpoint every 160, complex FP64",
             "batched_grads_per_s": B / tB, "one_instance_per_launch_grads_per_s": B / t1,
-            "batched_vs_one_per_launch": t1 / tB, "max_rel_diff_batched_vs_single": worst}
+            "batched_vs_one_per_launch": t1 / tB, "max_rel_diff_batched_vs_single": worst, "tile_batched": tile}
 
 
 def methods_leg(B: int = 1024, Ns=(10, 20, 40), steps: int = 100, acc_steps: int = 50000):

@@ -198,6 +198,9 @@ typedef struct bq_tune {
   int n_candidates;      /* bq_autotune: schedules measured */
   double step_us;        /* bq_autotune: device time of one RK4 step with bq_step's schedule */
   double solve_us;       /* bq_autotune: device time per RK4 step with bq_solve's schedule */
+  int tile;              /* BQ_PATH_TILED: points per tile of a split system (0 = enough tiles
+                          * for two CTAs per SM; >= 64); also the adjoint's tiles */
+  int pad;
 } bq_tune;
 
 /* Current schedules of the state (step_us / solve_us: last bq_autotune result, else 0). */
@@ -205,7 +208,9 @@ int bq_get_tune(const bq_state* s, bq_tune* out);
 
 /* Sets the schedules.  BQ_EUNSUPPORTED if a path or kernel is not available for this state
  * (BQ_PATH_PIPE / BQ_PATH_SYSTEM need a single-mode state; BQ_SOLVE_MERGED needs every
- * stencil shift in {-1, 0, 1}; pipe_slots must fit in shared memory). */
+ * stencil shift in {-1, 0, 1}; pipe_slots and tiles must fit in shared memory).  A new tile
+ * length rewrites the state's work items with a synchronous copy: call it while no step of
+ * the state is in flight. */
 int bq_set_tune(bq_state* s, const bq_tune* t);
 
 /* Device bytes of the scratch buffer bq_autotune needs: a copy of the state and its
@@ -213,7 +218,7 @@ int bq_set_tune(bq_state* s, const bq_tune* t);
 int bq_autotune_scratch_bytes(const bq_state* s, size_t* out);
 
 /* Measures every available schedule on the state itself: for bq_step the available paths x
- * slot counts x CTAs per SM, for bq_solve the available kernels x CTAs per SM, each over
+ * slot counts x CTAs per SM (pipelined) or tile lengths (tiled), for bq_solve the available kernels x CTAs per SM, each over
  * trial_steps RK4 steps of size dt after one warm-up step (CUDA events on stream), and sets
  * the fastest.  The state, its compensation and its time are saved into the caller-owned
  * device buffer scratch (scratch_bytes >= bq_autotune_scratch_bytes) first and restored

@@ -756,6 +756,7 @@ struct bq_state {
   int has_diag = 0;     // some term acts only on diagonal index pairs (secular dissipator)
   int r_diag = 0;       // diagonal residual layout
   int has_gread = 0;    // some work item reads its R sources from global memory
+  int work_cap = 0, tile = 0;  // work-item capacity of the pool; tiled schedule (0 = default)
   int ng_max = 0;      // largest G_x / G_y point count over the systems
   // schedules (bq_get_tune / bq_set_tune / bq_autotune)
   int pipe_ok = 0;      // the pipelined path is available (single mode, two slots fit)
@@ -809,6 +810,7 @@ struct Plan {
   int pipe_slot[3] = {0, 0, 0};
   std::vector<unsigned char> pparams;
   std::vector<bq::PipeRec> precs;
+  size_t work_cap = 0;  // work-item capacity of the pool (the smallest schedulable tile)
   std::vector<cplx> pcoef;           // stage coefficients that do not depend on time (n_sys x BQ_PIPE_COEF)
   std::vector<bq::CoefDyn> pcdyn;    // and the entries that do
   int solve_smem = 0;
@@ -823,6 +825,60 @@ struct Plan {
   double rho = 0.0, dt_max = 0.0;
   Layout L{};
 };
+
+// Work items of the tiled stage kernel: tiles of R, the first tile of a system also updates
+// G_x and G_y.  A system that fits in one shared-memory tile takes one CTA unless the batch
+// is too small to fill the GPU that way; larger ones are split into tiles with halo windows
+// (or, when the halo does not fit beside a tile, tiles that read R from global memory).
+// tile > 0 sets the length of the split tiles (a schedule); 0 = enough tiles for two CTAs
+// per SM.  smem_max / adj_max: complex elements of shared memory of the forward and the
+// adjoint stage kernel.
+static void build_work(const std::vector<SysDesc>& sys, size_t cs, int tile, std::vector<WorkItem>& work,
+                       int& smem_max, int& adj_max) {
+  const int budget = (int)(96 * 1024 / cs);
+  work.clear();
+  smem_max = adj_max = 0;
+  const int nsys = (int)sys.size();
+  for (int i = 0; i < nsys; ++i) {
+    const SysDesc& sd = sys[i];
+    const int sep = sd.has_sep ? 2 * sd.n_g : 0;
+    const int adj_sep = sd.has_sep ? (2 + 2 * sd.n_sterms) * sd.n_g : 0;
+    if (!sd.has_r) {
+      work.push_back(WorkItem{i, 0, 0, 1, 0, 0, sep, 0});
+      smem_max = std::max(smem_max, sep);
+      adj_max = std::max(adj_max, adj_sep);
+      continue;
+    }
+    const bool few = nsys < 2 * 152 && sd.n_r >= 2 * 256;
+    if (sd.n_r + sep <= budget && !few) {
+      work.push_back(WorkItem{i, 0, sd.n_r, sd.has_sep, 0, sd.n_r, sd.n_r + sep, 0});
+      smem_max = std::max(smem_max, sd.n_r + sep);
+      adj_max = std::max(adj_max, sd.n_r + adj_sep);
+      continue;
+    }
+    int tl = budget - sep - sd.halo_lo - sd.halo_hi;
+    const int gread = tl < 64 ? 1 : 0;  // the halo does not fit next to a tile: read R from global memory
+    if (gread) tl = 1 << 30;
+    if (tile > 0) {
+      tl = gread ? tile : std::min(tl, tile);
+    } else {
+      // enough CTAs per launch to occupy every SM twice
+      const int want_tiles = std::max(1, (2 * 152 + nsys - 1) / nsys);
+      const int tl_par = std::max(few ? 256 : 64, (sd.n_r + want_tiles - 1) / want_tiles);
+      tl = std::min(tl, tl_par);
+    }
+    for (int s0 = 0; s0 < sd.n_r; s0 += tl) {
+      WorkItem w;
+      w.sys = i; w.start = s0; w.len = std::min(tl, sd.n_r - s0); w.do_sep = (s0 == 0) ? sd.has_sep : 0;
+      w.win_lo = gread ? s0 : std::max(0, s0 - sd.halo_lo);
+      w.win_hi = gread ? s0 : std::min(sd.n_r, s0 + w.len + sd.halo_hi);
+      w.smem_elems = (w.win_hi - w.win_lo) + sep; w.gread = gread;
+      smem_max = std::max(smem_max, w.smem_elems);
+      adj_max = std::max(adj_max, (w.win_hi - w.win_lo) + adj_sep);
+      work.push_back(w);
+    }
+  }
+}
 
 static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o, Plan& P) {
   if (!probs || B < 1 || !o) return fail(BQ_EINVAL, "bad map arguments");
@@ -1132,59 +1188,29 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
   }
 
   // ---- work items (tiles of R; the first tile of a system also updates G_x, G_y) ------
-  const int budget = (int)(96 * 1024 / cs);
-  int smem_max = 0;
-  for (int i = 0; i < (int)P.sys.size() && !P.use_m1; ++i) {
-    const SysDesc& sd = P.sys[i];
-    const int sep = sd.has_sep ? 2 * sd.n_g : 0;
-    if (!sd.has_r) {
-      WorkItem w{i, 0, 0, 1, 0, 0, sep, 0};
-      P.work.push_back(w);
-      smem_max = std::max(smem_max, sep);
-      continue;
-    }
-    // a system that fits in one tile takes one CTA, unless the batch is too small to fill the
-    // GPU that way (then it is split like a large one)
-    const bool few = (int)P.sys.size() < 2 * 152 && sd.n_r >= 2 * 256;
-    if (sd.n_r + sep <= budget && !few) {
-      WorkItem w{i, 0, sd.n_r, sd.has_sep, 0, sd.n_r, sd.n_r + sep, 0};
-      P.work.push_back(w);
-      smem_max = std::max(smem_max, sd.n_r + sep);
-      continue;
-    }
-    int tl = budget - sep - sd.halo_lo - sd.halo_hi;
-    const int gread = tl < 64 ? 1 : 0;  // the halo does not fit next to a tile: read R from global memory
-    if (gread) tl = 1 << 30;
-    // enough CTAs per launch to occupy every SM twice (the multi-mode kernels are ALU-bound
-    // in FP64, so the larger halo share of small tiles costs L2 bandwidth, not time)
-    {
-      const int want_tiles = std::max(1, (2 * 152 + (int)P.sys.size() - 1) / (int)P.sys.size());
-      const int tl_par = std::max(few ? 256 : 64, (sd.n_r + want_tiles - 1) / want_tiles);
-      tl = std::min(tl, tl_par);
-    }
-    for (int s = 0; s < sd.n_r; s += tl) {
-      WorkItem w;
-      w.sys = i; w.start = s; w.len = std::min(tl, sd.n_r - s); w.do_sep = (s == 0) ? sd.has_sep : 0;
-      w.win_lo = gread ? s : std::max(0, s - sd.halo_lo);
-      w.win_hi = gread ? s : std::min(sd.n_r, s + w.len + sd.halo_hi);
-      w.smem_elems = (w.win_hi - w.win_lo) + sep; w.gread = gread;
-      smem_max = std::max(smem_max, w.smem_elems);
-      P.work.push_back(w);
-    }
+  for (SysDesc& sd : P.sys) {
+    int ns = 0;
+    for (auto& td : P.comp[sd.prob].terms) ns += td.side == bq::SIDE_S;
+    sd.n_sterms = ns;
+    P.srcred_stride = std::max(P.srcred_stride, (sd.has_sep && sd.has_r) ? 2 * ns * sd.n_g : 0);
+    P.max_s = std::max(P.max_s, (sd.has_sep && sd.has_r) ? ns : 0);
   }
-  if (!P.use_m1) P.smem_bytes = (int)(smem_max * cs);
-  // adjoint stage kernel: b window + b_gx + b_gy + transposed-source reductions
-  {
+  if (!P.use_m1) {
+    int smem_max = 0, adj_max = 0;
+    build_work(P.sys, cs, 0, P.work, smem_max, adj_max);
+    P.smem_bytes = (int)(smem_max * cs);
+    P.adj_smem = (int)(adj_max * cs);
+    // capacity for the smallest tile the schedules may choose
+    std::vector<WorkItem> w64;
+    int s64 = 0, a64 = 0;
+    build_work(P.sys, cs, 64, w64, s64, a64);
+    P.work_cap = std::max(P.work.size(), w64.size());
+  } else {  // one-CTA-per-system items (whole system as the window) for the adjoint kernel
     size_t adj_max = 0;
     for (auto& w : P.work) {
       const SysDesc& sd = P.sys[w.sys];
-      const Compiled& C = P.comp[sd.prob];
-      int ns = 0;
-      for (auto& td : C.terms) ns += td.side == bq::SIDE_S;
-      const size_t e = (size_t)(w.win_hi - w.win_lo) + (sd.has_sep ? (size_t)(2 + 2 * ns) * sd.n_g : 0);
-      adj_max = std::max(adj_max, e);
-      P.srcred_stride = std::max(P.srcred_stride, (sd.has_sep && sd.has_r) ? 2 * ns * sd.n_g : 0);
-      P.max_s = std::max(P.max_s, (sd.has_sep && sd.has_r) ? ns : 0);
+      adj_max = std::max(adj_max, (size_t)(w.win_hi - w.win_lo) +
+                                      (sd.has_sep ? (size_t)(2 + 2 * sd.n_sterms) * sd.n_g : 0));
     }
     P.adj_smem = (int)(adj_max * cs);
   }
@@ -1200,7 +1226,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
   L.off_terms = seg(P.terms.size() * sizeof(TermDesc));
   L.off_chans = seg(P.chans.size() * sizeof(ChanDesc));
   L.off_chpar = seg(P.chpar.size() * sizeof(double));
-  L.off_work = seg(P.work.size() * sizeof(WorkItem));
+  L.off_work = seg(std::max(P.work.size(), P.work_cap) * sizeof(WorkItem));
   L.off_m1 = seg(P.m1.size() * sizeof(bq::M1Sys));
   L.off_order = seg(P.order.size() * sizeof(int));
   L.off_pparams = seg(P.pparams.size());
@@ -1334,6 +1360,7 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   auto* st = new bq_state();
   st->B = B; st->nm = probs[0]->nm; st->dtype = o->dtype; st->method = o->method; st->basis = P.comp[0].basis;
   st->n_sys = (int)P.sys.size(); st->n_work = (int)P.work.size(); st->smem_bytes = P.smem_bytes;
+  st->work_cap = (int)std::max(P.work.size(), P.work_cap);
   st->use_m1 = P.use_m1;
   {
     int mt = 0, mb = 0;
@@ -1626,6 +1653,30 @@ static void drop_graph(bq_state* s) {
   if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
 }
 
+// Rewrites the tiled kernel's work items for tile length `tile` (0 = default).
+static int apply_tile(bq_state* s, int tile) {
+  if (s->use_m1) return fail(BQ_EUNSUPPORTED, "single-mode states have no tiled work items");
+  if (tile != 0 && tile < 64) return fail(BQ_EINVAL, "tile must be 0 or >= 64");
+  const size_t cs = s->dtype == BQ_F64 ? 16 : 8;
+  std::vector<WorkItem> work;
+  int smem = 0, adj = 0;
+  build_work(s->sys, cs, tile, work, smem, adj);
+  if ((int)work.size() > s->work_cap) return fail(BQ_EUNSUPPORTED, "tile %d needs %zu work items > %d", tile, work.size(), s->work_cap);
+  if ((size_t)smem * cs > BQ_MAX_DYN_SMEM || (size_t)adj * cs > BQ_MAX_DYN_SMEM)
+    return fail(BQ_EUNSUPPORTED, "tile %d needs more shared memory than a CTA has", tile);
+  CUDA_TRY(cudaMemcpy(s->pool + s->L.off_work, work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+  s->n_work = (int)work.size();
+  s->smem_bytes = (int)(smem * cs);
+  s->adj_smem = (int)(adj * cs);
+  s->tile = tile;
+  int g = 0;
+  for (const WorkItem& w : work) g = g || w.gread;
+  s->has_gread = g;
+  s->work_host = std::move(work);
+  drop_graph(s);
+  return BQ_OK;
+}
+
 extern "C" int bq_get_tune(const bq_state* s, bq_tune* out) {
   if (!s || !out) return fail(BQ_EINVAL, "NULL argument");
   std::memset(out, 0, sizeof(*out));
@@ -1637,6 +1688,7 @@ extern "C" int bq_get_tune(const bq_state* s, bq_tune* out) {
   out->n_candidates = s->tune_n;
   out->step_us = s->tune_step_us;
   out->solve_us = s->tune_solve_us;
+  out->tile = s->tile;
   return BQ_OK;
 }
 
@@ -1655,9 +1707,14 @@ extern "C" int bq_set_tune(bq_state* s, const bq_tune* t) {
       if (!s->use_m1) return fail(BQ_EUNSUPPORTED, "the one-CTA-per-system path needs a single-mode state");
       s->use_pipe = 0;
       break;
-    case BQ_PATH_TILED:
+    case BQ_PATH_TILED: {
       if (s->use_m1) return fail(BQ_EUNSUPPORTED, "single-mode states have no tiled work items");
+      if (t->tile != s->tile) {
+        const int rc = apply_tile(s, t->tile);
+        if (rc != BQ_OK) return rc;
+      }
       break;
+    }
     default:
       return fail(BQ_EINVAL, "unknown stage path %d", t->stage_path);
   }
@@ -1750,12 +1807,17 @@ extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratc
         if (per_sm > 2 && s->n_sys > per_sm * nsm) cands.push_back({BQ_PATH_PIPE, slots, per_sm - 1});
       }
     }
-    if (s->use_m1) cands.push_back({BQ_PATH_SYSTEM, 0, 0});
-    else cands.push_back({BQ_PATH_TILED, 0, 0});
+    if (s->use_m1) {
+      cands.push_back({BQ_PATH_SYSTEM, 0, 0});
+    } else {  // tile lengths (the cap field carries the tile; 0 = default)
+      for (int tl : {0, 64, 96, 128, 192, 256, 384, 512, 1024}) cands.push_back({BQ_PATH_TILED, 0, tl});
+    }
     for (const Cand& c : cands) {
       if (c.path == BQ_PATH_PIPE) {
         if ((rc = pipe_configure(s, c.slots, c.cap)) != BQ_OK) break;
         s->use_pipe = 1;
+      } else if (c.path == BQ_PATH_TILED) {
+        if (apply_tile(s, c.cap) != BQ_OK) { g_err.clear(); continue; }  // a tile that does not fit
       } else {
         s->use_pipe = 0;
       }
@@ -1766,7 +1828,8 @@ extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratc
         best_step = us;
         best.stage_path = c.path;
         best.pipe_slots = c.path == BQ_PATH_PIPE ? c.slots : 2;
-        best.pipe_ctas_per_sm = c.cap;
+        best.pipe_ctas_per_sm = c.path == BQ_PATH_PIPE ? c.cap : 0;
+        best.tile = c.path == BQ_PATH_TILED ? c.cap : s->tile;
       }
     }
   }

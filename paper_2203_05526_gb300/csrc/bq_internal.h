@@ -73,7 +73,7 @@ struct SysDesc {
   int n_params;         // parameters of the problem
   int grad_off;         // gradient slot of the problem's first parameter
   int r_diag;           // R stored only at k = l (n_r = n_g entries, index = flat k)
-  int pad2;
+  int n_sterms;         // sandwich terms of the system's problem (adjoint source reductions)
 };
 
 // A CTA's share of one stage: a tile of R points of one system (plus G_x, G_y if sep).

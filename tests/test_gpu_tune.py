@@ -121,3 +121,43 @@ def test_unavailable_schedules_are_refused():
         one.set_tune(stage_path="tiled")
     tune = st.autotune(two.dt, trial_steps=2)
     assert tune["stage_path"] == "tiled" and tune["solve_kernel"] is None
+
+
+def test_tile_lengths_compute_the_same_step_and_gradients():
+    """The tiled kernel evaluates every point from the same sources whatever the tile length
+    (shared-memory halo or global reads): the step and the adjoint gradients agree with the
+    default tiling to rounding, and the autotuner keeps a tile from its candidate list."""
+    p = configs.two_mode_control(n_seg=3, T=0.18, steps_per_seg=6, N=7)
+    p.measured = {((1, 0), (0, 1)): 0.7 + 0.2j, ((0, 1), (1, 0)): 0.7 - 0.2j, ((1, 0), (1, 0)): 1.0,
+                  ((2, 1), (0, 0)): 0.3, ((0, 0), (2, 1)): 0.3}
+    ref = gpu_state(p)
+    assert ref.get_tune()["stage_path"] == "tiled" and ref.get_tune()["tile"] == 0
+    ref.step(p.dt, p.n_steps)
+    _sync()
+    l0, g0 = gpu_state(p).grad(p.dt, p.n_steps, 6)
+    for tile in (64, 96, 192, 1024):
+        st = gpu_state(p)
+        st.set_tune(tile=tile)
+        assert st.get_tune()["tile"] == tile
+        st.step(p.dt, p.n_steps)
+        _sync()
+        for s in range(ref.n_systems()):
+            for x, y in zip(st.read_system(s)[1:], ref.read_system(s)[1:]):
+                if y is not None:
+                    assert rel_err(x, y) <= 1e-13, (tile, s)
+        gs = gpu_state(p)
+        gs.set_tune(tile=tile)
+        l1, g1 = gs.grad(p.dt, p.n_steps, 6)
+        assert abs(l1[0] - l0[0]) <= 1e-13 * max(1.0, abs(l0[0]))
+        assert np.max(np.abs(g1 - g0)) <= 1e-12 * np.max(np.abs(g0)), tile
+    st = gpu_state(p)
+    with pytest.raises(bq.BQError):
+        st.set_tune(tile=32)
+    tune = st.autotune(p.dt, trial_steps=2)
+    assert tune["tile"] in (0, 64, 96, 128, 192, 256, 384, 512, 1024)
+    assert tune["n_candidates"] >= 2
+    st.step(p.dt, p.n_steps)
+    _sync()
+    for x, y in zip(st.read_system(0)[1:], ref.read_system(0)[1:]):
+        if y is not None:
+            assert rel_err(x, y) <= 1e-13
