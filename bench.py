@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--only-grad", action="store_true",
                     help="profiling aid: only the adjoint gradient of the control problem for --grad-steps steps")
     ap.add_argument("--grad-steps", type=int, default=None)
+    ap.add_argument("--grad-tile", type=int, default=None,
+                    help="profiling aid: tile length of the gradient leg's state instead of the autotuned one")
     ap.add_argument("--no-autotune", action="store_true",
                     help="profiling aid: keep the default schedule of the timed state (no tuning launches)")
     ap.add_argument("--n-range", type=int, nargs=2, default=(10, 40), metavar=("LO", "HI"),
@@ -275,7 +277,7 @@ def batched_leg(world: int):
     return out
 
 
-def grads_leg(n_steps=None):
+def grads_leg(n_steps=None, tile=None):
     """Gradient of P(|1,0>) at T = 200 ns for the two-mode control problem (64 complex
     piecewise-constant drive segments, K_1, K_2, g: 131 real parameters; 20 480 RK4 steps,
     complex FP64, checkpoint every 160 steps) by the discrete adjoint kernels (bq_grad)."""
@@ -286,7 +288,11 @@ def grads_leg(n_steps=None):
     from workloads import configs
     p = configs.two_mode_control()
     st = bq.State([bq.problem_from_spec(p)], bq.map_opts(dtype="f64", horizon=p.T, dt=p.dt))
-    tune = st.autotune(p.dt, trial_steps=16)  # tile length of the tiled kernels
+    if tile is None:
+        tune = st.autotune(p.dt, trial_steps=16)  # tile length of the tiled kernels
+    else:
+        st.set_tune(tile=tile)
+        tune = st.get_tune()
     st.grad(p.dt, 320, 160)  # warm-up (modules, workspace)
     torch.cuda.synchronize()
     steps = p.n_steps if n_steps is None else n_steps
@@ -296,7 +302,8 @@ def grads_leg(n_steps=None):
     out = {"workload": f"two_mode_control: 2 modes x M=12, 64 pwc segments, 131 parameters, {steps} RK4 steps, "
                        "checkpoint every 160, complex FP64",
            "seconds_per_gradient": el, "grads_per_s": 1.0 / el, "loss": float(loss[0]),
-           "grad_norm": float(np.linalg.norm(g)), "n_params": int(g.size), "tile": tune["tile"]}
+           "grad_norm": float(np.linalg.norm(g)), "n_params": int(g.size), "tile": tune["tile"],
+           "lanes": tune["lanes"]}
     if n_steps is None:
         out["batched"] = grads_batched_leg()
     return out
@@ -315,7 +322,7 @@ def grads_batched_leg(B: int = 16, steps: int = 1280):
     dt = probs[0].dt
     opts = bq.map_opts(dtype="f64", horizon=probs[0].T, dt=dt)
     stB = bq.State([bq.problem_from_spec(q) for q in probs], opts)
-    tile = stB.autotune(dt, trial_steps=8)["tile"]
+    tuneB = stB.autotune(dt, trial_steps=8)
     stB.grad(dt, 160, 160)  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -336,7 +343,8 @@ def grads_batched_leg(B: int = 16, steps: int = 1280):
     return {"workload": f"{B} two_mode_control problems (seeds 5526..{5526 + B - 1}), first {steps} RK4 steps, "
                         "checkpoint every 160, complex FP64",
             "batched_grads_per_s": B / tB, "one_instance_per_launch_grads_per_s": B / t1,
-            "batched_vs_one_per_launch": t1 / tB, "max_rel_diff_batched_vs_single": worst, "tile_batched": tile}
+            "batched_vs_one_per_launch": t1 / tB, "max_rel_diff_batched_vs_single": worst,
+            "tile_batched": tuneB["tile"], "lanes_batched": tuneB["lanes"]}
 
 
 def methods_leg(B: int = 1024, Ns=(10, 20, 40), steps: int = 100, acc_steps: int = 50000):
@@ -533,7 +541,7 @@ def main():
     from paper_2203_05526_gb300 import build
     build.build()
     if args.only_grad:
-        print(json.dumps({"only_grad": True, **grads_leg(args.grad_steps)}))
+        print(json.dumps({"only_grad": True, **grads_leg(args.grad_steps, args.grad_tile)}))
         return
     if args.only_solve:
         specs = configs_batch(args.instances)

@@ -757,6 +757,7 @@ struct bq_state {
   int r_diag = 0;       // diagonal residual layout
   int has_gread = 0;    // some work item reads its R sources from global memory
   int work_cap = 0, tile = 0;  // work-item capacity of the pool; tiled schedule (0 = default)
+  int lanes = 1;               // lanes per point of the tiled forward and the adjoint stage kernels
   int ng_max = 0;      // largest G_x / G_y point count over the systems
   // schedules (bq_get_tune / bq_set_tune / bq_autotune)
   int pipe_ok = 0;      // the pipelined path is available (single mode, two slots fit)
@@ -826,13 +827,24 @@ struct Plan {
   Layout L{};
 };
 
-// Work items of the tiled stage kernel: tiles of R, the first tile of a system also updates
-// G_x and G_y.  A system that fits in one shared-memory tile takes one CTA unless the batch
-// is too small to fill the GPU that way; larger ones are split into tiles with halo windows
-// (or, when the halo does not fit beside a tile, tiles that read R from global memory).
+// Work items of the tiled stage kernel.  A system that fits in one shared-memory tile takes
+// one CTA (R, G_x and G_y) unless the batch is too small to fill the GPU that way; larger ones
+// are split into tiles of R with halo windows (or, when the halo does not fit beside a tile,
+// tiles that read R from global memory) and items that update chunks of [G_x | G_y].
 // tile > 0 sets the length of the split tiles (a schedule); 0 = enough tiles for two CTAs
 // per SM.  smem_max / adj_max: complex elements of shared memory of the forward and the
 // adjoint stage kernel.
+#define BQ_SEP_CHUNK 64
+
+// Lanes per point of the tiled kernels: enough threads for about half the GPU's warp slots
+// (152 SMs x 16 warps), with up to four lanes sharing the terms of a point when the launch
+// has fewer points than that.
+static int default_lanes(const std::vector<SysDesc>& sys) {
+  int64_t pts = 0;
+  for (const SysDesc& sd : sys) pts += (sd.has_r ? sd.n_r : 0) + (sd.has_sep ? 2 * sd.n_g : 0);
+  const int64_t half = 152 * 16 * 32;
+  return pts >= half ? 1 : (pts >= half / 2 ? 2 : 4);
+}
 static void build_work(const std::vector<SysDesc>& sys, size_t cs, int tile, std::vector<WorkItem>& work,
                        int& smem_max, int& adj_max) {
   const int budget = (int)(96 * 1024 / cs);
@@ -843,15 +855,16 @@ static void build_work(const std::vector<SysDesc>& sys, size_t cs, int tile, std
     const SysDesc& sd = sys[i];
     const int sep = sd.has_sep ? 2 * sd.n_g : 0;
     const int adj_sep = sd.has_sep ? (2 + 2 * sd.n_sterms) * sd.n_g : 0;
+    const int nsep = sd.has_sep ? 2 * sd.n_g : 0;
     if (!sd.has_r) {
-      work.push_back(WorkItem{i, 0, 0, 1, 0, 0, sep, 0});
+      work.push_back(WorkItem{i, 0, 0, 0, nsep, 0, 0, sep, 0});
       smem_max = std::max(smem_max, sep);
       adj_max = std::max(adj_max, adj_sep);
       continue;
     }
     const bool few = nsys < 2 * 152 && sd.n_r >= 2 * 256;
     if (sd.n_r + sep <= budget && !few) {
-      work.push_back(WorkItem{i, 0, sd.n_r, sd.has_sep, 0, sd.n_r, sd.n_r + sep, 0});
+      work.push_back(WorkItem{i, 0, sd.n_r, 0, nsep, 0, sd.n_r, sd.n_r + sep, 0});
       smem_max = std::max(smem_max, sd.n_r + sep);
       adj_max = std::max(adj_max, sd.n_r + adj_sep);
       continue;
@@ -867,9 +880,15 @@ static void build_work(const std::vector<SysDesc>& sys, size_t cs, int tile, std
       const int tl_par = std::max(few ? 256 : 64, (sd.n_r + want_tiles - 1) / want_tiles);
       tl = std::min(tl, tl_par);
     }
+    // the separable part of a split system: items of its own, BQ_SEP_CHUNK points each
+    for (int g0 = 0; g0 < nsep; g0 += BQ_SEP_CHUNK) {
+      work.push_back(WorkItem{i, 0, 0, g0, std::min(nsep, g0 + BQ_SEP_CHUNK), 0, 0, sep, 0});
+      smem_max = std::max(smem_max, sep);
+      adj_max = std::max(adj_max, adj_sep);
+    }
     for (int s0 = 0; s0 < sd.n_r; s0 += tl) {
       WorkItem w;
-      w.sys = i; w.start = s0; w.len = std::min(tl, sd.n_r - s0); w.do_sep = (s0 == 0) ? sd.has_sep : 0;
+      w.sys = i; w.start = s0; w.len = std::min(tl, sd.n_r - s0); w.sep_lo = w.sep_hi = 0;
       w.win_lo = gread ? s0 : std::max(0, s0 - sd.halo_lo);
       w.win_hi = gread ? s0 : std::min(sd.n_r, s0 + w.len + sd.halo_hi);
       w.smem_elems = (w.win_hi - w.win_lo) + sep; w.gread = gread;
@@ -1046,7 +1065,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
         m.off_gx = sd.off_gx; m.off_gy = sd.off_gy; m.off_r = sd.off_r;
         m.c_re = sd.c_re; m.c_im = sd.c_im;
         P.m1.push_back(m);
-        WorkItem w{i, 0, sd.has_r ? sd.n_r : 0, sd.has_sep, 0, sd.has_r ? sd.n_r : 0, 0, 0};
+        WorkItem w{i, 0, sd.has_r ? sd.n_r : 0, 0, sd.has_sep ? 2 * sd.n_g : 0, 0, sd.has_r ? sd.n_r : 0, 0, 0};
         P.work.push_back(w);
       }
       P.smem_bytes = (int)m1_max;
@@ -1361,6 +1380,7 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   st->B = B; st->nm = probs[0]->nm; st->dtype = o->dtype; st->method = o->method; st->basis = P.comp[0].basis;
   st->n_sys = (int)P.sys.size(); st->n_work = (int)P.work.size(); st->smem_bytes = P.smem_bytes;
   st->work_cap = (int)std::max(P.work.size(), P.work_cap);
+  st->lanes = default_lanes(P.sys);
   st->use_m1 = P.use_m1;
   {
     int mt = 0, mb = 0;
@@ -1453,6 +1473,7 @@ static bq::StageArgs stage_args(bq_state* s, int stage, double dt) {
   a.horizon = s->horizon;
   a.reverse = s->reverse;
   a.stage = stage;
+  a.lanes = s->lanes;
   return a;
 }
 
@@ -1689,12 +1710,15 @@ extern "C" int bq_get_tune(const bq_state* s, bq_tune* out) {
   out->step_us = s->tune_step_us;
   out->solve_us = s->tune_solve_us;
   out->tile = s->tile;
+  out->lanes = s->lanes;
   return BQ_OK;
 }
 
 extern "C" int bq_set_tune(bq_state* s, const bq_tune* t) {
   if (!s || !t) return fail(BQ_EINVAL, "NULL argument");
   if (t->pipe_ctas_per_sm < 0 || t->solve_ctas_per_sm < 0) return fail(BQ_EINVAL, "negative CTA count");
+  if (t->lanes != 0 && t->lanes != 1 && t->lanes != 2 && t->lanes != 4)
+    return fail(BQ_EINVAL, "lanes must be 0, 1, 2 or 4");
   switch (t->stage_path) {
     case BQ_PATH_PIPE: {
       if (!s->pipe_ok) return fail(BQ_EUNSUPPORTED, "the pipelined path is not available for this state");
@@ -1729,6 +1753,7 @@ extern "C" int bq_set_tune(bq_state* s, const bq_tune* t) {
     }
     s->solve_cap = t->solve_ctas_per_sm;
   }
+  s->lanes = t->lanes == 0 ? default_lanes(s->sys) : t->lanes;
   drop_graph(s);
   return BQ_OK;
 }
@@ -1793,7 +1818,7 @@ extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratc
   bq_get_tune(s, &best);
   double best_step = 1e300;
   {
-    struct Cand { int path, slots, cap; };
+    struct Cand { int path, slots, cap, lanes; };
     std::vector<Cand> cands;
     if (s->pipe_ok) {
       for (int slots = 2; slots <= 4; ++slots) {
@@ -1803,21 +1828,24 @@ extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratc
         CUDA_TRY(cudaGetDevice(&dev));
         CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         const int per_sm = (s->pipe_grid[1] + nsm - 1) / nsm;
-        cands.push_back({BQ_PATH_PIPE, slots, 0});
-        if (per_sm > 2 && s->n_sys > per_sm * nsm) cands.push_back({BQ_PATH_PIPE, slots, per_sm - 1});
+        cands.push_back({BQ_PATH_PIPE, slots, 0, 1});
+        if (per_sm > 2 && s->n_sys > per_sm * nsm) cands.push_back({BQ_PATH_PIPE, slots, per_sm - 1, 1});
       }
     }
     if (s->use_m1) {
-      cands.push_back({BQ_PATH_SYSTEM, 0, 0});
-    } else {  // tile lengths (the cap field carries the tile; 0 = default)
-      for (int tl : {0, 64, 96, 128, 192, 256, 384, 512, 1024}) cands.push_back({BQ_PATH_TILED, 0, tl});
+      cands.push_back({BQ_PATH_SYSTEM, 0, 0, 1});
+    } else {  // tile lengths (the cap field carries the tile; 0 = default) x lanes per point
+      for (int tl : {0, 64, 96, 128, 192, 256, 512})
+        for (int ln : {1, 2, 4}) cands.push_back({BQ_PATH_TILED, 0, tl, ln});
     }
+    const int lanes0 = s->lanes;
     for (const Cand& c : cands) {
       if (c.path == BQ_PATH_PIPE) {
         if ((rc = pipe_configure(s, c.slots, c.cap)) != BQ_OK) break;
         s->use_pipe = 1;
       } else if (c.path == BQ_PATH_TILED) {
-        if (apply_tile(s, c.cap) != BQ_OK) { g_err.clear(); continue; }  // a tile that does not fit
+        if (c.cap != s->tile && apply_tile(s, c.cap) != BQ_OK) { g_err.clear(); continue; }  // a tile that does not fit
+        s->lanes = c.lanes;
       } else {
         s->use_pipe = 0;
       }
@@ -1830,8 +1858,10 @@ extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratc
         best.pipe_slots = c.path == BQ_PATH_PIPE ? c.slots : 2;
         best.pipe_ctas_per_sm = c.path == BQ_PATH_PIPE ? c.cap : 0;
         best.tile = c.path == BQ_PATH_TILED ? c.cap : s->tile;
+        best.lanes = c.path == BQ_PATH_TILED ? c.lanes : lanes0;
       }
     }
+    s->lanes = lanes0;
   }
   // ---- bq_solve schedules -------------------------------------------------------------
   double best_solve = 0.0;
@@ -1995,6 +2025,7 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
   a.reverse = s->reverse;
   a.srcred_stride = s->srcred_stride;
   a.ng_max = s->ng_max;
+  a.lanes = s->lanes;
   for (int64_t c = G.n_ckpt - 1; c >= 0; --c) {
     const int64_t n0 = c * k, n1 = std::min<int64_t>(n_steps, n0 + k);
     // recompute the segment from its checkpoint, recording every stage input

@@ -80,7 +80,7 @@ struct SysDesc {
 struct WorkItem {
   int sys;
   int start, len;       // R tile [start, start + len)
-  int do_sep;           // this CTA also updates G_x and G_y
+  int sep_lo, sep_hi;   // G points [sep_lo, sep_hi) of [G_x | G_y] (2 n_g) this CTA updates
   int win_lo, win_hi;   // R window staged in shared memory
   int smem_elems;       // complex elements of shared memory this item needs
   int gread;            // 1: no R window (the halo does not fit); sources are read from global memory
@@ -137,6 +137,8 @@ struct StageArgs {
   double horizon;
   int reverse;
   int stage;            // 1..4
+  int lanes;            // lanes per point of the tiled kernel (1, 2 or 4): the terms are split
+                        // across them and the partial sums combined with shuffles
 };
 
 // Pipelined single-mode stage kernel (k_stage_pipe): one record per system and one
@@ -240,6 +242,7 @@ struct AdjArgs {
   double tau_step, dt, horizon;
   int reverse, stage, srcred_stride;
   int ng_max;            // largest n_g (G_x / G_y points) over the systems
+  int lanes;             // lanes per point (1, 2 or 4), as in StageArgs
 };
 
 }  // namespace bq

@@ -139,7 +139,8 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
   auto rsrc_at = [&](int i) { return wi.gread ? urg[i] : win[i - wi.win_lo]; };
   C* gxs = win + wn;
   C* gys = gxs + sd.n_g;
-  if (sd.has_sep && (wi.do_sep || sd.has_r)) {
+  const bool do_sep = sd.has_sep && wi.sep_hi > wi.sep_lo;
+  if (sd.has_sep && (do_sep || sd.has_r)) {
     const C* sx = uin + sd.off_gx;
     const C* sy = uin + sd.off_gy;
     for (int i = tid; i < sd.n_g; i += blockDim.x) {
@@ -196,10 +197,27 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
     }
   };
 
+  // Each point is handled by a group of L = A.lanes adjacent lanes: lane `sub` of the group
+  // sums the terms t = sub, sub + L, ... (the first lane also the diagonal part), the group
+  // combines its partial sums with shuffles and the first lane writes the point.  L = 1
+  // keeps the plain one-thread-per-point loop; L > 1 gives the small launches of a few large
+  // systems more warps to hide latency with.
+  const int L = A.lanes;
+  const int sub = tid & (L - 1);
+  const unsigned gmask = L == 1 ? (1u << (tid & 31)) : (((1u << L) - 1u) << ((tid & 31) & ~(L - 1)));
+  const int pstride = (int)blockDim.x / L;
+  auto group_sum = [&](C k) {
+    for (int o = 1; o < L; o <<= 1) {
+      k.x += __shfl_xor_sync(gmask, k.x, o);
+      k.y += __shfl_xor_sync(gmask, k.y, o);
+    }
+    return k;
+  };
+
   // ---- R points of the tile -------------------------------------------------------
   if (sd.has_r) {
     const int ng = sd.n_g;
-    for (int p = wi.start + tid; p < wi.start + wi.len; p += blockDim.x) {
+    for (int p = wi.start + tid / L; p < wi.start + wi.len; p += pstride) {
       int idx[ND];
       const int kx = sd.r_diag ? p : p / ng;  // diagonal residual layout: point p is (p, p)
       const int ly = sd.r_diag ? p : p - kx * ng;
@@ -212,11 +230,14 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
         for (int d = ND - 1; d >= NM; --d) { idx[d] = r % Md[d]; r /= Md[d]; }
       }
       const C uc = rsrc_at(p);
-      C dg = D[doff[0] + idx[0]];
+      C k = cmk<C>(0.0, 0.0);
+      if (sub == 0) {
+        C dg = D[doff[0] + idx[0]];
 #pragma unroll
-      for (int d = 1; d < ND; ++d) dg = cadd(dg, D[doff[d] + idx[d]]);
-      C k = cmul(dg, uc);
-      for (int t = 0; t < nt; ++t) {
+        for (int d = 1; d < ND; ++d) dg = cadd(dg, D[doff[d] + idx[d]]);
+        k = cmul(dg, uc);
+      }
+      for (int t = sub; t < nt; t += L) {
         const TermDesc& td = st[t];
         if (td.diagp1 && idx[td.diagp1 - 1] != idx[NM + td.diagp1 - 1]) continue;  // projector P
         T wx = (T)1, wy = (T)1;
@@ -236,16 +257,19 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
           k = cfma(sc[t], cmul(cscale(gxs[sx], wx), cscale(gys[sy], wy)), k);
         }
       }
-      if (A.rec) reinterpret_cast<C*>(A.rec)[sd.off_r + p] = uc;
-      combine(sd.off_r + p, uc, k);
+      k = group_sum(k);
+      if (sub == 0) {
+        if (A.rec) reinterpret_cast<C*>(A.rec)[sd.off_r + p] = uc;
+        combine(sd.off_r + p, uc, k);
+      }
     }
   }
 
   // ---- separable part: G_x (left operator + C) and G_y (right operator - C) --------
-  if (sd.has_sep && wi.do_sep) {
+  if (do_sep) {
     const C Cc = cmk<C>(sd.c_re, sd.c_im);
     const int ng = sd.n_g;
-    for (int i = tid; i < 2 * ng; i += blockDim.x) {
+    for (int i = wi.sep_lo + tid / L; i < wi.sep_hi; i += pstride) {
       const int side = i < ng ? SIDE_X : SIDE_Y;
       const int g = side == SIDE_X ? i : i - ng;
       const int d0 = side == SIDE_X ? 0 : NM;
@@ -257,11 +281,14 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
       }
       const C* gs = side == SIDE_X ? gxs : gys;
       const C uc = gs[g];
-      C dg = side == SIDE_X ? Cc : cmk<C>(-sd.c_re, -sd.c_im);
+      C k = cmk<C>(0.0, 0.0);
+      if (sub == 0) {
+        C dg = side == SIDE_X ? Cc : cmk<C>(-sd.c_re, -sd.c_im);
 #pragma unroll
-      for (int d = 0; d < NM; ++d) dg = cadd(dg, D[doff[d0 + d] + idx[d0 + d]]);
-      C k = cmul(dg, uc);
-      for (int t = 0; t < nt; ++t) {
+        for (int d = 0; d < NM; ++d) dg = cadd(dg, D[doff[d0 + d] + idx[d0 + d]]);
+        k = cmul(dg, uc);
+      }
+      for (int t = sub; t < nt; t += L) {
         const TermDesc& td = st[t];
         if (td.side != side) continue;
         T w = (T)1;
@@ -270,8 +297,11 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
         const int src = (w != (T)0) ? g + delta : g;
         k = cfma(sc[t], cscale(gs[src], w), k);
       }
-      if (A.rec) reinterpret_cast<C*>(A.rec)[(side == SIDE_X ? sd.off_gx : sd.off_gy) + g] = uc;
-      combine((side == SIDE_X ? sd.off_gx : sd.off_gy) + g, uc, k);
+      k = group_sum(k);
+      if (sub == 0) {
+        if (A.rec) reinterpret_cast<C*>(A.rec)[(side == SIDE_X ? sd.off_gx : sd.off_gy) + g] = uc;
+        combine((side == SIDE_X ? sd.off_gx : sd.off_gy) + g, uc, k);
+      }
     }
   }
 
@@ -1211,7 +1241,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
   __shared__ int gidx[BQ_MAX_TERMS];
   __shared__ int s_ngt, s_nS;
   __shared__ int sidx[BQ_MAX_TERMS];       // ordinal of an S term
-  __shared__ double2 red[BQ_MAX_GT + 1][BQ_BLOCK / 32];
+  __shared__ double red[BQ_BLOCK / 32][2 * BQ_MAX_GT + 2];  // per-warp sums of the gradient terms
 
   const int tid = threadIdx.x;
   const int stage = A.stage;
@@ -1245,14 +1275,15 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
   C* bgx = bw + wn;
   C* bgy = bgx + sd.n_g;
   C* vw = bgy + sd.n_g;  // [nS][2][n_g] source reductions of this system
-  if (sd.has_sep && wi.do_sep) {
+  const bool do_sep = sd.has_sep && wi.sep_hi > wi.sep_lo;
+  if (do_sep) {
     for (int i = tid; i < sd.n_g; i += blockDim.x) {
       bgx[i] = cscale(bsrc[sd.off_gx + i], bscale);
       bgy[i] = cscale(bsrc[sd.off_gy + i], bscale);
     }
   }
   __syncthreads();
-  if (sd.has_sep && wi.do_sep && sd.has_r) {
+  if (do_sep && sd.has_r) {
     const C* srcr = reinterpret_cast<const C*>(A.srcred) + (int64_t)wi.sys * A.srcred_stride;
     for (int i = tid; i < 2 * s_nS * sd.n_g; i += blockDim.x) vw[i] = srcr[i];
   }
@@ -1303,9 +1334,23 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
     }
   };
 
+  // lanes per point: as in the forward stage kernel, lane `sub` of a group of L takes the
+  // terms t = sub, sub + L, ... and keeps its own gradient partial sums
+  const int L = A.lanes;
+  const int sub = tid & (L - 1);
+  const unsigned gmask = L == 1 ? (1u << (tid & 31)) : (((1u << L) - 1u) << ((tid & 31) & ~(L - 1)));
+  const int pstride = (int)blockDim.x / L;
+  auto group_sum = [&](C k) {
+    for (int o = 1; o < L; o <<= 1) {
+      k.x += __shfl_xor_sync(gmask, k.x, o);
+      k.y += __shfl_xor_sync(gmask, k.y, o);
+    }
+    return k;
+  };
+
   if (sd.has_r) {
     const int ng = sd.n_g;
-    for (int p = wi.start + tid; p < wi.start + wi.len; p += blockDim.x) {
+    for (int p = wi.start + tid / L; p < wi.start + wi.len; p += pstride) {
       int idx[ND];
       const int kx = p / ng;
       const int ly = p - kx * ng;
@@ -1317,12 +1362,15 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
 #pragma unroll
         for (int d = ND - 1; d >= NM; --d) { idx[d] = r % Md[d]; r /= Md[d]; }
       }
-      C dg = D[doff[0] + idx[0]];
+      C q = cmk<C>(0.0, 0.0);
+      if (sub == 0) {
+        C dg = D[doff[0] + idx[0]];
 #pragma unroll
-      for (int d = 1; d < ND; ++d) dg = cadd(dg, D[doff[d] + idx[d]]);
-      C q = cmul(dg, bw[p - wi.win_lo]);
+        for (int d = 1; d < ND; ++d) dg = cadd(dg, D[doff[d] + idx[d]]);
+        q = cmul(dg, bw[p - wi.win_lo]);
+      }
       const C up = U[sd.off_r + p];
-      for (int t = 0; t < nt; ++t) {
+      for (int t = sub; t < nt; t += L) {
         const TermDesc& td = st[t];
         // secular projector term: it shifts x and y alike, so its source p - delta lies on the
         // diagonal of its mode exactly when p does
@@ -1341,13 +1389,14 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
         q = cfma(sc[t], cscale(bv, w), q);
         if (ngt) addg(t, up, bv, w);
       }
-      finish(sd.off_r + p, q);
+      q = group_sum(q);
+      if (sub == 0) finish(sd.off_r + p, q);
     }
   }
-  if (sd.has_sep && wi.do_sep) {
+  if (do_sep) {
     const int ng = sd.n_g;
     const C Cc = cmk<C>(sd.c_re, sd.c_im);
-    for (int i = tid; i < 2 * ng; i += blockDim.x) {
+    for (int i = wi.sep_lo + tid / L; i < wi.sep_hi; i += pstride) {
       const int side = i < ng ? SIDE_X : SIDE_Y;
       const int g = side == SIDE_X ? i : i - ng;
       const int d0 = side == SIDE_X ? 0 : NM;
@@ -1358,17 +1407,18 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
         for (int d = NM - 1; d >= 0; --d) { idx[d0 + d] = r % Md[d]; r /= Md[d]; }
       }
       const C* bs = side == SIDE_X ? bgx : bgy;
-      C dg = side == SIDE_X ? Cc : cmk<C>(-sd.c_re, -sd.c_im);
-#pragma unroll
-      for (int d = 0; d < NM; ++d) dg = cadd(dg, D[doff[d0 + d] + idx[d0 + d]]);
-      C q = cmul(dg, bs[g]);
+      C q = cmk<C>(0.0, 0.0);
       const C up = U[(side == SIDE_X ? sd.off_gx : sd.off_gy) + g];
-      {
+      if (sub == 0) {
+        C dg = side == SIDE_X ? Cc : cmk<C>(-sd.c_re, -sd.c_im);
+#pragma unroll
+        for (int d = 0; d < NM; ++d) dg = cadd(dg, D[doff[d0 + d] + idx[d0 + d]]);
+        q = cmul(dg, bs[g]);
         const C v = cmul(up, bs[g]);
         if (side == SIDE_X) { dcacc.x += (double)v.x; dcacc.y += (double)v.y; }
         else { dcacc.x -= (double)v.x; dcacc.y -= (double)v.y; }
       }
-      for (int t = 0; t < nt; ++t) {
+      for (int t = sub; t < nt; t += L) {
         const TermDesc& td = st[t];
         const bool own = td.side == side;
         const bool src_term = td.side == SIDE_S && sd.has_r;
@@ -1396,29 +1446,48 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
           q = cfma(sc[t], cscale(red_t[src], w), q);
         }
       }
-      finish((side == SIDE_X ? sd.off_gx : sd.off_gy) + g, q);
+      q = group_sum(q);
+      if (sub == 0) finish((side == SIDE_X ? sd.off_gx : sd.off_gy) + g, q);
     }
   }
 
-  // ---- gradient reductions: warp shuffles, then one atomic per term per CTA ----------
-  if (ngt > 0 || (sd.has_sep && wi.do_sep && sd.n_params > 0)) {
+  // ---- gradient reductions: per-warp reduce-scatter, then one atomic per term per CTA --
+  // The 2 BQ_MAX_GT = 32 real partial sums of every lane are reduced across the warp by
+  // halving exchanges (at offset o a lane keeps the half of its values selected by bit o of
+  // its lane index and adds the partner's copy of that half): 31 additions per lane instead
+  // of 5 per value, and afterwards lane j holds the warp's sum of value j.
+  static_assert(2 * BQ_MAX_GT == 32, "the reduce-scatter maps one value to each lane");
+  if (ngt > 0 || (do_sep && sd.n_params > 0)) {
     const int lane = tid & 31, warp = tid >> 5;
-    for (int g = 0; g <= BQ_MAX_GT; ++g) {
-      double2 v = g < BQ_MAX_GT ? gacc[g] : dcacc;
+    double v[32];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    for (int g = 0; g < BQ_MAX_GT; ++g) { v[2 * g] = gacc[g].x; v[2 * g + 1] = gacc[g].y; }
+#pragma unroll
+    for (int lev = 0; lev < 5; ++lev) {
+      const int o = 16 >> lev, h = 16 >> lev;  // h values kept out of 2 h
+      const bool upper = (lane & o) != 0;
+#pragma unroll
+      for (int j = 0; j < h; ++j) {
+        const double send = upper ? v[j] : v[j + h];
+        const double keep = upper ? v[j + h] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
       }
-      if (lane == 0) red[g][warp] = v;
     }
+    red[warp][lane] = v[0];
+    double2 dv = dcacc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dv.x += __shfl_down_sync(0xffffffffu, dv.x, o);
+      dv.y += __shfl_down_sync(0xffffffffu, dv.y, o);
+    }
+    if (lane == 0) { red[warp][32] = dv.x; red[warp][33] = dv.y; }
     __syncthreads();
     if (tid < nt) {
       const int t = tid;
       const int g = gidx[t];
       if (g >= 0) {
         double2 a = make_double2(0.0, 0.0);
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a.x += red[g][w].x; a.y += red[g][w].y; }
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a.x += red[w][2 * g]; a.y += red[w][2 * g + 1]; }
         const TermDesc& td = st[t];
         double2 e = make_double2(1.0, 0.0);
         double t_phys = 0.0;
@@ -1447,9 +1516,9 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
         }
       }
     }
-    if (sd.has_sep && wi.do_sep && tid < sd.n_params) {
+    if (do_sep && tid < sd.n_params) {
       double2 a = make_double2(0.0, 0.0);
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a.x += red[BQ_MAX_GT][w].x; a.y += red[BQ_MAX_GT][w].y; }
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a.x += red[w][32]; a.y += red[w][33]; }
       const double2 dcv = A.dc[sd.dc_off + tid];
       atomicAdd(A.grad + sd.grad_off + tid, dcv.x * a.x - dcv.y * a.y);
     }
@@ -1460,13 +1529,13 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
 //   v_t[kx] = sum_ly b_R[kx, ly] Wy_t(ly) G_y[ly + sy],   w_t[ly] = sum_kx b_R[kx, ly] Wx_t(kx) G_x[kx + sx]
 // (G_x, G_y of the recorded stage input; b_R = dt/6 lam at stage 4).  grid = (systems, max S terms, 2).
 #define BQ_SRC_THREADS 256
-#define BQ_SRC_TILE 32     // outputs per CTA
+#define BQ_SRC_TILE 8      // outputs per CTA (one row per warp; BQ_SRC_THREADS / 8 partial sums per column)
 #define BQ_SRC_ZCH 1024    // summed-index chunk held in shared memory
 template <typename T, int NM>
 __global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
   using C = typename C2T<T>::type;
   __shared__ C z[BQ_SRC_ZCH];
-  __shared__ C red[BQ_SRC_THREADS / 32][BQ_SRC_TILE];
+  __shared__ C red[BQ_SRC_THREADS / BQ_SRC_TILE][BQ_SRC_TILE];
   const SysDesc& sd = A.sys[blockIdx.x];
   if (!sd.has_sep || !sd.has_r) return;
   // the blockIdx.y-th sandwich term of the system
@@ -1532,11 +1601,12 @@ __global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
         }
       }
     } else {
-      // column i0 + lane: warps split j (coalesced across lanes)
-      const int i = i0 + lane;
+      // column i0 + tid % TILE: the CTA's BQ_SRC_THREADS / TILE thread groups split j (each
+      // group reads TILE adjacent columns of one row)
+      const int i = i0 + tid % BQ_SRC_TILE;
       const int mi = midx(i);
       if (i < ng)
-        for (int jj = warp; jj < nj; jj += BQ_SRC_THREADS / 32)
+        for (int jj = tid / BQ_SRC_TILE; jj < nj; jj += BQ_SRC_THREADS / BQ_SRC_TILE)
           if (dm < 0 || midx(jc + jj) == mi) accc = cfma(bsrc[(int64_t)(jc + jj) * ng + i], z[jj], accc);
     }
   }
@@ -1555,12 +1625,12 @@ __global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
       if (lane == 0 && i < ng) out[i] = cscale(v, bscale);
     }
   } else {
-    red[warp][lane] = accc;
+    red[tid / BQ_SRC_TILE][tid % BQ_SRC_TILE] = accc;
     __syncthreads();
-    if (warp == 0) {
-      C v = red[0][lane];
-      for (int w2 = 1; w2 < BQ_SRC_THREADS / 32; ++w2) v = cadd(v, red[w2][lane]);
-      const int i = i0 + lane;
+    if (tid < BQ_SRC_TILE) {
+      C v = red[0][tid];
+      for (int w2 = 1; w2 < BQ_SRC_THREADS / BQ_SRC_TILE; ++w2) v = cadd(v, red[w2][tid]);
+      const int i = i0 + tid;
       if (i < ng) out[i] = cscale(v, bscale);
     }
   }

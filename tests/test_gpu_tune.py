@@ -132,6 +132,7 @@ def test_tile_lengths_compute_the_same_step_and_gradients():
                   ((2, 1), (0, 0)): 0.3, ((0, 0), (2, 1)): 0.3}
     ref = gpu_state(p)
     assert ref.get_tune()["stage_path"] == "tiled" and ref.get_tune()["tile"] == 0
+    assert ref.get_tune()["lanes"] == 4  # a small launch: four lanes per point
     ref.step(p.dt, p.n_steps)
     _sync()
     l0, g0 = gpu_state(p).grad(p.dt, p.n_steps, 6)
@@ -153,11 +154,49 @@ def test_tile_lengths_compute_the_same_step_and_gradients():
     st = gpu_state(p)
     with pytest.raises(bq.BQError):
         st.set_tune(tile=32)
+    with pytest.raises(bq.BQError):
+        st.set_tune(lanes=3)
     tune = st.autotune(p.dt, trial_steps=2)
-    assert tune["tile"] in (0, 64, 96, 128, 192, 256, 384, 512, 1024)
+    assert tune["tile"] in (0, 64, 96, 128, 192, 256, 512) and tune["lanes"] in (1, 2, 4)
     assert tune["n_candidates"] >= 2
     st.step(p.dt, p.n_steps)
     _sync()
     for x, y in zip(st.read_system(0)[1:], ref.read_system(0)[1:]):
         if y is not None:
             assert rel_err(x, y) <= 1e-13
+
+
+@pytest.mark.parametrize("n_modes", [2, 3])
+def test_lanes_per_point_split_the_same_sums(n_modes):
+    """One, two or four lanes per point sum the same terms in different groupings: the step
+    and the adjoint gradients agree to rounding and match the oracle; the separable part runs
+    in work items of its own (several chunks of [G_x | G_y] per split system)."""
+    if n_modes == 2:
+        p = configs.two_mode_control(n_seg=3, T=0.18, steps_per_seg=6, N=7)
+        p.measured = {((1, 0), (0, 1)): 0.7 + 0.2j, ((0, 1), (1, 0)): 0.7 - 0.2j, ((1, 0), (1, 0)): 1.0,
+                      ((2, 1), (0, 0)): 0.3, ((0, 0), (2, 1)): 0.3}
+    else:
+        p = configs.random_problem(11, n_modes=3, N=3, n_steps=12, dt=0.01)
+    run = mapping.rk4_mapped(p)
+    res, grads = {}, {}
+    for lanes in (1, 2, 4):
+        st = gpu_state(p)
+        st.set_tune(lanes=lanes, tile=64)
+        assert st.get_tune()["lanes"] == lanes
+        st.step(p.dt, p.n_steps)
+        _sync()
+        compare_mapped_systems(st, run, 1e-10)
+        res[lanes] = [st.read_system(s) for s in range(st.n_systems())]
+        if n_modes == 2:
+            gs = gpu_state(p)
+            gs.set_tune(lanes=lanes, tile=64)
+            grads[lanes] = gs.grad(p.dt, p.n_steps, 6)
+    for lanes in (2, 4):
+        for a, b in zip(res[lanes], res[1]):
+            for x, y in zip(a[1:], b[1:]):
+                if y is not None:
+                    assert rel_err(x, y) <= 1e-13, lanes
+        if grads:
+            (l1, g1), (l0, g0) = grads[lanes], grads[1]
+            assert abs(l1[0] - l0[0]) <= 1e-13 * max(1.0, abs(l0[0]))
+            assert np.max(np.abs(g1 - g0)) <= 1e-12 * np.max(np.abs(g0)), lanes
