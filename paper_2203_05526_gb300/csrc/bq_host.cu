@@ -853,7 +853,7 @@ static void build_work(const std::vector<SysDesc>& sys, size_t cs, int tile, std
   const int nsys = (int)sys.size();
   for (int i = 0; i < nsys; ++i) {
     const SysDesc& sd = sys[i];
-    const int sep = sd.has_sep ? 2 * sd.n_g : 0;
+    const int sep = (sd.has_sep ? 2 * sd.n_g : 0) + sd.cw_elems;  // G_x, G_y and the forward kernel's tables
     const int adj_sep = sd.has_sep ? (2 + 2 * sd.n_sterms) * sd.n_g : 0;
     const int nsep = sd.has_sep ? 2 * sd.n_g : 0;
     if (!sd.has_r) {
@@ -1208,9 +1208,13 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
 
   // ---- work items (tiles of R; the first tile of a system also updates G_x, G_y) ------
   for (SysDesc& sd : P.sys) {
-    int ns = 0;
-    for (auto& td : P.comp[sd.prob].terms) ns += td.side == bq::SIDE_S;
+    int ns = 0, cw = 0;
+    for (auto& td : P.comp[sd.prob].terms) {
+      ns += td.side == bq::SIDE_S;
+      cw += td.n_act > 0 ? sd.M[td.dim[0] % sd.nm] : 1;
+    }
     sd.n_sterms = ns;
+    sd.cw_elems = cw;
     P.srcred_stride = std::max(P.srcred_stride, (sd.has_sep && sd.has_r) ? 2 * ns * sd.n_g : 0);
     P.max_s = std::max(P.max_s, (sd.has_sep && sd.has_r) ? ns : 0);
   }

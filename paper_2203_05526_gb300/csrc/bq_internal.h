@@ -74,6 +74,7 @@ struct SysDesc {
   int grad_off;         // gradient slot of the problem's first parameter
   int r_diag;           // R stored only at k = l (n_r = n_g entries, index = flat k)
   int n_sterms;         // sandwich terms of the system's problem (adjoint source reductions)
+  int cw_elems;         // complex elements of the tiled kernel's coefficient x weight tables
 };
 
 // A CTA's share of one stage: a tile of R points of one system (plus G_x, G_y if sep).

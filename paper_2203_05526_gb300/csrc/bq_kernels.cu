@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
   __shared__ WorkItem wi;
   __shared__ TermDesc st[BQ_MAX_TERMS];
   __shared__ C sc[BQ_MAX_TERMS];
+  __shared__ int cwoff[BQ_MAX_TERMS];
   __shared__ double s_tau;
 
   const int tid = threadIdx.x;
@@ -125,6 +126,14 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
     st[t] = A.terms[sd.term_off + t];
     const double2 c = term_coef(st[t], A.chans, A.chpar, s_tau, A.dt, A.stage, A.horizon, A.reverse);
     sc[t] = cmk<C>(c.x, c.y);
+  }
+  if (tid == 32) {  // offsets of the coefficient x weight tables (one table per term)
+    int o = 0;
+    for (int t = 0; t < nt; ++t) {
+      const TermDesc& td = A.terms[sd.term_off + t];
+      cwoff[t] = o;
+      o += td.n_act > 0 ? sd.M[td.dim[0] % NM] : 1;
+    }
   }
   // Stage the R window and (for the separable part) G_x, G_y of the stage input.
   const C* uin = reinterpret_cast<const C*>(A.u_in);
@@ -151,6 +160,23 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
   __syncthreads();
 
   const T* W = reinterpret_cast<const T*>(A.wtab);
+  // Coefficient x weight tables: cw_t[i] = c_t(stage) W_t,0[i] over the index of the term's
+  // first active dimension, so that a point's term costs one complex multiply-add (times the
+  // weights of further active dimensions) instead of weight products and a scaling.
+  C* cw = win + wn + (sd.has_sep ? 2 * sd.n_g : 0);
+  {
+    const int nwarp = (int)blockDim.x >> 5, lane = tid & 31;
+    for (int t = tid >> 5; t < nt; t += nwarp) {
+      const TermDesc& td = st[t];
+      if (td.n_act == 0) {
+        if (lane == 0) cw[cwoff[t]] = sc[t];
+      } else {
+        const int len = sd.M[td.dim[0] % NM];
+        for (int i = lane; i < len; i += 32) cw[cwoff[t] + i] = cscale(sc[t], W[td.wtab[0] + i]);
+      }
+    }
+  }
+  __syncthreads();
   const C* D = reinterpret_cast<const C*>(A.diag) + sd.diag_off;
   C* uout = reinterpret_cast<C*>(A.u_out);
   C* y = reinterpret_cast<C*>(A.y);
@@ -240,22 +266,27 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
       for (int t = sub; t < nt; t += L) {
         const TermDesc& td = st[t];
         if (td.diagp1 && idx[td.diagp1 - 1] != idx[NM + td.diagp1 - 1]) continue;  // projector P
-        T wx = (T)1, wy = (T)1;
+        // coefficient x weights; the source is inside the grid exactly when every shifted
+        // index is (else every weight table holds a zero at this point)
+        C c = cw[cwoff[t] + (td.n_act > 0 ? idx[td.dim[0]] : 0)];
+        bool in = true;
         for (int i = 0; i < td.n_act; ++i) {
           const int d = td.dim[i];
-          const T wv = W[td.wtab[i] + idx[d]];
-          if (d < NM) wx *= wv; else wy *= wv;
+          in = in && (unsigned)(idx[d] + td.sh[i]) < (unsigned)Md[d];
+          if (i > 0) c = cscale(c, W[td.wtab[i] + idx[d]]);
         }
-        const T w = wx * wy;
         // diagonal layout: only terms that shift x and y alike have an R source, at deltaGx
         const bool rsrc = !sd.r_diag || td.deltaGx == td.deltaGy;
-        const int src = (w != (T)0 && rsrc) ? p + (sd.r_diag ? td.deltaGx : td.deltaR) : p;
-        if (rsrc) k = cfma(sc[t], cscale(rsrc_at(src), w), k);
+        C v;
         if (td.side == SIDE_S && sd.has_sep) {
-          const int sx = (wx != (T)0) ? kx + td.deltaGx : kx;
-          const int sy = (wy != (T)0) ? ly + td.deltaGy : ly;
-          k = cfma(sc[t], cmul(cscale(gxs[sx], wx), cscale(gys[sy], wy)), k);
+          // c (R[src] + G_x[kx + sx] G_y[ly + sy])
+          v = in ? cmul(gxs[kx + td.deltaGx], gys[ly + td.deltaGy]) : cmk<C>(0.0, 0.0);
+          if (rsrc && in) v = cadd(rsrc_at(p + (sd.r_diag ? td.deltaGx : td.deltaR)), v);
+        } else {
+          if (!rsrc || !in) continue;
+          v = rsrc_at(p + (sd.r_diag ? td.deltaGx : td.deltaR));
         }
+        k = cfma(c, v, k);
       }
       k = group_sum(k);
       if (sub == 0) {
@@ -291,11 +322,15 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
       for (int t = sub; t < nt; t += L) {
         const TermDesc& td = st[t];
         if (td.side != side) continue;
-        T w = (T)1;
-        for (int j = 0; j < td.n_act; ++j) w *= W[td.wtab[j] + idx[td.dim[j]]];
-        const int delta = side == SIDE_X ? td.deltaGx : td.deltaGy;
-        const int src = (w != (T)0) ? g + delta : g;
-        k = cfma(sc[t], cscale(gs[src], w), k);
+        C c = cw[cwoff[t] + (td.n_act > 0 ? idx[td.dim[0]] : 0)];
+        bool in = true;
+        for (int j = 0; j < td.n_act; ++j) {
+          const int d = td.dim[j];
+          in = in && (unsigned)(idx[d] + td.sh[j]) < (unsigned)Md[d];
+          if (j > 0) c = cscale(c, W[td.wtab[j] + idx[d]]);
+        }
+        if (!in) continue;
+        k = cfma(c, gs[g + (side == SIDE_X ? td.deltaGx : td.deltaGy)], k);
       }
       k = group_sum(k);
       if (sub == 0) {
