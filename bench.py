@@ -303,7 +303,7 @@ def grads_leg(n_steps=None, tile=None):
                        "checkpoint every 160, complex FP64",
            "seconds_per_gradient": el, "grads_per_s": 1.0 / el, "loss": float(loss[0]),
            "grad_norm": float(np.linalg.norm(g)), "n_params": int(g.size), "tile": tune["tile"],
-           "lanes": tune["lanes"]}
+           "lanes": tune["lanes"], "gread": tune["gread"]}
     if n_steps is None:
         out["batched"] = grads_batched_leg()
     return out
@@ -344,7 +344,7 @@ def grads_batched_leg(B: int = 16, steps: int = 1280):
                         "checkpoint every 160, complex FP64",
             "batched_grads_per_s": B / tB, "one_instance_per_launch_grads_per_s": B / t1,
             "batched_vs_one_per_launch": t1 / tB, "max_rel_diff_batched_vs_single": worst,
-            "tile_batched": tuneB["tile"], "lanes_batched": tuneB["lanes"]}
+            "tile_batched": tuneB["tile"], "lanes_batched": tuneB["lanes"], "gread_batched": tuneB["gread"]}
 
 
 def methods_leg(B: int = 1024, Ns=(10, 20, 40), steps: int = 100, acc_steps: int = 50000):

@@ -203,6 +203,10 @@ typedef struct bq_tune {
   int lanes;             /* lanes per point of the tiled stage kernel and of the adjoint stage
                           * kernel: 1, 2 or 4 (the terms of a point are split across them);
                           * 0 in bq_set_tune = by the state's size */
+  int gread;             /* BQ_PATH_TILED: 1 = split tiles read R (and the adjoint its cotangent)
+                          * from global memory instead of staging halo windows in shared
+                          * memory; 0 = only where a halo does not fit */
+  int pad;
 } bq_tune;
 
 /* Current schedules of the state (step_us / solve_us: last bq_autotune result, else 0). */

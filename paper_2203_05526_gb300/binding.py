@@ -43,7 +43,8 @@ SOLVE_KERNEL = {-1: None, 0: "program", 1: "merged"}
 class bq_tune(C.Structure):
     _fields_ = [("stage_path", C.c_int), ("pipe_slots", C.c_int), ("pipe_ctas_per_sm", C.c_int),
                 ("solve_kernel", C.c_int), ("solve_ctas_per_sm", C.c_int), ("n_candidates", C.c_int),
-                ("step_us", C.c_double), ("solve_us", C.c_double), ("tile", C.c_int), ("lanes", C.c_int)]
+                ("step_us", C.c_double), ("solve_us", C.c_double), ("tile", C.c_int), ("lanes", C.c_int), ("gread", C.c_int),
+                ("pad", C.c_int)]
 
 
 class BQError(RuntimeError):
@@ -293,7 +294,8 @@ class State:
     def _tune_dict(t: "bq_tune") -> dict:
         return dict(stage_path=PATH[t.stage_path], pipe_slots=t.pipe_slots, pipe_ctas_per_sm=t.pipe_ctas_per_sm,
                     solve_kernel=SOLVE_KERNEL[t.solve_kernel], solve_ctas_per_sm=t.solve_ctas_per_sm,
-                    n_candidates=t.n_candidates, step_us=t.step_us, solve_us=t.solve_us, tile=t.tile, lanes=t.lanes)
+                    n_candidates=t.n_candidates, step_us=t.step_us, solve_us=t.solve_us, tile=t.tile, lanes=t.lanes,
+                    gread=t.gread)
 
     def get_tune(self) -> dict:
         t = bq_tune()

@@ -757,6 +757,7 @@ struct bq_state {
   int r_diag = 0;       // diagonal residual layout
   int has_gread = 0;    // some work item reads its R sources from global memory
   int work_cap = 0, tile = 0;  // work-item capacity of the pool; tiled schedule (0 = default)
+  int gread_sched = 0;         // split tiles read R from global memory (schedule)
   int lanes = 1;               // lanes per point of the tiled forward and the adjoint stage kernels
   int ng_max = 0;      // largest G_x / G_y point count over the systems
   // schedules (bq_get_tune / bq_set_tune / bq_autotune)
@@ -832,7 +833,8 @@ struct Plan {
 // are split into tiles of R with halo windows (or, when the halo does not fit beside a tile,
 // tiles that read R from global memory) and items that update chunks of [G_x | G_y].
 // tile > 0 sets the length of the split tiles (a schedule); 0 = enough tiles for two CTAs
-// per SM.  smem_max / adj_max: complex elements of shared memory of the forward and the
+// per SM.  force_gread: split tiles read R from global memory (L1 / L2) instead of staging a
+// halo window (a schedule: less shared memory per CTA, no staging phase).  smem_max / adj_max: complex elements of shared memory of the forward and the
 // adjoint stage kernel.
 #define BQ_SEP_CHUNK 64
 
@@ -845,8 +847,8 @@ static int default_lanes(const std::vector<SysDesc>& sys) {
   const int64_t half = 152 * 16 * 32;
   return pts >= half ? 1 : (pts >= half / 2 ? 2 : 4);
 }
-static void build_work(const std::vector<SysDesc>& sys, size_t cs, int tile, std::vector<WorkItem>& work,
-                       int& smem_max, int& adj_max) {
+static void build_work(const std::vector<SysDesc>& sys, size_t cs, int tile, int force_gread,
+                       std::vector<WorkItem>& work, int& smem_max, int& adj_max) {
   const int budget = (int)(96 * 1024 / cs);
   work.clear();
   smem_max = adj_max = 0;
@@ -870,7 +872,8 @@ static void build_work(const std::vector<SysDesc>& sys, size_t cs, int tile, std
       continue;
     }
     int tl = budget - sep - sd.halo_lo - sd.halo_hi;
-    const int gread = tl < 64 ? 1 : 0;  // the halo does not fit next to a tile: read R from global memory
+    // the halo does not fit next to a tile (or the schedule asks for it): read R from global memory
+    const int gread = (tl < 64 || force_gread) ? 1 : 0;
     if (gread) tl = 1 << 30;
     if (tile > 0) {
       tl = gread ? tile : std::min(tl, tile);
@@ -1220,13 +1223,13 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
   }
   if (!P.use_m1) {
     int smem_max = 0, adj_max = 0;
-    build_work(P.sys, cs, 0, P.work, smem_max, adj_max);
+    build_work(P.sys, cs, 0, 0, P.work, smem_max, adj_max);
     P.smem_bytes = (int)(smem_max * cs);
     P.adj_smem = (int)(adj_max * cs);
     // capacity for the smallest tile the schedules may choose
     std::vector<WorkItem> w64;
     int s64 = 0, a64 = 0;
-    build_work(P.sys, cs, 64, w64, s64, a64);
+    build_work(P.sys, cs, 64, 0, w64, s64, a64);
     P.work_cap = std::max(P.work.size(), w64.size());
   } else {  // one-CTA-per-system items (whole system as the window) for the adjoint kernel
     size_t adj_max = 0;
@@ -1678,14 +1681,15 @@ static void drop_graph(bq_state* s) {
   if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
 }
 
-// Rewrites the tiled kernel's work items for tile length `tile` (0 = default).
-static int apply_tile(bq_state* s, int tile) {
+// Rewrites the tiled kernel's work items for tile length `tile` (0 = default) and global-read
+// tiles on request.
+static int apply_tile(bq_state* s, int tile, int gread) {
   if (s->use_m1) return fail(BQ_EUNSUPPORTED, "single-mode states have no tiled work items");
   if (tile != 0 && tile < 64) return fail(BQ_EINVAL, "tile must be 0 or >= 64");
   const size_t cs = s->dtype == BQ_F64 ? 16 : 8;
   std::vector<WorkItem> work;
   int smem = 0, adj = 0;
-  build_work(s->sys, cs, tile, work, smem, adj);
+  build_work(s->sys, cs, tile, gread, work, smem, adj);
   if ((int)work.size() > s->work_cap) return fail(BQ_EUNSUPPORTED, "tile %d needs %zu work items > %d", tile, work.size(), s->work_cap);
   if ((size_t)smem * cs > BQ_MAX_DYN_SMEM || (size_t)adj * cs > BQ_MAX_DYN_SMEM)
     return fail(BQ_EUNSUPPORTED, "tile %d needs more shared memory than a CTA has", tile);
@@ -1694,6 +1698,7 @@ static int apply_tile(bq_state* s, int tile) {
   s->smem_bytes = (int)(smem * cs);
   s->adj_smem = (int)(adj * cs);
   s->tile = tile;
+  s->gread_sched = gread;
   int g = 0;
   for (const WorkItem& w : work) g = g || w.gread;
   s->has_gread = g;
@@ -1715,6 +1720,7 @@ extern "C" int bq_get_tune(const bq_state* s, bq_tune* out) {
   out->solve_us = s->tune_solve_us;
   out->tile = s->tile;
   out->lanes = s->lanes;
+  out->gread = s->gread_sched;
   return BQ_OK;
 }
 
@@ -1737,8 +1743,8 @@ extern "C" int bq_set_tune(bq_state* s, const bq_tune* t) {
       break;
     case BQ_PATH_TILED: {
       if (s->use_m1) return fail(BQ_EUNSUPPORTED, "single-mode states have no tiled work items");
-      if (t->tile != s->tile) {
-        const int rc = apply_tile(s, t->tile);
+      if (t->tile != s->tile || (t->gread != 0) != (s->gread_sched != 0)) {
+        const int rc = apply_tile(s, t->tile, t->gread != 0);
         if (rc != BQ_OK) return rc;
       }
       break;
@@ -1822,7 +1828,7 @@ extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratc
   bq_get_tune(s, &best);
   double best_step = 1e300;
   {
-    struct Cand { int path, slots, cap, lanes; };
+    struct Cand { int path, slots, cap, lanes, gread; };
     std::vector<Cand> cands;
     if (s->pipe_ok) {
       for (int slots = 2; slots <= 4; ++slots) {
@@ -1832,15 +1838,18 @@ extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratc
         CUDA_TRY(cudaGetDevice(&dev));
         CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         const int per_sm = (s->pipe_grid[1] + nsm - 1) / nsm;
-        cands.push_back({BQ_PATH_PIPE, slots, 0, 1});
-        if (per_sm > 2 && s->n_sys > per_sm * nsm) cands.push_back({BQ_PATH_PIPE, slots, per_sm - 1, 1});
+        cands.push_back({BQ_PATH_PIPE, slots, 0, 1, 0});
+        if (per_sm > 2 && s->n_sys > per_sm * nsm) cands.push_back({BQ_PATH_PIPE, slots, per_sm - 1, 1, 0});
       }
     }
     if (s->use_m1) {
-      cands.push_back({BQ_PATH_SYSTEM, 0, 0, 1});
-    } else {  // tile lengths (the cap field carries the tile; 0 = default) x lanes per point
+      cands.push_back({BQ_PATH_SYSTEM, 0, 0, 1, 0});
+    } else {  // tile lengths (the cap field carries the tile; 0 = default) x lanes per point,
+              // with halo windows and with global reads
       for (int tl : {0, 64, 96, 128, 192, 256, 512})
-        for (int ln : {1, 2, 4}) cands.push_back({BQ_PATH_TILED, 0, tl, ln});
+        for (int ln : {1, 2, 4}) cands.push_back({BQ_PATH_TILED, 0, tl, ln, 0});
+      for (int tl : {64, 128, 256, 512})
+        for (int ln : {1, 2, 4}) cands.push_back({BQ_PATH_TILED, 0, tl, ln, 1});
     }
     const int lanes0 = s->lanes;
     for (const Cand& c : cands) {
@@ -1848,7 +1857,10 @@ extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratc
         if ((rc = pipe_configure(s, c.slots, c.cap)) != BQ_OK) break;
         s->use_pipe = 1;
       } else if (c.path == BQ_PATH_TILED) {
-        if (c.cap != s->tile && apply_tile(s, c.cap) != BQ_OK) { g_err.clear(); continue; }  // a tile that does not fit
+        if ((c.cap != s->tile || c.gread != s->gread_sched) && apply_tile(s, c.cap, c.gread) != BQ_OK) {
+          g_err.clear();  // a tile that does not fit
+          continue;
+        }
         s->lanes = c.lanes;
       } else {
         s->use_pipe = 0;
@@ -1863,6 +1875,7 @@ extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratc
         best.pipe_ctas_per_sm = c.path == BQ_PATH_PIPE ? c.cap : 0;
         best.tile = c.path == BQ_PATH_TILED ? c.cap : s->tile;
         best.lanes = c.path == BQ_PATH_TILED ? c.lanes : lanes0;
+        best.gread = c.path == BQ_PATH_TILED ? c.gread : s->gread_sched;
       }
     }
     s->lanes = lanes0;
@@ -1972,8 +1985,6 @@ static int set_tau(bq_state* s, double tau, cudaStream_t st) {
 extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_every, void* work, size_t work_bytes,
                        double* loss_out, double* grad_out, void* stream) {
   if (s && s->r_diag) return fail(BQ_EUNSUPPORTED, "gradients with the diagonal residual layout are not implemented");
-  if (s && s->has_gread)
-    return fail(BQ_EUNSUPPORTED, "gradients of systems whose stencil halo exceeds a shared-memory tile are not implemented");
   if (!s || !work || !loss_out || !grad_out) return fail(BQ_EINVAL, "NULL argument");
   if (n_steps < 1 || checkpoint_every < 1 || !(dt > 0.0)) return fail(BQ_EINVAL, "bad step arguments");
   if (dt > s->dt_max * (1.0 + 1e-12)) return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 bound %g", dt, s->dt_max);

@@ -1305,8 +1305,12 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
   const T bscale = stage == 4 ? dt * (T)(1.0 / 6.0) : (T)1;
   const C* bsrc = reinterpret_cast<const C*>(stage == 4 ? A.lam : A.b_in);
   const int wn = wi.win_hi - wi.win_lo;
-  if (sd.has_r)
+  if (sd.has_r && !wi.gread)
     for (int i = tid; i < wn; i += blockDim.x) bw[i] = cscale(bsrc[sd.off_r + wi.win_lo + i], bscale);
+  // b_R at flat index i of the system: the staged window, or global memory (scaled on the
+  // fly) for tiles without a window
+  const C* brg = bsrc + (sd.has_r ? sd.off_r : 0);
+  auto b_at = [&](int i) { return wi.gread ? cscale(brg[i], bscale) : bw[i - wi.win_lo]; };
   C* bgx = bw + wn;
   C* bgy = bgx + sd.n_g;
   C* vw = bgy + sd.n_g;  // [nS][2][n_g] source reductions of this system
@@ -1402,7 +1406,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
         C dg = D[doff[0] + idx[0]];
 #pragma unroll
         for (int d = 1; d < ND; ++d) dg = cadd(dg, D[doff[d] + idx[d]]);
-        q = cmul(dg, bw[p - wi.win_lo]);
+        q = cmul(dg, b_at(p));
       }
       const C up = U[sd.off_r + p];
       for (int t = sub; t < nt; t += L) {
@@ -1420,7 +1424,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
         }
         if (!ok) w = (T)0;
         const int src = (w != (T)0) ? p - td.deltaR : p;
-        const C bv = bw[src - wi.win_lo];
+        const C bv = b_at(src);
         q = cfma(sc[t], cscale(bv, w), q);
         if (ngt) addg(t, up, bv, w);
       }

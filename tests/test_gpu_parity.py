@@ -193,5 +193,25 @@ def test_three_modes_with_halo_beyond_shared_memory():
     m.step(p.dt, p.n_steps)
     _sync()
     compare_mapped_systems(m, mapping.rk4_mapped(p), TOL64)
-    with pytest.raises(bq.BQError):
-        d.grad(p.dt, 4, 2)
+
+
+def test_three_modes_global_read_gradients_match_oracle_adjoint():
+    """Adjoint gradients of a three-mode network whose halo (5^5 points) exceeds a
+    shared-memory tile, so the forward and adjoint stage kernels read R and its cotangent from
+    global memory: loss and dl/dJ (the exchange coupling as a parameter) against the oracle's
+    discrete adjoint."""
+    from oracle import grad as ograd
+    from workloads.spec import HTerm
+    p = configs.table_one_network(3, 5, steps=4000)
+    J = configs.TABLE_ONE["J"]
+    h = [HTerm(1.0 + 0j, t.u, t.v, param=0) if (t.coef == J and t.u != t.v and sum(t.u) == 1 and sum(t.v) == 1)
+         else t for t in p.h_terms]
+    p = Problem(**{**p.__dict__, "h_terms": h, "params": [J], "T": 12 * p.dt,
+                   "rho0": {((0, 1, 1), (1, 0, 1)): 0.4, ((1, 0, 1), (0, 1, 1)): 0.4,
+                            ((1, 0, 1), (1, 0, 1)): 0.5, ((0, 1, 1), (0, 1, 1)): 0.5},
+                   "measured": {((1, 0, 1), (0, 1, 1)): 1.0 + 0.3j, ((0, 1, 1), (1, 0, 1)): 1.0 - 0.3j}})
+    loss_o, gt, _ = ograd.loss_and_grad(p, checkpoint_every=4)
+    st = gpu_state(p)
+    loss, g = st.grad(p.dt, p.n_steps, 4)
+    assert abs(loss[0] - loss_o) <= 1e-12 * max(1.0, abs(loss_o))
+    assert abs(g[0] - gt[0]) <= 1e-10 * abs(gt[0]), (g, gt)

@@ -124,9 +124,10 @@ def test_unavailable_schedules_are_refused():
 
 
 def test_tile_lengths_compute_the_same_step_and_gradients():
-    """The tiled kernel evaluates every point from the same sources whatever the tile length
-    (shared-memory halo or global reads): the step and the adjoint gradients agree with the
-    default tiling to rounding, and the autotuner keeps a tile from its candidate list."""
+    """The tiled kernels evaluate every point from the same sources whatever the tile length
+    and wherever the sources come from (shared-memory halo windows or global reads): the step
+    and the adjoint gradients agree with the default tiling to rounding, and the autotuner
+    keeps a tile from its candidate list."""
     p = configs.two_mode_control(n_seg=3, T=0.18, steps_per_seg=6, N=7)
     p.measured = {((1, 0), (0, 1)): 0.7 + 0.2j, ((0, 1), (1, 0)): 0.7 - 0.2j, ((1, 0), (1, 0)): 1.0,
                   ((2, 1), (0, 0)): 0.3, ((0, 0), (2, 1)): 0.3}
@@ -136,10 +137,10 @@ def test_tile_lengths_compute_the_same_step_and_gradients():
     ref.step(p.dt, p.n_steps)
     _sync()
     l0, g0 = gpu_state(p).grad(p.dt, p.n_steps, 6)
-    for tile in (64, 96, 192, 1024):
+    for tile, gread in ((64, 0), (96, 0), (192, 0), (1024, 0), (64, 1), (256, 1)):
         st = gpu_state(p)
-        st.set_tune(tile=tile)
-        assert st.get_tune()["tile"] == tile
+        st.set_tune(tile=tile, gread=gread)
+        assert st.get_tune()["tile"] == tile and st.get_tune()["gread"] == gread
         st.step(p.dt, p.n_steps)
         _sync()
         for s in range(ref.n_systems()):
@@ -147,7 +148,7 @@ def test_tile_lengths_compute_the_same_step_and_gradients():
                 if y is not None:
                     assert rel_err(x, y) <= 1e-13, (tile, s)
         gs = gpu_state(p)
-        gs.set_tune(tile=tile)
+        gs.set_tune(tile=tile, gread=gread)
         l1, g1 = gs.grad(p.dt, p.n_steps, 6)
         assert abs(l1[0] - l0[0]) <= 1e-13 * max(1.0, abs(l0[0]))
         assert np.max(np.abs(g1 - g0)) <= 1e-12 * np.max(np.abs(g0)), tile
