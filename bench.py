@@ -64,8 +64,8 @@ def parse():
     ap.add_argument("--only-grad", action="store_true",
                     help="profiling aid: only the adjoint gradient of the control problem for --grad-steps steps")
     ap.add_argument("--grad-steps", type=int, default=None)
-    ap.add_argument("--grad-tile", type=int, default=None,
-                    help="profiling aid: tile length of the gradient leg's state instead of the autotuned one")
+    ap.add_argument("--grad-tune", default=None, metavar="TILE,LANES,GREAD",
+                    help="profiling aid: tiled schedule of the gradient leg's state instead of the autotuned one")
     ap.add_argument("--no-autotune", action="store_true",
                     help="profiling aid: keep the default schedule of the timed state (no tuning launches)")
     ap.add_argument("--n-range", type=int, nargs=2, default=(10, 40), metavar=("LO", "HI"),
@@ -277,7 +277,7 @@ def batched_leg(world: int):
     return out
 
 
-def grads_leg(n_steps=None, tile=None):
+def grads_leg(n_steps=None, sched=None):
     """Gradient of P(|1,0>) at T = 200 ns for the two-mode control problem (64 complex
     piecewise-constant drive segments, K_1, K_2, g: 131 real parameters; 20 480 RK4 steps,
     complex FP64, checkpoint every 160 steps) by the discrete adjoint kernels (bq_grad)."""
@@ -288,10 +288,10 @@ def grads_leg(n_steps=None, tile=None):
     from workloads import configs
     p = configs.two_mode_control()
     st = bq.State([bq.problem_from_spec(p)], bq.map_opts(dtype="f64", horizon=p.T, dt=p.dt))
-    if tile is None:
-        tune = st.autotune(p.dt, trial_steps=16)  # tile length of the tiled kernels
+    if sched is None:
+        tune = st.autotune(p.dt, trial_steps=16)  # tile length, lanes and reads of the tiled kernels
     else:
-        st.set_tune(tile=tile)
+        st.set_tune(tile=sched[0], lanes=sched[1], gread=sched[2])
         tune = st.get_tune()
     st.grad(p.dt, 320, 160)  # warm-up (modules, workspace)
     torch.cuda.synchronize()
@@ -541,7 +541,8 @@ def main():
     from paper_2203_05526_gb300 import build
     build.build()
     if args.only_grad:
-        print(json.dumps({"only_grad": True, **grads_leg(args.grad_steps, args.grad_tile)}))
+        sched = None if args.grad_tune is None else [int(v) for v in args.grad_tune.split(",")]
+        print(json.dumps({"only_grad": True, **grads_leg(args.grad_steps, sched)}))
         return
     if args.only_solve:
         specs = configs_batch(args.instances)

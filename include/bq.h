@@ -199,7 +199,7 @@ typedef struct bq_tune {
   double step_us;        /* bq_autotune: device time of one RK4 step with bq_step's schedule */
   double solve_us;       /* bq_autotune: device time per RK4 step with bq_solve's schedule */
   int tile;              /* BQ_PATH_TILED: points per tile of a split system (0 = enough tiles
-                          * for two CTAs per SM; >= 64); also the adjoint's tiles */
+                          * for two CTAs per SM; >= 32); also the adjoint's tiles */
   int lanes;             /* lanes per point of the tiled stage kernel and of the adjoint stage
                           * kernel: 1, 2 or 4 (the terms of a point are split across them);
                           * 0 in bq_set_tune = by the state's size */

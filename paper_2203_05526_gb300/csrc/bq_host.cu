@@ -812,7 +812,7 @@ struct Plan {
   int pipe_slot[3] = {0, 0, 0};
   std::vector<unsigned char> pparams;
   std::vector<bq::PipeRec> precs;
-  size_t work_cap = 0;  // work-item capacity of the pool (the smallest schedulable tile)
+  size_t work_cap = 0;  // work-item capacity of the pool (the smallest schedulable tile, 32 points)
   std::vector<cplx> pcoef;           // stage coefficients that do not depend on time (n_sys x BQ_PIPE_COEF)
   std::vector<bq::CoefDyn> pcdyn;    // and the entries that do
   int solve_smem = 0;
@@ -1227,10 +1227,10 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
     P.smem_bytes = (int)(smem_max * cs);
     P.adj_smem = (int)(adj_max * cs);
     // capacity for the smallest tile the schedules may choose
-    std::vector<WorkItem> w64;
-    int s64 = 0, a64 = 0;
-    build_work(P.sys, cs, 64, 0, w64, s64, a64);
-    P.work_cap = std::max(P.work.size(), w64.size());
+    std::vector<WorkItem> wmin;
+    int smin = 0, amin = 0;
+    build_work(P.sys, cs, 32, 0, wmin, smin, amin);
+    P.work_cap = std::max(P.work.size(), wmin.size());
   } else {  // one-CTA-per-system items (whole system as the window) for the adjoint kernel
     size_t adj_max = 0;
     for (auto& w : P.work) {
@@ -1685,7 +1685,7 @@ static void drop_graph(bq_state* s) {
 // tiles on request.
 static int apply_tile(bq_state* s, int tile, int gread) {
   if (s->use_m1) return fail(BQ_EUNSUPPORTED, "single-mode states have no tiled work items");
-  if (tile != 0 && tile < 64) return fail(BQ_EINVAL, "tile must be 0 or >= 64");
+  if (tile != 0 && tile < 32) return fail(BQ_EINVAL, "tile must be 0 or >= 32");
   const size_t cs = s->dtype == BQ_F64 ? 16 : 8;
   std::vector<WorkItem> work;
   int smem = 0, adj = 0;
@@ -1848,7 +1848,7 @@ extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratc
               // with halo windows and with global reads
       for (int tl : {0, 64, 96, 128, 192, 256, 512})
         for (int ln : {1, 2, 4}) cands.push_back({BQ_PATH_TILED, 0, tl, ln, 0});
-      for (int tl : {64, 128, 256, 512})
+      for (int tl : {32, 64, 128, 256, 512})
         for (int ln : {1, 2, 4}) cands.push_back({BQ_PATH_TILED, 0, tl, ln, 1});
     }
     const int lanes0 = s->lanes;

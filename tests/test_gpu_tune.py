@@ -137,7 +137,7 @@ def test_tile_lengths_compute_the_same_step_and_gradients():
     ref.step(p.dt, p.n_steps)
     _sync()
     l0, g0 = gpu_state(p).grad(p.dt, p.n_steps, 6)
-    for tile, gread in ((64, 0), (96, 0), (192, 0), (1024, 0), (64, 1), (256, 1)):
+    for tile, gread in ((32, 0), (96, 0), (192, 0), (1024, 0), (32, 1), (256, 1)):
         st = gpu_state(p)
         st.set_tune(tile=tile, gread=gread)
         assert st.get_tune()["tile"] == tile and st.get_tune()["gread"] == gread
@@ -154,11 +154,11 @@ def test_tile_lengths_compute_the_same_step_and_gradients():
         assert np.max(np.abs(g1 - g0)) <= 1e-12 * np.max(np.abs(g0)), tile
     st = gpu_state(p)
     with pytest.raises(bq.BQError):
-        st.set_tune(tile=32)
+        st.set_tune(tile=16)
     with pytest.raises(bq.BQError):
         st.set_tune(lanes=3)
     tune = st.autotune(p.dt, trial_steps=2)
-    assert tune["tile"] in (0, 64, 96, 128, 192, 256, 512) and tune["lanes"] in (1, 2, 4)
+    assert tune["tile"] in (0, 32, 64, 96, 128, 192, 256, 512) and tune["lanes"] in (1, 2, 4)
     assert tune["n_candidates"] >= 2
     st.step(p.dt, p.n_steps)
     _sync()
