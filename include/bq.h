@@ -241,8 +241,8 @@ int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratch, size_t s
 int bq_grad_size(const bq_state* s, int* n);
 
 /* Device bytes of the gradient workspace for n_steps steps checkpointed every
- * checkpoint_every steps: ceil(n/k) checkpoints of the state and 4 k recorded stage inputs,
- * plus four cotangent arrays. */
+ * checkpoint_every steps: ceil(n/k) checkpoints of the state and 2 x 4 k recorded stage
+ * inputs (two segments), plus four cotangent arrays. */
 int bq_grad_required_bytes(const bq_state* s, int64_t n_steps, int checkpoint_every, size_t* out);
 
 /* Loss l_b = Re Tr(rho0_b A_b(tau0 + n_steps dt)) of every problem (loss_out[B]) and the
@@ -250,7 +250,9 @@ int bq_grad_required_bytes(const bq_state* s, int64_t n_steps, int checkpoint_ev
  * piecewise-constant segment value, by the exact discrete adjoint of the RK4 solve: a forward
  * pass storing the state every checkpoint_every steps, then, segment by segment in reverse, a
  * recomputation recording the RK4 stage inputs and four adjoint stage kernels per step
- * (transposed stencils, transposed separable source, per-term gradient reductions).  The
+ * (transposed stencils, transposed separable source, per-term gradient reductions); the
+ * recomputation of a segment runs on an internal stream concurrently with the adjoint of the
+ * following segment on another, both ordered after the work already on `stream`.  The
  * separation constant's dependence on the parameters (Eq. 304) is included.  The state is left
  * as it was (content and tau).  work: caller-owned device buffer, 256-byte aligned.
  * Synchronises stream. */

@@ -783,6 +783,7 @@ struct bq_state {
   // tau control (host mirror) and graph cache
   double tau_base_host = 0.0;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t grad_stream[2] = {nullptr, nullptr};  // bq_grad: segment recomputation, backward sweep
   cudaGraphExec_t graph = nullptr;
   double graph_dt = 0.0;
   int graph_steps = 0;
@@ -1446,6 +1447,8 @@ extern "C" void bq_state_destroy(bq_state* s) {
   if (!s) return;
   if (s->graph) cudaGraphExecDestroy(s->graph);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  for (cudaStream_t& gs : s->grad_stream)
+    if (gs) cudaStreamDestroy(gs);
   delete s;
 }
 
@@ -1938,7 +1941,7 @@ static GradLayout grad_layout(const bq_state* s, int64_t n_steps, int k) {
   auto seg = [&](size_t bytes) { size_t r = o; o = align_up(o + std::max<size_t>(bytes, 1)); return r; };
   g.n_ckpt = (n_steps + k - 1) / k;
   g.ckpt = seg(2 * arr * (size_t)g.n_ckpt);
-  g.rec = seg(4 * arr * (size_t)k);
+  g.rec = seg(2 * 4 * arr * (size_t)k);  // two segments' stage inputs (recompute overlaps the backward sweep)
   g.lam = seg(arr);
   g.lacc = seg(arr);
   g.ba = seg(arr);
@@ -2021,6 +2024,23 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
                                s->dtype, st));
   g_launches++;
   // ---- backward sweep ----------------------------------------------------------------------
+  // Segment c is recomputed from its checkpoint (recording every stage input into buffer
+  // c % 2) on one stream while the adjoint of segment c + 1 runs on another: the two chains
+  // are independent until the adjoint of c needs the recording of c, and the recomputation of
+  // c - 1 reuses the buffer of c + 1 only after that segment's adjoint has finished.
+  for (cudaStream_t& gs : s->grad_stream)
+    if (!gs) CUDA_TRY(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+  cudaStream_t sF = s->grad_stream[0], sB = s->grad_stream[1];
+  cudaEvent_t ev[6] = {};  // start, recorded[2], adjoint done[2], end
+  for (cudaEvent_t& e : ev) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() { for (int i = 0; i < 6; ++i) if (e[i]) cudaEventDestroy(e[i]); }
+  } ev_guard{ev};
+  CUDA_TRY(cudaEventRecord(ev[0], st));
+  CUDA_TRY(cudaStreamWaitEvent(sF, ev[0], 0));
+  CUDA_TRY(cudaStreamWaitEvent(sB, ev[0], 0));
+  const size_t rec_bytes = 4 * arr * (size_t)k;
   char* lam = w + G.lam;
   char* lacc = w + G.lacc;
   bq::AdjArgs a;
@@ -2043,27 +2063,38 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
   a.lanes = s->lanes;
   for (int64_t c = G.n_ckpt - 1; c >= 0; --c) {
     const int64_t n0 = c * k, n1 = std::min<int64_t>(n_steps, n0 + k);
+    const int buf = (int)(c & 1);
+    char* rec = w + G.rec + (size_t)buf * rec_bytes;
     // recompute the segment from its checkpoint, recording every stage input
-    CUDA_TRY(cudaMemcpyAsync(b + L.off_y, w + G.ckpt + (2 * c) * arr, arr, cudaMemcpyDeviceToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(b + L.off_comp, w + G.ckpt + (2 * c + 1) * arr, arr, cudaMemcpyDeviceToDevice, st));
-    r = set_tau(s, tau0 + (double)n0 * dt, st);
+    if (c + 2 < G.n_ckpt) CUDA_TRY(cudaStreamWaitEvent(sF, ev[3 + buf], 0));  // adjoint of c + 2 is done with the buffer
+    CUDA_TRY(cudaMemcpyAsync(b + L.off_y, w + G.ckpt + (2 * c) * arr, arr, cudaMemcpyDeviceToDevice, sF));
+    CUDA_TRY(cudaMemcpyAsync(b + L.off_comp, w + G.ckpt + (2 * c + 1) * arr, arr, cudaMemcpyDeviceToDevice, sF));
+    r = set_tau(s, tau0 + (double)n0 * dt, sF);
     if (r != BQ_OK) return r;
-    CUDA_TRY(enqueue_steps_rec(s, dt, n1 - n0, st, w + G.rec, arr));
+    CUDA_TRY(enqueue_steps_rec(s, dt, n1 - n0, sF, rec, arr));
+    CUDA_TRY(cudaEventRecord(ev[1 + buf], sF));
+    CUDA_TRY(cudaStreamWaitEvent(sB, ev[1 + buf], 0));
     for (int64_t n = n1 - 1; n >= n0; --n) {
       a.tau_step = tau0 + (double)n * dt;
       a.lam = lam;
       a.lacc = lacc;
       for (int stage = 4; stage >= 1; --stage) {
         a.stage = stage;
-        a.u = w + G.rec + ((size_t)(n - n0) * 4 + stage - 1) * arr;
+        a.u = rec + ((size_t)(n - n0) * 4 + stage - 1) * arr;
         a.b_in = stage == 4 ? nullptr : (stage == 3 ? (void*)(w + G.ba) : (stage == 2 ? (void*)(w + G.bb) : (void*)(w + G.ba)));
         a.b_out = stage == 4 ? (void*)(w + G.ba) : (stage == 3 ? (void*)(w + G.bb) : (stage == 2 ? (void*)(w + G.ba) : nullptr));
-        CUDA_TRY(bq::launch_adjoint(a, s->dtype, s->nm, s->n_work, s->adj_smem, s->n_sys, s->max_s, st));
+        CUDA_TRY(bq::launch_adjoint(a, s->dtype, s->nm, s->n_work, s->adj_smem, s->n_sys, s->max_s, sB));
         g_launches += s->max_s > 0 ? 2 : 1;
       }
       std::swap(lam, lacc);
     }
+    CUDA_TRY(cudaEventRecord(ev[3 + buf], sB));
   }
+  // join both streams into the caller's
+  CUDA_TRY(cudaEventRecord(ev[5], sB));
+  CUDA_TRY(cudaStreamWaitEvent(st, ev[5], 0));
+  CUDA_TRY(cudaEventRecord(ev[1], sF));
+  CUDA_TRY(cudaStreamWaitEvent(st, ev[1], 0));
   // leave the state as it was before the call (initial content, tau0)
   CUDA_TRY(cudaMemcpyAsync(b + L.off_y, w + G.ckpt, arr, cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(b + L.off_comp, w + G.ckpt + arr, arr, cudaMemcpyDeviceToDevice, st));
