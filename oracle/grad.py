@@ -20,9 +20,15 @@ with <.,.> the bilinear (unconjugated) pairing: the system is complex-linear in 
 J^T of the bilinear source S(G_x G_y) contributes to G_x and G_y.  Forward states are
 checkpointed every ``checkpoint_every`` steps and each segment is recomputed once.
 
+Diagonal residual layout (``r_layout="diag"``, the R(xy) reading of oracle.mapping): the R
+equation is projected onto its diagonal k = l, dR = D(f_R), and R stays diagonal.  D is
+symmetric under the bilinear pairing, so J^T acts on D(b_R) and its R component is projected
+again; the cotangent of the final R is D(dl/dG).
+
 Parity status: pinned by central finite differences of oracle.mapping.rk4_mapped
 (tests/test_oracle_grad.py), with conventional jump operators and with the secular
-dissipator (one and two modes, finite temperature).
+dissipator (one and two modes, finite temperature), in the full and the diagonal residual
+layouts.
 """
 
 from __future__ import annotations
@@ -91,8 +97,14 @@ class _Derivs:
         return out
 
 
-def loss_and_grad(problem: Problem, M: Optional[Sequence[int]] = None, checkpoint_every: int = 64):
-    """Returns (loss, dl/dtheta (len P), {channel: dl/d(Re, Im) of each segment (n_seg, 2)})."""
+def loss_and_grad(problem: Problem, M: Optional[Sequence[int]] = None, checkpoint_every: int = 64,
+                  r_layout: str = "full"):
+    """Returns (loss, dl/dtheta (len P), {channel: dl/d(Re, Im) of each segment (n_seg, 2)}).
+    r_layout: "full" (Eq. 303c) or "diag" (R kept on k = l, as in oracle.mapping)."""
+    if r_layout not in ("full", "diag"):
+        raise ValueError(f"r_layout {r_layout!r}")
+    diag = r_layout == "diag"
+    proj = (lambda X: np.diag(np.diag(X))) if diag else (lambda X: X)
     model = MappedModel(problem, M)
     M = model.M
     der = _Derivs(problem, model)
@@ -113,11 +125,12 @@ def loss_and_grad(problem: Problem, M: Optional[Sequence[int]] = None, checkpoin
         return model.operators(tau, c, dt)
 
     def f(z, O, C):
-        return model.rhs(z[0], z[1], z[2], O[0], O[1], C, "full")
+        return model.rhs(z[0], z[1], z[2], O[0], O[1], C, r_layout)
 
     def JT(b, u, O, C):
         """Transpose of df/dz at u applied to b = (b_gx, b_gy, b_R)."""
         bx, by, bR = b
+        bR = proj(bR)
         Ox, Oy = O
         qx = Ox.T @ bx + C * bx
         qy = Oy.T @ by - C * by
@@ -133,11 +146,12 @@ def loss_and_grad(problem: Problem, M: Optional[Sequence[int]] = None, checkpoin
             qR += PT
             qx += PT @ u[1]
             qy += PT.T @ u[0]
-        return qx, qy, qR
+        return qx, qy, proj(qR)
 
     def param_dot(b, u, tau_step, c, C_derivs):
         """Adds Re <b, df/dtheta(u)> for every parameter and pwc segment."""
         bx, by, bR = b
+        bR = proj(bR)
         ux, uy, uR = u
         for lo, ro, coef, param, chn, conj in der.terms:
             # action of d(Ox)/dh and d(Oy)/dh for this term (h = coef * theta * chan)
@@ -185,7 +199,7 @@ def loss_and_grad(problem: Problem, M: Optional[Sequence[int]] = None, checkpoin
         G = np.outer(z[0], z[1]) + z[2]
         loss += (w * np.sum(lamG * G)).real
         # cotangent of the final state
-        lam = [w * (lamG @ z[1]), w * (lamG.T @ z[0]), w * lamG.copy()]
+        lam = [w * (lamG @ z[1]), w * (lamG.T @ z[0]), w * proj(lamG)]
         starts = sorted(ckpt)
         for s0 in reversed(starts):
             s1 = min(s0 + checkpoint_every, steps)
@@ -224,11 +238,11 @@ def loss_and_grad(problem: Problem, M: Optional[Sequence[int]] = None, checkpoin
     return loss, grad_theta, grad_pwc
 
 
-def loss_only(problem: Problem, M: Optional[Sequence[int]] = None) -> float:
+def loss_only(problem: Problem, M: Optional[Sequence[int]] = None, r_layout: str = "full") -> float:
     """l = Re Tr(rho0 A(T)) from oracle.mapping (used by finite differences)."""
     from .mapping import rk4_mapped
     from .fock import operator_matrix
-    run = rk4_mapped(problem, M)
+    run = rk4_mapped(problem, M, r_layout=r_layout)
     A = run.fock_matrix()
     Mx = run.model.M
     rho = operator_matrix(problem.rho0_items(), Mx)

@@ -31,13 +31,14 @@ def _small_control(n_modes=1, N=5, n_seg=4, steps_per_seg=6, seed=3):
     return p
 
 
-def _fd(p, h=1e-6):
+def _fd(p, h=1e-6, r_layout="full"):
+    loss = lambda q: grad.loss_only(q, r_layout=r_layout)
     gt = []
     for i in range(len(p.params)):
         a, b = copy.deepcopy(p), copy.deepcopy(p)
         a.params[i] += h
         b.params[i] -= h
-        gt.append((grad.loss_only(a) - grad.loss_only(b)) / (2 * h))
+        gt.append((loss(a) - loss(b)) / (2 * h))
     ch = p.channels[0]
     n_seg = (len(ch.params) - 2) // 2
     gp = np.zeros((n_seg, 2))
@@ -49,7 +50,7 @@ def _fd(p, h=1e-6):
             pb[2 + 2 * s + r] -= h
             a.channels = [Channel("pwc", tuple(pa))]
             b.channels = [Channel("pwc", tuple(pb))]
-            gp[s, r] = (grad.loss_only(a) - grad.loss_only(b)) / (2 * h)
+            gp[s, r] = (loss(a) - loss(b)) / (2 * h)
     return np.array(gt), gp
 
 
@@ -88,3 +89,28 @@ def test_adjoint_with_secular_dissipator_matches_central_differences(n_modes, N)
     scale = max(np.max(np.abs(ft)), np.max(np.abs(fp)))
     assert np.max(np.abs(gt - ft)) < 1e-7 * scale, (gt, ft)
     assert np.max(np.abs(gp[0] - fp)) < 1e-7 * scale, (gp[0], fp)
+
+
+@pytest.mark.parametrize("n_modes,N", [(1, 5), (2, 3)])
+def test_adjoint_with_diagonal_residual_layout_matches_central_differences(n_modes, N):
+    """R kept only on k = l (the R(xy) layout) with the secular dissipator: the adjoint of
+    the projected system (D on b_R, on the R part of J^T and on the final cotangent) against
+    central differences of the same projected forward solve; the loss differs from the full
+    layout's (the projection is an approximation), the gradient machinery must not."""
+    from workloads.spec import SecularDamping
+    p = _small_control(n_modes=n_modes, N=N)
+    p.jumps = []
+    p.secular = [SecularDamping(j, 0.6 + 0.2 * j, (0.1, 0.15, 0.2)) for j in range(n_modes)]
+    p.measured = ({((1,), (1,)): 1.0, ((2,), (2,)): -0.4, ((0,), (1,)): 0.3 + 0.2j, ((1,), (0,)): 0.3 - 0.2j}
+                  if n_modes == 1 else
+                  {((1, 0), (1, 0)): 1.0, ((0, 1), (0, 1)): 0.5, ((0, 1), (1, 0)): 0.4 + 0.1j,
+                   ((1, 0), (0, 1)): 0.4 - 0.1j})
+    loss, gt, gp = grad.loss_and_grad(p, checkpoint_every=5, r_layout="diag")
+    assert abs(loss - grad.loss_only(p, r_layout="diag")) < 1e-13
+    assert abs(loss - grad.loss_only(p)) > 1e-9  # the layouts differ
+    ft, fp = _fd(p, r_layout="diag")
+    scale = max(np.max(np.abs(ft)), np.max(np.abs(fp)))
+    assert np.max(np.abs(gt - ft)) < 1e-7 * scale, (gt, ft)
+    assert np.max(np.abs(gp[0] - fp)) < 1e-7 * scale, (gp[0], fp)
+    full = grad.loss_and_grad(p, checkpoint_every=5)
+    assert np.max(np.abs(full[1] - gt)) > 1e-9 * scale  # a dropped projection would not show here otherwise
