@@ -84,7 +84,8 @@ typedef struct bq_map_opts {
                       * x_j y_j, the paper's observation with Fig. 2; Eq. 303c projected onto
                       * those entries: exact when the dynamics keep R diagonal, an
                       * approximation of order kappa t otherwise; mapped method, tiled stage
-                      * kernel, no gradients).  bq_read_system returns R expanded to n_g x n_g. */
+                      * kernel; bq_grad differentiates the projected system).  bq_read_system
+                      * returns R expanded to n_g x n_g. */
   int basis;         /* BQ_BASIS_*                                                      */
   int c_mode;        /* BQ_C_EQ304 | BQ_C_ZERO: separation constant                     */
   int reverse_time;  /* 1: t = horizon - tau                                            */

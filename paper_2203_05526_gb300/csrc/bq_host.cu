@@ -1987,7 +1987,6 @@ static int set_tau(bq_state* s, double tau, cudaStream_t st) {
 
 extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_every, void* work, size_t work_bytes,
                        double* loss_out, double* grad_out, void* stream) {
-  if (s && s->r_diag) return fail(BQ_EUNSUPPORTED, "gradients with the diagonal residual layout are not implemented");
   if (!s || !work || !loss_out || !grad_out) return fail(BQ_EINVAL, "NULL argument");
   if (n_steps < 1 || checkpoint_every < 1 || !(dt > 0.0)) return fail(BQ_EINVAL, "bad step arguments");
   if (dt > s->dt_max * (1.0 + 1e-12)) return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 bound %g", dt, s->dt_max);

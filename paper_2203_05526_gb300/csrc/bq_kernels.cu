@@ -1391,8 +1391,8 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
     const int ng = sd.n_g;
     for (int p = wi.start + tid / L; p < wi.start + wi.len; p += pstride) {
       int idx[ND];
-      const int kx = p / ng;
-      const int ly = p - kx * ng;
+      const int kx = sd.r_diag ? p : p / ng;  // diagonal residual layout: point p is (p, p)
+      const int ly = sd.r_diag ? p : p - kx * ng;
       {
         int r = kx;
 #pragma unroll
@@ -1414,6 +1414,9 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
         // secular projector term: it shifts x and y alike, so its source p - delta lies on the
         // diagonal of its mode exactly when p does
         if (td.diagp1 && idx[td.diagp1 - 1] != idx[NM + td.diagp1 - 1]) continue;
+        // diagonal layout: only terms that shift x and y alike couple diagonal points (the
+        // projection D of the forward equation), at offset deltaGx in the diagonal index
+        if (sd.r_diag && td.deltaGx != td.deltaGy) continue;
         T w = (T)1;
         bool ok = true;
         for (int i = 0; i < td.n_act; ++i) {
@@ -1423,7 +1426,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
           w *= ok ? W[td.wtab[i] + (ok ? s : 0)] : (T)0;
         }
         if (!ok) w = (T)0;
-        const int src = (w != (T)0) ? p - td.deltaR : p;
+        const int src = (w != (T)0) ? p - (sd.r_diag ? td.deltaGx : td.deltaR) : p;
         const C bv = b_at(src);
         q = cfma(sc[t], cscale(bv, w), q);
         if (ngt) addg(t, up, bv, w);
@@ -1601,6 +1604,28 @@ __global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
   // secular projector term: only pairs whose indices of mode dm agree contribute
   const int dm = td.diagp1 - 1;
   auto midx = [&](int f) { return dm >= 0 ? (f / sd.stG[dm]) % sd.M[dm] : 0; };
+  if (sd.r_diag) {
+    // diagonal layout: B(i, j) is zero off i = j, so out[i] = bscale b_R[i] z[i]
+    if (tid < BQ_SRC_TILE && i0 + tid < ng) {
+      const int i = i0 + tid;
+      int rem = i;
+      int id[NM];
+#pragma unroll
+      for (int d = NM - 1; d >= 0; --d) { id[d] = rem % sd.M[d]; rem /= sd.M[d]; }
+      T w = (T)1;
+      for (int a = 0; a < td.n_act; ++a) {
+        const int d = td.dim[a];
+        const bool isx = d < NM;
+        if (isx == (bool)dirx) continue;  // the summed side's dims
+        w *= W[td.wtab[a] + id[isx ? d : d - NM]];
+      }
+      const C zi = w == (T)0 ? cmk<C>(0.0, 0.0) : cscale(other[i + delta], w);
+      C* outd = reinterpret_cast<C*>(const_cast<void*>(A.srcred)) + (int64_t)blockIdx.x * A.srcred_stride +
+                (s * 2 + (dirx ? 0 : 1)) * ng;
+      outd[i] = cscale(cmul(bsrc[i], zi), bscale);
+    }
+    return;
+  }
   // out[i] = bscale sum_j B(i, j) z[j], z[j] = w(j) other[j + delta], with B(i, j) the R
   // cotangent at (i, j) (dirx) or (j, i), and w(j) the product of the term's weights on the
   // summed side.  Chunks of z go through shared memory; the sums run in a fixed order.
@@ -1692,8 +1717,8 @@ __global__ void k_adj_seed(const SysDesc* __restrict__ sys, const EvalGroup* __r
       const double fr = sd.w_re * en.f_re - sd.w_im * en.f_im;
       const double fi = sd.w_re * en.f_im + sd.w_im * en.f_re;
       const C f = cmk<C>(fr, fi);
-      if (sd.has_r) {
-        C& r = L[sd.off_r + (int64_t)en.kx * sd.n_g + en.ly];
+      if (sd.has_r && (!sd.r_diag || en.kx == en.ly)) {  // the diagonal layout keeps k = l only
+        C& r = L[sd.off_r + (sd.r_diag ? (int64_t)en.kx : (int64_t)en.kx * sd.n_g + en.ly)];
         r = cadd(r, f);
       }
       if (sd.has_sep) {

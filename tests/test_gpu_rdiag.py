@@ -88,7 +88,40 @@ def test_diag_layout_refusals():
     with pytest.raises(bq.BQError) as e:
         gpu_state(p, method="direct", r_layout="diag")
     assert e.value.args[0].startswith(f"bq status {BQ_EINVAL}")
+
+
+@pytest.mark.parametrize("n_modes", [1, 2])
+def test_diag_layout_gradients_match_oracle_adjoint(n_modes):
+    """Adjoint gradients of the projected (R(xy)) system: loss and gradients with respect to
+    the H parameters and the piecewise-constant drive segments against the oracle's adjoint
+    of the same layout."""
+    from oracle import grad as ograd
+    from workloads.spec import Channel, SecularDamping
+    rng = np.random.default_rng(5)
+    if n_modes == 1:
+        p = configs.kerr_driven(N=6, dt=0.01, T=0.24, n_th=0.0)
+        p.h_terms = (configs.kerr_mode_terms(1, 0, 0.0, 0.0, delta_param=0, kerr_param=1)
+                     + configs.gauss_drive_terms(1, 0, 0))
+        p.params = [0.3, -1.1]
+        p.measured = {((1,), (1,)): 1.0, ((2,), (2,)): -0.4, ((0,), (1,)): 0.3 + 0.2j, ((1,), (0,)): 0.3 - 0.2j}
+        p.rho0 = {((0,), (0,)): 0.5, ((1,), (1,)): 0.3, ((2,), (2,)): 0.2}
+    else:
+        p = configs.two_mode_control(n_seg=4, T=0.24, steps_per_seg=6, N=4)
+        p.measured = {((1, 0), (1, 0)): 1.0, ((0, 1), (0, 1)): 0.5, ((0, 1), (1, 0)): 0.4 + 0.1j,
+                      ((1, 0), (0, 1)): 0.4 - 0.1j}
+        p.rho0 = {((0, 0), (0, 0)): 0.4, ((1, 0), (1, 0)): 0.3, ((0, 1), (0, 1)): 0.3}
+    p.jumps = []
+    p.secular = [SecularDamping(j, 0.6 + 0.2 * j, (0.1, 0.15, 0.2)) for j in range(n_modes)]
+    n_seg = 4
+    seg_len = p.T / n_seg
+    vals = []
+    for _ in range(n_seg):
+        vals += [float(rng.normal(0, 0.5)), float(rng.normal(0, 0.5))]
+    p.channels = [Channel("pwc", (0.0, seg_len, *vals))]
+    p.dt = seg_len / 6
+    loss_o, gt, gp = ograd.loss_and_grad(p, checkpoint_every=5, r_layout="diag")
+    ref = np.concatenate([gt, gp[0].reshape(-1)])
     st = gpu_state(p, r_layout="diag")
-    with pytest.raises(bq.BQError) as e:
-        st.grad(p.dt, 10, 5)
-    assert e.value.args[0].startswith(f"bq status {BQ_EUNSUPPORTED}")
+    loss, g = st.grad(p.dt, p.n_steps, 5)
+    assert abs(loss[0] - loss_o) <= 1e-12 * max(1.0, abs(loss_o))
+    assert np.max(np.abs(g - ref)) <= 1e-10 * np.max(np.abs(ref)), (g, ref)
