@@ -860,12 +860,17 @@ static void build_work(const std::vector<SysDesc>& sys, size_t cs, int tile, int
     const int adj_sep = sd.has_sep ? (2 + 2 * sd.n_sterms) * sd.n_g : 0;
     const int nsep = sd.has_sep ? 2 * sd.n_g : 0;
     if (!sd.has_r) {
-      work.push_back(WorkItem{i, 0, 0, 0, nsep, 0, 0, sep, 0});
+      // separable part only: one CTA per system, or chunks of it (the tile length, else
+      // BQ_SEP_CHUNK points) when the batch is too small to fill the GPU with systems
+      const int chunk = nsys < 2 * 152 ? (tile > 0 ? tile : BQ_SEP_CHUNK) : std::max(nsep, 1);
+      for (int g0 = 0; g0 < std::max(nsep, 1); g0 += chunk)
+        work.push_back(WorkItem{i, 0, 0, g0, std::min(nsep, g0 + chunk), 0, 0, sep, 0});
       smem_max = std::max(smem_max, sep);
       adj_max = std::max(adj_max, adj_sep);
       continue;
     }
-    const bool few = nsys < 2 * 152 && sd.n_r >= 2 * 256;
+    // too few systems to fill the GPU with one CTA each: split those with a few hundred points
+    const bool few = nsys < 2 * 152 && sd.n_r + nsep >= 2 * 128;
     if (sd.n_r + sep <= budget && !few) {
       work.push_back(WorkItem{i, 0, sd.n_r, 0, nsep, 0, sd.n_r, sd.n_r + sep, 0});
       smem_max = std::max(smem_max, sd.n_r + sep);
@@ -884,9 +889,11 @@ static void build_work(const std::vector<SysDesc>& sys, size_t cs, int tile, int
       const int tl_par = std::max(few ? 256 : 64, (sd.n_r + want_tiles - 1) / want_tiles);
       tl = std::min(tl, tl_par);
     }
-    // the separable part of a split system: items of its own, BQ_SEP_CHUNK points each
-    for (int g0 = 0; g0 < nsep; g0 += BQ_SEP_CHUNK) {
-      work.push_back(WorkItem{i, 0, 0, g0, std::min(nsep, g0 + BQ_SEP_CHUNK), 0, 0, sep, 0});
+    // the separable part of a split system: items of its own (the tile length, else
+    // BQ_SEP_CHUNK points each)
+    const int chunk = tile > 0 ? tile : BQ_SEP_CHUNK;
+    for (int g0 = 0; g0 < nsep; g0 += chunk) {
+      work.push_back(WorkItem{i, 0, 0, g0, std::min(nsep, g0 + chunk), 0, 0, sep, 0});
       smem_max = std::max(smem_max, sep);
       adj_max = std::max(adj_max, adj_sep);
     }

@@ -215,3 +215,19 @@ def test_three_modes_global_read_gradients_match_oracle_adjoint():
     loss, g = st.grad(p.dt, p.n_steps, 4)
     assert abs(loss[0] - loss_o) <= 1e-12 * max(1.0, abs(loss_o))
     assert abs(g[0] - gt[0]) <= 1e-10 * abs(gt[0]), (g, gt)
+
+
+@pytest.mark.parametrize("n_modes,N", [(2, 5), (3, 4)])
+def test_separable_only_layout_matches_oracle(n_modes, N):
+    """R = 0 (the separated equations alone): the few systems of one Table I network are
+    split into chunks of [G_x | G_y] (default and tuned chunk lengths, one CTA per system
+    for long chunks), against the oracle's run of the same layout."""
+    p = configs.table_one_network(n_modes, N, steps=400)
+    p = Problem(**{**p.__dict__, "T": 20 * p.dt})
+    run = mapping.rk4_mapped(p, r_layout="off")
+    for tile in (0, 32, 4096):
+        st = gpu_state(p, r_layout="off")
+        st.set_tune(tile=tile)
+        st.step(p.dt, p.n_steps)
+        _sync()
+        compare_mapped_systems(st, run, TOL64)
