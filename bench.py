@@ -290,7 +290,7 @@ def grads_leg(n_steps=None, sched=None):
     p = configs.two_mode_control()
     st = bq.State([bq.problem_from_spec(p)], bq.map_opts(dtype="f64", horizon=p.T, dt=p.dt))
     if sched is None:
-        tune = st.autotune(p.dt, trial_steps=16)  # tile length, lanes and reads of the tiled kernels
+        tune = st.autotune_grad(p.dt, trial_steps=64, checkpoint_every=32)  # measured on the gradient itself
     else:
         st.set_tune(tile=sched[0], lanes=sched[1], gread=sched[2])
         tune = st.get_tune()
@@ -304,7 +304,7 @@ def grads_leg(n_steps=None, sched=None):
                        "checkpoint every 160, complex FP64",
            "seconds_per_gradient": el, "grads_per_s": 1.0 / el, "loss": float(loss[0]),
            "grad_norm": float(np.linalg.norm(g)), "n_params": int(g.size), "tile": tune["tile"],
-           "lanes": tune["lanes"], "gread": tune["gread"]}
+           "lanes": tune["lanes"], "gread": tune["gread"], "tuned_on": "gradient" if sched is None else "fixed"}
     if n_steps is None:
         out["batched"] = grads_batched_leg()
     return out
@@ -323,7 +323,7 @@ def grads_batched_leg(B: int = 16, steps: int = 1280):
     dt = probs[0].dt
     opts = bq.map_opts(dtype="f64", horizon=probs[0].T, dt=dt)
     stB = bq.State([bq.problem_from_spec(q) for q in probs], opts)
-    tuneB = stB.autotune(dt, trial_steps=8)
+    tuneB = stB.autotune_grad(dt, trial_steps=64, checkpoint_every=32)
     stB.grad(dt, 160, 160)  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -331,10 +331,12 @@ def grads_batched_leg(B: int = 16, steps: int = 1280):
     tB = time.perf_counter() - t0
     t1 = 0.0
     worst = 0.0
+    # one problem per state: the schedule tuned on the first such state serves all of them
+    tune1 = bq.State([bq.problem_from_spec(probs[0])], opts).autotune_grad(dt, trial_steps=64, checkpoint_every=32)
     n_per = gB.size // B
     for b, q in enumerate(probs):
         st1 = bq.State([bq.problem_from_spec(q)], opts)
-        st1.autotune(dt, trial_steps=8)
+        st1.set_tune(tile=tune1["tile"], lanes=tune1["lanes"], gread=tune1["gread"])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         l1, g1 = st1.grad(dt, steps, 160)

@@ -208,6 +208,7 @@ typedef struct bq_tune {
                           * from global memory instead of staging halo windows in shared
                           * memory; 0 = only where a halo does not fit */
   int pad;
+  double grad_us;        /* bq_autotune_grad: device time of the trial gradient per RK4 step */
 } bq_tune;
 
 /* Current schedules of the state (step_us / solve_us: last bq_autotune result, else 0). */
@@ -259,6 +260,17 @@ int bq_grad_required_bytes(const bq_state* s, int64_t n_steps, int checkpoint_ev
  * Synchronises stream. */
 int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_every, void* work, size_t work_bytes,
             double* loss_out, double* grad_out, void* stream);
+
+/* Schedules for bq_grad chosen by measuring bq_grad itself (no counterpart in the paper: the
+ * adjoint kernels' schedule): every available tiled schedule (tile length x lanes per point x
+ * global-read tiles; lanes only for single-mode states) runs one gradient of trial_steps
+ * steps of size dt checkpointed every checkpoint_every steps (after one warm-up gradient),
+ * timed with CUDA events on stream, and the fastest is set.  The stepping path, pipelined and
+ * persistent-solve schedules are kept.  work: as for bq_grad with (trial_steps,
+ * checkpoint_every).  The state is unchanged on return (bq_grad leaves it as it was).
+ * Synchronises stream.  out (may be NULL) receives the schedules and grad_us. */
+int bq_autotune_grad(bq_state* s, double dt, int trial_steps, int checkpoint_every, void* work, size_t work_bytes,
+                     void* stream, bq_tune* out);
 
 /* bq_step without any memory allocation, for callers that cannot allocate device memory
  * (code running inside another framework's CUDA-graph capture, where cudaMalloc is

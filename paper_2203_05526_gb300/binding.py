@@ -44,7 +44,7 @@ class bq_tune(C.Structure):
     _fields_ = [("stage_path", C.c_int), ("pipe_slots", C.c_int), ("pipe_ctas_per_sm", C.c_int),
                 ("solve_kernel", C.c_int), ("solve_ctas_per_sm", C.c_int), ("n_candidates", C.c_int),
                 ("step_us", C.c_double), ("solve_us", C.c_double), ("tile", C.c_int), ("lanes", C.c_int), ("gread", C.c_int),
-                ("pad", C.c_int)]
+                ("pad", C.c_int), ("grad_us", C.c_double)]
 
 
 class BQError(RuntimeError):
@@ -94,6 +94,7 @@ def lib() -> C.CDLL:
         "bq_set_tune": (C.c_int, [vp, C.POINTER(bq_tune)]),
         "bq_autotune_scratch_bytes": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
         "bq_autotune": (C.c_int, [vp, C.c_double, C.c_int, vp, C.c_size_t, vp, C.POINTER(bq_tune)]),
+        "bq_autotune_grad": (C.c_int, [vp, C.c_double, C.c_int, C.c_int, vp, C.c_size_t, vp, C.POINTER(bq_tune)]),
         "bq_stage_variant": (C.c_int, [vp, ip]),
         "bq_time": (C.c_int, [vp, dp]),
         "bq_evaluate": (C.c_int, [vp, dp, vp]),
@@ -295,7 +296,7 @@ class State:
         return dict(stage_path=PATH[t.stage_path], pipe_slots=t.pipe_slots, pipe_ctas_per_sm=t.pipe_ctas_per_sm,
                     solve_kernel=SOLVE_KERNEL[t.solve_kernel], solve_ctas_per_sm=t.solve_ctas_per_sm,
                     n_candidates=t.n_candidates, step_us=t.step_us, solve_us=t.solve_us, tile=t.tile, lanes=t.lanes,
-                    gread=t.gread)
+                    gread=t.gread, grad_us=t.grad_us)
 
     def get_tune(self) -> dict:
         t = bq_tune()
@@ -326,6 +327,18 @@ class State:
         t = bq_tune()
         check(lib().bq_autotune(self.ptr, float(dt), int(trial_steps), C.c_void_p(scratch.data_ptr()), nb.value,
                                 _stream_ptr(stream), C.byref(t)))
+        return self._tune_dict(t)
+
+    def autotune_grad(self, dt: float, trial_steps: int = 64, checkpoint_every: int = 32, stream=None) -> dict:
+        """Measures the tiled schedules on bq_grad itself (bq_autotune_grad) and keeps the
+        fastest; returns the chosen schedules and the trial gradient's time per step."""
+        import torch
+        nb = C.c_size_t()
+        check(lib().bq_grad_required_bytes(self.ptr, int(trial_steps), int(checkpoint_every), C.byref(nb)))
+        work = torch.empty(nb.value, dtype=torch.uint8, device=self.pool.device)
+        t = bq_tune()
+        check(lib().bq_autotune_grad(self.ptr, float(dt), int(trial_steps), int(checkpoint_every),
+                                     C.c_void_p(work.data_ptr()), nb.value, _stream_ptr(stream), C.byref(t)))
         return self._tune_dict(t)
 
     def step_fixed_scratch(self, dt: float, n_steps: int, stream=None):

@@ -758,6 +758,7 @@ struct bq_state {
   int has_gread = 0;    // some work item reads its R sources from global memory
   int work_cap = 0, tile = 0;  // work-item capacity of the pool; tiled schedule (0 = default)
   int gread_sched = 0;         // split tiles read R from global memory (schedule)
+  double tune_grad_us = 0.0;   // last bq_autotune_grad result
   int lanes = 1;               // lanes per point of the tiled forward and the adjoint stage kernels
   int ng_max = 0;      // largest G_x / G_y point count over the systems
   // schedules (bq_get_tune / bq_set_tune / bq_autotune)
@@ -1731,6 +1732,7 @@ extern "C" int bq_get_tune(const bq_state* s, bq_tune* out) {
   out->tile = s->tile;
   out->lanes = s->lanes;
   out->gread = s->gread_sched;
+  out->grad_us = s->tune_grad_us;
   return BQ_OK;
 }
 
@@ -2110,6 +2112,72 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
   CUDA_TRY(cudaStreamSynchronize(st));
   for (int i = 0; i < s->grad_size; ++i)
     if (!std::isfinite(grad_out[i])) return fail(BQ_ENONFINITE, "non-finite gradient");
+  return BQ_OK;
+}
+
+extern "C" int bq_autotune_grad(bq_state* s, double dt, int trial_steps, int checkpoint_every, void* work,
+                                size_t work_bytes, void* stream, bq_tune* out) {
+  if (!s || !work) return fail(BQ_EINVAL, "NULL argument");
+  if (trial_steps < 1 || checkpoint_every < 1) return fail(BQ_EINVAL, "bad trial arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<double> loss(s->B), g(std::max(1, s->grad_size));
+  struct Cand { int tile, lanes, gread; };
+  std::vector<Cand> cands;
+  if (s->use_m1) {
+    for (int ln : {1, 2, 4}) cands.push_back({s->tile, ln, s->gread_sched});
+  } else {
+    for (int gr : {0, 1})
+      for (int tl : {0, 32, 64, 96, 128, 192, 256, 512})
+        for (int ln : {1, 2, 4}) cands.push_back({tl, ln, gr});
+  }
+  const int tile0 = s->tile, lanes0 = s->lanes, gread0 = s->gread_sched;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  } guard{e0, e1};
+  double best_us = 1e300;
+  Cand best{tile0, lanes0, gread0};
+  int ntried = 0;
+  for (const Cand& c : cands) {
+    if (!s->use_m1 && (c.tile != s->tile || c.gread != s->gread_sched) && apply_tile(s, c.tile, c.gread) != BQ_OK) {
+      g_err.clear();  // a tile that does not fit
+      continue;
+    }
+    s->lanes = c.lanes;
+    int rc = bq_grad(s, dt, std::min(trial_steps, checkpoint_every), checkpoint_every, work, work_bytes, loss.data(),
+                     g.data(), stream);  // warm-up
+    if (rc == BQ_OK) {
+      CUDA_TRY(cudaEventRecord(e0, st));
+      rc = bq_grad(s, dt, trial_steps, checkpoint_every, work, work_bytes, loss.data(), g.data(), stream);
+      CUDA_TRY(cudaEventRecord(e1, st));
+    }
+    if (rc != BQ_OK) {
+      // restore the schedule the state had, then report
+      if (!s->use_m1) apply_tile(s, tile0, gread0);
+      s->lanes = lanes0;
+      return rc;
+    }
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    const double us = 1000.0 * ms / trial_steps;
+    ++ntried;
+    if (us < best_us) { best_us = us; best = c; }
+  }
+  if (!s->use_m1 && (best.tile != s->tile || best.gread != s->gread_sched)) {
+    const int rc = apply_tile(s, best.tile, best.gread);
+    if (rc != BQ_OK) return rc;
+  }
+  s->lanes = best.lanes;
+  s->tune_grad_us = best_us;
+  drop_graph(s);
+  if (out) {
+    bq_get_tune(s, out);
+    out->n_candidates = ntried;
+  }
   return BQ_OK;
 }
 

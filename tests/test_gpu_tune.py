@@ -201,3 +201,22 @@ def test_lanes_per_point_split_the_same_sums(n_modes):
             (l1, g1), (l0, g0) = grads[lanes], grads[1]
             assert abs(l1[0] - l0[0]) <= 1e-13 * max(1.0, abs(l0[0]))
             assert np.max(np.abs(g1 - g0)) <= 1e-12 * np.max(np.abs(g0)), lanes
+
+
+def test_gradient_autotuner_keeps_a_candidate_and_the_gradient():
+    """bq_autotune_grad times bq_grad under every tiled schedule: the state is unchanged,
+    the chosen schedule is one of the candidates, and the gradient afterwards equals the
+    default schedule's to rounding."""
+    p = configs.two_mode_control(n_seg=3, T=0.18, steps_per_seg=6, N=7)
+    ref = gpu_state(p)
+    l0, g0 = ref.grad(p.dt, p.n_steps, 6)
+    st = gpu_state(p)
+    before, t0 = _snapshot(st), st.time()
+    tune = st.autotune_grad(p.dt, trial_steps=8, checkpoint_every=4)
+    assert np.array_equal(_snapshot(st), before) and st.time() == t0
+    assert tune["n_candidates"] >= 24 and tune["grad_us"] > 0
+    assert tune["tile"] in (0, 32, 64, 96, 128, 192, 256, 512) and tune["lanes"] in (1, 2, 4)
+    assert st.get_tune()["tile"] == tune["tile"] and st.get_tune()["lanes"] == tune["lanes"]
+    l1, g1 = st.grad(p.dt, p.n_steps, 6)
+    assert abs(l1[0] - l0[0]) <= 1e-13 * max(1.0, abs(l0[0]))
+    assert np.max(np.abs(g1 - g0)) <= 1e-12 * np.max(np.abs(g0))
