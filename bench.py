@@ -402,6 +402,63 @@ def methods_leg(B: int = 1024, Ns=(10, 20, 40), steps: int = 100, acc_steps: int
             "rows": rows}
 
 
+def fig2_left_leg(modes=(1, 2), times=(2.0, 5.0, 10.0, 20.0, 40.0), target: float = 1e-4, steps_per_unit: int = 200,
+                  n_max: int = 16):
+    """The paper's Fig. 2 (left panels) on this GPU: the same Table I networks for one and two
+    oscillators as functions of the scaled time omega_q t / pi.  For every time and method the
+    smallest truncation with epsilon_r <= `target` against the conventional method at a
+    larger truncation with half the time step (FP64, the same step size at every time), its
+    stored elements (largest over the run: the state is allocated once) and its device time per
+    RK4 step."""
+    import numpy as np
+    import torch
+
+    import paper_2203_05526_gb300 as bq
+    from workloads import configs
+    ref_n = {1: 20, 2: 13}
+    rows = []
+
+    def run(p, dt, n, **kw):
+        st = bq.State([bq.problem_from_spec(p)], bq.map_opts(dtype="f64", horizon=p.T, dt=dt, **kw))
+        st.step(dt, n)
+        torch.cuda.synchronize()
+        return st
+
+    for nm in modes:
+        for tsc in times:
+            steps = int(round(steps_per_unit * tsc))
+            pr = configs.table_one_network(nm, ref_n[nm], scaled_time=tsc, steps=2 * steps)
+            ref = run(pr, pr.dt, 2 * steps, method="direct").fock_block(3, dim=3 ** nm)[0]
+            for name, kw in (("conventional", dict(method="direct")), ("mapping_R_diag", dict(r_layout="diag")),
+                             ("mapping_R_off", dict(r_layout="off"))):
+                found = None
+                for N in range(3, min(n_max, ref_n[nm] - 1) + 1):
+                    p = configs.table_one_network(nm, N, scaled_time=tsc, steps=steps)
+                    st = run(p, p.dt, steps, **kw)
+                    blk = st.fock_block(3, dim=3 ** nm)[0]
+                    eps = float(np.linalg.norm(blk - ref) / np.linalg.norm(ref))
+                    if eps <= target:
+                        found = (N, p, st, eps)
+                        break
+                if found is None:
+                    rows.append({"modes": nm, "scaled_time": tsc, "method": name, "truncation": None})
+                    continue
+                N, p, st, eps = found
+                st.autotune(p.dt, trial_steps=10)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st.step(p.dt, 200)
+                e1.record()
+                torch.cuda.synchronize()
+                n_sys = st.n_systems()
+                rows.append({"modes": nm, "scaled_time": tsc, "method": name, "truncation": N, "eps_r": eps,
+                             "systems": n_sys, "elements_per_system": st.state_bytes() / 16 / n_sys,
+                             "elements_total": st.state_bytes() / 16, "us_per_step": e0.elapsed_time(e1) * 1e3 / 200})
+    return {"workload": "Table I network, lab frame, secular dissipator at T_E = 0, A(0) = a_1 x ... x a_n, "
+                        f"scaled times {list(times)} at {steps_per_unit} RK4 steps per unit, complex FP64; "
+                        f"truncation tuned to eps_r <= {target:g}", "rows": rows}
+
+
 def fig2_leg(modes=(1, 2, 3), target: float = 1e-4, steps: int = 2000, n_max: int = 12):
     """The paper's Fig. 2 (right panels) on this GPU: the Table I network of n coupled
     driven anharmonic oscillators in the lab frame (secular dissipator, A(0) = a_1 (x) ... (x)
@@ -546,7 +603,7 @@ def main():
     from paper_2203_05526_gb300 import build
     build.build()
     if args.only_fig2:
-        print(json.dumps({"only_fig2": True, **fig2_leg()}))
+        print(json.dumps({"only_fig2": True, "right": fig2_leg(), "left": fig2_left_leg()}))
         return
     if args.only_grad:
         sched = None if args.grad_tune is None else [int(v) for v in args.grad_tune.split(",")]
@@ -661,7 +718,7 @@ def main():
     if not args.no_batched and world == 1:
         methods = methods_leg()
         secular = secular_leg()
-        fig2 = fig2_leg()
+        fig2 = fig2_leg()  # the left panels (time dependence): --only-fig2
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
