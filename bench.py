@@ -472,7 +472,7 @@ def fig2_leg(modes=(1, 2, 3), target: float = 1e-4, steps: int = 2000, n_max: in
 
     import paper_2203_05526_gb300 as bq
     from workloads import configs
-    ref_n = {1: 14, 2: 10, 3: 8}
+    ref_n = {1: 14, 2: 10, 3: 8, 4: 7}
     rows = []
 
     def run(p, dt, n, **kw):
@@ -603,7 +603,7 @@ def main():
     from paper_2203_05526_gb300 import build
     build.build()
     if args.only_fig2:
-        print(json.dumps({"only_fig2": True, "right": fig2_leg(), "left": fig2_left_leg()}))
+        print(json.dumps({"only_fig2": True, "right": fig2_leg(modes=(1, 2, 3, 4)), "left": fig2_left_leg()}))
         return
     if args.only_grad:
         sched = None if args.grad_tune is None else [int(v) for v in args.grad_tune.split(",")]

@@ -71,7 +71,7 @@ enum { BQ_C_EQ304 = 0, BQ_C_ZERO = 1 };
  * the summed result equals the monomial one up to the RK4 error of the different C). */
 enum { BQ_IC_MONOMIAL = 0, BQ_IC_SVD = 1 };
 
-#define BQ_MAX_MODES 3
+#define BQ_MAX_MODES 4
 
 typedef struct bq_problem bq_problem;
 typedef struct bq_state bq_state;
@@ -170,7 +170,7 @@ int bq_step(bq_state* s, double dt, int64_t n_steps, void* stream);
  * most two stencil terms per side; other states are stepped with bq_step.  Asynchronous. */
 int bq_solve(bq_state* s, double dt, int64_t n_steps, void* stream);
 
-/* Which fused stage kernel bq_step launches for this state: 0 = generic (1-3 modes, tiles
+/* Which fused stage kernel bq_step launches for this state: 0 = generic (1-4 modes, tiles
  * with halo windows), 1 = single-mode one-CTA-per-system, 2 = single-mode pipelined
  * (persistent CTAs with 1-D bulk-copy prefetch of the next systems).  Diagnostic only. */
 int bq_stage_variant(const bq_state* s, int* variant);

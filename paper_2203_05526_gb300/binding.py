@@ -33,7 +33,7 @@ R_LAYOUT = {"full": 0, "off": 1, "diag": 2}
 BASIS = {"auto": 0, "monomial": 1, "number": 2}
 C_MODE = {"eq304": 0, "zero": 1}
 IC_MODE = {"monomial": 0, "svd": 1}
-MAX_MODES = 3
+MAX_MODES = 4
 
 
 PATH = {0: "tiled", 1: "system", 2: "pipe"}

@@ -243,7 +243,7 @@ struct RawTerm {
 };
 
 struct Compiled {
-  int nm, M[3], method, basis, has_sep, has_r, r_diag = 0;
+  int nm, M[BQ_MAX_MODES], method, basis, has_sep, has_r, r_diag = 0;
   int n_g, n_r;
   std::vector<TermDesc> terms;         // wtab offsets relative to this problem's weight block
   std::vector<double> wtab;            // weight tables
@@ -365,7 +365,7 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
   C.basis = o.basis != BQ_BASIS_AUTO ? o.basis
             : (o.method == BQ_METHOD_MAPPED && o.dtype == BQ_F64 ? BQ_BASIS_MONOMIAL : BQ_BASIS_NUMBER);
   if (o.method == BQ_METHOD_DIRECT) C.basis = BQ_BASIS_NUMBER;
-  for (int j = 0; j < 3; ++j) C.M[j] = 1;
+  for (int j = 0; j < BQ_MAX_MODES; ++j) C.M[j] = 1;
   long long ng = 1;
   for (int j = 0; j < nm; ++j) {
     C.M[j] = o.grid[j] > 0 ? o.grid[j] : p->N[j];
@@ -464,7 +464,7 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
   if ((int)merged.size() > BQ_MAX_TERMS) return fail(BQ_EUNSUPPORTED, "%zu stencil terms > %d", merged.size(), BQ_MAX_TERMS);
 
   // strides: R index = kflat * n_g + lflat; flat = row-major over modes
-  int stG[3] = {1, 1, 1};
+  int stG[BQ_MAX_MODES] = {1, 1, 1, 1};
   for (int j = nm - 2; j >= 0; --j) stG[j] = stG[j + 1] * C.M[j + 1];
   int stR[BQ_MAXD];
   for (int j = 0; j < nm; ++j) { stR[j] = stG[j] * C.n_g; stR[nm + j] = stG[j]; }
@@ -718,7 +718,7 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
     e.f_re = f.real(); e.f_im = f.imag();
     C.trace_entries.push_back(e);
   }
-  int lo[3] = {1, 1, 1};
+  int lo[BQ_MAX_MODES] = {1, 1, 1, 1};
   int D = 1;
   for (int j = 0; j < nm; ++j) { lo[j] = std::min(3, C.M[j]); D *= lo[j]; }
   C.block_dim = D;
@@ -780,7 +780,7 @@ struct bq_state {
   char* pool = nullptr;
   Layout L{};
   std::vector<SysDesc> sys;
-  std::vector<int> prob_M;  // B * 3
+  std::vector<int> prob_M;  // B * BQ_MAX_MODES
   // tau control (host mirror) and graph cache
   double tau_base_host = 0.0;
   cudaStream_t cap_stream = nullptr;
@@ -960,11 +960,11 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
       SysDesc sd;
       std::memset(&sd, 0, sizeof(sd));
       sd.prob = b; sd.nm = nm;
-      for (int j = 0; j < 3; ++j) sd.M[j] = C.M[j];
+      for (int j = 0; j < BQ_MAX_MODES; ++j) sd.M[j] = C.M[j];
       sd.has_sep = C.has_sep; sd.has_r = C.has_r; sd.n_g = C.n_g; sd.n_r = C.n_r; sd.r_diag = C.r_diag;
       sd.term_off = term_off; sd.n_terms = (int)C.terms.size(); sd.diag_off = diag_off;
       sd.halo_lo = C.halo_lo; sd.halo_hi = C.halo_hi; sd.p_flat = s.p_flat; sd.q_flat = s.q_flat;
-      int stG[3] = {1, 1, 1};
+      int stG[BQ_MAX_MODES] = {1, 1, 1, 1};
       for (int j = nm - 2; j >= 0; --j) stG[j] = stG[j + 1] * C.M[j + 1];
       for (int j = 0; j < nm; ++j) { sd.stG[j] = stG[j]; sd.stR[j] = stG[j] * C.n_g; sd.stR[nm + j] = stG[j]; }
       sd.off_gx = sd.off_gy = sd.off_r = -1;
@@ -1446,7 +1446,7 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   st->n_trace_groups = P.n_trace_groups; st->n_block_groups = P.n_block_groups; st->block_dim = P.block_dim;
   st->total_elems = P.total_elems; st->dt_max = dt_max; st->horizon = o->horizon; st->reverse = o->reverse_time;
   st->pool = base; st->L = L; st->sys = P.sys;
-  for (int b = 0; b < B; ++b) for (int j = 0; j < 3; ++j) st->prob_M.push_back(P.comp[b].M[j]);
+  for (int b = 0; b < B; ++b) for (int j = 0; j < BQ_MAX_MODES; ++j) st->prob_M.push_back(P.comp[b].M[j]);
   *out = st;
   return BQ_OK;
 }

@@ -5,7 +5,7 @@
 
 #include <stdint.h>
 
-#define BQ_MAXD 6          // max R dimensions = 2 * BQ_MAX_MODES
+#define BQ_MAXD 8          // max R dimensions = 2 * BQ_MAX_MODES
 #define BQ_MAX_TERMS 64    // max general (non-folded) stencil terms per problem
 #define BQ_BLOCK 128       // threads per CTA of the stage kernels
 
@@ -55,7 +55,7 @@ struct ChanDesc {
 struct SysDesc {
   int prob;             // problem index in the batch
   int nm;               // number of modes
-  int M[3];             // grid per mode
+  int M[BQ_MAXD / 2];   // grid per mode
   int has_sep;          // G_x, G_y present (mapped method)
   int has_r;            // R present
   int n_g;              // elements of G_x (= of G_y) = prod M
@@ -65,7 +65,7 @@ struct SysDesc {
   int halo_lo, halo_hi; // max negative / positive linear offset of any R term
   int p_flat, q_flat;   // initial condition indices (flattened)
   int stR[BQ_MAXD];     // element strides of R (x-dims outer, y-dims inner)
-  int stG[3];           // element strides of G_x / G_y
+  int stG[BQ_MAXD / 2]; // element strides of G_x / G_y
   int dc_off;           // offset of d C / d theta_p (complex, one per parameter) in the gradient tables
   int64_t off_gx, off_gy, off_r;  // complex element offsets into the state arrays
   double c_re, c_im;    // separation constant C (Eq. 304)

@@ -2272,12 +2272,14 @@ cudaError_t launch_adjoint(const AdjArgs& a, int dtype, int nm, int n_work, int 
       case 1: return launch_adj_t<double, 1>(a, n_work, smem_bytes, n_sys, max_s, s);
       case 2: return launch_adj_t<double, 2>(a, n_work, smem_bytes, n_sys, max_s, s);
       case 3: return launch_adj_t<double, 3>(a, n_work, smem_bytes, n_sys, max_s, s);
+      case 4: return launch_adj_t<double, 4>(a, n_work, smem_bytes, n_sys, max_s, s);
     }
   } else {
     switch (nm) {
       case 1: return launch_adj_t<float, 1>(a, n_work, smem_bytes, n_sys, max_s, s);
       case 2: return launch_adj_t<float, 2>(a, n_work, smem_bytes, n_sys, max_s, s);
       case 3: return launch_adj_t<float, 3>(a, n_work, smem_bytes, n_sys, max_s, s);
+      case 4: return launch_adj_t<float, 4>(a, n_work, smem_bytes, n_sys, max_s, s);
     }
   }
   return cudaErrorInvalidValue;
@@ -2364,12 +2366,14 @@ cudaError_t launch_stage(const StageArgs& a, int dtype, int nm, int n_work, int 
       case 1: return launch_stage_t<double, 1>(a, n_work, smem_bytes, s);
       case 2: return launch_stage_t<double, 2>(a, n_work, smem_bytes, s);
       case 3: return launch_stage_t<double, 3>(a, n_work, smem_bytes, s);
+      case 4: return launch_stage_t<double, 4>(a, n_work, smem_bytes, s);
     }
   } else {
     switch (nm) {
       case 1: return launch_stage_t<float, 1>(a, n_work, smem_bytes, s);
       case 2: return launch_stage_t<float, 2>(a, n_work, smem_bytes, s);
       case 3: return launch_stage_t<float, 3>(a, n_work, smem_bytes, s);
+      case 4: return launch_stage_t<float, 4>(a, n_work, smem_bytes, s);
     }
   }
   return cudaErrorInvalidValue;

@@ -75,7 +75,7 @@ def test_bad_arguments():
     with pytest.raises(bq.BQError):
         bq.ProblemHandle(0, [4])
     with pytest.raises(bq.BQError):
-        bq.ProblemHandle(4, [4, 4, 4, 4])
+        bq.ProblemHandle(5, [4, 4, 4, 4, 4])  # more than BQ_MAX_MODES = 4
     h = bq.ProblemHandle(1, [4])
     with pytest.raises(bq.BQError):
         h.add_h_term(1.0, [1], [1], channel=3)

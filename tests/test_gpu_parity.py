@@ -231,3 +231,49 @@ def test_separable_only_layout_matches_oracle(n_modes, N):
         st.step(p.dt, p.n_steps)
         _sync()
         compare_mapped_systems(st, run, TOL64)
+
+
+def _with_idle_fourth_mode(p3: Problem) -> Problem:
+    """The three-mode problem with a fourth mode that is neither coupled, driven nor damped
+    (omega_q a^dag a + eta a^dag^2 a^2 only), in its ground state in rho0 and measured as
+    |0><0|: A(t) = A_3(t) (x) |0><0| exactly, so the four-mode run reduces to the three-mode
+    one (Tr(rho0 A) and gradients equal)."""
+    from workloads.spec import HTerm, SecularDamping
+    ext = lambda k: tuple(k) + (0,)
+    tq = configs.TABLE_ONE
+    h = [HTerm(t.coef, ext(t.u), ext(t.v), t.channel, t.conj, t.param) for t in p3.h_terms]
+    h += [HTerm(tq["omega_q"] + 0j, (0, 0, 0, 1), (0, 0, 0, 1)), HTerm(tq["eta"] + 0j, (0, 0, 0, 2), (0, 0, 0, 2))]
+    return Problem(**{**p3.__dict__, "n_modes": 4, "N": tuple(p3.N) + (3,), "h_terms": h,
+                      "secular": [SecularDamping(s.mode, s.kappa, s.nbar) for s in p3.secular],
+                      "measured": {(ext(k), ext(l)): v for (k, l), v in p3.measured.items()},
+                      "rho0": {(ext(k), ext(l)): v for (k, l), v in p3.rho0_items().items()}})
+
+
+def test_four_modes_reduce_to_three_modes():
+    """Four modes (the limit of the library): direct and mapped runs and the mapped adjoint
+    gradient of a network whose fourth mode is idle in its ground state, against the oracle's
+    three-mode results (Tr(rho0 A(T)), dl/dJ)."""
+    from oracle import grad as ograd
+    from workloads.spec import HTerm
+    p = configs.table_one_network(3, 3, steps=4000)
+    J = configs.TABLE_ONE["J"]
+    h = [HTerm(1.0 + 0j, t.u, t.v, param=0) if (t.coef == J and t.u != t.v and sum(t.u) == 1 and sum(t.v) == 1)
+         else t for t in p.h_terms]
+    p3 = Problem(**{**p.__dict__, "h_terms": h, "params": [J], "T": 12 * p.dt,
+                    "rho0": {((0, 1, 1), (1, 0, 1)): 0.4, ((1, 0, 1), (0, 1, 1)): 0.4,
+                             ((1, 0, 1), (1, 0, 1)): 0.5, ((0, 1, 1), (0, 1, 1)): 0.5},
+                    "measured": {((1, 0, 1), (0, 1, 1)): 1.0 + 0.3j, ((0, 1, 1), (1, 0, 1)): 1.0 - 0.3j,
+                                 ((1, 1, 0), (1, 1, 0)): 0.5}})
+    p4 = _with_idle_fourth_mode(p3)
+    A3 = fock.rk4_adjoint(p3)
+    ref = fock.expectation(A3, fock.operator_matrix(p3.rho0_items(), p3.N))
+    for method in ("direct", "mapped"):
+        st = gpu_state(p4, method=method)
+        st.step(p4.dt, p4.n_steps)
+        _sync()
+        ev = st.evaluate()[0]
+        assert abs(ev - ref) <= TOL64 * max(1.0, abs(ref)), (method, ev, ref)
+    loss_o, gt, _ = ograd.loss_and_grad(p3, checkpoint_every=4)
+    loss, g = gpu_state(p4).grad(p4.dt, p4.n_steps, 4)
+    assert abs(loss[0] - loss_o) <= 1e-12 * max(1.0, abs(loss_o))
+    assert abs(g[0] - gt[0]) <= 1e-10 * abs(gt[0]), (g, gt)
