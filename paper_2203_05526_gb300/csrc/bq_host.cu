@@ -772,7 +772,6 @@ struct bq_state {
   std::vector<TermDesc> terms_host;
   std::vector<ChanDesc> chans_host;
   std::vector<double> chpar_host;
-  std::vector<WorkItem> work_host;  // thread-per-group evaluation (few pairs per group)
   int n_trace_groups = 0, n_block_groups = 0, block_dim = 0;
   int64_t total_elems = 0;
   double dt_max = 0.0, horizon = 0.0, tau = 0.0;
@@ -1438,7 +1437,6 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   st->terms_host = P.terms;
   st->chans_host = P.chans;
   st->chpar_host = P.chpar;
-  st->work_host = P.work;
   st->solve_smem = P.solve_smem;
   st->solve_mg = P.solve_mg;
   st->solve_mg_ok = P.solve_mg;
@@ -1713,7 +1711,6 @@ static int apply_tile(bq_state* s, int tile, int gread) {
   int g = 0;
   for (const WorkItem& w : work) g = g || w.gread;
   s->has_gread = g;
-  s->work_host = std::move(work);
   drop_graph(s);
   return BQ_OK;
 }
