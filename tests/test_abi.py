@@ -86,3 +86,18 @@ def test_bad_arguments():
 def test_too_many_modes_grid_unsupported():
     st, _ = required(configs.kerr_static(N=200), dt=1e-4)
     assert st == binding.BQ_EUNSUPPORTED
+
+
+def test_four_mode_networks_plan_and_scale_with_the_layout():
+    """Planning (host only) of the Table I network with four modes: the mapped layouts need
+    far less memory per initial condition than the conventional matrix, the direct method
+    holds the N^8 matrix, and the diagonal residual layout sits between R = 0 and full R."""
+    p = configs.table_one_network(4, 4, steps=4000)
+    sizes = {}
+    for name, kw in (("direct", dict(method="direct")), ("full", {}), ("diag", dict(r_layout="diag")),
+                     ("off", dict(r_layout="off"))):
+        st, n = required(p, dt=p.dt, horizon=p.T, **kw)
+        assert st == 0, (name, bq.lib().bq_last_error().decode())
+        sizes[name] = n
+    assert sizes["off"] < sizes["diag"] < sizes["full"]
+    assert sizes["direct"] > 5 * 16 * 4 ** 8  # five complex FP64 arrays of the 4^8 matrix
