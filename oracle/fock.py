@@ -57,14 +57,26 @@ def ladder(n: int) -> np.ndarray:
     return a
 
 
-def monomial(u: Sequence[int], v: Sequence[int], dims: Sequence[int]) -> np.ndarray:
-    """prod_j (a_j^dag)^u_j a_j^v_j on the tensor product (mode 0 outermost)."""
+def monomial_factors(u: Sequence[int], v: Sequence[int], dims: Sequence[int]) -> List[np.ndarray]:
+    """Per-mode factors (a_j^dag)^u_j a_j^v_j of the monomial at the sizes `dims`."""
     mats = []
     for uj, vj, n in zip(u, v, dims):
         a = ladder(n)
         ad = a.conj().T
         mats.append(np.linalg.matrix_power(ad, uj) @ np.linalg.matrix_power(a, vj))
-    return reduce(np.kron, mats)
+    return mats
+
+
+def monomial(u: Sequence[int], v: Sequence[int], dims: Sequence[int]) -> np.ndarray:
+    """prod_j (a_j^dag)^u_j a_j^v_j on the tensor product (mode 0 outermost)."""
+    return reduce(np.kron, monomial_factors(u, v, dims))
+
+
+def kron_restricted(factors: Sequence[np.ndarray], small: Sequence[int]) -> np.ndarray:
+    """restrict(kron(factors), big, small) built factor by factor: the kept states (n_j <
+    small_j in every mode) form a product sub-grid, on which a Kronecker product is the
+    Kronecker product of the restricted factors (same entries, no full-size matrix)."""
+    return reduce(np.kron, [f[:s, :s] for f, s in zip(factors, small)])
 
 
 def restriction_indices(big: Sequence[int], small: Sequence[int]) -> np.ndarray:
@@ -110,16 +122,19 @@ class FockModel:
             c = complex(t.coef)
             if t.param >= 0:
                 c *= problem.params[t.param]
-            m = r(monomial(t.u, t.v, big))
+            m = kron_restricted(monomial_factors(t.u, t.v, big), self.N)
             if t.channel < 0:
                 self.h_static += c * m
             else:
                 self.h_dyn.append((m, t.channel, t.conj, c))
         self.jumps = []  # (rate, L, L^dag, (L^dag L))
         for j in problem.jumps:
-            L_big = sum(c * monomial(u, v, big) for c, u, v in j.terms)
-            LdL = r(L_big.conj().T @ L_big)
-            L = r(L_big)
+            # L = sum_t c_t M_t and L^dag L = sum_{s,t} conj(c_s) c_t M_s^dag M_t, every product
+            # formed per mode at the padded size, then restricted
+            fac = [(c, monomial_factors(u, v, big)) for c, u, v in j.terms]
+            L = sum(c * kron_restricted(f, self.N) for c, f in fac)
+            LdL = sum(np.conj(cs) * ct * kron_restricted([a.conj().T @ b for a, b in zip(fs, ft)], self.N)
+                      for cs, fs in fac for ct, ft in fac)
             self.jumps.append((j.rate, L, L.conj().T, LdL))
         # secular dissipators: K_n, P_n, P_{n+1} on a space padded by one level per mode
         # (enough: they change a mode's level by at most one), with their weights

@@ -40,8 +40,8 @@ import numpy as np
 
 from workloads.spec import Problem
 from .channels import stage_value
-from .fock import _max_degree, restrict
-from .mapping import MappedModel, left_of, map_initial, omega_eta, right_of, separation_constant
+from .fock import _max_degree, kron_restricted
+from .mapping import MappedModel, left_factors, map_initial, omega_eta, right_factors, separation_constant
 
 RK_C = (0.0, 0.5, 0.5, 1.0)
 
@@ -73,8 +73,8 @@ class _Derivs:
         for t in problem.h_terms:
             if t.param < 0 and t.channel < 0:
                 continue
-            lo = restrict(left_of(t.u, t.v, big), big, model.M)
-            ro = restrict(right_of(t.u, t.v, big), big, model.M)
+            lo = kron_restricted(left_factors(t.u, t.v, big), model.M)
+            ro = kron_restricted(right_factors(t.u, t.v, big), model.M)
             self.terms.append((lo, ro, complex(t.coef), t.param, t.channel, t.conj))
         self.n_params = len(problem.params)
 

@@ -61,7 +61,7 @@ import scipy.linalg
 
 from workloads.spec import Problem
 from .channels import stage_value
-from .fock import _max_degree, restrict
+from .fock import _max_degree, kron_restricted
 
 
 # ---------------------------------------------------------------------------------------
@@ -84,19 +84,27 @@ def d_matrix(P: int) -> np.ndarray:
     return D
 
 
+def left_factors(u: Sequence[int], v: Sequence[int], dims: Sequence[int]) -> List[np.ndarray]:
+    """Per-mode factors x_j^u_j (d/dx_j)^v_j of left multiplication by prod_j (a_j^dag)^u_j a_j^v_j."""
+    return [np.linalg.matrix_power(x_matrix(P), uj) @ np.linalg.matrix_power(d_matrix(P), vj)
+            for uj, vj, P in zip(u, v, dims)]
+
+
+def right_factors(u: Sequence[int], v: Sequence[int], dims: Sequence[int]) -> List[np.ndarray]:
+    """Per-mode factors y_j^v_j (d/dy_j)^u_j of right multiplication by prod_j (a_j^dag)^u_j a_j^v_j
+    (first u_j right-multiplications by a^dag, i.e. d/dy, then v_j by a, i.e. y)."""
+    return [np.linalg.matrix_power(x_matrix(P), vj) @ np.linalg.matrix_power(d_matrix(P), uj)
+            for uj, vj, P in zip(u, v, dims)]
+
+
 def left_of(u: Sequence[int], v: Sequence[int], dims: Sequence[int]) -> np.ndarray:
     """Left multiplication by prod_j (a_j^dag)^u_j a_j^v_j -> prod_j x_j^u_j (d/dx_j)^v_j."""
-    mats = [np.linalg.matrix_power(x_matrix(P), uj) @ np.linalg.matrix_power(d_matrix(P), vj)
-            for uj, vj, P in zip(u, v, dims)]
-    return reduce(np.kron, mats)
+    return reduce(np.kron, left_factors(u, v, dims))
 
 
 def right_of(u: Sequence[int], v: Sequence[int], dims: Sequence[int]) -> np.ndarray:
-    """Right multiplication A -> A prod_j (a_j^dag)^u_j a_j^v_j -> prod_j y_j^v_j (d/dy_j)^u_j
-    (first u_j right-multiplications by a^dag, i.e. d/dy, then v_j by a, i.e. y)."""
-    mats = [np.linalg.matrix_power(x_matrix(P), vj) @ np.linalg.matrix_power(d_matrix(P), uj)
-            for uj, vj, P in zip(u, v, dims)]
-    return reduce(np.kron, mats)
+    """Right multiplication A -> A prod_j (a_j^dag)^u_j a_j^v_j -> prod_j y_j^v_j (d/dy_j)^u_j."""
+    return reduce(np.kron, right_factors(u, v, dims))
 
 
 # ---------------------------------------------------------------------------------------
@@ -280,8 +288,14 @@ class MappedModel:
         big = tuple(m + pad for m in self.M)
         self.dim = int(np.prod(self.M))
 
-        def r(m):
-            return restrict(m, big, self.M)
+        M = self.M
+
+        def kr(factors):
+            return kron_restricted(factors, M)
+
+        def pair_sum(fa, fb, coef):
+            # sum_{s,t} coef(s, t) kron_j(A_s,j B_t,j): products per mode at the padded size
+            return sum(coef(ca, cb) * kr([a @ b for a, b in zip(xa, xb)]) for ca, xa in fa for cb, xb in fb)
 
         d = self.dim
         self.Ox = np.zeros((d, d), dtype=np.complex128)
@@ -289,8 +303,8 @@ class MappedModel:
         self.dyn = []  # (left, right, channel, conj, coef)
         for t in problem.h_terms:
             c = complex(t.coef) * (problem.params[t.param] if t.param >= 0 else 1.0)
-            lo = r(left_of(t.u, t.v, big))
-            ro = r(right_of(t.u, t.v, big))
+            lo = kr(left_factors(t.u, t.v, big))
+            ro = kr(right_factors(t.u, t.v, big))
             if t.channel < 0:
                 self.Ox += 1j * c * lo
                 self.Oy += -1j * c * ro
@@ -298,14 +312,15 @@ class MappedModel:
                 self.dyn.append((lo, ro, t.channel, t.conj, c))
         self.sandwich = []  # (kappa, [L^dag]_left, [L]_right)
         for jmp in problem.jumps:
-            Ld_left = sum(np.conj(c) * left_of(v, u, big) for c, u, v in jmp.terms)
-            L_left = sum(c * left_of(u, v, big) for c, u, v in jmp.terms)
-            L_right = sum(c * right_of(u, v, big) for c, u, v in jmp.terms)
-            Ld_right = sum(np.conj(c) * right_of(v, u, big) for c, u, v in jmp.terms)
-            self.Ox += -0.5 * jmp.rate * r(Ld_left @ L_left)
+            # [L^dag]_left, [L]_left, [L]_right, [L^dag]_right as sums of per-mode factors
+            Ld_left = [(np.conj(c), left_factors(v, u, big)) for c, u, v in jmp.terms]
+            L_left = [(c, left_factors(u, v, big)) for c, u, v in jmp.terms]
+            L_right = [(c, right_factors(u, v, big)) for c, u, v in jmp.terms]
+            Ld_right = [(np.conj(c), right_factors(v, u, big)) for c, u, v in jmp.terms]
+            self.Ox += -0.5 * jmp.rate * pair_sum(Ld_left, L_left, lambda a, b: a * b)
             # A L^dag L = (A L^dag) L: apply [L^dag]_right first, then [L]_right
-            self.Oy += -0.5 * jmp.rate * r(L_right @ Ld_right)
-            self.sandwich.append((jmp.rate, r(Ld_left), r(L_right)))
+            self.Oy += -0.5 * jmp.rate * pair_sum(L_right, Ld_right, lambda a, b: a * b)
+            self.sandwich.append((jmp.rate, sum(c * kr(f) for c, f in Ld_left), sum(c * kr(f) for c, f in L_right)))
         # secular dissipators: separable decay into O_x / O_y, projector weights for P
         self.secular = []  # (mode, w_down[m] (source m-1), w_up[m] (source m+1))
         grids = np.meshgrid(*[np.arange(m) for m in self.M], indexing="ij")
