@@ -192,7 +192,7 @@ def test_closed_system_residual_vanishes():
     assert np.max(np.abs(run.fock_matrix() - ref)) < 1e-8
 
 
-@pytest.mark.parametrize("seed,n_modes,N", [(11, 1, 7), (12, 2, 4), (13, 1, 6)])
+@pytest.mark.parametrize("seed,n_modes,N", [(11, 1, 7), (12, 2, 4), (13, 1, 6), (14, 4, 2)])
 def test_all_in_R_equals_number_basis(seed, n_modes, N):
     """With G_x = G_y = 0 and R = x^p y^q the coupled system is the linear RK4 on G; since
     g = D^-1 A D^-1 (D = diag sqrt(k!)) it must equal O1 to rounding, for every term type."""
@@ -273,3 +273,24 @@ def test_svd_run_equals_monomial_run_for_equal_separation_constant(n_modes, N):
     # with Eq. 304's per-IC constants the two differ only at the RK4-error level
     c = mapping.rk4_mapped(p).fock_matrix()
     assert np.max(np.abs(c - b)) < 1e-6 * np.max(np.abs(a))
+
+
+def test_four_mode_oracles_reduce_to_three_modes():
+    """A fourth mode that is idle (no coupling, drive or dissipation) and in its ground state
+    in the measured operator leaves Tr(rho0 A(T)) of the first three unchanged, in the number
+    basis and in the mapped solve (the four-mode oracle paths against the pinned three-mode
+    ones)."""
+    from workloads.spec import HTerm
+    p3 = configs.random_problem(16, n_modes=3, N=3, n_steps=10, dt=0.01)
+    ext = lambda k: tuple(k) + (0,)
+    h = [HTerm(t.coef, ext(t.u), ext(t.v), t.channel, t.conj, t.param) for t in p3.h_terms]
+    h += [HTerm(0.7 + 0j, (0, 0, 0, 1), (0, 0, 0, 1)), HTerm(-0.3 + 0j, (0, 0, 0, 2), (0, 0, 0, 2))]
+    jumps = [type(j)(j.rate, tuple((c, ext(u), ext(v)) for c, u, v in j.terms)) for j in p3.jumps]
+    p4 = Problem(**{**p3.__dict__, "n_modes": 4, "N": tuple(p3.N) + (3,), "h_terms": h, "jumps": jumps,
+                    "measured": {(ext(k), ext(l)): v for (k, l), v in p3.measured.items()},
+                    "rho0": {(ext(k), ext(l)): v for (k, l), v in p3.rho0_items().items()}})
+    for solve in (lambda q: fock.rk4_adjoint(q), lambda q: mapping.rk4_mapped(q).fock_matrix()):
+        A3, A4 = solve(p3), solve(p4)
+        t3 = fock.expectation(A3, fock.operator_matrix(p3.rho0_items(), p3.N))
+        t4 = fock.expectation(A4, fock.operator_matrix(p4.rho0_items(), p4.N))
+        assert abs(t4 - t3) <= 1e-12 * max(1.0, abs(t3))
