@@ -20,7 +20,11 @@ problems batched in one state vs one problem per state), ``methods`` (memory and
 step, and accuracy, of the conventional number-basis method vs the mapping with full R, with
 R kept at k = l and with R = 0, on secular-dissipator instances),
 ``secular`` (the paper's secular dissipator on the same instances: updates/s and HBM GB/s),
-and ``config.schedule`` (the schedule bq_autotune picked for the timed state).
+``fig2`` (Fig. 2's right panels: Table I networks of 1-3 oscillators, truncation tuned to
+epsilon_r <= 1e-4 per method, stored elements and time per step; ``--only-fig2`` adds four
+oscillators and the left panels, against scaled time), and ``config.schedule`` (the
+schedule bq_autotune picked for the timed state).  The gradient legs tune their states with
+bq_autotune_grad (``--grad-tune TILE,LANES,GREAD`` fixes the schedule instead).
 
 ``--impl reference`` times the oracle (the plain FP64 CPU implementation) on the same
 workload, each step a bounded sample.  Multi-GPU: every rank solves its own shard of
