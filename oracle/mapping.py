@@ -17,7 +17,10 @@ Steps, in the paper's order (single mode in the main text, multimode in Sec. S1)
         S(G) = sum_n kappa_n [L_n^dag]_left [L_n]_right G   (the sandwich term);
      each of x, d/dx, y, d/dy is a matrix on the monomial basis {x^k} truncated at M
      (coefficients with an index >= M are zero), products are formed at a padded size
-     and then truncated (the same compression as O1's);
+     and then truncated (the same compression as O1's); operators are tensor products
+     over modes, so the padding and truncation are applied to each mode's factor and the
+     truncated factors are combined by Kronecker products (equal, entry by entry, to
+     truncating the padded product);
   6. reconstruction of f(t) by Eq. 11 and of A(t)'s number-basis elements by Eq. 2.
 
 Secular dissipator (Eq. 203 / Eq. S9; Eq. S15 is its zero-temperature mapped form
@@ -47,7 +50,9 @@ Parity status (tests/test_oracle_mapping.py):
     Kerr oscillator measured on |m><m| (derived from Eq. 313 / S-eq. 315 reasoning for the
     standard dissipator), (b) R == 0 for a closed system (Eq. 9c with kappa = 0), (c) the
     'all in R' run, which is the linear RK4 on G and equals O1 (similarity by
-    diag(sqrt k!)) to rounding, (d) fourth-order convergence of the separated run to O1.
+    diag(sqrt k!)) to rounding (one, two and four modes), (d) fourth-order convergence of
+    the separated run to O1, (e) a fourth mode idle in its ground state leaving the three-mode
+    result unchanged.
 """
 
 from __future__ import annotations
