@@ -145,6 +145,25 @@ int bq_problem_set_rho0(bq_problem* p, int n, const int* k, const int* l, const 
 /* Device bytes bq_map() needs for B problems mapped with the same options. */
 int bq_required_bytes(const bq_problem* const* probs, int B, const bq_map_opts* opts, size_t* out);
 
+/* Host-only view of the plan bq_map() would build (no device needed; no counterpart in the
+ * paper: the work decomposition of the stage kernels).  n_work: CTAs of one stage launch of
+ * the tiled kernel at the default schedule (single-mode states: one item per system, used by
+ * the adjoint); work_cap: capacity of the work-item segment (the shortest tile); lanes: the
+ * default lanes per point; smem_bytes / adj_smem_bytes: dynamic shared memory per CTA of the
+ * tiled forward and adjoint stage kernels; stage_variant as bq_stage_variant. */
+typedef struct bq_plan_info {
+  int n_systems;
+  int n_work;
+  int work_cap;
+  int lanes;
+  int stage_variant;
+  int smem_bytes;
+  int adj_smem_bytes;
+  int pad;
+  int64_t total_elems;
+} bq_plan_info;
+int bq_plan(const bq_problem* const* probs, int B, const bq_map_opts* opts, bq_plan_info* out);
+
 /* Maps B problems into one batched state inside [device_pool, device_pool + pool_bytes)
  * (256-byte aligned, caller-owned).  For the mapped method every non-negligible
  * g_{p,q}(0) = <p|A|q>/sqrt(p! q!) (Eq. 6 with Eq. 8's basis) becomes one separable

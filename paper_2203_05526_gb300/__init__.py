@@ -5,4 +5,4 @@ is the thin ctypes binding.  ``build.build()`` compiles the library in-tree.
 """
 
 from .binding import (BQError, ProblemHandle, State, check, exported_symbols, launch_count, lib,  # noqa: F401
-                      map_opts, problem_from_spec)
+                      map_opts, plan, problem_from_spec)

@@ -47,6 +47,12 @@ class bq_tune(C.Structure):
                 ("pad", C.c_int), ("grad_us", C.c_double)]
 
 
+class bq_plan_info(C.Structure):
+    _fields_ = [("n_systems", C.c_int), ("n_work", C.c_int), ("work_cap", C.c_int), ("lanes", C.c_int),
+                ("stage_variant", C.c_int), ("smem_bytes", C.c_int), ("adj_smem_bytes", C.c_int), ("pad", C.c_int),
+                ("total_elems", C.c_int64)]
+
+
 class BQError(RuntimeError):
     def __init__(self, status: int, detail: str):
         super().__init__(f"bq status {status}: {detail}")
@@ -95,6 +101,7 @@ def lib() -> C.CDLL:
         "bq_autotune_scratch_bytes": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
         "bq_autotune": (C.c_int, [vp, C.c_double, C.c_int, vp, C.c_size_t, vp, C.POINTER(bq_tune)]),
         "bq_autotune_grad": (C.c_int, [vp, C.c_double, C.c_int, C.c_int, vp, C.c_size_t, vp, C.POINTER(bq_tune)]),
+        "bq_plan": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(bq_map_opts), C.POINTER(bq_plan_info)]),
         "bq_stage_variant": (C.c_int, [vp, ip]),
         "bq_time": (C.c_int, [vp, dp]),
         "bq_evaluate": (C.c_int, [vp, dp, vp]),
@@ -236,6 +243,18 @@ def _stream_ptr(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
+
+
+def plan(handles: Sequence["ProblemHandle"], opts: "bq_map_opts") -> dict:
+    """Host-only view of the plan bq_map would build for these problems (bq_plan): no device
+    is needed."""
+    arr = (C.c_void_p * len(handles))(*[h.ptr.value for h in handles])
+    info = bq_plan_info()
+    check(lib().bq_plan(arr, len(handles), C.byref(opts), C.byref(info)))
+    variant = {0: "generic", 1: "single_mode", 2: "pipelined"}[info.stage_variant]
+    return dict(n_systems=info.n_systems, n_work=info.n_work, work_cap=info.work_cap, lanes=info.lanes,
+                stage_variant=variant, smem_bytes=info.smem_bytes, adj_smem_bytes=info.adj_smem_bytes,
+                total_elems=info.total_elems)
 
 
 class State:

@@ -1317,6 +1317,23 @@ extern "C" int bq_required_bytes(const bq_problem* const* probs, int B, const bq
   return BQ_OK;
 }
 
+extern "C" int bq_plan(const bq_problem* const* probs, int B, const bq_map_opts* opts, bq_plan_info* out) {
+  if (!out) return fail(BQ_EINVAL, "out is NULL");
+  Plan P;
+  int r = make_plan(probs, B, opts, P);
+  if (r != BQ_OK) return r;
+  std::memset(out, 0, sizeof(*out));
+  out->n_systems = (int)P.sys.size();
+  out->n_work = (int)P.work.size();
+  out->work_cap = (int)std::max(P.work.size(), P.work_cap);
+  out->lanes = default_lanes(P.sys);
+  out->stage_variant = P.use_pipe ? 2 : (P.use_m1 ? 1 : 0);
+  out->smem_bytes = P.smem_bytes;
+  out->adj_smem_bytes = P.adj_smem;
+  out->total_elems = P.total_elems;
+  return BQ_OK;
+}
+
 template <typename T>
 static std::vector<T> to_real(const std::vector<double>& v) { return std::vector<T>(v.begin(), v.end()); }
 

@@ -101,3 +101,36 @@ def test_four_mode_networks_plan_and_scale_with_the_layout():
         sizes[name] = n
     assert sizes["off"] < sizes["diag"] < sizes["full"]
     assert sizes["direct"] > 5 * 16 * 4 ** 8  # five complex FP64 arrays of the 4^8 matrix
+
+
+def _plan(specs, **kw):
+    specs = specs if isinstance(specs, (list, tuple)) else [specs]
+    return bq.plan([bq.problem_from_spec(s) for s in specs], bq.map_opts(dt=specs[0].dt, horizon=specs[0].T, **kw))
+
+
+def test_work_decomposition_of_a_large_two_mode_system():
+    """One 2-mode system of 20 736 R points and 288 G points (the control problem): split into
+    256-point R tiles (a single system cannot fill the GPU otherwise) plus 64-point chunks of
+    [G_x | G_y]; four lanes per point; capacity for 32-point tiles."""
+    p = configs.two_mode_control()
+    info = _plan(p, dtype="f64")
+    assert info["stage_variant"] == "generic" and info["n_systems"] == 1
+    assert info["n_work"] == 20736 // 256 + 288 // 64 + 1  # 81 R tiles, 5 G chunks (4 full + 1 of 32)
+    assert info["work_cap"] == 20736 // 32 + 288 // 32
+    assert info["lanes"] == 4
+
+
+def test_work_decomposition_of_small_batches_and_layouts():
+    """Three-mode Table I network (125 initial conditions of 216 points per mode space):
+    separable-only systems (R = 0) are split into 64-point chunks, R(xy) systems into one R
+    tile plus chunks, full-R systems (46 656 points each) into tiles; large batches of small
+    single-mode systems stay one CTA per system on the single-mode paths."""
+    p = configs.table_one_network(3, 6, steps=2000)
+    off = _plan(p, r_layout="off")
+    assert off["n_systems"] == 125 and off["n_work"] == 125 * 7  # 432 G points -> 7 chunks
+    diag = _plan(p, r_layout="diag")
+    assert diag["n_work"] == 125 * 8  # + one 216-point R tile
+    assert diag["smem_bytes"] >= off["smem_bytes"] + 16 * 216  # plus the staged R window
+    batch = configs.kerr_batch(B=512, T=1.0, dt=0.002)
+    b = _plan(batch, dtype="f32")
+    assert b["stage_variant"] == "pipelined" and b["n_work"] == 512 and b["lanes"] == 1
