@@ -134,3 +134,14 @@ def test_work_decomposition_of_small_batches_and_layouts():
     batch = configs.kerr_batch(B=512, T=1.0, dt=0.002)
     b = _plan(batch, dtype="f32")
     assert b["stage_variant"] == "pipelined" and b["n_work"] == 512 and b["lanes"] == 1
+
+
+def test_svd_initial_conditions_plan_fewer_systems():
+    """Host Jacobi SVD of g(0) (BQ_IC_SVD): a dense measured operator on a two-mode grid of
+    d = 16 points needs at most d systems (its rank), against one per non-zero element of
+    g(0) for the monomial decomposition."""
+    p = configs.random_problem(43, n_modes=2, N=4, n_steps=4, dt=0.01, dense_measured=True)
+    mono = _plan(p, c_mode="zero")
+    svd = _plan(p, ic_mode="svd")
+    assert svd["n_systems"] <= 16 < mono["n_systems"]
+    assert svd["total_elems"] < mono["total_elems"]
