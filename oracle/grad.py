@@ -25,10 +25,15 @@ equation is projected onto its diagonal k = l, dR = D(f_R), and R stays diagonal
 symmetric under the bilinear pairing, so J^T acts on D(b_R) and its R component is projected
 again; the cotangent of the final R is D(dl/dG).
 
+The number-basis method (O1, oracle.fock) has its own discrete adjoint,
+``loss_and_grad_direct``: the same RK4 pull-back with the transposed generator of Eq. 3
+(every product X A Y becomes X^T B Y^T under the bilinear pairing).
+
 Parity status: pinned by central finite differences of oracle.mapping.rk4_mapped
 (tests/test_oracle_grad.py), with conventional jump operators and with the secular
 dissipator (one and two modes, finite temperature), in the full and the diagonal residual
-layouts.
+layouts; ``loss_and_grad_direct`` by central finite differences of oracle.fock.rk4_adjoint
+(one and two modes, thermal jump operators and the secular dissipator).
 """
 
 from __future__ import annotations
@@ -246,4 +251,135 @@ def loss_only(problem: Problem, M: Optional[Sequence[int]] = None, r_layout: str
     A = run.fock_matrix()
     Mx = run.model.M
     rho = operator_matrix(problem.rho0_items(), Mx)
+    return float(np.trace(rho @ A).real)
+
+
+# ---- O3 for O1: the discrete adjoint of the number-basis RK4 solve ---------------------
+def _direct_transpose(model, B: np.ndarray, H: np.ndarray) -> np.ndarray:
+    """F^T(B) for the generator F(A) = i[H, A] + sum_n kappa_n (L^dag A L - 1/2 {L^dag L, A})
+    (+ the secular dissipators) of Eq. 3, transposed under the bilinear pairing
+    <B, A> = sum_kl B_kl A_kl: every product X A Y becomes X^T B Y^T."""
+    out = 1j * (H.T @ B - B @ H.T)
+    for rate, L, Ld, LdL in model.jumps:
+        out += rate * (Ld.T @ B @ L.T - 0.5 * (LdL.T @ B + B @ LdL.T))
+    if model.secular:
+        # the secular terms K^dag A K, K A K^dag, P A, A P with real K and symmetric P
+        # transpose to K B K^dag, K^dag B K, P B, B P: the Schroedinger form of the same
+        # dissipator applied to B (evaluated padded and restricted like the adjoint)
+        out += model.secular_schrodinger(B)
+    return out
+
+
+def loss_and_grad_direct(problem: Problem, N: Optional[Sequence[int]] = None, checkpoint_every: int = 64):
+    """Loss l = Re Tr(rho0 A(T)) of the number-basis solve (oracle.fock.rk4_adjoint, O1) and
+    its gradient by the exact discrete adjoint of classical RK4 on Eq. 3: with stage inputs
+    u_i and the cotangent lam' of A(tau + h),
+        b4 = h/6 lam', q_i = F_i^T(b_i), b3 = h/3 lam' + h q4, b2 = h/3 lam' + h/2 q3,
+        b1 = h/6 lam' + h/2 q2, lam = lam' + q1 + q2 + q3 + q4,
+        dl/dtheta += Re <b_i, i (dH/dtheta u_i - u_i dH/dtheta)>.
+    Parameters as in loss_and_grad (H-term parameters, Re / Im of every piecewise-constant
+    segment); the number-basis method has no separation constant.  Forward states are
+    checkpointed every checkpoint_every steps and each segment is recomputed once.
+    Returns (loss, dl/dtheta, {channel: (n_seg, 2)})."""
+    from . import fock
+    model = fock.FockModel(problem, N)
+    Nm = model.N
+    p = problem
+    dt = p.dt
+    steps = p.n_steps
+    pad = 2 * _max_degree(problem) + 2
+    big = tuple(n + pad for n in Nm)
+    # every H term that carries a parameter or a channel, as its restricted matrix
+    terms = []
+    for t in p.h_terms:
+        if t.param < 0 and t.channel < 0:
+            continue
+        m = kron_restricted(fock.monomial_factors(t.u, t.v, big), Nm)
+        terms.append((m, complex(t.coef), t.param, t.channel, t.conj))
+    grad_theta = np.zeros(len(p.params))
+    grad_pwc: Dict[int, np.ndarray] = {}
+    for ci, ch in enumerate(p.channels):
+        if ch.kind == "pwc":
+            grad_pwc[ci] = np.zeros(((len(ch.params) - 2) // 2, 2))
+    rho = fock.operator_matrix(p.rho0_items(), Nm)
+    lam_T = rho.T.copy()  # d Re Tr(rho0 A) / dA_kl = rho0_lk
+
+    def F(A, H):
+        return model.adjoint_generator(A, H)
+
+    def param_dot(b, u, tau_step, c):
+        for m, coef, param, chn, conj in terms:
+            act = np.sum(b * (1j * (m @ u - u @ m)))  # <b, i [M_t, u]>
+            theta = p.params[param] if param >= 0 else 1.0
+            e = 1.0 + 0j
+            if chn >= 0:
+                e = stage_value(p.channels[chn], tau_step, c, dt, p.T, p.reverse_time)
+                e = np.conj(e) if conj else e
+            if param >= 0:
+                grad_theta[param] += (coef * e * act).real
+            if chn >= 0 and p.channels[chn].kind == "pwc":
+                chd = p.channels[chn]
+                tt = (p.T - (tau_step + 0.5 * dt)) if p.reverse_time else tau_step + 0.5 * dt
+                s = int(math.floor((tt - chd.params[0]) / chd.params[1]))
+                if 0 <= s < grad_pwc[chn].shape[0]:
+                    g = coef * theta * act
+                    grad_pwc[chn][s, 0] += g.real
+                    grad_pwc[chn][s, 1] += (g * (-1j if conj else 1j)).real
+
+    A = fock.operator_matrix(p.measured, Nm)
+    ckpt = {}
+    for n in range(steps):
+        if n % checkpoint_every == 0:
+            ckpt[n] = A.copy()
+        tau = n * dt
+        H1, H2, H4 = model.hamiltonian(tau, 0.0, dt), model.hamiltonian(tau, 0.5, dt), model.hamiltonian(tau, 1.0, dt)
+        k1 = F(A, H1)
+        k2 = F(A + 0.5 * dt * k1, H2)
+        k3 = F(A + 0.5 * dt * k2, H2)
+        k4 = F(A + dt * k3, H4)
+        A = A + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    loss = float(np.sum(lam_T * A).real)
+    lam = lam_T
+    for s0 in reversed(sorted(ckpt)):
+        s1 = min(s0 + checkpoint_every, steps)
+        Z = ckpt[s0].copy()
+        rec = []
+        for n in range(s0, s1):
+            tau = n * dt
+            H1, H2, H4 = model.hamiltonian(tau, 0.0, dt), model.hamiltonian(tau, 0.5, dt), model.hamiltonian(tau, 1.0, dt)
+            u1 = Z
+            k1 = F(u1, H1)
+            u2 = Z + 0.5 * dt * k1
+            k2 = F(u2, H2)
+            u3 = Z + 0.5 * dt * k2
+            k3 = F(u3, H2)
+            u4 = Z + dt * k3
+            k4 = F(u4, H4)
+            rec.append((u1, u2, u3, u4, H1, H2, H4))
+            Z = Z + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+        for n in reversed(range(s0, s1)):
+            u1, u2, u3, u4, H1, H2, H4 = rec[n - s0]
+            tau = n * dt
+            b4 = (dt / 6.0) * lam
+            q4 = _direct_transpose(model, b4, H4)
+            param_dot(b4, u4, tau, 1.0)
+            b3 = (dt / 3.0) * lam + dt * q4
+            q3 = _direct_transpose(model, b3, H2)
+            param_dot(b3, u3, tau, 0.5)
+            b2 = (dt / 3.0) * lam + 0.5 * dt * q3
+            q2 = _direct_transpose(model, b2, H2)
+            param_dot(b2, u2, tau, 0.5)
+            b1 = (dt / 6.0) * lam + 0.5 * dt * q2
+            q1 = _direct_transpose(model, b1, H1)
+            param_dot(b1, u1, tau, 0.0)
+            lam = lam + q1 + q2 + q3 + q4
+    return loss, grad_theta, grad_pwc
+
+
+def loss_only_direct(problem: Problem, N: Optional[Sequence[int]] = None) -> float:
+    """l = Re Tr(rho0 A(T)) from oracle.fock.rk4_adjoint (used by finite differences)."""
+    from . import fock
+    A = fock.rk4_adjoint(problem, N)
+    Nm = tuple(N if N is not None else problem.N)
+    rho = fock.operator_matrix(problem.rho0_items(), Nm)
     return float(np.trace(rho @ A).real)

@@ -29,6 +29,17 @@ def rel_err(a, ref, floor=0.0):
     return float(np.max(np.abs(a - ref)) / scale)
 
 
+# Floors of the scalar-observable tolerance (|x - x_ref| <= tol * max(|x_ref|, floor)): a value
+# below the floor is compared in absolute terms at tol * floor.
+FLOOR64 = 1e-14
+FLOOR32 = 1e-7
+
+
+def scalar_err(x, ref, floor):
+    """|x - ref| / max(|ref|, floor) for a scalar observable such as Tr(rho0 A)."""
+    return abs(complex(x) - complex(ref)) / max(abs(complex(ref)), floor)
+
+
 def compare_mapped_systems(state, run, tol, sys_offset=0, n_sys=None):
     """Every system (initial condition) of ``state`` against the oracle run's IC with the
     same (p, q): G_x, G_y and R element by element, relative to the IC's largest value."""

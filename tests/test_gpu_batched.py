@@ -1,6 +1,7 @@
 """Batched solving on the GPU: the persistent one-launch solve (bq_solve) and the streamed
 stage kernels over a ragged batch, against the FP64 oracle and against each other."""
 
+import functools
 import json
 import os
 
@@ -10,7 +11,7 @@ import pytest
 from oracle import mapping
 from workloads import configs
 
-from parity import compare_mapped_systems, gpu_state, rel_err
+from parity import FLOOR32, FLOOR64, compare_mapped_systems, gpu_state, rel_err, scalar_err
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "kerr_batch_golden.json")
@@ -46,7 +47,7 @@ def test_solve_f64_ragged_batch_matches_oracle_per_system():
     ev = st.evaluate()
     for b, p in enumerate(ps[:6]):
         ref = mapping.rk4_mapped(p).fock_matrix()[0, 0]
-        assert abs(ev[b] - ref) <= 1e-10 * max(1.0, abs(ref))
+        assert scalar_err(ev[b], ref, FLOOR64) <= 1e-10
 
 
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-6)])
@@ -106,6 +107,38 @@ def test_kerr_batch_4096_full_horizon_f32_vs_oracle_samples(path):
         ref = np.array(g["block_re"]) + 1j * np.array(g["block_im"])
         worst = max(worst, rel_err(blk[i], ref))
         tr = complex(*g["tr_rho0_A"])
-        assert abs(ev[i] - tr) <= 1e-5 * max(1.0, abs(tr))
+        assert scalar_err(ev[i], tr, FLOOR32) <= 1e-5, (i, ev[i], tr)
     assert worst <= 1e-5, worst
     assert np.all(np.isfinite(ev))
+
+
+_SPOT_STEPS = 50
+
+
+@functools.lru_cache(maxsize=None)
+def _spot_oracle(b):
+    return mapping.rk4_mapped(configs.kerr_batch(B=64, T=_SPOT_STEPS * 0.002)[b])
+
+
+@pytest.mark.parametrize("path", ["solve", "step"])
+def test_kerr_batch_first_64_f64_spot_check(path):
+    """FP64 spot check of the batch itself: its first 64 instances (seed 20220311, N in
+    10..40, dt = 0.002 ns) over 50 steps in FP64 through the persistent solve and through
+    the stage kernels, every system against the oracle element by element (1e-10), with
+    Tr(rho0 A) and the three-level block."""
+    ps = configs.kerr_batch(B=64, T=_SPOT_STEPS * 0.002)
+    st = gpu_state(ps)
+    if path == "solve":
+        assert st.solve_eligible()
+        st.solve(ps[0].dt, ps[0].n_steps)
+    else:
+        st.step(ps[0].dt, ps[0].n_steps)
+    _sync()
+    ev = st.evaluate()
+    blk = st.fock_block(3, dim=3)
+    for b, p in enumerate(ps):
+        run = _spot_oracle(b)
+        compare_mapped_systems(st, run, 1e-10, sys_offset=b, n_sys=b + 1)
+        A = run.fock_matrix()
+        assert scalar_err(ev[b], A[0, 0], FLOOR64) <= 1e-10, (b, ev[b], A[0, 0])
+        assert rel_err(blk[b], A[:3, :3]) <= 1e-10

@@ -130,6 +130,24 @@ def test_grad_direct_method_matches_finite_differences():
     assert err <= 1e-7
 
 
+@pytest.mark.parametrize("n_modes,N,ck,secular", [(1, 5, 6, False), (2, 3, 5, False), (1, 5, 4, True)])
+def test_grad_direct_method_matches_oracle_adjoint(n_modes, N, ck, secular):
+    """The number-basis method's gradient on the GPU against the oracle's discrete adjoint of
+    its own number-basis solve (oracle.grad.loss_and_grad_direct), element by element."""
+    from workloads.spec import SecularDamping
+    p = _small_control(n_modes=n_modes, N=N)
+    if secular:
+        p.jumps = []
+        p.secular = [SecularDamping(0, 0.6, (0.1, 0.15, 0.2))]
+    loss_o, gt, gp = ograd.loss_and_grad_direct(p, checkpoint_every=ck)
+    st = gpu_state(p, method="direct")
+    loss, g = st.grad(p.dt, p.n_steps, ck)
+    ref = _flat_oracle(gt, gp)
+    assert abs(loss[0] - loss_o) <= 1e-12 * max(1.0, abs(loss_o))
+    err = float(np.max(np.abs(g - ref)) / np.max(np.abs(ref)))
+    assert err <= 1e-10, (err, g, ref)
+
+
 def test_checkpoint_interval_and_autograd():
     import torch
     from paper_2203_05526_gb300.autograd import measured_probability

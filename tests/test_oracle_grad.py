@@ -114,3 +114,65 @@ def test_adjoint_with_diagonal_residual_layout_matches_central_differences(n_mod
     assert np.max(np.abs(gp[0] - fp)) < 1e-7 * scale, (gp[0], fp)
     full = grad.loss_and_grad(p, checkpoint_every=5)
     assert np.max(np.abs(full[1] - gt)) > 1e-9 * scale  # a dropped projection would not show here otherwise
+
+
+def _fd_direct(p, h=1e-6):
+    loss = grad.loss_only_direct
+    gt = []
+    for i in range(len(p.params)):
+        a, b = copy.deepcopy(p), copy.deepcopy(p)
+        a.params[i] += h
+        b.params[i] -= h
+        gt.append((loss(a) - loss(b)) / (2 * h))
+    ch = p.channels[0]
+    n_seg = (len(ch.params) - 2) // 2
+    gp = np.zeros((n_seg, 2))
+    for s in range(n_seg):
+        for r in range(2):
+            a, b = copy.deepcopy(p), copy.deepcopy(p)
+            pa, pb = list(ch.params), list(ch.params)
+            pa[2 + 2 * s + r] += h
+            pb[2 + 2 * s + r] -= h
+            a.channels = [Channel("pwc", tuple(pa))]
+            b.channels = [Channel("pwc", tuple(pb))]
+            gp[s, r] = (loss(a) - loss(b)) / (2 * h)
+    return np.array(gt), gp
+
+
+@pytest.mark.parametrize("n_modes,N,ck,secular", [(1, 5, 7, False), (2, 3, 5, False), (1, 5, 4, True)])
+def test_direct_adjoint_matches_central_differences(n_modes, N, ck, secular):
+    """The discrete adjoint of the number-basis RK4 solve (O1) against central differences
+    of O1 itself: thermal jump operators (a and a^dag), H-term parameters (Delta, K; on two
+    modes K_1, K_2, g) and complex piecewise-constant segments, or the secular dissipator."""
+    from workloads.spec import SecularDamping
+    p = _small_control(n_modes=n_modes, N=N)
+    if secular:
+        p.jumps = []
+        p.secular = [SecularDamping(0, 0.6, (0.1, 0.15, 0.2))]
+    loss, gt, gp = grad.loss_and_grad_direct(p, checkpoint_every=ck)
+    assert abs(loss - grad.loss_only_direct(p)) < 1e-13
+    ft, fp = _fd_direct(p)
+    scale = max(np.max(np.abs(ft)), np.max(np.abs(fp)))
+    assert scale > 1e-3
+    assert np.max(np.abs(gt - ft)) < 1e-7 * scale, (gt, ft)
+    assert np.max(np.abs(gp[0] - fp)) < 1e-7 * scale, (gp[0], fp)
+
+
+def test_direct_adjoint_checkpoint_interval_and_transpose():
+    """Checkpoint intervals change nothing; the transposed generator satisfies
+    <B, F(A)> = <F^T(B), A> for random A, B (the identity the pull-back relies on)."""
+    from oracle import fock
+    p = _small_control(n_modes=2, N=3)
+    a = grad.loss_and_grad_direct(p, checkpoint_every=1)
+    b = grad.loss_and_grad_direct(p, checkpoint_every=1000)
+    assert np.max(np.abs(a[1] - b[1])) < 1e-14
+    assert np.max(np.abs(a[2][0] - b[2][0])) < 1e-14
+    model = fock.FockModel(p)
+    rng = np.random.default_rng(1)
+    d = model.dim
+    A = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    B = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    H = model.hamiltonian(0.05, 0.5, p.dt)
+    lhs = np.sum(B * model.adjoint_generator(A, H))
+    rhs = np.sum(grad._direct_transpose(model, B, H) * A)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
