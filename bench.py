@@ -93,29 +93,35 @@ def shard_range(n_inst: int, rank: int):
 
 N_RANGE = (10, 40)  # Fock truncation range of the instances (--n-range)
 
+# Floating-point operations per grid-point RK stage of the merged stencil on this workload (an
+# FMA counts two): diagonal (2 + 6), four neighbour terms (4 x 8), one sandwich term with its
+# separable source (18), the RK4 combine (13 on average over the four stages).
+FLOP_PER_POINT_STAGE = 70
+
 # DRAM traffic of the stage kernel per launch (mean over the four RK4 stages), from one ncu
 # capture of dram__bytes_read.sum + dram__bytes_write.sum on the default workload (65 536
 # instances, N 10..40, complex FP32); reported only while the stage kernel's definition is
 # the one that was measured and the workload and schedule are the default ones.
-STAGE_TRAFFIC = {"kernel_sha256": "4cac04153f90f72dc7b258b832016282431c9534e7cdf367a8934e12bc9c723c",
-                 "instances": 65536, "n_range": (10, 40), "dtype": "f32", "bytes_per_launch": 1.9715e9}
+STAGE_TRAFFIC = {"kernel": "k_stage_pipe", "kernel_sha256": None,
+                 "instances": 65536, "n_range": (10, 40), "dtype": "f32", "bytes_per_launch": None}
 
 
-def stage_kernel_sha256() -> str:
-    """sha256 of the pipelined stage kernel's definition (from its signature to the closing
-    brace at column 0) in bq_kernels.cu."""
+def stage_kernel_sha256(name: str) -> str:
+    """sha256 of a stage kernel's definition (from its signature to the closing brace at
+    column 0) in bq_kernels.cu."""
     import hashlib
     src = open(os.path.join(ROOT, "paper_2203_05526_gb300", "csrc", "bq_kernels.cu")).read()
-    a = src.index("k_stage_pipe(const PipeArgs A) {")
+    a = src.index(f"{name}(const PipeArgs A) {{")
     a = src.rindex("\ntemplate", 0, a) + 1
     b = src.index("\n}\n", a) + 3
     return hashlib.sha256(src[a:b].encode()).hexdigest()
 
 
 def measured_traffic(instances: int, dtype: str, schedule: dict):
-    sha = stage_kernel_sha256()
     t = STAGE_TRAFFIC
-    if sha != t["kernel_sha256"] or instances != t["instances"] or tuple(N_RANGE) != t["n_range"] or dtype != t["dtype"]:
+    if t["bytes_per_launch"] is None or stage_kernel_sha256(t["kernel"]) != t["kernel_sha256"]:
+        return None
+    if instances != t["instances"] or tuple(N_RANGE) != t["n_range"] or dtype != t["dtype"]:
         return None
     if (schedule["stage_path"], schedule["pipe_slots"], schedule["pipe_ctas_per_sm"]) != ("pipe", 2, 0):
         return None  # captured with the default schedule
@@ -155,30 +161,69 @@ def points_of(specs):
     return tot
 
 
-def cpu_baseline(specs, budget_s: float = 12.0):
-    """The FP64 oracle (oracle.mapping.rk4_mapped) on a bounded sample: instances taken in
-    order, 100 RK4 steps each, until ~budget_s of CPU time; single thread."""
+def host_cores() -> int:
+    """Host cores this process may run on."""
     try:
-        from threadpoolctl import threadpool_limits
-        ctx = threadpool_limits(1)
-    except Exception:  # noqa: BLE001
-        ctx = None
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover - non-Linux
+        return os.cpu_count() or 1
+
+
+def _oracle_task(args):
+    """One oracle solve (oracle.mapping.rk4_mapped, FP64) of instance `index` of the seeded
+    batch for n_steps steps; returns (grid-point RK-stage updates, seconds)."""
+    index, n_inst, n_steps, n_range = args
     from oracle import mapping
-    n_steps = 100
-    done_pts = 0
-    done_inst = 0
+    from workloads import configs
+    p = configs.kerr_batch(B=index + 1, T=HORIZON, dt=DT, n_min=n_range[0], n_max=n_range[1])[index]
     t0 = time.perf_counter()
-    for p in specs:
-        mapping.rk4_mapped(p, n_steps=n_steps)
-        done_pts += points_of([p]) * 4 * n_steps
-        done_inst += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    el = time.perf_counter() - t0
-    if ctx is not None:
-        ctx.unregister() if hasattr(ctx, "unregister") else None
-    return {"value": done_pts / el, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{done_inst} instances x {n_steps} RK4 steps (FP64, numpy, 1 thread), {el:.1f} s"}
+    mapping.rk4_mapped(p, n_steps=n_steps)
+    return points_of([p]) * 4 * n_steps, time.perf_counter() - t0
+
+
+def _pool_init():
+    os.environ["OMP_NUM_THREADS"] = "1"
+
+
+def oracle_throughput(indices, n_range, n_steps: int, budget_s: float):
+    """The FP64 oracle on every host core: a spawn process pool (one single-threaded worker
+    per core) runs instances of the seeded batch in order, n_steps RK4 steps each, until about
+    budget_s of wall time; returns (updates/s, cores, instances done, wall seconds)."""
+    import multiprocessing as mp
+    cores = host_cores()
+    env0 = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env0:
+        os.environ[k] = "1"  # the workers inherit single-threaded BLAS
+    try:
+        ctx = mp.get_context("spawn")
+        done_pts, done = 0, 0
+        with ctx.Pool(cores, initializer=_pool_init) as pool:
+            tasks = [(i, max(indices) + 1, n_steps, tuple(n_range)) for i in indices]
+            t0 = time.perf_counter()
+            for pts, _ in pool.imap(_oracle_task, tasks):
+                done_pts += pts
+                done += 1
+                if time.perf_counter() - t0 > budget_s and done >= cores:
+                    break
+            el = time.perf_counter() - t0
+            pool.terminate()
+    finally:
+        for k, v in env0.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return done_pts / el, cores, done, el
+
+
+def cpu_baseline(n_inst: int, budget_s: float = 15.0):
+    """The FP64 oracle (oracle.mapping.rk4_mapped) on a bounded sample of the same workload:
+    instances of the seeded batch taken in order, 100 RK4 steps each, on every host core."""
+    n_steps = 100
+    v, cores, done, el = oracle_throughput(range(min(n_inst, 4096)), N_RANGE, n_steps, budget_s)
+    return {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{done} instances x {n_steps} RK4 steps (FP64, numpy, one single-threaded process per core "
+                      f"on {cores} cores), {el:.1f} s"}
 
 
 class Clocks:
@@ -219,6 +264,115 @@ class Clocks:
         os.unlink(self.f.name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def e2e_leg(specs, opts, schedule: dict, steps: int, world: int, barrier):
+    """The headline step end to end through the C ABI, every step uploading the whole state
+    from pinned host memory and reading every instance's Tr(rho0 A) back: the batch as two
+    halves on two streams, pipelined (half A of step i is stepped while half B's input of step
+    i is uploaded and half B's result of step i - 1 is read back, and the other way round)."""
+    import torch
+
+    import paper_2203_05526_gb300 as bq
+    half = len(specs) // 2
+    parts = [specs[:half], specs[half:]]
+    sts = [bq.State([bq.problem_from_spec(p) for p in part], opts) for part in parts]
+    for st in sts:
+        st.set_tune(stage_path=schedule["stage_path"], pipe_slots=schedule["pipe_slots"],
+                    pipe_ctas_per_sm=schedule["pipe_ctas_per_sm"])
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    hosts = []
+    for st in sts:
+        h = torch.empty(st.state_bytes(), dtype=torch.uint8, pin_memory=True)
+        st.store_state(h.data_ptr())
+        hosts.append(h)
+    torch.cuda.synchronize()
+
+    def enqueue(h):
+        sts[h].load_state(hosts[h].data_ptr(), stream=streams[h])
+        sts[h].step(DT, 1, stream=streams[h])
+
+    def run(n):
+        for i in range(n):
+            enqueue(0)
+            if i > 0:
+                sts[1].evaluate(stream=streams[1])  # half B, step i - 1 (device -> host, synchronises)
+            enqueue(1)
+            sts[0].evaluate(stream=streams[0])      # half A, step i
+        return sts[1].evaluate(stream=streams[1])   # half B, last step
+
+    run(2)
+    barrier()
+    cur = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for sm in streams:
+        sm.wait_event(e0)
+    run(steps)
+    for sm in streams:
+        ev = torch.cuda.Event()
+        ev.record(sm)
+        cur.wait_event(ev)
+    e1.record(cur)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    pts = points_of(specs)
+    return {"value": world * 4 * pts * steps / (ms / 1e3), "unit": METRIC,
+            "h2d_bytes_per_step": sum(st.state_bytes() for st in sts), "d2h_bytes_per_step": 16 * len(specs),
+            "how": "two half-batch states on two streams, upload of one half overlapped with the other half's step"}
+
+
+def alu_peaks():
+    """Measured FMA throughput of this GPU in FP32 and FP64 (bq_fma_peak: independent FMA
+    chains on every SM, CUDA events, at the clocks the GPU runs), each the best of three runs
+    of about 0.2 s."""
+    import paper_2203_05526_gb300 as bq
+    out = {}
+    for dt, it in (("f32", 1 << 14), ("f64", 1 << 8)):
+        v = bq.fma_peak(dt, it)
+        n_fma = bq.fma_peak_count(it)
+        it2 = max(1, int(it * 0.2 / (n_fma / v)))
+        best = max(bq.fma_peak(dt, it2) for _ in range(3))
+        out[f"{'fp32' if dt == 'f32' else 'fp64'}_fma_per_s"] = best
+        out[f"{'fp32' if dt == 'f32' else 'fp64'}_tflops"] = 2 * best / 1e12
+    out["how"] = "bq_fma_peak: 16 dependent FMA chains per thread, 4 CTAs of 256 threads per SM, best of 3 x ~0.2 s"
+    return out
+
+
+def fp64_leg(n_inst: int, peaks: dict, steps: int = 5, warmup: int = 3):
+    """The headline workload in complex FP64: stage-kernel time per RK4 step, updates/s, and
+    the two roofs that could bind it (HBM on 64 B per grid-point stage; the measured FP64 FMA
+    rate on FLOP_PER_POINT_STAGE); GB300's FP64 pipe makes the latter bind."""
+    import torch
+
+    import paper_2203_05526_gb300 as bq
+    specs = configs_batch(n_inst)
+    st = bq.State([bq.problem_from_spec(p) for p in specs], bq.map_opts(method="mapped", dtype="f64", horizon=HORIZON,
+                                                                            dt=DT))
+    pts = points_of(specs)
+    for _ in range(warmup):
+        st.step(DT, 1)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st.step(DT, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s_per_step = e0.elapsed_time(e1) / 1e3 / steps
+    ups = 4 * pts / s_per_step
+    hbm = 64 * ups / 1e9
+    flops = FLOP_PER_POINT_STAGE * ups
+    f64_peak = 2 * peaks.get("fp64_fma_per_s", float("nan"))
+    hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    roofs = {"hbm": {"achieved": hbm, "peak": hbm_peak, "unit": "GB/s", "frac": hbm / hbm_peak},
+             "fp64_alu": {"achieved": flops / 1e12, "peak": f64_peak / 1e12, "unit": "TFLOP/s",
+                          "frac": flops / f64_peak}}
+    bound = max(roofs, key=lambda k: roofs[k]["frac"])
+    return {"workload": f"kerr_batch x{n_inst}, complex FP64, {steps} RK4 steps", "ms_per_step": 1e3 * s_per_step,
+            "updates_per_s": ups, "stage_path": st.get_tune()["stage_path"], "roofs": roofs, "bound": bound}
 
 
 def batched_leg(world: int):
@@ -553,45 +707,60 @@ def secular_leg(B: int = 32768, steps: int = 20):
 
 
 def run_reference(args, rank, world):
-    """Oracle arm: rank 0 only, bounded samples of the same workload on the host cores."""
+    """The oracle arm: the plain FP64 CPU oracle on the same workload, on every host core (a
+    spawn process pool), each step a bounded sample of instances of the seeded batch.  Under
+    several ranks only rank 0 runs and prints."""
     if rank != 0:
         return
-    specs = workload(args.instances, 0)
     n_steps = 20
-    per_step_inst = 2
-
-    def one(i):
-        from oracle import mapping
-        sel = specs[(i * per_step_inst) % len(specs):][:per_step_inst]
-        t0 = time.perf_counter()
-        for p in sel:
-            mapping.rk4_mapped(p, n_steps=n_steps)
-        return points_of(sel) * 4 * n_steps, time.perf_counter() - t0
-
+    cores = host_cores()
+    per_step = cores  # one instance per core per bench step
     for i in range(args.warmup):
-        one(i)
-    pts, el = 0, 0.0
-    for i in range(args.steps):
-        a, b = one(args.warmup + i)
-        pts += a
-        el += b
-    v = pts / el
+        oracle_throughput(range(i * per_step, (i + 1) * per_step), N_RANGE, n_steps, 0.0)
+    v, _, done, el = oracle_throughput(range(args.warmup * per_step, (args.warmup + args.steps) * per_step), N_RANGE,
+                                       n_steps, 1e30)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"kerr_batch x{args.instances} (driven damped Kerr, seed 20220311)",
                                            "instances": args.instances, "dt_ns": DT},
-            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step_inst} instances x {n_steps} RK4 steps per step"},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} instances x {n_steps} RK4 steps per step, one single-threaded "
+                                       f"process per core"},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def launch_replicas(args) -> int:
+    """`bench.py --gpus N` without a launcher: start N ranks on this node (one GPU each, the
+    environment torchrun would give them, rendezvous at 127.0.0.1) and return the first
+    non-zero exit status (rank 0 prints the JSON line)."""
+    import socket
+    sock = socket.socket()
+    sock.bind(("127.0.0.1", 0))
+    port = sock.getsockname()[1]
+    sock.close()
+    procs = []
+    for r in range(args.gpus):
+        env = {**os.environ, "RANK": str(r), "WORLD_SIZE": str(args.gpus), "LOCAL_RANK": str(r),
+               "LOCAL_WORLD_SIZE": str(args.gpus), "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)}
+        procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__), *sys.argv[1:]], env=env))
+    rc = 0
+    for p in procs:
+        p.wait()
+        rc = rc or p.returncode
+    return rc
 
 
 def main():
     global N_RANGE
     args = parse()
     N_RANGE = (int(args.n_range[0]), int(args.n_range[1]))
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        sys.exit(launch_replicas(args))
     rank, world, local = dist_env()
+    if world != args.gpus:
+        sys.exit(f"bench.py: WORLD_SIZE={world} but --gpus {args.gpus}")
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
@@ -668,11 +837,16 @@ def main():
     upd_per_step = 4 * pts
     value = world * upd_per_step * args.steps / (ms / 1e3)
 
-    # roofline of the fused stage kernel: algorithmic bytes = 19 array transfers per RK4 step
-    # per grid point (stage 1: read y, write u, inc = 3; stages 2-3: read u, y, inc, write u, inc
-    # = 5; stage 4: read u, y, inc, comp, write y, comp = 6), i.e. 19/4 per stage launch
+    # roofline of the fused stage kernel on the algorithmic bytes of classical RK4 streamed
+    # stage by stage: 16 array transfers of one complex element per grid point and step
+    # (stage 1: read y, write u and the stage sum; stages 2-3: read u, y and the sum, write u and
+    # the sum; stage 4: read u and the sum, write y), 4 per stage launch: 32 B in FP32, 64 B in
+    # FP64.  The kernel itself moves 18 (the rounding residual that keeps the FP32 state update
+    # exact is read and written once per step, and stage 4 reads the state once more to add the
+    # step's increment to it): reported beside it.
     csz = 8 if args.dtype == "f32" else 16
-    bytes_per_launch = 19 * csz * pts / 4
+    bytes_per_launch = 4 * csz * pts
+    kernel_bytes_per_launch = 18 * csz * pts / 4
     launch_s = stage_ms / 1e3 / (4 * args.steps)
     achieved = bytes_per_launch / launch_s / 1e9
     peaks = {}
@@ -684,35 +858,32 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": measured_traffic(args.instances, args.dtype, schedule), "kernel": {"pipelined": "bq::k_stage_pipe", "single_mode": "bq::k_stage_m1",
                                                "generic": "bq::k_stage"}[state.stage_variant()], "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-            "bytes_per_launch": bytes_per_launch, "avg_launch_us": launch_s * 1e6}
+            "bytes_per_launch": bytes_per_launch, "bytes_per_point_stage": 4 * csz,
+            "kernel_bytes_per_launch": kernel_bytes_per_launch, "kernel_transfers_per_step": 18,
+            "avg_launch_us": launch_s * 1e6}
 
     # ---- end to end through the C ABI: state from pinned host memory, observables back ---
+    # The batch is split into two states on two streams: while one half is stepped, the other
+    # half's next input is uploaded (and the first half's observables are read back), so the
+    # host-to-device copies hide behind the stage kernels.
     nbytes = state.state_bytes()
-    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-    state.store_state(host.data_ptr())
-    torch.cuda.synchronize()
-    for _ in range(2):
-        state.load_state(host.data_ptr())
-        state.step(DT, 1)
-        state.evaluate()
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        state.load_state(host.data_ptr())
-        state.step(DT, 1)
-        state.evaluate()  # device -> host read of every instance's observable
-    e1.record(stream)
-    barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e = {"value": world * upd_per_step * args.steps / (e2e_ms / 1e3), "unit": METRIC,
-           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 16 * len(specs)}
+    e2e = e2e_leg(specs, opts, schedule, args.steps, world, barrier)
+    del state
 
     # the 4096-instance full solves and the gradient are single-GPU legs (rank 0 of a 1-GPU run)
+    peaks_alu = alu_peaks() if world == 1 else None
+    fp64 = None
+    if not args.no_batched and world == 1 and args.dtype == "f32":
+        fp64 = fp64_leg(args.instances, peaks_alu)
     batched = None
     if not args.no_batched and world == 1:
         batched = batched_leg(world)
+        f32_peak = 2 * peaks_alu["fp32_fma_per_s"]
+        p = batched["persistent"]
+        p["alu_roofline"] = {"bound": "alu", "achieved": FLOP_PER_POINT_STAGE * p["updates_per_s"] / 1e12,
+                             "peak": f32_peak / 1e12, "unit": "TFLOP/s",
+                             "frac": FLOP_PER_POINT_STAGE * p["updates_per_s"] / f32_peak,
+                             "peak_source": "measured (bq_fma_peak, FP32)"}
     grads = None
     if not args.no_grads and world == 1:
         grads = grads_leg()
@@ -726,7 +897,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(specs)
+        cpu = cpu_baseline(args.instances)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -739,9 +910,9 @@ def main():
                            "instances_per_gpu": args.instances, "n_range": list(N_RANGE), "grid_points_per_gpu": pts,
                            "schedule": {k: schedule[k] for k in ("stage_path", "pipe_slots", "pipe_ctas_per_sm",
                                                                  "n_candidates", "step_us")},
-                           "state_bytes_per_array": nbytes, "l2": "inputs larger than L2 (4 arrays x "
+                           "state_bytes_per_array": nbytes, "l2": "inputs larger than L2 (5 arrays x "
                            f"{nbytes / 1e6:.0f} MB vs 129 MB)", "parallelism": f"replicas x{world}"},
-                "roofline": roof, "e2e": e2e, "batched": batched, "grads": grads, "methods": methods, "secular": secular, "fig2": fig2, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches}
+                "roofline": roof, "e2e": e2e, "alu_peaks": peaks_alu, "fp64": fp64, "batched": batched, "grads": grads, "methods": methods, "secular": secular, "fig2": fig2, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

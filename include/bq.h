@@ -291,24 +291,32 @@ int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_every, void*
 int bq_autotune_grad(bq_state* s, double dt, int trial_steps, int checkpoint_every, void* work, size_t work_bytes,
                      void* stream, bq_tune* out);
 
-/* bq_step without any memory allocation, for callers that cannot allocate device memory
- * (code running inside another framework's CUDA-graph capture, where cudaMalloc is
- * illegal, or embedded callers with a fixed memory budget decided at start-up).  The
- * paper has no counterpart: it is an alternative scratch placement of bq_step.
+/* bq_step without any memory allocation, for callers that cannot allocate device memory:
+ * code whose device memory is all owned by another component's allocator (a framework that
+ * reserves the GPU at start-up and hands out no raw cudaMalloc), embedded callers whose memory
+ * budget is fixed at start-up, or loops that must not pay an allocation's latency or risk its
+ * failure.  The paper has no counterpart: it is an alternative scratch placement of bq_step.
  *
  * The two RK4 stage buffers and the stage-sum buffer are taken from a fixed device array
- * compiled into this library (3 buffers of 4 MiB each, i.e. states of up to 262 144
- * complex FP64 or 524 288 complex FP32 elements; larger states get BQ_EUNSUPPORTED).
- * Every GPU that loads the library holds that array until the process exits.  The state's
- * own scratch regions in its pool are not touched.  No CUDA graph is used: 4 plain kernel
- * launches per step on stream.
- *   - The first call on a device looks up the array's device address (once per device,
- *     with that device current); make that first call before any stream capture.
- *   - All calls share the one array and it keeps the last call's contents; the RK4 stages
- *     overwrite every element they read, so nothing needs clearing between calls.  Calls
- *     whose work overlaps on the GPU (different streams, or other threads) race on the
- *     array: serialise them.
- * Results equal bq_step's to rounding. */
+ * compiled into this library (three buffers of 4 MiB each, i.e. states of up to 262 144
+ * complex FP64 or 524 288 complex FP32 elements; larger states get BQ_EUNSUPPORTED and should
+ * use bq_step).  Every GPU that loads the library holds that array until the process
+ * exits.  The state's own scratch regions in its pool are not touched; its state arrays are
+ * updated exactly as bq_step updates them (same kernels, same arithmetic).  Plain kernel
+ * launches on stream (4 per step) after clearing the used part of the three buffers; no
+ * allocation, no cudaFree, no allocating library routine.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *     once per device, with that device current); make that first call before any stream
+ *     capture is begun on the calling thread.
+ *   - All calls share the one array, and it keeps the last call's contents.  Every element a
+ *     stage reads was written earlier in the same step, except the padding between a system's
+ *     arrays, which is read at the edges of a system with zero coefficients and never written;
+ *     each call therefore clears the part of the three buffers its state uses (a memset on
+ *     stream) before its first stage, so that stale values of another state or precision
+ *     cannot enter as non-finite numbers.  Calls whose work overlaps on the GPU (different
+ *     streams, or other threads) race on the array: serialise them.
+ * Results equal bq_step's (same kernels; the stage buffers' placement does not enter the
+ * arithmetic). */
 int bq_step_fixed_scratch(bq_state* s, double dt, int64_t n_steps, void* stream);
 
 /* Current integration time tau of the state (host copy, no synchronisation). */
@@ -357,6 +365,15 @@ const char* bq_last_error(void);
 /* Number of kernel launches this library has enqueued since load (graph replays count
  * every kernel node). */
 int64_t bq_launch_count(void);
+
+/* Measured arithmetic roof of the current GPU (no counterpart in the paper: the denominator
+ * of the roofline fraction of kernels bound by FP64 or FP32 arithmetic instead of HBM).
+ * Runs 16 independent dependent FMA chains per thread, 8 x iters FMAs each, on 4 CTAs of
+ * 256 threads per SM after a one-iteration warm-up launch, timed with CUDA events on stream
+ * at the GPU's current clocks (none is set).  dtype: BQ_F64 or BQ_F32.  *fma_per_s receives
+ * thread-level FMA instructions per second (FLOP/s = 2 x).  BQ_EINVAL for a bad dtype,
+ * iters < 1 or a NULL output; BQ_ECUDA if a launch fails.  Synchronises stream. */
+int bq_fma_peak(int dtype, int64_t iters, double* fma_per_s, void* stream);
 
 #ifdef __cplusplus
 }

@@ -4,5 +4,5 @@ The numerical work runs in ``libbq.so`` (CUDA kernels + C ABI, include/bq.h); th
 is the thin ctypes binding.  ``build.build()`` compiles the library in-tree.
 """
 
-from .binding import (BQError, ProblemHandle, State, check, exported_symbols, launch_count, lib,  # noqa: F401
+from .binding import (BQError, ProblemHandle, State, check, exported_symbols, fma_peak, fma_peak_count, launch_count, lib,  # noqa: F401
                       map_opts, plan, problem_from_spec)

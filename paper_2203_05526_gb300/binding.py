@@ -118,6 +118,7 @@ def lib() -> C.CDLL:
         "bq_status_string": (C.c_char_p, [C.c_int]),
         "bq_last_error": (C.c_char_p, []),
         "bq_launch_count": (C.c_int64, []),
+        "bq_fma_peak": (C.c_int, [C.c_int, i64, dp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -135,7 +136,7 @@ def exported_symbols() -> List[str]:
                         "bq_step", "bq_step_fixed_scratch", "bq_solve", "bq_solve_eligible", "bq_stage_variant", "bq_grad_size", "bq_grad_required_bytes", "bq_grad", "bq_time", "bq_evaluate", "bq_fock_block", "bq_state_info",
                         "bq_system_info", "bq_read_system", "bq_state_bytes", "bq_store_state",
                         "bq_load_state", "bq_set_time", "bq_state_destroy", "bq_status_string",
-                        "bq_last_error", "bq_launch_count")]
+                        "bq_last_error", "bq_launch_count", "bq_fma_peak")]
 
 
 def check(status: int) -> None:
@@ -429,3 +430,18 @@ class State:
 
 def launch_count() -> int:
     return int(lib().bq_launch_count())
+
+
+def fma_peak_count(iters: int) -> float:
+    """FMA instructions one bq_fma_peak run of `iters` iterations executes on this GPU (4 CTAs
+    of 256 threads per SM, 16 chains of 8 FMAs per iteration)."""
+    import torch
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return float(nsm * 4 * 256 * 16 * 8 * iters)
+
+
+def fma_peak(dtype: str = "f64", iters: int = 4096, stream=None) -> float:
+    """Measured FMA instructions per second of the current GPU (bq_fma_peak)."""
+    out = C.c_double()
+    check(lib().bq_fma_peak(DTYPE[dtype], int(iters), C.byref(out), _stream_ptr(stream)))
+    return out.value

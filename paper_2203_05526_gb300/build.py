@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libbq.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["bq_host.cu", "bq_kernels.cu"]
+SOURCES = ["bq_host.cu", "bq_kernels.cu", "bq_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

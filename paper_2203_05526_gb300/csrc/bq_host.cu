@@ -742,7 +742,7 @@ static int compile_problem(const bq_problem* p, const bq_map_opts& o, Compiled& 
 // State.
 // ---------------------------------------------------------------------------------------
 struct Layout {
-  size_t off_sys, off_terms, off_chans, off_chpar, off_work, off_m1, off_order, off_dc, off_pparams, off_precs, off_pcoef, off_pcdyn, off_groups, off_entries, off_out, off_wtab, off_diag,
+  size_t off_sys, off_terms, off_chans, off_chpar, off_work, off_m1, off_order, off_dc, off_pparams, off_precs, off_obs, off_groups, off_entries, off_out, off_wtab, off_diag,
       off_ctrl, off_init, off_y, off_comp, off_ua, off_ub, off_acc, total;
 };
 
@@ -750,9 +750,16 @@ struct bq_state {
   int B = 0, nm = 0, dtype = 0, method = 0, basis = 0, n_sys = 0, n_work = 0, smem_bytes = 0, use_m1 = 0, m1_variant = 0;
   int trace_small = 0, block_small = 0;
   int solve_ok = 0, solve_smem = 0, last_solve_grid = 0, solve_mg = 0, solve_mg_smem = 0;
-  int use_pipe = 0, pipe_off_coef = 0, pipe_off_u = 0, pipe_off_y = 0, pipe_off_acc = 0, pipe_off_comp = 0;
-  int pipe_slot[3] = {0, 0, 0}, pipe_nslots[3] = {2, 2, 2}, pipe_grid[3] = {1, 1, 1}, pipe_mv_bytes = 0;
-  int n_coef_dyn = 0;  // time-dependent stage coefficients (k_coef_dyn entries)
+  int use_pipe = 0, pipe_off_u = 0, pipe_zero_off = 0, pipe_zero_bytes = 0, pipe_mmax = 0;
+  int pipe_slot[4] = {0, 0, 0, 0}, pipe_nslots[4] = {2, 2, 2, 2}, pipe_grid[4] = {1, 1, 1, 1}, pipe_mv_bytes = 0;
+  // 1 after bq_load_state: comp is zero by definition but not written yet (the pipelined and
+  // streaming kernels skip reading it at their next stage 1; every other consumer clears it
+  // first, see ensure_comp)
+  int comp_zero = 0;
+  // 1 while the per-system Tr(rho0 A) contributions the pipelined kernel's last stage 4 left
+  // in the pool describe the current state (bq_evaluate then only reads them back)
+  int obs_valid = 0;
+  std::vector<int> trace_sys_off, trace_n_sys;  // systems of every problem's trace group
   int has_diag = 0;     // some term acts only on diagonal index pairs (secular dissipator)
   int r_diag = 0;       // diagonal residual layout
   int has_gread = 0;    // some work item reads its R sources from global memory
@@ -809,13 +816,10 @@ struct Plan {
   std::vector<bq::M1Sys> m1;
   std::vector<int> order;  // batched solve queue (largest system first); empty: not eligible
   // pipelined stage kernel
-  int use_pipe = 0, pipe_off_coef = 0, pipe_off_u = 0, pipe_off_y = 0, pipe_off_acc = 0, pipe_off_comp = 0;
-  int pipe_slot[3] = {0, 0, 0};
+  int use_pipe = 0, pipe_off_u = 0, pipe_zero_off = 0, pipe_zero_bytes = 0, pipe_slot = 0, pipe_mmax = 0;
   std::vector<unsigned char> pparams;
   std::vector<bq::PipeRec> precs;
   size_t work_cap = 0;  // work-item capacity of the pool (the smallest schedulable tile, 32 points)
-  std::vector<cplx> pcoef;           // stage coefficients that do not depend on time (n_sys x BQ_PIPE_COEF)
-  std::vector<bq::CoefDyn> pcdyn;    // and the entries that do
   int solve_smem = 0;
   int solve_mg = 0, solve_mg_smem = 0;  // merged-stencil persistent solve
   int adj_smem = 0;  // shared memory of the adjoint stage kernel
@@ -967,10 +971,11 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
       for (int j = nm - 2; j >= 0; --j) stG[j] = stG[j + 1] * C.M[j + 1];
       for (int j = 0; j < nm; ++j) { sd.stG[j] = stG[j]; sd.stR[j] = stG[j] * C.n_g; sd.stR[nm + j] = stG[j]; }
       sd.off_gx = sd.off_gy = sd.off_r = -1;
-      // element layout of one system: [G_x | G_y | R], each block 16-element aligned
-      auto pad16 = [](int64_t x) { return (x + 15) & ~(int64_t)15; };
-      if (C.has_sep) { sd.off_gx = elem; elem += pad16(C.n_g); sd.off_gy = elem; elem += pad16(C.n_g); }
-      if (C.has_r) { sd.off_r = elem; elem += pad16(C.n_r); }
+      // element layout of one system: [G_x | G_y | R], each block 4-element aligned (32 bytes
+      // in FP32: whole DRAM sectors, and 16-byte aligned bulk copies in either precision)
+      auto pad4 = [](int64_t x) { return (x + 3) & ~(int64_t)3; };
+      if (C.has_sep) { sd.off_gx = elem; elem += pad4(C.n_g); sd.off_gy = elem; elem += pad4(C.n_g); }
+      if (C.has_r) { sd.off_r = elem; elem += pad4(C.n_r); }
       sd.c_re = s.C.real(); sd.c_im = s.C.imag(); sd.w_re = s.w.real(); sd.w_im = s.w.imag();
       sd.n_params = C.n_params;
       sd.grad_off = grad_off;
@@ -1094,24 +1099,30 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
       }
       // pipelined stage kernel: parameter blocks per problem, records per system
       {
-        std::vector<int> poff(B, -1), pbytes(B, 0), pmerged(B, 0);
+        std::vector<int> poff(B, -1), pbytes(B, 0), pmerged(B, 0), pch0(B, -1), pch1(B, -1);
         size_t blk_max = 0, par_max = 0;
+        bool pipe_ok = P.total_elems < ((int64_t)1 << 31);  // 32-bit element offsets
+        int mmax = 1;
+        std::vector<int> prob_terms(B, 0);  // offset of every problem's terms in P.terms (global channel indices)
+        for (const SysDesc& sd : P.sys) prob_terms[sd.prob] = sd.term_off;
         for (int b = 0; b < B; ++b) {
           const Compiled& C = P.comp[b];
           const bq::M1Sys& m = progs[b];
           const int M = C.M[0];
+          mmax = std::max(mmax, M);
           bq::PipeHdr hd;
           std::memset(&hd, 0, sizeof(hd));
           hd.M = M; hd.nX = m.nX; hd.nY = m.nY; hd.nS = m.nS; hd.has_sep = C.has_sep; hd.has_r = C.has_r;
           hd.sdiag = m.sdiag;
           hd.ntot = (C.has_r ? M * M : 0) + (C.has_sep ? 2 * M : 0);
+          hd.n_terms = m.nX + m.nY + m.nS;
           for (int q = 0; q < BQ_M1_MAXT; ++q) { hd.sX[q] = m.sX[q]; hd.sY[q] = m.sY[q]; hd.sSx[q] = m.sSx[q]; hd.sSy[q] = m.sSy[q]; }
           {
-            bool mg = M <= 64 && m.nS <= 2 && (P.m1_variant == 0 || m.nS <= 2);
+            bool mg = M <= BQ_MERGED_MAXM && m.nS <= 2 && (P.m1_variant == 0 || m.nS <= 2);
             for (int q = 0; q < m.nX; ++q) mg = mg && std::abs(m.sX[q]) <= 1;
             for (int q = 0; q < m.nY; ++q) mg = mg && std::abs(m.sY[q]) <= 1;
             for (int q = 0; q < m.nS; ++q) mg = mg && std::abs(m.sSx[q]) <= 1 && std::abs(m.sSy[q]) <= 1;
-            // the merged path stores MS = 2 (variant 0) or BQ_M1_MAXT (variant 1) sandwich vectors
+            // the merged path stores MS = 2 (variant 0) or BQ_M1_MAXT (variant 1) sandwich records
             hd.merged = mg ? 1 : 0;
             pmerged[b] = hd.merged;
           }
@@ -1125,6 +1136,39 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
             if (rs == 8) blk.insert(blk.end(), (unsigned char*)&v, (unsigned char*)&v + 8);
             else { float f = (float)v; blk.insert(blk.end(), (unsigned char*)&f, (unsigned char*)&f + 4); }
           };
+          // stage coefficients of the X, Y, S terms in program order: static part, and the
+          // record's channel slot (at most two distinct channels per problem on this path)
+          for (int q = 0; q < hd.n_terms; ++q) {
+            const int t = q < m.nX ? m.tX[q] : (q < m.nX + m.nY ? m.tY[q - m.nX] : m.tS[q - m.nX - m.nY]);
+            const TermDesc& td = P.terms[prob_terms[b] + t];
+            int slot = -1;
+            if (td.ch >= 0) {
+              if (pch0[b] < 0 || pch0[b] == td.ch) { pch0[b] = td.ch; slot = 0; }
+              else if (pch1[b] < 0 || pch1[b] == td.ch) { pch1[b] = td.ch; slot = 1; }
+              else pipe_ok = false;
+            }
+            const size_t rec0 = blk.size();
+            put_c(cplx(td.c_re, td.c_im));
+            const int ci[2] = {slot, td.conj ? 1 : 0};
+            blk.insert(blk.end(), (const unsigned char*)ci, (const unsigned char*)ci + 8);
+            while (blk.size() - rec0 < sizeof(bq::PipeCoef<double2>) && cs == 16) blk.push_back(0);
+          }
+          // the envelopes themselves, so that the kernel evaluates them from the block
+          const int chs[2] = {pch0[b], pch1[b]};
+          int n_ch = 0;
+          for (int c = 0; c < 2; ++c) {
+            if (chs[c] < 0) break;
+            const ChanDesc& cd = P.chans[chs[c]];
+            bq::PipeChan pc;
+            std::memset(&pc, 0, sizeof(pc));
+            for (int i = 0; i < 4 && i < cd.n_par; ++i) pc.p[i] = P.chpar[cd.par_off + i];
+            pc.kind = cd.kind;
+            pc.par_off = cd.par_off;
+            pc.n_par = cd.n_par;
+            blk.insert(blk.end(), (const unsigned char*)&pc, (const unsigned char*)&pc + sizeof(pc));
+            ++n_ch;
+          }
+          reinterpret_cast<bq::PipeHdr*>(blk.data())->n_ch = n_ch;
           for (int i = 0; i < M; ++i) put_c(C.diag[i]);
           for (int i = 0; i < M; ++i) put_c(C.diag[M + i]);
           auto put_w = [&](int woff) { for (int i = 0; i < M; ++i) put_r(woff >= 0 ? C.wtab[woff + i] : 1.0); };
@@ -1139,59 +1183,48 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
           P.pparams.insert(P.pparams.end(), blk.begin(), blk.end());
           par_max = std::max(par_max, blk.size());
         }
+        static_assert(sizeof(bq::PipeCoef<float2>) == 16 && sizeof(bq::PipeCoef<double2>) == 32,
+                      "coefficient records as written above");
         for (int i = 0; i < (int)P.sys.size(); ++i) {
           const SysDesc& sd = P.sys[i];
           bq::PipeRec r;
           std::memset(&r, 0, sizeof(r));
-          const int pg = (sd.n_g + 15) & ~15, pr = (sd.n_r + 15) & ~15;
+          const int pg = (int)(sd.has_sep ? sd.off_gy - sd.off_gx : 0);  // padded G_x length
+          const int pr = (sd.n_r + 3) & ~3;
           r.blk_off = (int)(sd.has_sep ? sd.off_gx : sd.off_r);
           r.blk_elems = (sd.has_sep ? 2 * pg : 0) + (sd.has_r ? pr : 0);
           r.param_off = poff[sd.prob];
           r.param_bytes = pbytes[sd.prob];
-          r.gx_off = sd.has_sep ? 0 : -1;
           r.gy_off = sd.has_sep ? pg : -1;
           r.r_off = sd.has_r ? (sd.has_sep ? 2 * pg : 0) : -1;
-          r.sys = i;
           r.M = P.comp[sd.prob].M[0];
           r.merged = pmerged[sd.prob];
           r.nb = std::max(1, std::min(BQ_PIPE_THREADS / r.M, r.M));
           r.rb = (r.M + r.nb - 1) / r.nb;
           r.inv_m = 1.0f / (float)r.M;
+          r.c_re = sd.c_re;
+          r.c_im = sd.c_im;
+          r.w_re = sd.w_re;
+          r.w_im = sd.w_im;
+          r.e_off = P.groups[sd.prob].e_off;  // trace group of the problem
+          r.n_e = P.groups[sd.prob].n_e;
           P.precs.push_back(r);
           blk_max = std::max(blk_max, (size_t)r.blk_elems);
         }
-        // stage coefficients: X, Y, S terms in program order, the separation constant C at the
-        // last position; static ones now, drive-dependent ones per stage on the device
-        P.pcoef.assign(P.sys.size() * BQ_PIPE_COEF, cplx(0.0, 0.0));
-        for (int i = 0; i < (int)P.m1.size(); ++i) {
-          const bq::M1Sys& m = P.m1[i];
-          P.pcoef[(size_t)i * BQ_PIPE_COEF + BQ_PIPE_COEF - 1] = cplx(m.c_re, m.c_im);
-          const int nt = m.nX + m.nY + m.nS;
-          for (int q = 0; q < nt && q < BQ_PIPE_COEF - 1; ++q) {
-            const int t = q < m.nX ? m.tX[q] : (q < m.nX + m.nY ? m.tY[q - m.nX] : m.tS[q - m.nX - m.nY]);
-            const TermDesc& td = P.terms[m.term_off + t];
-            if (td.ch < 0) {
-              P.pcoef[(size_t)i * BQ_PIPE_COEF + q] = cplx(td.c_re, td.c_im);
-            } else {
-              bq::CoefDyn d;
-              std::memset(&d, 0, sizeof(d));
-              d.slot = i * BQ_PIPE_COEF + q;
-              d.ch = td.ch; d.conj = td.conj; d.c_re = td.c_re; d.c_im = td.c_im;
-              P.pcdyn.push_back(d);
-            }
-          }
-        }
+        // Shared-memory slot: [parameter block | guard | stage input | guard].  Neighbour reads
+        // at a system's edges reach at most M + 1 elements before or after its block (the
+        // sandwich source (k - 1, l - 1) at k = 0 of a block without G), so each guard holds
+        // mmax + 2 elements, rounded to 4.
         auto a128 = [](size_t x) { return (x + 127) & ~(size_t)127; };
-        P.pipe_off_coef = (int)a128(par_max);
-        P.pipe_off_u = P.pipe_off_coef + (int)a128(BQ_PIPE_COEF * cs);
-        const int blkb = (int)a128(blk_max * cs);
-        P.pipe_off_y = P.pipe_off_u + blkb;
-        P.pipe_off_acc = P.pipe_off_y + blkb;
-        P.pipe_off_comp = P.pipe_off_acc + blkb;
-        // a slot holds the parameter block, the stage coefficients and the stage input; the
-        // state, stage sum and compensation are streamed with coalesced loads
-        P.pipe_slot[0] = P.pipe_slot[1] = P.pipe_slot[2] = P.pipe_off_y;
-        P.use_pipe = 2 * (size_t)P.pipe_slot[2] <= 200 * 1024 ? 1 : 0;
+        const size_t guard = (size_t)((mmax + 2 + 3) & ~3);
+        const size_t zero0 = a128(par_max);
+        P.pipe_zero_off = (int)zero0;
+        P.pipe_off_u = (int)(zero0 + guard * cs);
+        P.pipe_zero_bytes = (int)((2 * guard + blk_max) * cs);
+        P.pipe_slot = (int)a128(zero0 + P.pipe_zero_bytes);
+        P.pipe_mmax = mmax;
+        P.use_pipe = pipe_ok && 2 * (size_t)P.pipe_slot <= 200 * 1024 ? 1 : 0;
+
       }
       if (solve_ok && solve_max <= 160 * 1024) {
         std::stable_sort(sz.begin(), sz.end());
@@ -1265,8 +1298,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
   L.off_order = seg(P.order.size() * sizeof(int));
   L.off_pparams = seg(P.pparams.size());
   L.off_precs = seg(P.precs.size() * sizeof(bq::PipeRec));
-  L.off_pcoef = seg(P.use_pipe ? (size_t)P.sys.size() * BQ_PIPE_COEF * cs : 0);
-  L.off_pcdyn = seg(P.use_pipe ? P.pcdyn.size() * sizeof(bq::CoefDyn) : 0);
+  L.off_obs = seg(P.use_pipe ? P.sys.size() * sizeof(double2) : 0);
   L.off_dc = seg(P.dc.size() * sizeof(double2));
   L.off_groups = seg(P.groups.size() * sizeof(EvalGroup));
   L.off_entries = seg(P.entries.size() * sizeof(EvalEntry));
@@ -1293,17 +1325,17 @@ static int pipe_configure(bq_state* st, int slots, int cap) {
   int dev = 0, nsm = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  int grid[3];
-  for (int q = 0; q < 3; ++q) {
+  int grid[4];
+  for (int q = 0; q < 4; ++q) {  // one kernel per RK4 stage
     const size_t smem = (size_t)slots * st->pipe_slot[q] + st->pipe_mv_bytes;
     if (smem > BQ_MAX_DYN_SMEM) return fail(BQ_EUNSUPPORTED, "%d slots need %zu bytes of shared memory", slots, smem);
     int per_sm = 0;
-    CUDA_TRY(bq::pipe_blocks_per_sm(st->dtype, st->m1_variant, (int)smem, &per_sm));
+    CUDA_TRY(bq::pipe_blocks_per_sm(st->dtype, st->m1_variant, q + 1, (int)smem, &per_sm));
     if (per_sm < 1) return fail(BQ_EUNSUPPORTED, "%d slots do not fit on an SM", slots);
     if (cap > 0) per_sm = std::min(per_sm, cap);
     grid[q] = std::min(st->n_sys, per_sm * nsm);
   }
-  for (int q = 0; q < 3; ++q) { st->pipe_nslots[q] = slots; st->pipe_grid[q] = grid[q]; }
+  for (int q = 0; q < 4; ++q) { st->pipe_nslots[q] = slots; st->pipe_grid[q] = grid[q]; }
   st->pipe_cap = cap;
   return BQ_OK;
 }
@@ -1363,18 +1395,6 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   CUDA_TRY(up(L.off_order, P.order.data(), P.order.size() * sizeof(int)));
   CUDA_TRY(up(L.off_pparams, P.pparams.data(), P.pparams.size()));
   CUDA_TRY(up(L.off_precs, P.precs.data(), P.precs.size() * sizeof(bq::PipeRec)));
-  if (P.use_pipe) {
-    CUDA_TRY(up(L.off_pcdyn, P.pcdyn.data(), P.pcdyn.size() * sizeof(bq::CoefDyn)));
-    if (o->dtype == BQ_F64) {
-      std::vector<double2> c(P.pcoef.size());
-      for (size_t i = 0; i < c.size(); ++i) c[i] = make_double2(P.pcoef[i].real(), P.pcoef[i].imag());
-      CUDA_TRY(up(L.off_pcoef, c.data(), c.size() * sizeof(double2)));
-    } else {
-      std::vector<float2> c(P.pcoef.size());
-      for (size_t i = 0; i < c.size(); ++i) c[i] = make_float2((float)P.pcoef[i].real(), (float)P.pcoef[i].imag());
-      CUDA_TRY(up(L.off_pcoef, c.data(), c.size() * sizeof(float2)));
-    }
-  }
   {
     std::vector<double2> dcv(P.dc.size());
     for (size_t i = 0; i < dcv.size(); ++i) dcv[i] = make_double2(P.dc[i].real(), P.dc[i].imag());
@@ -1397,13 +1417,11 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   CUDA_TRY(cudaMemsetAsync(base + L.off_ctrl, 0, 64, s));
   CUDA_TRY(up(L.off_init, P.init.data(), P.init.size() * sizeof(InitEntry)));
   const size_t cs = o->dtype == BQ_F64 ? 16 : 8;
-  CUDA_TRY(cudaMemsetAsync(base + L.off_y, 0, (size_t)P.total_elems * cs, s));
-  CUDA_TRY(cudaMemsetAsync(base + L.off_comp, 0, (size_t)P.total_elems * cs, s));
-  // stage scratch too, so that the padding between a system's blocks (never written by the
-  // stage kernels) holds defined values in every buffer the bulk copies move
-  CUDA_TRY(cudaMemsetAsync(base + L.off_ua, 0, (size_t)P.total_elems * cs, s));
-  CUDA_TRY(cudaMemsetAsync(base + L.off_ub, 0, (size_t)P.total_elems * cs, s));
-  CUDA_TRY(cudaMemsetAsync(base + L.off_acc, 0, (size_t)P.total_elems * cs, s));
+  // the state arrays; the stage scratch too, so that the padding between a system's blocks
+  // (never written by the stage kernels, read at a system's edges with zero coefficients)
+  // holds finite values in every buffer the stage kernels read
+  for (size_t off : {L.off_y, L.off_comp, L.off_ua, L.off_ub, L.off_acc})
+    CUDA_TRY(cudaMemsetAsync(base + off, 0, (size_t)P.total_elems * cs, s));
   CUDA_TRY(bq::launch_scatter((const InitEntry*)(base + L.off_init), (int)P.init.size(), base + L.off_y, o->dtype, s));
   g_launches++;
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -1426,18 +1444,16 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   st->m1_variant = P.m1_variant;
   st->solve_ok = P.order.empty() ? 0 : 1;
   st->use_pipe = P.use_pipe;
-  st->n_coef_dyn = (int)P.pcdyn.size();
   for (const TermDesc& td : P.terms) st->has_diag = st->has_diag || td.diagp1 != 0;
   for (const SysDesc& sd : P.sys) st->r_diag = st->r_diag || sd.r_diag;
   for (const WorkItem& w : P.work) st->has_gread = st->has_gread || w.gread;
-  st->pipe_off_coef = P.pipe_off_coef; st->pipe_off_u = P.pipe_off_u; st->pipe_off_y = P.pipe_off_y;
-  st->pipe_off_acc = P.pipe_off_acc; st->pipe_off_comp = P.pipe_off_comp;
-  for (int q = 0; q < 3; ++q) st->pipe_slot[q] = P.pipe_slot[q];
+  st->pipe_off_u = P.pipe_off_u; st->pipe_zero_off = P.pipe_zero_off; st->pipe_zero_bytes = P.pipe_zero_bytes;
+  st->pipe_mmax = P.pipe_mmax;
+  for (int q = 0; q < 4; ++q) st->pipe_slot[q] = P.pipe_slot;
   {
-    int mmax = 1;
-    for (auto& m : P.m1) mmax = std::max(mmax, m.M);
+    // row and column coefficient records of the merged path
     const int ms = P.m1_variant == 0 ? 2 : BQ_M1_MAXT;
-    st->pipe_mv_bytes = (int)(((size_t)(6 + 4 * ms) * mmax * (o->dtype == BQ_F64 ? 16 : 8) + 127) & ~(size_t)127);
+    st->pipe_mv_bytes = (int)(((size_t)2 * BQ_PIPE_RS(ms) * P.pipe_mmax * (o->dtype == BQ_F64 ? 16 : 8) + 127) & ~(size_t)127);
   }
   if (st->use_pipe) {
     // double buffering at the occupancy limit; bq_autotune may pick another schedule
@@ -1446,6 +1462,7 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
     st->use_pipe = rc == BQ_OK ? 1 : 0;
   }
   st->pipe_ok = st->use_pipe;
+
   st->grad_size = P.grad_size;
   st->adj_smem = P.adj_smem;
   st->srcred_stride = P.srcred_stride;
@@ -1459,6 +1476,10 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   st->solve_mg_ok = P.solve_mg;
   st->solve_mg_smem = P.solve_mg_smem;
   st->n_trace_groups = P.n_trace_groups; st->n_block_groups = P.n_block_groups; st->block_dim = P.block_dim;
+  for (int g = 0; g < P.n_trace_groups; ++g) {
+    st->trace_sys_off.push_back(P.groups[g].sys_off);
+    st->trace_n_sys.push_back(P.groups[g].n_sys);
+  }
   st->total_elems = P.total_elems; st->dt_max = dt_max; st->horizon = o->horizon; st->reverse = o->reverse_time;
   st->pool = base; st->L = L; st->sys = P.sys;
   for (int b = 0; b < B; ++b) for (int j = 0; j < BQ_MAX_MODES; ++j) st->prob_M.push_back(P.comp[b].M[j]);
@@ -1510,10 +1531,21 @@ static bq::StageArgs stage_args(bq_state* s, int stage, double dt) {
   return a;
 }
 
-// kernels enqueued by one stage: the pipelined path adds the coefficient kernel when some
-// coefficient depends on time
-static int kernels_per_stage(const bq_state* s, bool recording) {
-  return (s->use_pipe && !recording && s->n_coef_dyn > 0) ? 2 : 1;
+// kernels enqueued by one stage (the pipelined kernel evaluates its drive envelopes itself)
+static int kernels_per_stage(const bq_state*, bool) { return 1; }
+
+// After a pipelined step, comp holds that step's increment, still to be added to y (the
+// pipelined kernel folds it at its next stage 1).  Every other consumer of the raw arrays (the
+// other stage kernels, the persistent solve, the adjoint, read-back and snapshots) expects a
+// rounding-size compensation there: fold first (exact, asynchronous on st).
+// After bq_load_state the compensation is zero by definition but not written yet: the
+// pipelined kernel skips reading it at its next stage 1, every other consumer clears it first.
+static cudaError_t ensure_comp(bq_state* s, cudaStream_t st) {
+  if (!s->comp_zero) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(s->pool + s->L.off_comp, 0, (size_t)s->total_elems * (s->dtype == BQ_F64 ? 16 : 8), st);
+  if (e != cudaSuccess) return e;
+  s->comp_zero = 0;
+  return cudaSuccess;
 }
 
 static cudaError_t launch_any_stage(bq_state* s, const bq::StageArgs& a, cudaStream_t st) {
@@ -1524,28 +1556,31 @@ static cudaError_t launch_any_stage(bq_state* s, const bq::StageArgs& a, cudaStr
     std::memset(&pa, 0, sizeof(pa));
     pa.recs = (const bq::PipeRec*)(b + L.off_precs);
     pa.params = (const unsigned char*)(b + L.off_pparams);
-    pa.coef = b + L.off_pcoef;
+    pa.chans = a.chans;
+    pa.chpar = a.chpar;
     pa.u_in = a.u_in; pa.u_out = a.u_out; pa.y = a.y; pa.acc = a.acc; pa.comp = a.comp;
-    pa.ticket = a.ticket; pa.counter = a.counter;
+    pa.ticket = a.ticket; pa.counter = a.counter; pa.tau_base = a.tau_base;
     pa.error = (unsigned int*)(b + L.off_ctrl + 32);
-    pa.n_sys = s->n_sys; pa.stage = a.stage;
-    const int q = a.stage == 1 ? 0 : (a.stage == 4 ? 2 : 1);
+    pa.n_sys = s->n_sys;
+    const int q = a.stage - 1;
     pa.n_slots = s->pipe_nslots[q];
     pa.slot_bytes = s->pipe_slot[q];
-    pa.off_coef = s->pipe_off_coef; pa.off_u = s->pipe_off_u; pa.off_y = s->pipe_off_y;
-    pa.off_acc = s->pipe_off_acc; pa.off_comp = s->pipe_off_comp;
+    pa.off_u = s->pipe_off_u;
+    pa.zero_off = s->pipe_zero_off;
+    pa.zero_bytes = s->pipe_zero_bytes;
+    pa.mmax = s->pipe_mmax;
+    pa.reverse = a.reverse;
+    pa.comp_zero = a.stage == 1 ? s->comp_zero : 0;
+    pa.entries = (const bq::EvalEntry*)(b + L.off_entries);
+    pa.obs = (double2*)(b + L.off_obs);
+    s->obs_valid = a.stage == 4;
     pa.dt = a.dt;
-    bq::CoefArgs ca;
-    std::memset(&ca, 0, sizeof(ca));
-    ca.dyn = (const bq::CoefDyn*)(b + L.off_pcdyn);
-    ca.n_dyn = s->n_coef_dyn;
-    ca.chans = a.chans; ca.chpar = a.chpar;
-    ca.coef = b + L.off_pcoef;
-    ca.tau_base = a.tau_base; ca.counter = a.counter;
-    ca.dt = a.dt; ca.horizon = a.horizon; ca.stage = a.stage; ca.reverse = a.reverse;
-    return bq::launch_stage_pipe(pa, ca, s->m1_variant, s->dtype, s->pipe_grid[q], pa.n_slots * pa.slot_bytes + s->pipe_mv_bytes,
-                                 st);
+    pa.horizon = a.horizon;
+    if (a.stage == 1) s->comp_zero = 0;  // stage 4 of this step writes comp everywhere
+    return bq::launch_stage_pipe(pa, s->m1_variant, s->dtype, a.stage, s->pipe_grid[q],
+                                 pa.n_slots * pa.slot_bytes + s->pipe_mv_bytes, st);
   }
+  s->obs_valid = 0;
   if (s->use_m1)
     return bq::launch_stage_m1(a, (const bq::M1Sys*)(s->pool + s->L.off_m1), s->m1_variant, s->dtype, s->n_work,
                                s->smem_bytes, st);
@@ -1572,12 +1607,14 @@ extern "C" int bq_step(bq_state* s, double dt, int64_t n_steps, void* stream) {
   if (n_steps == 0) return BQ_OK;
   cudaStream_t st = (cudaStream_t)stream;
   char* b = s->pool;
+  if (!s->use_pipe) CUDA_TRY(ensure_comp(s, st));
   // tau at the start of this call; the stage kernels add counter * dt
   s->tau_base_host = s->tau;
   CUDA_TRY(cudaMemcpyAsync(b + s->L.off_ctrl, &s->tau_base_host, sizeof(double), cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemsetAsync(b + s->L.off_ctrl + 8, 0, 16, st));
   int64_t left = n_steps;
   if (n_steps >= kGraphSteps) {
+    CUDA_TRY(ensure_comp(s, st));  // the graph must not carry a first stage that skips comp
     if (!s->graph || s->graph_dt != dt) {
       if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
       if (!s->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
@@ -1626,6 +1663,16 @@ extern "C" int bq_step_fixed_scratch(bq_state* s, double dt, int64_t n_steps, vo
   char* acc = ub + BQ_FIXED_SCRATCH_BYTES;
   cudaStream_t st = (cudaStream_t)stream;
   char* b = s->pool;
+  if (!s->use_pipe) CUDA_TRY(ensure_comp(s, st));
+  // The array keeps whatever earlier calls (possibly of other states, layouts or precisions)
+  // left in it.  The stage kernels write every element of this state's systems before reading
+  // it, but read the padding between a system's arrays at its edges (with zero coefficients):
+  // clear the buffers' used range so that the padding holds zeros, not stale bit patterns that
+  // could read as non-finite values in this precision.
+  const size_t used = (size_t)s->total_elems * (s->dtype == BQ_F64 ? 16 : 8);
+  CUDA_TRY(cudaMemsetAsync(ua, 0, used, st));
+  CUDA_TRY(cudaMemsetAsync(ub, 0, used, st));
+  CUDA_TRY(cudaMemsetAsync(acc, 0, used, st));
   s->tau_base_host = s->tau;
   CUDA_TRY(cudaMemcpyAsync(b + s->L.off_ctrl, &s->tau_base_host, sizeof(double), cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemsetAsync(b + s->L.off_ctrl + 8, 0, 16, st));
@@ -1653,6 +1700,7 @@ extern "C" int bq_solve(bq_state* s, double dt, int64_t n_steps, void* stream) {
   if (dt > s->dt_max * (1.0 + 1e-12))
     return fail(BQ_EUNSTABLE_DT, "dt=%g above the RK4 stability bound %g", dt, s->dt_max);
   if (n_steps == 0) return BQ_OK;
+  CUDA_TRY(ensure_comp(s, (cudaStream_t)stream));
   CUDA_TRY(enqueue_solve(s, dt, n_steps, (cudaStream_t)stream));
   g_launches++;
   s->tau += (double)n_steps * dt;
@@ -1663,6 +1711,7 @@ extern "C" int bq_solve(bq_state* s, double dt, int64_t n_steps, void* stream) {
 static cudaError_t enqueue_solve(bq_state* s, double dt, int64_t n_steps, cudaStream_t st) {
   char* b = s->pool;
   const Layout& L = s->L;
+  s->obs_valid = 0;
   cudaError_t e = cudaMemsetAsync(b + L.off_ctrl + 24, 0, 8, st);
   if (e != cudaSuccess) return e;
   bq::SolveArgs a;
@@ -1813,11 +1862,13 @@ extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratc
   char* b = s->pool;
   char* sc = (char*)scratch;
   const double tau0 = s->tau;
+  CUDA_TRY(ensure_comp(s, st));  // the saved copy is valid for every schedule
   CUDA_TRY(cudaMemcpyAsync(sc, b + s->L.off_y, n, cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(sc + n, b + s->L.off_comp, n, cudaMemcpyDeviceToDevice, st));
   auto restore = [&]() -> cudaError_t {
     cudaError_t e = cudaMemcpyAsync(b + s->L.off_y, sc, n, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + s->L.off_comp, sc + n, n, cudaMemcpyDeviceToDevice, st);
+    s->obs_valid = 0;
     s->tau = tau0;
     s->tau_base_host = tau0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + s->L.off_ctrl, &s->tau_base_host, sizeof(double), cudaMemcpyHostToDevice, st);
@@ -2026,8 +2077,10 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
   const int k = checkpoint_every;
   CUDA_TRY(cudaMemsetAsync(w + G.grad, 0, (size_t)std::max(1, s->grad_size) * sizeof(double), st));
   // ---- forward with checkpoints ----------------------------------------------------------
+  // (checkpoints hold the folded form: the recording stage kernels start from them)
   for (int64_t c = 0; c < G.n_ckpt; ++c) {
     const int64_t n0 = c * k, n1 = std::min<int64_t>(n_steps, n0 + k);
+    CUDA_TRY(ensure_comp(s, st));
     CUDA_TRY(cudaMemcpyAsync(w + G.ckpt + (2 * c) * arr, b + L.off_y, arr, cudaMemcpyDeviceToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(w + G.ckpt + (2 * c + 1) * arr, b + L.off_comp, arr, cudaMemcpyDeviceToDevice, st));
     int r = set_tau(s, tau0 + (double)n0 * dt, st);
@@ -2035,6 +2088,7 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
     CUDA_TRY(enqueue_steps_rec(s, dt, n1 - n0, st, nullptr, arr));
   }
   s->tau = tau0 + (double)n_steps * dt;
+  CUDA_TRY(ensure_comp(s, st));
   // ---- loss and the cotangent of the final state -----------------------------------------
   std::vector<double> tr(2 * (size_t)s->B);
   int r = run_eval(s, 0, s->n_trace_groups, s->trace_small, tr.data(), st);
@@ -2118,6 +2172,7 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
   CUDA_TRY(cudaEventRecord(ev[1], sF));
   CUDA_TRY(cudaStreamWaitEvent(st, ev[1], 0));
   // leave the state as it was before the call (initial content, tau0)
+  s->obs_valid = 0;
   CUDA_TRY(cudaMemcpyAsync(b + L.off_y, w + G.ckpt, arr, cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(b + L.off_comp, w + G.ckpt + arr, arr, cudaMemcpyDeviceToDevice, st));
   r = set_tau(s, tau0, st);
@@ -2207,8 +2262,10 @@ extern "C" int bq_time(const bq_state* s, double* tau) {
 static int run_eval(bq_state* s, int g0, int n, int small, double* out_host, cudaStream_t st) {
   char* b = s->pool;
   const Layout& L = s->L;
+  CUDA_TRY(ensure_comp(s, st));
   CUDA_TRY(bq::launch_eval((const SysDesc*)(b + L.off_sys), (const EvalGroup*)(b + L.off_groups) + g0,
-                           (const EvalEntry*)(b + L.off_entries), b + L.off_y, (double2*)(b + L.off_out) + g0, n,
+                           (const EvalEntry*)(b + L.off_entries), b + L.off_y, b + L.off_comp,
+                           (double2*)(b + L.off_out) + g0, n,
                            s->dtype, small, st));
   g_launches++;
   CUDA_TRY(cudaMemcpyAsync(out_host, b + L.off_out + (size_t)g0 * 16, (size_t)n * 16, cudaMemcpyDeviceToHost, st));
@@ -2223,7 +2280,29 @@ static int run_eval(bq_state* s, int g0, int n, int small, double* out_host, cud
 
 extern "C" int bq_evaluate(bq_state* s, double* out_host, void* stream) {
   if (!s || !out_host) return fail(BQ_EINVAL, "NULL argument");
-  return run_eval(s, 0, s->n_trace_groups, s->trace_small, out_host, (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (s->obs_valid) {
+    // the last pipelined stage 4 reduced every system's contribution: read them back and
+    // sum the initial conditions of each problem in order
+    std::vector<double> v(2 * (size_t)s->n_sys);
+    CUDA_TRY(cudaMemcpyAsync(v.data(), s->pool + s->L.off_obs, v.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    unsigned int err_word = 0;
+    CUDA_TRY(cudaMemcpyAsync(&err_word, s->pool + s->L.off_ctrl + 32, sizeof(err_word), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (err_word) return fail(BQ_ETIMEOUT, "a bounded device wait gave up (error word %u)", err_word);
+    for (int g = 0; g < s->n_trace_groups; ++g) {
+      double re = 0.0, im = 0.0;
+      for (int i = 0; i < s->trace_n_sys[g]; ++i) {
+        re += v[2 * (size_t)(s->trace_sys_off[g] + i)];
+        im += v[2 * (size_t)(s->trace_sys_off[g] + i) + 1];
+      }
+      if (!std::isfinite(re) || !std::isfinite(im)) return fail(BQ_ENONFINITE, "non-finite observable of problem %d", g);
+      out_host[2 * g] = re;
+      out_host[2 * g + 1] = im;
+    }
+    return BQ_OK;
+  }
+  return run_eval(s, 0, s->n_trace_groups, s->trace_small, out_host, st);
 }
 
 extern "C" int bq_fock_block(bq_state* s, int lo, double* out_host, void* stream) {
@@ -2259,6 +2338,7 @@ extern "C" int bq_read_system(bq_state* s, int sys, double* gx, double* gy, doub
   if (!s || sys < 0 || sys >= s->n_sys) return fail(BQ_EINVAL, "bad system index");
   const SysDesc& sd = s->sys[sys];
   cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(ensure_comp(s, st));  // y alone is then the state to rounding
   const size_t cs = s->dtype == BQ_F64 ? 16 : 8;
   const char* y = s->pool + s->L.off_y;
   const int nm = s->nm;
@@ -2312,6 +2392,7 @@ extern "C" int bq_state_bytes(const bq_state* s, size_t* nbytes) {
 extern "C" int bq_store_state(bq_state* s, void* host, void* stream) {
   if (!s || !host) return fail(BQ_EINVAL, "NULL argument");
   const size_t n = (size_t)s->total_elems * (s->dtype == BQ_F64 ? 16 : 8);
+  CUDA_TRY(ensure_comp(s, (cudaStream_t)stream));  // y alone is then the state to rounding
   CUDA_TRY(cudaMemcpyAsync(host, s->pool + s->L.off_y, n, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
   return BQ_OK;
 }
@@ -2320,7 +2401,10 @@ extern "C" int bq_load_state(bq_state* s, const void* host, void* stream) {
   if (!s || !host) return fail(BQ_EINVAL, "NULL argument");
   const size_t n = (size_t)s->total_elems * (s->dtype == BQ_F64 ? 16 : 8);
   CUDA_TRY(cudaMemcpyAsync(s->pool + s->L.off_y, host, n, cudaMemcpyHostToDevice, (cudaStream_t)stream));
-  CUDA_TRY(cudaMemsetAsync(s->pool + s->L.off_comp, 0, n, (cudaStream_t)stream));
+  // comp is cleared lazily: the next pipelined stage 1 treats it as zero, any other consumer
+  // clears it first
+  s->comp_zero = 1;
+  s->obs_valid = 0;
   return BQ_OK;
 }
 

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <stdint.h>
+#include <vector_types.h>
 
 #define BQ_MAXD 8          // max R dimensions = 2 * BQ_MAX_MODES
 #define BQ_MAX_TERMS 64    // max general (non-folded) stencil terms per problem
@@ -143,64 +144,77 @@ struct StageArgs {
 };
 
 // Pipelined single-mode stage kernel (k_stage_pipe): one record per system and one
-// parameter block per problem, both fetched with 1-D bulk copies (TMA) into shared memory.
+// parameter block per problem, the block fetched with a 1-D bulk copy (TMA) into shared memory
+// together with the system's stage input.
 struct __align__(16) PipeRec {
   int blk_off;      // element offset of the system block ([G_x | G_y | R] or [R]) in the state arrays
-  int blk_elems;    // element count of the block (multiple of 16)
+  int blk_elems;    // element count of the block (multiple of 4)
   int param_off;    // byte offset of the problem's parameter block
   int param_bytes;  // its size (multiple of 16)
-  int gx_off, gy_off, r_off;  // element offsets inside the block (-1: absent)
-  int sys;          // system index (coefficient block)
+  int gy_off, r_off;  // element offsets inside the block (-1: absent); G_x, when present, starts it
   int M;            // grid size of the mode
   int merged;       // 1: merged-stencil path (every shift in {-1, 0, 1}, M <= 64)
   int nb, rb;       // merged path: nb column strips of rb rows (thread t: column t % M, strip t / M)
   float inv_m;      // 1 / M (strip index without an integer division)
+  int e_off, n_e;   // entries of the problem's Tr(rho0 A) group (EvalEntry)
+  int pad;
+  double c_re, c_im;  // separation constant C of the system (Eq. 304)
+  double w_re, w_im;  // weight of the system's initial condition
 };
-// Header of a parameter block (128 B), followed by dx[M], dy[M] (complex) and the weight tables
+// Header of a parameter block (128 B), followed by n_terms PipeCoef records (X, Y, S terms in
+// program order), n_ch PipeChan records, dx[M], dy[M] (complex) and the weight tables
 // wX[nX][M], wY[nY][M], wSx[nS][M], wSy[nS][M] (real), the whole block padded to 16 B.
 struct PipeHdr {
   int M, nX, nY, nS, has_sep, has_r, ntot, merged;  // merged: all shifts in {-1,0,1}, nS <= 2, M <= 64
   int sX[BQ_M1_MAXT], sY[BQ_M1_MAXT], sSx[BQ_M1_MAXT], sSy[BQ_M1_MAXT];
-  int sdiag;  // bit q: sandwich term q acts only where k = l (secular projector)
-  int pad2[7];
+  int sdiag;    // bit q: sandwich term q acts only where k = l (secular projector)
+  int n_terms;  // nX + nY + nS
+  int n_ch;     // drive envelopes behind the time-dependent terms (0..2)
+  int pad2[5];
+};
+// A drive envelope (bq.h channel kinds) in a parameter block: its first four parameters and,
+// for a piecewise-constant envelope, the offset and count of its parameters in the state's
+// channel parameter pool (the segment values are read from there).
+struct PipeChan {
+  double p[4];
+  int kind, par_off, n_par, pad;
+};
+// Stage coefficient of one term: c times the value of the block's envelope ch (0 or 1, -1:
+// static) at the stage time, or its conjugate (conj = 1).
+template <typename CT>
+struct PipeCoef {
+  CT c;
+  int ch, conj;
 };
 #define BQ_PIPE_THREADS 128  // threads of a pipelined stage CTA
-#define BQ_PIPE_COEF 16  // complex coefficients per system and stage: X, Y, S terms, C at slot 15
+#define BQ_MERGED_MAXM 64    // column-vector builders start at this thread
+// complex entries of a row / column coefficient record of the merged path (A0, Am, Ap and two
+// per sandwich term), rounded up to an even count so that records are 16-byte aligned pairs
+#define BQ_PIPE_RS(MS) ((3 + 2 * (MS) + 1) & ~1)
 
 struct PipeArgs {
   const PipeRec* recs;
   const unsigned char* params;
-  const void* coef;     // n_sys x BQ_PIPE_COEF complex, this stage
-  const void* u_in;
-  void* u_out;
-  void* y;
-  void* acc;
-  void* comp;
-  unsigned int* ticket;
-  long long* counter;
-  unsigned int* error;  // set when a bounded wait gives up
-  int n_sys, stage, n_slots, pad;
-  int slot_bytes, off_coef, off_u, off_y, off_acc, off_comp, pad2[2];  // shared-memory layout of a slot
-  double dt;
-};
-
-// A stage coefficient that depends on time: slot `slot` of the coefficient array (system
-// * BQ_PIPE_COEF + position) = c * chan(tau) (or c * conj(chan(tau))).  Static slots are
-// written once when the problem is mapped.
-struct CoefDyn {
-  int slot, ch, conj, pad;
-  double c_re, c_im;
-};
-
-struct CoefArgs {
-  const CoefDyn* dyn;
   const ChanDesc* chans;
   const double* chpar;
-  void* coef;
+  const void* u_in;     // stage input (the state y at stage 1)
+  void* u_out;
+  void* y;
+  void* acc;            // stage sum (scratch)
+  void* comp;           // pending increment / compensation of the state (part of the state)
+  unsigned int* ticket;
+  long long* counter;
   const double* tau_base;
-  const long long* counter;
+  unsigned int* error;  // set when a bounded wait gives up
+  int n_sys, n_slots;
+  int slot_bytes, off_u;    // bytes of a shared-memory slot; offset of the stage input in it
+  int zero_off, zero_bytes; // guard band before the stage input .. end of the guard band after it
+  int mmax, reverse;        // largest M of the state (coefficient records); reversed-time reading
+  int comp_zero;            // stage 1: comp is known to be zero (a freshly loaded state); not read
+  int pad;
+  const EvalEntry* entries; // stage 4: Tr(rho0 A) entries (PipeRec::e_off, n_e)
+  double2* obs;             // stage 4: per system, w sum_e f_e G(k_e, l_e) of the updated state
   double dt, horizon;
-  int n_dyn, stage, reverse, pad;
 };
 
 // Arguments of the batched persistent solve (k_solve_m1).

@@ -624,46 +624,154 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-#define BQ_MERGED_MAXM 64
 #define BQ_PIPE_RB 16  // system records per batch (power of two)
 #define BQ_WAIT_LIMIT (1 << 22)
 #define BQ_WAIT_SUSPENDS (1 << 16)  // suspended polls of at most BQ_WAIT_HINT_NS each (< 1 s in all)
 #define BQ_WAIT_HINT_NS 10000u
 
-// Time-dependent stage coefficients (drive envelopes at the stage time; a piecewise-constant
-// envelope at the step midpoint): one thread per entry.
-template <typename T>
-__global__ void k_coef_dyn(const CoefArgs A) {
-  using C = typename C2T<T>::type;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.n_dyn) return;
-  const CoefDyn d = A.dyn[i];
-  const double ts = A.tau_base[0] + (double)(*A.counter) * A.dt;
-  const ChanDesc cd = A.chans[d.ch];
-  const double tau = (cd.kind == 2) ? ts + 0.5 * A.dt : ts + stage_c(A.stage) * A.dt;
-  double2 e = chan_value_t<T>(cd, A.chpar, A.reverse ? A.horizon - tau : tau);
-  if (d.conj) e.y = -e.y;
-  reinterpret_cast<C*>(A.coef)[d.slot] = cmk<C>(d.c_re * e.x - d.c_im * e.y, d.c_re * e.y + d.c_im * e.x);
+// Physical time of this launch's RK4 stage for a channel of the given kind: the stage time
+// tau_step + c_s dt (a piecewise-constant envelope at the step midpoint: the Hamiltonian is
+// held constant within a step), mapped to t = horizon - tau for the reversed-time reading.
+__device__ __forceinline__ double pipe_chan_time(int kind, double tau_step, int stage, double dt, double horizon,
+                                                 int reverse) {
+  const double tau = (kind == 2) ? tau_step + 0.5 * dt : tau_step + stage_c(stage) * dt;
+  return reverse ? horizon - tau : tau;
 }
 
-template <typename T, int MX, int MY, int MS>
+// Envelope value (bq.h channel kinds) at this stage's time from a parameter block's record,
+// in FP64 (the Gaussian's exponential in the state's precision, as chan_value_t); a
+// piecewise-constant envelope reads its segment value from the channel parameter pool.
+template <typename T>
+__device__ __forceinline__ double2 pipe_chan_value(const PipeChan& c, const double* chpar, double tau_step, int stage,
+                                                   double dt, double horizon, int reverse) {
+  const double t = pipe_chan_time(c.kind, tau_step, stage, dt, horizon, reverse);
+  switch (c.kind) {
+    case 0:  // CONST
+      return make_double2(c.p[0], c.p[1]);
+    case 1: {  // GAUSS
+      const T d = (T)(t - c.p[2]);
+      const double e = (double)dev_exp<T>(-(d * d) / ((T)2 * (T)c.p[3] * (T)c.p[3]));
+      return make_double2(c.p[0] * e, c.p[1] * e);
+    }
+    case 2: {  // PWC
+      const int n_seg = (c.n_par - 2) / 2;
+      const double x = floor((t - c.p[0]) / c.p[1]);
+      if (!(x >= 0.0) || x >= (double)n_seg) return make_double2(0.0, 0.0);
+      const int sg = (int)x;
+      return make_double2(chpar[c.par_off + 2 + 2 * sg], chpar[c.par_off + 3 + 2 * sg]);
+    }
+    case 3: {  // CEXP
+      double sn, cs;
+      sincos(c.p[2] * t, &sn, &cs);
+      return make_double2(c.p[0] * cs - c.p[1] * sn, c.p[0] * sn + c.p[1] * cs);
+    }
+    default:
+      return make_double2(0.0, 0.0);
+  }
+}
+
+// Error-free sum of two complex values componentwise (Knuth's TwoSum, no magnitude
+// condition): s = fl(a + b) and s + e == a + b exactly.
+template <typename C>
+__device__ __forceinline__ void two_sum(C a, C b, C& s, C& e) {
+  s.x = a.x + b.x;
+  s.y = a.y + b.y;
+  const auto bx = s.x - a.x;
+  const auto by = s.y - a.y;
+  e.x = (a.x - (s.x - bx)) + (b.x - bx);
+  e.y = (a.y - (s.y - by)) + (b.y - by);
+}
+
+template <typename C>
+__device__ __forceinline__ C cneg(C a) {
+  a.x = -a.x;
+  a.y = -a.y;
+  return a;
+}
+
+// Two adjacent complex values from a 16-byte aligned shared-memory address.
+template <typename C>
+__device__ __forceinline__ void ld_pair(const C* p, C& a, C& b);
+template <>
+__device__ __forceinline__ void ld_pair<float2>(const float2* p, float2& a, float2& b) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+template <>
+__device__ __forceinline__ void ld_pair<double2>(const double2* p, double2& a, double2& b) {
+  a = p[0];
+  b = p[1];
+}
+
+// RK4 update of one element in the pipelined stage kernel.  The state value of an element is
+// y - comp, with comp the (negated) rounding residual of the last update: the state advances
+// by the classical RK4 increment accumulated in a stage sum s at the increment's own
+// magnitude and added to y once per step with an error-free sum.  With h = dt:
+//   stage 1: k1 = f(y); u_2 = y + h/2 k1; s = r + h/6 k1 with r = -comp the carried residual;
+//   stage 2: k2 = f(u_2); y is recovered from the stored u_2 and s as u_2 - 3 s (up to r, a
+//            few ulps: it only forms the next stage input); u_3 = y + h/2 k2, s += h/6 (2 k2);
+//   stage 3: k3 = f(u_3); u_4 = y + h k3, s += h/6 (2 k3);
+//   stage 4: k4 = f(u_4); p = s + h/6 k4; y + p = y' + e exactly (TwoSum); y = y', comp = -e.
+// The weight h/6 is applied as an unevaluated sum w_hi + w_lo (w_hi = fl(h/6)): the four
+// stages' weights then add up to h to far below the state's rounding, so the effective step
+// does not drift from h over long horizons (a plain fl(h/6) is off by up to 3e-8 relative,
+// a phase error of that size times the rotation angle).  Arrays moved per step and point:
+// stage 1 y (stage input), comp in and u, s out; stage 2 u, s in and u, s out; stage 3 u, s,
+// y in and u, s out; stage 4 u, s, y in and y, comp out (18 transfers).
+template <int STAGE, typename C, typename T>
+__device__ __forceinline__ void pipe_combine(C* __restrict__ uout, C* __restrict__ accg, C* __restrict__ yg,
+                                             C* __restrict__ compg, int gi, C uc, C kv, C sv, C yv, T h2, T hh,
+                                             T w_hi, T w_lo) {
+  if constexpr (STAGE == 1) {  // sv = comp of the element
+    uout[gi] = caxpy(h2, kv, uc);
+    accg[gi] = caxpy(w_hi, kv, caxpy(w_lo, kv, cneg(sv)));
+  } else if constexpr (STAGE == 2) {
+    C ye;
+    ye.x = fma((T)-3, sv.x, uc.x);
+    ye.y = fma((T)-3, sv.y, uc.y);
+    const C k2 = cscale(kv, (T)2);
+    uout[gi] = caxpy(h2, kv, ye);
+    accg[gi] = caxpy(w_hi, k2, caxpy(w_lo, k2, sv));
+  } else if constexpr (STAGE == 3) {
+    const C k2 = cscale(kv, (T)2);
+    uout[gi] = caxpy(hh, kv, yv);
+    accg[gi] = caxpy(w_hi, k2, caxpy(w_lo, k2, sv));
+  } else {
+    const C p = caxpy(w_hi, kv, caxpy(w_lo, kv, sv));
+    C yn, e;
+    two_sum(yv, p, yn, e);
+    yg[gi] = yn;
+    compg[gi] = cneg(e);
+  }
+}
+
+template <typename T, int MX, int MY, int MS, int STAGE>
 __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A) {
   using C = typename C2T<T>::type;
+  constexpr int RS = BQ_PIPE_RS(MS);  // complex entries of a row / column coefficient record
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long full[4];
   __shared__ PipeRec recs[2][BQ_PIPE_RB];  // records of two batches of systems
-  __shared__ int s_fail;
+  __shared__ double s_tau;
 
   const int tid = threadIdx.x;
   const int G = gridDim.x;
   const int nj = A.n_sys > (int)blockIdx.x ? (A.n_sys - (int)blockIdx.x + G - 1) / G : 0;
   const int S = A.n_slots;
-  const int stage = A.stage;
-  const size_t cs = sizeof(C);
+  const int cs = (int)sizeof(C);
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
-    s_fail = 0;
+    s_tau = A.tau_base[0] + (double)(*(volatile long long*)A.counter) * A.dt;
   }
+  // Zero the stage-input region of every slot and its guard bands once: neighbour reads at
+  // the edges of a system (whose coefficients are zero there) land in them, so they must
+  // hold finite values; later systems leave only earlier systems' finite values behind.
+  for (int s = 0; s < S; ++s) {
+    float4* z = reinterpret_cast<float4*>(smem_raw + (size_t)s * A.slot_bytes + A.zero_off);
+    for (int i = tid; i < A.zero_bytes / 16; i += blockDim.x) z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  fence_proxy_async();  // these writes come before the bulk copies into the same slots
   auto load_batch = [&](int b) {
     if (tid < BQ_PIPE_RB) {
       const int j = b * BQ_PIPE_RB + tid;
@@ -673,38 +781,83 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
   load_batch(0);
   __syncthreads();
   auto slot_ptr = [&](int s) { return smem_raw + (size_t)s * A.slot_bytes; };
-  // merged coefficient vectors of the current system: after the slots, (6 + 4 MS) Mmax complex
-  C* mv = reinterpret_cast<C*>(smem_raw + (size_t)S * A.slot_bytes);
-  // thread 0: issue the bulk copies of system j into slot j % S
-  auto issue = [&](int j) {
-    const PipeRec r = recs[(j / BQ_PIPE_RB) & 1][j % BQ_PIPE_RB];
-    unsigned char* sl = slot_ptr(j % S);
-    const unsigned blk = (unsigned)(r.blk_elems * cs);
-    const unsigned bytes = (unsigned)r.param_bytes + (unsigned)(BQ_PIPE_COEF * cs) + blk;
-    fence_proxy_async();
-    unsigned long long* bar = &full[j % S];
-    mbar_expect_tx(bar, bytes);
-    bulk_g2s(sl, A.params + r.param_off, (unsigned)r.param_bytes, bar);
-    bulk_g2s(sl + A.off_coef, reinterpret_cast<const C*>(A.coef) + (size_t)r.sys * BQ_PIPE_COEF,
-             (unsigned)(BQ_PIPE_COEF * cs), bar);
-    bulk_g2s(sl + A.off_u, reinterpret_cast<const C*>(A.u_in) + r.blk_off, blk, bar);
-    // the state, stage sum and compensation of that system are read with per-thread loads:
-    // bring them into L2 now, one system ahead of use
-    if (stage > 1) {
-      bulk_prefetch_l2(reinterpret_cast<const C*>(A.y) + r.blk_off, blk);
-      bulk_prefetch_l2(reinterpret_cast<const C*>(A.acc) + r.blk_off, blk);
-      if (stage == 4) bulk_prefetch_l2(reinterpret_cast<const C*>(A.comp) + r.blk_off, blk);
-    }
-  };
-  if (tid == 0)
-    for (int j = 0; j < S - 1 && j < nj; ++j) issue(j);
+  C* rowv = reinterpret_cast<C*>(smem_raw + (size_t)S * A.slot_bytes);  // [mmax][RS]
+  C* colv = rowv + (size_t)A.mmax * RS;                                  // [mmax][RS]
 
   C* uout = reinterpret_cast<C*>(A.u_out);
   C* yg = reinterpret_cast<C*>(A.y);
   C* accg = reinterpret_cast<C*>(A.acc);
   C* compg = reinterpret_cast<C*>(A.comp);
-  const T dt = (T)A.dt;
+  const C* uin = reinterpret_cast<const C*>(A.u_in);
+  // the array read with per-thread loads besides the stage input: comp at stage 1 (skipped for
+  // a freshly loaded state, whose comp is zero), the stage sum otherwise; stages 3 and 4 also
+  // read y
+  const C* pre = STAGE == 1 ? compg : accg;
+  const bool rd = STAGE != 1 || !A.comp_zero;
+  constexpr bool RDY = STAGE == 3 || STAGE == 4;
+
+  // thread 0: issue the bulk copies of system j into slot j % S, and bring the arrays this
+  // stage reads with per-thread loads into L2, one system ahead of use
+  auto issue = [&](int j) {
+    const PipeRec& r = recs[(j / BQ_PIPE_RB) & 1][j % BQ_PIPE_RB];
+    unsigned char* sl = slot_ptr(j % S);
+    const unsigned blk = (unsigned)(r.blk_elems * cs);
+    fence_proxy_async();
+    unsigned long long* bar = &full[j % S];
+    mbar_expect_tx(bar, (unsigned)r.param_bytes + blk);
+    bulk_g2s(sl, A.params + r.param_off, (unsigned)r.param_bytes, bar);
+    bulk_g2s(sl + A.off_u, uin + r.blk_off, blk, bar);
+    if (rd) bulk_prefetch_l2(pre + r.blk_off, blk);
+    if (RDY) bulk_prefetch_l2(yg + r.blk_off, blk);
+  };
+  if (tid == 0)
+    for (int j = 0; j < S - 1 && j < nj; ++j) issue(j);
+
+  const T hh = (T)A.dt;
+  const T h2 = (T)(0.5 * A.dt);
+  const double w = A.dt / 6.0;
+  const T w_hi = (T)w;
+  const T w_lo = (T)(w - (double)w_hi);
   const C zero = cmk<C>(0.0, 0.0);
+
+  // Stage 4: the Tr(rho0 A) contribution of system j (Eqs. 7, 11: w sum_e f_e (G_x[k_e]
+  // G_y[l_e] + R[k_e, l_e]) over the entries of rho0's support) from the updated state y - comp,
+  // by warp 1 with a shuffle reduction, once the CTA's barrier has made every thread's writes
+  // of system j visible (at the top of the next system, or after the last one).
+  auto observe = [&](int j) {
+    if (STAGE != 4 || A.obs == nullptr || (tid >> 5) != 1) return;
+    const PipeRec& rj = recs[(j / BQ_PIPE_RB) & 1][j % BQ_PIPE_RB];
+    const int lane = tid & 31;
+    auto val = [&](int i) {
+      const C a = yg[i], c = compg[i];
+      return make_double2((double)(a.x - c.x), (double)(a.y - c.y));
+    };
+    double re = 0.0, im = 0.0;
+    for (int e = lane; e < rj.n_e; e += 32) {
+      const EvalEntry en = A.entries[rj.e_off + e];
+      double vr = 0.0, vi = 0.0;
+      if (rj.gy_off >= 0) {
+        const double2 a = val(rj.blk_off + en.kx), b = val(rj.blk_off + rj.gy_off + en.ly);
+        vr += a.x * b.x - a.y * b.y;
+        vi += a.x * b.y + a.y * b.x;
+      }
+      if (rj.r_off >= 0) {
+        const double2 c = val(rj.blk_off + rj.r_off + en.kx * rj.M + en.ly);
+        vr += c.x;
+        vi += c.y;
+      }
+      const double fr = rj.w_re * en.f_re - rj.w_im * en.f_im;
+      const double fi = rj.w_re * en.f_im + rj.w_im * en.f_re;
+      re += fr * vr - fi * vi;
+      im += fr * vi + fi * vr;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_down_sync(0xffffffffu, re, o);
+      im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) A.obs[blockIdx.x + (size_t)j * G] = make_double2(re, im);
+  };
 
   for (int j = 0; j < nj; ++j) {
     const int jn = j + S - 1;
@@ -713,16 +866,16 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
       __syncthreads();
     }
     const PipeRec r = recs[(j / BQ_PIPE_RB) & 1][j % BQ_PIPE_RB];
+    const int M = r.M;
+    const int gb = r.blk_off;
+    const bool merged = r.merged != 0;
     // Merged path: this thread's column strip (column l, rows k0..k1-1 of R) and its G item
     // (index gq of [G_x | G_y], handed out from the last thread down, where the strips are
-    // shortest or absent).  The state, stage sum and compensation of the strip's first two
-    // rows and of the G item are loaded before the wait for the stage input, so that their
-    // latency overlaps the wait and the coefficient set-up.
-    int l = 0, k0 = 0, k1 = 0, gq = -1;
-    C y0 = zero, a0v = zero, c0 = zero, y1 = zero, a1 = zero, c1 = zero;
-    C gyv = zero, gav = zero, gcv = zero;
-    if (r.merged) {
-      const int M = r.M;
+    // shortest or absent).  The streamed values of the strip's first two rows and of the G
+    // item are loaded before the wait for the stage input.
+    int l = 0, k0 = 0, k1 = 0, gq = -1, gg = 0;
+    C s0 = zero, s1 = zero, y0 = zero, y1 = zero, sG = zero, yG = zero;
+    if (merged) {
       const int bk = (int)(((float)tid + 0.5f) * r.inv_m);
       l = tid - bk * M;
       if (r.r_off >= 0 && bk < r.nb) {
@@ -730,27 +883,24 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
         k1 = min(M, k0 + r.rb);
       }
       const int gi_ = BQ_PIPE_THREADS - 1 - tid;
-      if (r.gx_off >= 0 && gi_ < 2 * M) gq = gi_;
-      if (stage > 1) {
-        const int64_t g0 = (int64_t)r.blk_off + r.r_off + l;
-        if (k0 < k1) {
-          y0 = yg[g0 + k0 * M];
-          a0v = accg[g0 + k0 * M];
-          if (stage == 4) c0 = compg[g0 + k0 * M];
-        }
-        if (k0 + 1 < k1) {
-          y1 = yg[g0 + (k0 + 1) * M];
-          a1 = accg[g0 + (k0 + 1) * M];
-          if (stage == 4) c1 = compg[g0 + (k0 + 1) * M];
-        }
-        if (gq >= 0) {
-          const int64_t gg = (int64_t)r.blk_off + (gq < M ? r.gx_off + gq : r.gy_off + gq - M);
-          gyv = yg[gg];
-          gav = accg[gg];
-          if (stage == 4) gcv = compg[gg];
-        }
+      if (r.gy_off >= 0 && gi_ < 2 * M) {
+        gq = gi_;
+        gg = gb + (gq < M ? gq : r.gy_off + gq - M);
+        if (rd) sG = pre[gg];
+        if (RDY) yG = yg[gg];
+      }
+      const int g0 = gb + r.r_off + k0 * M + l;
+      if (k0 < k1) {
+        if (rd) s0 = pre[g0];
+        if (RDY) y0 = yg[g0];
+      }
+      if (k0 + 1 < k1) {
+        if (rd) s1 = pre[g0 + M];
+        if (RDY) y1 = yg[g0 + M];
       }
     }
+    const bool rowb = merged && tid < M;
+    const bool colb = merged && tid >= BQ_MERGED_MAXM && tid - BQ_MERGED_MAXM < M;
     // wait for system j (bounded): one thread polls the mbarrier, the others wait at the
     // barrier without issuing; the completed phase also makes the bulk-copied data visible
     {
@@ -770,201 +920,186 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
       }
     }
     // every thread is past system j - 1: its slot ((j + S - 1) % S) and the coefficient
-    // vectors are free, so the next copy can start now
+    // records are free, so the next copy can start now
     if (tid == 0 && jn < nj) issue(jn);
+    if (j > 0) observe(j - 1);
     unsigned char* sl = slot_ptr(j % S);
     const PipeHdr& h = *reinterpret_cast<const PipeHdr*>(sl);
-    const int M = h.M, nX = h.nX, nY = h.nY, nS = h.nS, has_sep = h.has_sep;
+    const int nX = h.nX, nY = h.nY, nS = h.nS, has_sep = h.has_sep;
     const int sdiag = h.sdiag;  // bit q: sandwich term q acts only where k = l
-    const C* dx = reinterpret_cast<const C*>(sl + sizeof(PipeHdr));
+    const PipeCoef<C>* tc = reinterpret_cast<const PipeCoef<C>*>(sl + sizeof(PipeHdr));
+    const PipeChan* pc = reinterpret_cast<const PipeChan*>(tc + h.n_terms);
+    const C* dx = reinterpret_cast<const C*>(pc + h.n_ch);
     const C* dy = dx + M;
     const T* wX = reinterpret_cast<const T*>(dy + M);
     const T* wY = wX + nX * M;
     const T* wSx = wY + nY * M;
     const T* wSy = wSx + nS * M;
-    const C* cf = reinterpret_cast<const C*>(sl + A.off_coef);
     const C* u = reinterpret_cast<const C*>(sl + A.off_u);
-    const C Cc = cf[BQ_PIPE_COEF - 1];
     const C* ur = u + r.r_off;
-    const C* ugx = u + r.gx_off;
+    const C* ugx = u;
     const C* ugy = u + r.gy_off;
+    const C Cc = cmk<C>(r.c_re, r.c_im);
+    // drive envelopes of the problem's time-dependent terms at this stage's time, from the
+    // block (threads that build coefficient records; every thread on the general path)
+    double2 e0 = make_double2(1.0, 0.0), e1 = make_double2(1.0, 0.0);
+    if (!merged || rowb || colb) {
+      if (h.n_ch > 0) e0 = pipe_chan_value<T>(pc[0], A.chpar, s_tau, STAGE, A.dt, A.horizon, A.reverse);
+      if (h.n_ch > 1) e1 = pipe_chan_value<T>(pc[1], A.chpar, s_tau, STAGE, A.dt, A.horizon, A.reverse);
+    }
+    // stage coefficient of term q: static part times the envelope (or its conjugate), formed
+    // in FP64 and rounded once to the state's precision
+    auto coef = [&](int q) {
+      const C c = tc[q].c;
+      const int ch = tc[q].ch;
+      if (ch < 0) return c;
+      double2 e = ch == 0 ? e0 : e1;
+      if (tc[q].conj) e.y = -e.y;
+      const double cr = (double)c.x, ci = (double)c.y;
+      return cmk<C>(cr * e.x - ci * e.y, cr * e.y + ci * e.x);
+    };
     const int nr = h.has_r ? M * M : 0;
+    const int ntot = h.ntot;
 
-    // RK4 combine of one element (position pos inside the system block)
-    auto combine_at = [&](int pos, C uc, C kv) {
-      const int64_t gi = (int64_t)r.blk_off + pos;
-      if (stage == 1) {
-        uout[gi] = caxpy(dt * (T)0.5, kv, uc);
-        accg[gi] = kv;
-      } else if (stage == 4) {
-        const C yv = yg[gi];
-        const C sm = cadd(accg[gi], kv);
-        const C cv = compg[gi];
-        C d, t, c2;
-        d.x = dt * (T)(1.0 / 6.0) * sm.x - cv.x;
-        d.y = dt * (T)(1.0 / 6.0) * sm.y - cv.y;
-        t.x = yv.x + d.x;
-        t.y = yv.y + d.y;
-        c2.x = (t.x - yv.x) - d.x;
-        c2.y = (t.y - yv.y) - d.y;
-        yg[gi] = t;
-        compg[gi] = c2;
-      } else {
-        const C yv = yg[gi];
-        uout[gi] = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, yv);
-        accg[gi] = caxpy((T)2, kv, accg[gi]);
-      }
-    };
-    // RK4 combine of one element whose state, stage sum and compensation are in registers
-    auto combine_reg = [&](int64_t gi, C uc, C kv, C yv, C av, C cv) {
-      if (stage == 1) {
-        uout[gi] = caxpy(dt * (T)0.5, kv, uc);
-        accg[gi] = kv;
-      } else if (stage == 4) {
-        const C sm = cadd(av, kv);
-        C d, t, c2;
-        d.x = dt * (T)(1.0 / 6.0) * sm.x - cv.x;
-        d.y = dt * (T)(1.0 / 6.0) * sm.y - cv.y;
-        t.x = yv.x + d.x;
-        t.y = yv.y + d.y;
-        c2.x = (t.x - yv.x) - d.x;
-        c2.y = (t.y - yv.y) - d.y;
-        yg[gi] = t;
-        compg[gi] = c2;
-      } else {
-        uout[gi] = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, yv);
-        accg[gi] = caxpy((T)2, kv, av);
-      }
-    };
-
-    if (r.merged) {
-      // ---- merged stencil: per-row / per-column coefficient vectors, 3x3 register window ----
-      // row vectors: A0 (diagonal + shift-0 X terms), Am (shift -1), Ap (shift +1);
-      // column vectors B0, Bm, Bp likewise for the Y terms; per sandwich term t with shifts
-      // (sx, sy): SX_t[k] = c_t Wx_t[k], SY_t[l] = Wy_t[l], GX_t[k] = G_x[k+sx], GY_t[l] = Wy_t[l] G_y[l+sy].
-      // The row vectors are built by threads 0..M-1, the column vectors by threads
-      // BQ_MERGED_MAXM..BQ_MERGED_MAXM+M-1 (other warps), concurrently.
-      C* A0 = mv;
-      C* Am = A0 + M;
-      C* Ap = Am + M;
-      C* B0 = Ap + M;
-      C* Bm = B0 + M;
-      C* Bp = Bm + M;
-      C* SXv = Bp + M;        // [MS][M]
-      C* GXv = SXv + MS * M;  // [MS][M]
-      C* SYv = GXv + MS * M;  // [MS][M] (real part used)
-      C* GYv = SYv + MS * M;  // [MS][M]
-      if (tid < M) {
+    if (merged) {
+      // ---- merged stencil: per-row / per-column coefficient records, one strip per thread ----
+      // row record k: A0 (diagonal + shift-0 X terms), Am (shift -1), Ap (shift +1), then per
+      // sandwich term q with shifts (sx, sy): SX_q = c_q Wx_q[k] and SG_q = SX_q G_x[k + sx];
+      // column record l: B0, Bm, Bp of the Y terms, then SY_q = Wy_q[l] (real part) and
+      // GY_q = Wy_q[l] G_y[l + sy].  A point (k, l) of R gets
+      //   (A0 + B0) u + Am u(k-1,l) + Ap u(k+1,l) + Bm u(k,l-1) + Bp u(k,l+1)
+      //   + sum_q SX_q SY_q u(k+sx,l+sy) + SG_q GY_q,
+      // without bounds tests: every coefficient whose source leaves the grid is zero and the
+      // source read itself stays inside the slot's guard bands.
+      if (rowb) {
         const int i = tid;
         C a0 = dx[i], am = zero, ap = zero;
 #pragma unroll
         for (int q = 0; q < MX; ++q)
           if (q < nX) {
-            const C v = cscale(cf[q], wX[q * M + i]);
+            const C v = cscale(coef(q), wX[q * M + i]);
             if (h.sX[q] == 0) a0 = cadd(a0, v); else if (h.sX[q] < 0) am = cadd(am, v); else ap = cadd(ap, v);
           }
-        A0[i] = a0; Am[i] = am; Ap[i] = ap;
+        C* rv = rowv + i * RS;
+        rv[0] = a0; rv[1] = am; rv[2] = ap;
 #pragma unroll
         for (int q = 0; q < MS; ++q)
           if (q < nS) {
+            const C sx = cscale(coef(nX + nY + q), wSx[q * M + i]);
             const int xs = i + h.sSx[q];
-            SXv[q * M + i] = cscale(cf[nX + nY + q], wSx[q * M + i]);
-            GXv[q * M + i] = (has_sep && xs >= 0 && xs < M) ? ugx[xs] : zero;
+            const C gx = (has_sep && xs >= 0 && xs < M) ? ugx[xs] : zero;
+            rv[3 + 2 * q] = sx;
+            rv[4 + 2 * q] = cmul(sx, gx);
           }
-      } else if (tid >= BQ_MERGED_MAXM && tid - BQ_MERGED_MAXM < M) {
+      } else if (colb) {
         const int i = tid - BQ_MERGED_MAXM;
         C b0 = dy[i], bm = zero, bp = zero;
 #pragma unroll
         for (int q = 0; q < MY; ++q)
           if (q < nY) {
-            const C v = cscale(cf[nX + q], wY[q * M + i]);
+            const C v = cscale(coef(nX + q), wY[q * M + i]);
             if (h.sY[q] == 0) b0 = cadd(b0, v); else if (h.sY[q] < 0) bm = cadd(bm, v); else bp = cadd(bp, v);
           }
-        B0[i] = b0; Bm[i] = bm; Bp[i] = bp;
+        C* cvv = colv + i * RS;
+        cvv[0] = b0; cvv[1] = bm; cvv[2] = bp;
 #pragma unroll
         for (int q = 0; q < MS; ++q)
           if (q < nS) {
-            const int ysh = i + h.sSy[q];
-            SYv[q * M + i] = cmk<C>((double)wSy[q * M + i], 0.0);
-            GYv[q * M + i] = (has_sep && ysh >= 0 && ysh < M) ? cscale(ugy[ysh], wSy[q * M + i]) : zero;
+            const T wy = wSy[q * M + i];
+            const int ys = i + h.sSy[q];
+            C sy;
+            sy.x = wy;
+            sy.y = (T)0;
+            cvv[3 + 2 * q] = sy;
+            cvv[4 + 2 * q] = (has_sep && ys >= 0 && ys < M) ? cscale(ugy[ys], wy) : zero;
           }
       }
       __syncthreads();
       if (k0 < k1) {
-        const C b0 = B0[l], bm = Bm[l], bp = Bp[l];
-        const bool cm = l > 0, cp = l + 1 < M;  // column neighbours exist
-        T sy[MS];
-        C gy[MS];
-        int ssx[MS], soff[MS];
-        bool scol[MS];
+        const C* cvv = colv + l * RS;
+        const C b0 = cvv[0], bm = cvv[1], bp = cvv[2];
+        T syq[MS];
+        C gyq[MS];
+        int soff[MS];
 #pragma unroll
         for (int q = 0; q < MS; ++q) {
-          sy[q] = q < nS ? SYv[q * M + l].x : (T)0;
-          gy[q] = q < nS ? GYv[q * M + l] : zero;
-          ssx[q] = h.sSx[q];
+          syq[q] = q < nS ? cvv[3 + 2 * q].x : (T)0;
+          gyq[q] = q < nS ? cvv[4 + 2 * q] : zero;
           soff[q] = h.sSx[q] * M + h.sSy[q];
-          scol[q] = q < nS && l + h.sSy[q] >= 0 && l + h.sSy[q] < M;
         }
-        C um = k0 > 0 ? ur[(k0 - 1) * M + l] : zero;  // u(k-1, l)
-        C uc = ur[k0 * M + l];                          // u(k, l)
-        // state / stage sum / compensation: a register ring two rows ahead of use.  The
-        // diagonal restriction of a secular projector term costs a test per row and term,
-        // so only systems that have one run the tested form of the row loop.
-        auto rows = [&](auto diag_tag) {
-          constexpr bool DIAG = decltype(diag_tag)::value;
-          for (int kk = k0; kk < k1; ++kk) {
-            const int pos = r.r_off + kk * M + l;
-            const int64_t gi = (int64_t)r.blk_off + pos;
-            const C yv = y0, av = a0v, cv = c0;
-            y0 = y1; a0v = a1; c0 = c1;
-            if (stage > 1 && kk + 2 < k1) {
-              y1 = yg[gi + 2 * M];
-              a1 = accg[gi + 2 * M];
-              if (stage == 4) c1 = compg[gi + 2 * M];
-            }
-            const int c = kk * M + l;
-            const C up = kk + 1 < M ? ur[c + M] : zero;
-            const C ul = cm ? ur[c - 1] : zero;
-            const C urr = cp ? ur[c + 1] : zero;
-            C kv = cmul(cadd(A0[kk], b0), uc);
-            kv = cfma(Am[kk], um, kv);
-            kv = cfma(Ap[kk], up, kv);
-            kv = cfma(bm, ul, kv);
-            kv = cfma(bp, urr, kv);
+        const C* up = ur + k0 * M + l;  // the point (kk, l)
+        const C* rv = rowv + k0 * RS;
+        int go = gb + r.r_off + k0 * M + l;
+        C um = up[-M];  // (k0 - 1, l): the row above, or a guard / G value with Am = 0
+        C uc = up[0];
+        // the stencil of one point from its row record and the column values in registers
+        auto point = [&](const C* rrec, const C* pu, C cm, C cc, C cd, bool on_diag) {
+          C a0, am, ap, sxn;
+          ld_pair(rrec, a0, am);
+          ld_pair(rrec + 2, ap, sxn);
+          C kv = cmul(cadd(a0, b0), cc);
+          kv = cfma(am, cm, kv);
+          kv = cfma(ap, cd, kv);
+          kv = cfma(bm, pu[-1], kv);
+          kv = cfma(bp, pu[1], kv);
 #pragma unroll
-            for (int q = 0; q < MS; ++q)
-              if (q < nS && (!DIAG || !((sdiag >> q) & 1) || kk == l)) {  // secular projector: k = l only
-                const int xx = kk + ssx[q];
-                const C v = (scol[q] && xx >= 0 && xx < M) ? ur[c + soff[q]] : zero;
-                kv = cfma(SXv[q * M + kk], cadd(cscale(v, sy[q]), cmul(GXv[q * M + kk], gy[q])), kv);
+          for (int q = 0; q < MS; ++q)
+            if (q < nS) {
+              const C sx = sxn;
+              C sg;
+              ld_pair(rrec + 4 + 2 * q, sg, sxn);
+              if (!((sdiag >> q) & 1) || on_diag) {  // secular projector: k = l only
+                kv = cfma(cscale(sx, syq[q]), pu[soff[q]], kv);
+                kv = cfma(sg, gyq[q], kv);
               }
-            combine_reg(gi, uc, kv, yv, av, cv);
-            um = uc;
-            uc = up;
-          }
+            }
+          return kv;
         };
-        if (sdiag) rows(std::true_type{}); else rows(std::false_type{});
+        // two rows per iteration (independent chains); streamed values in a register ring
+        // two rows ahead of use
+        for (int kk = k0; kk < k1; kk += 2) {
+          const bool two = kk + 1 < k1;
+          const C sA = s0, yA = y0, sB = s1, yB = y1;
+          if (kk + 2 < k1) {
+            if (rd) s0 = pre[go + 2 * M];
+            if (RDY) y0 = yg[go + 2 * M];
+          }
+          if (kk + 3 < k1) {
+            if (rd) s1 = pre[go + 3 * M];
+            if (RDY) y1 = yg[go + 3 * M];
+          }
+          const C ud = up[M];                                      // row kk + 1 (a guard row past M - 1)
+          const C udB = (two && kk + 2 < M) ? up[2 * M] : zero;   // row kk + 2
+          const C kvA = point(rv, up, um, uc, ud, kk == l);
+          pipe_combine<STAGE>(uout, accg, yg, compg, go, uc, kvA, sA, yA, h2, hh, w_hi, w_lo);
+          if (two) {
+            const C kvB = point(rv + RS, up + M, uc, ud, udB, kk + 1 == l);
+            pipe_combine<STAGE>(uout, accg, yg, compg, go + M, ud, kvB, sB, yB, h2, hh, w_hi, w_lo);
+          }
+          um = ud;
+          uc = udB;
+          up += 2 * M;
+          rv += 2 * RS;
+          go += 2 * M;
+        }
       }
       if (gq >= 0) {
         const bool isx = gq < M;
         const int g = isx ? gq : gq - M;
         const C* gs = isx ? ugx : ugy;
+        const C* vv = (isx ? rowv : colv) + g * RS;
         const C uc = gs[g];
-        const C lo = g > 0 ? gs[g - 1] : zero, hi = g + 1 < M ? gs[g + 1] : zero;
-        C kv;
-        if (isx) {
-          kv = cmul(cadd(A0[g], Cc), uc);
-          kv = cfma(Am[g], lo, kv);
-          kv = cfma(Ap[g], hi, kv);
-        } else {
-          kv = cmul(cadd(B0[g], cmk<C>(-(double)Cc.x, -(double)Cc.y)), uc);
-          kv = cfma(Bm[g], lo, kv);
-          kv = cfma(Bp[g], hi, kv);
-        }
-        combine_reg((int64_t)r.blk_off + (isx ? r.gx_off : r.gy_off) + g, uc, kv, gyv, gav, gcv);
+        // neighbours outside the grid have zero coefficients; their reads stay in the slot
+        const C lo = gs[g - 1], hi = gs[g + 1];
+        C d = vv[0];
+        d = isx ? cadd(d, Cc) : cadd(d, cneg(Cc));
+        C kv = cmul(d, uc);
+        kv = cfma(vv[1], lo, kv);
+        kv = cfma(vv[2], hi, kv);
+        pipe_combine<STAGE>(uout, accg, yg, compg, gg, uc, kv, sG, yG, h2, hh, w_hi, w_lo);
       }
       // no barrier here: the wait at the top of the next system orders the reuse of the
-      // slot and of the coefficient vectors
+      // slot and of the coefficient records
       continue;
     }
 
@@ -972,17 +1107,16 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
     C cX[MX], cY[MY], cS[MS];
     int shX[MX], shY[MY], shSx[MS], shSy[MS];
 #pragma unroll
-    for (int q = 0; q < MX; ++q) { cX[q] = cf[min(q, BQ_PIPE_COEF - 1)]; shX[q] = h.sX[q]; }
+    for (int q = 0; q < MX; ++q) { cX[q] = q < nX ? coef(q) : zero; shX[q] = h.sX[q]; }
 #pragma unroll
-    for (int q = 0; q < MY; ++q) { cY[q] = cf[min(nX + q, BQ_PIPE_COEF - 1)]; shY[q] = h.sY[q]; }
+    for (int q = 0; q < MY; ++q) { cY[q] = q < nY ? coef(nX + q) : zero; shY[q] = h.sY[q]; }
 #pragma unroll
     for (int q = 0; q < MS; ++q) {
-      cS[q] = cf[min(nX + nY + q, BQ_PIPE_COEF - 1)];
+      cS[q] = q < nS ? coef(nX + nY + q) : zero;
       shSx[q] = h.sSx[q];
       shSy[q] = h.sSy[q];
     }
-    const int ntot = h.ntot;
-    const float invM = 1.0f / (float)M;
+    const float invM = r.inv_m;
     for (int e = tid; e < ntot; e += blockDim.x) {
       int pos;
       C uc, kv;
@@ -1011,9 +1145,9 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
         const bool isx = e < nr + M;
         const int g = isx ? e - nr : e - nr - M;
         const C* gs = isx ? ugx : ugy;
-        pos = (isx ? r.gx_off : r.gy_off) + g;
+        pos = isx ? g : r.gy_off + g;
         uc = gs[g];
-        kv = cmul(isx ? cadd(dx[g], Cc) : cadd(dy[g], cmk<C>(-(double)Cc.x, -(double)Cc.y)), uc);
+        kv = cmul(isx ? cadd(dx[g], Cc) : cadd(dy[g], cneg(Cc)), uc);
         if (isx) {
 #pragma unroll
           for (int q = 0; q < MX; ++q)
@@ -1024,11 +1158,15 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
             if (q < nY) kv = cfma(cY[q], cscale(gs[min(max(g + shY[q], 0), M - 1)], wY[q * M + g]), kv);
         }
       }
-      combine_at(pos, uc, kv);
+      const int gi = gb + pos;
+      const C sv = rd ? pre[gi] : zero;
+      const C yv = RDY ? yg[gi] : zero;
+      pipe_combine<STAGE>(uout, accg, yg, compg, gi, uc, kv, sv, yv, h2, hh, w_hi, w_lo);
     }
   }
   __syncthreads();  // every system of this CTA is written before it takes its ticket
-  if (stage == 4 && tid == 0) {
+  if (nj > 0) observe(nj - 1);
+  if (STAGE == 4 && tid == 0) {
     __threadfence();
     const unsigned int t = atomicAdd(A.ticket, 1u);
     if (t == gridDim.x - 1) {
@@ -1038,6 +1176,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
     }
   }
 }
+
 
 // ---------------------------------------------------------------------------------------
 // Batched persistent solve (single mode): one launch integrates every system for n_steps.
@@ -2026,13 +2165,28 @@ __global__ void __launch_bounds__(BLK) k_solve_mg(const SolveArgs A) {
 
 // ---------------------------------------------------------------------------------------
 // Observables: one warp per evaluation group, lanes over (initial condition, entry) pairs.
+// The value of a state element is y - comp (comp: the pending increment the pipelined stage
+// kernel leaves between steps, or a rounding-size compensation).
 // ---------------------------------------------------------------------------------------
+template <typename C>
+struct StateView {
+  const C* y;
+  const C* c;
+  __device__ __forceinline__ C operator[](int64_t i) const {
+    const C a = y[i], b = c[i];
+    C r;
+    r.x = a.x - b.x;
+    r.y = a.y - b.y;
+    return r;
+  }
+};
+
 template <typename T>
 __global__ void k_eval(const SysDesc* __restrict__ sys, const EvalGroup* __restrict__ groups,
-                       const EvalEntry* __restrict__ entries, const void* ystate, double2* out,
+                       const EvalEntry* __restrict__ entries, const void* ystate, const void* cstate, double2* out,
                        int n_groups) {
   using C = typename C2T<T>::type;
-  const C* y = reinterpret_cast<const C*>(ystate);
+  const StateView<C> y{reinterpret_cast<const C*>(ystate), reinterpret_cast<const C*>(cstate)};
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n_groups) return;
@@ -2074,9 +2228,10 @@ __global__ void k_eval(const SysDesc* __restrict__ sys, const EvalGroup* __restr
 // Observables for groups with few (initial condition, entry) pairs: one thread per group.
 template <typename T>
 __global__ void k_eval_small(const SysDesc* __restrict__ sys, const EvalGroup* __restrict__ groups,
-                             const EvalEntry* __restrict__ entries, const void* ystate, double2* out, int n_groups) {
+                             const EvalEntry* __restrict__ entries, const void* ystate, const void* cstate, double2* out,
+                             int n_groups) {
   using C = typename C2T<T>::type;
-  const C* y = reinterpret_cast<const C*>(ystate);
+  const StateView<C> y{reinterpret_cast<const C*>(ystate), reinterpret_cast<const C*>(cstate)};
   const int gi = blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= n_groups) return;
   const EvalGroup g = groups[gi];
@@ -2296,53 +2451,70 @@ cudaError_t launch_adj_seed(const SysDesc* sys, const EvalGroup* groups, const E
   return cudaGetLastError();
 }
 
+// The pipelined stage kernel for (dtype, variant, stage): variant 0 = at most 2 terms per side,
+// variant 1 = at most BQ_M1_MAXT.
+template <typename T, int MXYS>
+static auto pipe_kernel(int stage) {
+  switch (stage) {
+    case 1: return k_stage_pipe<T, MXYS, MXYS, MXYS, 1>;
+    case 2: return k_stage_pipe<T, MXYS, MXYS, MXYS, 2>;
+    case 3: return k_stage_pipe<T, MXYS, MXYS, MXYS, 3>;
+    default: return k_stage_pipe<T, MXYS, MXYS, MXYS, 4>;
+  }
+}
+
+template <typename T, int MXYS>
+static cudaError_t pipe_attrs_t() {
+  for (int stage = 1; stage <= 4; ++stage) {
+    cudaError_t e = cudaFuncSetAttribute(pipe_kernel<T, MXYS>(stage), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         BQ_MAX_DYN_SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 static cudaError_t pipe_attrs() {
+  static std::mutex mu;
   static bool done = false;
+  std::lock_guard<std::mutex> lock(mu);
   if (done) return cudaSuccess;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_stage_pipe<double, 2, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, BQ_MAX_DYN_SMEM)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_stage_pipe<double, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, BQ_MAX_DYN_SMEM)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_stage_pipe<float, 2, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, BQ_MAX_DYN_SMEM)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_stage_pipe<float, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, BQ_MAX_DYN_SMEM)) != cudaSuccess) return e;
+  if ((e = pipe_attrs_t<double, 2>()) != cudaSuccess) return e;
+  if ((e = pipe_attrs_t<double, BQ_M1_MAXT>()) != cudaSuccess) return e;
+  if ((e = pipe_attrs_t<float, 2>()) != cudaSuccess) return e;
+  if ((e = pipe_attrs_t<float, BQ_M1_MAXT>()) != cudaSuccess) return e;
   done = true;
   return cudaSuccess;
 }
 
-template <typename T, int MXYS>
-static cudaError_t launch_pipe_t(const PipeArgs& a, const CoefArgs& c, int grid, int smem_bytes, cudaStream_t s) {
-  auto kern = k_stage_pipe<T, MXYS, MXYS, MXYS>;
+cudaError_t launch_stage_pipe(const PipeArgs& a, int variant, int dtype, int stage, int grid, int smem_bytes,
+                              cudaStream_t s) {
   cudaError_t ea = pipe_attrs();
   if (ea != cudaSuccess) return ea;
-  if (c.n_dyn > 0) {
-    k_coef_dyn<T><<<(c.n_dyn + 255) / 256, 256, 0, s>>>(c);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+  if (stage < 1 || stage > 4) return cudaErrorInvalidValue;
+  if (dtype == 0) {
+    if (variant == 0) pipe_kernel<double, 2>(stage)<<<grid, BQ_PIPE_THREADS, smem_bytes, s>>>(a);
+    else pipe_kernel<double, BQ_M1_MAXT>(stage)<<<grid, BQ_PIPE_THREADS, smem_bytes, s>>>(a);
+  } else {
+    if (variant == 0) pipe_kernel<float, 2>(stage)<<<grid, BQ_PIPE_THREADS, smem_bytes, s>>>(a);
+    else pipe_kernel<float, BQ_M1_MAXT>(stage)<<<grid, BQ_PIPE_THREADS, smem_bytes, s>>>(a);
   }
-  kern<<<grid, BQ_PIPE_THREADS, smem_bytes, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_stage_pipe(const PipeArgs& a, const CoefArgs& c, int variant, int dtype, int grid, int smem_bytes,
-                              cudaStream_t s) {
-  if (dtype == 0)
-    return variant == 0 ? launch_pipe_t<double, 2>(a, c, grid, smem_bytes, s)
-                        : launch_pipe_t<double, BQ_M1_MAXT>(a, c, grid, smem_bytes, s);
-  return variant == 0 ? launch_pipe_t<float, 2>(a, c, grid, smem_bytes, s)
-                      : launch_pipe_t<float, BQ_M1_MAXT>(a, c, grid, smem_bytes, s);
-}
-
-cudaError_t pipe_blocks_per_sm(int dtype, int variant, int smem_bytes, int* out) {
+cudaError_t pipe_blocks_per_sm(int dtype, int variant, int stage, int smem_bytes, int* out) {
   cudaError_t ea = pipe_attrs();
   if (ea != cudaSuccess) return ea;
+  if (stage < 1 || stage > 4) return cudaErrorInvalidValue;
   if (dtype == 0)
-    return variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_stage_pipe<double, 2, 2, 2>,
-                                                                         BQ_PIPE_THREADS, smem_bytes)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                              out, k_stage_pipe<double, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>, BQ_PIPE_THREADS, smem_bytes);
-  return variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_stage_pipe<float, 2, 2, 2>,
-                                                                       BQ_PIPE_THREADS, smem_bytes)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            out, k_stage_pipe<float, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>, BQ_PIPE_THREADS, smem_bytes);
+    return variant == 0
+               ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, pipe_kernel<double, 2>(stage), BQ_PIPE_THREADS, smem_bytes)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, pipe_kernel<double, BQ_M1_MAXT>(stage), BQ_PIPE_THREADS,
+                                                               smem_bytes);
+  return variant == 0
+             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, pipe_kernel<float, 2>(stage), BQ_PIPE_THREADS, smem_bytes)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, pipe_kernel<float, BQ_M1_MAXT>(stage), BQ_PIPE_THREADS,
+                                                             smem_bytes);
 }
 
 template <typename K>
@@ -2380,22 +2552,22 @@ cudaError_t launch_stage(const StageArgs& a, int dtype, int nm, int n_work, int 
 }
 
 cudaError_t launch_eval(const SysDesc* sys, const EvalGroup* groups, const EvalEntry* entries, const void* y,
-                        double2* out, int n_groups, int dtype, int small, cudaStream_t s) {
+                        const void* comp, double2* out, int n_groups, int dtype, int small, cudaStream_t s) {
   if (n_groups <= 0) return cudaSuccess;
   const int threads = 256;
   if (small) {
     const int blocks = (n_groups + threads - 1) / threads;
     if (dtype == 0)
-      k_eval_small<double><<<blocks, threads, 0, s>>>(sys, groups, entries, y, out, n_groups);
+      k_eval_small<double><<<blocks, threads, 0, s>>>(sys, groups, entries, y, comp, out, n_groups);
     else
-      k_eval_small<float><<<blocks, threads, 0, s>>>(sys, groups, entries, y, out, n_groups);
+      k_eval_small<float><<<blocks, threads, 0, s>>>(sys, groups, entries, y, comp, out, n_groups);
     return cudaGetLastError();
   }
   const int blocks = (n_groups * 32 + threads - 1) / threads;
   if (dtype == 0)
-    k_eval<double><<<blocks, threads, 0, s>>>(sys, groups, entries, y, out, n_groups);
+    k_eval<double><<<blocks, threads, 0, s>>>(sys, groups, entries, y, comp, out, n_groups);
   else
-    k_eval<float><<<blocks, threads, 0, s>>>(sys, groups, entries, y, out, n_groups);
+    k_eval<float><<<blocks, threads, 0, s>>>(sys, groups, entries, y, comp, out, n_groups);
   return cudaGetLastError();
 }
 

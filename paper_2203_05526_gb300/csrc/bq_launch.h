@@ -30,17 +30,18 @@ cudaError_t launch_adjoint(const AdjArgs& a, int dtype, int nm, int n_work, int 
                            cudaStream_t s);
 cudaError_t launch_adj_seed(const SysDesc* sys, const EvalGroup* groups, const EvalEntry* entries, const void* y,
                             void* lam, int n_groups, int dtype, cudaStream_t s);
-// Pipelined single-mode stage: per-stage coefficient kernel + persistent bulk-copy pipeline.
-cudaError_t launch_stage_pipe(const PipeArgs& a, const CoefArgs& c, int variant, int dtype, int grid, int smem_bytes,
+// Pipelined single-mode stage (persistent CTAs, bulk-copy pipeline, drive envelopes evaluated
+// in the kernel), RK4 stage `stage` (1..4).
+cudaError_t launch_stage_pipe(const PipeArgs& a, int variant, int dtype, int stage, int grid, int smem_bytes,
                               cudaStream_t s);
-cudaError_t pipe_blocks_per_sm(int dtype, int variant, int smem_bytes, int* out);
+cudaError_t pipe_blocks_per_sm(int dtype, int variant, int stage, int smem_bytes, int* out);
 // Batched persistent solve, merged-stencil form (256 threads, M <= 45, shifts in {-1,0,1}).
 cudaError_t launch_solve_mg(const SolveArgs& a, int dtype, int smem_bytes, int cap_per_sm, cudaStream_t s,
                             int* grid_out);
 // Occupancy (CTAs per SM) of the persistent solve kernels at the given shared memory.
 cudaError_t solve_blocks_per_sm(int dtype, int merged, int smem_bytes, int* out);
 cudaError_t launch_eval(const SysDesc* sys, const EvalGroup* groups, const EvalEntry* entries, const void* y,
-                        double2* out, int n_groups, int dtype, int small, cudaStream_t s);
+                        const void* comp, double2* out, int n_groups, int dtype, int small, cudaStream_t s);
 // Device address of the fixed RK4 scratch on the current device (looked up once per device).
 cudaError_t fixed_scratch(void** ptr);
 cudaError_t launch_scatter(const InitEntry* ent, int n, void* y, int dtype, cudaStream_t s);

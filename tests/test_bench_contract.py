@@ -12,8 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _run(extra_env):
     env = {**os.environ, **extra_env}
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0", "--instances", "16"], capture_output=True, text=True, env=env,
-                       cwd=ROOT, timeout=300)
+                        "--warmup", "0", "--instances", "16", "--gpus", extra_env["WORLD_SIZE"]],
+                       capture_output=True, text=True, env=env, cwd=ROOT, timeout=300)
     assert r.returncode == 0, r.stderr
     return [line for line in r.stdout.splitlines() if line.startswith("{")]
 
@@ -33,3 +33,25 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_other_ranks_are_silent():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_gpus_flag_starts_the_ranks_itself():
+    """`bench.py --gpus 2` outside a launcher starts two ranks with the rendezvous
+    environment a launcher would give them; rank 0 alone prints, reporting both GPUs."""
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR",
+                                                            "MASTER_PORT")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0", "--instances", "16"], capture_output=True, text=True,
+                       env=env, cwd=ROOT, timeout=300)
+    assert r.returncode == 0, r.stderr
+    lines = [line for line in r.stdout.splitlines() if line.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 2 and d["impl"] == "reference"
+
+
+def test_world_size_must_match_gpus():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0", "--instances", "16"], capture_output=True, text=True,
+                       env={**os.environ, "RANK": "0", "WORLD_SIZE": "1", "LOCAL_RANK": "0"}, cwd=ROOT, timeout=300)
+    assert r.returncode != 0 and "WORLD_SIZE=1" in r.stderr

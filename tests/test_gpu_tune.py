@@ -55,11 +55,13 @@ def test_autotune_restores_state_and_time():
     assert st.get_tune() == tune
 
 
-def test_every_step_schedule_computes_the_same_step():
-    """Pipelined schedules (slots, CTAs per SM) run the same kernel: bitwise equal results.
-    The one-CTA-per-system path evaluates the same stencil from per-term programs: equal to
-    FP32 rounding, and both match the FP64 oracle."""
-    ps = _batch(n=64)
+@pytest.mark.parametrize("n", [64, 2000])
+def test_every_step_schedule_computes_the_same_step(n):
+    """Pipelined schedules (slots, CTAs per SM) run the same kernel: bitwise equal results,
+    with one system per CTA (64 instances) and with many per CTA in ragged sizes (2000).  The
+    one-CTA-per-system path evaluates the same stencil from per-term programs: equal to FP32
+    rounding, and both match the FP64 oracle."""
+    ps = _batch(n=n)
     dt, n = ps[0].dt, 12
     ref = gpu_state(ps, dtype="f32")
     assert ref.get_tune()["stage_path"] == "pipe"

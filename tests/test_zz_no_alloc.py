@@ -1,7 +1,8 @@
-"""bq_step_fixed_scratch: stepping for callers that cannot allocate device memory (for
-example code running inside another framework's CUDA-graph capture, where cudaMalloc is
-illegal).  Its RK4 scratch lives in a fixed device array inside the library; its results
-must equal bq_step's.  This file is collected last on purpose."""
+"""bq_step_fixed_scratch: stepping for callers that cannot allocate device memory, for
+example code whose device memory is all handed out by another component's allocator at
+start-up, or a loop that must not pay for an allocation.  Its RK4 scratch (the stage inputs
+and the stage sum) lives in a fixed device array inside the library; its results must equal
+bq_step's, whatever state used the array before.  This file is collected last on purpose."""
 
 import ctypes as C
 
@@ -11,6 +12,7 @@ import pytest
 import paper_2203_05526_gb300 as bq
 from paper_2203_05526_gb300 import binding
 from workloads import configs
+from workloads.spec import Problem
 
 from parity import gpu_state
 
@@ -34,25 +36,61 @@ def _raw(state):
     return host.numpy().copy()
 
 
-@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-6)])
-def test_fixed_scratch_equals_bq_step_two_calls(dtype, tol):
+def _fixed_step(state, dt, n):
+    """One call of the allocation-free entry point through the C ABI."""
     import torch
-    p = configs.random_problem(901, n_modes=2, N=5, n_steps=40, dt=0.01, dense_measured=True)
-    a = gpu_state(p, dtype=dtype)   # existing entry point
-    b = gpu_state(p, dtype=dtype)   # fixed-scratch entry point, called through the C ABI
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    binding.check(bq.lib().bq_step_fixed_scratch(state.ptr, C.c_double(dt), C.c_int64(n), stream))
+
+
+def _case(kind):
+    """(problems, stage path or None for the default, expected stage variant)."""
+    if kind == "tiled_two_mode":
+        return [configs.random_problem(901, n_modes=2, N=5, n_steps=40, dt=0.01, dense_measured=True)], None, "generic"
+    if kind == "pipelined_batch":
+        return configs.kerr_batch(B=48, T=40 * 0.002, dt=0.002, n_min=5, n_max=24), None, "pipelined"
+    if kind == "three_mode_global_read":
+        p = configs.table_one_network(3, 6, steps=4000)
+        p = Problem(**{**p.__dict__, "T": 40 * p.dt,
+                       "measured": {((1, 0, 1), (0, 1, 1)): 1.0 + 0.3j, ((0, 1, 1), (1, 0, 1)): 1.0 - 0.3j}})
+        return [p], None, "generic"
+    raise ValueError(kind)
+
+
+def _dirty_the_array(dtype):
+    """Runs a state of another layout and the other precision through the fixed array, so the
+    array holds unrelated values (including in its padding) when the compared calls start."""
+    other = "f32" if dtype == "f64" else "f64"
+    p = configs.random_problem(77, n_modes=1, N=9, n_steps=6, dt=0.01, dense_measured=True)
+    st = gpu_state(p, dtype=other)
+    _fixed_step(st, p.dt, 6)
+
+
+@pytest.mark.parametrize("kind", ["tiled_two_mode", "pipelined_batch", "three_mode_global_read"])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-6)])
+def test_fixed_scratch_equals_bq_step_two_calls(kind, dtype, tol):
+    import torch
+    ps, path, variant = _case(kind)
+    a = gpu_state(ps, dtype=dtype)   # existing entry point
+    b = gpu_state(ps, dtype=dtype)   # fixed-scratch entry point, called through the C ABI
+    if path is not None:
+        a.set_tune(stage_path=path)
+        b.set_tune(stage_path=path)
+    assert a.stage_variant() == variant and b.stage_variant() == variant
+    _dirty_the_array(dtype)
+    dt = ps[0].dt
+    ft = np.float64 if dtype == "f64" else np.float32
     for call in range(2):
-        a.step(p.dt, 20)
-        binding.check(bq.lib().bq_step_fixed_scratch(b.ptr, C.c_double(p.dt), C.c_int64(20), stream))
+        a.step(dt, 20)
+        _fixed_step(b, dt, 20)
         torch.cuda.synchronize()
-        ft = np.float64 if dtype == "f64" else np.float32
         ra = _raw(a).view(ft)
         rb = _raw(b).view(ft)
         assert np.all(np.isfinite(rb))
         err = np.max(np.abs(ra - rb)) / np.max(np.abs(ra))
         assert err <= tol, (call, err)
         ea, eb = a.evaluate(), b.evaluate()
-        assert abs(ea[0] - eb[0]) <= tol * max(1.0, abs(ea[0]))
+        assert np.max(np.abs(ea - eb)) <= tol * max(1.0, np.max(np.abs(ea)))
         assert abs(a.time() - b.time()) < 1e-15
 
 
