@@ -750,7 +750,7 @@ struct bq_state {
   int B = 0, nm = 0, dtype = 0, method = 0, basis = 0, n_sys = 0, n_work = 0, smem_bytes = 0, use_m1 = 0, m1_variant = 0;
   int trace_small = 0, block_small = 0;
   int solve_ok = 0, solve_smem = 0, last_solve_grid = 0, solve_mg = 0, solve_mg_smem = 0;
-  int use_pipe = 0, pipe_off_u = 0, pipe_zero_off = 0, pipe_zero_bytes = 0, pipe_mmax = 0;
+  int use_pipe = 0, pipe_off_u = 0, pipe_zero_off = 0, pipe_zero_bytes = 0, pipe_mmax = 0, pipe_obs = 0;
   int pipe_slot[4] = {0, 0, 0, 0}, pipe_nslots[4] = {2, 2, 2, 2}, pipe_grid[4] = {1, 1, 1, 1}, pipe_mv_bytes = 0;
   // 1 after bq_load_state: comp is zero by definition but not written yet (the pipelined and
   // streaming kernels skip reading it at their next stage 1; every other consumer clears it
@@ -817,6 +817,7 @@ struct Plan {
   std::vector<int> order;  // batched solve queue (largest system first); empty: not eligible
   // pipelined stage kernel
   int use_pipe = 0, pipe_off_u = 0, pipe_zero_off = 0, pipe_zero_bytes = 0, pipe_slot = 0, pipe_mmax = 0;
+  int pipe_obs = 1;  // the last stage evaluates every problem's Tr(rho0 A) (supports of <= 32 entries)
   std::vector<unsigned char> pparams;
   std::vector<bq::PipeRec> precs;
   size_t work_cap = 0;  // work-item capacity of the pool (the smallest schedulable tile, 32 points)
@@ -1162,6 +1163,9 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
             bq::PipeChan pc;
             std::memset(&pc, 0, sizeof(pc));
             for (int i = 0; i < 4 && i < cd.n_par; ++i) pc.p[i] = P.chpar[cd.par_off + i];
+            pc.f[0] = (float)pc.p[0];
+            pc.f[1] = (float)pc.p[1];
+            pc.f[2] = cd.kind == BQ_CH_GAUSS ? (float)(1.0 / (2.0 * pc.p[3] * pc.p[3])) : 0.f;
             pc.kind = cd.kind;
             pc.par_off = cd.par_off;
             pc.n_par = cd.n_par;
@@ -1178,6 +1182,29 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
           for (int q = 0; q < m.nS; ++q) put_w(m.wSx[q] >= 0 ? local(m.wSx[q]) : -1);
           for (int q = 0; q < m.nS; ++q) put_w(m.wSy[q] >= 0 ? local(m.wSy[q]) : -1);
           while (blk.size() % 16) blk.push_back(0);
+          // the problem's Tr(rho0 A) entries, one per lane of the warp that evaluates the
+          // observable in the last stage (a larger support leaves it to the evaluation kernel)
+          {
+            const EvalGroup& g = P.groups[b];
+            auto* hp = reinterpret_cast<bq::PipeHdr*>(blk.data());
+            hp->obs_off = (int)blk.size();
+            hp->n_obs = g.n_e <= 32 ? g.n_e : 0;
+            if (g.n_e > 32) P.pipe_obs = 0;
+            for (int e = 0; e < hp->n_obs; ++e) {
+              const EvalEntry& en = P.entries[g.e_off + e];
+              if (cs == 16) {
+                bq::PipeObs<double2> o;
+                std::memset(&o, 0, sizeof(o));
+                o.kx = en.kx; o.ly = en.ly; o.f = make_double2(en.f_re, en.f_im);
+                blk.insert(blk.end(), (const unsigned char*)&o, (const unsigned char*)&o + sizeof(o));
+              } else {
+                bq::PipeObs<float2> o;
+                o.kx = en.kx; o.ly = en.ly; o.f = make_float2((float)en.f_re, (float)en.f_im);
+                blk.insert(blk.end(), (const unsigned char*)&o, (const unsigned char*)&o + sizeof(o));
+              }
+            }
+          }
+          while (blk.size() % 16) blk.push_back(0);
           poff[b] = (int)P.pparams.size();
           pbytes[b] = (int)blk.size();
           P.pparams.insert(P.pparams.end(), blk.begin(), blk.end());
@@ -1185,6 +1212,8 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
         }
         static_assert(sizeof(bq::PipeCoef<float2>) == 16 && sizeof(bq::PipeCoef<double2>) == 32,
                       "coefficient records as written above");
+        static_assert(sizeof(bq::PipeObs<float2>) == 16 && sizeof(bq::PipeObs<double2>) == 32,
+                      "entry records keep the block 16-B aligned");
         for (int i = 0; i < (int)P.sys.size(); ++i) {
           const SysDesc& sd = P.sys[i];
           bq::PipeRec r;
@@ -1206,8 +1235,8 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
           r.c_im = sd.c_im;
           r.w_re = sd.w_re;
           r.w_im = sd.w_im;
-          r.e_off = P.groups[sd.prob].e_off;  // trace group of the problem
-          r.n_e = P.groups[sd.prob].n_e;
+          r.w32_re = (float)sd.w_re;
+          r.w32_im = (float)sd.w_im;
           P.precs.push_back(r);
           blk_max = std::max(blk_max, (size_t)r.blk_elems);
         }
@@ -1449,6 +1478,7 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   for (const WorkItem& w : P.work) st->has_gread = st->has_gread || w.gread;
   st->pipe_off_u = P.pipe_off_u; st->pipe_zero_off = P.pipe_zero_off; st->pipe_zero_bytes = P.pipe_zero_bytes;
   st->pipe_mmax = P.pipe_mmax;
+  st->pipe_obs = P.pipe_obs;
   for (int q = 0; q < 4; ++q) st->pipe_slot[q] = P.pipe_slot;
   {
     // row and column coefficient records of the merged path
@@ -1571,9 +1601,8 @@ static cudaError_t launch_any_stage(bq_state* s, const bq::StageArgs& a, cudaStr
     pa.mmax = s->pipe_mmax;
     pa.reverse = a.reverse;
     pa.comp_zero = a.stage == 1 ? s->comp_zero : 0;
-    pa.entries = (const bq::EvalEntry*)(b + L.off_entries);
-    pa.obs = (double2*)(b + L.off_obs);
-    s->obs_valid = a.stage == 4;
+    pa.obs = s->pipe_obs ? (double2*)(b + L.off_obs) : nullptr;
+    s->obs_valid = a.stage == 4 && s->pipe_obs;
     pa.dt = a.dt;
     pa.horizon = a.horizon;
     if (a.stage == 1) s->comp_zero = 0;  // stage 4 of this step writes comp everywhere

@@ -156,21 +156,30 @@ struct __align__(16) PipeRec {
   int merged;       // 1: merged-stencil path (every shift in {-1, 0, 1}, M <= 64)
   int nb, rb;       // merged path: nb column strips of rb rows (thread t: column t % M, strip t / M)
   float inv_m;      // 1 / M (strip index without an integer division)
-  int e_off, n_e;   // entries of the problem's Tr(rho0 A) group (EvalEntry)
+  float w32_re, w32_im;  // the weight below rounded to FP32 (the FP32 kernels' observable)
   int pad;
   double c_re, c_im;  // separation constant C of the system (Eq. 304)
   double w_re, w_im;  // weight of the system's initial condition
 };
 // Header of a parameter block (128 B), followed by n_terms PipeCoef records (X, Y, S terms in
 // program order), n_ch PipeChan records, dx[M], dy[M] (complex) and the weight tables
-// wX[nX][M], wY[nY][M], wSx[nS][M], wSy[nS][M] (real), the whole block padded to 16 B.
+// wX[nX][M], wY[nY][M], wSx[nS][M], wSy[nS][M] (real), then n_obs PipeObs records at a 16-B
+// boundary, the whole block padded to 16 B.
 struct PipeHdr {
   int M, nX, nY, nS, has_sep, has_r, ntot, merged;  // merged: all shifts in {-1,0,1}, nS <= 2, M <= 64
   int sX[BQ_M1_MAXT], sY[BQ_M1_MAXT], sSx[BQ_M1_MAXT], sSy[BQ_M1_MAXT];
   int sdiag;    // bit q: sandwich term q acts only where k = l (secular projector)
   int n_terms;  // nX + nY + nS
   int n_ch;     // drive envelopes behind the time-dependent terms (0..2)
-  int pad2[5];
+  int obs_off;  // byte offset of the PipeObs records (the problem's Tr(rho0 A) entries)
+  int n_obs;    // their count (0..32; 0 also when the kernel does not evaluate the observable)
+  int pad2[3];
+};
+// An entry (k, l, f) of rho0's support in a parameter block, f in the state's precision.
+template <typename CT>
+struct PipeObs {
+  int kx, ly;  // flat indices (this path has one mode)
+  CT f;
 };
 // A drive envelope (bq.h channel kinds) in a parameter block: its first four parameters and,
 // for a piecewise-constant envelope, the offset and count of its parameters in the state's
@@ -178,6 +187,7 @@ struct PipeHdr {
 struct PipeChan {
   double p[4];
   int kind, par_off, n_par, pad;
+  float f[4];  // the same in FP32: amplitude (re, im), then 1 / (2 sigma^2) for a Gaussian
 };
 // Stage coefficient of one term: c times the value of the block's envelope ch (0 or 1, -1:
 // static) at the stage time, or its conjugate (conj = 1).
@@ -212,8 +222,7 @@ struct PipeArgs {
   int mmax, reverse;        // largest M of the state (coefficient records); reversed-time reading
   int comp_zero;            // stage 1: comp is known to be zero (a freshly loaded state); not read
   int pad;
-  const EvalEntry* entries; // stage 4: Tr(rho0 A) entries (PipeRec::e_off, n_e)
-  double2* obs;             // stage 4: per system, w sum_e f_e G(k_e, l_e) of the updated state
+  double2* obs;             // stage 4 (or null): per system, w sum_e f_e G(k_e, l_e) of the updated state
   double dt, horizon;
 };
 

@@ -623,6 +623,16 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Asynchronous copy of one complex value (8 or 16 bytes, naturally aligned) from global to
+// shared memory; the issuing thread reads it after cp_async_wait_all.
+template <typename C>
+__device__ __forceinline__ void cp_async_c(C* dst, const C* src) {
+  static_assert(sizeof(C) == 8 || sizeof(C) == 16, "complex FP32 or FP64");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"((int)sizeof(C))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 #define BQ_PIPE_RB 16  // system records per batch (power of two)
 #define BQ_WAIT_LIMIT (1 << 22)
@@ -638,35 +648,48 @@ __device__ __forceinline__ double pipe_chan_time(int kind, double tau_step, int 
   return reverse ? horizon - tau : tau;
 }
 
-// Envelope value (bq.h channel kinds) at this stage's time from a parameter block's record,
-// in FP64 (the Gaussian's exponential in the state's precision, as chan_value_t); a
-// piecewise-constant envelope reads its segment value from the channel parameter pool.
+// Envelope value (bq.h channel kinds) at physical time t (t_mid: the step midpoint, where a
+// piecewise-constant envelope is read) from a parameter block's record.  In FP32 the Gaussian
+// costs one FP64 subtraction and otherwise runs on the FP32 pipe with the record's FP32
+// copies (GB300's FP64 rate is a small fraction of its FP32 rate and this sits on every
+// system's path); a piecewise-constant envelope reads its segment value from the channel
+// parameter pool.
 template <typename T>
-__device__ __forceinline__ double2 pipe_chan_value(const PipeChan& c, const double* chpar, double tau_step, int stage,
-                                                   double dt, double horizon, int reverse) {
-  const double t = pipe_chan_time(c.kind, tau_step, stage, dt, horizon, reverse);
+__device__ __forceinline__ typename C2T<T>::type pipe_chan_value(const PipeChan& c, const double* chpar, double t,
+                                                                 double t_mid) {
+  using C = typename C2T<T>::type;
   switch (c.kind) {
     case 0:  // CONST
-      return make_double2(c.p[0], c.p[1]);
+      return cmk<C>(c.p[0], c.p[1]);
     case 1: {  // GAUSS
-      const T d = (T)(t - c.p[2]);
-      const double e = (double)dev_exp<T>(-(d * d) / ((T)2 * (T)c.p[3] * (T)c.p[3]));
-      return make_double2(c.p[0] * e, c.p[1] * e);
+      C v;
+      if constexpr (sizeof(T) == 8) {
+        const double d = t - c.p[2];
+        const double e = dev_exp<double>(-(d * d) / (2.0 * c.p[3] * c.p[3]));
+        v.x = c.p[0] * e;
+        v.y = c.p[1] * e;
+      } else {
+        const float d = (float)(t - c.p[2]);
+        const float e = dev_exp<float>(-(d * d) * c.f[2]);
+        v.x = c.f[0] * e;
+        v.y = c.f[1] * e;
+      }
+      return v;
     }
     case 2: {  // PWC
       const int n_seg = (c.n_par - 2) / 2;
-      const double x = floor((t - c.p[0]) / c.p[1]);
-      if (!(x >= 0.0) || x >= (double)n_seg) return make_double2(0.0, 0.0);
+      const double x = floor((t_mid - c.p[0]) / c.p[1]);
+      if (!(x >= 0.0) || x >= (double)n_seg) return cmk<C>(0.0, 0.0);
       const int sg = (int)x;
-      return make_double2(chpar[c.par_off + 2 + 2 * sg], chpar[c.par_off + 3 + 2 * sg]);
+      return cmk<C>(chpar[c.par_off + 2 + 2 * sg], chpar[c.par_off + 3 + 2 * sg]);
     }
     case 3: {  // CEXP
       double sn, cs;
       sincos(c.p[2] * t, &sn, &cs);
-      return make_double2(c.p[0] * cs - c.p[1] * sn, c.p[0] * sn + c.p[1] * cs);
+      return cmk<C>(c.p[0] * cs - c.p[1] * sn, c.p[0] * sn + c.p[1] * cs);
     }
     default:
-      return make_double2(0.0, 0.0);
+      return cmk<C>(0.0, 0.0);
   }
 }
 
@@ -753,7 +776,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long full[4];
   __shared__ PipeRec recs[2][BQ_PIPE_RB];  // records of two batches of systems
-  __shared__ double s_tau;
+  __shared__ double s_t[2];  // physical time of this stage, and of the step midpoint
 
   const int tid = threadIdx.x;
   const int G = gridDim.x;
@@ -762,7 +785,9 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
   const int cs = (int)sizeof(C);
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
-    s_tau = A.tau_base[0] + (double)(*(volatile long long*)A.counter) * A.dt;
+    const double tau = A.tau_base[0] + (double)(*(volatile long long*)A.counter) * A.dt;
+    s_t[0] = pipe_chan_time(1, tau, STAGE, A.dt, A.horizon, A.reverse);
+    s_t[1] = pipe_chan_time(2, tau, STAGE, A.dt, A.horizon, A.reverse);
   }
   // Zero the stage-input region of every slot and its guard bands once: neighbour reads at
   // the edges of a system (whose coefficients are zero there) land in them, so they must
@@ -821,42 +846,72 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
   const C zero = cmk<C>(0.0, 0.0);
 
   // Stage 4: the Tr(rho0 A) contribution of system j (Eqs. 7, 11: w sum_e f_e (G_x[k_e]
-  // G_y[l_e] + R[k_e, l_e]) over the entries of rho0's support) from the updated state y - comp,
-  // by warp 1 with a shuffle reduction, once the CTA's barrier has made every thread's writes
-  // of system j visible (at the top of the next system, or after the last one).
-  auto observe = [&](int j) {
-    if (STAGE != 4 || A.obs == nullptr || (tid >> 5) != 1) return;
+  // G_y[l_e] + R[k_e, l_e]) over the entries of rho0's support) from the updated state
+  // y - comp, in the state's precision, by warp 1 (lane e: entry e).  No global round trip
+  // sits on the warp's path between two barriers: at the end of system j it takes the entries
+  // from the parameter block still in slot j (obs_take); after the barrier that makes every
+  // thread's writes of system j visible it starts asynchronous copies of the values into
+  // shared memory (obs_load, so that no register is held across the next system); they are
+  // first read at the end of system j + 1 (obs_give: the products, a shuffle reduction, one
+  // store per system).
+  const bool obs_on = STAGE == 4 && A.obs != nullptr && (tid >> 5) == 1;
+  __shared__ C s_of[32];     // w f_e of the pending entries
+  __shared__ C s_ov[6][32];  // y and comp at their G_x, G_y and R points
+  int oa = -1, ob = -1, oc = -1, on = 0;
+  auto obs_take = [&](int j) {
     const PipeRec& rj = recs[(j / BQ_PIPE_RB) & 1][j % BQ_PIPE_RB];
+    const unsigned char* sj = slot_ptr(j % S);
+    const PipeHdr& hj = *reinterpret_cast<const PipeHdr*>(sj);
     const int lane = tid & 31;
-    auto val = [&](int i) {
-      const C a = yg[i], c = compg[i];
-      return make_double2((double)(a.x - c.x), (double)(a.y - c.y));
-    };
-    double re = 0.0, im = 0.0;
-    for (int e = lane; e < rj.n_e; e += 32) {
-      const EvalEntry en = A.entries[rj.e_off + e];
-      double vr = 0.0, vi = 0.0;
+    on = hj.n_obs;
+    oa = ob = oc = -1;
+    if (lane < on) {
+      const PipeObs<C>& en = reinterpret_cast<const PipeObs<C>*>(sj + hj.obs_off)[lane];
       if (rj.gy_off >= 0) {
-        const double2 a = val(rj.blk_off + en.kx), b = val(rj.blk_off + rj.gy_off + en.ly);
-        vr += a.x * b.x - a.y * b.y;
-        vi += a.x * b.y + a.y * b.x;
+        oa = rj.blk_off + en.kx;
+        ob = rj.blk_off + rj.gy_off + en.ly;
       }
-      if (rj.r_off >= 0) {
-        const double2 c = val(rj.blk_off + rj.r_off + en.kx * rj.M + en.ly);
-        vr += c.x;
-        vi += c.y;
-      }
-      const double fr = rj.w_re * en.f_re - rj.w_im * en.f_im;
-      const double fi = rj.w_re * en.f_im + rj.w_im * en.f_re;
-      re += fr * vr - fi * vi;
-      im += fr * vi + fi * vr;
+      if (rj.r_off >= 0) oc = rj.blk_off + rj.r_off + en.kx * rj.M + en.ly;
+      C w;
+      if constexpr (sizeof(T) == 8) w = cmk<C>(rj.w_re, rj.w_im);
+      else w = make_float2(rj.w32_re, rj.w32_im);
+      s_of[lane] = cmul(w, en.f);
     }
+  };
+  auto obs_load = [&]() {
+    const int lane = tid & 31;
+    if (oa >= 0) {
+      cp_async_c(&s_ov[0][lane], yg + oa);
+      cp_async_c(&s_ov[1][lane], compg + oa);
+      cp_async_c(&s_ov[2][lane], yg + ob);
+      cp_async_c(&s_ov[3][lane], compg + ob);
+    }
+    if (oc >= 0) {
+      cp_async_c(&s_ov[4][lane], yg + oc);
+      cp_async_c(&s_ov[5][lane], compg + oc);
+    }
+    cp_async_commit();
+  };
+  auto obs_give = [&](int j) {
+    const int lane = tid & 31;
+    cp_async_wait_all();
+    C v = zero;
+    if (oa >= 0) v = cmul(cadd(s_ov[0][lane], cneg(s_ov[1][lane])), cadd(s_ov[2][lane], cneg(s_ov[3][lane])));
+    if (oc >= 0) v = cadd(v, cadd(s_ov[4][lane], cneg(s_ov[5][lane])));
+    C c = lane < on ? cmul(s_of[lane], v) : zero;
+    if (on > 1) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      re += __shfl_down_sync(0xffffffffu, re, o);
-      im += __shfl_down_sync(0xffffffffu, im, o);
+      for (int o = 16; o > 0; o >>= 1) {
+        c.x += __shfl_down_sync(0xffffffffu, c.x, o);
+        c.y += __shfl_down_sync(0xffffffffu, c.y, o);
+      }
     }
-    if (lane == 0) A.obs[blockIdx.x + (size_t)j * G] = make_double2(re, im);
+    if (lane == 0) A.obs[blockIdx.x + (size_t)j * G] = make_double2((double)c.x, (double)c.y);
+  };
+  auto obs_end = [&](int j) {
+    if (!obs_on) return;
+    if (j > 0) obs_give(j - 1);
+    obs_take(j);
   };
 
   for (int j = 0; j < nj; ++j) {
@@ -922,7 +977,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
     // every thread is past system j - 1: its slot ((j + S - 1) % S) and the coefficient
     // records are free, so the next copy can start now
     if (tid == 0 && jn < nj) issue(jn);
-    if (j > 0) observe(j - 1);
+    if (obs_on && j > 0) obs_load();
     unsigned char* sl = slot_ptr(j % S);
     const PipeHdr& h = *reinterpret_cast<const PipeHdr*>(sl);
     const int nX = h.nX, nY = h.nY, nS = h.nS, has_sep = h.has_sep;
@@ -942,21 +997,19 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
     const C Cc = cmk<C>(r.c_re, r.c_im);
     // drive envelopes of the problem's time-dependent terms at this stage's time, from the
     // block (threads that build coefficient records; every thread on the general path)
-    double2 e0 = make_double2(1.0, 0.0), e1 = make_double2(1.0, 0.0);
+    C e0 = cmk<C>(1.0, 0.0), e1 = cmk<C>(1.0, 0.0);
     if (!merged || rowb || colb) {
-      if (h.n_ch > 0) e0 = pipe_chan_value<T>(pc[0], A.chpar, s_tau, STAGE, A.dt, A.horizon, A.reverse);
-      if (h.n_ch > 1) e1 = pipe_chan_value<T>(pc[1], A.chpar, s_tau, STAGE, A.dt, A.horizon, A.reverse);
+      if (h.n_ch > 0) e0 = pipe_chan_value<T>(pc[0], A.chpar, s_t[0], s_t[1]);
+      if (h.n_ch > 1) e1 = pipe_chan_value<T>(pc[1], A.chpar, s_t[0], s_t[1]);
     }
-    // stage coefficient of term q: static part times the envelope (or its conjugate), formed
-    // in FP64 and rounded once to the state's precision
+    // stage coefficient of term q: static part times the envelope (or its conjugate)
     auto coef = [&](int q) {
       const C c = tc[q].c;
       const int ch = tc[q].ch;
       if (ch < 0) return c;
-      double2 e = ch == 0 ? e0 : e1;
+      C e = ch == 0 ? e0 : e1;
       if (tc[q].conj) e.y = -e.y;
-      const double cr = (double)c.x, ci = (double)c.y;
-      return cmk<C>(cr * e.x - ci * e.y, cr * e.y + ci * e.x);
+      return cmul(c, e);
     };
     const int nr = h.has_r ? M * M : 0;
     const int ntot = h.ntot;
@@ -1098,6 +1151,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
         kv = cfma(vv[2], hi, kv);
         pipe_combine<STAGE>(uout, accg, yg, compg, gg, uc, kv, sG, yG, h2, hh, w_hi, w_lo);
       }
+      obs_end(j);
       // no barrier here: the wait at the top of the next system orders the reuse of the
       // slot and of the coefficient records
       continue;
@@ -1163,9 +1217,13 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
       const C yv = RDY ? yg[gi] : zero;
       pipe_combine<STAGE>(uout, accg, yg, compg, gi, uc, kv, sv, yv, h2, hh, w_hi, w_lo);
     }
+    obs_end(j);
   }
   __syncthreads();  // every system of this CTA is written before it takes its ticket
-  if (nj > 0) observe(nj - 1);
+  if (obs_on && nj > 0) {
+    obs_load();
+    obs_give(nj - 1);
+  }
   if (STAGE == 4 && tid == 0) {
     __threadfence();
     const unsigned int t = atomicAdd(A.ticket, 1u);
