@@ -1483,7 +1483,7 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   {
     // row and column coefficient records of the merged path
     const int ms = P.m1_variant == 0 ? 2 : BQ_M1_MAXT;
-    st->pipe_mv_bytes = (int)(((size_t)2 * BQ_PIPE_RS(ms) * P.pipe_mmax * (o->dtype == BQ_F64 ? 16 : 8) + 127) & ~(size_t)127);
+    st->pipe_mv_bytes = (int)(((size_t)2 * BQ_PIPE_RS(ms) * BQ_MERGED_MAXM * (o->dtype == BQ_F64 ? 16 : 8) + 127) & ~(size_t)127);
   }
   if (st->use_pipe) {
     // double buffering at the occupancy limit; bq_autotune may pick another schedule

@@ -726,6 +726,17 @@ __device__ __forceinline__ void ld_pair<double2>(const double2* p, double2& a, d
   a = p[0];
   b = p[1];
 }
+template <typename C>
+__device__ __forceinline__ void st_pair(C* p, C a, C b);
+template <>
+__device__ __forceinline__ void st_pair<float2>(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+template <>
+__device__ __forceinline__ void st_pair<double2>(double2* p, double2 a, double2 b) {
+  p[0] = a;
+  p[1] = b;
+}
 
 // RK4 update of one element in the pipelined stage kernel.  The state value of an element is
 // y - comp, with comp the (negated) rounding residual of the last update: the state advances
@@ -806,8 +817,11 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
   load_batch(0);
   __syncthreads();
   auto slot_ptr = [&](int s) { return smem_raw + (size_t)s * A.slot_bytes; };
-  C* rowv = reinterpret_cast<C*>(smem_raw + (size_t)S * A.slot_bytes);  // [mmax][RS]
-  C* colv = rowv + (size_t)A.mmax * RS;                                  // [mmax][RS]
+  // coefficient records of rows and columns, pair-major: pair p (fields 2p, 2p + 1) of row k
+  // at rowv[(p BQ_MERGED_MAXM + k) 2], so that lanes with consecutive k or l touch consecutive
+  // 16-byte words
+  C* rowv = reinterpret_cast<C*>(smem_raw + (size_t)S * A.slot_bytes);  // [RS / 2][BQ_MERGED_MAXM][2]
+  C* colv = rowv + (size_t)BQ_MERGED_MAXM * RS;                          // [RS / 2][BQ_MERGED_MAXM][2]
 
   C* uout = reinterpret_cast<C*>(A.u_out);
   C* yg = reinterpret_cast<C*>(A.y);
@@ -1033,17 +1047,23 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
             const C v = cscale(coef(q), wX[q * M + i]);
             if (h.sX[q] == 0) a0 = cadd(a0, v); else if (h.sX[q] < 0) am = cadd(am, v); else ap = cadd(ap, v);
           }
-        C* rv = rowv + i * RS;
-        rv[0] = a0; rv[1] = am; rv[2] = ap;
+        C f[RS];
+        f[0] = a0; f[1] = am; f[2] = ap;
 #pragma unroll
-        for (int q = 0; q < MS; ++q)
+        for (int q = 0; q < MS; ++q) {
+          f[3 + 2 * q] = zero;
+          f[4 + 2 * q] = zero;
           if (q < nS) {
             const C sx = cscale(coef(nX + nY + q), wSx[q * M + i]);
             const int xs = i + h.sSx[q];
             const C gx = (has_sep && xs >= 0 && xs < M) ? ugx[xs] : zero;
-            rv[3 + 2 * q] = sx;
-            rv[4 + 2 * q] = cmul(sx, gx);
+            f[3 + 2 * q] = sx;
+            f[4 + 2 * q] = cmul(sx, gx);
           }
+        }
+        if (RS > 3 + 2 * MS) f[RS - 1] = zero;
+#pragma unroll
+        for (int p = 0; p < RS / 2; ++p) st_pair(rowv + (p * BQ_MERGED_MAXM + i) * 2, f[2 * p], f[2 * p + 1]);
       } else if (colb) {
         const int i = tid - BQ_MERGED_MAXM;
         C b0 = dy[i], bm = zero, bp = zero;
@@ -1053,60 +1073,70 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
             const C v = cscale(coef(nX + q), wY[q * M + i]);
             if (h.sY[q] == 0) b0 = cadd(b0, v); else if (h.sY[q] < 0) bm = cadd(bm, v); else bp = cadd(bp, v);
           }
-        C* cvv = colv + i * RS;
-        cvv[0] = b0; cvv[1] = bm; cvv[2] = bp;
+        C f[RS];
+        f[0] = b0; f[1] = bm; f[2] = bp;
 #pragma unroll
-        for (int q = 0; q < MS; ++q)
+        for (int q = 0; q < MS; ++q) {
+          f[3 + 2 * q] = zero;
+          f[4 + 2 * q] = zero;
           if (q < nS) {
             const T wy = wSy[q * M + i];
             const int ys = i + h.sSy[q];
-            C sy;
-            sy.x = wy;
-            sy.y = (T)0;
-            cvv[3 + 2 * q] = sy;
-            cvv[4 + 2 * q] = (has_sep && ys >= 0 && ys < M) ? cscale(ugy[ys], wy) : zero;
+            f[3 + 2 * q].x = wy;
+            if (has_sep && ys >= 0 && ys < M) f[4 + 2 * q] = cscale(ugy[ys], wy);
           }
+        }
+        if (RS > 3 + 2 * MS) f[RS - 1] = zero;
+#pragma unroll
+        for (int p = 0; p < RS / 2; ++p) st_pair(colv + (p * BQ_MERGED_MAXM + i) * 2, f[2 * p], f[2 * p + 1]);
       }
       __syncthreads();
       if (k0 < k1) {
-        const C* cvv = colv + l * RS;
-        const C b0 = cvv[0], bm = cvv[1], bp = cvv[2];
+        // field f of column l's record: pair f / 2, half f % 2
+        auto cfld = [&](int f) { return colv[((f >> 1) * BQ_MERGED_MAXM + l) * 2 + (f & 1)]; };
+        const C b0 = cfld(0), bm = cfld(1), bp = cfld(2);
         T syq[MS];
         C gyq[MS];
         int soff[MS];
 #pragma unroll
         for (int q = 0; q < MS; ++q) {
-          syq[q] = q < nS ? cvv[3 + 2 * q].x : (T)0;
-          gyq[q] = q < nS ? cvv[4 + 2 * q] : zero;
+          syq[q] = q < nS ? cfld(3 + 2 * q).x : (T)0;
+          gyq[q] = q < nS ? cfld(4 + 2 * q) : zero;
           soff[q] = h.sSx[q] * M + h.sSy[q];
         }
         const C* up = ur + k0 * M + l;  // the point (kk, l)
-        const C* rv = rowv + k0 * RS;
+        const C* rv = rowv + k0 * 2;     // pair 0 of row kk's record
         int go = gb + r.r_off + k0 * M + l;
         C um = up[-M];  // (k0 - 1, l): the row above, or a guard / G value with Am = 0
         C uc = up[0];
-        // the stencil of one point from its row record and the column values in registers
+        // the stencil of one point from its row record (pair p at rrec + 2 p BQ_MERGED_MAXM)
+        // and the column values in registers.  The row-neighbour, column-neighbour and
+        // sandwich parts are summed in independent chains and the row and column parts added
+        // to each other before the diagonal part: a point and its mirror (l, k) then round
+        // alike, so R keeps the conjugate symmetry of a Hermitian operator's expansion.
+        constexpr int PS = 2 * BQ_MERGED_MAXM;
         auto point = [&](const C* rrec, const C* pu, C cm, C cc, C cd, bool on_diag) {
           C a0, am, ap, sxn;
           ld_pair(rrec, a0, am);
-          ld_pair(rrec + 2, ap, sxn);
-          C kv = cmul(cadd(a0, b0), cc);
-          kv = cfma(am, cm, kv);
-          kv = cfma(ap, cd, kv);
-          kv = cfma(bm, pu[-1], kv);
-          kv = cfma(bp, pu[1], kv);
+          ld_pair(rrec + PS, ap, sxn);
+          const C kd = cmul(cadd(a0, b0), cc);
+          C kr = cmul(am, cm);
+          C kc = cmul(bm, pu[-1]);
+          kr = cfma(ap, cd, kr);
+          kc = cfma(bp, pu[1], kc);
+          C ks = zero;
 #pragma unroll
           for (int q = 0; q < MS; ++q)
             if (q < nS) {
               const C sx = sxn;
               C sg;
-              ld_pair(rrec + 4 + 2 * q, sg, sxn);
+              ld_pair(rrec + (2 + q) * PS, sg, sxn);
               if (!((sdiag >> q) & 1) || on_diag) {  // secular projector: k = l only
-                kv = cfma(cscale(sx, syq[q]), pu[soff[q]], kv);
-                kv = cfma(sg, gyq[q], kv);
+                ks = cfma(cscale(sx, syq[q]), pu[soff[q]], ks);
+                ks = cfma(sg, gyq[q], ks);
               }
             }
-          return kv;
+          return cadd(cadd(kd, cadd(kr, kc)), ks);
         };
         // two rows per iteration (independent chains); streamed values in a register ring
         // two rows ahead of use
@@ -1121,18 +1151,18 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
             if (rd) s1 = pre[go + 3 * M];
             if (RDY) y1 = yg[go + 3 * M];
           }
-          const C ud = up[M];                                      // row kk + 1 (a guard row past M - 1)
-          const C udB = (two && kk + 2 < M) ? up[2 * M] : zero;   // row kk + 2
+          const C ud = up[M];                     // row kk + 1 (a guard row past M - 1)
+          const C udB = two ? up[2 * M] : zero;   // row kk + 2 (at most row M: the guard band)
           const C kvA = point(rv, up, um, uc, ud, kk == l);
           pipe_combine<STAGE>(uout, accg, yg, compg, go, uc, kvA, sA, yA, h2, hh, w_hi, w_lo);
           if (two) {
-            const C kvB = point(rv + RS, up + M, uc, ud, udB, kk + 1 == l);
+            const C kvB = point(rv + 2, up + M, uc, ud, udB, kk + 1 == l);
             pipe_combine<STAGE>(uout, accg, yg, compg, go + M, ud, kvB, sB, yB, h2, hh, w_hi, w_lo);
           }
           um = ud;
           uc = udB;
           up += 2 * M;
-          rv += 2 * RS;
+          rv += 4;
           go += 2 * M;
         }
       }
@@ -1140,7 +1170,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
         const bool isx = gq < M;
         const int g = isx ? gq : gq - M;
         const C* gs = isx ? ugx : ugy;
-        const C* vv = (isx ? rowv : colv) + g * RS;
+        const C* vv = (isx ? rowv : colv) + g * 2;  // fields 0, 1 (pair 0) and 2 (pair 1)
         const C uc = gs[g];
         // neighbours outside the grid have zero coefficients; their reads stay in the slot
         const C lo = gs[g - 1], hi = gs[g + 1];
@@ -1148,7 +1178,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
         d = isx ? cadd(d, Cc) : cadd(d, cneg(Cc));
         C kv = cmul(d, uc);
         kv = cfma(vv[1], lo, kv);
-        kv = cfma(vv[2], hi, kv);
+        kv = cfma(vv[2 * BQ_MERGED_MAXM], hi, kv);
         pipe_combine<STAGE>(uout, accg, yg, compg, gg, uc, kv, sG, yG, h2, hh, w_hi, w_lo);
       }
       obs_end(j);
