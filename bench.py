@@ -266,21 +266,25 @@ class Clocks:
                 "samples": len(sm)}
 
 
+E2E_PARTS = 4
+
+
 def e2e_leg(specs, opts, schedule: dict, steps: int, world: int, barrier):
     """The headline step end to end through the C ABI, every step uploading the whole state
-    from pinned host memory and reading every instance's Tr(rho0 A) back: the batch as two
-    halves on two streams, pipelined (half A of step i is stepped while half B's input of step
-    i is uploaded and half B's result of step i - 1 is read back, and the other way round)."""
+    from pinned host memory and reading every instance's Tr(rho0 A) back: the batch as
+    E2E_PARTS states on as many streams, pipelined (while one part is stepped, the next part's
+    input is uploaded and the previous part's result is read back)."""
+    import numpy as np
     import torch
 
     import paper_2203_05526_gb300 as bq
-    half = len(specs) // 2
-    parts = [specs[:half], specs[half:]]
+    cut = [len(specs) * i // E2E_PARTS for i in range(E2E_PARTS + 1)]
+    parts = [specs[cut[i]:cut[i + 1]] for i in range(E2E_PARTS)]
     sts = [bq.State([bq.problem_from_spec(p) for p in part], opts) for part in parts]
     for st in sts:
         st.set_tune(stage_path=schedule["stage_path"], pipe_slots=schedule["pipe_slots"],
                     pipe_ctas_per_sm=schedule["pipe_ctas_per_sm"])
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    streams = [torch.cuda.Stream() for _ in parts]
     hosts = []
     for st in sts:
         h = torch.empty(st.state_bytes(), dtype=torch.uint8, pin_memory=True)
@@ -288,18 +292,16 @@ def e2e_leg(specs, opts, schedule: dict, steps: int, world: int, barrier):
         hosts.append(h)
     torch.cuda.synchronize()
 
-    def enqueue(h):
-        sts[h].load_state(hosts[h].data_ptr(), stream=streams[h])
-        sts[h].step(DT, 1, stream=streams[h])
+    outs = [torch.empty(2 * len(part), dtype=torch.float64, pin_memory=True) for part in parts]
 
     def run(n):
-        for i in range(n):
-            enqueue(0)
-            if i > 0:
-                sts[1].evaluate(stream=streams[1])  # half B, step i - 1 (device -> host, synchronises)
-            enqueue(1)
-            sts[0].evaluate(stream=streams[0])      # half A, step i
-        return sts[1].evaluate(stream=streams[1])   # half B, last step
+        # per step and part: upload the state, one RK4 step, Tr(rho0 A) of every instance back
+        # to pinned host memory, all enqueued on the part's stream (no host wait inside)
+        for _ in range(n):
+            for h in range(len(parts)):
+                sts[h].load_state(hosts[h].data_ptr(), stream=streams[h])
+                sts[h].step(DT, 1, stream=streams[h])
+                sts[h].evaluate_async(outs[h].data_ptr(), stream=streams[h])
 
     run(2)
     barrier()
@@ -317,10 +319,15 @@ def e2e_leg(specs, opts, schedule: dict, steps: int, world: int, barrier):
     e1.record(cur)
     barrier()
     ms = e0.elapsed_time(e1)
+    for h in range(len(parts)):
+        ref = sts[h].evaluate(stream=streams[h])  # synchronising read: error word, finiteness
+        assert np.array_equal(outs[h].numpy(), np.stack([ref.real, ref.imag], 1).ravel())
     pts = points_of(specs)
     return {"value": world * 4 * pts * steps / (ms / 1e3), "unit": METRIC,
             "h2d_bytes_per_step": sum(st.state_bytes() for st in sts), "d2h_bytes_per_step": 16 * len(specs),
-            "how": "two half-batch states on two streams, upload of one half overlapped with the other half's step"}
+            "how": f"{E2E_PARTS} states of a quarter of the batch each on as many streams, the upload of one part "
+                   "overlapped with the other parts' steps; observables read back with bq_evaluate_async into "
+                   "pinned host memory"}
 
 
 def alu_peaks():
@@ -814,6 +821,9 @@ def main():
         state.step(DT, 1)
         state.evaluate()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # every step's Tr(rho0 A) of all instances goes to pinned host memory (bq_evaluate_async:
+    # enqueued on the stream, so the host keeps the GPU fed instead of waiting for each read)
+    obs_host = [torch.empty(2 * len(specs), dtype=torch.float64, pin_memory=True) for _ in range(2)]
     clk = Clocks()
     clk.start(local)
     barrier()
@@ -825,9 +835,11 @@ def main():
         ev[i][0].record(stream)
         state.step(DT, 1)
         ev[i][1].record(stream)
-        obs = state.evaluate()
+        state.evaluate_async(obs_host[i % 2].data_ptr(), stream)
     t1.record(stream)
     barrier()
+    obs = state.evaluate()  # synchronising read: checks the device error word and finiteness
+    assert np.array_equal(obs_host[(args.steps - 1) % 2].numpy(), np.stack([obs.real, obs.imag], 1).ravel())
     launches = bq.launch_count() - n_launch0
     clocks = clk.stop()
     ms = t0.elapsed_time(t1)
@@ -863,9 +875,9 @@ def main():
             "avg_launch_us": launch_s * 1e6}
 
     # ---- end to end through the C ABI: state from pinned host memory, observables back ---
-    # The batch is split into two states on two streams: while one half is stepped, the other
-    # half's next input is uploaded (and the first half's observables are read back), so the
-    # host-to-device copies hide behind the stage kernels.
+    # The batch is split into E2E_PARTS states on as many streams: while one part is stepped,
+    # the next part's input is uploaded (and the previous part's observables are read back), so
+    # the host-to-device copies hide behind the stage kernels.
     nbytes = state.state_bytes()
     e2e = e2e_leg(specs, opts, schedule, args.steps, world, barrier)
     del state

@@ -226,7 +226,10 @@ typedef struct bq_tune {
   int gread;             /* BQ_PATH_TILED: 1 = split tiles read R (and the adjoint its cotangent)
                           * from global memory instead of staging halo windows in shared
                           * memory; 0 = only where a halo does not fit */
-  int pad;
+  int grad_coop;         /* bq_grad on the tiled path: 1 = one cooperative launch per checkpoint
+                          * segment and direction (all stages of the segment, separated by
+                          * grid barriers whose waits are bounded), 0 = one launch per stage;
+                          * ignored where the device has no cooperative launch */
   double grad_us;        /* bq_autotune_grad: device time of the trial gradient per RK4 step */
 } bq_tune;
 
@@ -327,6 +330,14 @@ int bq_time(const bq_state* s, double* tau);
 /* out_host[2b], out_host[2b+1] = Re, Im of Tr(rho0_b A_b(tau)) for every problem b
  * (warp reductions over initial conditions and rho0's support).  Synchronises stream. */
 int bq_evaluate(bq_state* s, double* out_host, void* stream);
+
+/* The same values without synchronising: the computation and the copy into out are
+ * enqueued on stream, and out holds them once the stream has reached that point.  out is
+ * device memory or pinned host memory (2 * B doubles, owned by the caller; pageable host
+ * memory also works but makes the copy synchronous for the host, as cudaMemcpyAsync does).
+ * Neither the device error word nor finiteness is checked here: bq_evaluate, or any later
+ * synchronising call, reports a bounded wait that gave up. */
+int bq_evaluate_async(bq_state* s, double* out, void* stream);
 
 /* Number-basis block <k|A_b(tau)|l> for every mode index < lo (the paper's epsilon_r
  * block uses lo = 3).  out_host holds B * D * D complex values (re, im interleaved),

@@ -44,7 +44,7 @@ class bq_tune(C.Structure):
     _fields_ = [("stage_path", C.c_int), ("pipe_slots", C.c_int), ("pipe_ctas_per_sm", C.c_int),
                 ("solve_kernel", C.c_int), ("solve_ctas_per_sm", C.c_int), ("n_candidates", C.c_int),
                 ("step_us", C.c_double), ("solve_us", C.c_double), ("tile", C.c_int), ("lanes", C.c_int), ("gread", C.c_int),
-                ("pad", C.c_int), ("grad_us", C.c_double)]
+                ("grad_coop", C.c_int), ("grad_us", C.c_double)]
 
 
 class bq_plan_info(C.Structure):
@@ -105,6 +105,7 @@ def lib() -> C.CDLL:
         "bq_stage_variant": (C.c_int, [vp, ip]),
         "bq_time": (C.c_int, [vp, dp]),
         "bq_evaluate": (C.c_int, [vp, dp, vp]),
+        "bq_evaluate_async": (C.c_int, [vp, vp, vp]),
         "bq_fock_block": (C.c_int, [vp, C.c_int, dp, vp]),
         "bq_state_info": (C.c_int, [vp, ip, C.POINTER(C.c_int64)]),
         "bq_system_info": (C.c_int, [vp, C.c_int, ip, ip, ip, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -133,7 +134,7 @@ def exported_symbols() -> List[str]:
     return [n for n in ("bq_problem_create", "bq_problem_destroy", "bq_problem_add_channel",
                         "bq_problem_add_h_term", "bq_problem_set_params", "bq_problem_add_jump",
                         "bq_problem_set_measured", "bq_problem_set_rho0", "bq_required_bytes", "bq_map",
-                        "bq_step", "bq_step_fixed_scratch", "bq_solve", "bq_solve_eligible", "bq_stage_variant", "bq_grad_size", "bq_grad_required_bytes", "bq_grad", "bq_time", "bq_evaluate", "bq_fock_block", "bq_state_info",
+                        "bq_step", "bq_step_fixed_scratch", "bq_solve", "bq_solve_eligible", "bq_stage_variant", "bq_grad_size", "bq_grad_required_bytes", "bq_grad", "bq_time", "bq_evaluate", "bq_evaluate_async", "bq_fock_block", "bq_state_info",
                         "bq_system_info", "bq_read_system", "bq_state_bytes", "bq_store_state",
                         "bq_load_state", "bq_set_time", "bq_state_destroy", "bq_status_string",
                         "bq_last_error", "bq_launch_count", "bq_fma_peak")]
@@ -316,7 +317,7 @@ class State:
         return dict(stage_path=PATH[t.stage_path], pipe_slots=t.pipe_slots, pipe_ctas_per_sm=t.pipe_ctas_per_sm,
                     solve_kernel=SOLVE_KERNEL[t.solve_kernel], solve_ctas_per_sm=t.solve_ctas_per_sm,
                     n_candidates=t.n_candidates, step_us=t.step_us, solve_us=t.solve_us, tile=t.tile, lanes=t.lanes,
-                    gread=t.gread, grad_us=t.grad_us)
+                    gread=t.gread, grad_coop=t.grad_coop, grad_us=t.grad_us)
 
     def get_tune(self) -> dict:
         t = bq_tune()
@@ -375,6 +376,11 @@ class State:
         check(lib().bq_evaluate(self.ptr, out, _stream_ptr(stream)))
         a = np.frombuffer(out, dtype=np.float64).copy()
         return a[0::2] + 1j * a[1::2]
+
+    def evaluate_async(self, out_ptr: int, stream=None) -> None:
+        """bq_evaluate_async: Re, Im of Tr(rho0_b A_b) (2 B doubles) into device or pinned host
+        memory at out_ptr, enqueued on stream without synchronising."""
+        check(lib().bq_evaluate_async(self.ptr, C.c_void_p(out_ptr), _stream_ptr(stream)))
 
     def fock_block(self, lo: int = 3, dim: Optional[int] = None, stream=None) -> np.ndarray:
         if dim is None:

@@ -767,6 +767,7 @@ struct bq_state {
   int gread_sched = 0;         // split tiles read R from global memory (schedule)
   double tune_grad_us = 0.0;   // last bq_autotune_grad result
   int lanes = 1;               // lanes per point of the tiled forward and the adjoint stage kernels
+  int grad_coop = 1;           // bq_grad: cooperative segment kernels where available
   int ng_max = 0;      // largest G_x / G_y point count over the systems
   // schedules (bq_get_tune / bq_set_tune / bq_autotune)
   int pipe_ok = 0;      // the pipelined path is available (single mode, two slots fit)
@@ -1824,6 +1825,7 @@ extern "C" int bq_get_tune(const bq_state* s, bq_tune* out) {
   out->tile = s->tile;
   out->lanes = s->lanes;
   out->gread = s->gread_sched;
+  out->grad_coop = s->grad_coop;
   out->grad_us = s->tune_grad_us;
   return BQ_OK;
 }
@@ -1868,6 +1870,7 @@ extern "C" int bq_set_tune(bq_state* s, const bq_tune* t) {
     s->solve_cap = t->solve_ctas_per_sm;
   }
   s->lanes = t->lanes == 0 ? default_lanes(s->sys) : t->lanes;
+  s->grad_coop = t->grad_coop != 0;
   drop_graph(s);
   return BQ_OK;
 }
@@ -2105,6 +2108,39 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
   const double tau0 = s->tau;
   const int k = checkpoint_every;
   CUDA_TRY(cudaMemsetAsync(w + G.grad, 0, (size_t)std::max(1, s->grad_size) * sizeof(double), st));
+  // Cooperative segment kernels (tiled path): one launch per segment and direction, grids of
+  // at most the resident CTAs and no more than the largest phase's items.
+  int grid_f = 0, grid_b = 0;
+  if (s->grad_coop && !s->use_m1) {
+    CUDA_TRY(bq::coop_max_grid(s->dtype, s->nm, false, s->smem_bytes, &grid_f));
+    CUDA_TRY(bq::coop_max_grid(s->dtype, s->nm, true, s->adj_smem, &grid_b));
+    const int src_items = s->max_s > 0 ? s->n_sys * s->max_s * 2 * ((s->ng_max + 7) / 8) : 0;
+    grid_f = std::min(grid_f, s->n_work);
+    grid_b = std::min(grid_b, std::max(s->n_work, src_items));
+  }
+  const bool coop = grid_f > 0 && grid_b > 0;
+  bq::CoopArgs P;
+  std::memset(&P, 0, sizeof(P));
+  if (coop) {
+    P.st = stage_args(s, 1, dt);
+    P.ua = b + L.off_ua;
+    P.ub = b + L.off_ub;
+    P.arr = arr;
+    P.n_work = s->n_work;
+    P.n_sys = s->n_sys;
+    P.max_s = s->max_s;
+    P.bar = (unsigned int*)(b + L.off_ctrl + 48);
+    P.error = (unsigned int*)(b + L.off_ctrl + 32);
+  }
+  auto coop_fwd = [&](double tau_seg, int64_t n, char* rec, cudaStream_t cs) -> cudaError_t {
+    P.tau0 = tau_seg;
+    P.n_steps = (int)n;
+    P.rec = rec;
+    cudaError_t e = cudaMemsetAsync(P.bar, 0, 8, cs);
+    if (e == cudaSuccess) e = bq::launch_coop(s->dtype, s->nm, false, P, s->smem_bytes, grid_f, cs);
+    g_launches++;
+    return e;
+  };
   // ---- forward with checkpoints ----------------------------------------------------------
   // (checkpoints hold the folded form: the recording stage kernels start from them)
   for (int64_t c = 0; c < G.n_ckpt; ++c) {
@@ -2112,6 +2148,10 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
     CUDA_TRY(ensure_comp(s, st));
     CUDA_TRY(cudaMemcpyAsync(w + G.ckpt + (2 * c) * arr, b + L.off_y, arr, cudaMemcpyDeviceToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(w + G.ckpt + (2 * c + 1) * arr, b + L.off_comp, arr, cudaMemcpyDeviceToDevice, st));
+    if (coop) {
+      CUDA_TRY(coop_fwd(tau0 + (double)n0 * dt, n1 - n0, nullptr, st));
+      continue;
+    }
     int r = set_tau(s, tau0 + (double)n0 * dt, st);
     if (r != BQ_OK) return r;
     CUDA_TRY(enqueue_steps_rec(s, dt, n1 - n0, st, nullptr, arr));
@@ -2129,6 +2169,43 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
                                s->dtype, st));
   g_launches++;
   // ---- backward sweep ----------------------------------------------------------------------
+  if (coop) {
+    // per segment, last first: restore its checkpoint, one cooperative launch recomputes it
+    // recording every stage input, one runs its adjoint (all on the caller's stream)
+    P.adj.sys = (const SysDesc*)(b + L.off_sys);
+    P.adj.terms = (const TermDesc*)(b + L.off_terms);
+    P.adj.chans = (const ChanDesc*)(b + L.off_chans);
+    P.adj.chpar = (const double*)(b + L.off_chpar);
+    P.adj.wtab = b + L.off_wtab;
+    P.adj.diag = b + L.off_diag;
+    P.adj.work = (const WorkItem*)(b + L.off_work);
+    P.adj.dc = (const double2*)(b + L.off_dc);
+    P.adj.srcred = w + G.srcred;
+    P.adj.grad = (double*)(w + G.grad);
+    P.adj.dt = dt;
+    P.adj.horizon = s->horizon;
+    P.adj.reverse = s->reverse;
+    P.adj.srcred_stride = s->srcred_stride;
+    P.adj.ng_max = s->ng_max;
+    P.adj.lanes = s->lanes;
+    P.ba = w + G.ba;
+    P.bb = w + G.bb;
+    char* lam = w + G.lam;
+    char* lacc = w + G.lacc;
+    char* rec = w + G.rec;
+    for (int64_t c = G.n_ckpt - 1; c >= 0; --c) {
+      const int64_t n0 = c * k, n1 = std::min<int64_t>(n_steps, n0 + k);
+      CUDA_TRY(cudaMemcpyAsync(b + L.off_y, w + G.ckpt + (2 * c) * arr, arr, cudaMemcpyDeviceToDevice, st));
+      CUDA_TRY(cudaMemcpyAsync(b + L.off_comp, w + G.ckpt + (2 * c + 1) * arr, arr, cudaMemcpyDeviceToDevice, st));
+      CUDA_TRY(coop_fwd(tau0 + (double)n0 * dt, n1 - n0, rec, st));
+      P.lam = lam;
+      P.lacc = lacc;
+      CUDA_TRY(cudaMemsetAsync(P.bar, 0, 8, st));
+      CUDA_TRY(bq::launch_coop(s->dtype, s->nm, true, P, s->adj_smem, grid_b, st));
+      g_launches++;
+      if ((n1 - n0) & 1) std::swap(lam, lacc);
+    }
+  } else {
   // Segment c is recomputed from its checkpoint (recording every stage input into buffer
   // c % 2) on one stream while the adjoint of segment c + 1 runs on another: the two chains
   // are independent until the adjoint of c needs the recording of c, and the recomputation of
@@ -2200,6 +2277,7 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
   CUDA_TRY(cudaStreamWaitEvent(st, ev[5], 0));
   CUDA_TRY(cudaEventRecord(ev[1], sF));
   CUDA_TRY(cudaStreamWaitEvent(st, ev[1], 0));
+  }
   // leave the state as it was before the call (initial content, tau0)
   s->obs_valid = 0;
   CUDA_TRY(cudaMemcpyAsync(b + L.off_y, w + G.ckpt, arr, cudaMemcpyDeviceToDevice, st));
@@ -2207,7 +2285,10 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
   r = set_tau(s, tau0, st);
   if (r != BQ_OK) return r;
   CUDA_TRY(cudaMemcpyAsync(grad_out, w + G.grad, (size_t)s->grad_size * sizeof(double), cudaMemcpyDeviceToHost, st));
+  unsigned int err_word = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err_word, b + L.off_ctrl + 32, sizeof(err_word), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  if (err_word) return fail(BQ_ETIMEOUT, "a bounded device wait gave up during the gradient (error word %u)", err_word);
   for (int i = 0; i < s->grad_size; ++i)
     if (!std::isfinite(grad_out[i])) return fail(BQ_ENONFINITE, "non-finite gradient");
   return BQ_OK;
@@ -2307,31 +2388,49 @@ static int run_eval(bq_state* s, int g0, int n, int small, double* out_host, cud
   return BQ_OK;
 }
 
+// Enqueues Tr(rho0_b A_b) of every problem into the pool's output slots: from the per-system
+// contributions of the last pipelined stage 4 when they describe the current state, else
+// with the evaluation kernel.
+static int enqueue_trace(bq_state* s, cudaStream_t st) {
+  char* b = s->pool;
+  const Layout& L = s->L;
+  if (s->obs_valid) {
+    CUDA_TRY(bq::launch_obs_sum((const double2*)(b + L.off_obs), (const EvalGroup*)(b + L.off_groups),
+                                s->n_trace_groups, (double2*)(b + L.off_out), st));
+    g_launches++;
+    return BQ_OK;
+  }
+  CUDA_TRY(ensure_comp(s, st));
+  CUDA_TRY(bq::launch_eval((const SysDesc*)(b + L.off_sys), (const EvalGroup*)(b + L.off_groups),
+                           (const EvalEntry*)(b + L.off_entries), b + L.off_y, b + L.off_comp,
+                           (double2*)(b + L.off_out), s->n_trace_groups, s->dtype, s->trace_small, st));
+  g_launches++;
+  return BQ_OK;
+}
+
 extern "C" int bq_evaluate(bq_state* s, double* out_host, void* stream) {
   if (!s || !out_host) return fail(BQ_EINVAL, "NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
-  if (s->obs_valid) {
-    // the last pipelined stage 4 reduced every system's contribution: read them back and
-    // sum the initial conditions of each problem in order
-    std::vector<double> v(2 * (size_t)s->n_sys);
-    CUDA_TRY(cudaMemcpyAsync(v.data(), s->pool + s->L.off_obs, v.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-    unsigned int err_word = 0;
-    CUDA_TRY(cudaMemcpyAsync(&err_word, s->pool + s->L.off_ctrl + 32, sizeof(err_word), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-    if (err_word) return fail(BQ_ETIMEOUT, "a bounded device wait gave up (error word %u)", err_word);
-    for (int g = 0; g < s->n_trace_groups; ++g) {
-      double re = 0.0, im = 0.0;
-      for (int i = 0; i < s->trace_n_sys[g]; ++i) {
-        re += v[2 * (size_t)(s->trace_sys_off[g] + i)];
-        im += v[2 * (size_t)(s->trace_sys_off[g] + i) + 1];
-      }
-      if (!std::isfinite(re) || !std::isfinite(im)) return fail(BQ_ENONFINITE, "non-finite observable of problem %d", g);
-      out_host[2 * g] = re;
-      out_host[2 * g + 1] = im;
-    }
-    return BQ_OK;
-  }
-  return run_eval(s, 0, s->n_trace_groups, s->trace_small, out_host, st);
+  const int n = s->n_trace_groups;
+  int r = enqueue_trace(s, st);
+  if (r != BQ_OK) return r;
+  CUDA_TRY(cudaMemcpyAsync(out_host, s->pool + s->L.off_out, (size_t)n * 16, cudaMemcpyDeviceToHost, st));
+  unsigned int err_word = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err_word, s->pool + s->L.off_ctrl + 32, sizeof(err_word), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (err_word) return fail(BQ_ETIMEOUT, "a bounded device wait gave up during stepping (error word %u)", err_word);
+  for (int i = 0; i < 2 * n; ++i)
+    if (!std::isfinite(out_host[i])) return fail(BQ_ENONFINITE, "non-finite observable of problem %d", i / 2);
+  return BQ_OK;
+}
+
+extern "C" int bq_evaluate_async(bq_state* s, double* out, void* stream) {
+  if (!s || !out) return fail(BQ_EINVAL, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int r = enqueue_trace(s, st);
+  if (r != BQ_OK) return r;
+  CUDA_TRY(cudaMemcpyAsync(out, s->pool + s->L.off_out, (size_t)s->n_trace_groups * 16, cudaMemcpyDefault, st));
+  return BQ_OK;
 }
 
 extern "C" int bq_fock_block(bq_state* s, int lo, double* out_host, void* stream) {

@@ -269,4 +269,25 @@ struct AdjArgs {
   int lanes;             // lanes per point (1, 2 or 4), as in StageArgs
 };
 
+// Cooperative segment kernels of the gradient (k_coop_fwd, k_coop_bwd): all stages of a
+// checkpoint segment in one launch, the dependent phases separated by bounded grid barriers.
+struct CoopArgs {
+  StageArgs st;           // forward template (stage, u_in, u_out, rec set per phase)
+  AdjArgs adj;            // adjoint template (stage, u, b_in, b_out, lam, lacc, tau_step set per phase)
+  void* ua;               // forward ping-pong stage inputs
+  void* ub;
+  char* rec;              // recorded stage inputs of the segment (4 per step), or null
+  size_t arr;             // bytes of one state array
+  void* ba;               // adjoint b ping-pong buffers
+  void* bb;
+  void* lam;              // cotangent after the segment's last step (swapped with lacc per step)
+  void* lacc;
+  double tau0;            // tau at the segment's first step
+  int n_steps;
+  int n_work;             // work items of a stage
+  int n_sys, max_s, src_tiles;  // transposed-source items: n_sys x max_s x 2 src_tiles
+  unsigned int* bar;      // grid barrier words: [0] arrivals, [1] generation
+  unsigned int* error;    // set (bit 2) when a barrier wait gives up
+};
+
 }  // namespace bq

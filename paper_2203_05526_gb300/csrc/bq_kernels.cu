@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "bq_internal.h"
 #include "bq_launch.h"
@@ -100,8 +101,12 @@ __device__ __forceinline__ double2 term_coef(const TermDesc& td, const ChanDesc*
 // ---------------------------------------------------------------------------------------
 // Fused RK4 stage.
 // ---------------------------------------------------------------------------------------
+// One work item of a stage (k_stage: one item per CTA; the cooperative segment kernels: the
+// CTA's items of every stage of a segment).  tau: tau at the start of the step.  fresh: load
+// the item's descriptors (else the shared-memory copies of the CTA's previous call, for the
+// same item, are reused and only the stage coefficients are re-evaluated).
 template <typename T, int NM>
-__global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
+__device__ __forceinline__ void stage_body(const StageArgs& A, int item, double tau, bool fresh) {
   using C = typename C2T<T>::type;
   constexpr int ND = 2 * NM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -115,19 +120,22 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
   __shared__ double s_tau;
 
   const int tid = threadIdx.x;
+  __syncthreads();  // the CTA's previous item is done with the shared copies
   if (tid == 0) {
-    wi = A.work[blockIdx.x];
-    sd = A.sys[wi.sys];
-    s_tau = A.tau_base[0] + (double)(*(volatile long long*)A.counter) * A.dt;
+    if (fresh) {
+      wi = A.work[item];
+      sd = A.sys[wi.sys];
+    }
+    s_tau = tau;
   }
   __syncthreads();
   const int nt = sd.n_terms;
   for (int t = tid; t < nt; t += blockDim.x) {
-    st[t] = A.terms[sd.term_off + t];
+    if (fresh) st[t] = A.terms[sd.term_off + t];
     const double2 c = term_coef(st[t], A.chans, A.chpar, s_tau, A.dt, A.stage, A.horizon, A.reverse);
     sc[t] = cmk<C>(c.x, c.y);
   }
-  if (tid == 32) {  // offsets of the coefficient x weight tables (one table per term)
+  if (fresh && tid == 32) {  // offsets of the coefficient x weight tables (one table per term)
     int o = 0;
     for (int t = 0; t < nt; ++t) {
       const TermDesc& td = A.terms[sd.term_off + t];
@@ -340,10 +348,15 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
     }
   }
 
+}
+
+template <typename T, int NM>
+__global__ void __launch_bounds__(BQ_BLOCK) k_stage(const StageArgs A) {
+  stage_body<T, NM>(A, blockIdx.x, A.tau_base[0] + (double)(*(volatile long long*)A.counter) * A.dt, true);
   // ---- step bookkeeping: the last CTA of stage 4 advances the step counter ----------
-  if (stage == 4) {
+  if (A.stage == 4) {
     __syncthreads();
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
       __threadfence();
       const unsigned int t = atomicAdd(A.ticket, 1u);
       if (t == gridDim.x - 1) {
@@ -1490,8 +1503,10 @@ __device__ __forceinline__ int pwc_segment(const ChanDesc& cd, const double* par
   return (int)x;
 }
 
+// One work item of an adjoint stage (k_adj_stage: one per CTA; the cooperative backward
+// segment kernel: the CTA's items of every stage); fresh as in stage_body.
 template <typename T, int NM>
-__global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
+__device__ __forceinline__ void adj_stage_body(const AdjArgs& A, int item, bool fresh) {
   using C = typename C2T<T>::type;
   constexpr int ND = 2 * NM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1507,18 +1522,19 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
 
   const int tid = threadIdx.x;
   const int stage = A.stage;
-  if (tid == 0) {
-    wi = A.work[blockIdx.x];
+  __syncthreads();  // the CTA's previous item is done with the shared copies
+  if (tid == 0 && fresh) {
+    wi = A.work[item];
     sd = A.sys[wi.sys];
   }
   __syncthreads();
   const int nt = sd.n_terms;
   for (int t = tid; t < nt; t += blockDim.x) {
-    st[t] = A.terms[sd.term_off + t];
+    if (fresh) st[t] = A.terms[sd.term_off + t];
     const double2 c = term_coef(st[t], A.chans, A.chpar, A.tau_step, A.dt, stage, A.horizon, A.reverse);
     sc[t] = cmk<C>(c.x, c.y);
   }
-  if (tid == 0) {
+  if (tid == 0 && fresh) {
     int g = 0, s = 0;
     for (int t = 0; t < nt; ++t) {
       const TermDesc& td = A.terms[sd.term_off + t];
@@ -1794,30 +1810,39 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
   }
 }
 
+template <typename T, int NM>
+__global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
+  adj_stage_body<T, NM>(A, blockIdx.x, true);
+}
+
 // Transposed separable source: for every system and sandwich term t
 //   v_t[kx] = sum_ly b_R[kx, ly] Wy_t(ly) G_y[ly + sy],   w_t[ly] = sum_kx b_R[kx, ly] Wx_t(kx) G_x[kx + sx]
 // (G_x, G_y of the recorded stage input; b_R = dt/6 lam at stage 4).  grid = (systems, max S terms, 2).
 #define BQ_SRC_THREADS 256
 #define BQ_SRC_TILE 8      // outputs per CTA (one row per warp; BQ_SRC_THREADS / 8 partial sums per column)
 #define BQ_SRC_ZCH 1024    // summed-index chunk held in shared memory
-template <typename T, int NM>
-__global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
+// One CTA's part of the transposed source, (bx, by, bz) = (system, sandwich term, direction
+// and output tile), with NTH threads (k_adj_src: BQ_SRC_THREADS; the cooperative backward
+// segment kernel: BQ_BLOCK).
+template <typename T, int NM, int NTH>
+__device__ __forceinline__ void adj_src_body(const AdjArgs& A, int bx, int by, int bz) {
   using C = typename C2T<T>::type;
   __shared__ C z[BQ_SRC_ZCH];
-  __shared__ C red[BQ_SRC_THREADS / BQ_SRC_TILE][BQ_SRC_TILE];
-  const SysDesc& sd = A.sys[blockIdx.x];
+  __shared__ C red[NTH / BQ_SRC_TILE][BQ_SRC_TILE];
+  __syncthreads();  // the CTA's previous item is done with z and red
+  const SysDesc& sd = A.sys[bx];
   if (!sd.has_sep || !sd.has_r) return;
-  // the blockIdx.y-th sandwich term of the system
+  // the by-th sandwich term of the system
   int t = -1, s = 0;
   for (int q = 0; q < sd.n_terms; ++q)
     if (A.terms[sd.term_off + q].side == SIDE_S) {
-      if (s == (int)blockIdx.y) { t = q; break; }
+      if (s == by) { t = q; break; }
       ++s;
     }
   if (t < 0) return;
   const TermDesc td = A.terms[sd.term_off + t];
-  const int dirx = (blockIdx.z & 1) == 0;  // 1: v_t over kx (sum over ly), 0: w_t over ly (sum over kx)
-  const int i0 = (int)(blockIdx.z >> 1) * BQ_SRC_TILE;
+  const int dirx = (bz & 1) == 0;  // 1: v_t over kx (sum over ly), 0: w_t over ly (sum over kx)
+  const int i0 = (bz >> 1) * BQ_SRC_TILE;
   const int ng = sd.n_g;
   if (i0 >= ng) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1847,7 +1872,7 @@ __global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
         w *= W[td.wtab[a] + id[isx ? d : d - NM]];
       }
       const C zi = w == (T)0 ? cmk<C>(0.0, 0.0) : cscale(other[i + delta], w);
-      C* outd = reinterpret_cast<C*>(const_cast<void*>(A.srcred)) + (int64_t)blockIdx.x * A.srcred_stride +
+      C* outd = reinterpret_cast<C*>(const_cast<void*>(A.srcred)) + (int64_t)bx * A.srcred_stride +
                 (s * 2 + (dirx ? 0 : 1)) * ng;
       outd[i] = cscale(cmul(bsrc[i], zi), bscale);
     }
@@ -1856,14 +1881,14 @@ __global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
   // out[i] = bscale sum_j B(i, j) z[j], z[j] = w(j) other[j + delta], with B(i, j) the R
   // cotangent at (i, j) (dirx) or (j, i), and w(j) the product of the term's weights on the
   // summed side.  Chunks of z go through shared memory; the sums run in a fixed order.
-  C acc[BQ_SRC_TILE / (BQ_SRC_THREADS / 32)];
+  C acc[BQ_SRC_TILE / (NTH / 32)];
 #pragma unroll
-  for (int r = 0; r < BQ_SRC_TILE / (BQ_SRC_THREADS / 32); ++r) acc[r] = cmk<C>(0.0, 0.0);
+  for (int r = 0; r < BQ_SRC_TILE / (NTH / 32); ++r) acc[r] = cmk<C>(0.0, 0.0);
   C accc = cmk<C>(0.0, 0.0);
   for (int jc = 0; jc < ng; jc += BQ_SRC_ZCH) {
     const int nj = min(BQ_SRC_ZCH, ng - jc);
     __syncthreads();  // the previous chunk is consumed
-    for (int jj = tid; jj < nj; jj += BQ_SRC_THREADS) {
+    for (int jj = tid; jj < nj; jj += NTH) {
       const int j = jc + jj;
       int rem = j;
       int id[NM];
@@ -1882,8 +1907,8 @@ __global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
     if (dirx) {
       // rows i0 + warp * R + r: lanes stride over j (coalesced along the row)
 #pragma unroll
-      for (int r = 0; r < BQ_SRC_TILE / (BQ_SRC_THREADS / 32); ++r) {
-        const int i = i0 + warp * (BQ_SRC_TILE / (BQ_SRC_THREADS / 32)) + r;
+      for (int r = 0; r < BQ_SRC_TILE / (NTH / 32); ++r) {
+        const int i = i0 + warp * (BQ_SRC_TILE / (NTH / 32)) + r;
         if (i < ng) {
           const C* row = bsrc + (int64_t)i * ng + jc;
           const int mi = midx(i);
@@ -1892,27 +1917,27 @@ __global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
         }
       }
     } else {
-      // column i0 + tid % TILE: the CTA's BQ_SRC_THREADS / TILE thread groups split j (each
+      // column i0 + tid % TILE: the CTA's NTH / TILE thread groups split j (each
       // group reads TILE adjacent columns of one row)
       const int i = i0 + tid % BQ_SRC_TILE;
       const int mi = midx(i);
       if (i < ng)
-        for (int jj = tid / BQ_SRC_TILE; jj < nj; jj += BQ_SRC_THREADS / BQ_SRC_TILE)
+        for (int jj = tid / BQ_SRC_TILE; jj < nj; jj += NTH / BQ_SRC_TILE)
           if (dm < 0 || midx(jc + jj) == mi) accc = cfma(bsrc[(int64_t)(jc + jj) * ng + i], z[jj], accc);
     }
   }
-  C* out = reinterpret_cast<C*>(const_cast<void*>(A.srcred)) + (int64_t)blockIdx.x * A.srcred_stride +
+  C* out = reinterpret_cast<C*>(const_cast<void*>(A.srcred)) + (int64_t)bx * A.srcred_stride +
            (s * 2 + (dirx ? 0 : 1)) * ng;
   if (dirx) {
 #pragma unroll
-    for (int r = 0; r < BQ_SRC_TILE / (BQ_SRC_THREADS / 32); ++r) {
+    for (int r = 0; r < BQ_SRC_TILE / (NTH / 32); ++r) {
       C v = acc[r];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         v.x += __shfl_down_sync(0xffffffffu, v.x, o);
         v.y += __shfl_down_sync(0xffffffffu, v.y, o);
       }
-      const int i = i0 + warp * (BQ_SRC_TILE / (BQ_SRC_THREADS / 32)) + r;
+      const int i = i0 + warp * (BQ_SRC_TILE / (NTH / 32)) + r;
       if (lane == 0 && i < ng) out[i] = cscale(v, bscale);
     }
   } else {
@@ -1920,10 +1945,128 @@ __global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
     __syncthreads();
     if (tid < BQ_SRC_TILE) {
       C v = red[0][tid];
-      for (int w2 = 1; w2 < BQ_SRC_THREADS / BQ_SRC_TILE; ++w2) v = cadd(v, red[w2][tid]);
+      for (int w2 = 1; w2 < NTH / BQ_SRC_TILE; ++w2) v = cadd(v, red[w2][tid]);
       const int i = i0 + tid;
       if (i < ng) out[i] = cscale(v, bscale);
     }
+  }
+}
+
+template <typename T, int NM>
+__global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
+  adj_src_body<T, NM, BQ_SRC_THREADS>(A, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// ---------------------------------------------------------------------------------------
+// Cooperative segment kernels of the gradient.  A checkpoint segment of a small state is a
+// long chain of short dependent stages; one launch per stage leaves the GPU mostly idle
+// between them.  Here one cooperative launch (every CTA resident, so the CTAs can wait for
+// one another) runs all stages of a segment: each CTA takes the work items blockIdx.x,
+// blockIdx.x + gridDim.x, ... of a phase, and a grid barrier separates dependent phases.
+// With at most one item per CTA the item's descriptors stay in shared memory for the whole
+// segment.
+// ---------------------------------------------------------------------------------------
+#define BQ_GRID_WAIT_CYCLES (4000000000LL)  // about 2 s at the maximum SM clock
+
+// Grid-wide barrier of a cooperative launch: thread 0 of each CTA arrives (release) and waits
+// (acquire) for the generation to change; the last arrival resets the count and starts the
+// next generation.  The wait is bounded: on timeout the CTA sets bit 2 of *error and the
+// caller returns (the other CTAs then time out at the same barrier or the next).
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int* error) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int gen;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
+    int ok = 1;
+    if (old == gridDim.x - 1) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
+    } else {
+      const long long t0 = clock64();
+      for (;;) {
+        unsigned int g;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+        if (g != gen) break;
+        if (clock64() - t0 > BQ_GRID_WAIT_CYCLES) {
+          ok = 0;
+          atomicOr(error, 4u);
+          break;
+        }
+        __nanosleep(40);
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Forward stages of n_steps steps from y (and comp), the stage inputs alternating between ua
+// and ub as in the per-stage launches; with rec, every stage input is also recorded at
+// rec + (4 i + stage - 1) arr.
+template <typename T, int NM>
+__global__ void __launch_bounds__(BQ_BLOCK) k_coop_fwd(const CoopArgs P) {
+  const bool reload = P.n_work > (int)gridDim.x;
+  bool first = true;
+  for (int i = 0; i < P.n_steps; ++i) {
+    const double tau = P.tau0 + (double)i * P.st.dt;
+    for (int stage = 1; stage <= 4; ++stage) {
+      StageArgs a = P.st;
+      a.stage = stage;
+      a.u_in = stage == 1 ? a.y : (stage == 2 ? P.ua : (stage == 3 ? P.ub : P.ua));
+      a.u_out = stage == 1 ? P.ua : (stage == 2 ? P.ub : (stage == 3 ? P.ua : nullptr));
+      a.rec = P.rec ? P.rec + ((size_t)i * 4 + stage - 1) * P.arr : nullptr;
+      for (int it = blockIdx.x; it < P.n_work; it += gridDim.x) {
+        stage_body<T, NM>(a, it, tau, reload || first);
+        first = false;
+      }
+      if (!grid_barrier(P.bar, P.error)) return;
+    }
+  }
+}
+
+// Adjoint of the segment's steps, last step first, from the recorded stage inputs: per stage
+// the transposed-source reductions (if the systems have sandwich terms), a barrier, the
+// transposed stage with the parameter gradients, a barrier.  lam and lacc swap after every
+// step, as in the per-stage launches; the cotangent before the segment ends in lam if
+// n_steps is even, else in lacc.
+template <typename T, int NM>
+__global__ void __launch_bounds__(BQ_BLOCK) k_coop_bwd(const CoopArgs P) {
+  const bool reload = P.n_work > (int)gridDim.x;
+  bool first = true;
+  void* lam = P.lam;
+  void* lacc = P.lacc;
+  const int src_per_sys = P.max_s * 2 * P.src_tiles;
+  const int n_src = P.max_s > 0 ? P.n_sys * src_per_sys : 0;
+  for (int n = P.n_steps - 1; n >= 0; --n) {
+    for (int stage = 4; stage >= 1; --stage) {
+      AdjArgs a = P.adj;
+      a.stage = stage;
+      a.tau_step = P.tau0 + (double)n * a.dt;
+      a.lam = lam;
+      a.lacc = lacc;
+      a.u = P.rec + ((size_t)n * 4 + stage - 1) * P.arr;
+      a.b_in = stage == 4 ? nullptr : (stage == 3 ? P.ba : (stage == 2 ? P.bb : P.ba));
+      a.b_out = stage == 4 ? P.ba : (stage == 3 ? P.bb : (stage == 2 ? P.ba : nullptr));
+      if (n_src > 0) {
+        for (int it = blockIdx.x; it < n_src; it += gridDim.x) {
+          const int bx = it / src_per_sys, rem = it - bx * src_per_sys;
+          adj_src_body<T, NM, BQ_BLOCK>(a, bx, rem / (2 * P.src_tiles), rem % (2 * P.src_tiles));
+        }
+        if (!grid_barrier(P.bar, P.error)) return;
+      }
+      for (int it = blockIdx.x; it < P.n_work; it += gridDim.x) {
+        adj_stage_body<T, NM>(a, it, reload || first);
+        first = false;
+      }
+      if (!grid_barrier(P.bar, P.error)) return;
+    }
+    void* t = lam;
+    lam = lacc;
+    lacc = t;
   }
 }
 
@@ -2528,6 +2671,78 @@ cudaError_t launch_adjoint(const AdjArgs& a, int dtype, int nm, int n_work, int 
   return cudaErrorInvalidValue;
 }
 
+// Cooperative segment kernels: the kernel for (dtype, modes, direction), its dynamic shared
+// memory limit set once (static + dynamic within the per-block maximum).
+template <typename T, int NM>
+static const void* coop_kernel(bool bwd) {
+  return bwd ? (const void*)k_coop_bwd<T, NM> : (const void*)k_coop_fwd<T, NM>;
+}
+
+static const void* coop_func(int dtype, int nm, bool bwd) {
+  if (dtype == 0) {
+    switch (nm) {
+      case 1: return coop_kernel<double, 1>(bwd);
+      case 2: return coop_kernel<double, 2>(bwd);
+      case 3: return coop_kernel<double, 3>(bwd);
+      case 4: return coop_kernel<double, 4>(bwd);
+    }
+  } else {
+    switch (nm) {
+      case 1: return coop_kernel<float, 1>(bwd);
+      case 2: return coop_kernel<float, 2>(bwd);
+      case 3: return coop_kernel<float, 3>(bwd);
+      case 4: return coop_kernel<float, 4>(bwd);
+    }
+  }
+  return nullptr;
+}
+
+static cudaError_t coop_prepare(const void* f, int smem_bytes) {
+  static std::mutex mu;
+  static std::vector<const void*> done;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const void* d : done)
+    if (d == f) return cudaSuccess;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, f);
+  if (e != cudaSuccess) return e;
+  int dev = 0, optin = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  const int lim = std::min<int>(BQ_MAX_DYN_SMEM, optin - (int)fa.sharedSizeBytes);
+  if (smem_bytes > lim) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e != cudaSuccess) return e;
+  done.push_back(f);
+  return cudaSuccess;
+}
+
+cudaError_t coop_max_grid(int dtype, int nm, bool bwd, int smem_bytes, int* out) {
+  const void* f = coop_func(dtype, nm, bwd);
+  if (!f) return cudaErrorInvalidValue;
+  cudaError_t e = coop_prepare(f, smem_bytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, BQ_BLOCK, smem_bytes);
+  if (e != cudaSuccess) return e;
+  *out = coop ? per_sm * sms : 0;
+  return cudaSuccess;
+}
+
+cudaError_t launch_coop(int dtype, int nm, bool bwd, CoopArgs P, int smem_bytes, int grid, cudaStream_t s) {
+  const void* f = coop_func(dtype, nm, bwd);
+  if (!f || grid < 1) return cudaErrorInvalidValue;
+  cudaError_t e = coop_prepare(f, smem_bytes);
+  if (e != cudaSuccess) return e;
+  P.src_tiles = (P.adj.ng_max + BQ_SRC_TILE - 1) / BQ_SRC_TILE;
+  void* args[] = {(void*)&P};
+  return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(BQ_BLOCK), args, (size_t)smem_bytes, s);
+}
+
 cudaError_t launch_adj_seed(const SysDesc* sys, const EvalGroup* groups, const EvalEntry* entries, const void* y,
                             void* lam, int n_groups, int dtype, cudaStream_t s) {
   if (n_groups <= 0) return cudaSuccess;
@@ -2656,6 +2871,30 @@ cudaError_t launch_eval(const SysDesc* sys, const EvalGroup* groups, const EvalE
     k_eval<double><<<blocks, threads, 0, s>>>(sys, groups, entries, y, comp, out, n_groups);
   else
     k_eval<float><<<blocks, threads, 0, s>>>(sys, groups, entries, y, comp, out, n_groups);
+  return cudaGetLastError();
+}
+
+// Tr(rho0_b A_b) of every problem from the per-system contributions the last pipelined stage
+// left (Eq. 11: the sum over the problem's initial conditions), one thread per problem,
+// summed in system order.
+__global__ void k_obs_sum(const double2* __restrict__ obs, const EvalGroup* __restrict__ groups, int n_groups,
+                          double2* __restrict__ out) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_groups) return;
+  const EvalGroup gr = groups[g];
+  double re = 0.0, im = 0.0;
+  for (int i = 0; i < gr.n_sys; ++i) {
+    const double2 v = obs[gr.sys_off + i];
+    re += v.x;
+    im += v.y;
+  }
+  out[g] = make_double2(re, im);
+}
+
+cudaError_t launch_obs_sum(const double2* obs, const EvalGroup* groups, int n_groups, double2* out, cudaStream_t s) {
+  if (n_groups <= 0) return cudaSuccess;
+  const int threads = 256;
+  k_obs_sum<<<(n_groups + threads - 1) / threads, threads, 0, s>>>(obs, groups, n_groups, out);
   return cudaGetLastError();
 }
 

@@ -42,6 +42,13 @@ cudaError_t launch_solve_mg(const SolveArgs& a, int dtype, int smem_bytes, int c
 cudaError_t solve_blocks_per_sm(int dtype, int merged, int smem_bytes, int* out);
 cudaError_t launch_eval(const SysDesc* sys, const EvalGroup* groups, const EvalEntry* entries, const void* y,
                         const void* comp, double2* out, int n_groups, int dtype, int small, cudaStream_t s);
+// Cooperative segment kernels of the gradient (forward with or without recording, adjoint):
+// the largest grid whose CTAs are all resident (0 if the device has no cooperative launch),
+// and the launch itself (grid CTAs of BQ_BLOCK threads, at most that largest grid).
+cudaError_t coop_max_grid(int dtype, int nm, bool bwd, int smem_bytes, int* out);
+cudaError_t launch_coop(int dtype, int nm, bool bwd, CoopArgs P, int smem_bytes, int grid, cudaStream_t s);
+// Per-problem sums of the per-system Tr(rho0 A) contributions of the pipelined stage 4.
+cudaError_t launch_obs_sum(const double2* obs, const EvalGroup* groups, int n_groups, double2* out, cudaStream_t s);
 // Device address of the fixed RK4 scratch on the current device (looked up once per device).
 cudaError_t fixed_scratch(void** ptr);
 cudaError_t launch_scatter(const InitEntry* ent, int n, void* y, int dtype, cudaStream_t s);

@@ -82,6 +82,39 @@ def test_batched_gradients_equal_single_problem_gradients():
     assert np.max(np.abs(g[:n_per] - ref)) <= 1e-10 * np.max(np.abs(ref))
 
 
+def _coop_vs_per_stage(p, ck, n_steps=None, **tune):
+    n_steps = p.n_steps if n_steps is None else n_steps
+    out = []
+    for coop in (0, 1):
+        st = gpu_state(p)
+        st.set_tune(grad_coop=coop, **tune)
+        assert st.get_tune()["grad_coop"] == coop
+        out.append(st.grad(p.dt, n_steps, ck) + (st,))
+    (l0, g0, _), (l1, g1, st) = out
+    assert abs(l1[0] - l0[0]) <= 1e-14 * max(1.0, abs(l0[0]))
+    assert np.max(np.abs(g1 - g0)) <= 1e-12 * np.max(np.abs(g0))
+    assert abs(st.time()) == 0.0
+    return l1, g1
+
+
+@pytest.mark.parametrize("ck", [5, 7, 24])
+def test_grad_cooperative_segments_match_per_stage_launches_and_oracle(ck):
+    """The cooperative segment kernels (one launch per checkpoint segment and direction, grid
+    barriers between the stages) against one launch per stage (equal up to the order of the
+    gradient atomics) and against the oracle's adjoint, for even and odd segment lengths."""
+    p = _small_control(n_modes=2, N=4, n_seg=4, steps_per_seg=6)
+    _, g = _coop_vs_per_stage(p, ck)
+    loss_o, gt, gp = ograd.loss_and_grad(p, checkpoint_every=ck)
+    ref = _flat_oracle(gt, gp)
+    assert np.max(np.abs(g - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+def test_grad_cooperative_segments_with_more_items_than_ctas():
+    """The full-size two-mode control state with 32-point tiles: more work items per stage
+    than resident CTAs, so each CTA takes several items per stage (40 steps, segments of 7)."""
+    _coop_vs_per_stage(configs.two_mode_control(), 7, n_steps=40, tile=32)
+
+
 @pytest.mark.parametrize("n_modes,N,ck", [(1, 5, 7), (2, 3, 5)])
 def test_grad_with_secular_dissipator_matches_oracle_adjoint(n_modes, N, ck):
     """The secular dissipator at finite temperature in place of the jump operators: the
