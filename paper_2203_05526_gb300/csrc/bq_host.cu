@@ -1238,9 +1238,19 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
           r.w_im = sd.w_im;
           r.w32_re = (float)sd.w_re;
           r.w32_im = (float)sd.w_im;
+          r.sys = i;
           P.precs.push_back(r);
           blk_max = std::max(blk_max, (size_t)r.blk_elems);
         }
+        // Within each run of kPipeSortRun consecutive systems, largest first: CTA b takes
+        // records b, b + G, b + 2G, ..., so every CTA gets one system of each size band of a
+        // run and the CTAs finish together (in problem order a CTA's load is a sum of a few
+        // random sizes, and the slowest CTA sets the stage's time).  Sorting only within runs
+        // keeps the systems in flight at any moment in one region of the state arrays.
+        const size_t kPipeSortRun = 4096;
+        for (size_t r0 = 0; r0 < P.precs.size(); r0 += kPipeSortRun)
+          std::stable_sort(P.precs.begin() + r0, P.precs.begin() + std::min(P.precs.size(), r0 + kPipeSortRun),
+                           [](const bq::PipeRec& a, const bq::PipeRec& b) { return a.blk_elems > b.blk_elems; });
         // Shared-memory slot: [parameter block | guard | stage input | guard].  Neighbour reads
         // at a system's edges reach at most M + 1 elements before or after its block (the
         // sandwich source (k - 1, l - 1) at k = 0 of a block without G), so each guard holds

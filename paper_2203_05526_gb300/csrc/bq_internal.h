@@ -157,7 +157,7 @@ struct __align__(16) PipeRec {
   int nb, rb;       // merged path: nb column strips of rb rows (thread t: column t % M, strip t / M)
   float inv_m;      // 1 / M (strip index without an integer division)
   float w32_re, w32_im;  // the weight below rounded to FP32 (the FP32 kernels' observable)
-  int pad;
+  int sys;          // index of the system (records are ordered by size, largest first)
   double c_re, c_im;  // separation constant C of the system (Eq. 304)
   double w_re, w_im;  // weight of the system's initial condition
 };

@@ -933,7 +933,7 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
         c.y += __shfl_down_sync(0xffffffffu, c.y, o);
       }
     }
-    if (lane == 0) A.obs[blockIdx.x + (size_t)j * G] = make_double2((double)c.x, (double)c.y);
+    if (lane == 0) A.obs[recs[(j / BQ_PIPE_RB) & 1][j % BQ_PIPE_RB].sys] = make_double2((double)c.x, (double)c.y);
   };
   auto obs_end = [&](int j) {
     if (!obs_on) return;
