@@ -469,7 +469,18 @@ def grads_leg(n_steps=None, sched=None):
                        "checkpoint every 160, complex FP64",
            "seconds_per_gradient": el, "grads_per_s": 1.0 / el, "loss": float(loss[0]),
            "grad_norm": float(np.linalg.norm(g)), "n_params": int(g.size), "tile": tune["tile"],
-           "lanes": tune["lanes"], "gread": tune["gread"], "tuned_on": "gradient" if sched is None else "fixed"}
+           "lanes": tune["lanes"], "gread": tune["gread"], "grad_coop": tune["grad_coop"],
+           "tuned_on": "gradient" if sched is None else "fixed"}
+    # the same gradient with a workspace that holds every segment's recording (GB300's HBM:
+    # 4 x 20 480 states of 0.34 MB = 27.5 GB), so that no segment is recomputed
+    per, nseg = bq.grad_record_bytes(st, steps, 160)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss_r, g_r = st.grad(p.dt, steps, 160, record_segments=-1)
+    el_r = time.perf_counter() - t0
+    out["all_segments_recorded"] = {
+        "seconds_per_gradient": el_r, "grads_per_s": 1.0 / el_r, "recording_bytes": per * nseg,
+        "max_rel_diff": float(np.max(np.abs(g_r - g)) / np.max(np.abs(g)))}
     if n_steps is None:
         out["batched"] = grads_batched_leg()
     return out

@@ -269,14 +269,26 @@ int bq_grad_size(const bq_state* s, int* n);
  * inputs (two segments), plus four cotangent arrays. */
 int bq_grad_required_bytes(const bq_state* s, int64_t n_steps, int checkpoint_every, size_t* out);
 
+/* Bytes of one segment's recorded stage inputs (4 checkpoint_every states) and the number of
+ * segments.  A workspace larger than bq_grad_required_bytes holds
+ * 2 + (work_bytes - required) / per_segment recordings: on the cooperative path (bq_tune
+ * grad_coop) bq_grad records that many segments, the last ones, in its forward pass and does
+ * not recompute them; with n_segments - 2 extra recordings nothing is recomputed. */
+int bq_grad_record_bytes(const bq_state* s, int64_t n_steps, int checkpoint_every, size_t* per_segment,
+                         int64_t* n_segments);
+
 /* Loss l_b = Re Tr(rho0_b A_b(tau0 + n_steps dt)) of every problem (loss_out[B]) and the
  * gradient of sum_b l_b (grad_out[bq_grad_size]) with respect to every H parameter and every
  * piecewise-constant segment value, by the exact discrete adjoint of the RK4 solve: a forward
  * pass storing the state every checkpoint_every steps, then, segment by segment in reverse, a
- * recomputation recording the RK4 stage inputs and four adjoint stage kernels per step
- * (transposed stencils, transposed separable source, per-term gradient reductions); the
- * recomputation of a segment runs on an internal stream concurrently with the adjoint of the
- * following segment on another, both ordered after the work already on `stream`.  The
+ * recomputation recording the RK4 stage inputs and four adjoint stages per step (transposed
+ * stencils, transposed separable source, per-term gradient reductions).  With grad_coop
+ * (bq_tune; the default where the device allows cooperative launches) each segment's forward
+ * and adjoint stages run in one cooperative launch each on `stream`, and segments recorded in
+ * the forward pass (see bq_grad_record_bytes) are not recomputed; otherwise one launch per
+ * stage, the recomputation of a segment on an internal stream concurrent with the adjoint of
+ * the following segment on another, both ordered after the work already on `stream`.  A grid
+ * barrier that waits longer than about 2 s sets the error word: BQ_ETIMEOUT.  The
  * separation constant's dependence on the parameters (Eq. 304) is included.  The state is left
  * as it was (content and tau).  work: caller-owned device buffer, 256-byte aligned.
  * Synchronises stream. */

@@ -106,6 +106,7 @@ def lib() -> C.CDLL:
         "bq_time": (C.c_int, [vp, dp]),
         "bq_evaluate": (C.c_int, [vp, dp, vp]),
         "bq_evaluate_async": (C.c_int, [vp, vp, vp]),
+        "bq_grad_record_bytes": (C.c_int, [vp, C.c_int64, C.c_int, C.POINTER(C.c_size_t), C.POINTER(C.c_int64)]),
         "bq_fock_block": (C.c_int, [vp, C.c_int, dp, vp]),
         "bq_state_info": (C.c_int, [vp, ip, C.POINTER(C.c_int64)]),
         "bq_system_info": (C.c_int, [vp, C.c_int, ip, ip, ip, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -134,7 +135,7 @@ def exported_symbols() -> List[str]:
     return [n for n in ("bq_problem_create", "bq_problem_destroy", "bq_problem_add_channel",
                         "bq_problem_add_h_term", "bq_problem_set_params", "bq_problem_add_jump",
                         "bq_problem_set_measured", "bq_problem_set_rho0", "bq_required_bytes", "bq_map",
-                        "bq_step", "bq_step_fixed_scratch", "bq_solve", "bq_solve_eligible", "bq_stage_variant", "bq_grad_size", "bq_grad_required_bytes", "bq_grad", "bq_time", "bq_evaluate", "bq_evaluate_async", "bq_fock_block", "bq_state_info",
+                        "bq_step", "bq_step_fixed_scratch", "bq_solve", "bq_solve_eligible", "bq_stage_variant", "bq_grad_size", "bq_grad_required_bytes", "bq_grad_record_bytes", "bq_grad", "bq_time", "bq_evaluate", "bq_evaluate_async", "bq_fock_block", "bq_state_info",
                         "bq_system_info", "bq_read_system", "bq_state_bytes", "bq_store_state",
                         "bq_load_state", "bq_set_time", "bq_state_destroy", "bq_status_string",
                         "bq_last_error", "bq_launch_count", "bq_fma_peak")]
@@ -247,6 +248,13 @@ def _stream_ptr(stream=None):
     return C.c_void_p(s.cuda_stream)
 
 
+def grad_record_bytes(state: "State", n_steps: int, checkpoint_every: int):
+    """(bytes of one segment's recording, number of segments) of bq_grad (bq_grad_record_bytes)."""
+    per, nseg = C.c_size_t(), C.c_int64()
+    check(lib().bq_grad_record_bytes(state.ptr, int(n_steps), int(checkpoint_every), C.byref(per), C.byref(nseg)))
+    return per.value, nseg.value
+
+
 def plan(handles: Sequence["ProblemHandle"], opts: "bq_map_opts") -> dict:
     """Host-only view of the plan bq_map would build for these problems (bq_plan): no device
     is needed."""
@@ -288,18 +296,24 @@ class State:
         """Batched persistent solve: all n_steps of every system in one kernel launch."""
         check(lib().bq_solve(self.ptr, float(dt), int(n_steps), _stream_ptr(stream)))
 
-    def grad(self, dt: float, n_steps: int, checkpoint_every: int = 160, stream=None):
-        """(losses[B], gradient) of Re Tr(rho0 A(T)) by the discrete adjoint (bq_grad)."""
+    def grad(self, dt: float, n_steps: int, checkpoint_every: int = 160, stream=None, record_segments: int = 2):
+        """(losses[B], gradient) of Re Tr(rho0 A(T)) by the discrete adjoint (bq_grad).
+        record_segments: recordings the workspace holds (2 = the minimum; on the cooperative
+        path every recording beyond those the backward sweep needs spares one segment's
+        recomputation; -1 = all segments)."""
         import torch
         n = C.c_int()
         check(lib().bq_grad_size(self.ptr, C.byref(n)))
         nb = C.c_size_t()
         check(lib().bq_grad_required_bytes(self.ptr, int(n_steps), int(checkpoint_every), C.byref(nb)))
-        work = torch.empty(nb.value, dtype=torch.uint8, device=self.pool.device)
+        per, nseg = C.c_size_t(), C.c_int64()
+        check(lib().bq_grad_record_bytes(self.ptr, int(n_steps), int(checkpoint_every), C.byref(per), C.byref(nseg)))
+        extra = (nseg.value if record_segments < 0 else record_segments) - 2
+        work = torch.empty(nb.value + max(0, extra) * per.value, dtype=torch.uint8, device=self.pool.device)
         loss = (C.c_double * self.B)()
         g = (C.c_double * max(1, n.value))()
         check(lib().bq_grad(self.ptr, float(dt), int(n_steps), int(checkpoint_every), C.c_void_p(work.data_ptr()),
-                            nb.value, loss, g, _stream_ptr(stream)))
+                            work.numel(), loss, g, _stream_ptr(stream)))
         return np.array(loss[:]), np.array(g[:n.value])
 
     def stage_variant(self) -> str:

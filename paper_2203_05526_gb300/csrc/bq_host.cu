@@ -2046,6 +2046,7 @@ static int run_eval(bq_state* s, int g0, int n, int small, double* out_host, cud
 // ---------------------------------------------------------------------------------------
 struct GradLayout {
   size_t ckpt, rec, lam, lacc, ba, bb, srcred, grad, total;
+  size_t rec_seg;  // bytes of one segment's recorded stage inputs (4 k states)
   int64_t n_ckpt;
 };
 
@@ -2056,14 +2057,18 @@ static GradLayout grad_layout(const bq_state* s, int64_t n_steps, int k) {
   size_t o = 0;
   auto seg = [&](size_t bytes) { size_t r = o; o = align_up(o + std::max<size_t>(bytes, 1)); return r; };
   g.n_ckpt = (n_steps + k - 1) / k;
+  g.rec_seg = 4 * arr * (size_t)k;
   g.ckpt = seg(2 * arr * (size_t)g.n_ckpt);
-  g.rec = seg(2 * 4 * arr * (size_t)k);  // two segments' stage inputs (recompute overlaps the backward sweep)
   g.lam = seg(arr);
   g.lacc = seg(arr);
   g.ba = seg(arr);
   g.bb = seg(arr);
   g.srcred = seg((size_t)s->n_sys * std::max(1, s->srcred_stride) * cs);
   g.grad = seg((size_t)std::max(1, s->grad_size) * sizeof(double));
+  // two segments' stage inputs (recompute overlaps the backward sweep), last: a larger
+  // workspace holds further recordings (bq_grad records that many segments in its forward
+  // pass and does not recompute them)
+  g.rec = seg(2 * g.rec_seg);
   g.total = o;
   return g;
 }
@@ -2077,6 +2082,15 @@ extern "C" int bq_grad_size(const bq_state* s, int* n) {
 extern "C" int bq_grad_required_bytes(const bq_state* s, int64_t n_steps, int checkpoint_every, size_t* out) {
   if (!s || !out || n_steps < 1 || checkpoint_every < 1) return fail(BQ_EINVAL, "bad argument");
   *out = grad_layout(s, n_steps, checkpoint_every).total;
+  return BQ_OK;
+}
+
+extern "C" int bq_grad_record_bytes(const bq_state* s, int64_t n_steps, int checkpoint_every, size_t* per_segment,
+                                    int64_t* n_segments) {
+  if (!s || !per_segment || !n_segments || n_steps < 1 || checkpoint_every < 1) return fail(BQ_EINVAL, "bad argument");
+  const GradLayout G = grad_layout(s, n_steps, checkpoint_every);
+  *per_segment = G.rec_seg;
+  *n_segments = G.n_ckpt;
   return BQ_OK;
 }
 
@@ -2129,6 +2143,13 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
     grid_b = std::min(grid_b, std::max(s->n_work, src_items));
   }
   const bool coop = grid_f > 0 && grid_b > 0;
+  // Recording buffers: the two of the layout plus as many more as the workspace holds.  On
+  // the cooperative path the forward pass records the last n_rec segments, which the
+  // backward sweep then does not recompute; segment c uses buffer c % n_rec.
+  int64_t n_rec = 2 + (int64_t)((work_bytes - G.total) / G.rec_seg);
+  n_rec = std::max<int64_t>(1, std::min<int64_t>(n_rec, G.n_ckpt));
+  auto rec_buf = [&](int64_t c) { return w + G.rec + (size_t)(c % n_rec) * G.rec_seg; };
+  auto recorded = [&](int64_t c) { return coop && c >= G.n_ckpt - n_rec; };
   bq::CoopArgs P;
   std::memset(&P, 0, sizeof(P));
   if (coop) {
@@ -2159,7 +2180,7 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
     CUDA_TRY(cudaMemcpyAsync(w + G.ckpt + (2 * c) * arr, b + L.off_y, arr, cudaMemcpyDeviceToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(w + G.ckpt + (2 * c + 1) * arr, b + L.off_comp, arr, cudaMemcpyDeviceToDevice, st));
     if (coop) {
-      CUDA_TRY(coop_fwd(tau0 + (double)n0 * dt, n1 - n0, nullptr, st));
+      CUDA_TRY(coop_fwd(tau0 + (double)n0 * dt, n1 - n0, recorded(c) ? rec_buf(c) : nullptr, st));
       continue;
     }
     int r = set_tau(s, tau0 + (double)n0 * dt, st);
@@ -2202,12 +2223,17 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
     P.bb = w + G.bb;
     char* lam = w + G.lam;
     char* lacc = w + G.lacc;
-    char* rec = w + G.rec;
     for (int64_t c = G.n_ckpt - 1; c >= 0; --c) {
       const int64_t n0 = c * k, n1 = std::min<int64_t>(n_steps, n0 + k);
-      CUDA_TRY(cudaMemcpyAsync(b + L.off_y, w + G.ckpt + (2 * c) * arr, arr, cudaMemcpyDeviceToDevice, st));
-      CUDA_TRY(cudaMemcpyAsync(b + L.off_comp, w + G.ckpt + (2 * c + 1) * arr, arr, cudaMemcpyDeviceToDevice, st));
-      CUDA_TRY(coop_fwd(tau0 + (double)n0 * dt, n1 - n0, rec, st));
+      char* rec = rec_buf(c);
+      if (!recorded(c)) {
+        CUDA_TRY(cudaMemcpyAsync(b + L.off_y, w + G.ckpt + (2 * c) * arr, arr, cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(b + L.off_comp, w + G.ckpt + (2 * c + 1) * arr, arr, cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(coop_fwd(tau0 + (double)n0 * dt, n1 - n0, rec, st));
+      }
+      P.tau0 = tau0 + (double)n0 * dt;  // (the recomputation, when it runs, sets the same)
+      P.n_steps = (int)(n1 - n0);
+      P.rec = rec;
       P.lam = lam;
       P.lacc = lacc;
       CUDA_TRY(cudaMemsetAsync(P.bar, 0, 8, st));

@@ -109,6 +109,30 @@ def test_grad_cooperative_segments_match_per_stage_launches_and_oracle(ck):
     assert np.max(np.abs(g - ref)) <= 1e-10 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("record_segments", [3, -1])
+def test_grad_recorded_segments_skip_recomputation(record_segments):
+    """A workspace with more recordings: the forward pass records the last segments and the
+    backward sweep does not recompute them (-1: all five segments).  Equal to the default
+    workspace up to the order of the gradient atomics, and to the oracle."""
+    import paper_2203_05526_gb300 as bq
+    p = _small_control(n_modes=2, N=4, n_seg=4, steps_per_seg=6)
+    l0, g0 = gpu_state(p).grad(p.dt, p.n_steps, 5)
+    st = gpu_state(p)
+    n0 = bq.launch_count()
+    l1, g1 = st.grad(p.dt, p.n_steps, 5, record_segments=record_segments)
+    launches = bq.launch_count() - n0
+    n_rec = 5 if record_segments < 0 else record_segments
+    # cooperative launches: one forward per segment, one recomputation per unrecorded
+    # segment, one adjoint per segment, plus evaluation and seeding
+    assert launches <= 5 + (5 - n_rec) + 5 + 3, launches
+    assert abs(l1[0] - l0[0]) <= 1e-14 * max(1.0, abs(l0[0]))
+    assert np.max(np.abs(g1 - g0)) <= 1e-12 * np.max(np.abs(g0))
+    loss_o, gt, gp = ograd.loss_and_grad(p, checkpoint_every=5)
+    ref = _flat_oracle(gt, gp)
+    assert np.max(np.abs(g1 - ref)) <= 1e-10 * np.max(np.abs(ref))
+    assert abs(st.time()) == 0.0
+
+
 def test_grad_cooperative_segments_with_more_items_than_ctas():
     """The full-size two-mode control state with 32-point tiles: more work items per stage
     than resident CTAs, so each CTA takes several items per stage (40 steps, segments of 7)."""
