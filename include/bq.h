@@ -231,6 +231,10 @@ typedef struct bq_tune {
                           * grid barriers whose waits are bounded), 0 = one launch per stage;
                           * ignored where the device has no cooperative launch */
   double grad_us;        /* bq_autotune_grad: device time of the trial gradient per RK4 step */
+  int pipe_fused;        /* BQ_PATH_PIPE: 1 = the four stages of a step in one launch (every CTA
+                          * runs its own systems' stages in order; no CTA waits for another),
+                          * 0 = one launch per RK4 stage.  The arithmetic is the same. */
+  int pad;
 } bq_tune;
 
 /* Current schedules of the state (step_us / solve_us: last bq_autotune result, else 0). */

@@ -44,7 +44,7 @@ class bq_tune(C.Structure):
     _fields_ = [("stage_path", C.c_int), ("pipe_slots", C.c_int), ("pipe_ctas_per_sm", C.c_int),
                 ("solve_kernel", C.c_int), ("solve_ctas_per_sm", C.c_int), ("n_candidates", C.c_int),
                 ("step_us", C.c_double), ("solve_us", C.c_double), ("tile", C.c_int), ("lanes", C.c_int), ("gread", C.c_int),
-                ("grad_coop", C.c_int), ("grad_us", C.c_double)]
+                ("grad_coop", C.c_int), ("grad_us", C.c_double), ("pipe_fused", C.c_int), ("pad", C.c_int)]
 
 
 class bq_plan_info(C.Structure):
@@ -331,7 +331,7 @@ class State:
         return dict(stage_path=PATH[t.stage_path], pipe_slots=t.pipe_slots, pipe_ctas_per_sm=t.pipe_ctas_per_sm,
                     solve_kernel=SOLVE_KERNEL[t.solve_kernel], solve_ctas_per_sm=t.solve_ctas_per_sm,
                     n_candidates=t.n_candidates, step_us=t.step_us, solve_us=t.solve_us, tile=t.tile, lanes=t.lanes,
-                    gread=t.gread, grad_coop=t.grad_coop, grad_us=t.grad_us)
+                    gread=t.gread, grad_coop=t.grad_coop, grad_us=t.grad_us, pipe_fused=t.pipe_fused)
 
     def get_tune(self) -> dict:
         t = bq_tune()

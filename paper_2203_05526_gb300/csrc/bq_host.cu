@@ -752,6 +752,9 @@ struct bq_state {
   int solve_ok = 0, solve_smem = 0, last_solve_grid = 0, solve_mg = 0, solve_mg_smem = 0;
   int use_pipe = 0, pipe_off_u = 0, pipe_zero_off = 0, pipe_zero_bytes = 0, pipe_mmax = 0, pipe_obs = 0;
   int pipe_slot[4] = {0, 0, 0, 0}, pipe_nslots[4] = {2, 2, 2, 2}, pipe_grid[4] = {1, 1, 1, 1}, pipe_mv_bytes = 0;
+  // one launch for all steps of a bq_step call (k_steps_pipe): enabled, and its grid (0: does
+  // not fit)
+  int pipe_fused = 1, pipe_steps_grid = 0;
   // 1 after bq_load_state: comp is zero by definition but not written yet (the pipelined and
   // streaming kernels skip reading it at their next stage 1; every other consumer clears it
   // first, see ensure_comp)
@@ -1375,7 +1378,13 @@ static int pipe_configure(bq_state* st, int slots, int cap) {
     if (cap > 0) per_sm = std::min(per_sm, cap);
     grid[q] = std::min(st->n_sys, per_sm * nsm);
   }
+  // the multi-step kernel holds all four stages: its own occupancy
+  int per_sm = 0;
+  CUDA_TRY(bq::steps_pipe_blocks_per_sm(st->dtype, st->m1_variant,
+                                        (int)((size_t)slots * st->pipe_slot[0] + st->pipe_mv_bytes), &per_sm));
+  if (cap > 0) per_sm = std::min(per_sm, cap);
   for (int q = 0; q < 4; ++q) { st->pipe_nslots[q] = slots; st->pipe_grid[q] = grid[q]; }
+  st->pipe_steps_grid = per_sm > 0 ? std::min(st->n_sys, per_sm * nsm) : 0;
   st->pipe_cap = cap;
   return BQ_OK;
 }
@@ -1572,8 +1581,13 @@ static bq::StageArgs stage_args(bq_state* s, int stage, double dt) {
   return a;
 }
 
-// kernels enqueued by one stage (the pipelined kernel evaluates its drive envelopes itself)
+// kernels enqueued by one stage launch (the pipelined kernel evaluates its drive envelopes itself)
 static int kernels_per_stage(const bq_state*, bool) { return 1; }
+
+// bq_step's pipelined path runs the four stages of a step in one kernel (k_steps_pipe)
+static bool pipe_fused_on(const bq_state* s) { return s->use_pipe && s->pipe_fused && s->pipe_steps_grid > 0; }
+// kernels bq_step enqueues per RK4 step
+static int kernels_per_step(const bq_state* s) { return pipe_fused_on(s) ? 1 : 4 * kernels_per_stage(s, false); }
 
 // After a pipelined step, comp holds that step's increment, still to be added to y (the
 // pipelined kernel folds it at its next stage 1).  Every other consumer of the raw arrays (the
@@ -1589,33 +1603,40 @@ static cudaError_t ensure_comp(bq_state* s, cudaStream_t st) {
   return cudaSuccess;
 }
 
+// Arguments of the pipelined kernels for stage a.stage (1..4) of a.
+static bq::PipeArgs pipe_args(bq_state* s, const bq::StageArgs& a) {
+  char* b = s->pool;
+  const Layout& L = s->L;
+  bq::PipeArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.recs = (const bq::PipeRec*)(b + L.off_precs);
+  pa.params = (const unsigned char*)(b + L.off_pparams);
+  pa.chans = a.chans;
+  pa.chpar = a.chpar;
+  pa.u_in = a.u_in; pa.u_out = a.u_out; pa.y = a.y; pa.acc = a.acc; pa.comp = a.comp;
+  pa.ticket = a.ticket; pa.counter = a.counter; pa.tau_base = a.tau_base;
+  pa.error = (unsigned int*)(b + L.off_ctrl + 32);
+  pa.n_sys = s->n_sys;
+  const int q = a.stage - 1;
+  pa.n_slots = s->pipe_nslots[q];
+  pa.slot_bytes = s->pipe_slot[q];
+  pa.off_u = s->pipe_off_u;
+  pa.zero_off = s->pipe_zero_off;
+  pa.zero_bytes = s->pipe_zero_bytes;
+  pa.mmax = s->pipe_mmax;
+  pa.reverse = a.reverse;
+  pa.comp_zero = a.stage == 1 ? s->comp_zero : 0;
+  pa.obs = s->pipe_obs ? (double2*)(b + L.off_obs) : nullptr;
+  pa.dt = a.dt;
+  pa.horizon = a.horizon;
+  return pa;
+}
+
 static cudaError_t launch_any_stage(bq_state* s, const bq::StageArgs& a, cudaStream_t st) {
   if (s->use_pipe && !a.rec) {
-    char* b = s->pool;
-    const Layout& L = s->L;
-    bq::PipeArgs pa;
-    std::memset(&pa, 0, sizeof(pa));
-    pa.recs = (const bq::PipeRec*)(b + L.off_precs);
-    pa.params = (const unsigned char*)(b + L.off_pparams);
-    pa.chans = a.chans;
-    pa.chpar = a.chpar;
-    pa.u_in = a.u_in; pa.u_out = a.u_out; pa.y = a.y; pa.acc = a.acc; pa.comp = a.comp;
-    pa.ticket = a.ticket; pa.counter = a.counter; pa.tau_base = a.tau_base;
-    pa.error = (unsigned int*)(b + L.off_ctrl + 32);
-    pa.n_sys = s->n_sys;
+    const bq::PipeArgs pa = pipe_args(s, a);
     const int q = a.stage - 1;
-    pa.n_slots = s->pipe_nslots[q];
-    pa.slot_bytes = s->pipe_slot[q];
-    pa.off_u = s->pipe_off_u;
-    pa.zero_off = s->pipe_zero_off;
-    pa.zero_bytes = s->pipe_zero_bytes;
-    pa.mmax = s->pipe_mmax;
-    pa.reverse = a.reverse;
-    pa.comp_zero = a.stage == 1 ? s->comp_zero : 0;
-    pa.obs = s->pipe_obs ? (double2*)(b + L.off_obs) : nullptr;
     s->obs_valid = a.stage == 4 && s->pipe_obs;
-    pa.dt = a.dt;
-    pa.horizon = a.horizon;
     if (a.stage == 1) s->comp_zero = 0;  // stage 4 of this step writes comp everywhere
     return bq::launch_stage_pipe(pa, s->m1_variant, s->dtype, a.stage, s->pipe_grid[q],
                                  pa.n_slots * pa.slot_bytes + s->pipe_mv_bytes, st);
@@ -1628,6 +1649,23 @@ static cudaError_t launch_any_stage(bq_state* s, const bq::StageArgs& a, cudaStr
 }
 
 static cudaError_t enqueue_steps(bq_state* s, double dt, int64_t n, cudaStream_t st) {
+  if (pipe_fused_on(s)) {
+    // The four stages of a step in one launch of the multi-step kernel, one launch per step.
+    // (Several steps per launch were slower, 146 against 110 us per step on a 4096-system
+    // batch whose arrays fit in L2 and 1.95 against 1.43 ms on 65 536 systems: without the
+    // launch boundary the CTAs drift apart by stages and the data in flight outgrows L2 and
+    // spreads over the arrays in HBM.)
+    for (int64_t i = 0; i < n; ++i) {
+      const bq::PipeArgs pa = pipe_args(s, stage_args(s, 1, dt));
+      s->comp_zero = 0;
+      s->obs_valid = s->pipe_obs;
+      cudaError_t e = bq::launch_steps_pipe(pa, s->pool + s->L.off_ua, s->pool + s->L.off_ub, 1, s->m1_variant,
+                                            s->dtype, s->pipe_steps_grid,
+                                            pa.n_slots * pa.slot_bytes + s->pipe_mv_bytes, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   for (int64_t i = 0; i < n; ++i)
     for (int stage = 1; stage <= 4; ++stage) {
       cudaError_t e = launch_any_stage(s, stage_args(s, stage, dt), st);
@@ -1670,13 +1708,13 @@ extern "C" int bq_step(bq_state* s, double dt, int64_t n_steps, void* stream) {
     }
     while (left >= kGraphSteps) {
       CUDA_TRY(cudaGraphLaunch(s->graph, st));
-      g_launches += 4 * kGraphSteps * kernels_per_stage(s, false);
+      g_launches += kGraphSteps * kernels_per_step(s);
       left -= kGraphSteps;
     }
   }
   if (left > 0) {
     CUDA_TRY(enqueue_steps(s, dt, left, st));
-    g_launches += 4 * left * kernels_per_stage(s, false);
+    g_launches += left * kernels_per_step(s);
   }
   s->tau += (double)n_steps * dt;
   return BQ_OK;
@@ -1837,6 +1875,7 @@ extern "C" int bq_get_tune(const bq_state* s, bq_tune* out) {
   out->gread = s->gread_sched;
   out->grad_coop = s->grad_coop;
   out->grad_us = s->tune_grad_us;
+  out->pipe_fused = s->pipe_fused;
   return BQ_OK;
 }
 
@@ -1881,6 +1920,7 @@ extern "C" int bq_set_tune(bq_state* s, const bq_tune* t) {
   }
   s->lanes = t->lanes == 0 ? default_lanes(s->sys) : t->lanes;
   s->grad_coop = t->grad_coop != 0;
+  s->pipe_fused = t->pipe_fused != 0;
   drop_graph(s);
   return BQ_OK;
 }
@@ -1928,7 +1968,7 @@ extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratc
       if (rep == 1) CUDA_TRY(cudaEventRecord(e0, st));
       const int64_t ns = rep == 0 ? 1 : trial_steps;
       CUDA_TRY(solve ? enqueue_solve(s, dt, ns, st) : enqueue_steps(s, dt, ns, st));
-      g_launches += solve ? 1 : 4 * ns * kernels_per_stage(s, false);
+      g_launches += solve ? 1 : ns * kernels_per_step(s);
       if (rep == 1) CUDA_TRY(cudaEventRecord(e1, st));
     }
     CUDA_TRY(cudaEventSynchronize(e1));

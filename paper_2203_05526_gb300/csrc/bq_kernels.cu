@@ -636,6 +636,7 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 // Asynchronous copy of one complex value (8 or 16 bytes, naturally aligned) from global to
 // shared memory; the issuing thread reads it after cp_async_wait_all.
 template <typename C>
@@ -793,34 +794,61 @@ __device__ __forceinline__ void pipe_combine(C* __restrict__ uout, C* __restrict
   }
 }
 
+// State of a pipelined CTA shared by its stage calls: the slots' mbarriers, two batches of
+// system records, the stage times and the observable's staging.
+template <typename C>
+struct PipeShared {
+  unsigned long long full[4];
+  PipeRec recs[2][BQ_PIPE_RB];  // records of two batches of systems
+  double s_t[2];                // physical time of this stage, and of the step midpoint
+  C s_of[32];                   // w f_e of the pending observable entries
+  C s_ov[6][32];                // y and comp at their G_x, G_y and R points
+};
+
+// Once per CTA before its first stage: the slots' mbarriers, and the stage-input region of
+// every slot with its guard bands zeroed (neighbour reads at the edges of a system, whose
+// coefficients are zero there, land in them, so they must hold finite values; later systems
+// leave only earlier systems' finite values behind).
+template <typename C>
+__device__ __forceinline__ void pipe_init(const PipeArgs& A, PipeShared<C>& sh) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  if (threadIdx.x == 0)
+    for (int s = 0; s < A.n_slots; ++s) mbar_init(&sh.full[s], 1);
+  for (int s = 0; s < A.n_slots; ++s) {
+    float4* z = reinterpret_cast<float4*>(smem_raw + (size_t)s * A.slot_bytes + A.zero_off);
+    for (int i = threadIdx.x; i < A.zero_bytes / 16; i += blockDim.x) z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  fence_proxy_async();  // these writes come before the bulk copies into the same slots
+}
+
+// One RK4 stage of every system of this CTA (records blockIdx.x, blockIdx.x + G, ...).  tau:
+// tau at the start of the step.  jbase: systems this CTA has put through its slots before
+// (system j of this call uses slot (jbase + j) % n_slots and its mbarrier's phase
+// ((jbase + j) / n_slots) & 1).  Returns false if a bounded wait gave up (the error word is
+// set; the CTA must stop).
 template <typename T, int MX, int MY, int MS, int STAGE>
-__global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A) {
+__device__ __forceinline__ bool pipe_stage(const PipeArgs& A, PipeShared<typename C2T<T>::type>& sh, double tau,
+                                           int jbase) {
   using C = typename C2T<T>::type;
   constexpr int RS = BQ_PIPE_RS(MS);  // complex entries of a row / column coefficient record
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) unsigned long long full[4];
-  __shared__ PipeRec recs[2][BQ_PIPE_RB];  // records of two batches of systems
-  __shared__ double s_t[2];  // physical time of this stage, and of the step midpoint
+  auto& full = sh.full;
+  auto& recs = sh.recs;
+  auto& s_t = sh.s_t;
 
   const int tid = threadIdx.x;
   const int G = gridDim.x;
   const int nj = A.n_sys > (int)blockIdx.x ? (A.n_sys - (int)blockIdx.x + G - 1) / G : 0;
   const int S = A.n_slots;
   const int cs = (int)sizeof(C);
+  __syncthreads();  // the previous stage of this CTA is done with the records and times
   if (tid == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
-    const double tau = A.tau_base[0] + (double)(*(volatile long long*)A.counter) * A.dt;
     s_t[0] = pipe_chan_time(1, tau, STAGE, A.dt, A.horizon, A.reverse);
     s_t[1] = pipe_chan_time(2, tau, STAGE, A.dt, A.horizon, A.reverse);
+    // the stage input this stage bulk-copies was written by this CTA's threads in its previous
+    // stage (generic proxy); order those writes before the copies (async proxy)
+    fence_proxy_async_global();
   }
-  // Zero the stage-input region of every slot and its guard bands once: neighbour reads at
-  // the edges of a system (whose coefficients are zero there) land in them, so they must
-  // hold finite values; later systems leave only earlier systems' finite values behind.
-  for (int s = 0; s < S; ++s) {
-    float4* z = reinterpret_cast<float4*>(smem_raw + (size_t)s * A.slot_bytes + A.zero_off);
-    for (int i = tid; i < A.zero_bytes / 16; i += blockDim.x) z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  fence_proxy_async();  // these writes come before the bulk copies into the same slots
   auto load_batch = [&](int b) {
     if (tid < BQ_PIPE_RB) {
       const int j = b * BQ_PIPE_RB + tid;
@@ -852,10 +880,10 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
   // stage reads with per-thread loads into L2, one system ahead of use
   auto issue = [&](int j) {
     const PipeRec& r = recs[(j / BQ_PIPE_RB) & 1][j % BQ_PIPE_RB];
-    unsigned char* sl = slot_ptr(j % S);
+    unsigned char* sl = slot_ptr((jbase + j) % S);
     const unsigned blk = (unsigned)(r.blk_elems * cs);
     fence_proxy_async();
-    unsigned long long* bar = &full[j % S];
+    unsigned long long* bar = &full[(jbase + j) % S];
     mbar_expect_tx(bar, (unsigned)r.param_bytes + blk);
     bulk_g2s(sl, A.params + r.param_off, (unsigned)r.param_bytes, bar);
     bulk_g2s(sl + A.off_u, uin + r.blk_off, blk, bar);
@@ -882,12 +910,12 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
   // first read at the end of system j + 1 (obs_give: the products, a shuffle reduction, one
   // store per system).
   const bool obs_on = STAGE == 4 && A.obs != nullptr && (tid >> 5) == 1;
-  __shared__ C s_of[32];     // w f_e of the pending entries
-  __shared__ C s_ov[6][32];  // y and comp at their G_x, G_y and R points
+  auto& s_of = sh.s_of;  // w f_e of the pending entries
+  auto& s_ov = sh.s_ov;  // y and comp at their G_x, G_y and R points
   int oa = -1, ob = -1, oc = -1, on = 0;
   auto obs_take = [&](int j) {
     const PipeRec& rj = recs[(j / BQ_PIPE_RB) & 1][j % BQ_PIPE_RB];
-    const unsigned char* sj = slot_ptr(j % S);
+    const unsigned char* sj = slot_ptr((jbase + j) % S);
     const PipeHdr& hj = *reinterpret_cast<const PipeHdr*>(sj);
     const int lane = tid & 31;
     on = hj.n_obs;
@@ -990,22 +1018,25 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
       if (tid == 0) {
         ok = false;
         for (int it = 0; it < BQ_WAIT_SUSPENDS; ++it)
-          if (mbar_try_wait_for(&full[j % S], (unsigned)((j / S) & 1), BQ_WAIT_HINT_NS)) { ok = true; break; }
+          if (mbar_try_wait_for(&full[(jbase + j) % S], (unsigned)(((jbase + j) / S) & 1), BQ_WAIT_HINT_NS)) {
+            ok = true;
+            break;
+          }
       }
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicOr(A.error, 1u);
         // give the copies in flight a bounded chance to land before the CTA leaves
         for (int s = 0; s < S; ++s)
           for (int it = 0; it < BQ_WAIT_LIMIT; ++it)
-            if (mbar_try_wait(&full[s], (unsigned)((j / S) & 1))) break;
-        return;
+            if (mbar_try_wait(&full[s], (unsigned)(((jbase + j) / S) & 1))) break;
+        return false;
       }
     }
     // every thread is past system j - 1: its slot ((j + S - 1) % S) and the coefficient
     // records are free, so the next copy can start now
     if (tid == 0 && jn < nj) issue(jn);
     if (obs_on && j > 0) obs_load();
-    unsigned char* sl = slot_ptr(j % S);
+    unsigned char* sl = slot_ptr((jbase + j) % S);
     const PipeHdr& h = *reinterpret_cast<const PipeHdr*>(sl);
     const int nX = h.nX, nY = h.nY, nS = h.nS, has_sep = h.has_sep;
     const int sdiag = h.sdiag;  // bit q: sandwich term q acts only where k = l
@@ -1262,20 +1293,71 @@ __global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A
     }
     obs_end(j);
   }
-  __syncthreads();  // every system of this CTA is written before it takes its ticket
+  __syncthreads();  // every system of this CTA is written (and its slots are free)
   if (obs_on && nj > 0) {
     obs_load();
     obs_give(nj - 1);
   }
-  if (STAGE == 4 && tid == 0) {
+  return true;
+}
+
+// The last CTA to finish advances the state's step counter by n.
+__device__ __forceinline__ void pipe_ticket(const PipeArgs& A, long long n) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int t = atomicAdd(A.ticket, 1u);
     if (t == gridDim.x - 1) {
       *A.ticket = 0u;
-      *A.counter = *(volatile long long*)A.counter + 1;
+      *A.counter = *(volatile long long*)A.counter + n;
       __threadfence();
     }
   }
+}
+
+// One stage launch.
+template <typename T, int MX, int MY, int MS, int STAGE>
+__global__ void __launch_bounds__(BQ_PIPE_THREADS) k_stage_pipe(const PipeArgs A) {
+  __shared__ PipeShared<typename C2T<T>::type> sh;
+  pipe_init(A, sh);
+  const double tau = A.tau_base[0] + (double)(*(volatile long long*)A.counter) * A.dt;
+  if (!pipe_stage<T, MX, MY, MS, STAGE>(A, sh, tau, 0)) return;
+  if (STAGE == 4) pipe_ticket(A, 1);
+}
+
+// n_steps RK4 steps in one launch.  A system's stage depends only on the same system's
+// previous stage, and every CTA owns the same systems in every stage, so the CTAs never wait
+// for one another: each runs its systems' stages in order (the stage inputs alternate
+// between ua and ub as in the per-stage launches) while the other CTAs are at other stages.
+// bq_step launches it one step at a time (the CTAs then drift apart by at most a step).
+template <typename T, int MX, int MY, int MS>
+__global__ void __launch_bounds__(BQ_PIPE_THREADS) k_steps_pipe(const PipeArgs A, void* ua, void* ub, int n_steps) {
+  __shared__ PipeShared<typename C2T<T>::type> sh;
+  pipe_init(A, sh);
+  const int G = gridDim.x;
+  const int nj = A.n_sys > (int)blockIdx.x ? (A.n_sys - (int)blockIdx.x + G - 1) / G : 0;
+  const double tau0 = A.tau_base[0] + (double)(*(volatile long long*)A.counter) * A.dt;
+  int jbase = 0;
+  for (int i = 0; i < n_steps; ++i) {
+    const double tau = tau0 + (double)i * A.dt;
+    PipeArgs a = A;
+    a.comp_zero = i == 0 ? A.comp_zero : 0;
+    a.obs = nullptr;
+    a.u_in = A.y; a.u_out = ua;
+    if (!pipe_stage<T, MX, MY, MS, 1>(a, sh, tau, jbase)) return;
+    jbase += nj;
+    a.u_in = ua; a.u_out = ub;
+    if (!pipe_stage<T, MX, MY, MS, 2>(a, sh, tau, jbase)) return;
+    jbase += nj;
+    a.u_in = ub; a.u_out = ua;
+    if (!pipe_stage<T, MX, MY, MS, 3>(a, sh, tau, jbase)) return;
+    jbase += nj;
+    a.u_in = ua; a.u_out = nullptr;
+    a.obs = i == n_steps - 1 ? A.obs : nullptr;  // the observable of the last step
+    if (!pipe_stage<T, MX, MY, MS, 4>(a, sh, tau, jbase)) return;
+    jbase += nj;
+  }
+  pipe_ticket(A, n_steps);
 }
 
 
@@ -2786,6 +2868,13 @@ static cudaError_t pipe_attrs() {
   if ((e = pipe_attrs_t<double, BQ_M1_MAXT>()) != cudaSuccess) return e;
   if ((e = pipe_attrs_t<float, 2>()) != cudaSuccess) return e;
   if ((e = pipe_attrs_t<float, BQ_M1_MAXT>()) != cudaSuccess) return e;
+  const void* steps[4] = {(const void*)k_steps_pipe<double, 2, 2, 2>,
+                          (const void*)k_steps_pipe<double, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>,
+                          (const void*)k_steps_pipe<float, 2, 2, 2>,
+                          (const void*)k_steps_pipe<float, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>};
+  for (const void* f : steps)
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, BQ_MAX_DYN_SMEM)) != cudaSuccess)
+      return e;
   done = true;
   return cudaSuccess;
 }
@@ -2803,6 +2892,33 @@ cudaError_t launch_stage_pipe(const PipeArgs& a, int variant, int dtype, int sta
     else pipe_kernel<float, BQ_M1_MAXT>(stage)<<<grid, BQ_PIPE_THREADS, smem_bytes, s>>>(a);
   }
   return cudaGetLastError();
+}
+
+// The multi-step kernel for (dtype, variant).
+static const void* steps_pipe_func(int dtype, int variant) {
+  if (dtype == 0)
+    return variant == 0 ? (const void*)k_steps_pipe<double, 2, 2, 2>
+                        : (const void*)k_steps_pipe<double, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>;
+  return variant == 0 ? (const void*)k_steps_pipe<float, 2, 2, 2>
+                      : (const void*)k_steps_pipe<float, BQ_M1_MAXT, BQ_M1_MAXT, BQ_M1_MAXT>;
+}
+
+cudaError_t launch_steps_pipe(const PipeArgs& a, void* ua, void* ub, int n_steps, int variant, int dtype, int grid,
+                              int smem_bytes, cudaStream_t s) {
+  cudaError_t ea = pipe_attrs();
+  if (ea != cudaSuccess) return ea;
+  if (n_steps < 1) return cudaSuccess;
+  PipeArgs pa = a;
+  void* args[] = {(void*)&pa, (void*)&ua, (void*)&ub, (void*)&n_steps};
+  return cudaLaunchKernel(steps_pipe_func(dtype, variant), dim3(grid), dim3(BQ_PIPE_THREADS), args,
+                          (size_t)smem_bytes, s);
+}
+
+cudaError_t steps_pipe_blocks_per_sm(int dtype, int variant, int smem_bytes, int* out) {
+  cudaError_t ea = pipe_attrs();
+  if (ea != cudaSuccess) return ea;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, steps_pipe_func(dtype, variant), BQ_PIPE_THREADS,
+                                                       smem_bytes);
 }
 
 cudaError_t pipe_blocks_per_sm(int dtype, int variant, int stage, int smem_bytes, int* out) {

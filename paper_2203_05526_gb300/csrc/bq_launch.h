@@ -34,6 +34,11 @@ cudaError_t launch_adj_seed(const SysDesc* sys, const EvalGroup* groups, const E
 // in the kernel), RK4 stage `stage` (1..4).
 cudaError_t launch_stage_pipe(const PipeArgs& a, int variant, int dtype, int stage, int grid, int smem_bytes,
                               cudaStream_t s);
+// n_steps RK4 steps of the pipelined path in one launch (stage inputs alternating between ua
+// and ub; the step counter advances by n_steps), and its resident CTAs per SM.
+cudaError_t launch_steps_pipe(const PipeArgs& a, void* ua, void* ub, int n_steps, int variant, int dtype, int grid,
+                              int smem_bytes, cudaStream_t s);
+cudaError_t steps_pipe_blocks_per_sm(int dtype, int variant, int smem_bytes, int* out);
 cudaError_t pipe_blocks_per_sm(int dtype, int variant, int stage, int smem_bytes, int* out);
 // Batched persistent solve, merged-stencil form (256 threads, M <= 45, shifts in {-1,0,1}).
 cudaError_t launch_solve_mg(const SolveArgs& a, int dtype, int smem_bytes, int cap_per_sm, cudaStream_t s,

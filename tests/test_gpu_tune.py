@@ -57,8 +57,9 @@ def test_autotune_restores_state_and_time():
 
 @pytest.mark.parametrize("n", [64, 2000])
 def test_every_step_schedule_computes_the_same_step(n):
-    """Pipelined schedules (slots, CTAs per SM) run the same kernel: bitwise equal results,
-    with one system per CTA (64 instances) and with many per CTA in ragged sizes (2000).  The
+    """Pipelined schedules (slots, CTAs per SM, all steps of a call in one launch or one launch
+    per stage) run the same stage code: bitwise equal states and observables, with one system
+    per CTA (64 instances) and with many per CTA in ragged sizes (2000).  The
     one-CTA-per-system path evaluates the same stencil from per-term programs: equal to FP32
     rounding, and both match the FP64 oracle."""
     ps = _batch(n=n)
@@ -67,11 +68,17 @@ def test_every_step_schedule_computes_the_same_step(n):
     assert ref.get_tune()["stage_path"] == "pipe"
     ref.step(dt, n)
     base = _snapshot(ref)
-    for slots, cap in ((3, 0), (2, 1), (4, 2)):
+    assert ref.get_tune()["pipe_fused"] == 1
+    for slots, cap, fused in ((3, 0, 1), (2, 1, 1), (4, 2, 1), (2, 0, 0), (3, 1, 0)):
         st = gpu_state(ps, dtype="f32")
-        st.set_tune(stage_path="pipe", pipe_slots=slots, pipe_ctas_per_sm=cap)
-        st.step(dt, n)
-        assert np.array_equal(_snapshot(st), base), (slots, cap)
+        st.set_tune(stage_path="pipe", pipe_slots=slots, pipe_ctas_per_sm=cap, pipe_fused=fused)
+        if fused:
+            st.step(dt, n)
+        else:
+            for _ in range(n):  # one launch per stage, one call per step
+                st.step(dt, 1)
+        assert np.array_equal(_snapshot(st), base), (slots, cap, fused)
+        assert np.array_equal(st.evaluate(), ref.evaluate()), (slots, cap, fused)
     st = gpu_state(ps, dtype="f32")
     st.set_tune(stage_path="system")
     st.step(dt, n)
