@@ -413,6 +413,9 @@ def batched_leg(world: int):
     st.solve(DT, 200)  # warm-up
     st = bq.State(handles, opts)
     out["schedule"] = st.autotune(DT, trial_steps=20)  # bq_autotune: state restored afterwards
+    if out["schedule"]["solve_kernel"] == "step":  # bq_solve would step: time the persistent kernel
+        st.set_tune(solve_kernel="merged" if st.solve_eligible() else "program")
+    out["persistent_kernel"] = st.get_tune()["solve_kernel"]
     n0 = bq.launch_count()
     t_solve = timed(lambda: st.solve(DT, n_steps))
     launches = bq.launch_count() - n0
@@ -426,7 +429,9 @@ def batched_leg(world: int):
     st2.autotune(DT, trial_steps=8)
     t_step = timed(lambda: st2.step(DT, n_steps))
     out["streamed"] = {"seconds": t_step, "solves_per_s": 4096 / t_step,
-                       "updates_per_s": 4 * pts * n_steps / t_step}
+                       "updates_per_s": 4 * pts * n_steps / t_step,
+                       "launches_per_step": 1 if st2.get_tune()["pipe_fused"] else 4}
+    out["bq_solve_path"] = out["schedule"]["solve_kernel"]  # what bq_solve runs after bq_autotune
     # one instance per launch: 16 sampled instances, 2000 steps each, scaled
     sample = list(range(0, 4096, 256))
     sample_steps = 2000

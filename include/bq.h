@@ -206,6 +206,8 @@ int bq_solve_eligible(const bq_state* s, int* eligible);
 #define BQ_PATH_TILED 0    /* generic kernel, tiles of R with halo windows (any mode count) */
 #define BQ_PATH_SYSTEM 1   /* single mode, one CTA per system */
 #define BQ_PATH_PIPE 2     /* single mode, persistent CTAs with bulk-copy prefetch */
+#define BQ_SOLVE_STEP (-1)  /* bq_solve steps with bq_step's schedule (where bq_autotune measured it
+                             * faster than the persistent kernels, or no persistent kernel fits) */
 #define BQ_SOLVE_PROGRAM 0 /* persistent solve, per-term stencil programs */
 #define BQ_SOLVE_MERGED 1  /* persistent solve, merged per-row / per-column coefficients */
 
@@ -213,7 +215,7 @@ typedef struct bq_tune {
   int stage_path;        /* BQ_PATH_* used by bq_step */
   int pipe_slots;        /* BQ_PATH_PIPE: shared-memory slots per CTA (2..4) */
   int pipe_ctas_per_sm;  /* BQ_PATH_PIPE: resident CTAs per SM (0 = occupancy limit) */
-  int solve_kernel;      /* BQ_SOLVE_* used by bq_solve (-1: bq_solve falls back to bq_step) */
+  int solve_kernel;      /* BQ_SOLVE_* used by bq_solve (BQ_SOLVE_STEP: bq_solve runs bq_step) */
   int solve_ctas_per_sm; /* persistent solve: resident CTAs per SM (0 = occupancy limit) */
   int n_candidates;      /* bq_autotune: schedules measured */
   double step_us;        /* bq_autotune: device time of one RK4 step with bq_step's schedule */

@@ -37,7 +37,7 @@ MAX_MODES = 4
 
 
 PATH = {0: "tiled", 1: "system", 2: "pipe"}
-SOLVE_KERNEL = {-1: None, 0: "program", 1: "merged"}
+SOLVE_KERNEL = {-1: "step", 0: "program", 1: "merged"}  # -1: bq_solve runs bq_step
 
 
 class bq_tune(C.Structure):

@@ -750,6 +750,7 @@ struct bq_state {
   int B = 0, nm = 0, dtype = 0, method = 0, basis = 0, n_sys = 0, n_work = 0, smem_bytes = 0, use_m1 = 0, m1_variant = 0;
   int trace_small = 0, block_small = 0;
   int solve_ok = 0, solve_smem = 0, last_solve_grid = 0, solve_mg = 0, solve_mg_smem = 0;
+  int solve_via_step = 0;  // bq_solve runs bq_step (BQ_SOLVE_STEP)
   int use_pipe = 0, pipe_off_u = 0, pipe_zero_off = 0, pipe_zero_bytes = 0, pipe_mmax = 0, pipe_obs = 0;
   int pipe_slot[4] = {0, 0, 0, 0}, pipe_nslots[4] = {2, 2, 2, 2}, pipe_grid[4] = {1, 1, 1, 1}, pipe_mv_bytes = 0;
   // one launch for all steps of a bq_step call (k_steps_pipe): enabled, and its grid (0: does
@@ -1772,7 +1773,7 @@ static cudaError_t enqueue_solve(bq_state* s, double dt, int64_t n_steps, cudaSt
 
 extern "C" int bq_solve(bq_state* s, double dt, int64_t n_steps, void* stream) {
   if (!s) return fail(BQ_EINVAL, "state is NULL");
-  if (!s->solve_ok) return bq_step(s, dt, n_steps, stream);
+  if (!s->solve_ok || s->solve_via_step) return bq_step(s, dt, n_steps, stream);
   if (n_steps < 0) return fail(BQ_EINVAL, "n_steps < 0");
   if (!(dt > 0.0)) return fail(BQ_EINVAL, "dt must be > 0");
   if (dt > s->dt_max * (1.0 + 1e-12))
@@ -1865,7 +1866,7 @@ extern "C" int bq_get_tune(const bq_state* s, bq_tune* out) {
   out->stage_path = s->use_pipe ? BQ_PATH_PIPE : (s->use_m1 ? BQ_PATH_SYSTEM : BQ_PATH_TILED);
   out->pipe_slots = s->pipe_nslots[0];
   out->pipe_ctas_per_sm = s->pipe_cap;
-  out->solve_kernel = s->solve_ok ? (s->solve_mg ? BQ_SOLVE_MERGED : BQ_SOLVE_PROGRAM) : -1;
+  out->solve_kernel = s->solve_ok && !s->solve_via_step ? (s->solve_mg ? BQ_SOLVE_MERGED : BQ_SOLVE_PROGRAM) : BQ_SOLVE_STEP;
   out->solve_ctas_per_sm = s->solve_cap;
   out->n_candidates = s->tune_n;
   out->step_us = s->tune_step_us;
@@ -1911,8 +1912,12 @@ extern "C" int bq_set_tune(bq_state* s, const bq_tune* t) {
     if (t->solve_kernel == BQ_SOLVE_MERGED) {
       if (!s->solve_mg_ok) return fail(BQ_EUNSUPPORTED, "the merged persistent solve is not available");
       s->solve_mg = 1;
+      s->solve_via_step = 0;
     } else if (t->solve_kernel == BQ_SOLVE_PROGRAM) {
       s->solve_mg = 0;
+      s->solve_via_step = 0;
+    } else if (t->solve_kernel == BQ_SOLVE_STEP) {
+      s->solve_via_step = 1;
     } else {
       return fail(BQ_EINVAL, "unknown solve kernel %d", t->solve_kernel);
     }
@@ -2064,6 +2069,8 @@ extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratc
       if (rc != BQ_OK) break;
     }
   }
+  // bq_solve steps with bq_step's schedule when that was faster than every persistent kernel
+  if (rc == BQ_OK && s->solve_ok && best_step < best_solve) best.solve_kernel = BQ_SOLVE_STEP;
   cudaError_t er = restore();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -112,6 +112,16 @@ def test_solve_kernels_agree_and_tuned_solve_matches_streaming():
     for x, y in zip(st.read_system(5)[1:], streamed.read_system(5)[1:]):
         if x is not None:
             assert rel_err(x, y) <= 1e-10
+    # bq_solve with BQ_SOLVE_STEP runs bq_step: bitwise the streamed result
+    st = gpu_state(ps, dtype="f64")
+    st.set_tune(solve_kernel="step")
+    assert st.get_tune()["solve_kernel"] == "step"
+    st.solve(dt, n)
+    _sync()
+    for i in (0, 41, 95):
+        for x, y in zip(st.read_system(i)[1:], streamed.read_system(i)[1:]):
+            if x is not None:
+                assert np.array_equal(x, y)
 
 
 def test_unavailable_schedules_are_refused():
@@ -129,7 +139,7 @@ def test_unavailable_schedules_are_refused():
     with pytest.raises(bq.BQError):
         one.set_tune(stage_path="tiled")
     tune = st.autotune(two.dt, trial_steps=2)
-    assert tune["stage_path"] == "tiled" and tune["solve_kernel"] is None
+    assert tune["stage_path"] == "tiled" and tune["solve_kernel"] == "step"
 
 
 def test_tile_lengths_compute_the_same_step_and_gradients():
