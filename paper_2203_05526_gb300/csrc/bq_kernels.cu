@@ -1135,18 +1135,23 @@ __device__ __forceinline__ bool pipe_stage(const PipeArgs& A, PipeShared<typenam
         for (int p = 0; p < RS / 2; ++p) st_pair(colv + (p * BQ_MERGED_MAXM + i) * 2, f[2 * p], f[2 * p + 1]);
       }
       __syncthreads();
-      if (k0 < k1) {
+      // the strip loop, compiled for the system's number of sandwich terms NS (the per-point
+      // term loop then has no runtime bound)
+      auto strip = [&](auto ns_c) {
+        constexpr int NS = decltype(ns_c)::value;
         // field f of column l's record: pair f / 2, half f % 2
         auto cfld = [&](int f) { return colv[((f >> 1) * BQ_MERGED_MAXM + l) * 2 + (f & 1)]; };
         const C b0 = cfld(0), bm = cfld(1), bp = cfld(2);
-        T syq[MS];
-        C gyq[MS];
-        int soff[MS];
+        T syq[NS > 0 ? NS : 1];
+        C gyq[NS > 0 ? NS : 1];
+        int soff[NS > 0 ? NS : 1];
+        bool sdq[NS > 0 ? NS : 1];
 #pragma unroll
-        for (int q = 0; q < MS; ++q) {
-          syq[q] = q < nS ? cfld(3 + 2 * q).x : (T)0;
-          gyq[q] = q < nS ? cfld(4 + 2 * q) : zero;
+        for (int q = 0; q < NS; ++q) {
+          syq[q] = cfld(3 + 2 * q).x;
+          gyq[q] = cfld(4 + 2 * q);
           soff[q] = h.sSx[q] * M + h.sSy[q];
+          sdq[q] = (sdiag >> q) & 1;
         }
         const C* up = ur + k0 * M + l;  // the point (kk, l)
         const C* rv = rowv + k0 * 2;     // pair 0 of row kk's record
@@ -1170,16 +1175,15 @@ __device__ __forceinline__ bool pipe_stage(const PipeArgs& A, PipeShared<typenam
           kc = cfma(bp, pu[1], kc);
           C ks = zero;
 #pragma unroll
-          for (int q = 0; q < MS; ++q)
-            if (q < nS) {
-              const C sx = sxn;
-              C sg;
-              ld_pair(rrec + (2 + q) * PS, sg, sxn);
-              if (!((sdiag >> q) & 1) || on_diag) {  // secular projector: k = l only
-                ks = cfma(cscale(sx, syq[q]), pu[soff[q]], ks);
-                ks = cfma(sg, gyq[q], ks);
-              }
+          for (int q = 0; q < NS; ++q) {
+            const C sx = sxn;
+            C sg;
+            ld_pair(rrec + (2 + q) * PS, sg, sxn);
+            if (!sdq[q] || on_diag) {  // secular projector: k = l only
+              ks = cfma(cscale(sx, syq[q]), pu[soff[q]], ks);
+              ks = cfma(sg, gyq[q], ks);
             }
+          }
           return cadd(cadd(kd, cadd(kr, kc)), ks);
         };
         // two rows per iteration (independent chains); streamed values in a register ring
@@ -1208,6 +1212,15 @@ __device__ __forceinline__ bool pipe_stage(const PipeArgs& A, PipeShared<typenam
           up += 2 * M;
           rv += 4;
           go += 2 * M;
+        }
+      };
+      if (k0 < k1) {
+        switch (nS) {
+          case 0: strip(std::integral_constant<int, 0>{}); break;
+          case 1: if constexpr (MS >= 1) strip(std::integral_constant<int, 1>{}); break;
+          case 2: if constexpr (MS >= 2) strip(std::integral_constant<int, 2>{}); break;
+          case 3: if constexpr (MS >= 3) strip(std::integral_constant<int, 3>{}); break;
+          default: if constexpr (MS >= 4) strip(std::integral_constant<int, 4>{}); break;
         }
       }
       if (gq >= 0) {
