@@ -98,28 +98,31 @@ N_RANGE = (10, 40)  # Fock truncation range of the instances (--n-range)
 # separable source (18), the RK4 combine (13 on average over the four stages).
 FLOP_PER_POINT_STAGE = 70
 
-# DRAM traffic of the stage kernel per launch (mean over the four RK4 stages), from one ncu
-# capture of dram__bytes_read.sum + dram__bytes_write.sum on the default workload (65 536
-# instances, N 10..40, complex FP32); reported only while the stage kernel's definition is
-# the one that was measured and the workload and schedule are the default ones.
-STAGE_TRAFFIC = {"kernel": "k_stage_pipe", "kernel_sha256": "7c0b32b1bb82de8895dd7cd22556525cc7277a07a323404caaddb6841c1a42e5",
-                 "instances": 65536, "n_range": (10, 40), "dtype": "f32", "bytes_per_launch": 1.8457e+09}
+# DRAM traffic of the fused step kernel per launch (one RK4 step), from one ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum on the default workload (65 536 instances,
+# N 10..40, complex FP32); reported only while the kernel's definition is the one that was
+# measured and the workload and schedule are the default ones.
+STAGE_TRAFFIC = {"kernel": "k_steps_pipe", "kernel_sha256": "f395747679ce58d7a51a22bd1e0ea58a0a2f4f470a00059fd0bd39eccbd8475f",
+                 "instances": 65536, "n_range": (10, 40), "dtype": "f32", "bytes_per_launch": 7.565e9}
 
 
-def stage_kernel_sha256(name: str) -> str:
-    """sha256 of a stage kernel's definition (from its signature to the closing brace at
-    column 0) in bq_kernels.cu."""
+def stage_kernel_sha256(names=("pipe_stage", "pipe_combine", "k_steps_pipe")) -> str:
+    """sha256 of the definitions (each from its template line to the closing brace at column
+    0) of the functions that make up the measured kernel, in bq_kernels.cu."""
     import hashlib
     src = open(os.path.join(ROOT, "paper_2203_05526_gb300", "csrc", "bq_kernels.cu")).read()
-    a = src.index(f"{name}(const PipeArgs A) {{")
-    a = src.rindex("\ntemplate", 0, a) + 1
-    b = src.index("\n}\n", a) + 3
-    return hashlib.sha256(src[a:b].encode()).hexdigest()
+    h = hashlib.sha256()
+    for name in names:
+        a = src.index(f" {name}(")
+        a = src.rindex("\ntemplate", 0, a) + 1
+        b = src.index("\n}\n", a) + 3
+        h.update(src[a:b].encode())
+    return h.hexdigest()
 
 
 def measured_traffic(instances: int, dtype: str, schedule: dict):
     t = STAGE_TRAFFIC
-    if t["bytes_per_launch"] is None or stage_kernel_sha256(t["kernel"]) != t["kernel_sha256"]:
+    if t["bytes_per_launch"] is None or stage_kernel_sha256() != t["kernel_sha256"]:
         return None
     if instances != t["instances"] or tuple(N_RANGE) != t["n_range"] or dtype != t["dtype"]:
         return None
@@ -877,9 +880,14 @@ def main():
     # exact is read and written once per step, and stage 4 reads the state once more to add the
     # step's increment to it): reported beside it.
     csz = 8 if args.dtype == "f32" else 16
-    bytes_per_launch = 4 * csz * pts
-    kernel_bytes_per_launch = 18 * csz * pts / 4
-    launch_s = stage_ms / 1e3 / (4 * args.steps)
+    # the pipelined path runs the four stages of a step in one launch (k_steps_pipe); the other
+    # paths launch once per stage
+    variant = state.stage_variant()
+    fused = variant == "pipelined" and state.get_tune()["pipe_fused"] == 1
+    stages_per_launch = 4 if fused else 1
+    bytes_per_launch = stages_per_launch * 4 * csz * pts
+    kernel_bytes_per_launch = stages_per_launch * 18 * csz * pts / 4
+    launch_s = stage_ms / 1e3 / (4 * args.steps / stages_per_launch)
     achieved = bytes_per_launch / launch_s / 1e9
     peaks = {}
     try:
@@ -888,9 +896,11 @@ def main():
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": measured_traffic(args.instances, args.dtype, schedule), "kernel": {"pipelined": "bq::k_stage_pipe", "single_mode": "bq::k_stage_m1",
-                                               "generic": "bq::k_stage"}[state.stage_variant()], "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-            "bytes_per_launch": bytes_per_launch, "bytes_per_point_stage": 4 * csz,
+            "traffic": measured_traffic(args.instances, args.dtype, schedule) if fused else None,
+            "kernel": "bq::k_steps_pipe" if fused else {"pipelined": "bq::k_stage_pipe", "single_mode": "bq::k_stage_m1",
+                                                          "generic": "bq::k_stage"}[variant],
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "stages_per_launch": stages_per_launch, "bytes_per_launch": bytes_per_launch, "bytes_per_point_stage": 4 * csz,
             "kernel_bytes_per_launch": kernel_bytes_per_launch, "kernel_transfers_per_step": 18,
             "avg_launch_us": launch_s * 1e6}
 
