@@ -1214,14 +1214,13 @@ __device__ __forceinline__ bool pipe_stage(const PipeArgs& A, PipeShared<typenam
           go += 2 * M;
         }
       };
+      // (a system without sandwich terms takes the one-term loop: the builders zero-fill the
+      // unused record fields, so the extra term adds exact zeros; fewer loop copies keep the
+      // kernel's code small)
       if (k0 < k1) {
-        switch (nS) {
-          case 0: strip(std::integral_constant<int, 0>{}); break;
-          case 1: if constexpr (MS >= 1) strip(std::integral_constant<int, 1>{}); break;
-          case 2: if constexpr (MS >= 2) strip(std::integral_constant<int, 2>{}); break;
-          case 3: if constexpr (MS >= 3) strip(std::integral_constant<int, 3>{}); break;
-          default: if constexpr (MS >= 4) strip(std::integral_constant<int, 4>{}); break;
-        }
+        if (nS <= 1) strip(std::integral_constant<int, 1>{});
+        else if (nS == 2 || MS == 2) strip(std::integral_constant<int, (MS >= 2 ? 2 : 1)>{});
+        else strip(std::integral_constant<int, MS>{});
       }
       if (gq >= 0) {
         const bool isx = gq < M;
