@@ -763,7 +763,6 @@ struct bq_state {
   // 1 while the per-system Tr(rho0 A) contributions the pipelined kernel's last stage 4 left
   // in the pool describe the current state (bq_evaluate then only reads them back)
   int obs_valid = 0;
-  std::vector<int> trace_sys_off, trace_n_sys;  // systems of every problem's trace group
   int has_diag = 0;     // some term acts only on diagonal index pairs (secular dissipator)
   int r_diag = 0;       // diagonal residual layout
   int has_gread = 0;    // some work item reads its R sources from global memory
@@ -1527,10 +1526,6 @@ extern "C" int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* 
   st->solve_mg_ok = P.solve_mg;
   st->solve_mg_smem = P.solve_mg_smem;
   st->n_trace_groups = P.n_trace_groups; st->n_block_groups = P.n_block_groups; st->block_dim = P.block_dim;
-  for (int g = 0; g < P.n_trace_groups; ++g) {
-    st->trace_sys_off.push_back(P.groups[g].sys_off);
-    st->trace_n_sys.push_back(P.groups[g].n_sys);
-  }
   st->total_elems = P.total_elems; st->dt_max = dt_max; st->horizon = o->horizon; st->reverse = o->reverse_time;
   st->pool = base; st->L = L; st->sys = P.sys;
   for (int b = 0; b < B; ++b) for (int j = 0; j < BQ_MAX_MODES; ++j) st->prob_M.push_back(P.comp[b].M[j]);
@@ -1590,12 +1585,10 @@ static bool pipe_fused_on(const bq_state* s) { return s->use_pipe && s->pipe_fus
 // kernels bq_step enqueues per RK4 step
 static int kernels_per_step(const bq_state* s) { return pipe_fused_on(s) ? 1 : 4 * kernels_per_stage(s, false); }
 
-// After a pipelined step, comp holds that step's increment, still to be added to y (the
-// pipelined kernel folds it at its next stage 1).  Every other consumer of the raw arrays (the
-// other stage kernels, the persistent solve, the adjoint, read-back and snapshots) expects a
-// rounding-size compensation there: fold first (exact, asynchronous on st).
-// After bq_load_state the compensation is zero by definition but not written yet: the
-// pipelined kernel skips reading it at its next stage 1, every other consumer clears it first.
+// comp holds the rounding residual of the last state update (true state = y - comp).  After
+// bq_load_state it is zero by definition but not written yet: the pipelined kernel skips
+// reading it at its next stage 1, and every other consumer of the raw arrays clears it first
+// (asynchronous on st).
 static cudaError_t ensure_comp(bq_state* s, cudaStream_t st) {
   if (!s->comp_zero) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(s->pool + s->L.off_comp, 0, (size_t)s->total_elems * (s->dtype == BQ_F64 ? 16 : 8), st);

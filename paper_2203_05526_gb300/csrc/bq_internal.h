@@ -211,7 +211,7 @@ struct PipeArgs {
   void* u_out;
   void* y;
   void* acc;            // stage sum (scratch)
-  void* comp;           // pending increment / compensation of the state (part of the state)
+  void* comp;           // rounding residual of the state (part of the state: true value y - comp)
   unsigned int* ticket;
   long long* counter;
   const double* tau_base;

@@ -801,7 +801,7 @@ struct PipeShared {
   unsigned long long full[4];
   PipeRec recs[2][BQ_PIPE_RB];  // records of two batches of systems
   double s_t[2];                // physical time of this stage, and of the step midpoint
-  C s_of[32];                   // w f_e of the pending observable entries
+  C s_of[32];                   // w f_e of the observable entries being evaluated
   C s_ov[6][32];                // y and comp at their G_x, G_y and R points
 };
 
@@ -910,7 +910,7 @@ __device__ __forceinline__ bool pipe_stage(const PipeArgs& A, PipeShared<typenam
   // first read at the end of system j + 1 (obs_give: the products, a shuffle reduction, one
   // store per system).
   const bool obs_on = STAGE == 4 && A.obs != nullptr && (tid >> 5) == 1;
-  auto& s_of = sh.s_of;  // w f_e of the pending entries
+  auto& s_of = sh.s_of;  // w f_e of the entries being evaluated
   auto& s_ov = sh.s_ov;  // y and comp at their G_x, G_y and R points
   int oa = -1, ob = -1, oc = -1, on = 0;
   auto obs_take = [&](int j) {
@@ -2490,8 +2490,7 @@ __global__ void __launch_bounds__(BLK) k_solve_mg(const SolveArgs A) {
 
 // ---------------------------------------------------------------------------------------
 // Observables: one warp per evaluation group, lanes over (initial condition, entry) pairs.
-// The value of a state element is y - comp (comp: the pending increment the pipelined stage
-// kernel leaves between steps, or a rounding-size compensation).
+// The value of a state element is y - comp (comp: the rounding residual of the last update).
 // ---------------------------------------------------------------------------------------
 template <typename C>
 struct StateView {
