@@ -2178,7 +2178,7 @@ extern "C" int bq_grad(bq_state* s, double dt, int64_t n_steps, int checkpoint_e
   if (s->grad_coop && !s->use_m1) {
     CUDA_TRY(bq::coop_max_grid(s->dtype, s->nm, false, s->smem_bytes, &grid_f));
     CUDA_TRY(bq::coop_max_grid(s->dtype, s->nm, true, s->adj_smem, &grid_b));
-    const int src_items = s->max_s > 0 ? s->n_sys * s->max_s * 2 * ((s->ng_max + 7) / 8) : 0;
+    const int src_items = s->max_s > 0 ? s->n_sys * s->max_s * 2 * ((s->ng_max + 3) / 4) : 0;  // BQ_SRC_TILE_COOP
     grid_f = std::min(grid_f, s->n_work);
     grid_b = std::min(grid_b, std::max(s->n_work, src_items));
   }

@@ -1914,15 +1914,19 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
 // (G_x, G_y of the recorded stage input; b_R = dt/6 lam at stage 4).  grid = (systems, max S terms, 2).
 #define BQ_SRC_THREADS 256
 #define BQ_SRC_TILE 8      // outputs per CTA (one row per warp; BQ_SRC_THREADS / 8 partial sums per column)
+// outputs per CTA in the cooperative backward kernel (BQ_BLOCK threads): smaller tiles give the
+// phase more items, since the CTAs of a cooperative launch that have none just wait
+#define BQ_SRC_TILE_COOP 4
 #define BQ_SRC_ZCH 1024    // summed-index chunk held in shared memory
 // One CTA's part of the transposed source, (bx, by, bz) = (system, sandwich term, direction
 // and output tile), with NTH threads (k_adj_src: BQ_SRC_THREADS; the cooperative backward
 // segment kernel: BQ_BLOCK).
-template <typename T, int NM, int NTH>
+template <typename T, int NM, int NTH, int TILE>
 __device__ __forceinline__ void adj_src_body(const AdjArgs& A, int bx, int by, int bz) {
+  static_assert(TILE % (NTH / 32) == 0, "every warp sums TILE / (NTH / 32) rows");
   using C = typename C2T<T>::type;
   __shared__ C z[BQ_SRC_ZCH];
-  __shared__ C red[NTH / BQ_SRC_TILE][BQ_SRC_TILE];
+  __shared__ C red[NTH / TILE][TILE];
   __syncthreads();  // the CTA's previous item is done with z and red
   const SysDesc& sd = A.sys[bx];
   if (!sd.has_sep || !sd.has_r) return;
@@ -1936,7 +1940,7 @@ __device__ __forceinline__ void adj_src_body(const AdjArgs& A, int bx, int by, i
   if (t < 0) return;
   const TermDesc td = A.terms[sd.term_off + t];
   const int dirx = (bz & 1) == 0;  // 1: v_t over kx (sum over ly), 0: w_t over ly (sum over kx)
-  const int i0 = (bz >> 1) * BQ_SRC_TILE;
+  const int i0 = (bz >> 1) * TILE;
   const int ng = sd.n_g;
   if (i0 >= ng) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1952,7 +1956,7 @@ __device__ __forceinline__ void adj_src_body(const AdjArgs& A, int bx, int by, i
   auto midx = [&](int f) { return dm >= 0 ? (f / sd.stG[dm]) % sd.M[dm] : 0; };
   if (sd.r_diag) {
     // diagonal layout: B(i, j) is zero off i = j, so out[i] = bscale b_R[i] z[i]
-    if (tid < BQ_SRC_TILE && i0 + tid < ng) {
+    if (tid < TILE && i0 + tid < ng) {
       const int i = i0 + tid;
       int rem = i;
       int id[NM];
@@ -1975,9 +1979,9 @@ __device__ __forceinline__ void adj_src_body(const AdjArgs& A, int bx, int by, i
   // out[i] = bscale sum_j B(i, j) z[j], z[j] = w(j) other[j + delta], with B(i, j) the R
   // cotangent at (i, j) (dirx) or (j, i), and w(j) the product of the term's weights on the
   // summed side.  Chunks of z go through shared memory; the sums run in a fixed order.
-  C acc[BQ_SRC_TILE / (NTH / 32)];
+  C acc[TILE / (NTH / 32)];
 #pragma unroll
-  for (int r = 0; r < BQ_SRC_TILE / (NTH / 32); ++r) acc[r] = cmk<C>(0.0, 0.0);
+  for (int r = 0; r < TILE / (NTH / 32); ++r) acc[r] = cmk<C>(0.0, 0.0);
   C accc = cmk<C>(0.0, 0.0);
   for (int jc = 0; jc < ng; jc += BQ_SRC_ZCH) {
     const int nj = min(BQ_SRC_ZCH, ng - jc);
@@ -2001,8 +2005,8 @@ __device__ __forceinline__ void adj_src_body(const AdjArgs& A, int bx, int by, i
     if (dirx) {
       // rows i0 + warp * R + r: lanes stride over j (coalesced along the row)
 #pragma unroll
-      for (int r = 0; r < BQ_SRC_TILE / (NTH / 32); ++r) {
-        const int i = i0 + warp * (BQ_SRC_TILE / (NTH / 32)) + r;
+      for (int r = 0; r < TILE / (NTH / 32); ++r) {
+        const int i = i0 + warp * (TILE / (NTH / 32)) + r;
         if (i < ng) {
           const C* row = bsrc + (int64_t)i * ng + jc;
           const int mi = midx(i);
@@ -2013,10 +2017,10 @@ __device__ __forceinline__ void adj_src_body(const AdjArgs& A, int bx, int by, i
     } else {
       // column i0 + tid % TILE: the CTA's NTH / TILE thread groups split j (each
       // group reads TILE adjacent columns of one row)
-      const int i = i0 + tid % BQ_SRC_TILE;
+      const int i = i0 + tid % TILE;
       const int mi = midx(i);
       if (i < ng)
-        for (int jj = tid / BQ_SRC_TILE; jj < nj; jj += NTH / BQ_SRC_TILE)
+        for (int jj = tid / TILE; jj < nj; jj += NTH / TILE)
           if (dm < 0 || midx(jc + jj) == mi) accc = cfma(bsrc[(int64_t)(jc + jj) * ng + i], z[jj], accc);
     }
   }
@@ -2024,22 +2028,22 @@ __device__ __forceinline__ void adj_src_body(const AdjArgs& A, int bx, int by, i
            (s * 2 + (dirx ? 0 : 1)) * ng;
   if (dirx) {
 #pragma unroll
-    for (int r = 0; r < BQ_SRC_TILE / (NTH / 32); ++r) {
+    for (int r = 0; r < TILE / (NTH / 32); ++r) {
       C v = acc[r];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         v.x += __shfl_down_sync(0xffffffffu, v.x, o);
         v.y += __shfl_down_sync(0xffffffffu, v.y, o);
       }
-      const int i = i0 + warp * (BQ_SRC_TILE / (NTH / 32)) + r;
+      const int i = i0 + warp * (TILE / (NTH / 32)) + r;
       if (lane == 0 && i < ng) out[i] = cscale(v, bscale);
     }
   } else {
-    red[tid / BQ_SRC_TILE][tid % BQ_SRC_TILE] = accc;
+    red[tid / TILE][tid % TILE] = accc;
     __syncthreads();
-    if (tid < BQ_SRC_TILE) {
+    if (tid < TILE) {
       C v = red[0][tid];
-      for (int w2 = 1; w2 < NTH / BQ_SRC_TILE; ++w2) v = cadd(v, red[w2][tid]);
+      for (int w2 = 1; w2 < NTH / TILE; ++w2) v = cadd(v, red[w2][tid]);
       const int i = i0 + tid;
       if (i < ng) out[i] = cscale(v, bscale);
     }
@@ -2048,7 +2052,7 @@ __device__ __forceinline__ void adj_src_body(const AdjArgs& A, int bx, int by, i
 
 template <typename T, int NM>
 __global__ void __launch_bounds__(BQ_SRC_THREADS) k_adj_src(const AdjArgs A) {
-  adj_src_body<T, NM, BQ_SRC_THREADS>(A, blockIdx.x, blockIdx.y, blockIdx.z);
+  adj_src_body<T, NM, BQ_SRC_THREADS, BQ_SRC_TILE>(A, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -2148,7 +2152,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_coop_bwd(const CoopArgs P) {
       if (n_src > 0) {
         for (int it = blockIdx.x; it < n_src; it += gridDim.x) {
           const int bx = it / src_per_sys, rem = it - bx * src_per_sys;
-          adj_src_body<T, NM, BQ_BLOCK>(a, bx, rem / (2 * P.src_tiles), rem % (2 * P.src_tiles));
+          adj_src_body<T, NM, BQ_BLOCK, BQ_SRC_TILE_COOP>(a, bx, rem / (2 * P.src_tiles), rem % (2 * P.src_tiles));
         }
         if (!grid_barrier(P.bar, P.error)) return;
       }
@@ -2831,7 +2835,7 @@ cudaError_t launch_coop(int dtype, int nm, bool bwd, CoopArgs P, int smem_bytes,
   if (!f || grid < 1) return cudaErrorInvalidValue;
   cudaError_t e = coop_prepare(f, smem_bytes);
   if (e != cudaSuccess) return e;
-  P.src_tiles = (P.adj.ng_max + BQ_SRC_TILE - 1) / BQ_SRC_TILE;
+  P.src_tiles = (P.adj.ng_max + BQ_SRC_TILE_COOP - 1) / BQ_SRC_TILE_COOP;
   void* args[] = {(void*)&P};
   return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(BQ_BLOCK), args, (size_t)smem_bytes, s);
 }
