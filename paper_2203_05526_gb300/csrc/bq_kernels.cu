@@ -1598,9 +1598,15 @@ __device__ __forceinline__ int pwc_segment(const ChanDesc& cd, const double* par
 }
 
 // One work item of an adjoint stage (k_adj_stage: one per CTA; the cooperative backward
-// segment kernel: the CTA's items of every stage); fresh as in stage_body.
+// segment kernel: the CTA's items of every stage); fresh as in stage_body.  gacc / dcacc: the
+// calling thread's partial gradient sums, owned by the caller.  With accumulate, they carry
+// over to the CTA's next call (same item) and are reduced into the gradient slots only when
+// a term's factor changes before that call (a time-dependent envelope other than a piecewise
+// constant one, or a new piecewise-constant segment) or when last; otherwise every call
+// reduces them.
 template <typename T, int NM>
-__device__ __forceinline__ void adj_stage_body(const AdjArgs& A, int item, bool fresh) {
+__device__ __forceinline__ void adj_stage_body(const AdjArgs& A, int item, bool fresh, double2 (&gacc)[BQ_MAX_GT],
+                                               double2& dcacc, bool accumulate, bool last) {
   using C = typename C2T<T>::type;
   constexpr int ND = 2 * NM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1683,10 +1689,6 @@ __device__ __forceinline__ void adj_stage_body(const AdjArgs& A, int item, bool 
   // b_{i-1} = dt beta lam + cq dt q
   const T beta = stage == 4 ? (T)(1.0 / 3.0) : (stage == 3 ? (T)(1.0 / 3.0) : (T)(1.0 / 6.0));
   const T cq = stage == 4 ? dt : dt * (T)0.5;
-  double2 gacc[BQ_MAX_GT];
-  double2 dcacc = make_double2(0.0, 0.0);
-#pragma unroll
-  for (int g = 0; g < BQ_MAX_GT; ++g) gacc[g] = make_double2(0.0, 0.0);
   const int ngt = s_ngt;
 
   auto finish = [&](int64_t gi, C q) {
@@ -1836,6 +1838,24 @@ __device__ __forceinline__ void adj_stage_body(const AdjArgs& A, int item, bool 
   // its lane index and adds the partner's copy of that half): 31 additions per lane instead
   // of 5 per value, and afterwards lane j holds the warp's sum of value j.
   static_assert(2 * BQ_MAX_GT == 32, "the reduce-scatter maps one value to each lane");
+  if (accumulate && !last) {
+    // keep the partial sums unless a gradient term's factor changes before the next call
+    // (uniform over the CTA: it depends on the terms and the times only)
+    bool change = false;
+    for (int t = 0; t < nt && !change; ++t) {
+      if (gidx[t] < 0 || st[t].ch < 0) continue;
+      const ChanDesc cd = A.chans[st[t].ch];
+      if (cd.kind == 0) continue;  // constant
+      if (cd.kind != 2) { change = true; break; }
+      if (stage == 1) {  // the next call is the previous step: its piecewise-constant segment
+        const double tm = A.tau_step + 0.5 * A.dt, tn = tm - A.dt;
+        const int s0 = pwc_segment(cd, A.chpar, A.reverse ? A.horizon - tm : tm);
+        const int s1 = pwc_segment(cd, A.chpar, A.reverse ? A.horizon - tn : tn);
+        change = s0 != s1;
+      }
+    }
+    if (!change) return;
+  }
   if (ngt > 0 || (do_sep && sd.n_params > 0)) {
     const int lane = tid & 31, warp = tid >> 5;
     double v[32];
@@ -1902,11 +1922,18 @@ __device__ __forceinline__ void adj_stage_body(const AdjArgs& A, int item, bool 
       atomicAdd(A.grad + sd.grad_off + tid, dcv.x * a.x - dcv.y * a.y);
     }
   }
+#pragma unroll
+  for (int g = 0; g < BQ_MAX_GT; ++g) gacc[g] = make_double2(0.0, 0.0);
+  dcacc = make_double2(0.0, 0.0);
 }
 
 template <typename T, int NM>
 __global__ void __launch_bounds__(BQ_BLOCK) k_adj_stage(const AdjArgs A) {
-  adj_stage_body<T, NM>(A, blockIdx.x, true);
+  double2 gacc[BQ_MAX_GT];
+#pragma unroll
+  for (int g = 0; g < BQ_MAX_GT; ++g) gacc[g] = make_double2(0.0, 0.0);
+  double2 dcacc = make_double2(0.0, 0.0);
+  adj_stage_body<T, NM>(A, blockIdx.x, true, gacc, dcacc, false, true);
 }
 
 // Transposed separable source: for every system and sandwich term t
@@ -2135,6 +2162,12 @@ template <typename T, int NM>
 __global__ void __launch_bounds__(BQ_BLOCK) k_coop_bwd(const CoopArgs P) {
   const bool reload = P.n_work > (int)gridDim.x;
   bool first = true;
+  // per-thread partial gradient sums, kept across the stages of the segment when every CTA
+  // keeps one item (reduced into the gradient slots when a factor changes and at the end)
+  double2 gacc[BQ_MAX_GT];
+#pragma unroll
+  for (int g = 0; g < BQ_MAX_GT; ++g) gacc[g] = make_double2(0.0, 0.0);
+  double2 dcacc = make_double2(0.0, 0.0);
   void* lam = P.lam;
   void* lacc = P.lacc;
   const int src_per_sys = P.max_s * 2 * P.src_tiles;
@@ -2157,7 +2190,7 @@ __global__ void __launch_bounds__(BQ_BLOCK) k_coop_bwd(const CoopArgs P) {
         if (!grid_barrier(P.bar, P.error)) return;
       }
       for (int it = blockIdx.x; it < P.n_work; it += gridDim.x) {
-        adj_stage_body<T, NM>(a, it, reload || first);
+        adj_stage_body<T, NM>(a, it, reload || first, gacc, dcacc, !reload, n == 0 && stage == 1);
         first = false;
       }
       if (!grid_barrier(P.bar, P.error)) return;
