@@ -2384,6 +2384,33 @@ extern "C" int bq_autotune_grad(bq_state* s, double dt, int trial_steps, int che
     for (int gr : {0, 1})
       for (int tl : {0, 32, 64, 96, 128, 192, 256, 512})
         for (int ln : {1, 2, 4}) cands.push_back({tl, ln, gr});
+    // tiles that give at most k work items per SM (k = 1, 2, 3): a stage then puts the same
+    // number of items on every SM instead of one more on some (the FP64 stages are bound by
+    // each SM's FP64 pipe, so the SM with the most items sets the stage's time)
+    int dev = 0, nsm = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const size_t cs = s->dtype == BQ_F64 ? 16 : 8;
+    auto items = [&](int tl) {
+      std::vector<WorkItem> w;
+      int sm = 0, ad = 0;
+      build_work(s->sys, cs, tl, 1, w, sm, ad);
+      return (int)w.size();
+    };
+    int64_t max_pts = 32;
+    for (const SysDesc& sd : s->sys) max_pts = std::max<int64_t>(max_pts, sd.has_r ? sd.n_r : 0);
+    for (int k = 1; k <= 3; ++k) {
+      int lo = 32, hi = (int)std::min<int64_t>(max_pts, 1 << 20);
+      if (items(hi) > k * nsm) continue;  // even whole systems are more items than that
+      while (lo < hi) {                   // smallest tile with at most k * nsm items
+        const int mid = lo + (hi - lo) / 2;
+        if (items(mid) <= k * nsm) hi = mid; else lo = mid + 1;
+      }
+      bool have = false;
+      for (const Cand& c : cands) have = have || (c.tile == lo && c.gread == 1);
+      if (!have)
+        for (int ln : {1, 2, 4}) cands.push_back({lo, ln, 1});
+    }
   }
   const int tile0 = s->tile, lanes0 = s->lanes, gread0 = s->gread_sched;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
