@@ -1929,6 +1929,35 @@ extern "C" int bq_autotune_scratch_bytes(const bq_state* s, size_t* out) {
   return BQ_OK;
 }
 
+// Tiles (with global reads) that give at most k work items per SM, k = 1, 2, 3: the smallest
+// such tile for each k.  A stage then puts the same number of items on every SM instead of one
+// more on some, and the SM with the most items sets the stage's time.
+static std::vector<int> sm_aligned_tiles(const bq_state* s) {
+  std::vector<int> out;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return out;
+  const size_t cs = s->dtype == BQ_F64 ? 16 : 8;
+  auto items = [&](int tl) {
+    std::vector<WorkItem> w;
+    int sm = 0, ad = 0;
+    build_work(s->sys, cs, tl, 1, w, sm, ad);
+    return (int)w.size();
+  };
+  int64_t max_pts = 32;
+  for (const SysDesc& sd : s->sys) max_pts = std::max<int64_t>(max_pts, sd.has_r ? sd.n_r : 0);
+  for (int k = 1; k <= 3; ++k) {
+    int lo = 32, hi = (int)std::min<int64_t>(max_pts, 1 << 20);
+    if (items(hi) > k * nsm) continue;  // even whole systems are more items than that
+    while (lo < hi) {                   // smallest tile with at most k * nsm items
+      const int mid = lo + (hi - lo) / 2;
+      if (items(mid) <= k * nsm) hi = mid; else lo = mid + 1;
+    }
+    if (std::find(out.begin(), out.end(), lo) == out.end()) out.push_back(lo);
+  }
+  return out;
+}
+
 extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratch, size_t scratch_bytes, void* stream,
                            bq_tune* out) {
   if (!s || !scratch) return fail(BQ_EINVAL, "NULL argument");
@@ -2006,6 +2035,8 @@ extern "C" int bq_autotune(bq_state* s, double dt, int trial_steps, void* scratc
       for (int tl : {0, 64, 96, 128, 192, 256, 512})
         for (int ln : {1, 2, 4}) cands.push_back({BQ_PATH_TILED, 0, tl, ln, 0});
       for (int tl : {32, 64, 128, 256, 512})
+        for (int ln : {1, 2, 4}) cands.push_back({BQ_PATH_TILED, 0, tl, ln, 1});
+      for (int tl : sm_aligned_tiles(s))
         for (int ln : {1, 2, 4}) cands.push_back({BQ_PATH_TILED, 0, tl, ln, 1});
     }
     const int lanes0 = s->lanes;
@@ -2384,32 +2415,13 @@ extern "C" int bq_autotune_grad(bq_state* s, double dt, int trial_steps, int che
     for (int gr : {0, 1})
       for (int tl : {0, 32, 64, 96, 128, 192, 256, 512})
         for (int ln : {1, 2, 4}) cands.push_back({tl, ln, gr});
-    // tiles that give at most k work items per SM (k = 1, 2, 3): a stage then puts the same
-    // number of items on every SM instead of one more on some (the FP64 stages are bound by
-    // each SM's FP64 pipe, so the SM with the most items sets the stage's time)
-    int dev = 0, nsm = 0;
-    CUDA_TRY(cudaGetDevice(&dev));
-    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const size_t cs = s->dtype == BQ_F64 ? 16 : 8;
-    auto items = [&](int tl) {
-      std::vector<WorkItem> w;
-      int sm = 0, ad = 0;
-      build_work(s->sys, cs, tl, 1, w, sm, ad);
-      return (int)w.size();
-    };
-    int64_t max_pts = 32;
-    for (const SysDesc& sd : s->sys) max_pts = std::max<int64_t>(max_pts, sd.has_r ? sd.n_r : 0);
-    for (int k = 1; k <= 3; ++k) {
-      int lo = 32, hi = (int)std::min<int64_t>(max_pts, 1 << 20);
-      if (items(hi) > k * nsm) continue;  // even whole systems are more items than that
-      while (lo < hi) {                   // smallest tile with at most k * nsm items
-        const int mid = lo + (hi - lo) / 2;
-        if (items(mid) <= k * nsm) hi = mid; else lo = mid + 1;
-      }
+    // tiles that give at most k work items per SM (the FP64 stages are bound by each SM's
+    // FP64 pipe, so the SM with the most items sets the stage's time)
+    for (int tl : sm_aligned_tiles(s)) {
       bool have = false;
-      for (const Cand& c : cands) have = have || (c.tile == lo && c.gread == 1);
+      for (const Cand& c : cands) have = have || (c.tile == tl && c.gread == 1);
       if (!have)
-        for (int ln : {1, 2, 4}) cands.push_back({lo, ln, 1});
+        for (int ln : {1, 2, 4}) cands.push_back({tl, ln, 1});
     }
   }
   const int tile0 = s->tile, lanes0 = s->lanes, gread0 = s->gread_sched;

@@ -146,7 +146,7 @@ def test_tile_lengths_compute_the_same_step_and_gradients():
     """The tiled kernels evaluate every point from the same sources whatever the tile length
     and wherever the sources come from (shared-memory halo windows or global reads): the step
     and the adjoint gradients agree with the default tiling to rounding, and the autotuner
-    keeps a tile from its candidate list."""
+    keeps a valid tile."""
     p = configs.two_mode_control(n_seg=3, T=0.18, steps_per_seg=6, N=7)
     p.measured = {((1, 0), (0, 1)): 0.7 + 0.2j, ((0, 1), (1, 0)): 0.7 - 0.2j, ((1, 0), (1, 0)): 1.0,
                   ((2, 1), (0, 0)): 0.3, ((0, 0), (2, 1)): 0.3}
@@ -156,7 +156,7 @@ def test_tile_lengths_compute_the_same_step_and_gradients():
     ref.step(p.dt, p.n_steps)
     _sync()
     l0, g0 = gpu_state(p).grad(p.dt, p.n_steps, 6)
-    for tile, gread in ((32, 0), (96, 0), (192, 0), (1024, 0), (32, 1), (256, 1)):
+    for tile, gread in ((32, 0), (96, 0), (192, 0), (1024, 0), (32, 1), (47, 1), (256, 1)):
         st = gpu_state(p)
         st.set_tune(tile=tile, gread=gread)
         assert st.get_tune()["tile"] == tile and st.get_tune()["gread"] == gread
@@ -177,7 +177,8 @@ def test_tile_lengths_compute_the_same_step_and_gradients():
     with pytest.raises(bq.BQError):
         st.set_tune(lanes=3)
     tune = st.autotune(p.dt, trial_steps=2)
-    assert tune["tile"] in (0, 32, 64, 96, 128, 192, 256, 512) and tune["lanes"] in (1, 2, 4)
+    # a tile of the fixed list, or one of the tiles that give at most 1, 2 or 3 items per SM
+    assert (tune["tile"] == 0 or tune["tile"] >= 32) and tune["lanes"] in (1, 2, 4)
     assert tune["n_candidates"] >= 2
     st.step(p.dt, p.n_steps)
     _sync()
