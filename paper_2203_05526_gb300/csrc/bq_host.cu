@@ -1170,6 +1170,8 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
             pc.f[0] = (float)pc.p[0];
             pc.f[1] = (float)pc.p[1];
             pc.f[2] = cd.kind == BQ_CH_GAUSS ? (float)(1.0 / (2.0 * pc.p[3] * pc.p[3])) : 0.f;
+            pc.f[3] = cd.kind == BQ_CH_GAUSS ? (float)pc.p[2] : 0.f;
+            pc.c_lo = cd.kind == BQ_CH_GAUSS ? (float)(pc.p[2] - (double)pc.f[3]) : 0.f;
             pc.kind = cd.kind;
             pc.par_off = cd.par_off;
             pc.n_par = cd.n_par;
@@ -1218,6 +1220,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
                       "coefficient records as written above");
         static_assert(sizeof(bq::PipeObs<float2>) == 16 && sizeof(bq::PipeObs<double2>) == 32,
                       "entry records keep the block 16-B aligned");
+        static_assert(sizeof(bq::PipeRec) == 96, "two batches of records in the kernel's static shared memory");
         for (int i = 0; i < (int)P.sys.size(); ++i) {
           const SysDesc& sd = P.sys[i];
           bq::PipeRec r;
@@ -1241,6 +1244,8 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
           r.w_im = sd.w_im;
           r.w32_re = (float)sd.w_re;
           r.w32_im = (float)sd.w_im;
+          r.c32_re = (float)sd.c_re;
+          r.c32_im = (float)sd.c_im;
           r.sys = i;
           P.precs.push_back(r);
           blk_max = std::max(blk_max, (size_t)r.blk_elems);

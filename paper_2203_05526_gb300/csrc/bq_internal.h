@@ -157,6 +157,7 @@ struct __align__(16) PipeRec {
   int nb, rb;       // merged path: nb column strips of rb rows (thread t: column t % M, strip t / M)
   float inv_m;      // 1 / M (strip index without an integer division)
   float w32_re, w32_im;  // the weight below rounded to FP32 (the FP32 kernels' observable)
+  float c32_re, c32_im;  // C below rounded to FP32 (the FP32 kernels' G items)
   int sys;          // index of the system (records are ordered by size, largest first)
   double c_re, c_im;  // separation constant C of the system (Eq. 304)
   double w_re, w_im;  // weight of the system's initial condition
@@ -186,8 +187,9 @@ struct PipeObs {
 // channel parameter pool (the segment values are read from there).
 struct PipeChan {
   double p[4];
-  int kind, par_off, n_par, pad;
-  float f[4];  // the same in FP32: amplitude (re, im), then 1 / (2 sigma^2) for a Gaussian
+  int kind, par_off, n_par;
+  float c_lo;  // Gaussian: the centre p[2] - f[3] (the FP32 remainder of the centre)
+  float f[4];  // the same in FP32: amplitude (re, im), then 1 / (2 sigma^2) and the centre for a Gaussian
 };
 // Stage coefficient of one term: c times the value of the block's envelope ch (0 or 1, -1:
 // static) at the stage time, or its conjugate (conj = 1).

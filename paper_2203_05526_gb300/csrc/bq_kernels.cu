@@ -664,13 +664,15 @@ __device__ __forceinline__ double pipe_chan_time(int kind, double tau_step, int 
 
 // Envelope value (bq.h channel kinds) at physical time t (t_mid: the step midpoint, where a
 // piecewise-constant envelope is read) from a parameter block's record.  In FP32 the Gaussian
-// costs one FP64 subtraction and otherwise runs on the FP32 pipe with the record's FP32
-// copies (GB300's FP64 rate is a small fraction of its FP32 rate and this sits on every
-// system's path); a piecewise-constant envelope reads its segment value from the channel
-// parameter pool.
+// runs on the FP32 pipe alone (GB300's FP64 rate is a small fraction of its FP32 rate and this
+// sits on every system's path): t and the centre come as unevaluated FP32 pairs (t32: hi, lo),
+// and t - centre = (t_hi - c_hi) + (t_lo - c_lo), where the first difference is exact wherever
+// the pulse is not negligible (Sterbenz: t within a factor 2 of the centre) and elsewhere off
+// by at most half an ulp of the centre.  A piecewise-constant envelope reads its segment value
+// from the channel parameter pool.
 template <typename T>
 __device__ __forceinline__ typename C2T<T>::type pipe_chan_value(const PipeChan& c, const double* chpar, double t,
-                                                                 double t_mid) {
+                                                                 double t_mid, const float (&t32)[2]) {
   using C = typename C2T<T>::type;
   switch (c.kind) {
     case 0:  // CONST
@@ -683,7 +685,7 @@ __device__ __forceinline__ typename C2T<T>::type pipe_chan_value(const PipeChan&
         v.x = c.p[0] * e;
         v.y = c.p[1] * e;
       } else {
-        const float d = (float)(t - c.p[2]);
+        const float d = (t32[0] - c.f[3]) + (t32[1] - c.c_lo);
         const float e = dev_exp<float>(-(d * d) * c.f[2]);
         v.x = c.f[0] * e;
         v.y = c.f[1] * e;
@@ -801,6 +803,7 @@ struct PipeShared {
   unsigned long long full[4];
   PipeRec recs[2][BQ_PIPE_RB];  // records of two batches of systems
   double s_t[2];                // physical time of this stage, and of the step midpoint
+  float s_t32[2];               // the stage time as an unevaluated FP32 pair (hi, lo)
   C s_of[32];                   // w f_e of the observable entries being evaluated
   C s_ov[6][32];                // y and comp at their G_x, G_y and R points
 };
@@ -845,6 +848,8 @@ __device__ __forceinline__ bool pipe_stage(const PipeArgs& A, PipeShared<typenam
   if (tid == 0) {
     s_t[0] = pipe_chan_time(1, tau, STAGE, A.dt, A.horizon, A.reverse);
     s_t[1] = pipe_chan_time(2, tau, STAGE, A.dt, A.horizon, A.reverse);
+    sh.s_t32[0] = (float)s_t[0];
+    sh.s_t32[1] = (float)(s_t[0] - (double)sh.s_t32[0]);
     // the stage input this stage bulk-copies was written by this CTA's threads in its previous
     // stage (generic proxy); order those writes before the copies (async proxy)
     fence_proxy_async_global();
@@ -1052,13 +1057,15 @@ __device__ __forceinline__ bool pipe_stage(const PipeArgs& A, PipeShared<typenam
     const C* ur = u + r.r_off;
     const C* ugx = u;
     const C* ugy = u + r.gy_off;
-    const C Cc = cmk<C>(r.c_re, r.c_im);
+    C Cc;
+    if constexpr (sizeof(T) == 8) Cc = cmk<C>(r.c_re, r.c_im);
+    else Cc = make_float2(r.c32_re, r.c32_im);
     // drive envelopes of the problem's time-dependent terms at this stage's time, from the
     // block (threads that build coefficient records; every thread on the general path)
     C e0 = cmk<C>(1.0, 0.0), e1 = cmk<C>(1.0, 0.0);
     if (!merged || rowb || colb) {
-      if (h.n_ch > 0) e0 = pipe_chan_value<T>(pc[0], A.chpar, s_t[0], s_t[1]);
-      if (h.n_ch > 1) e1 = pipe_chan_value<T>(pc[1], A.chpar, s_t[0], s_t[1]);
+      if (h.n_ch > 0) e0 = pipe_chan_value<T>(pc[0], A.chpar, s_t[0], s_t[1], sh.s_t32);
+      if (h.n_ch > 1) e1 = pipe_chan_value<T>(pc[1], A.chpar, s_t[0], s_t[1], sh.s_t32);
     }
     // stage coefficient of term q: static part times the envelope (or its conjugate)
     auto coef = [&](int q) {
@@ -2244,11 +2251,13 @@ __global__ void k_adj_seed(const SysDesc* __restrict__ sys, const EvalGroup* __r
 // stages ahead (triple buffered), the merged vectors one stage ahead (double buffered).
 // ---------------------------------------------------------------------------------------
 template <typename T, int BLK, int RB, int MX, int MY, int MS, bool DIAG>
-__global__ void __launch_bounds__(BLK) k_solve_mg(const SolveArgs A) {
+__global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 2 : 1) k_solve_mg(const SolveArgs A) {
   using C = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ M1Sys s;
   __shared__ C coef[3][3 * BQ_M1_MAXT];
+  __shared__ float cf32[3 * BQ_M1_MAXT][8];  // FP32 stage coefficients (see eval_coef)
+  __shared__ float tp32[4];                  // t0 and dt as FP32 pairs (hi, lo)
   __shared__ int s_next;
   const int tid = threadIdx.x;
   C* y_g = reinterpret_cast<C*>(A.y);
@@ -2283,26 +2292,88 @@ __global__ void __launch_bounds__(BLK) k_solve_mg(const SolveArgs A) {
     T* wSx = wY + nY * M;
     T* wSy = wSx + nS * M;
     const int nt = nX + nY + nS;
+    // Thread roles besides the strips, each in warps of its own counted from the top of the
+    // block down, so that no warp carries more than one of them on top of its strip (a warp
+    // runs its lanes' roles one after the other, and the slowest warp sets every stage's
+    // barrier): the G items (the last 2M threads), the rows of the merged vectors, the stage
+    // coefficients.  With M <= 42 and at most 6 terms they fit below the block's top.
+    const int g_lo = BLK - (has_sep ? 2 * M : 0);
+    const int b_lo = max((g_lo & ~31) - M, 0);
+    const int c_lo = max((b_lo & ~31) - nt, 0);
+    // Stage coefficient c_t e(t) of term t.  In FP64, and in FP32 for envelopes other than a
+    // Gaussian: the stage time in FP64, the envelope and the product in the state's precision.
+    // An FP32 Gaussian costs no FP64 operation (this sits on a warp's path every stage, and
+    // GB300's FP64 rate is a small fraction of its FP32 rate): its amplitude, 1 / (2 sigma^2)
+    // and centre (an FP32 pair) are set once per system in cf32; the stage time t = t0 + x dt
+    // (x = step + c_s, exact in FP32 below 2^23 steps; reversed reading: t0 = horizon - tau0
+    // and -dt) is formed as an unevaluated FP32 pair from the pairs of t0 and dt (error-free
+    // product by FMA, TwoSum), and t - centre = (t_hi - c_hi) + (t_lo - c_lo) is exact to the
+    // rounding of the difference wherever the pulse is not negligible.
     auto eval_coef = [&](int buf, int64_t step, int stage) {
-      if (tid < nt) {
-        const int t = tid < nX ? s.tX[tid] : (tid < nX + nY ? s.tY[tid - nX] : s.tS[tid - nX - nY]);
+      const int ct = tid - c_lo;
+      if (ct >= 0 && ct < nt) {
+        const float* k = cf32[ct];
+        if (sizeof(T) == 4 && k[2] > 0.5f) {
+          const float x = (float)step + (stage == 1 ? 0.f : (stage == 4 ? 1.f : 0.5f));
+          const float ph = x * tp32[2];
+          const float pl = fmaf(x, tp32[2], -ph) + x * tp32[3];
+          const float th = tp32[0] + ph;
+          const float bv = th - tp32[0];
+          const float tl = ((tp32[0] - (th - bv)) + (ph - bv)) + (tp32[1] + pl);
+          const float d = (th - k[6]) + (tl - k[7]);
+          const float g = dev_exp<float>(-(d * d) * k[5]);
+          coef[buf][ct] = cmul(cmk<C>(k[0], k[1]), cmk<C>(k[3] * g, k[4] * g));
+          return;
+        }
+        const int t = ct < nX ? s.tX[ct] : (ct < nX + nY ? s.tY[ct - nX] : s.tS[ct - nX - nY]);
         const TermDesc& td = A.terms[s.term_off + t];
-        double2 c = make_double2(td.c_re, td.c_im);
+        C c = cmk<C>(td.c_re, td.c_im);
         if (td.ch >= 0) {
           const ChanDesc cd = A.chans[td.ch];
           const double ts = A.tau0 + (double)step * A.dt;
           const double tau = (cd.kind == 2) ? ts + 0.5 * A.dt : ts + stage_c(stage) * A.dt;
-          double2 e = chan_value_t<T>(cd, A.chpar, A.reverse ? A.horizon - tau : tau);
-          if (td.conj) e.y = -e.y;
-          c = make_double2(c.x * e.x - c.y * e.y, c.x * e.y + c.y * e.x);
+          const double2 e = chan_value_t<T>(cd, A.chpar, A.reverse ? A.horizon - tau : tau);
+          c = cmul(c, cmk<C>(e.x, td.conj ? -e.y : e.y));
         }
-        coef[buf][tid] = cmk<C>(c.x, c.y);
+        coef[buf][ct] = c;
       }
     };
+    {
+      const int ct = tid - c_lo;
+      if (ct >= 0 && ct < nt) {
+        float* k = cf32[ct];
+        k[2] = 0.f;
+        if (sizeof(T) == 4 && A.n_steps < (1LL << 23)) {
+          const int t = ct < nX ? s.tX[ct] : (ct < nX + nY ? s.tY[ct - nX] : s.tS[ct - nX - nY]);
+          const TermDesc& td = A.terms[s.term_off + t];
+          if (td.ch >= 0 && A.chans[td.ch].kind == 1) {
+            const double* p = A.chpar + A.chans[td.ch].par_off;
+            k[0] = (float)td.c_re;
+            k[1] = (float)td.c_im;
+            k[2] = 1.f;
+            k[3] = (float)p[0];
+            k[4] = (float)(td.conj ? -p[1] : p[1]);
+            k[5] = (float)(1.0 / (2.0 * p[3] * p[3]));
+            k[6] = (float)p[2];
+            k[7] = (float)(p[2] - (double)k[6]);
+          }
+        }
+      }
+      if (tid == c_lo) {
+        const double t0 = A.reverse ? A.horizon - A.tau0 : A.tau0;
+        const double d0 = A.reverse ? -A.dt : A.dt;
+        tp32[0] = (float)t0;
+        tp32[1] = (float)(t0 - (double)tp32[0]);
+        tp32[2] = (float)d0;
+        tp32[3] = (float)(d0 - (double)tp32[2]);
+      }
+      __syncthreads();
+    }
     // merged vectors from coef[cb] into MV half mb: A0 Am Ap (rows) B0 Bm Bp (columns) SX_t
     auto build_mv = [&](int cb, int mb) {
       C* V = MV + mb * mvs;
-      for (int i = tid; i < M; i += BLK) {
+      if (tid >= b_lo && tid < b_lo + M) {
+        const int i = tid - b_lo;
         C a0 = dx[i], am = zero, ap = zero, b0 = dy[i], bm = zero, bp = zero;
 #pragma unroll
         for (int q = 0; q < MX; ++q)
@@ -2343,14 +2414,15 @@ __global__ void __launch_bounds__(BLK) k_solve_mg(const SolveArgs A) {
       }
       av[j] = zero;
     }
-    // G_x, G_y (elements nr .. nr + 2M): thread tid < 2M owns one
-    const bool gown = has_sep && tid < 2 * M;
+    // G_x, G_y (elements nr .. nr + 2M): thread g_lo + q owns element nr + q
+    const bool gown = has_sep && tid >= g_lo;
+    const int gq = tid - g_lo;
     C gy_v = zero, ga_v = zero, gc_v = zero;
-    const int64_t g_gi = gown ? (tid < M ? s.off_gx + tid : s.off_gy + (tid - M)) : 0;
+    const int64_t g_gi = gown ? (gq < M ? s.off_gx + gq : s.off_gy + (gq - M)) : 0;
     if (gown) {
       gy_v = y_g[g_gi];
       gc_v = comp_g[g_gi];
-      B0[nr + tid] = gy_v;
+      B0[nr + gq] = gy_v;
     }
     {
       const C* Dg = reinterpret_cast<const C*>(A.diag) + s.diag_off;
@@ -2467,8 +2539,8 @@ __global__ void __launch_bounds__(BLK) k_solve_mg(const SolveArgs A) {
           }
         }
         if (gown) {
-          const bool isx = tid < M;
-          const int g = isx ? tid : tid - M;
+          const bool isx = gq < M;
+          const int g = isx ? gq : gq - M;
           const C* gs = isx ? gxi : gyi;
           const C lo = g > 0 ? gs[g - 1] : zero, hi = g + 1 < M ? gs[g + 1] : zero;
           C kv;
@@ -2500,7 +2572,7 @@ __global__ void __launch_bounds__(BLK) k_solve_mg(const SolveArgs A) {
             outv = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, gy_v);
             ga_v = caxpy((T)2, kv, ga_v);
           }
-          uout[nr + tid] = outv;
+          uout[nr + gq] = outv;
         }
         // merged vectors of the next stage (its coefficients were evaluated two stages ago)
         build_mv((cbuf + 1) % 3, mbuf ^ 1);
