@@ -2295,11 +2295,13 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 2 : 1) k_solve_mg(const 
     // Thread roles besides the strips, each in warps of its own counted from the top of the
     // block down, so that no warp carries more than one of them on top of its strip (a warp
     // runs its lanes' roles one after the other, and the slowest warp sets every stage's
-    // barrier): the G items (the last 2M threads), the rows of the merged vectors, the stage
-    // coefficients.  With M <= 42 and at most 6 terms they fit below the block's top.
+    // barrier): the G items (the last 2M threads), the column entries of the merged vectors,
+    // their row entries, the stage coefficients.  With M <= 42 and at most 6 terms they fit
+    // below the block's top (BLK = 256).
     const int g_lo = BLK - (has_sep ? 2 * M : 0);
-    const int b_lo = max((g_lo & ~31) - M, 0);
-    const int c_lo = max((b_lo & ~31) - nt, 0);
+    const int bc_lo = max((g_lo & ~31) - M, 0);
+    const int br_lo = max((bc_lo & ~31) - M, 0);
+    const int c_lo = max((br_lo & ~31) - nt, 0);
     // Stage coefficient c_t e(t) of term t.  In FP64, and in FP32 for envelopes other than a
     // Gaussian: the stage time in FP64, the envelope and the product in the state's precision.
     // An FP32 Gaussian costs no FP64 operation (this sits on a warp's path every stage, and
@@ -2372,26 +2374,29 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 2 : 1) k_solve_mg(const 
     // merged vectors from coef[cb] into MV half mb: A0 Am Ap (rows) B0 Bm Bp (columns) SX_t
     auto build_mv = [&](int cb, int mb) {
       C* V = MV + mb * mvs;
-      if (tid >= b_lo && tid < b_lo + M) {
-        const int i = tid - b_lo;
-        C a0 = dx[i], am = zero, ap = zero, b0 = dy[i], bm = zero, bp = zero;
+      if (tid >= br_lo && tid < br_lo + M) {  // row i: A0, Am, Ap and the sandwich rows
+        const int i = tid - br_lo;
+        C a0 = dx[i], am = zero, ap = zero;
 #pragma unroll
         for (int q = 0; q < MX; ++q)
           if (q < nX) {
             const C v = cscale(coef[cb][q], wX[q * M + i]);
             if (s.sX[q] == 0) a0 = cadd(a0, v); else if (s.sX[q] < 0) am = cadd(am, v); else ap = cadd(ap, v);
           }
+        V[i] = a0; V[M + i] = am; V[2 * M + i] = ap;
+#pragma unroll
+        for (int q = 0; q < MS; ++q)
+          if (q < nS) V[(6 + q) * M + i] = cscale(coef[cb][nX + nY + q], wSx[q * M + i]);
+      } else if (tid >= bc_lo && tid < bc_lo + M) {  // column i: B0, Bm, Bp
+        const int i = tid - bc_lo;
+        C b0 = dy[i], bm = zero, bp = zero;
 #pragma unroll
         for (int q = 0; q < MY; ++q)
           if (q < nY) {
             const C v = cscale(coef[cb][nX + q], wY[q * M + i]);
             if (s.sY[q] == 0) b0 = cadd(b0, v); else if (s.sY[q] < 0) bm = cadd(bm, v); else bp = cadd(bp, v);
           }
-        V[i] = a0; V[M + i] = am; V[2 * M + i] = ap;
         V[3 * M + i] = b0; V[4 * M + i] = bm; V[5 * M + i] = bp;
-#pragma unroll
-        for (int q = 0; q < MS; ++q)
-          if (q < nS) V[(6 + q) * M + i] = cscale(coef[cb][nX + nY + q], wSx[q * M + i]);
       }
     };
     // ---- load: state, tables; coefficients of stages (0,1) and (0,2); vectors of (0,1) ----
@@ -2499,19 +2504,23 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 2 : 1) k_solve_mg(const 
               const C up = kk + 1 < M ? uin[c + M] : zero;
               const C ul = cm ? uin[c - 1] : zero;
               const C urr = cp ? uin[c + 1] : zero;
-              C kv = cmul(cadd(V[kk], b0), ucn);
-              kv = cfma(V[M + kk], um, kv);
-              kv = cfma(V[2 * M + kk], up, kv);
-              kv = cfma(bm, ul, kv);
-              kv = cfma(bp, urr, kv);
+              // the row-neighbour, column-neighbour and sandwich parts in independent chains
+              // (short dependency chains; a point and its mirror round alike), then the sum
+              const C kd = cmul(cadd(V[kk], b0), ucn);
+              C kr = cmul(V[M + kk], um);
+              C kc = cmul(bm, ul);
+              kr = cfma(V[2 * M + kk], up, kr);
+              kc = cfma(bp, urr, kc);
+              C ks = zero;
 #pragma unroll
               for (int q = 0; q < MS; ++q)
                 if (q < nS && (!DIAG || !((sdiag >> q) & 1) || kk == cl)) {  // secular projector: k = l only
                   const int xx = kk + ssx[q];
                   const C v = (scol[q] && xx >= 0 && xx < M) ? uin[c + soff[q]] : zero;
                   const C gxv = (has_sep && xx >= 0 && xx < M) ? gxi[xx] : zero;
-                  kv = cfma(V[(6 + q) * M + kk], cadd(cscale(v, sy[q]), cmul(gxv, gyp[q])), kv);
+                  ks = cfma(V[(6 + q) * M + kk], cadd(cscale(v, sy[q]), cmul(gxv, gyp[q])), ks);
                 }
+              const C kv = cadd(cadd(kd, cadd(kr, kc)), ks);
               // RK4 combine (stage sum + compensated state update)
               C outv;
               if (stage == 1) {
