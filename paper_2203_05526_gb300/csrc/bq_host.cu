@@ -1291,7 +1291,9 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
           for (int q = 0; q < m.nY; ++q) mg = mg && std::abs(m.sY[q]) <= 1;
           for (int q = 0; q < m.nS; ++q) mg = mg && std::abs(m.sSx[q]) <= 1 && std::abs(m.sSy[q]) <= 1;
           const int ntot = (m.has_r ? M * M : 0) + (m.has_sep ? 2 * M : 0);
-          mg_max = std::max(mg_max, (size_t)(2 * ntot + 2 * M + 2 * 8 * M) * cs + (size_t)(m.nX + m.nY + 2 * m.nS) * M * rs);
+          const int nr = m.has_r ? M * M : 0;  // stage sum and compensation of the R points
+          mg_max = std::max(mg_max, (size_t)(2 * ntot + 2 * nr + 2 * M + 2 * 8 * M) * cs +
+                                        (size_t)(m.nX + m.nY + 2 * m.nS) * M * rs);
         }
         if (mg && mg_max <= 160 * 1024) { P.solve_mg = 1; P.solve_mg_smem = (int)mg_max; }
       }

@@ -2251,7 +2251,7 @@ __global__ void k_adj_seed(const SysDesc* __restrict__ sys, const EvalGroup* __r
 // stages ahead (triple buffered), the merged vectors one stage ahead (double buffered).
 // ---------------------------------------------------------------------------------------
 template <typename T, int BLK, int RB, int MX, int MY, int MS, bool DIAG>
-__global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 2 : 1) k_solve_mg(const SolveArgs A) {
+__global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 3 : 1) k_solve_mg(const SolveArgs A) {
   using C = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ M1Sys s;
@@ -2280,10 +2280,15 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 2 : 1) k_solve_mg(const 
     const int has_r = s.has_r, has_sep = s.has_sep;
     const int nr = has_r ? M * M : 0;
     const int ntot = nr + (has_sep ? 2 * M : 0);
-    // shared: B0[ntot] | B1[ntot] | dx[M] dy[M] | MV[2][(6 + MS) M] | wX wY wSx wSy (real)
+    // shared: B0[ntot] | B1[ntot] | AS[nr] CS[nr] | dx[M] dy[M] | MV[2][(6 + MS) M] | wX wY wSx
+    // wSy (real).  AS and CS hold the stage sum and the compensation of the R points (each
+    // touched only by the thread that owns the point; in shared memory rather than registers,
+    // so that three CTAs fit an SM in FP32)
     C* B0 = reinterpret_cast<C*>(smem_raw);
     C* B1 = B0 + ntot;
-    C* dx = B1 + ntot;
+    C* AS = B1 + ntot;
+    C* CS = AS + nr;
+    C* dx = CS + nr;
     C* dy = dx + M;
     C* MV = dy + M;
     const int mvs = (6 + MS) * M;
@@ -2405,19 +2410,18 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 2 : 1) k_solve_mg(const 
     const int cl = tid % M, cbk = tid / M;
     const bool owner = has_r && cbk < nb;
     const int k0 = cbk * rb, k1 = owner ? min(M, k0 + rb) : k0;
-    C yv[RB], av[RB], cv[RB];
+    C yv[RB];
     auto gidx_r = [&](int kk) { return s.off_r + (int64_t)kk * M + cl; };
 #pragma unroll
     for (int j = 0; j < RB; ++j) {
       const int kk = k0 + j;
       if (kk < k1) {
         yv[j] = y_g[gidx_r(kk)];
-        cv[j] = comp_g[gidx_r(kk)];
+        CS[kk * M + cl] = comp_g[gidx_r(kk)];
         B0[kk * M + cl] = yv[j];
       } else {
-        yv[j] = zero; cv[j] = zero;
+        yv[j] = zero;
       }
-      av[j] = zero;
     }
     // G_x, G_y (elements nr .. nr + 2M): thread g_lo + q owns element nr + q
     const bool gown = has_sep && tid >= g_lo;
@@ -2523,23 +2527,28 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 2 : 1) k_solve_mg(const 
               const C kv = cadd(cadd(kd, cadd(kr, kc)), ks);
               // RK4 combine (stage sum + compensated state update)
               C outv;
+              C& av = AS[c];
               if (stage == 1) {
                 outv = caxpy(dt * (T)0.5, kv, yv[j]);
-                av[j] = kv;
+                av = kv;
               } else if (stage == 4) {
-                const C sm = cadd(av[j], kv);
+                const C sm = cadd(av, kv);
+                C& cv = CS[c];
+                const C cw = cv;
                 C d, t;
-                d.x = dt * (T)(1.0 / 6.0) * sm.x - cv[j].x;
-                d.y = dt * (T)(1.0 / 6.0) * sm.y - cv[j].y;
+                d.x = dt * (T)(1.0 / 6.0) * sm.x - cw.x;
+                d.y = dt * (T)(1.0 / 6.0) * sm.y - cw.y;
                 t.x = yv[j].x + d.x;
                 t.y = yv[j].y + d.y;
-                cv[j].x = (t.x - yv[j].x) - d.x;
-                cv[j].y = (t.y - yv[j].y) - d.y;
+                C cn;
+                cn.x = (t.x - yv[j].x) - d.x;
+                cn.y = (t.y - yv[j].y) - d.y;
+                cv = cn;
                 yv[j] = t;
                 outv = t;
               } else {
                 outv = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, yv[j]);
-                av[j] = caxpy((T)2, kv, av[j]);
+                av = caxpy((T)2, kv, av);
               }
               uout[kk * M + cl] = outv;
               um = ucn;
@@ -2595,7 +2604,7 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 2 : 1) k_solve_mg(const 
       const int kk = k0 + j;
       if (kk < k1) {
         y_g[gidx_r(kk)] = yv[j];
-        comp_g[gidx_r(kk)] = cv[j];
+        comp_g[gidx_r(kk)] = CS[kk * M + cl];
       }
     }
     if (gown) {
