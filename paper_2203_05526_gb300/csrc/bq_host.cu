@@ -1285,8 +1285,9 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
         for (int i = 0; i < (int)P.m1.size() && mg; ++i) {
           const bq::M1Sys& m = P.m1[i];
           const int M = m.M;
-          const int nb = std::min(256 / M, M);
-          mg = mg && M >= 1 && nb >= 1 && (M + nb - 1) / nb <= 8 && m.nS <= 2;
+          const int np = (M + 1) / 2;  // strips of an even number of rows (k_solve_mg)
+          const int nb = std::min(256 / M, np);
+          mg = mg && M >= 1 && nb >= 1 && 2 * ((np + nb - 1) / nb) <= 8 && m.nS <= 2;
           for (int q = 0; q < m.nX; ++q) mg = mg && std::abs(m.sX[q]) <= 1;
           for (int q = 0; q < m.nY; ++q) mg = mg && std::abs(m.sY[q]) <= 1;
           for (int q = 0; q < m.nS; ++q) mg = mg && std::abs(m.sSx[q]) <= 1 && std::abs(m.sSy[q]) <= 1;

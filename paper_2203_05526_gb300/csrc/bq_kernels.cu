@@ -2405,8 +2405,11 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 3 : 1) k_solve_mg(const 
       }
     };
     // ---- load: state, tables; coefficients of stages (0,1) and (0,2); vectors of (0,1) ----
-    const int nb = min(BLK / M, M);
-    const int rb = (M + nb - 1) / nb;
+    // column strips of rb rows, rb even (the strip loop takes two rows per iteration): nb
+    // strips of the M columns' np = ceil(M / 2) row pairs
+    const int np = (M + 1) / 2;
+    const int nb = min(BLK / M, np);
+    const int rb = 2 * ((np + nb - 1) / nb);
     const int cl = tid % M, cbk = tid / M;
     const bool owner = has_r && cbk < nb;
     const int k0 = cbk * rb, k1 = owner ? min(M, k0 + rb) : k0;
@@ -2498,61 +2501,76 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 3 : 1) k_solve_mg(const 
             soff[q] = ssx[q] * M + ssy[q];
             scol[q] = q < nS && cl + ssy[q] >= 0 && cl + ssy[q] < M;
           }
+          // the stencil of point (kk, cl) at element c from the centre column's values above
+          // (cm_), at (cc_) and below (cd_) it.  The row-neighbour, column-neighbour and
+          // sandwich parts are summed in independent chains (a point and its mirror round
+          // alike), then added.
+          auto point = [&](int kk, int c, C cm_, C cc_, C cd_) {
+            const C ul = cm ? uin[c - 1] : zero;
+            const C urr = cp ? uin[c + 1] : zero;
+            const C kd = cmul(cadd(V[kk], b0), cc_);
+            C kr = cmul(V[M + kk], cm_);
+            C kc = cmul(bm, ul);
+            kr = cfma(V[2 * M + kk], cd_, kr);
+            kc = cfma(bp, urr, kc);
+            C ks = zero;
+#pragma unroll
+            for (int q = 0; q < MS; ++q)
+              if (q < nS && (!DIAG || !((sdiag >> q) & 1) || kk == cl)) {  // secular projector: k = l only
+                const int xx = kk + ssx[q];
+                const C v = (scol[q] && xx >= 0 && xx < M) ? uin[c + soff[q]] : zero;
+                const C gxv = (has_sep && xx >= 0 && xx < M) ? gxi[xx] : zero;
+                ks = cfma(V[(6 + q) * M + kk], cadd(cscale(v, sy[q]), cmul(gxv, gyp[q])), ks);
+              }
+            return cadd(cadd(kd, cadd(kr, kc)), ks);
+          };
+          // RK4 combine of the point at element c with state yj (stage sum and compensated
+          // state update)
+          auto combine = [&](int c, C kv, C& yj) {
+            C outv;
+            C& av = AS[c];
+            if (stage == 1) {
+              outv = caxpy(dt * (T)0.5, kv, yj);
+              av = kv;
+            } else if (stage == 4) {
+              const C sm = cadd(av, kv);
+              C& cv = CS[c];
+              const C cw = cv;
+              C d, t;
+              d.x = dt * (T)(1.0 / 6.0) * sm.x - cw.x;
+              d.y = dt * (T)(1.0 / 6.0) * sm.y - cw.y;
+              t.x = yj.x + d.x;
+              t.y = yj.y + d.y;
+              C cn;
+              cn.x = (t.x - yj.x) - d.x;
+              cn.y = (t.y - yj.y) - d.y;
+              cv = cn;
+              yj = t;
+              outv = t;
+            } else {
+              outv = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, yj);
+              av = caxpy((T)2, kv, av);
+            }
+            uout[c] = outv;
+          };
+          // two rows per iteration, both stencils computed in one block (independent chains
+          // the compiler can interleave); the second row's is computed also where the strip
+          // has ended (its reads stay inside the shared-memory arrays) and then dropped
           C um = k0 > 0 ? uin[(k0 - 1) * M + cl] : zero;
           C ucn = uin[k0 * M + cl];
 #pragma unroll
-          for (int j = 0; j < RB; ++j) {
+          for (int j = 0; j < RB; j += 2) {
             const int kk = k0 + j;
             if (kk < k1) {
               const int c = kk * M + cl;
-              const C up = kk + 1 < M ? uin[c + M] : zero;
-              const C ul = cm ? uin[c - 1] : zero;
-              const C urr = cp ? uin[c + 1] : zero;
-              // the row-neighbour, column-neighbour and sandwich parts in independent chains
-              // (short dependency chains; a point and its mirror round alike), then the sum
-              const C kd = cmul(cadd(V[kk], b0), ucn);
-              C kr = cmul(V[M + kk], um);
-              C kc = cmul(bm, ul);
-              kr = cfma(V[2 * M + kk], up, kr);
-              kc = cfma(bp, urr, kc);
-              C ks = zero;
-#pragma unroll
-              for (int q = 0; q < MS; ++q)
-                if (q < nS && (!DIAG || !((sdiag >> q) & 1) || kk == cl)) {  // secular projector: k = l only
-                  const int xx = kk + ssx[q];
-                  const C v = (scol[q] && xx >= 0 && xx < M) ? uin[c + soff[q]] : zero;
-                  const C gxv = (has_sep && xx >= 0 && xx < M) ? gxi[xx] : zero;
-                  ks = cfma(V[(6 + q) * M + kk], cadd(cscale(v, sy[q]), cmul(gxv, gyp[q])), ks);
-                }
-              const C kv = cadd(cadd(kd, cadd(kr, kc)), ks);
-              // RK4 combine (stage sum + compensated state update)
-              C outv;
-              C& av = AS[c];
-              if (stage == 1) {
-                outv = caxpy(dt * (T)0.5, kv, yv[j]);
-                av = kv;
-              } else if (stage == 4) {
-                const C sm = cadd(av, kv);
-                C& cv = CS[c];
-                const C cw = cv;
-                C d, t;
-                d.x = dt * (T)(1.0 / 6.0) * sm.x - cw.x;
-                d.y = dt * (T)(1.0 / 6.0) * sm.y - cw.y;
-                t.x = yv[j].x + d.x;
-                t.y = yv[j].y + d.y;
-                C cn;
-                cn.x = (t.x - yv[j].x) - d.x;
-                cn.y = (t.y - yv[j].y) - d.y;
-                cv = cn;
-                yv[j] = t;
-                outv = t;
-              } else {
-                outv = caxpy(stage == 2 ? dt * (T)0.5 : dt, kv, yv[j]);
-                av = caxpy((T)2, kv, av);
-              }
-              uout[kk * M + cl] = outv;
-              um = ucn;
-              ucn = up;
+              const C u1 = kk + 1 < M ? uin[c + M] : zero;
+              const C u2 = kk + 2 < M ? uin[c + 2 * M] : zero;
+              const C kvA = point(kk, c, um, ucn, u1);
+              const C kvB = point(kk + 1, c + M, ucn, u1, u2);
+              combine(c, kvA, yv[j]);
+              if (kk + 1 < k1) combine(c + M, kvB, yv[j + 1]);
+              um = u1;
+              ucn = u2;
             }
           }
         }
