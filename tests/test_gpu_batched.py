@@ -1,6 +1,7 @@
 """Batched solving on the GPU: the persistent one-launch solve (bq_solve) and the streamed
 stage kernels over a ragged batch, against the FP64 oracle and against each other."""
 
+import dataclasses
 import functools
 import json
 import os
@@ -10,6 +11,7 @@ import pytest
 
 from oracle import mapping
 from workloads import configs
+from workloads.spec import Channel
 
 from parity import FLOOR32, FLOOR64, compare_mapped_systems, gpu_state, rel_err, scalar_err
 
@@ -64,6 +66,40 @@ def test_solve_equals_streamed_stages(dtype, tol):
     blk_a = a.fock_block(3, dim=3)
     blk_b = b.fock_block(3, dim=3)
     assert rel_err(blk_a, blk_b) <= tol
+
+
+def _mixed_channel_batch(reverse, n=16, steps=60, dt=0.002):
+    """The ragged batch with the drive envelope of instance b of kind b % 4: a Gaussian with a
+    complex amplitude, piecewise constant (three segments), complex exponential, constant.
+    The persistent solve evaluates an FP32 Gaussian on the FP32 pipe (stage time as an FP32
+    pair, forwards or reversed) and the other kinds through the FP64 path."""
+    ps = _ragged_batch(n=n, steps=steps, dt=dt)
+    T = steps * dt
+    out = []
+    for b, p in enumerate(ps):
+        peak = p.channels[0].params[0]
+        ch = [Channel("gauss", (peak, 0.3 * peak, 0.4 * T, 0.3 * T)),
+              Channel("pwc", (0.0, T / 3.0, peak, 0.1, -0.5 * peak, 0.2, 0.3 * peak, -0.1)),
+              Channel("cexp", (peak, -0.2 * peak, 2.0)),
+              Channel("const", (0.5 * peak, 0.1))][b % 4]
+        out.append(dataclasses.replace(p, channels=[ch], reverse_time=reverse))
+    return out
+
+
+@pytest.mark.parametrize("reverse", [True, False])
+def test_solve_f32_every_envelope_kind_matches_stepping_and_oracle(reverse):
+    ps = _mixed_channel_batch(reverse)
+    a = gpu_state(ps, dtype="f32")
+    b = gpu_state(ps, dtype="f32")
+    assert a.solve_eligible() and a.get_tune()["solve_kernel"] == "merged"
+    a.solve(ps[0].dt, ps[0].n_steps)
+    b.step(ps[0].dt, ps[0].n_steps)
+    _sync()
+    ea, eb = a.evaluate(), b.evaluate()
+    assert np.max(np.abs(ea - eb)) <= 1e-6 * max(1.0, np.max(np.abs(eb)))
+    for i, p in enumerate(ps):
+        ref = mapping.rk4_mapped(p).fock_matrix()[0, 0]
+        assert scalar_err(ea[i], ref, FLOOR32) <= 1e-5, (i, p.channels[0].kind, ea[i], ref)
 
 
 def test_solve_split_calls_and_time():
