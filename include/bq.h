@@ -176,15 +176,19 @@ int bq_map(const bq_problem* const* probs, int B, const bq_map_opts* opts, void*
 /* ---- stepping (Eqs. 9a-c / 303a-c, classical RK4) ----------------------------------- */
 
 /* Advances every system of the state by n_steps RK4 steps of size dt (the mapped value
- * of dt must not exceed the bound checked at bq_map).  Four fused stage kernels per step,
- * replayed from a CUDA graph; asynchronous on stream. */
+ * of dt must not exceed the bound checked at bq_map).  Fused stage kernels: on the
+ * pipelined single-mode path the four stages of a step run in one launch (bq_tune
+ * pipe_fused), otherwise one launch per stage; replayed from a CUDA graph; asynchronous on
+ * stream. */
 int bq_step(bq_state* s, double dt, int64_t n_steps, void* stream);
 
 /* Batched persistent solve (one launch for all steps of all systems of the batch; the
  * paper's independent initial conditions, main text after Eq. 13, processed as a work
- * queue): every CTA takes systems from an atomic queue, largest first, keeps the RK4 stage
- * buffers in shared memory and the state in registers for all n_steps steps.  Same
- * arithmetic as bq_step (classical RK4, compensated state update).  Applies to single-mode
+ * queue): every CTA takes systems from an atomic queue, largest first, and keeps the
+ * system on chip for all n_steps steps (the RK4 stage buffers, stage sums and compensation
+ * in shared memory, the state in registers).  The same arithmetic as bq_step (classical
+ * RK4, compensated state update) up to rounding order.  Where bq_autotune measured stepping
+ * faster (bq_tune solve_kernel = BQ_SOLVE_STEP), bq_solve runs bq_step instead.  Applies to single-mode
  * states whose systems hold at most 1792 points (M <= 41 with the separable part) and at
  * most two stencil terms per side; other states are stepped with bq_step.  Asynchronous. */
 int bq_solve(bq_state* s, double dt, int64_t n_steps, void* stream);

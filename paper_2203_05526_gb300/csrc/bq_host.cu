@@ -1279,7 +1279,7 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
         for (auto& e : sz) P.order.push_back(e.second);
         P.solve_smem = (int)solve_max;
         // merged-stencil persistent solve: shifts in {-1, 0, 1}, <= 2 sandwich terms,
-        // column strips of at most 8 rows with 256 threads (M <= 45)
+        // column strips of an even number of rows, at most 8, with 256 threads (M <= 42)
         bool mg = true;
         size_t mg_max = 0;
         for (int i = 0; i < (int)P.m1.size() && mg; ++i) {

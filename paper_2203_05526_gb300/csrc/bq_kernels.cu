@@ -2857,7 +2857,7 @@ static cudaError_t launch_solve_mg_t(const SolveArgs& a, int smem_bytes, int cap
 
 cudaError_t launch_solve_mg(const SolveArgs& a, int dtype, int smem_bytes, int cap_per_sm, cudaStream_t s,
                             int* grid_out) {
-  // 256 threads; column strips of at most 8 rows (M <= 45)
+  // 256 threads; column strips of an even number of rows, at most 8 (M <= 42)
   return dtype == 0 ? launch_solve_mg_t<double, 256, 8>(a, smem_bytes, cap_per_sm, s, grid_out)
                     : launch_solve_mg_t<float, 256, 8>(a, smem_bytes, cap_per_sm, s, grid_out);
 }
