@@ -2245,10 +2245,12 @@ __global__ void k_adj_seed(const SysDesc* __restrict__ sys, const EvalGroup* __r
 // Batched persistent solve, merged-stencil form (single mode, every shift in {-1, 0, 1}):
 // the solve of k_solve_m1 with the per-term stencil replaced by per-row / per-column
 // coefficient vectors (rebuilt for the next stage while the current one is computed) and a
-// column-strip thread mapping with a 3x3 register window of the stage input.  Thread (l, b)
-// owns column l, rows [b rb, (b+1) rb); its state, stage sum and compensation stay in
-// registers for the whole solve.  One barrier per stage; coefficients are evaluated two
-// stages ahead (triple buffered), the merged vectors one stage ahead (double buffered).
+// column-strip thread mapping with a register window of the stage input.  Thread (l, b)
+// owns column l, rows [b rb, (b+1) rb) (rb even: two rows per iteration); the state y of its
+// points stays in registers, their stage sum and compensation in shared memory, for the
+// whole solve (FP32: 80 registers, three CTAs per SM).  One barrier per stage; coefficients
+// are evaluated two stages ahead (triple buffered), the merged vectors one stage ahead
+// (double buffered), each role in warps of its own.
 // ---------------------------------------------------------------------------------------
 template <typename T, int BLK, int RB, int MX, int MY, int MS, bool DIAG>
 __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 3 : 1) k_solve_mg(const SolveArgs A) {
