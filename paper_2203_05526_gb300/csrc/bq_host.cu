@@ -1105,6 +1105,8 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
       // pipelined stage kernel: parameter blocks per problem, records per system
       {
         std::vector<int> poff(B, -1), pbytes(B, 0), pmerged(B, 0), pch0(B, -1), pch1(B, -1);
+        std::vector<int> pgauss(B, 0);   // the problem's only envelope is a Gaussian (FP32 records)
+        std::vector<float> pgpar(5 * (size_t)B, 0.f);
         size_t blk_max = 0, par_max = 0;
         bool pipe_ok = P.total_elems < ((int64_t)1 << 31);  // 32-bit element offsets
         int mmax = 1;
@@ -1179,6 +1181,17 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
             ++n_ch;
           }
           reinterpret_cast<bq::PipeHdr*>(blk.data())->n_ch = n_ch;
+          if (n_ch == 1 && P.chans[chs[0]].kind == BQ_CH_GAUSS) {
+            // the same FP32 values as the block's record (pc.f, pc.c_lo above)
+            const double* cp = P.chpar.data() + P.chans[chs[0]].par_off;
+            float* g = pgpar.data() + 5 * (size_t)b;
+            g[0] = (float)cp[0];
+            g[1] = (float)cp[1];
+            g[2] = (float)(1.0 / (2.0 * cp[3] * cp[3]));
+            g[3] = (float)cp[2];
+            g[4] = (float)(cp[2] - (double)g[3]);
+            pgauss[b] = 1;
+          }
           for (int i = 0; i < M; ++i) put_c(C.diag[i]);
           for (int i = 0; i < M; ++i) put_c(C.diag[M + i]);
           auto put_w = [&](int woff) { for (int i = 0; i < M; ++i) put_r(woff >= 0 ? C.wtab[woff + i] : 1.0); };
@@ -1238,10 +1251,20 @@ static int make_plan(const bq_problem* const* probs, int B, const bq_map_opts* o
           r.nb = std::max(1, std::min(BQ_PIPE_THREADS / r.M, r.M));
           r.rb = (r.M + r.nb - 1) / r.nb;
           r.inv_m = 1.0f / (float)r.M;
-          r.c_re = sd.c_re;
-          r.c_im = sd.c_im;
-          r.w_re = sd.w_re;
-          r.w_im = sd.w_im;
+          if (cs == 16) {
+            r.d.c_re = sd.c_re;
+            r.d.c_im = sd.c_im;
+            r.d.w_re = sd.w_re;
+            r.d.w_im = sd.w_im;
+          } else if (pgauss[sd.prob]) {
+            const float* g = pgpar.data() + 5 * (size_t)sd.prob;
+            r.f.amp_re = g[0];
+            r.f.amp_im = g[1];
+            r.f.k = g[2];
+            r.f.c_hi = g[3];
+            r.f.c_lo = g[4];
+            r.f.gauss = 1;
+          }
           r.w32_re = (float)sd.w_re;
           r.w32_im = (float)sd.w_im;
           r.c32_re = (float)sd.c_re;

@@ -159,8 +159,18 @@ struct __align__(16) PipeRec {
   float w32_re, w32_im;  // the weight below rounded to FP32 (the FP32 kernels' observable)
   float c32_re, c32_im;  // C below rounded to FP32 (the FP32 kernels' G items)
   int sys;          // index of the system (records are ordered by size, largest first)
-  double c_re, c_im;  // separation constant C of the system (Eq. 304)
-  double w_re, w_im;  // weight of the system's initial condition
+  union {
+    struct {
+      double c_re, c_im;  // separation constant C of the system (Eq. 304)
+      double w_re, w_im;  // weight of the system's initial condition
+    } d;                  // FP64 kernels
+    struct {              // FP32 kernels: the problem's drive envelope when it is one Gaussian
+      float amp_re, amp_im, k;  // amplitude, 1 / (2 sigma^2)
+      float c_hi, c_lo;         // centre as an unevaluated FP32 pair
+      int gauss;                // 1: the fields above are set
+      float e_re, e_im;         // its value at the stage time (set in the kernel's copy)
+    } f;
+  };
 };
 // Header of a parameter block (128 B), followed by n_terms PipeCoef records (X, Y, S terms in
 // program order), n_ch PipeChan records, dx[M], dy[M] (complex) and the weight tables

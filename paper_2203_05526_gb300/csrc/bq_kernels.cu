@@ -854,10 +854,31 @@ __device__ __forceinline__ bool pipe_stage(const PipeArgs& A, PipeShared<typenam
     // stage (generic proxy); order those writes before the copies (async proxy)
     fence_proxy_async_global();
   }
+  // FP32: the stage time as an unevaluated FP32 pair, in the threads that load the records
+  float t32[2] = {0.f, 0.f};
+  if (sizeof(T) == 4 && tid < BQ_PIPE_RB) {
+    const double ts = pipe_chan_time(1, tau, STAGE, A.dt, A.horizon, A.reverse);
+    t32[0] = (float)ts;
+    t32[1] = (float)(ts - (double)t32[0]);
+  }
+  // a batch of system records; in FP32 each loading thread also evaluates its system's
+  // Gaussian envelope at the stage time (as pipe_chan_value does, once per system instead of
+  // in every record-building thread ahead of the per-system barrier)
   auto load_batch = [&](int b) {
     if (tid < BQ_PIPE_RB) {
       const int j = b * BQ_PIPE_RB + tid;
-      if (j < nj) recs[b & 1][tid] = A.recs[blockIdx.x + (size_t)j * G];
+      if (j < nj) {
+        PipeRec& rr = recs[b & 1][tid];
+        rr = A.recs[blockIdx.x + (size_t)j * G];
+        if constexpr (sizeof(T) == 4) {
+          if (rr.f.gauss) {
+            const float d = (t32[0] - rr.f.c_hi) + (t32[1] - rr.f.c_lo);
+            const float e = dev_exp<float>(-(d * d) * rr.f.k);
+            rr.f.e_re = rr.f.amp_re * e;
+            rr.f.e_im = rr.f.amp_im * e;
+          }
+        }
+      }
     }
   };
   load_batch(0);
@@ -933,7 +954,7 @@ __device__ __forceinline__ bool pipe_stage(const PipeArgs& A, PipeShared<typenam
       }
       if (rj.r_off >= 0) oc = rj.blk_off + rj.r_off + en.kx * rj.M + en.ly;
       C w;
-      if constexpr (sizeof(T) == 8) w = cmk<C>(rj.w_re, rj.w_im);
+      if constexpr (sizeof(T) == 8) w = cmk<C>(rj.d.w_re, rj.d.w_im);
       else w = make_float2(rj.w32_re, rj.w32_im);
       s_of[lane] = cmul(w, en.f);
     }
@@ -1058,14 +1079,23 @@ __device__ __forceinline__ bool pipe_stage(const PipeArgs& A, PipeShared<typenam
     const C* ugx = u;
     const C* ugy = u + r.gy_off;
     C Cc;
-    if constexpr (sizeof(T) == 8) Cc = cmk<C>(r.c_re, r.c_im);
+    if constexpr (sizeof(T) == 8) Cc = cmk<C>(r.d.c_re, r.d.c_im);
     else Cc = make_float2(r.c32_re, r.c32_im);
     // drive envelopes of the problem's time-dependent terms at this stage's time, from the
     // block (threads that build coefficient records; every thread on the general path)
     C e0 = cmk<C>(1.0, 0.0), e1 = cmk<C>(1.0, 0.0);
     if (!merged || rowb || colb) {
-      if (h.n_ch > 0) e0 = pipe_chan_value<T>(pc[0], A.chpar, s_t[0], s_t[1], sh.s_t32);
-      if (h.n_ch > 1) e1 = pipe_chan_value<T>(pc[1], A.chpar, s_t[0], s_t[1], sh.s_t32);
+      bool pre_e = false;
+      if constexpr (sizeof(T) == 4) {
+        if (r.f.gauss) {  // evaluated with the batch of records
+          e0 = make_float2(r.f.e_re, r.f.e_im);
+          pre_e = true;
+        }
+      }
+      if (!pre_e) {
+        if (h.n_ch > 0) e0 = pipe_chan_value<T>(pc[0], A.chpar, s_t[0], s_t[1], sh.s_t32);
+        if (h.n_ch > 1) e1 = pipe_chan_value<T>(pc[1], A.chpar, s_t[0], s_t[1], sh.s_t32);
+      }
     }
     // stage coefficient of term q: static part times the envelope (or its conjugate)
     auto coef = [&](int q) {
