@@ -2333,8 +2333,8 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? 3 : 1) k_solve_mg(const 
     // block down, so that no warp carries more than one of them on top of its strip (a warp
     // runs its lanes' roles one after the other, and the slowest warp sets every stage's
     // barrier): the G items (the last 2M threads), the column entries of the merged vectors,
-    // their row entries, the stage coefficients.  With M <= 42 and at most 6 terms they fit
-    // below the block's top (BLK = 256).
+    // their row entries, the stage coefficients.  With M <= 42 and at most 10 terms (4 X,
+    // 4 Y, 2 sandwich) they fit below the block's top without overlap (BLK = 256).
     const int g_lo = BLK - (has_sep ? 2 * M : 0);
     const int bc_lo = max((g_lo & ~31) - M, 0);
     const int br_lo = max((bc_lo & ~31) - M, 0);
